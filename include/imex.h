@@ -1,0 +1,192 @@
+/*
+ * imex.h - C-ABI of the GB300 immersed Newmark IMEX library (libimex).
+ *
+ * The library time-steps the scalar wave equation
+ *     rho u'' - div(rho c^2 grad u) = f_t(t) f_x(x)   on a box minus holes,
+ * discretised by the spectral cell method, with the immersed Newmark IMEX
+ * scheme of Faßbender et al., "Implicit-Explicit Time Integration for the
+ * Immersed Wave Equation" (arXiv 2310.14712):
+ *   - explicit DOFs I_d (supported only by uncut cells): central differences on
+ *     the GLL-lumped diagonal mass (Eqs. CDMstep, CDMacc);
+ *   - implicit DOFs I_c (touching a cut cell): trapezoidal Newmark
+ *     (beta = 1/4, gamma = 1/2) with S = M^cc + beta dt^2 K^cc factorised once
+ *     (Fig. TrapCDMIMEX).
+ * Setup runs on the host (C++); every time step runs in CUDA kernels for
+ * sm_103a on the caller's stream.  All arithmetic is IEEE FP64.
+ *
+ * Conventions
+ *   - Every function returns 0 (IMEX_OK) or a negative IMEX_ERR_* code; no C++
+ *     exception crosses the ABI.  imex_last_error() describes the last failure
+ *     of the calling thread.
+ *   - Pointers passed in are owned by the caller and only read during the call.
+ *     The context owns all device memory it allocates (through the optional
+ *     allocator hooks, else cudaMalloc) and releases it in imex_destroy().
+ *   - Fields use the canonical layout: the (n_x p + 1) x (n_y p + 1)
+ *     [x (n_z p + 1)] lattice of GLL nodes of the Cartesian cell grid,
+ *     x fastest, FP64, inactive nodes (only in empty cells) = 0.
+ *   - imex_step() is asynchronous on the given stream; device-side failures
+ *     surface at the next synchronising call.
+ */
+#ifndef IMEX_H
+#define IMEX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IMEX_OK 0
+#define IMEX_ERR_ARG (-1)      /* invalid argument or size */
+#define IMEX_ERR_GEOM (-2)     /* degenerate geometry */
+#define IMEX_ERR_ALLOC (-3)    /* allocation failed */
+#define IMEX_ERR_CUDA (-4)     /* CUDA runtime error */
+#define IMEX_ERR_NOT_SPD (-5)  /* S or M^cc not positive definite */
+#define IMEX_ERR_TIMEOUT (-6)  /* a bounded device wait gave up */
+#define IMEX_ERR_DIVERGED (-7) /* non-finite field values */
+
+/* Source time functions f_t (Sec. Spatial discretization: f(t) = f_t(t) f_x). */
+#define IMEX_WAVELET_RICKER 0      /* (1 - 2 pi^2 f0^2 s^2) exp(-pi^2 f0^2 s^2), s = t - 1/f0 */
+#define IMEX_WAVELET_GAUSS_DERIV 1 /* Eq. ft of the 2D example, t0 = 1/f0, sigma_t = 1/(2 pi f0) */
+#define IMEX_WAVELET_SINE_BURST 2  /* two-cycle sine burst of the 3D example */
+
+/* Field selectors for imex_fields / imex_set_fields (canonical full-grid layout). */
+#define IMEX_FIELD_U 0          /* u_n on all active nodes */
+#define IMEX_FIELD_U_PREV_D 1   /* u^d_{n-1} on I_d (CDM history), 0 elsewhere */
+#define IMEX_FIELD_V_C 2        /* velocity on I_c, 0 elsewhere */
+#define IMEX_FIELD_A_C 3        /* acceleration on I_c, 0 elsewhere */
+#define IMEX_FIELD_FX 4         /* assembled spatial load f_x (read only) */
+#define IMEX_FIELD_MASK_D 5     /* 1.0 on I_d, 0 elsewhere (read only) */
+#define IMEX_FIELD_MASK_C 6     /* 1.0 on I_c, 0 elsewhere (read only) */
+
+typedef struct imex_ctx imex_ctx; /* opaque; owned by the library */
+
+/* Geometry and material (Sec. Spatial discretization).  Read during setup only. */
+typedef struct {
+  int dim;               /* 2 or 3 */
+  double lo[3], hi[3];   /* embedding box Omega */
+  int ncells[3];         /* Cartesian cells per axis (>= 1) */
+  int nholes;            /* holes removed from Omega */
+  const double *holes;   /* nholes x (centre[dim], semi_axes[dim]); axis-aligned ellipsoids */
+  int tree_depth;        /* spacetree depth for cut cells, root = level 0 */
+  double rho;            /* density (> 0) */
+  double c0;             /* wave speed (> 0) */
+  const double *cell_c;  /* optional per-cell wave speed (prod ncells, x fastest) or NULL */
+} imex_mesh;
+
+/* Source: Gaussian bell(s) f_x (Eq. fx) times a wavelet f_t.  nsrc bells are summed. */
+typedef struct {
+  int nsrc;
+  const double *pos;     /* nsrc x dim */
+  double f0;             /* wavelet frequency */
+  double sigma;          /* bell width */
+  double amp;            /* bell amplitude (the paper uses 10) */
+  int wavelet;           /* IMEX_WAVELET_* */
+} imex_source;
+
+/* Optional device allocator (e.g. a PyTorch caching allocator).  NULL -> cudaMalloc. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *user); /* returns a device pointer or NULL */
+  void (*release)(void *ptr, void *user);
+  void *user;
+} imex_alloc;
+
+typedef struct {
+  int64_t n_nodes;       /* canonical lattice size */
+  int64_t n_d, n_c;      /* |I_d|, |I_c| */
+  int64_t n_cut, n_uncut, n_empty;
+  int64_t n_iface;       /* cells contributing to K^c u (cut + uncut touching I_c) */
+  int64_t nnz_L;         /* nonzeros of the Cholesky factor of S */
+  int64_t n_components;  /* connected components of I_c */
+  int64_t n_tree;        /* nested-dissection tree nodes */
+  int64_t max_block;     /* largest supernode */
+  int64_t step;          /* steps taken so far, n */
+  int64_t device_bytes;  /* device memory held by the context */
+  double dt, dt_crit_uncut;
+  double setup_seconds;
+  double residual_S, residual_M; /* relative residuals of a host replay of the device solve */
+} imex_stats;
+
+/*
+ * imex_setup - discretise, partition and factorise; upload to the current device.
+ *   p      : polynomial order of the GLL Lagrange basis (1..8; 2D p <= 8, 3D p <= 4)
+ *   alpha  : fictitious-domain indicator alpha_f in (0, 1] (scales rho, so M, K, f)
+ *   dt     : time step; <= 0 selects 0.9 x the critical step of one uncut cell
+ *            (2 / sqrt(lambda_max(K_e, M_e)), Table criticaltimestepsizes)
+ *   alloc  : optional allocator hooks (NULL -> cudaMalloc)
+ *   out    : receives the context
+ * The initial state is u_0 = 0, v_0 = 0 with the derived CDM history
+ * u^d_{-1} and initial acceleration a^c_0 (Fig. TrapCDMIMEX "Calculation of
+ * initial acceleration"); imex_set_initial() replaces it.
+ * Errors: IMEX_ERR_ARG, IMEX_ERR_GEOM, IMEX_ERR_NOT_SPD, IMEX_ERR_ALLOC, IMEX_ERR_CUDA.
+ */
+int imex_setup(const imex_mesh *mesh, int p, double alpha, double dt, const imex_source *src,
+               const imex_alloc *alloc, imex_ctx **out);
+
+/*
+ * imex_step - advance n >= 0 Newmark IMEX steps (Fig. TrapCDMIMEX), each:
+ *   diagonal CDM step on I_d, prediction on I_c, acceleration calculation
+ *   S a^c_{n+1} = f_t(t_{n+1}) f_x^c - K^c u_pred, correction on I_c.
+ * stream: a cudaStream_t (NULL = legacy default stream).  Asynchronous.
+ * Errors: IMEX_ERR_ARG, IMEX_ERR_CUDA (launch failures).
+ */
+int imex_step(imex_ctx *ctx, int64_t n, void *stream);
+
+/*
+ * imex_fields - copy one field (IMEX_FIELD_*) in canonical layout into dst.
+ *   len          : number of doubles in dst; must equal imex_stats.n_nodes
+ *   dst_on_device: nonzero if dst is device memory (copy stays on the device)
+ * Synchronises the context's last stream.  Errors: IMEX_ERR_ARG, IMEX_ERR_CUDA.
+ */
+int imex_fields(imex_ctx *ctx, int which, double *dst, int64_t len, int dst_on_device);
+
+/*
+ * imex_set_fields - overwrite one state field (U, U_PREV_D, V_C or A_C) from src
+ * (canonical layout, len = n_nodes); entries outside the field's partition are
+ * ignored.  With imex_set_step() this restores a checkpoint exactly.
+ */
+int imex_set_fields(imex_ctx *ctx, int which, const double *src, int64_t len, int src_on_device);
+
+/* imex_set_step - set the step counter n (t_n = n dt). */
+int imex_set_step(imex_ctx *ctx, int64_t n);
+
+/*
+ * imex_set_initial - restart from u_0, v_0 (canonical layout, len = n_nodes) at
+ * n = 0: stores u_0, v^c_0, and computes on the device the CDM history
+ * u^d_{-1} = u^d_0 - dt v^d_0 + dt^2/2 a^d_0 (Taylor start) and a^c_0 from
+ * M^cc a^c_0 = f_t(0) f_x^c - K^c u_0.  v0 may be NULL (zero).
+ */
+int imex_set_initial(imex_ctx *ctx, const double *u0, const double *v0, int64_t len, int on_device);
+
+/* imex_info - sizes, counts and the time step. */
+int imex_info(imex_ctx *ctx, imex_stats *out);
+
+/* imex_last_error - message of the calling thread's last failure ("" if none). */
+const char *imex_last_error(void);
+
+/* imex_destroy - free device and host state; NULL is ignored. */
+void imex_destroy(imex_ctx *ctx);
+
+/*
+ * Host-side building blocks (no GPU needed), for tests of the setup path:
+ * imex_gll_points - GLL points and weights of order p (p+1 values each).
+ * imex_gauss_points - n-point Gauss-Legendre rule.
+ */
+int imex_gll_points(int p, double *x, double *w);
+int imex_gauss_points(int n, double *x, double *w);
+
+/*
+ * imex_host_setup_export - run the host setup only (no GPU) and export the
+ * partition and implicit system for checking: node_class (n_nodes bytes:
+ * 0 inactive, 1 I_d, 2 I_c; may be NULL), fx (n_nodes doubles; may be NULL).
+ * stats receives the counts.  Same arguments as imex_setup.
+ */
+int imex_host_setup_export(const imex_mesh *mesh, int p, double alpha, double dt,
+                           const imex_source *src, uint8_t *node_class, double *fx,
+                           imex_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IMEX_H */

@@ -190,53 +190,88 @@ class Discretization:
     """Assembled SCM system: K, M (CSR, canonical numbering), f_x, partition."""
 
 
+def all_cell_nodes(grid):
+    """Global node ids of every cell, shape (ncells, P^d), cells in flat order,
+    local nodes x fastest (same numbering as Grid.cell_nodes)."""
+    P, dim = grid.p + 1, grid.dim
+    cells = np.array(list(grid.cells()), dtype=np.int64)            # (nc, dim)
+    local = np.array([tuple(reversed(li)) for li in itertools.product(*[range(P)] * dim)],
+                     dtype=np.int64)                                 # (P^d, dim), x fastest
+    ids = np.zeros((len(cells), len(local)), dtype=np.int64)
+    stride = 1
+    for k in range(dim):
+        ids += (cells[:, k:k + 1] * grid.p + local[None, :, k]) * stride
+        stride *= grid.nnodes_axis[k]
+    return cells, ids
+
+
 def discretize(grid, geom, alpha, depth, rho=1.0, c0=1.0, cell_c=None, fx=None):
     """Build the assembled system for all non-empty cells of `grid`.
 
     geom: object with physical(x) and classify_box(lo, hi) (Holes / HalfSpace).
     cell_c: optional per-cell wave speed (flat cell order), default c0 everywhere.
     fx: callable, spatial load f_x(x) for points (n, dim), or None.
+
+    Uncut cells all share one reference element: their K_e (c^2-scaled) and
+    GLL mass are computed once, and their loads f_e = sum_q w_q |J| f(x_q) N(x_q)
+    are evaluated for all uncut cells at once with the same reference values N.
+    Cut cells are integrated one by one on their spacetree.
     """
     dim, p = grid.dim, grid.p
+    cells, nodes = all_cell_nodes(grid)
+    ncell = len(cells)
+    ctype = np.zeros(ncell, dtype=np.int8)
+    for cid in range(ncell):
+        lo, hi = grid.cell_box(cells[cid])
+        ctype[cid] = geom.classify_box(lo, hi)
+    fill = np.where(ctype == UNCUT, 1.0, 0.0)
+    speed = np.full(ncell, float(c0)) if cell_c is None else np.asarray(cell_c, dtype=np.float64)
+    jac = np.prod(grid.h / 2.0)
+    Pd = (p + 1) ** dim
     rows, cols, kv, mv = [], [], [], []
     fglob = np.zeros(grid.nnodes)
-    ctype = np.full(grid.ncell_total, EMPTY, dtype=np.int8)
-    fill = np.zeros(grid.ncell_total)
-    uncut_cache = {}
-    for ci in grid.cells():
-        cid = grid.cell_index(ci)
-        lo, hi = grid.cell_box(ci)
-        t = geom.classify_box(lo, hi)
-        if t == EMPTY:
+
+    # Uncut cells: one reference element, scaled by c_e^2 for the stiffness.
+    uncut = np.flatnonzero(ctype == UNCUT)
+    if len(uncut):
+        Ke1, Me1, _ = uncut_element(p, grid.h, rho, 1.0, np.zeros(dim), None)
+        xg, wg = basis.gauss_points(p + 1)
+        xr, wr = tensor_points(xg, wg, dim)
+        Nq, _ = shape_functions(p, xr, grid.h)                   # (P^d points, P^d basis)
+        ids = nodes[uncut]
+        rr = np.repeat(ids, Pd, axis=1)
+        cc = np.tile(ids, (1, Pd))
+        rows.append(rr.ravel())
+        cols.append(cc.ravel())
+        kv.append((speed[uncut, None] ** 2 * Ke1.ravel()[None, :]).ravel())
+        mv.append(np.tile(Me1.ravel(), len(uncut)))
+        if fx is not None:
+            lo = grid.lo + cells[uncut] * grid.h                     # (n, dim)
+            xq = lo[:, None, :] + (xr[None, :, :] + 1.0) / 2.0 * grid.h
+            fv = fx(xq.reshape(-1, dim)).reshape(len(uncut), -1)     # (n, points)
+            fe = (fv * (wr * jac)[None, :]) @ Nq                     # (n, P^d)
+            np.add.at(fglob, ids.ravel(), fe.ravel())
+
+    # Cut cells: spacetree quadrature, one at a time.
+    for cid in np.flatnonzero(ctype == CUT):
+        lo, hi = grid.cell_box(cells[cid])
+        xr, wr, phys = spacetree_points(geom, lo, hi, depth, p, dim)
+        eta = float(wr[phys].sum() / wr.sum())
+        fill[cid] = eta
+        if eta < EMPTY_FILL:
+            ctype[cid] = EMPTY
             continue
-        c = c0 if cell_c is None else float(cell_c[cid])
-        if t == UNCUT:
-            key = c
-            if key not in uncut_cache:
-                uncut_cache[key] = uncut_element(p, grid.h, rho, c, lo, None)
-            Ke, Me, _ = uncut_cache[key]
-            if fx is not None:
-                _, _, fe = uncut_element(p, grid.h, rho, c, lo, fx)
-            else:
-                fe = np.zeros(Ke.shape[0])
-            fill[cid] = 1.0
-        else:
-            xr, wr, phys = spacetree_points(geom, lo, hi, depth, p, dim)
-            eta = float(wr[phys].sum() / wr.sum())
-            fill[cid] = eta
-            if eta < EMPTY_FILL:
-                continue
-            aq = np.where(phys, 1.0, alpha)
-            fv = fx(lo + (xr + 1.0) / 2.0 * grid.h) if fx is not None else None
-            Ke, Me, fe = element_from_points(p, grid.h, xr, wr, aq, rho, c, fv)
-        ctype[cid] = t
-        ids = grid.cell_nodes(ci)
+        aq = np.where(phys, 1.0, alpha)
+        fv = fx(lo + (xr + 1.0) / 2.0 * grid.h) if fx is not None else None
+        Ke, Me, fe = element_from_points(p, grid.h, xr, wr, aq, rho, float(speed[cid]), fv)
+        ids = nodes[cid]
         rr, cc = np.meshgrid(ids, ids, indexing="ij")
         rows.append(rr.ravel())
         cols.append(cc.ravel())
         kv.append(Ke.ravel())
         mv.append(Me.ravel())
         np.add.at(fglob, ids, fe)
+
     n = grid.nnodes
     if rows:
         r = np.concatenate(rows)
@@ -251,14 +286,8 @@ def discretize(grid, geom, alpha, depth, rho=1.0, c0=1.0, cell_c=None, fx=None):
 
     active = np.zeros(n, dtype=bool)
     is_c = np.zeros(n, dtype=bool)
-    for ci in grid.cells():
-        cid = grid.cell_index(ci)
-        if ctype[cid] == EMPTY:
-            continue
-        ids = grid.cell_nodes(ci)
-        active[ids] = True
-        if ctype[cid] == CUT:
-            is_c[ids] = True
+    active[nodes[ctype != EMPTY].ravel()] = True
+    is_c[nodes[ctype == CUT].ravel()] = True
     d = Discretization()
     d.grid, d.K, d.M, d.fx = grid, K, M, fglob
     d.active, d.is_c = active, is_c

@@ -5,11 +5,12 @@ time stepping in hand-written CUDA for sm_103a) declared in ``include/imex.h``.
 ``paper_2310_14712_gb300.imex`` is the thin ctypes binding; it is imported
 lazily so that ``workloads`` (seeded inputs only) can be used without it.
 """
+import importlib
+
 __all__ = ["workloads", "imex"]
 
 
 def __getattr__(name):
-    if name == "imex":
-        from . import imex as _imex
-        return _imex
+    if name in ("imex", "workloads"):
+        return importlib.import_module("." + name, __name__)
     raise AttributeError(name)

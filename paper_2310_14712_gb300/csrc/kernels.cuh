@@ -1,0 +1,123 @@
+// Time-stepping kernels of the immersed Newmark IMEX method (sm_103a, FP64).
+//
+// One IMEX step (Fig. TrapCDMIMEX) is three launches:
+//   k_explicit   A1 + A2: K^d u_n over uncut cells by sum factorisation on the
+//                tensor grid (exact for every I_d row, whose cells are all
+//                uncut), fused with the CDM update on the lumped mass
+//                (Eqs. CDMacc, CDMstep); extra blocks do the Newmark
+//                prediction on I_c (A3).
+//   k_iface      A4: dense element products K_e u_pred for every cell touching
+//                I_c (stored matrices of cut cells, the uncut-cell matrix
+//                otherwise).
+//   k_solve      A4 gather + A5 + A6: right-hand side f_t(t_{n+1}) f_x^c - K^c
+//                u_pred, forward/backward substitution with the supernodal
+//                nested-dissection Cholesky factor of S, Newmark correction.
+#pragma once
+#include <cstdint>
+
+namespace imex {
+
+constexpr double kNewmarkBeta = 0.25;
+constexpr double kNewmarkGamma = 0.5;
+
+// Source time function f_t (Sec. Spatial discretization, f(t) = f_t(t) f_x).
+__host__ __device__ inline double wavelet_value(int kind, double f0, double t) {
+  const double pi = 3.14159265358979323846;
+  if (kind == 0) {  // Ricker, centred at 1/f0
+    double s = pi * f0 * (t - 1.0 / f0);
+    double a = s * s;
+    return (1.0 - 2.0 * a) * exp(-a);
+  } else if (kind == 1) {  // Eq. ft: derivative of a Gaussian, t0 = 1/f0, sigma_t = 1/(2 pi f0)
+    double t0 = 1.0 / f0, sg = 1.0 / (2.0 * pi * f0);
+    double d = t - t0;
+    return -d / (sqrt(2.0 * pi) * sg * sg * sg) * exp(-d * d / (2.0 * sg * sg));
+  } else {  // two-cycle sine burst of the 3D example
+    const double nc = 2.0;
+    if (t > nc / f0) return 0.0;
+    double s = sin(pi * f0 * t / nc);
+    return sin(2.0 * pi * f0 * t) * s * s;
+  }
+}
+
+// 1D operators of the explicit apply, pre-scaled (2D):
+//   r = sx (M1_y (x) K1_x) u + sy (K1_y (x) M1_x) u
+// kx = sx K1, mx = M1 (x pass), my = M1, ky = sy K1 (y pass); P x P row-major.
+struct Ops2D {
+  double kx[81], mx[81], my[81], ky[81];
+};
+
+struct ExplicitArgs {
+  const double* U;        // u_n (full grid)
+  const double* W;        // u_{n-1} (step) or v_0 (init), full grid
+  double* OUT;            // u_{n+1} on I_d (may alias W); u_pred on I_c
+  const uint8_t* cls;     // node class (0 inactive, 1 I_d, 2 I_c)
+  const double* fx;       // f_x, full grid
+  const double* winv_x;   // 1 / assembled GLL weight along x, per node column
+  const double* winv_y;   // idem along y, scaled by dt-independent 1/(rho |J|)
+  int nx, ny;             // nodes per axis
+  int ncx, ncy;           // cells per axis
+  int ntx, nty;           // tiles per axis
+  double cu, cw, ca;      // out = cu u + cw w + ca minv (ft fx - r)
+  double ft;              // f_t(t_n)
+  // Newmark prediction on I_c (blocks after the tiles); n_c = 0 disables it.
+  int n_c;
+  const int* c_node;
+  const double* v_c;
+  const double* a_c;
+  double dt;
+};
+
+struct IfaceArgs {
+  const double* SRC;      // u_pred (full grid)
+  const int* cell;        // interface cell ids
+  const int* kidx;        // >= 0: index into cutK; -1: uncut form
+  const double* c2;       // multiplier of the uncut form
+  const double* cutK;     // Pd x Pd column-major per cut cell
+  const double* uncutK;   // Pd x Pd column-major
+  double* Y;              // n_iface x Pd products
+  int n_iface;
+  int dim, p, P, Pd;
+  int ncx, ncy;
+  int nx, ny;
+};
+
+struct SolveArgs {
+  // factor
+  const double* vals;
+  const double* invdiag;
+  const int* t_beg;
+  const int* t_end;
+  const int* t_nrows;
+  const int64_t* t_off_diag;
+  const int64_t* t_off_diagT;
+  const int64_t* t_off_rect;
+  const int64_t* t_off_rows;
+  const int64_t* t_off_upd;
+  const int* rows_idx;
+  // schedule
+  const int* level_nodes;
+  const int* comp_level_ptr;
+  const int* comp_level_base;
+  const int* comp_cbeg;
+  const int* comp_cend;
+  // right-hand side
+  const int* contrib_ptr;
+  const int* contrib_pos;
+  const double* Y;
+  const int* fwd_ptr;
+  const int* fwd_pos;
+  double* upd;
+  double* sol;
+  const double* fxc;
+  double ft;              // f_t(t_{n+1}) (step) or f_t(0) (init)
+  // state
+  int mode;               // 0: step with correction; 1: store a^c only
+  const int* c_node;
+  double* U;              // holds u_pred on I_c; receives u^c_{n+1}
+  double* v_c;
+  double* a_c;
+  double dt;
+  int max_block;
+};
+
+}  // namespace imex

@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libimex (include/imex.h): argument marshalling only.
+
+Every step of the time integration runs in the library's CUDA kernels; this
+module converts Python/NumPy/PyTorch arguments to the C structs, passes device
+pointers and streams through, and raises on error codes.  If libimex.so is
+missing it raises ImportError: there is no Python or CPU fallback.
+
+PyTorch supplies device memory (through the allocator hooks) and streams.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libimex.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libimex.so not built ({LIB_PATH}); run "
+                      "`python -m paper_2310_14712_gb300.build` (needs nvcc)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK = 0
+ERR = {-1: "IMEX_ERR_ARG", -2: "IMEX_ERR_GEOM", -3: "IMEX_ERR_ALLOC", -4: "IMEX_ERR_CUDA",
+       -5: "IMEX_ERR_NOT_SPD", -6: "IMEX_ERR_TIMEOUT", -7: "IMEX_ERR_DIVERGED"}
+
+FIELD_U, FIELD_U_PREV_D, FIELD_V_C, FIELD_A_C, FIELD_FX, FIELD_MASK_D, FIELD_MASK_C = range(7)
+FIELDS = {"u": FIELD_U, "u_prev_d": FIELD_U_PREV_D, "v_c": FIELD_V_C, "a_c": FIELD_A_C,
+          "fx": FIELD_FX, "mask_d": FIELD_MASK_D, "mask_c": FIELD_MASK_C}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("ncells", ctypes.c_int * 3), ("nholes", ctypes.c_int), ("holes", _dp),
+                ("tree_depth", ctypes.c_int), ("rho", ctypes.c_double), ("c0", ctypes.c_double),
+                ("cell_c", _dp)]
+
+
+class Source(ctypes.Structure):
+    _fields_ = [("nsrc", ctypes.c_int), ("pos", _dp), ("f0", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("amp", ctypes.c_double), ("wavelet", ctypes.c_int)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Alloc(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("release", _RELEASE_FN), ("user", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "n_nodes", "n_d", "n_c", "n_cut", "n_uncut", "n_empty", "n_iface", "nnz_L",
+        "n_components", "n_tree", "max_block", "step", "device_bytes")] + \
+        [(n, ctypes.c_double) for n in ("dt", "dt_crit_uncut", "setup_seconds", "residual_S", "residual_M")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_lib.imex_setup.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                            ctypes.POINTER(Source), ctypes.POINTER(Alloc), ctypes.POINTER(_vp)]
+_lib.imex_step.argtypes = [_vp, ctypes.c_int64, _vp]
+_lib.imex_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int64, ctypes.c_int]
+_lib.imex_set_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int64, ctypes.c_int]
+_lib.imex_set_step.argtypes = [_vp, ctypes.c_int64]
+_lib.imex_set_initial.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int]
+_lib.imex_info.argtypes = [_vp, ctypes.POINTER(Stats)]
+_lib.imex_last_error.restype = ctypes.c_char_p
+_lib.imex_destroy.argtypes = [_vp]
+_lib.imex_destroy.restype = None
+_lib.imex_gll_points.argtypes = [ctypes.c_int, _dp, _dp]
+_lib.imex_gauss_points.argtypes = [ctypes.c_int, _dp, _dp]
+_lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, ctypes.POINTER(Source), _vp, _dp,
+                                        ctypes.POINTER(Stats)]
+
+# Every symbol include/imex.h declares (checked by the CPU tests).
+EXPORTS = ("imex_setup", "imex_step", "imex_fields", "imex_set_fields", "imex_set_step",
+           "imex_set_initial", "imex_info", "imex_last_error", "imex_destroy", "imex_gll_points",
+           "imex_gauss_points", "imex_host_setup_export")
+
+
+class ImexError(RuntimeError):
+    def __init__(self, code, what):
+        msg = _lib.imex_last_error().decode()
+        super().__init__(f"{what}: {ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code, what):
+    if code != OK:
+        raise ImexError(code, what)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _mesh_source(dim, lo, hi, ncells, depth, holes, rho, c0, cell_c, src_pos, f0, sigma, amp, wavelet):
+    keep = []
+    m = Mesh()
+    m.dim = dim
+    for k in range(3):
+        m.lo[k] = lo[k] if k < dim else 0.0
+        m.hi[k] = hi[k] if k < dim else 1.0
+        m.ncells[k] = ncells[k] if k < dim else 1
+    h = _f64(holes).reshape(-1)
+    keep.append(h)
+    m.nholes = len(h) // (2 * dim)
+    m.holes = h.ctypes.data_as(_dp) if len(h) else None
+    m.tree_depth = depth
+    m.rho = rho
+    m.c0 = c0
+    if cell_c is not None:
+        cc = _f64(cell_c).reshape(-1)
+        keep.append(cc)
+        m.cell_c = cc.ctypes.data_as(_dp)
+    else:
+        m.cell_c = None
+    s = Source()
+    pos = _f64(src_pos).reshape(-1)
+    keep.append(pos)
+    s.nsrc = len(pos) // dim
+    s.pos = pos.ctypes.data_as(_dp)
+    s.f0, s.sigma, s.amp, s.wavelet = f0, sigma, amp, wavelet
+    return m, s, keep
+
+
+def gll_points(p):
+    x = np.zeros(p + 1)
+    w = np.zeros(p + 1)
+    _check(_lib.imex_gll_points(p, x.ctypes.data_as(_dp), w.ctypes.data_as(_dp)), "imex_gll_points")
+    return x, w
+
+
+def gauss_points(n):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    _check(_lib.imex_gauss_points(n, x.ctypes.data_as(_dp), w.ctypes.data_as(_dp)), "imex_gauss_points")
+    return x, w
+
+
+def host_setup_export(dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0, src_sigma,
+                      src_amp=10.0, wavelet=0, rho=1.0, c0=1.0, cell_c=None, dt=0.0, **_):
+    """Host setup only (no GPU): node classes, f_x and counts."""
+    m, s, keep = _mesh_source(dim, lo, hi, ncells, depth, holes, rho, c0, cell_c, src_pos, f0,
+                              src_sigma, src_amp, wavelet)
+    nn = int(np.prod([ncells[k] * p + 1 for k in range(dim)]))
+    cls = np.zeros(nn, dtype=np.uint8)
+    fx = np.zeros(nn)
+    st = Stats()
+    _check(_lib.imex_host_setup_export(ctypes.byref(m), p, alpha, dt, ctypes.byref(s),
+                                       cls.ctypes.data, fx.ctypes.data_as(_dp), ctypes.byref(st)),
+           "imex_host_setup_export")
+    return cls, fx, st.as_dict()
+
+
+class _TorchAllocator:
+    """Device allocations served by PyTorch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.blocks = {}
+        self._alloc = _ALLOC_FN(self._do_alloc)
+        self._release = _RELEASE_FN(self._do_release)
+        self.struct = Alloc(self._alloc, self._release, None)
+
+    def _do_alloc(self, nbytes, user):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:
+            return None
+        self.blocks[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _do_release(self, ptr, user):
+        self.blocks.pop(ptr, None)
+
+
+class Imex:
+    """One immersed Newmark IMEX problem on the current CUDA device.
+
+    Construct from a workload (paper_2310_14712_gb300.workloads.Workload) or
+    from explicit arguments.  Device memory comes from PyTorch.
+    """
+
+    def __init__(self, dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0, src_sigma,
+                 src_amp=10.0, wavelet=0, rho=1.0, c0=1.0, cell_c=None, dt=0.0, use_torch_alloc=True,
+                 **_):
+        import torch
+        self.torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        m, s, keep = _mesh_source(dim, lo, hi, ncells, depth, holes, rho, c0, cell_c, src_pos, f0,
+                                  src_sigma, src_amp, wavelet)
+        self._allocator = _TorchAllocator(self.device) if use_torch_alloc else None
+        ctx = _vp()
+        al = ctypes.byref(self._allocator.struct) if self._allocator else None
+        _check(_lib.imex_setup(ctypes.byref(m), p, alpha, dt, ctypes.byref(s), al, ctypes.byref(ctx)),
+               "imex_setup")
+        self._ctx = ctx
+        self.stats = self.info()
+        self.n_nodes = self.stats["n_nodes"]
+        self.dim = dim
+        self.shape = tuple(reversed([ncells[k] * p + 1 for k in range(dim)]))
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(**w.kwargs(), **kw)
+
+    def _stream(self, stream):
+        if stream is None:
+            stream = self.torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(stream.cuda_stream)
+
+    def step(self, n, stream=None):
+        """Advance n IMEX steps asynchronously on `stream` (default: torch's current stream)."""
+        _check(_lib.imex_step(self._ctx, int(n), self._stream(stream)), "imex_step")
+
+    def fields(self, which="u", out=None):
+        """Copy a field (canonical layout) into `out` (torch CUDA tensor or NumPy array)."""
+        code = FIELDS[which] if isinstance(which, str) else int(which)
+        if out is None:
+            out = self.torch.empty(self.n_nodes, dtype=self.torch.float64, device=self.device)
+        if isinstance(out, np.ndarray):
+            assert out.dtype == np.float64 and out.size == self.n_nodes and out.flags.c_contiguous
+            _check(_lib.imex_fields(self._ctx, code, out.ctypes.data, self.n_nodes, 0), "imex_fields")
+        else:
+            assert out.dtype == self.torch.float64 and out.numel() == self.n_nodes and out.is_contiguous()
+            _check(_lib.imex_fields(self._ctx, code, out.data_ptr(), self.n_nodes, 1 if out.is_cuda else 0),
+                   "imex_fields")
+        return out
+
+    def set_fields(self, which, src):
+        code = FIELDS[which] if isinstance(which, str) else int(which)
+        if isinstance(src, np.ndarray):
+            src = _f64(src)
+            _check(_lib.imex_set_fields(self._ctx, code, src.ctypes.data, self.n_nodes, 0), "imex_set_fields")
+        else:
+            src = src.contiguous()
+            _check(_lib.imex_set_fields(self._ctx, code, src.data_ptr(), self.n_nodes,
+                                        1 if src.is_cuda else 0), "imex_set_fields")
+
+    def set_step(self, n):
+        _check(_lib.imex_set_step(self._ctx, int(n)), "imex_set_step")
+
+    def set_initial(self, u0, v0=None):
+        u0 = _f64(u0)
+        v0p = None
+        if v0 is not None:
+            v0 = _f64(v0)
+            v0p = v0.ctypes.data
+        _check(_lib.imex_set_initial(self._ctx, u0.ctypes.data, v0p, self.n_nodes, 0), "imex_set_initial")
+
+    def info(self):
+        st = Stats()
+        _check(_lib.imex_info(self._ctx, ctypes.byref(st)), "imex_info")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            _lib.imex_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,79 @@
+"""The C-ABI library on the CPU: it loads, exports every symbol include/imex.h
+declares, and its host setup (partition, load vector, counts) agrees with the
+oracle.  No GPU is used here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import basis, pipeline
+from oracle.geometry import UNCUT, CUT, EMPTY
+from paper_2310_14712_gb300 import workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+imex = pytest.importorskip("paper_2310_14712_gb300.imex",
+                           reason="libimex.so not built (python -m paper_2310_14712_gb300.build)")
+
+
+def test_library_exports_every_declared_symbol():
+    header = open(os.path.join(ROOT, "include", "imex.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(imex_\w+)\s*\(", header, re.M))
+    assert declared, "no declarations parsed"
+    assert declared == set(imex.EXPORTS)
+    for name in declared:
+        assert hasattr(imex._lib, name), name
+
+
+@pytest.mark.parametrize("p", range(1, 9))
+def test_host_gll_and_gauss_match_oracle(p):
+    x, w = imex.gll_points(p)
+    xo, wo = basis.gll_points(p)
+    assert np.allclose(x, xo, atol=2e-15, rtol=0) and np.allclose(w, wo, atol=2e-15, rtol=0)
+    x, w = imex.gauss_points(p + 1)
+    xo, wo = basis.gauss_points(p + 1)
+    assert np.allclose(x, xo, atol=2e-15, rtol=0) and np.allclose(w, wo, atol=2e-15, rtol=0)
+
+
+def _compare_partition(w):
+    cls, fx, st = imex.host_setup_export(**w.kwargs())
+    s = pipeline.setup(**w.kwargs())
+    d = s.disc
+    ocls = np.zeros(len(cls), dtype=np.uint8)
+    ocls[d.is_d] = 1
+    ocls[d.is_c] = 2
+    assert np.array_equal(cls, ocls)                                  # index work: bit-exact
+    assert st["n_d"] == d.is_d.sum() and st["n_c"] == d.is_c.sum()
+    assert st["n_cut"] == (d.cell_type == CUT).sum()
+    assert st["n_uncut"] == (d.cell_type == UNCUT).sum()
+    assert st["n_empty"] == (d.cell_type == EMPTY).sum()
+    assert st["dt"] == pytest.approx(s.dt, rel=1e-14)
+    scale = np.abs(d.fx).max()
+    assert np.abs(fx - d.fx).max() <= 1e-13 * scale
+    return st
+
+
+def test_host_setup_plate16_matches_oracle():
+    st = _compare_partition(workloads.plate16())
+    assert st["n_components"] >= 1 and st["nnz_L"] > 0
+
+
+def test_host_setup_small_perforated_plate_matches_oracle():
+    w = workloads.plate256()
+    w.ncells = (32, 16)                      # same holes, coarse grid: fast on the CPU
+    w.p = 3
+    _compare_partition(w)
+
+
+def test_host_setup_rejects_bad_arguments():
+    w = workloads.plate16()
+    kw = w.kwargs()
+    kw["p"] = 0
+    with pytest.raises(imex.ImexError) as e:
+        imex.host_setup_export(**kw)
+    assert e.value.code == -1
+    kw = w.kwargs()
+    kw["alpha"] = 0.0
+    with pytest.raises(imex.ImexError):
+        imex.host_setup_export(**kw)
