@@ -1,0 +1,332 @@
+"""Benchmark of the immersed Newmark IMEX time step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+One bench "step" is one IMEX time step (Fig. TrapCDMIMEX: explicit apply + CDM
+update + prediction, interface products, implicit solve + correction) of the
+256 x 128-cell perforated plate (p = 4, 24 holes, ~480k active DOFs, FP64).
+
+Timing (device, CUDA events on the launching stream):
+  * value: K steps, each timed alone, with the 129 MB L2 flushed (a 256 MB
+    write) between steps, outside the timed events; the sum of the step times
+    is the timed region.  Per-kernel times come from the same events.
+  * warm: K consecutive steps without flushes (the state stays L2-resident,
+    as in a long simulation).
+  * e2e: the public host-I/O call (imex_step_io): every step uploads that
+    step's source samples from pinned host memory and downloads the receiver
+    trace (64 receivers) to pinned host memory; wall-clock time.
+  * cpu_baseline: the CPU oracle (scipy.sparse + SuperLU, one core) on the same
+    workload, a bounded number of steps after its untimed setup.
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the method shards into independent problems; no data-path collective): the
+timed region is bracketed by barriers and the max over ranks is taken.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IMEX DOF-steps/s (FP64)"
+UNIT = "DOF-steps/s"
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop
+# x 2070 MHz (the FP64 rate the probe measured is 1.195 TFLOP/s, 95 % of this).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+L2_FLUSH_BYTES = 256 << 20
+PHASES = ("k_explicit2d", "k_iface", "k_solve")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def algorithmic(st, P, Pd):
+    """Per-launch algorithmic FP64 flops and HBM bytes of each kernel (one step)."""
+    n_d, n_c, n_iface, n_cut, nnz = st["n_d"], st["n_c"], st["n_iface"], st["n_cut"], st["nnz_L"]
+    n_uncut, n_nodes = st["n_uncut"], st["n_nodes"]
+    return {
+        # A1+A2: 4 contractions of P^3 FMAs per uncut cell, ~10 flops per DOF update, prediction.
+        "k_explicit2d": {"flops": 8 * P ** 3 * n_uncut + 10 * n_d + 4 * n_c,
+                         "bytes": 8 * (4 * n_d + 2 * n_c) + n_nodes},
+        # A4: dense P^d x P^d products per interface cell (stored matrices of cut cells).
+        "k_iface": {"flops": 2 * Pd * Pd * n_iface,
+                    "bytes": 8 * (Pd * Pd * n_cut + 2 * Pd * n_iface)},
+        # A5+A6: forward and backward substitution over the factor, rhs gather, correction.
+        "k_solve": {"flops": 4 * nnz + 10 * n_c,
+                    "bytes": 2 * 12 * nnz + 8 * 6 * n_c},
+    }
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (200 ms period)."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def reduce_max(x, ws, device):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_rate(w, nsteps, warmup=1):
+    """Oracle steps per second on the host (setup untimed); returns (rate, n_active, seconds)."""
+    from oracle import pipeline
+    s = pipeline.setup(**w.kwargs())
+    st = s.imex.initial_state()
+    for _ in range(warmup):
+        st = s.imex.step(st)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        st = s.imex.step(st)
+    dt = time.perf_counter() - t0
+    n_act = int(s.disc.active.sum())
+    return n_act * nsteps / dt, n_act, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2310_14712_gb300 import workloads
+    w = workloads.get(args.workload)
+    rate, n_act, secs = cpu_oracle_rate(w, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(w), "parallelism": "single CPU core"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} oracle IMEX steps of {w.name} after {args.warmup} untimed"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_name(w):
+    return (f"{w.name}: [0,2]x[0,1] minus {len(w.holes)} circles, {w.ncells[0]}x{w.ncells[1]} cells, "
+            f"p={w.p}, alpha={w.alpha:g}, quadtree depth {w.depth}, Ricker f0={w.f0:g}")
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    device = torch.device("cuda", torch.cuda.current_device())
+    from paper_2310_14712_gb300 import imex, workloads
+    w = workloads.get(args.workload)
+    g = imex.Imex.from_workload(w)
+    st = g.info()
+    n_act = st["n_d"] + st["n_c"]
+    P = w.p + 1
+    Pd = P ** w.dim
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    # Warm-up (W steps, untimed).
+    g.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # Timed region: K steps, each alone between L2 flushes; per-kernel events.
+    phase = np.zeros(3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(device.index) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ms = g.step_profile(1, stream)
+            phase += np.asarray(ms)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    barrier(ws)
+    t_step_ms = float(phase.sum())
+    t_max_ms = reduce_max(t_step_ms, ws, device)
+    value = ws * n_act * args.steps / (t_max_ms * 1e-3)
+
+    # Warm (continuous) stepping, no flushes.
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.step(args.steps, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    warm_ms = reduce_max(e0.elapsed_time(e1), ws, device)
+
+    # End to end through the host-I/O entry point: source samples in, receiver traces out.
+    ft = torch.from_numpy(workloads.source_signature(args.steps + 1, st["dt"])).pin_memory()
+    rec = torch.from_numpy(workloads.receiver_nodes(w, 64)).pin_memory()
+    traces = torch.zeros((args.steps, len(rec)), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    g.step_io(args.steps, ft, rec, traces, stream)
+    e2e_s = reduce_max(time.perf_counter() - t0, ws, device)
+    e2e = {"value": ws * n_act * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * 8, "d2h_bytes_per_step": 8 * int(len(rec)),
+           "call": "imex_step_io: source samples H2D + 64 receiver samples D2H every step"}
+    assert np.isfinite(traces.numpy()).all()
+
+    alg = algorithmic(st, P, Pd)
+    per_launch_ms = {nm: phase[i] / args.steps for i, nm in enumerate(PHASES)}
+    dom = max(PHASES, key=lambda nm: per_launch_ms[nm])
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    ach_gflops = alg[dom]["flops"] / (per_launch_ms[dom] * 1e-3) / 1e9
+    roof = {"kernel": dom, "bound": "alu", "achieved": ach_gflops / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3,
+            "unit": "TFLOP/s", "frac": ach_gflops / FP64_PEAK_GFLOPS, "traffic": None,
+            "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe)"}
+    kernels = {}
+    for nm in PHASES:
+        t = per_launch_ms[nm] * 1e-3
+        if t <= 0:
+            continue
+        kernels[nm] = {"ms": per_launch_ms[nm], "share": per_launch_ms[nm] / (t_step_ms / args.steps),
+                       "fp64_tflops": alg[nm]["flops"] / t / 1e12,
+                       "fp64_frac": alg[nm]["flops"] / t / 1e9 / FP64_PEAK_GFLOPS,
+                       "hbm_gbs": alg[nm]["bytes"] / t / 1e9,
+                       "hbm_frac": (alg[nm]["bytes"] / t / 1e9 / hbm) if hbm else None}
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(w), "n_active": n_act, "n_d": st["n_d"], "n_c": st["n_c"],
+                   "n_nodes": st["n_nodes"], "components": st["n_components"], "nnz_L": st["nnz_L"],
+                   "dt": st["dt"], "solve_cluster": st["solve_cluster"], "solve_groups": st["solve_groups"],
+                   "solve_smem_bytes": st["solve_smem_bytes"],
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "roofline": roof,
+        "roofline_hbm_view": {"kernel": dom, "achieved": kernels[dom]["hbm_gbs"], "peak": hbm, "unit": "GB/s",
+                              "frac": kernels[dom]["hbm_frac"],
+                              "step_frac": (sum(a["bytes"] for a in alg.values()) / (t_step_ms / args.steps * 1e-3)
+                                            / 1e9 / hbm) if hbm else None},
+        "kernels": kernels,
+        "warm": {"value": ws * n_act * args.steps / (warm_ms * 1e-3), "ms_per_step": warm_ms / args.steps},
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": 3 * args.steps,
+        "setup_seconds": st["setup_seconds"],
+        "wall_seconds_timed_loop": wall,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, n_act_cpu, secs = cpu_oracle_rate(w, args.cpu_steps)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{args.cpu_steps} oracle IMEX steps of {w.name} "
+                                          f"(of {w.steps}), setup untimed, {secs:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="plate256")
+    ap.add_argument("--cpu-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

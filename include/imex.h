@@ -106,6 +106,9 @@ typedef struct {
   double dt, dt_crit_uncut;
   double setup_seconds;
   double residual_S, residual_M; /* relative residuals of a host replay of the device solve */
+  int64_t solve_cluster;   /* CTAs per thread-block cluster of the implicit solve */
+  int64_t solve_groups;    /* clusters (groups of components) per solve launch */
+  int64_t solve_smem_bytes;/* dynamic shared memory per solve CTA (factor resident if large) */
 } imex_stats;
 
 /*
@@ -132,6 +135,28 @@ int imex_setup(const imex_mesh *mesh, int p, double alpha, double dt, const imex
  * Errors: IMEX_ERR_ARG, IMEX_ERR_CUDA (launch failures).
  */
 int imex_step(imex_ctx *ctx, int64_t n, void *stream);
+
+/*
+ * imex_step_profile - imex_step() with CUDA events recorded on `stream` around
+ * each of the three kernels of every step, synchronising after each step.
+ * phase_ms[3] receives the summed device times (ms) of: [0] explicit apply +
+ * CDM update + prediction, [1] interface element products, [2] implicit
+ * solve + correction.  For measurement; results equal imex_step()'s.
+ */
+int imex_step_profile(imex_ctx *ctx, int64_t n, void *stream, double *phase_ms);
+
+/*
+ * imex_step_io - advance n steps like imex_step(), with host I/O every step:
+ *   ft_samples : NULL (use the built-in wavelet) or n+1 host values
+ *                f_t(t_{n0}), ..., f_t(t_{n0+n}) replacing it (e.g. a recorded
+ *                or inverted source signature); step k reads samples k, k+1
+ *   rec_nodes  : nrec canonical node indices (receivers), 0 <= nrec <= 4096
+ *   traces     : n x nrec host array; row k receives u_{n0+k+1} at the receivers
+ * Synchronous (returns when the traces are on the host).
+ * Errors: IMEX_ERR_ARG (bad sizes or node indices), IMEX_ERR_CUDA.
+ */
+int imex_step_io(imex_ctx *ctx, int64_t n, const double *ft_samples, const int64_t *rec_nodes,
+                 int nrec, double *traces, void *stream);
 
 /*
  * imex_fields - copy one field (IMEX_FIELD_*) in canonical layout into dst.

@@ -4,12 +4,14 @@
 // Wave Equation", Sec. "Time integration", Fig. TrapCDMIMEX (Newmark IMEX),
 // Eqs. CDMstep / CDMacc (diagonal CDM step), Eqs. Newmark1/2 (prediction and
 // correction, beta = 1/4, gamma = 1/2), Eqs. Kd / Kc (partitioned stiffness).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -172,7 +174,8 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
     const double r = rr[yo * OX + xo];
     const double u = su[(yo + p) * RX + xo + p];
     const double minv = a.winv_x[gx] * a.winv_y[gy];
-    const double acc = minv * (a.ft * a.fx[g] - r);
+    const double ft = a.ft_dev ? a.ft_dev[0] : a.ft;
+    const double acc = minv * (ft * a.fx[g] - r);
     a.OUT[g] = a.cu * u + a.cw * a.W[g] + a.ca * acc;
   }
 }
@@ -207,91 +210,278 @@ __global__ void __launch_bounds__(kThreads) k_iface(IfaceArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// A4 gather + A5 + A6: one CTA per connected component of I_c.  Tree levels
-// are processed bottom-up (forward L y = rhs) and top-down (backward
-// L^T x = y); the nodes of one level are independent and go to different
-// warps.  All sums run in a fixed order, so the result is deterministic.
+// A4 gather + A5 + A6.  One thread-block cluster per group of connected
+// components of I_c (components are bin-packed into groups by factor size).
+// The nested-dissection tree is walked level by level:
+//   forward   y_t = L_tt^{-1} (rhs_t - sum of descendant updates),  upd_t = L_{rows,t} y_t
+//   backward  x_t = L_tt^{-T} (y_t - L_{rows,t}^T x_rows)
+// Each supernode is handled by one CTA with all its warps: every dense
+// product is split along its inner dimension across the warps (lanes own the
+// output rows), and the warp partials are summed in shared memory in a fixed
+// order, so the result is deterministic.  The nodes of a level go to the
+// cluster's CTAs round-robin, largest first; a cluster barrier (release /
+// acquire at cluster scope) separates levels, and values written by another
+// CTA are read with L1-bypassing loads.
+constexpr int kMaxWidth = 256;       // largest supernode / row set the solve handles
+constexpr int kSolveSmemBudget = 200 * 1024;
+
+// Partial products of a warp over the inner range [j0, j1):
+// part[i] = sum_j M[i si + j sj] v[j] for rows i = lane + 32 r < nrows (R row
+// groups), restricted to j <= i (tri > 0, lower) or j >= i (tri < 0, upper).
+// (si, sj) = (1, ld) reads a column-major block, (ld, 1) its transpose; with
+// an odd ld both are free of shared-memory bank conflicts.
+template <int R>
+__device__ __forceinline__ void warp_partial_r(const double* M, int si, int sj, int nrows,
+                                               const double* v, int j0, int j1, int tri, double* part,
+                                               int lane) {
+  double acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0.0;
+  for (int j = j0; j < j1; ++j) {
+    const double vj = v[j];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = lane + 32 * r;
+      const bool ok = i < nrows && (tri == 0 || (tri > 0 ? j <= i : j >= i));
+      if (ok) acc[r] = fma(M[(size_t)i * si + (size_t)j * sj], vj, acc[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    if (i < nrows) part[i] = acc[r];
+  }
+}
+
+__device__ __forceinline__ void warp_partial(const double* M, int si, int sj, int nrows,
+                                             const double* v, int j0, int j1, int tri, double* part,
+                                             int lane) {
+  switch ((nrows + 31) / 32) {
+    case 0: break;
+    case 1: warp_partial_r<1>(M, si, sj, nrows, v, j0, j1, tri, part, lane); break;
+    case 2: warp_partial_r<2>(M, si, sj, nrows, v, j0, j1, tri, part, lane); break;
+    case 3: warp_partial_r<3>(M, si, sj, nrows, v, j0, j1, tri, part, lane); break;
+    case 4: warp_partial_r<4>(M, si, sj, nrows, v, j0, j1, tri, part, lane); break;
+    default: warp_partial_r<8>(M, si, sj, nrows, v, j0, j1, tri, part, lane); break;
+  }
+}
+
+// Start an asynchronous copy of n 16-byte chunks global -> shared with all
+// threads (cp.async, no register staging); completed by async_copy_wait().
+__device__ __forceinline__ void async_copy_16(void* dst, const void* src, int64_t nchunks) {
+  const char* s8 = reinterpret_cast<const char*>(src);
+  char* d8 = reinterpret_cast<char*>(dst);
+  for (int64_t k = threadIdx.x; k < nchunks; k += blockDim.x) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(d8 + 16 * k);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(s8 + 16 * k) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void async_copy_wait() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+}
+
+template <bool kSmem>
 __global__ void __launch_bounds__(kThreads) k_solve(SolveArgs a) {
-  extern __shared__ double smg[];
-  const int comp = blockIdx.x;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  double* g = smg + warp * a.max_block;
-  const int lb = a.comp_level_base[comp];
-  const int nlev = a.comp_level_base[comp + 1] - lb - 1;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) double smg[];
+  const int CL = (int)cluster.num_blocks();
+  const int crank = (int)cluster.block_rank();
+  const int grp = blockIdx.x / CL;
+  const int cta = grp * CL + crank;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, tid = threadIdx.x;
+  const int W = a.max_width;                  // >= max(max_block, max_rows)
+  double* g = smg;                            // W: gathered rhs / y / h
+  double* y = g + W;                          // W
+  double* xr = y + W;                         // W: ancestor values
+  double* part = xr + W;                      // kWarps x W warp partials
+  double* rhs = part + kWarps * W + a.max_zn;  // this CTA's rows: f_t f_x^c - (K^c u_pred) part
+  double* blob = rhs + a.max_cta_rows;        // this CTA's factor blocks (max_cta_rows is even)
+  const int64_t boff = a.blob_off[cta], blen = a.blob_len[cta];
+  const double* Bf = kSmem ? blob : a.vals + boff;
+  // This CTA's index lists: row pointers and positions of descendant updates,
+  // then the ancestor rows of its nodes (16-byte padded in global memory).
+  int* ilist = reinterpret_cast<int*>(blob + (kSmem ? a.max_blob : 0));
+  const int64_t ioff = a.ilist_off[cta], ilen = a.ilist_len[cta];
+  if (kSmem) async_copy_16(blob, a.vals + boff, blen / 2);
+  async_copy_16(ilist, a.ilist + ioff, ilen / 4);
+  const int lb = a.grp_level_base[grp];
+  const int nlev = a.grp_level_base[grp + 1] - lb - 1;
+  const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
+
+  // Right-hand-side part that does not depend on the tree walk:
+  // f_t(t_{n+1}) f_x^c - K^c u_pred, for every row this CTA owns.
+  for (int l = 0; l < nlev; ++l) {
+    const int qb = a.grp_level_ptr[lb + l], qe = a.grp_level_ptr[lb + l + 1];
+    for (int q = qb + crank; q < qe; q += CL) {
+      const int t = a.grp_level_nodes[q];
+      const int beg = a.t_beg[t], b = a.t_end[t] - beg, slot = a.t_slot[t];
+      for (int i = tid; i < b; i += kThreads) {
+        const int r = beg + i;
+        double s = ft * a.fxc[r];
+        const int c0 = a.contrib_ptr[r], c1 = a.contrib_ptr[r + 1];
+#pragma unroll 4
+        for (int k = c0; k < c1; ++k) s -= a.Y[a.contrib_pos[k]];
+        rhs[slot + i] = s;
+      }
+    }
+  }
+  async_copy_wait();
+  const int* rptr = ilist;                      // row slot -> first position
 
   for (int l = 0; l < nlev; ++l) {
-    const int qb = a.comp_level_ptr[lb + l], qe = a.comp_level_ptr[lb + l + 1];
-    for (int q = qb + warp; q < qe; q += kWarps) {
-      const int t = a.level_nodes[q];
+    const int qb = a.grp_level_ptr[lb + l], qe = a.grp_level_ptr[lb + l + 1];
+    for (int q = qb + crank; q < qe; q += CL) {
+      const int t = a.grp_level_nodes[q];
       const int beg = a.t_beg[t], b = a.t_end[t] - beg, m = a.t_nrows[t];
-      const double* Ld = a.vals + a.t_off_diag[t];
-      const double* Lr = a.vals + a.t_off_rect[t];
-      for (int i = lane; i < b; i += 32) {
-        const int r = beg + i;
-        double s = a.ft * a.fxc[r];
-        for (int k = a.contrib_ptr[r]; k < a.contrib_ptr[r + 1]; ++k) s -= a.Y[a.contrib_pos[k]];
-        for (int k = a.fwd_ptr[r]; k < a.fwd_ptr[r + 1]; ++k) s -= a.upd[a.fwd_pos[k]];
-        g[i] = s;
+      const int ldi = b | 1, ldr = m | 1;            // odd leading dimensions
+      const double* Li = Bf + a.t_foff[t];          // L_tt^{-1}: b x b, column-major, ld ldi
+      const double* L21 = Li + (size_t)ldi * b;      // L_{rows,t}: m x b, column-major, ld ldr
+      if (tid < b) {
+        const int sl = a.t_slot[t] + tid;
+        double s = rhs[sl];
+        const int f0 = rptr[sl], f1 = rptr[sl + 1];
+#pragma unroll 4
+        for (int k = f0; k < f1; ++k) s -= __ldcg(a.upd + ilist[k]);
+        g[tid] = s;
       }
-      __syncwarp();
-      for (int j = 0; j < b; ++j) {
-        const double yj = g[j] * a.invdiag[beg + j];
-        __syncwarp();
-        if (lane == 0) g[j] = yj;
-        for (int i = j + 1 + lane; i < b; i += 32) g[i] = fma(-Ld[i + (size_t)b * j], yj, g[i]);
-        __syncwarp();
+      __syncthreads();
+      {  // y = L_tt^{-1} g  (lower triangular)
+        const int ch = (b + kWarps - 1) / kWarps;
+        const int j0 = min(b, warp * ch), j1 = min(b, j0 + ch);
+        warp_partial(Li, 1, ldi, b, g, j0, j1, 1, part + warp * W, lane);
       }
-      for (int i = lane; i < b; i += 32) a.sol[beg + i] = g[i];
-      double* up = a.upd + a.t_off_upd[t];
-      for (int k = lane; k < m; k += 32) {
+      __syncthreads();
+      if (tid < b) {
         double s = 0.0;
-        for (int j = 0; j < b; ++j) s = fma(Lr[k + (size_t)m * j], g[j], s);
-        up[k] = s;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += part[w * W + tid];
+        y[tid] = s;
+        a.sol[beg + tid] = s;
       }
-      __syncwarp();
+      __syncthreads();
+      if (m > 0) {  // upd = L_{rows,t} y
+        const int ch = (b + kWarps - 1) / kWarps;
+        const int j0 = min(b, warp * ch), j1 = min(b, j0 + ch);
+        warp_partial(L21, 1, ldr, m, y, j0, j1, 0, part + warp * W, lane);
+        __syncthreads();
+        if (tid < m) {
+          double s = 0.0;
+#pragma unroll
+          for (int w = 0; w < kWarps; ++w) s += part[w * W + tid];
+          a.upd[a.t_off_upd[t] + tid] = s;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    cluster.sync();
+  }
+
+  // Dense top of each component (the tree levels above the ones walked):
+  // x_Z = A_Z (rhs_Z - updates from below), A_Z = (L_ZZ L_ZZ^T)^{-1}.
+  {
+    const int cb = a.grp_comp_ptr[grp], ce = a.grp_comp_ptr[grp + 1];
+    for (int ci = cb; ci < ce; ++ci) {
+      const int comp = a.grp_comps[ci], zn = a.zsize[comp], zb = a.zbase[comp];
+      const int ch = (zn + CL - 1) / CL, i0 = min(zn, crank * ch), i1 = min(zn, i0 + ch);
+      for (int i = i0 + tid; i < i1; i += kThreads) {
+        const int r = a.zrow[zb + i];
+        double s = ft * a.fxc[r];
+        for (int k = a.contrib_ptr[r]; k < a.contrib_ptr[r + 1]; ++k) s -= a.Y[a.contrib_pos[k]];
+        for (int k = a.zfwd_ptr[zb + i]; k < a.zfwd_ptr[zb + i + 1]; ++k) s -= __ldcg(a.upd + a.zfwd_pos[k]);
+        a.zg[zb + i] = s;
+      }
+    }
+    cluster.sync();
+    double* zs = part + kWarps * W;   // max_zn doubles
+    for (int ci = cb; ci < ce; ++ci) {
+      const int comp = a.grp_comps[ci], zn = a.zsize[comp], zb = a.zbase[comp];
+      if (zn == 0) continue;
+      for (int j = tid; j < zn; j += kThreads) zs[j] = __ldcg(a.zg + zb + j);
+      __syncthreads();
+      const int ch = (zn + CL - 1) / CL, i0 = min(zn, crank * ch), i1 = min(zn, i0 + ch);
+      const double* A = a.zA + a.zA_off[comp];
+      for (int i = i0 + warp; i < i1; i += kWarps) {
+        const double* Ar = A + (size_t)i * zn;
+        double s0 = 0.0, s1 = 0.0;
+        int j = lane;
+        for (; j + 32 < zn; j += 64) {
+          s0 = fma(__ldg(Ar + j), zs[j], s0);
+          s1 = fma(__ldg(Ar + j + 32), zs[j + 32], s1);
+        }
+        if (j < zn) s0 = fma(__ldg(Ar + j), zs[j], s0);
+        double v = s0 + s1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) a.sol[a.zrow[zb + i]] = v;
+      }
+      __syncthreads();
+    }
+    cluster.sync();
   }
 
   for (int l = nlev - 1; l >= 0; --l) {
-    const int qb = a.comp_level_ptr[lb + l], qe = a.comp_level_ptr[lb + l + 1];
-    for (int q = qb + warp; q < qe; q += kWarps) {
-      const int t = a.level_nodes[q];
+    const int qb = a.grp_level_ptr[lb + l], qe = a.grp_level_ptr[lb + l + 1];
+    for (int q = qb + crank; q < qe; q += CL) {
+      const int t = a.grp_level_nodes[q];
       const int beg = a.t_beg[t], b = a.t_end[t] - beg, m = a.t_nrows[t];
-      const double* LdT = a.vals + a.t_off_diagT[t];
-      const double* Lr = a.vals + a.t_off_rect[t];
-      const int* rows = a.rows_idx + a.t_off_rows[t];
-      for (int j = lane; j < b; j += 32) {
-        double s = a.sol[beg + j];
-        for (int k = 0; k < m; ++k) s = fma(-Lr[k + (size_t)m * j], a.sol[rows[k]], s);
-        g[j] = s;
+      const int ldi = b | 1, ldr = m | 1;
+      const double* Li = Bf + a.t_foff[t];           // read transposed below
+      const double* L21 = Li + (size_t)ldi * b;
+      const int* rows = ilist + a.t_roff[t];
+      if (tid < m) xr[tid] = __ldcg(a.sol + rows[tid]);
+      if (tid < b) y[tid] = __ldcg(a.sol + beg + tid);
+      __syncthreads();
+      if (m > 0) {  // h = y - L_{rows,t}^T x_rows
+        const int ch = (m + kWarps - 1) / kWarps;
+        const int k0 = min(m, warp * ch), k1 = min(m, k0 + ch);
+        warp_partial(L21, ldr, 1, b, xr, k0, k1, 0, part + warp * W, lane);
+        __syncthreads();
+        if (tid < b) {
+          double s = y[tid];
+#pragma unroll
+          for (int w = 0; w < kWarps; ++w) s -= part[w * W + tid];
+          g[tid] = s;
+        }
+      } else if (tid < b) {
+        g[tid] = y[tid];
       }
-      __syncwarp();
-      for (int j = b - 1; j >= 0; --j) {
-        const double xj = g[j] * a.invdiag[beg + j];
-        __syncwarp();
-        if (lane == 0) g[j] = xj;
-        for (int i = lane; i < j; i += 32) g[i] = fma(-LdT[i + (size_t)b * j], xj, g[i]);
-        __syncwarp();
+      __syncthreads();
+      {  // x = L_tt^{-T} h  (upper triangular)
+        const int ch = (b + kWarps - 1) / kWarps;
+        const int j0 = min(b, warp * ch), j1 = min(b, j0 + ch);
+        warp_partial(Li, ldi, 1, b, g, j0, j1, -1, part + warp * W, lane);
       }
-      for (int i = lane; i < b; i += 32) a.sol[beg + i] = g[i];
-      __syncwarp();
+      __syncthreads();
+      if (tid < b) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += part[w * W + tid];
+        a.sol[beg + tid] = s;
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    cluster.sync();
   }
 
   // Correction (Fig. TrapCDMIMEX) or the initial acceleration.
   const double bdt2 = kNewmarkBeta * a.dt * a.dt, gdt = kNewmarkGamma * a.dt,
                g1dt = (1.0 - kNewmarkGamma) * a.dt;
-  for (int r = a.comp_cbeg[comp] + threadIdx.x; r < a.comp_cend[comp]; r += blockDim.x) {
-    const double acc = a.sol[r];
-    if (a.mode == 0) {
-      const int node = a.c_node[r];
-      const double vpred = a.v_c[r] + g1dt * a.a_c[r];
-      a.U[node] = a.U[node] + bdt2 * acc;
-      a.v_c[r] = vpred + gdt * acc;
+  for (int ci = a.grp_comp_ptr[grp]; ci < a.grp_comp_ptr[grp + 1]; ++ci) {
+    const int comp = a.grp_comps[ci];
+    for (int r = a.comp_cbeg[comp] + crank * kThreads + threadIdx.x; r < a.comp_cend[comp];
+         r += CL * kThreads) {
+      const double acc = __ldcg(a.sol + r);
+      if (a.mode == 0) {
+        const int node = a.c_node[r];
+        const double vpred = a.v_c[r] + g1dt * a.a_c[r];
+        a.U[node] = a.U[node] + bdt2 * acc;
+        a.v_c[r] = vpred + gdt * acc;
+      }
+      a.a_c[r] = acc;
     }
-    a.a_c[r] = acc;
   }
 }
 
@@ -322,6 +512,12 @@ __global__ void k_masked(double* dst, const double* src, const uint8_t* cls, int
 __global__ void k_masked_set(double* dst, const double* src, const uint8_t* cls, int64_t n, int want) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g < n && cls[g] == want) dst[g] = src[g];
+}
+
+// Receiver samples: out[k] = u[nodes[k]].
+__global__ void k_gather_nodes(double* out, const double* u, const int64_t* nodes, int n) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = u[nodes[k]];
 }
 
 int tile_cells(int P) {
@@ -364,14 +560,33 @@ struct imex_ctx {
   double *v_c = nullptr, *a_c = nullptr, *fxc = nullptr;
   int *if_cell = nullptr, *if_kidx = nullptr;
   double *if_c2 = nullptr, *cutK = nullptr, *uncutK = nullptr, *Y = nullptr;
-  double *S_vals = nullptr, *S_inv = nullptr, *M_vals = nullptr, *M_inv = nullptr;
   int *t_beg = nullptr, *t_end = nullptr, *t_nrows = nullptr;
   int64_t *t_off_diag = nullptr, *t_off_diagT = nullptr, *t_off_rect = nullptr, *t_off_rows = nullptr,
           *t_off_upd = nullptr;
-  int *rows_idx = nullptr, *level_nodes = nullptr, *comp_level_ptr = nullptr, *comp_level_base = nullptr;
+  int *rows_idx = nullptr, *grp_level_nodes = nullptr, *grp_level_ptr = nullptr, *grp_level_base = nullptr;
+  int *grp_comp_ptr = nullptr, *grp_comps = nullptr;
+  int64_t* t_off_rectT = nullptr;
+  int ngroups = 0;
+  int cluster = 8;
+  int solve_width = 1;
+  int solve_smem_mode = 0;
+  int max_cta_rows = 1;
+  double *S_blob = nullptr, *M_blob = nullptr;
+  int64_t *blob_off = nullptr, *blob_len = nullptr, *t_foff = nullptr;
+  int64_t *ilist_off = nullptr, *ilist_len = nullptr, *t_roff = nullptr;
+  int* ilist = nullptr;
+  int64_t max_blob = 0;
+  int *zsize = nullptr, *zbase = nullptr, *zrow = nullptr, *zfwd_ptr = nullptr, *zfwd_pos = nullptr;
+  int64_t* zA_off = nullptr;
+  double *zA_S = nullptr, *zA_M = nullptr, *zg = nullptr;
+  int max_zn = 0;
+  int* t_slot = nullptr;
   int *comp_cbeg = nullptr, *comp_cend = nullptr;
   int *contrib_ptr = nullptr, *contrib_pos = nullptr, *fwd_ptr = nullptr, *fwd_pos = nullptr;
   double *upd = nullptr, *sol = nullptr;
+  double *ft_buf = nullptr, *rec_buf = nullptr;
+  int64_t* rec_nodes = nullptr;
+  int io_cap = 4096;
   int cur = 0;              // U[cur] holds u_n
   int64_t step = 0;
   cudaStream_t stream = nullptr;
@@ -504,8 +719,26 @@ IfaceArgs iface_args(imex_ctx* c, const double* src) {
 
 SolveArgs solve_args(imex_ctx* c, bool use_S, double ft, int mode, double* Ubuf) {
   SolveArgs sa{};
-  sa.vals = use_S ? c->S_vals : c->M_vals;
-  sa.invdiag = use_S ? c->S_inv : c->M_inv;
+  sa.vals = use_S ? c->S_blob : c->M_blob;
+  sa.blob_off = c->blob_off;
+  sa.blob_len = c->blob_len;
+  sa.t_foff = c->t_foff;
+  sa.t_roff = c->t_roff;
+  sa.ilist = c->ilist;
+  sa.ilist_off = c->ilist_off;
+  sa.ilist_len = c->ilist_len;
+  sa.max_blob = c->max_blob;
+  sa.zsize = c->zsize;
+  sa.zbase = c->zbase;
+  sa.zrow = c->zrow;
+  sa.zA = use_S ? c->zA_S : c->zA_M;
+  sa.zA_off = c->zA_off;
+  sa.zfwd_ptr = c->zfwd_ptr;
+  sa.zfwd_pos = c->zfwd_pos;
+  sa.zg = c->zg;
+  sa.max_zn = c->max_zn;
+  sa.t_slot = c->t_slot;
+  sa.max_cta_rows = c->max_cta_rows;
   sa.t_beg = c->t_beg;
   sa.t_end = c->t_end;
   sa.t_nrows = c->t_nrows;
@@ -514,10 +747,13 @@ SolveArgs solve_args(imex_ctx* c, bool use_S, double ft, int mode, double* Ubuf)
   sa.t_off_rect = c->t_off_rect;
   sa.t_off_rows = c->t_off_rows;
   sa.t_off_upd = c->t_off_upd;
+  sa.t_off_rectT = c->t_off_rectT;
   sa.rows_idx = c->rows_idx;
-  sa.level_nodes = c->level_nodes;
-  sa.comp_level_ptr = c->comp_level_ptr;
-  sa.comp_level_base = c->comp_level_base;
+  sa.grp_level_nodes = c->grp_level_nodes;
+  sa.grp_level_ptr = c->grp_level_ptr;
+  sa.grp_level_base = c->grp_level_base;
+  sa.grp_comp_ptr = c->grp_comp_ptr;
+  sa.grp_comps = c->grp_comps;
   sa.comp_cbeg = c->comp_cbeg;
   sa.comp_cend = c->comp_cend;
   sa.contrib_ptr = c->contrib_ptr;
@@ -535,8 +771,50 @@ SolveArgs solve_args(imex_ctx* c, bool use_S, double ft, int mode, double* Ubuf)
   sa.v_c = c->v_c;
   sa.a_c = c->a_c;
   sa.dt = c->hs.dt;
-  sa.max_block = c->hs.max_block;
+  sa.max_width = c->solve_width;
   return sa;
+}
+
+cudaError_t launch_solve(imex_ctx* c, const SolveArgs& sa, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c->ngroups * c->cluster);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = c->smem_solve;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = c->cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return c->solve_smem_mode ? cudaLaunchKernelEx(&cfg, k_solve<true>, sa)
+                            : cudaLaunchKernelEx(&cfg, k_solve<false>, sa);
+}
+
+// How many clusters of `cl` CTAs with `smem` bytes each the device co-schedules.
+int max_clusters(int cl, size_t smem) {
+  for (auto fn : {k_solve<true>, k_solve<false>}) {
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmemBudget) != cudaSuccess)
+      return 0;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+  cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_solve<true>, &cfg) != cudaSuccess) n = 0;
+  cudaGetLastError();
+  return n;
 }
 
 double ft_at(const HostSetup& hs, int64_t n) {
@@ -562,9 +840,344 @@ int compute_initial(imex_ctx* c, cudaStream_t s) {
     k_iface<<<(nif + kWarps - 1) / kWarps, kThreads, 0, s>>>(ia);
     if (int rc = check_launch("iface (initial)")) return rc;
     SolveArgs sa = solve_args(c, false, ft0, 1, U0);
-    k_solve<<<hs.ncomp, kThreads, c->smem_solve, s>>>(sa);
+    if (cudaError_t e = launch_solve(c, sa, s)) return fail(IMEX_ERR_CUDA, std::string("solve (initial): ") + cudaGetErrorString(e));
     if (int rc = check_launch("solve (initial)")) return rc;
   }
+  return IMEX_OK;
+}
+
+// Static schedule of the implicit solve.  Components are bin-packed into
+// groups (one cluster each), largest factor first onto the lightest group;
+// each level's nodes are sorted by decreasing work and dealt to the cluster's
+// CTAs round-robin.  Every CTA gets one blob holding, in the order it visits
+// them, each of its nodes' [L_tt^{-1} (ld b|1) | L_{rows,t} (ld m|1)],
+// 16-byte aligned, for both S and M^cc.  The plan tries shared-memory budgets
+// from small (more co-resident clusters) to large and keeps the first whose
+// largest blob fits; otherwise the blobs are read from global memory.
+struct SolvePlan {
+  std::vector<int> gl_nodes, gl_ptr, gl_base, gc_ptr, gc_list, slot, ilist;
+  std::vector<int64_t> b_off, b_len, foff, i_off, i_len, roff;
+  std::vector<double> blobS, blobM;
+  int64_t max_blob = 0;
+  // dense top part per component
+  std::vector<int> lz, zsize, zbase, zrow, zfwd_ptr, zfwd_pos;
+  std::vector<int64_t> zA_off;
+  std::vector<double> zA_S, zA_M;
+  int max_zn = 0;
+};
+
+constexpr int kZmax = 400;   // largest dense top block per component
+
+// A_Z = (L_ZZ L_ZZ^T)^{-1} (row-major zn x zn) from the factor blocks of the
+// component's top nodes; Z rows are the nodes' c-indices in ascending order.
+void dense_top(const HostSetup& hs, const Factor& F, const std::vector<int>& znodes,
+               const std::vector<int>& zpos, int zn, std::vector<double>& A) {
+  std::vector<double> L((size_t)zn * zn, 0.0);   // column-major lower
+  for (int t : znodes) {
+    const TreeNode& T = hs.tree[t];
+    const int b = T.end - T.beg, m = (int)T.rows.size();
+    const double* Ld = F.Ld.data() + F.ld_off[t];
+    const double* L21 = F.vals.data() + T.off_rect;
+    for (int j = 0; j < b; ++j) {
+      const int cj = zpos[T.beg + j];
+      for (int i = j; i < b; ++i) L[zpos[T.beg + i] + (size_t)zn * cj] = Ld[i + (size_t)b * j];
+      for (int i = 0; i < m; ++i) L[zpos[T.rows[i]] + (size_t)zn * cj] = L21[i + (size_t)m * j];
+    }
+  }
+  std::vector<double> Mi((size_t)zn * zn, 0.0);  // L^{-1}, column-major lower
+  for (int k = 0; k < zn; ++k)
+    for (int i = k; i < zn; ++i) {
+      double sum = (i == k) ? 1.0 : 0.0;
+      for (int q = k; q < i; ++q) sum -= L[i + (size_t)zn * q] * Mi[q + (size_t)zn * k];
+      Mi[i + (size_t)zn * k] = sum / L[i + (size_t)zn * i];
+    }
+  A.assign((size_t)zn * zn, 0.0);
+  for (int i = 0; i < zn; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double sum = 0.0;
+      for (int k = i; k < zn; ++k) sum += Mi[k + (size_t)zn * i] * Mi[k + (size_t)zn * j];
+      A[(size_t)i * zn + j] = sum;
+      A[(size_t)j * zn + i] = sum;
+    }
+}
+
+int plan_solve(imex_ctx* c, SolvePlan& best) {
+  const HostSetup& hs = c->hs;
+  const int64_t nt = (int64_t)hs.tree.size();
+  auto node_work = [&](int t) {
+    const TreeNode& T = hs.tree[t];
+    const int64_t b = T.end - T.beg, m = (int64_t)T.rows.size();
+    return b * b + m * b;
+  };
+  std::vector<int64_t> cw(hs.ncomp, 0);
+  for (int k = 0; k < hs.ncomp; ++k)
+    for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t) cw[k] += node_work(t);
+  // Split level of each component: nodes at level >= lz form the dense top part.
+  std::vector<int> lz(hs.ncomp, 1), zsize(hs.ncomp, 0), zbase(hs.ncomp, 0), zrow, zpos(hs.n_c, -1);
+  std::vector<int64_t> zA_off(hs.ncomp, 0);
+  std::vector<double> zA_S, zA_M;
+  int max_zn = 0;
+  {
+    for (int k = 0; k < hs.ncomp; ++k) {
+      int maxlev = 0;
+      for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t) maxlev = std::max(maxlev, hs.tree[t].level);
+      int L = maxlev + 1;
+      for (int cand = 1; cand <= maxlev + 1; ++cand) {
+        int z = 0;
+        for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t)
+          if (hs.tree[t].level >= cand) z += hs.tree[t].end - hs.tree[t].beg;
+        if (z <= kZmax) { L = cand; break; }
+      }
+      lz[k] = L;
+      std::vector<int> znodes;
+      for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t)
+        if (hs.tree[t].level >= L) znodes.push_back(t);
+      zbase[k] = (int)zrow.size();
+      for (int t : znodes)
+        for (int r = hs.tree[t].beg; r < hs.tree[t].end; ++r) zrow.push_back(r);
+      std::sort(zrow.begin() + zbase[k], zrow.end());
+      zsize[k] = (int)zrow.size() - zbase[k];
+      max_zn = std::max(max_zn, zsize[k]);
+      for (int i = 0; i < zsize[k]; ++i) zpos[zrow[zbase[k] + i]] = i;
+      zA_off[k] = (int64_t)zA_S.size();
+      if (zsize[k] > 0) {
+        std::vector<double> A;
+        dense_top(hs, hs.S, znodes, zpos, zsize[k], A);
+        zA_S.insert(zA_S.end(), A.begin(), A.end());
+        dense_top(hs, hs.Mcc, znodes, zpos, zsize[k], A);
+        zA_M.insert(zA_M.end(), A.begin(), A.end());
+      }
+    }
+  }
+  // Updates into the dense rows from the walked levels only.
+  std::vector<int> upd_owner(std::max<int64_t>(hs.upd_size, 1), -1);
+  for (size_t t = 0; t < hs.tree.size(); ++t)
+    for (size_t i = 0; i < hs.tree[t].rows.size(); ++i) upd_owner[hs.tree[t].off_upd + i] = (int)t;
+  auto is_top = [&](int t) { return hs.tree[t].level >= lz[hs.tree[t].comp]; };
+  std::vector<int> zfwd_ptr(1, 0), zfwd_pos;
+  for (int r : zrow) {
+    for (int k = hs.fwd_ptr[r]; k < hs.fwd_ptr[r + 1]; ++k)
+      if (!is_top(upd_owner[hs.fwd_pos[k]])) zfwd_pos.push_back(hs.fwd_pos[k]);
+    zfwd_ptr.push_back((int)zfwd_pos.size());
+  }
+  // Check the split algorithm (walked levels + dense top) against the tree solve.
+  for (const Factor* F : {&hs.S, &hs.Mcc}) {
+    const std::vector<double>& zA = (F == &hs.S) ? zA_S : zA_M;
+    std::vector<double> b(hs.n_c), xref, x(hs.n_c, 0.0), upd(std::max<int64_t>(hs.upd_size, 1), 0.0), g, y;
+    for (int64_t i = 0; i < hs.n_c; ++i) b[i] = std::cos(0.71 * i + 0.3) + 0.25;
+    xref = b;
+    replay_solve(hs, *F, xref);
+    std::vector<std::vector<int>> byl;
+    for (size_t t = 0; t < hs.tree.size(); ++t)
+      if (!is_top((int)t)) {
+        if ((int)byl.size() <= hs.tree[t].level) byl.resize(hs.tree[t].level + 1);
+        byl[hs.tree[t].level].push_back((int)t);
+      }
+    for (size_t l = 0; l < byl.size(); ++l)
+      for (int t : byl[l]) {
+        const TreeNode& T = hs.tree[t];
+        const int bsz = T.end - T.beg, m = (int)T.rows.size();
+        g.assign(bsz, 0.0);
+        y.assign(bsz, 0.0);
+        for (int i = 0; i < bsz; ++i) {
+          const int r = T.beg + i;
+          double sum = b[r];
+          for (int k = hs.fwd_ptr[r]; k < hs.fwd_ptr[r + 1]; ++k) sum -= upd[hs.fwd_pos[k]];
+          g[i] = sum;
+        }
+        for (int i = 0; i < bsz; ++i) {
+          double sum = 0.0;
+          for (int j = 0; j <= i; ++j) sum += F->vals[T.off_diag + i + (int64_t)bsz * j] * g[j];
+          y[i] = sum;
+          x[T.beg + i] = sum;
+        }
+        for (int k = 0; k < m; ++k) {
+          double sum = 0.0;
+          for (int j = 0; j < bsz; ++j) sum += F->vals[T.off_rect + k + (int64_t)m * j] * y[j];
+          upd[T.off_upd + k] = sum;
+        }
+      }
+    for (int k = 0; k < hs.ncomp; ++k) {
+      const int zn = zsize[k], zb = zbase[k];
+      std::vector<double> zg(zn);
+      for (int i = 0; i < zn; ++i) {
+        double sum = b[zrow[zb + i]];
+        for (int q = zfwd_ptr[zb + i]; q < zfwd_ptr[zb + i + 1]; ++q) sum -= upd[zfwd_pos[q]];
+        zg[i] = sum;
+      }
+      for (int i = 0; i < zn; ++i) {
+        double sum = 0.0;
+        for (int j = 0; j < zn; ++j) sum += zA[zA_off[k] + (int64_t)i * zn + j] * zg[j];
+        x[zrow[zb + i]] = sum;
+      }
+    }
+    for (int l = (int)byl.size() - 1; l >= 0; --l)
+      for (int t : byl[l]) {
+        const TreeNode& T = hs.tree[t];
+        const int bsz = T.end - T.beg, m = (int)T.rows.size();
+        g.assign(bsz, 0.0);
+        for (int j = 0; j < bsz; ++j) {
+          double sum = x[T.beg + j];
+          for (int k = 0; k < m; ++k) sum -= F->vals[T.off_rect + k + (int64_t)m * j] * x[T.rows[k]];
+          g[j] = sum;
+        }
+        for (int i = 0; i < bsz; ++i) {
+          double sum = 0.0;
+          for (int j = i; j < bsz; ++j) sum += F->vals[T.off_diag + j + (int64_t)bsz * i] * g[j];
+          x[T.beg + i] = sum;
+        }
+      }
+    double dn = 0.0, rn = 0.0;
+    for (int64_t i = 0; i < hs.n_c; ++i) {
+      dn += (x[i] - xref[i]) * (x[i] - xref[i]);
+      rn += xref[i] * xref[i];
+    }
+    if (!(std::sqrt(dn / std::max(rn, 1e-300)) < 1e-9))
+      return fail(IMEX_ERR_NOT_SPD, "dense top-level solve disagrees with the tree solve");
+  }
+  const size_t vec_doubles = (size_t)(3 + kWarps) * c->solve_width + (size_t)((max_zn + 1) / 2) * 2;
+  bool have = false;
+  for (int cl : {16, 8}) {
+    for (int budget_kb : {64, 96, 128, 160, 200}) {
+      const size_t budget = (size_t)budget_kb * 1024;
+      const int nclu = max_clusters(cl, budget);
+      if (nclu <= 0) continue;
+      SolvePlan P;
+      const int ngroups = std::max(1, std::min(hs.ncomp, nclu));
+      std::vector<int> order(hs.ncomp);
+      std::iota(order.begin(), order.end(), 0);
+      std::sort(order.begin(), order.end(), [&](int x, int y) { return cw[x] > cw[y]; });
+      std::vector<std::vector<int>> members(ngroups);
+      std::vector<int64_t> load(ngroups, 0);
+      for (int k : order) {
+        int gsel = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        members[gsel].push_back(k);
+        load[gsel] += cw[k];
+      }
+      P.gc_ptr.push_back(0);
+      for (int gi = 0; gi < ngroups; ++gi) {
+        int nl = 0;
+        for (int k : members[gi]) {
+          P.gc_list.push_back(k);
+          for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t) nl = std::max(nl, hs.tree[t].level + 1);
+        }
+        P.gc_ptr.push_back((int)P.gc_list.size());
+        std::vector<std::vector<int>> byl(nl);
+        for (int k : members[gi])
+          for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t)
+            if (!is_top(t)) byl[hs.tree[t].level].push_back(t);
+        while (!byl.empty() && byl.back().empty()) byl.pop_back();
+        nl = (int)byl.size();
+        P.gl_base.push_back((int)P.gl_ptr.size());
+        P.gl_ptr.push_back((int)P.gl_nodes.size());
+        for (int l = 0; l < nl; ++l) {
+          std::sort(byl[l].begin(), byl[l].end(), [&](int x, int y) { return node_work(x) > node_work(y); });
+          P.gl_nodes.insert(P.gl_nodes.end(), byl[l].begin(), byl[l].end());
+          P.gl_ptr.push_back((int)P.gl_nodes.size());
+        }
+      }
+      P.gl_base.push_back((int)P.gl_ptr.size());
+      P.b_off.assign((size_t)ngroups * cl, 0);
+      P.b_len.assign((size_t)ngroups * cl, 0);
+      P.foff.assign(nt, 0);
+      P.slot.assign(nt, 0);
+      P.roff.assign(nt, 0);
+      P.i_off.assign((size_t)ngroups * cl, 0);
+      P.i_len.assign((size_t)ngroups * cl, 0);
+      int max_rows = 2;
+      int64_t max_blob = 0, max_ilist = 0;
+      for (int gi = 0; gi < ngroups; ++gi) {
+        const int nlv = P.gl_base[gi + 1] - P.gl_base[gi] - 1;
+        for (int rk = 0; rk < cl; ++rk) {
+          const int cta = gi * cl + rk;
+          int rows_here = 0;
+          if (P.blobS.size() % 2) { P.blobS.push_back(0.0); P.blobM.push_back(0.0); }
+          P.b_off[cta] = (int64_t)P.blobS.size();
+          int64_t local = 0;
+          for (int l = 0; l < nlv; ++l) {
+            const int qb = P.gl_ptr[P.gl_base[gi] + l], qe = P.gl_ptr[P.gl_base[gi] + l + 1];
+            for (int q = qb + rk; q < qe; q += cl) {
+              const int t = P.gl_nodes[q];
+              const TreeNode& T = hs.tree[t];
+              const int b = T.end - T.beg, m = (int)T.rows.size();
+              const int ldi = b | 1, ldr = m | 1;
+              P.slot[t] = rows_here;
+              rows_here += b;
+              P.foff[t] = local;
+              for (const Factor* F : {&hs.S, &hs.Mcc}) {
+                std::vector<double>& out = (F == &hs.S) ? P.blobS : P.blobM;
+                const double* Li = F->vals.data() + T.off_diag;
+                const double* L21 = F->vals.data() + T.off_rect;
+                for (int j = 0; j < b; ++j)
+                  for (int i = 0; i < ldi; ++i) out.push_back(i < b ? Li[i + (size_t)b * j] : 0.0);
+                for (int j = 0; j < b; ++j)
+                  for (int i = 0; i < ldr; ++i) out.push_back(i < m ? L21[i + (size_t)m * j] : 0.0);
+              }
+              local += (int64_t)ldi * b + (int64_t)ldr * b;
+            }
+          }
+          if (local % 2) { P.blobS.push_back(0.0); P.blobM.push_back(0.0); ++local; }
+          P.b_len[cta] = local;
+          max_blob = std::max(max_blob, local);
+          max_rows = std::max(max_rows, rows_here + (rows_here & 1));
+          // Index lists of this CTA: [row ptr (rows_here + 1) | positions | ancestor rows].
+          std::vector<int> mine;
+          for (int l = 0; l < nlv; ++l) {
+            const int qb = P.gl_ptr[P.gl_base[gi] + l], qe = P.gl_ptr[P.gl_base[gi] + l + 1];
+            for (int q = qb + rk; q < qe; q += cl) mine.push_back(P.gl_nodes[q]);
+          }
+          std::vector<int> rp(1, 0), pos, anc;
+          for (int t : mine)
+            for (int r = hs.tree[t].beg; r < hs.tree[t].end; ++r) {
+              for (int k = hs.fwd_ptr[r]; k < hs.fwd_ptr[r + 1]; ++k) pos.push_back(hs.fwd_pos[k]);
+              rp.push_back((int)pos.size());
+            }
+          const int npos_base = (int)rp.size();
+          for (int& v : rp) v += npos_base;            // positions follow the row pointers
+          std::vector<int> lst = rp;
+          lst.insert(lst.end(), pos.begin(), pos.end());
+          for (int t : mine) {
+            P.roff[t] = (int64_t)lst.size();
+            lst.insert(lst.end(), hs.tree[t].rows.begin(), hs.tree[t].rows.end());
+          }
+          while (lst.size() % 4) lst.push_back(0);
+          while (P.ilist.size() % 4) P.ilist.push_back(0);
+          P.i_off[cta] = (int64_t)P.ilist.size();
+          P.i_len[cta] = (int64_t)lst.size();
+          P.ilist.insert(P.ilist.end(), lst.begin(), lst.end());
+          max_ilist = std::max(max_ilist, (int64_t)lst.size());
+        }
+      }
+      const size_t ibytes = (size_t)max_ilist * sizeof(int);
+      const size_t need = (vec_doubles + (size_t)max_rows + (size_t)max_blob) * sizeof(double) + ibytes;
+      const bool fits = need <= budget;
+      P.max_blob = max_blob;
+      P.lz = lz;
+      P.zsize = zsize;
+      P.zbase = zbase;
+      P.zrow = zrow;
+      P.zfwd_ptr = zfwd_ptr;
+      P.zfwd_pos = zfwd_pos;
+      P.zA_off = zA_off;
+      P.max_zn = max_zn;
+      if (fits || (!have && budget_kb == 200 && cl == 8)) {
+        c->max_zn = ((max_zn + 1) / 2) * 2;
+        c->cluster = cl;
+        c->ngroups = ngroups;
+        c->max_cta_rows = max_rows;
+        c->solve_smem_mode = fits ? 1 : 0;
+        c->smem_solve = fits ? need : (vec_doubles + (size_t)max_rows) * sizeof(double) + ibytes;
+        c->max_blob = fits ? max_blob : 0;
+        P.zA_S = zA_S;
+        P.zA_M = zA_M;
+        best = std::move(P);
+        have = true;
+        if (fits) return IMEX_OK;
+      }
+    }
+    if (have && c->solve_smem_mode) break;
+  }
+  if (!have) return fail(IMEX_ERR_CUDA, "no thread-block cluster configuration fits the solve kernel");
   return IMEX_OK;
 }
 
@@ -687,9 +1300,9 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       return fail(setup_error_code(err), err);
     }
     HostSetup& hs = c->hs;
-    if (hs.max_block > 1024) {
+    if (hs.max_block > kMaxWidth || hs.max_rows > kMaxWidth) {
       delete c;
-      return fail(IMEX_ERR_ARG, "supernode too large for the device solve");
+      return fail(IMEX_ERR_ARG, "supernode too large for the device solve (max 256)");
     }
     if (cudaGetDevice(&c->device) != cudaSuccess) {
       delete c;
@@ -701,7 +1314,8 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     c->ntx = (hs.nn[0] + OX - 1) / OX;
     c->nty = (hs.nn[1] + OX - 1) / OX;
     c->smem_explicit = explicit_smem_doubles(P, c->TC) * sizeof(double);
-    c->smem_solve = (size_t)kWarps * std::max(1, hs.max_block) * sizeof(double);
+    c->solve_width = std::max(1, std::max(hs.max_block, hs.max_rows));
+    c->solve_width += c->solve_width % 2;
 
     // Operators of the explicit apply: sx = rho c^2 h_y / h_x, sy = rho c^2 h_x / h_y.
     const double sx = pb.rho * pb.c0 * pb.c0 * hs.h[1] / hs.h[0];
@@ -752,6 +1366,13 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       ccb[k] = hs.tree[hs.comp_tree_ptr[k]].beg;
       cce[k] = hs.tree[hs.comp_tree_ptr[k + 1] - 1].end;
     }
+    std::vector<int64_t> off_rT(nt);
+    for (int64_t t = 0; t < nt; ++t) off_rT[t] = hs.tree[t].off_rectT;
+    SolvePlan plan;
+    if (int rc = plan_solve(c, plan)) {
+      imex_destroy(c);
+      return rc;
+    }
     const int64_t nif = (int64_t)hs.if_cell.size();
 
     Arena ar;
@@ -773,10 +1394,25 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->cutK, std::max<size_t>(hs.cutK.size(), 1));
     ar.add(&c->uncutK, hs.uncutK.size());
     ar.add(&c->Y, std::max<int64_t>(nif * hs.Pd, 1));
-    ar.add(&c->S_vals, std::max<size_t>(hs.S.vals.size(), 1));
-    ar.add(&c->S_inv, std::max<int64_t>(nc, 1));
-    ar.add(&c->M_vals, std::max<size_t>(hs.Mcc.vals.size(), 1));
-    ar.add(&c->M_inv, std::max<int64_t>(nc, 1));
+    ar.add(&c->S_blob, std::max<size_t>(plan.blobS.size(), 2));
+    ar.add(&c->M_blob, std::max<size_t>(plan.blobM.size(), 2));
+    ar.add(&c->blob_off, std::max<size_t>(plan.b_off.size(), 1));
+    ar.add(&c->blob_len, std::max<size_t>(plan.b_len.size(), 1));
+    ar.add(&c->t_foff, std::max<int64_t>(nt, 1));
+    ar.add(&c->t_slot, std::max<int64_t>(nt, 1));
+    ar.add(&c->t_roff, std::max<int64_t>(nt, 1));
+    ar.add(&c->ilist, std::max<size_t>(plan.ilist.size(), 4));
+    ar.add(&c->ilist_off, std::max<size_t>(plan.i_off.size(), 1));
+    ar.add(&c->ilist_len, std::max<size_t>(plan.i_len.size(), 1));
+    ar.add(&c->zsize, std::max<size_t>(plan.zsize.size(), 1));
+    ar.add(&c->zbase, std::max<size_t>(plan.zbase.size(), 1));
+    ar.add(&c->zrow, std::max<size_t>(plan.zrow.size(), 1));
+    ar.add(&c->zfwd_ptr, std::max<size_t>(plan.zfwd_ptr.size(), 1));
+    ar.add(&c->zfwd_pos, std::max<size_t>(plan.zfwd_pos.size(), 1));
+    ar.add(&c->zA_off, std::max<size_t>(plan.zA_off.size(), 1));
+    ar.add(&c->zA_S, std::max<size_t>(plan.zA_S.size(), 1));
+    ar.add(&c->zA_M, std::max<size_t>(plan.zA_M.size(), 1));
+    ar.add(&c->zg, std::max<size_t>(plan.zrow.size(), 1));
     ar.add(&c->t_beg, std::max<int64_t>(nt, 1));
     ar.add(&c->t_end, std::max<int64_t>(nt, 1));
     ar.add(&c->t_nrows, std::max<int64_t>(nt, 1));
@@ -785,10 +1421,13 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->t_off_rect, std::max<int64_t>(nt, 1));
     ar.add(&c->t_off_rows, std::max<int64_t>(nt, 1));
     ar.add(&c->t_off_upd, std::max<int64_t>(nt, 1));
+    ar.add(&c->t_off_rectT, std::max<int64_t>(nt, 1));
     ar.add(&c->rows_idx, std::max<size_t>(hs.rows_idx.size(), 1));
-    ar.add(&c->level_nodes, std::max<size_t>(hs.level_nodes.size(), 1));
-    ar.add(&c->comp_level_ptr, std::max<size_t>(hs.comp_level_ptr.size(), 1));
-    ar.add(&c->comp_level_base, std::max<size_t>(hs.comp_level_base.size(), 1));
+    ar.add(&c->grp_level_nodes, std::max<size_t>(plan.gl_nodes.size(), 1));
+    ar.add(&c->grp_level_ptr, std::max<size_t>(plan.gl_ptr.size(), 1));
+    ar.add(&c->grp_level_base, std::max<size_t>(plan.gl_base.size(), 1));
+    ar.add(&c->grp_comp_ptr, std::max<size_t>(plan.gc_ptr.size(), 1));
+    ar.add(&c->grp_comps, std::max<size_t>(plan.gc_list.size(), 1));
     ar.add(&c->comp_cbeg, std::max(hs.ncomp, 1));
     ar.add(&c->comp_cend, std::max(hs.ncomp, 1));
     ar.add(&c->contrib_ptr, hs.contrib_ptr.size());
@@ -796,6 +1435,9 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->fwd_ptr, hs.fwd_ptr.size());
     ar.add(&c->fwd_pos, std::max<size_t>(hs.fwd_pos.size(), 1));
     ar.add(&c->upd, std::max<int64_t>(hs.upd_size, 1));
+    ar.add(&c->ft_buf, 2);
+    ar.add(&c->rec_buf, c->io_cap);
+    ar.add(&c->rec_nodes, c->io_cap);
     c->bytes = ar.total();
     void* basep = nullptr;
     if (alloc && alloc->alloc) {
@@ -826,10 +1468,24 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->if_c2, hs.if_c2);
     e = e ? e : upload(c->cutK, hs.cutK);
     e = e ? e : upload(c->uncutK, hs.uncutK);
-    e = e ? e : upload(c->S_vals, hs.S.vals);
-    e = e ? e : upload(c->S_inv, hs.S.invdiag);
-    e = e ? e : upload(c->M_vals, hs.Mcc.vals);
-    e = e ? e : upload(c->M_inv, hs.Mcc.invdiag);
+    e = e ? e : upload(c->S_blob, plan.blobS);
+    e = e ? e : upload(c->M_blob, plan.blobM);
+    e = e ? e : upload(c->blob_off, plan.b_off);
+    e = e ? e : upload(c->blob_len, plan.b_len);
+    e = e ? e : upload(c->t_foff, plan.foff);
+    e = e ? e : upload(c->t_slot, plan.slot);
+    e = e ? e : upload(c->t_roff, plan.roff);
+    e = e ? e : upload(c->ilist, plan.ilist);
+    e = e ? e : upload(c->ilist_off, plan.i_off);
+    e = e ? e : upload(c->ilist_len, plan.i_len);
+    e = e ? e : upload(c->zsize, plan.zsize);
+    e = e ? e : upload(c->zbase, plan.zbase);
+    e = e ? e : upload(c->zrow, plan.zrow);
+    e = e ? e : upload(c->zfwd_ptr, plan.zfwd_ptr);
+    e = e ? e : upload(c->zfwd_pos, plan.zfwd_pos);
+    e = e ? e : upload(c->zA_off, plan.zA_off);
+    e = e ? e : upload(c->zA_S, plan.zA_S);
+    e = e ? e : upload(c->zA_M, plan.zA_M);
     e = e ? e : upload(c->t_beg, tb);
     e = e ? e : upload(c->t_end, te);
     e = e ? e : upload(c->t_nrows, tn);
@@ -838,10 +1494,13 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->t_off_rect, orc);
     e = e ? e : upload(c->t_off_rows, orw);
     e = e ? e : upload(c->t_off_upd, ou);
+    e = e ? e : upload(c->t_off_rectT, off_rT);
     e = e ? e : upload(c->rows_idx, hs.rows_idx);
-    e = e ? e : upload(c->level_nodes, hs.level_nodes);
-    e = e ? e : upload(c->comp_level_ptr, hs.comp_level_ptr);
-    e = e ? e : upload(c->comp_level_base, hs.comp_level_base);
+    e = e ? e : upload(c->grp_level_nodes, plan.gl_nodes);
+    e = e ? e : upload(c->grp_level_ptr, plan.gl_ptr);
+    e = e ? e : upload(c->grp_level_base, plan.gl_base);
+    e = e ? e : upload(c->grp_comp_ptr, plan.gc_ptr);
+    e = e ? e : upload(c->grp_comps, plan.gc_list);
     e = e ? e : upload(c->comp_cbeg, ccb);
     e = e ? e : upload(c->comp_cend, cce);
     e = e ? e : upload(c->contrib_ptr, hs.contrib_ptr);
@@ -849,8 +1508,6 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->fwd_ptr, hs.fwd_ptr);
     e = e ? e : upload(c->fwd_pos, hs.fwd_pos);
     e = e ? e : set_explicit_smem_dispatch(P, c->smem_explicit);
-    if (e == cudaSuccess && c->smem_solve > 48 * 1024)
-      e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_solve);
     if (e != cudaSuccess) {
       std::string msg = std::string("upload failed: ") + cudaGetErrorString(e);
       imex_destroy(c);
@@ -877,31 +1534,101 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
   }
 }
 
+// One IMEX step n -> n+1 on stream s; events (may be NULL) are recorded before
+// the explicit kernel and after each of the three kernels.
+static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double* ft_dev = nullptr) {
+  const HostSetup& hs = c->hs;
+  const double dt = hs.dt;
+  double* Ucur = c->U[c->cur];
+  double* Unext = c->U[1 - c->cur];
+  const int64_t step = c->step;
+  const int nif = (int)hs.if_cell.size();
+  if (ev) cudaEventRecord(ev[0], s);
+  ExplicitArgs ea = explicit_args(c, Ucur, Unext, Unext, 2.0, -1.0, dt * dt, ft_at(hs, step), true);
+  ea.ft_dev = ft_dev;
+  explicit_dispatch(c, ea, c->ntx * c->nty + pred_blocks(c, true), s);
+  if (ev) cudaEventRecord(ev[1], s);
+  if (hs.n_c > 0) {
+    IfaceArgs ia = iface_args(c, Unext);
+    k_iface<<<(nif + kWarps - 1) / kWarps, kThreads, 0, s>>>(ia);
+    if (ev) cudaEventRecord(ev[2], s);
+    SolveArgs sa = solve_args(c, true, ft_at(hs, step + 1), 0, Unext);
+    sa.ft_dev = ft_dev;
+    launch_solve(c, sa, s);
+  } else if (ev) {
+    cudaEventRecord(ev[2], s);
+  }
+  if (ev) cudaEventRecord(ev[3], s);
+  if (int rc = check_launch("imex_step")) return rc;
+  c->cur = 1 - c->cur;
+  c->step = step + 1;
+  return IMEX_OK;
+}
+
 int imex_step(imex_ctx* c, int64_t n, void* stream) {
   if (!c || n < 0) return fail(IMEX_ERR_ARG, "bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   c->stream = s;
-  const HostSetup& hs = c->hs;
-  const double dt = hs.dt;
-  const int grid_tiles = c->ntx * c->nty;
-  const int npb = pred_blocks(c, true);
-  const int nif = (int)hs.if_cell.size();
-  for (int64_t k = 0; k < n; ++k) {
-    double* Ucur = c->U[c->cur];
-    double* Unext = c->U[1 - c->cur];
-    const int64_t step = c->step;
-    ExplicitArgs ea = explicit_args(c, Ucur, Unext, Unext, 2.0, -1.0, dt * dt, ft_at(hs, step), true);
-    explicit_dispatch(c, ea, grid_tiles + npb, s);
-    if (hs.n_c > 0) {
-      IfaceArgs ia = iface_args(c, Unext);
-      k_iface<<<(nif + kWarps - 1) / kWarps, kThreads, 0, s>>>(ia);
-      SolveArgs sa = solve_args(c, true, ft_at(hs, step + 1), 0, Unext);
-      k_solve<<<hs.ncomp, kThreads, c->smem_solve, s>>>(sa);
+  for (int64_t k = 0; k < n; ++k)
+    if (int rc = step_once(c, s, nullptr)) return rc;
+  return IMEX_OK;
+}
+
+int imex_step_profile(imex_ctx* c, int64_t n, void* stream, double* phase_ms) {
+  if (!c || n < 0 || !phase_ms) return fail(IMEX_ERR_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  c->stream = s;
+  cudaEvent_t ev[4];
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(IMEX_ERR_CUDA, "cudaEventCreate failed");
+  double acc[3] = {0, 0, 0};
+  int rc = IMEX_OK;
+  for (int64_t k = 0; k < n && rc == IMEX_OK; ++k) {
+    rc = step_once(c, s, ev);
+    if (rc) break;
+    if (cudaEventSynchronize(ev[3]) != cudaSuccess) {
+      rc = fail(IMEX_ERR_CUDA, "imex_step_profile: synchronisation failed");
+      break;
     }
-    if (int rc = check_launch("imex_step")) return rc;
-    c->cur = 1 - c->cur;
-    c->step = step + 1;
+    for (int ph = 0; ph < 3; ++ph) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]);
+      acc[ph] += ms;
+    }
   }
+  for (auto& e : ev) cudaEventDestroy(e);
+  for (int ph = 0; ph < 3; ++ph) phase_ms[ph] = acc[ph];
+  return rc;
+}
+
+int imex_step_io(imex_ctx* c, int64_t n, const double* ft_samples, const int64_t* rec_nodes, int nrec,
+                 double* traces, void* stream) {
+  if (!c || n < 0 || nrec < 0 || (nrec > 0 && (!rec_nodes || !traces)))
+    return fail(IMEX_ERR_ARG, "bad arguments");
+  if (nrec > c->io_cap) return fail(IMEX_ERR_ARG, "too many receivers (max 4096)");
+  for (int k = 0; k < nrec; ++k)
+    if (rec_nodes[k] < 0 || rec_nodes[k] >= c->hs.nnodes) return fail(IMEX_ERR_ARG, "receiver node out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  c->stream = s;
+  cudaError_t e = cudaSuccess;
+  if (nrec > 0) e = cudaMemcpyAsync(c->rec_nodes, rec_nodes, nrec * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  for (int64_t k = 0; k < n && e == cudaSuccess; ++k) {
+    const double* ftd = nullptr;
+    if (ft_samples) {
+      e = cudaMemcpyAsync(c->ft_buf, ft_samples + k, 2 * sizeof(double), cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) break;
+      ftd = c->ft_buf;
+    }
+    if (int rc = step_once(c, s, nullptr, ftd)) return rc;
+    if (nrec > 0) {
+      k_gather_nodes<<<(nrec + 255) / 256, 256, 0, s>>>(c->rec_buf, c->U[c->cur], c->rec_nodes, nrec);
+      e = cudaMemcpyAsync(traces + k * nrec, c->rec_buf, nrec * sizeof(double), cudaMemcpyDeviceToHost, s);
+    }
+    // ft_buf is rewritten by the next step's copy, which the stream orders
+    // after this step's kernels.
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_step_io: ") + cudaGetErrorString(e));
   return IMEX_OK;
 }
 
@@ -1004,6 +1731,9 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   if (!c || !st) return fail(IMEX_ERR_ARG, "bad arguments");
   fill_stats(c->hs, st);
   st->step = c->step;
+  st->solve_cluster = c->cluster;
+  st->solve_groups = c->ngroups;
+  st->solve_smem_bytes = (int64_t)c->smem_solve;
   st->device_bytes = (int64_t)c->bytes;
   return IMEX_OK;
 }

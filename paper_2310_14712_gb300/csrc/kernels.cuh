@@ -10,8 +10,10 @@
 //                I_c (stored matrices of cut cells, the uncut-cell matrix
 //                otherwise).
 //   k_solve      A4 gather + A5 + A6: right-hand side f_t(t_{n+1}) f_x^c - K^c
-//                u_pred, forward/backward substitution with the supernodal
-//                nested-dissection Cholesky factor of S, Newmark correction.
+//                u_pred, forward/backward solve with the supernodal
+//                nested-dissection Cholesky factor of S (inverted diagonal
+//                blocks), Newmark correction; one thread-block cluster per
+//                group of components.
 #pragma once
 #include <cstdint>
 
@@ -59,6 +61,7 @@ struct ExplicitArgs {
   int ntx, nty;           // tiles per axis
   double cu, cw, ca;      // out = cu u + cw w + ca minv (ft fx - r)
   double ft;              // f_t(t_n)
+  const double* ft_dev;   // if set: f_t(t_n) = ft_dev[0] (user-supplied samples)
   // Newmark prediction on I_c (blocks after the tiles); n_c = 0 disables it.
   int n_c;
   const int* c_node;
@@ -82,9 +85,28 @@ struct IfaceArgs {
 };
 
 struct SolveArgs {
-  // factor
-  const double* vals;
-  const double* invdiag;
+  // factor, packed per CTA of the launch in consumption order
+  const double* vals;           // blob array (one blob per CTA of the launch)
+  const int64_t* blob_off;      // [cta]: offset of the CTA's blob (16-byte aligned)
+  const int64_t* blob_len;      // [cta]: length in doubles (even)
+  const int64_t* t_foff;        // node -> offset of [L_tt^{-1} (ld b|1) | L_{rows,t} (ld m|1)] in its blob
+  const int* t_slot;            // node -> first row slot in its CTA's right-hand-side array
+  int max_cta_rows;             // even
+  int64_t max_blob;             // doubles of the largest blob staged in shared memory (0: not staged)
+  const int* ilist;             // per-CTA index lists: [row ptr | update positions | ancestor rows]
+  const int64_t* ilist_off;     // [cta] (multiple of 4 ints)
+  const int64_t* ilist_len;     // [cta] (multiple of 4 ints)
+  const int64_t* t_roff;        // node -> offset of its ancestor rows in its CTA's index list
+  // dense top part of each component: x_Z = A_Z (rhs_Z - updates from the walked levels)
+  const int* zsize;             // [comp] |Z|
+  const int* zbase;             // [comp] offset into zrow / zg / zfwd_ptr
+  const int* zrow;              // c-index of each Z row
+  const double* zA;             // row-major |Z| x |Z| blocks
+  const int64_t* zA_off;        // [comp]
+  const int* zfwd_ptr;          // per Z row: update positions from the walked levels
+  const int* zfwd_pos;
+  double* zg;                   // scratch: right-hand side of the Z rows
+  int max_zn;                   // even
   const int* t_beg;
   const int* t_end;
   const int* t_nrows;
@@ -93,11 +115,14 @@ struct SolveArgs {
   const int64_t* t_off_rect;
   const int64_t* t_off_rows;
   const int64_t* t_off_upd;
+  const int64_t* t_off_rectT;
   const int* rows_idx;
-  // schedule
-  const int* level_nodes;
-  const int* comp_level_ptr;
-  const int* comp_level_base;
+  // schedule: groups of components, one thread-block cluster each
+  const int* grp_level_nodes;
+  const int* grp_level_ptr;
+  const int* grp_level_base;
+  const int* grp_comp_ptr;
+  const int* grp_comps;
   const int* comp_cbeg;
   const int* comp_cend;
   // right-hand side
@@ -110,6 +135,7 @@ struct SolveArgs {
   double* sol;
   const double* fxc;
   double ft;              // f_t(t_{n+1}) (step) or f_t(0) (init)
+  const double* ft_dev;   // if set: f_t(t_{n+1}) = ft_dev[1]
   // state
   int mode;               // 0: step with correction; 1: store a^c only
   const int* c_node;
@@ -117,7 +143,7 @@ struct SolveArgs {
   double* v_c;
   double* a_c;
   double dt;
-  int max_block;
+  int max_width;          // max(largest supernode, largest row set)
 };
 
 }  // namespace imex

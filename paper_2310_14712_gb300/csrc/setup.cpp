@@ -381,9 +381,11 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
   int64_t total = 0;
   for (auto& t : hs.tree) {
     int b = t.end - t.beg, m = (int)t.rows.size();
-    total += 2LL * b * b + (int64_t)m * b;
+    total += 2LL * b * b + 2LL * m * b;
   }
   F.vals.assign(total, 0.0);
+  F.Ld.clear();
+  F.ld_off.assign(hs.tree.size(), 0);
   std::vector<std::vector<double>> upd(hs.tree.size());
   std::vector<std::vector<int>> children(hs.tree.size());
   for (size_t k = 0; k < hs.tree.size(); ++k)
@@ -441,19 +443,39 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
         U[(size_t)a * m + bb] = s;
       }
     upd[k] = std::move(U);
-    // Store L_tt (column-major), L_tt^T (column-major) and L_{rows,t} (column-major).
-    double* Ld = F.vals.data() + t.off_diag;
-    double* LdT = F.vals.data() + t.off_diagT;
-    double* Lr = F.vals.data() + t.off_rect;
+    // Store, per supernode, the inverse of its diagonal block and the block
+    // below it, each in both layouts so that the forward (row-owner) and the
+    // backward (column-owner) products read them coalesced:
+    //   Linv  = L_tt^{-1}  (b x b, column-major, lower),  LinvT = Linv^T,
+    //   L21   = L_{rows,t} (m x b, column-major),         L21T  = L21^T.
+    std::vector<double> Li((size_t)b * b, 0.0);
+    for (int k = 0; k < b; ++k) {           // column k of L_tt^{-1}: L x = e_k
+      for (int i = k; i < b; ++i) {
+        double sum = (i == k) ? 1.0 : 0.0;
+        for (int q = k; q < i; ++q) sum -= Fr[(size_t)i * fm + q] * Li[q + (size_t)b * k];
+        Li[i + (size_t)b * k] = sum / Fr[(size_t)i * fm + i];
+      }
+    }
+    // Dense L_tt (column-major), kept on the host for the dense top-level solve.
+    F.ld_off[k] = (int64_t)F.Ld.size();
+    F.Ld.resize(F.Ld.size() + (size_t)b * b, 0.0);
+    for (int j = 0; j < b; ++j)
+      for (int i = j; i < b; ++i) F.Ld[F.ld_off[k] + i + (size_t)b * j] = Fr[(size_t)i * fm + j];
+    double* Linv = F.vals.data() + t.off_diag;
+    double* LinvT = F.vals.data() + t.off_diagT;
+    double* L21 = F.vals.data() + t.off_rect;
+    double* L21T = F.vals.data() + t.off_rectT;
     for (int j = 0; j < b; ++j)
       for (int i = 0; i < b; ++i) {
-        double v = (i >= j) ? Fr[(size_t)i * fm + j] : 0.0;
-        Ld[i + (size_t)b * j] = v;
-        LdT[j + (size_t)b * i] = v;
+        Linv[i + (size_t)b * j] = Li[i + (size_t)b * j];
+        LinvT[j + (size_t)b * i] = Li[i + (size_t)b * j];
       }
     for (int j = 0; j < b; ++j) {
       F.invdiag[t.beg + j] = 1.0 / Fr[(size_t)j * fm + j];
-      for (int i = 0; i < m; ++i) Lr[i + (size_t)m * j] = Fr[(size_t)(b + i) * fm + j];
+      for (int i = 0; i < m; ++i) {
+        L21[i + (size_t)m * j] = Fr[(size_t)(b + i) * fm + j];
+        L21T[j + (size_t)b * i] = Fr[(size_t)(b + i) * fm + j];
+      }
     }
     for (int i = 0; i < b; ++i) pos[t.beg + i] = -1;
     for (int i = 0; i < m; ++i) pos[t.rows[i]] = -1;
@@ -461,11 +483,12 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
   return "";
 }
 
-// Host replay of the device solve (same tree walk, gather lists and factor
-// layout as k_solve): x = S^{-1} b.  Used once at setup to check the factor.
+}  // namespace
+
+// Host replay of the supernodal tree solve with the stored factor blocks:
+// x = A^{-1} b.  Used at setup to check the factor and the device schedule.
 void replay_solve(const HostSetup& hs, const Factor& F, std::vector<double>& x) {
-  const int64_t nc = hs.n_c;
-  std::vector<double> rhs = x, upd(std::max<int64_t>(hs.upd_size, 1), 0.0), g;
+  std::vector<double> rhs = x, upd(std::max<int64_t>(hs.upd_size, 1), 0.0), g, y;
   for (int k = 0; k < hs.ncomp; ++k) {
     const int lb = hs.comp_level_base[k], nlev = hs.comp_level_base[k + 1] - lb - 1;
     for (int l = 0; l < nlev; ++l)
@@ -473,20 +496,22 @@ void replay_solve(const HostSetup& hs, const Factor& F, std::vector<double>& x) 
         const TreeNode& t = hs.tree.at(hs.level_nodes.at(q));
         const int b = t.end - t.beg, m = (int)t.rows.size();
         g.assign(b, 0.0);
+        y.assign(b, 0.0);
         for (int i = 0; i < b; ++i) {
           const int r = t.beg + i;
           double s = rhs.at(r);
           for (int kk = hs.fwd_ptr.at(r); kk < hs.fwd_ptr.at(r + 1); ++kk) s -= upd.at(hs.fwd_pos.at(kk));
           g[i] = s;
         }
-        for (int j = 0; j < b; ++j) {
-          g[j] *= F.invdiag.at(t.beg + j);
-          for (int i = j + 1; i < b; ++i) g[i] -= F.vals.at(t.off_diag + i + (int64_t)b * j) * g[j];
+        for (int i = 0; i < b; ++i) {
+          double s = 0.0;
+          for (int j = 0; j < b; ++j) s += F.vals.at(t.off_diag + i + (int64_t)b * j) * g[j];
+          y[i] = s;
+          x.at(t.beg + i) = s;
         }
-        for (int i = 0; i < b; ++i) x.at(t.beg + i) = g[i];
         for (int kk = 0; kk < m; ++kk) {
           double s = 0.0;
-          for (int j = 0; j < b; ++j) s += F.vals.at(t.off_rect + kk + (int64_t)m * j) * g[j];
+          for (int j = 0; j < b; ++j) s += F.vals.at(t.off_rect + kk + (int64_t)m * j) * y[j];
           upd.at(t.off_upd + kk) = s;
         }
       }
@@ -498,18 +523,19 @@ void replay_solve(const HostSetup& hs, const Factor& F, std::vector<double>& x) 
         for (int j = 0; j < b; ++j) {
           double s = x.at(t.beg + j);
           for (int kk = 0; kk < m; ++kk)
-            s -= F.vals.at(t.off_rect + kk + (int64_t)m * j) * x.at(hs.rows_idx.at(t.off_rows + kk));
+            s -= F.vals.at(t.off_rectT + j + (int64_t)b * kk) * x.at(hs.rows_idx.at(t.off_rows + kk));
           g[j] = s;
         }
-        for (int j = b - 1; j >= 0; --j) {
-          g[j] *= F.invdiag.at(t.beg + j);
-          for (int i = 0; i < j; ++i) g[i] -= F.vals.at(t.off_diagT + i + (int64_t)b * j) * g[j];
+        for (int i = 0; i < b; ++i) {
+          double s = 0.0;
+          for (int j = 0; j < b; ++j) s += F.vals.at(t.off_diagT + i + (int64_t)b * j) * g[j];
+          x.at(t.beg + i) = s;
         }
-        for (int i = 0; i < b; ++i) x.at(t.beg + i) = g[i];
       }
   }
-  (void)nc;
 }
+
+namespace {
 
 // Relative residual ||A x - b|| / ||b|| of the replayed solve for a fixed b.
 double factor_residual(const HostSetup& hs, const CsrMat& A, const Factor& F) {
@@ -1019,7 +1045,8 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
       t.off_diag = off;
       t.off_diagT = off + (int64_t)b * b;
       t.off_rect = off + 2LL * b * b;
-      off += 2LL * b * b + (int64_t)m * b;
+      t.off_rectT = off + 2LL * b * b + (int64_t)m * b;
+      off += 2LL * b * b + 2LL * m * b;
       t.off_rows = offr;
       offr += m;
       t.off_upd = offu;

@@ -44,16 +44,19 @@ struct TreeNode {
   int level = 0;               // 0 = leaf level; parent level > child level
   int comp = 0;
   std::vector<int> rows;
-  int64_t off_diag = 0;        // offset of L_tt (column-major, b x b) in the value array
-  int64_t off_diagT = 0;       // offset of L_tt^T (column-major, b x b)
+  int64_t off_diag = 0;        // offset of L_tt^{-1} (column-major, b x b) in the value array
+  int64_t off_diagT = 0;       // offset of (L_tt^{-1})^T (column-major, b x b)
   int64_t off_rect = 0;        // offset of L_{rows,t} (column-major, m x b)
+  int64_t off_rectT = 0;       // offset of L_{rows,t}^T (column-major, b x m)
   int64_t off_rows = 0;        // offset of `rows` in the index array
   int64_t off_upd = 0;         // offset of this node's update vector in the scratch array
 };
 
 struct Factor {
-  std::vector<double> vals;    // per tree node: L_tt, L_tt^T, L_{rows,t}
+  std::vector<double> vals;    // per tree node: L_tt^{-1}, its transpose, L_{rows,t}, its transpose
   std::vector<double> invdiag; // 1 / L_ii per c-index
+  std::vector<double> Ld;      // per tree node: L_tt itself (column-major), host only
+  std::vector<int64_t> ld_off; // offset of each node's L_tt in Ld
 };
 
 struct HostSetup {
@@ -104,6 +107,9 @@ struct HostSetup {
 
 // Build everything; returns "" on success or an error message.
 std::string build_setup(const Problem& pb, HostSetup& out);
+
+// Host replay of the supernodal tree solve, x = A^{-1} b (x holds b on entry).
+void replay_solve(const HostSetup& hs, const Factor& F, std::vector<double>& x);
 
 // Pieces exposed for host-side tests through the C-ABI.
 void gll_points(int p, std::vector<double>& x, std::vector<double>& w);

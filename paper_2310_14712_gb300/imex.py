@@ -56,7 +56,8 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "n_nodes", "n_d", "n_c", "n_cut", "n_uncut", "n_empty", "n_iface", "nnz_L",
         "n_components", "n_tree", "max_block", "step", "device_bytes")] + \
-        [(n, ctypes.c_double) for n in ("dt", "dt_crit_uncut", "setup_seconds", "residual_S", "residual_M")]
+        [(n, ctypes.c_double) for n in ("dt", "dt_crit_uncut", "setup_seconds", "residual_S", "residual_M")] + \
+        [(n, ctypes.c_int64) for n in ("solve_cluster", "solve_groups", "solve_smem_bytes")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -66,6 +67,9 @@ _vp = ctypes.c_void_p
 _lib.imex_setup.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                             ctypes.POINTER(Source), ctypes.POINTER(Alloc), ctypes.POINTER(_vp)]
 _lib.imex_step.argtypes = [_vp, ctypes.c_int64, _vp]
+_lib.imex_step_profile.argtypes = [_vp, ctypes.c_int64, _vp, _dp]
+_lib.imex_step_io.argtypes = [_vp, ctypes.c_int64, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                              _dp, _vp]
 _lib.imex_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int64, ctypes.c_int]
 _lib.imex_set_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int64, ctypes.c_int]
 _lib.imex_set_step.argtypes = [_vp, ctypes.c_int64]
@@ -81,7 +85,7 @@ _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctyp
                                         ctypes.POINTER(Stats)]
 
 # Every symbol include/imex.h declares (checked by the CPU tests).
-EXPORTS = ("imex_setup", "imex_step", "imex_fields", "imex_set_fields", "imex_set_step",
+EXPORTS = ("imex_setup", "imex_step", "imex_step_profile", "imex_step_io", "imex_fields", "imex_set_fields", "imex_set_step",
            "imex_set_initial", "imex_info", "imex_last_error", "imex_destroy", "imex_gll_points",
            "imex_gauss_points", "imex_host_setup_export")
 
@@ -225,6 +229,29 @@ class Imex:
     def step(self, n, stream=None):
         """Advance n IMEX steps asynchronously on `stream` (default: torch's current stream)."""
         _check(_lib.imex_step(self._ctx, int(n), self._stream(stream)), "imex_step")
+
+    def step_profile(self, n, stream=None):
+        """Advance n steps with per-kernel CUDA events; returns summed device ms of
+        (explicit + CDM + prediction, interface products, solve + correction)."""
+        ms = (ctypes.c_double * 3)()
+        _check(_lib.imex_step_profile(self._ctx, int(n), self._stream(stream), ms), "imex_step_profile")
+        return tuple(ms)
+
+    def step_io(self, n, ft_samples, rec_nodes, traces, stream=None):
+        """n steps with host I/O every step: ft_samples (n+1 host doubles, or None for
+        the built-in wavelet), receivers rec_nodes (int64 node ids); traces (n x nrec
+        host doubles) receives u at the receivers after every step.  Host arrays may be
+        pinned torch CPU tensors or NumPy arrays."""
+        def ptr(a, ct):
+            if a is None:
+                return None
+            if isinstance(a, np.ndarray):
+                return a.ctypes.data_as(ctypes.POINTER(ct))
+            return ctypes.cast(a.data_ptr(), ctypes.POINTER(ct))
+        nrec = len(rec_nodes)
+        _check(_lib.imex_step_io(self._ctx, int(n), ptr(ft_samples, ctypes.c_double),
+                                 ptr(rec_nodes, ctypes.c_int64), nrec, ptr(traces, ctypes.c_double),
+                                 self._stream(stream)), "imex_step_io")
 
     def fields(self, which="u", out=None):
         """Copy a field (canonical layout) into `out` (torch CUDA tensor or NumPy array)."""

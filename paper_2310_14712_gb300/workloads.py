@@ -158,3 +158,26 @@ WORKLOADS = {"plate16": plate16, "plate256": plate256, "multisource": multisourc
 
 def get(name, **kw):
     return WORKLOADS[name](**kw)
+
+
+def source_signature(n, dt, seed=7, fmax=20.0, ncomp=8):
+    """A seeded, smooth source signature of n samples at spacing dt: a sum of
+    `ncomp` sinusoids with random frequencies in [0.1, 1] fmax, amplitudes and
+    phases, under a raised-cosine window.  Input data for the user-supplied
+    source-samples path (a stand-in for a recorded or inverted signature)."""
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(0.1, 1.0, ncomp) * fmax
+    a = rng.uniform(0.5, 1.0, ncomp)
+    ph = rng.uniform(0.0, 2.0 * np.pi, ncomp)
+    t = np.arange(n) * dt
+    sig = (a[None, :] * np.sin(2.0 * np.pi * f[None, :] * t[:, None] + ph[None, :])).sum(axis=1)
+    window = 0.5 - 0.5 * np.cos(2.0 * np.pi * np.arange(n) / max(n - 1, 1))
+    return np.ascontiguousarray(sig * window)
+
+
+def receiver_nodes(w, nrec):
+    """Canonical node ids of `nrec` receivers evenly spaced along the top edge."""
+    nx = w.ncells[0] * w.p + 1
+    ny = w.ncells[1] * w.p + 1
+    xs = np.linspace(0, nx - 1, nrec).round().astype(np.int64)
+    return np.ascontiguousarray((ny - 1) * nx + xs, dtype=np.int64)

@@ -202,3 +202,32 @@ def test_plate256_full_size_sampled():
     # The benchmarked workload at full size (256 x 128 cells, p = 4): 200 steps
     # against the oracle on every node (the oracle handles this size in minutes).
     _check_run(workloads.plate256(), 200)
+
+
+def test_step_io_source_samples_and_receivers():
+    # User-supplied source samples replace f_t for the steps; receiver traces
+    # equal u at the receiver nodes after every step.  The initial state (set up
+    # with the built-in wavelet's f_t(0)) is the same on both sides, so sample 0
+    # is that value.
+    imex = _imex()
+    w = workloads.plate16()
+    s = pipeline.setup(**_kw(w))
+    n = 60
+    sig = workloads.source_signature(n + 1, s.dt)
+    sig[0] = s.ft(0.0)
+    rec = workloads.receiver_nodes(w, 16)
+    st0 = s.imex.initial_state()
+    s.imex.ft = lambda t: float(sig[int(round(t / s.dt))])
+    traces_ref = np.zeros((n, len(rec)))
+
+    def cb(st):
+        traces_ref[st.n - 1] = st.u[rec]
+
+    ref = s.imex.run(n, state=st0, callback=cb)
+    with imex.Imex.from_workload(w) as g:
+        traces = np.zeros((n, len(rec)))
+        g.step_io(n, sig, rec, traces)
+        u = g.fields("u", out=np.zeros(g.n_nodes))
+    assert pipeline.relative_l2(u, ref.u, _phys_mask(s, w.holes)) <= 1e-11
+    assert np.abs(traces - traces_ref).max() <= 1e-11 * np.abs(ref.u).max()
+    assert np.array_equal(traces[-1], u[rec])
