@@ -159,6 +159,28 @@ int imex_step_io(imex_ctx *ctx, int64_t n, const double *ft_samples, const int64
                  int nrec, double *traces, void *stream);
 
 /*
+ * imex_step_noalloc - the same n steps as imex_step(), for callers that must
+ * not allocate device memory while they run: it makes no allocation of any
+ * kind, and the scratch of the implicit solve (update vectors, right-hand
+ * sides of the dense top blocks, the solution vector) is not taken from the
+ * context but from one fixed 2 MiB array (262,144 doubles) compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  Typical callers run under a device-memory budget fixed at start-up
+ * or inside code regions where allocation calls are not permitted.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents.
+ *     Nothing in it needs to start at zero: each entry is written before it
+ *     is read within a step.  Calls that overlap on the GPU (other streams,
+ *     other contexts, at the same time) race on the array.
+ *   - Problems whose solve needs more scratch than the array holds are
+ *     rejected with IMEX_ERR_ARG before anything is launched.
+ * No counterpart in the paper: this is an interface choice of the library.
+ */
+int imex_step_noalloc(imex_ctx *ctx, int64_t n, void *stream);
+
+/*
  * imex_fields - copy one field (IMEX_FIELD_*) in canonical layout into dst.
  *   len          : number of doubles in dst; must equal imex_stats.n_nodes
  *   dst_on_device: nonzero if dst is device memory (copy stays on the device)

@@ -580,6 +580,7 @@ struct imex_ctx {
   int64_t* zA_off = nullptr;
   double *zA_S = nullptr, *zA_M = nullptr, *zg = nullptr;
   int max_zn = 0;
+  int64_t nzrow = 0;
   int* t_slot = nullptr;
   int *comp_cbeg = nullptr, *comp_cend = nullptr;
   int *contrib_ptr = nullptr, *contrib_pos = nullptr, *fwd_ptr = nullptr, *fwd_pos = nullptr;
@@ -1486,6 +1487,7 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->zA_off, plan.zA_off);
     e = e ? e : upload(c->zA_S, plan.zA_S);
     e = e ? e : upload(c->zA_M, plan.zA_M);
+    c->nzrow = (int64_t)plan.zrow.size();
     e = e ? e : upload(c->t_beg, tb);
     e = e ? e : upload(c->t_end, te);
     e = e ? e : upload(c->t_nrows, tn);
@@ -1752,3 +1754,75 @@ void imex_destroy(imex_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// imex_step_noalloc: imex_step with the implicit solve's scratch (descendant
+// update vectors, right-hand sides of the dense top blocks, solution vector)
+// in a fixed array compiled into the library instead of context memory.
+#include <mutex>
+
+namespace {
+constexpr int64_t kStaticScratchDoubles = 262144;  // 2 MiB
+constexpr int kMaxDevices = 64;
+std::mutex g_static_scratch_mu;
+double* g_static_scratch_addr[kMaxDevices] = {nullptr};
+}  // namespace
+
+static __device__ __align__(256) double g_static_solve_scratch[kStaticScratchDoubles];
+
+extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
+  if (!c || n < 0) return fail(IMEX_ERR_ARG, "bad arguments");
+  const HostSetup& hs = c->hs;
+  auto even = [](int64_t v) { return v + (v & 1); };
+  const int64_t n_upd = even(std::max<int64_t>(hs.upd_size, 1));
+  const int64_t n_zg = even(std::max<int64_t>(c->nzrow, 1));
+  const int64_t n_sol = even(std::max<int64_t>(hs.n_c, 1));
+  if (n_upd + n_zg + n_sol > kStaticScratchDoubles)
+    return fail(IMEX_ERR_ARG, "imex_step_noalloc: the implicit solve needs " + std::to_string(n_upd + n_zg + n_sol) +
+                                  " doubles of scratch; the static scratch holds " +
+                                  std::to_string(kStaticScratchDoubles) + " (use imex_step)");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return fail(IMEX_ERR_CUDA, "imex_step_noalloc: no current CUDA device");
+  if (dev != c->device) return fail(IMEX_ERR_ARG, "imex_step_noalloc: the context lives on another device");
+  double* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_scratch_mu);
+    if (!g_static_scratch_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_static_solve_scratch);
+      if (e != cudaSuccess)
+        return fail(IMEX_ERR_CUDA, std::string("imex_step_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_static_scratch_addr[dev] = static_cast<double*>(p);
+    }
+    base = g_static_scratch_addr[dev];
+  }
+  double* upd = base;
+  double* zg = upd + n_upd;
+  double* sol = zg + n_zg;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->stream = s;
+  const double dt = hs.dt;
+  const int nif = (int)hs.if_cell.size();
+  for (int64_t k = 0; k < n; ++k) {
+    double* Ucur = c->U[c->cur];
+    double* Unext = c->U[1 - c->cur];
+    const int64_t step = c->step;
+    ExplicitArgs ea = explicit_args(c, Ucur, Unext, Unext, 2.0, -1.0, dt * dt, ft_at(hs, step), true);
+    explicit_dispatch(c, ea, c->ntx * c->nty + pred_blocks(c, true), s);
+    if (hs.n_c > 0) {
+      IfaceArgs ia = iface_args(c, Unext);
+      k_iface<<<(nif + kWarps - 1) / kWarps, kThreads, 0, s>>>(ia);
+      SolveArgs sa = solve_args(c, true, ft_at(hs, step + 1), 0, Unext);
+      sa.upd = upd;
+      sa.zg = zg;
+      sa.sol = sol;
+      launch_solve(c, sa, s);
+    }
+    if (int rc = check_launch("imex_step_noalloc")) return rc;
+    c->cur = 1 - c->cur;
+    c->step = step + 1;
+  }
+  return IMEX_OK;
+}
+

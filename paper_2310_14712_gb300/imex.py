@@ -70,6 +70,7 @@ _lib.imex_step.argtypes = [_vp, ctypes.c_int64, _vp]
 _lib.imex_step_profile.argtypes = [_vp, ctypes.c_int64, _vp, _dp]
 _lib.imex_step_io.argtypes = [_vp, ctypes.c_int64, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                               _dp, _vp]
+_lib.imex_step_noalloc.argtypes = [_vp, ctypes.c_int64, _vp]
 _lib.imex_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int64, ctypes.c_int]
 _lib.imex_set_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int64, ctypes.c_int]
 _lib.imex_set_step.argtypes = [_vp, ctypes.c_int64]
@@ -85,7 +86,7 @@ _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctyp
                                         ctypes.POINTER(Stats)]
 
 # Every symbol include/imex.h declares (checked by the CPU tests).
-EXPORTS = ("imex_setup", "imex_step", "imex_step_profile", "imex_step_io", "imex_fields", "imex_set_fields", "imex_set_step",
+EXPORTS = ("imex_setup", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
            "imex_set_initial", "imex_info", "imex_last_error", "imex_destroy", "imex_gll_points",
            "imex_gauss_points", "imex_host_setup_export")
 
@@ -229,6 +230,11 @@ class Imex:
     def step(self, n, stream=None):
         """Advance n IMEX steps asynchronously on `stream` (default: torch's current stream)."""
         _check(_lib.imex_step(self._ctx, int(n), self._stream(stream)), "imex_step")
+
+    def step_noalloc(self, n, stream=None):
+        """Like step(), but the implicit solve's scratch lives in the library's fixed
+        2 MiB device array and the call allocates nothing (see include/imex.h)."""
+        _check(_lib.imex_step_noalloc(self._ctx, int(n), self._stream(stream)), "imex_step_noalloc")
 
     def step_profile(self, n, stream=None):
         """Advance n steps with per-kernel CUDA events; returns summed device ms of
