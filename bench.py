@@ -45,7 +45,7 @@ UNIT = "DOF-steps/s"
 # x 2070 MHz (the FP64 rate the probe measured is 1.195 TFLOP/s, 95 % of this).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 L2_FLUSH_BYTES = 256 << 20
-PHASES = ("k_explicit2d", "k_iface", "k_solve")
+PHASES = ("k_explicit2d", "k_iface", "k_walk+k_top")
 
 
 def measured_peaks():
@@ -68,7 +68,7 @@ def algorithmic(st, P, Pd):
         "k_iface": {"flops": 2 * Pd * Pd * n_iface,
                     "bytes": 8 * (Pd * Pd * n_cut + 2 * Pd * n_iface)},
         # A5+A6: forward and backward substitution over the factor, rhs gather, correction.
-        "k_solve": {"flops": 4 * nnz + 10 * n_c,
+        "k_walk+k_top": {"flops": 4 * nnz + 10 * n_c,
                     "bytes": 2 * 12 * nnz + 8 * 6 * n_c},
     }
 
@@ -280,8 +280,9 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(w), "n_active": n_act, "n_d": st["n_d"], "n_c": st["n_c"],
                    "n_nodes": st["n_nodes"], "components": st["n_components"], "nnz_L": st["nnz_L"],
-                   "dt": st["dt"], "solve_cluster": st["solve_cluster"], "solve_groups": st["solve_groups"],
+                   "dt": st["dt"], "solve_levels": st["solve_levels"], "solve_ctas": st["solve_ctas"],
                    "solve_smem_bytes": st["solve_smem_bytes"],
+                   "warm_kernel_ms": None,
                    "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "roofline": roof,

@@ -106,9 +106,9 @@ typedef struct {
   double dt, dt_crit_uncut;
   double setup_seconds;
   double residual_S, residual_M; /* relative residuals of a host replay of the device solve */
-  int64_t solve_cluster;   /* CTAs per thread-block cluster of the implicit solve */
-  int64_t solve_groups;    /* clusters (groups of components) per solve launch */
-  int64_t solve_smem_bytes;/* dynamic shared memory per solve CTA (factor resident if large) */
+  int64_t solve_levels;    /* tree levels walked per pass of the implicit solve (one launch each) */
+  int64_t solve_ctas;      /* CTAs of the widest solve launch */
+  int64_t solve_smem_bytes;/* shared memory per walk CTA (factor blocks staged when they fit) */
 } imex_stats;
 
 /*
@@ -161,8 +161,8 @@ int imex_step_io(imex_ctx *ctx, int64_t n, const double *ft_samples, const int64
 /*
  * imex_step_noalloc - the same n steps as imex_step(), for callers that must
  * not allocate device memory while they run: it makes no allocation of any
- * kind, and the scratch of the implicit solve (update vectors, right-hand
- * sides of the dense top blocks, the solution vector) is not taken from the
+ * kind, and the scratch of the implicit solve (update vectors and the
+ * solution vector) is not taken from the
  * context but from one fixed 2 MiB array (262,144 doubles) compiled into the
  * library, which every GPU that loads the library keeps until the process
  * exits.  Typical callers run under a device-memory budget fixed at start-up

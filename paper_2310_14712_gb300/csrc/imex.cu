@@ -184,6 +184,9 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
 // A4: element products y_e = K_e u_pred,e for every cell touching I_c.  One
 // warp per cell; the cell's nodal block is staged in shared memory.
 __global__ void __launch_bounds__(kThreads) k_iface(IfaceArgs a) {
+  // Let the solve launch now: it stages its factor while this kernel runs and
+  // waits (griddepcontrol.wait) before it reads the products.
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   __shared__ double ue[kWarps][128];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int e = blockIdx.x * kWarps + warp;
@@ -203,68 +206,33 @@ __global__ void __launch_bounds__(kThreads) k_iface(IfaceArgs a) {
   const double* K = ki >= 0 ? a.cutK + (size_t)ki * a.Pd * a.Pd : a.uncutK;
   const double sc = ki >= 0 ? 1.0 : a.c2[e];
   for (int l = lane; l < a.Pd; l += 32) {
-    double s = 0.0;
-    for (int m = 0; m < a.Pd; ++m) s = fma(K[l + (size_t)a.Pd * m], ue[warp][m], s);
-    a.Y[(size_t)e * a.Pd + l] = sc * s;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int m = 0;
+    for (; m + 4 <= a.Pd; m += 4) {
+      s0 = fma(__ldg(K + l + (size_t)a.Pd * m), ue[warp][m], s0);
+      s1 = fma(__ldg(K + l + (size_t)a.Pd * (m + 1)), ue[warp][m + 1], s1);
+      s2 = fma(__ldg(K + l + (size_t)a.Pd * (m + 2)), ue[warp][m + 2], s2);
+      s3 = fma(__ldg(K + l + (size_t)a.Pd * (m + 3)), ue[warp][m + 3], s3);
+    }
+    for (; m < a.Pd; ++m) s0 = fma(__ldg(K + l + (size_t)a.Pd * m), ue[warp][m], s0);
+    a.Y[(size_t)e * a.Pd + l] = sc * ((s0 + s1) + (s2 + s3));
   }
 }
 
 // ---------------------------------------------------------------------------
-// A4 gather + A5 + A6.  One thread-block cluster per group of connected
-// components of I_c (components are bin-packed into groups by factor size).
-// The nested-dissection tree is walked level by level:
-//   forward   y_t = L_tt^{-1} (rhs_t - sum of descendant updates),  upd_t = L_{rows,t} y_t
-//   backward  x_t = L_tt^{-T} (y_t - L_{rows,t}^T x_rows)
-// Each supernode is handled by one CTA with all its warps: every dense
-// product is split along its inner dimension across the warps (lanes own the
-// output rows), and the warp partials are summed in shared memory in a fixed
-// order, so the result is deterministic.  The nodes of a level go to the
-// cluster's CTAs round-robin, largest first; a cluster barrier (release /
-// acquire at cluster scope) separates levels, and values written by another
-// CTA are read with L1-bypassing loads.
-constexpr int kMaxWidth = 256;       // largest supernode / row set the solve handles
-constexpr int kSolveSmemBudget = 200 * 1024;
-
-// Partial products of a warp over the inner range [j0, j1):
-// part[i] = sum_j M[i si + j sj] v[j] for rows i = lane + 32 r < nrows (R row
-// groups), restricted to j <= i (tri > 0, lower) or j >= i (tri < 0, upper).
-// (si, sj) = (1, ld) reads a column-major block, (ld, 1) its transpose; with
-// an odd ld both are free of shared-memory bank conflicts.
-template <int R>
-__device__ __forceinline__ void warp_partial_r(const double* M, int si, int sj, int nrows,
-                                               const double* v, int j0, int j1, int tri, double* part,
-                                               int lane) {
-  double acc[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) acc[r] = 0.0;
-  for (int j = j0; j < j1; ++j) {
-    const double vj = v[j];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int i = lane + 32 * r;
-      const bool ok = i < nrows && (tri == 0 || (tri > 0 ? j <= i : j >= i));
-      if (ok) acc[r] = fma(M[(size_t)i * si + (size_t)j * sj], vj, acc[r]);
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int i = lane + 32 * r;
-    if (i < nrows) part[i] = acc[r];
-  }
-}
-
-__device__ __forceinline__ void warp_partial(const double* M, int si, int sj, int nrows,
-                                             const double* v, int j0, int j1, int tri, double* part,
-                                             int lane) {
-  switch ((nrows + 31) / 32) {
-    case 0: break;
-    case 1: warp_partial_r<1>(M, si, sj, nrows, v, j0, j1, tri, part, lane); break;
-    case 2: warp_partial_r<2>(M, si, sj, nrows, v, j0, j1, tri, part, lane); break;
-    case 3: warp_partial_r<3>(M, si, sj, nrows, v, j0, j1, tri, part, lane); break;
-    case 4: warp_partial_r<4>(M, si, sj, nrows, v, j0, j1, tri, part, lane); break;
-    default: warp_partial_r<8>(M, si, sj, nrows, v, j0, j1, tri, part, lane); break;
-  }
-}
+// A4 gather + A5 + A6: the implicit solve S a = f_t(t_{n+1}) f_x^c - K^c u_pred
+// with the supernodal nested-dissection Cholesky factor of S, and the Newmark
+// correction.  Per component, the lower levels of the dissection tree are
+// walked level by level (forward: y_t = L_tt^{-1}(rhs_t - descendant updates),
+// upd_t = L_{rows,t} y_t; backward: x_t = L_tt^{-T}(y_t - L_{rows,t}^T x_rows)),
+// and the upper levels are one dense product x_Z = A_Z (rhs_Z - updates from
+// below), A_Z = (L_ZZ L_ZZ^T)^{-1} (no lower node is an ancestor of an upper
+// one, so L_BZ = 0).  Every level is one launch over all components: kernel
+// boundaries are the barriers, so each launch spreads its FP64 work over every
+// SM.  Launches are chained with programmatic dependent launch: a kernel
+// stages its constant factor blocks (cp.async) while its predecessor runs and
+// waits (griddepcontrol.wait, a hardware wait) before it reads its results.
+// All sums run in a fixed order, so results are deterministic.
 
 // Start an asynchronous copy of n 16-byte chunks global -> shared with all
 // threads (cp.async, no register staging); completed by async_copy_wait().
@@ -282,205 +250,158 @@ __device__ __forceinline__ void async_copy_wait() {
   __syncthreads();
 }
 
-template <bool kSmem>
-__global__ void __launch_bounds__(kThreads) k_solve(SolveArgs a) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ __align__(16) double smg[];
-  const int CL = (int)cluster.num_blocks();
-  const int crank = (int)cluster.block_rank();
-  const int grp = blockIdx.x / CL;
-  const int cta = grp * CL + crank;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, tid = threadIdx.x;
-  const int W = a.max_width;                  // >= max(max_block, max_rows)
-  double* g = smg;                            // W: gathered rhs / y / h
-  double* y = g + W;                          // W
-  double* xr = y + W;                         // W: ancestor values
-  double* part = xr + W;                      // kWarps x W warp partials
-  double* rhs = part + kWarps * W + a.max_zn;  // this CTA's rows: f_t f_x^c - (K^c u_pred) part
-  double* blob = rhs + a.max_cta_rows;        // this CTA's factor blocks (max_cta_rows is even)
-  const int64_t boff = a.blob_off[cta], blen = a.blob_len[cta];
-  const double* Bf = kSmem ? blob : a.vals + boff;
-  // This CTA's index lists: row pointers and positions of descendant updates,
-  // then the ancestor rows of its nodes (16-byte padded in global memory).
-  int* ilist = reinterpret_cast<int*>(blob + (kSmem ? a.max_blob : 0));
-  const int64_t ioff = a.ilist_off[cta], ilen = a.ilist_len[cta];
-  if (kSmem) async_copy_16(blob, a.vals + boff, blen / 2);
-  async_copy_16(ilist, a.ilist + ioff, ilen / 4);
-  const int lb = a.grp_level_base[grp];
-  const int nlev = a.grp_level_base[grp + 1] - lb - 1;
-  const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
+// One warp, one supernode product: lanes own rows.  out[i] = sum_j M[i si + j sj] v[j]
+// for i < nrows, restricted to j <= i (tri > 0) or j >= i (tri < 0).
+// (si, sj) = (1, ld) reads a column-major block, (ld, 1) its transpose; with an
+// odd ld both are free of shared-memory bank conflicts.
+template <int R>
+__device__ __forceinline__ void warp_gemv_r(const double* M, int si, int sj, int nrows, int ncols,
+                                            const double* v, int tri, double* out, int lane) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    if (i >= nrows) break;
+    int j0 = 0, j1 = ncols;
+    if (tri > 0) j1 = min(ncols, i + 1);
+    if (tri < 0) j0 = i;
+    double s0 = 0.0, s1 = 0.0;
+    int j = j0;
+    for (; j + 2 <= j1; j += 2) {
+      s0 = fma(M[(size_t)i * si + (size_t)j * sj], v[j], s0);
+      s1 = fma(M[(size_t)i * si + (size_t)(j + 1) * sj], v[j + 1], s1);
+    }
+    if (j < j1) s0 = fma(M[(size_t)i * si + (size_t)j * sj], v[j], s0);
+    out[i] = s0 + s1;
+  }
+}
 
-  // Right-hand-side part that does not depend on the tree walk:
-  // f_t(t_{n+1}) f_x^c - K^c u_pred, for every row this CTA owns.
-  for (int l = 0; l < nlev; ++l) {
-    const int qb = a.grp_level_ptr[lb + l], qe = a.grp_level_ptr[lb + l + 1];
-    for (int q = qb + crank; q < qe; q += CL) {
-      const int t = a.grp_level_nodes[q];
-      const int beg = a.t_beg[t], b = a.t_end[t] - beg, slot = a.t_slot[t];
-      for (int i = tid; i < b; i += kThreads) {
+__device__ __forceinline__ void warp_gemv(const double* M, int si, int sj, int nrows, int ncols,
+                                          const double* v, int tri, double* out, int lane) {
+  switch ((nrows + 31) / 32) {
+    case 0: break;
+    case 1: warp_gemv_r<1>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
+    case 2: warp_gemv_r<2>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
+    case 3: warp_gemv_r<3>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
+    case 4: warp_gemv_r<4>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
+    default: warp_gemv_r<8>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
+  }
+}
+
+// Newmark correction of one implicit row (Fig. TrapCDMIMEX "Correction"), or
+// the initial acceleration only (mode 1).
+template <class Args>
+__device__ __forceinline__ void correct_row(const Args& a, int r, double acc) {
+  if (a.mode == 0) {
+    const int node = a.c_node[r];
+    const double vpred = a.v_c[r] + (1.0 - kNewmarkGamma) * a.dt * a.a_c[r];
+    a.U[node] = a.U[node] + kNewmarkBeta * a.dt * a.dt * acc;
+    a.v_c[r] = vpred + kNewmarkGamma * a.dt * acc;
+  }
+  a.a_c[r] = acc;
+}
+
+template <bool kForward, bool kSmem>
+__global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  const int cta = a.cta0 + blockIdx.x;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int W = a.W;                            // even
+  double* wg = sm + warp * 3 * W;
+  double* wy = wg + W;
+  double* wx = wy + W;
+  double* blob = sm + kWarps * 3 * W;
+  const int64_t boff = a.blob_off[cta];
+  if (kSmem) async_copy_16(blob, a.blob + boff, a.blob_len[cta] / 2);
+  const double* B = kSmem ? blob : a.blob + boff;
+  // Let the next launch stage its constants; wait for the previous results.
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  if (kSmem) async_copy_wait();
+  const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
+  for (int q = a.cta_node_ptr[cta] + warp; q < a.cta_node_ptr[cta + 1]; q += kWarps) {
+    const int t = a.cta_nodes[q];
+    const int beg = a.t_beg[t], b = a.t_end[t] - beg, m = a.t_nrows[t];
+    const int ldi = b | 1, ldr = m | 1;
+    const double* Li = B + a.node_boff[t];           // L_tt^{-1}: b x b, column-major, ld ldi
+    const double* L21 = Li + (size_t)ldi * b;        // L_{rows,t}: m x b, column-major, ld ldr
+    if (kForward) {
+      for (int i = lane; i < b; i += 32) {
         const int r = beg + i;
-        double s = ft * a.fxc[r];
+        double v = ft * a.fxc[r];
         const int c0 = a.contrib_ptr[r], c1 = a.contrib_ptr[r + 1];
 #pragma unroll 4
-        for (int k = c0; k < c1; ++k) s -= a.Y[a.contrib_pos[k]];
-        rhs[slot + i] = s;
-      }
-    }
-  }
-  async_copy_wait();
-  const int* rptr = ilist;                      // row slot -> first position
-
-  for (int l = 0; l < nlev; ++l) {
-    const int qb = a.grp_level_ptr[lb + l], qe = a.grp_level_ptr[lb + l + 1];
-    for (int q = qb + crank; q < qe; q += CL) {
-      const int t = a.grp_level_nodes[q];
-      const int beg = a.t_beg[t], b = a.t_end[t] - beg, m = a.t_nrows[t];
-      const int ldi = b | 1, ldr = m | 1;            // odd leading dimensions
-      const double* Li = Bf + a.t_foff[t];          // L_tt^{-1}: b x b, column-major, ld ldi
-      const double* L21 = Li + (size_t)ldi * b;      // L_{rows,t}: m x b, column-major, ld ldr
-      if (tid < b) {
-        const int sl = a.t_slot[t] + tid;
-        double s = rhs[sl];
-        const int f0 = rptr[sl], f1 = rptr[sl + 1];
+        for (int k = c0; k < c1; ++k) v -= a.Y[a.contrib_pos[k]];
+        const int f0 = a.fwd_ptr[r], f1 = a.fwd_ptr[r + 1];
 #pragma unroll 4
-        for (int k = f0; k < f1; ++k) s -= __ldcg(a.upd + ilist[k]);
-        g[tid] = s;
+        for (int k = f0; k < f1; ++k) v -= __ldcg(a.upd + a.fwd_pos[k]);
+        wg[i] = v;
       }
-      __syncthreads();
-      {  // y = L_tt^{-1} g  (lower triangular)
-        const int ch = (b + kWarps - 1) / kWarps;
-        const int j0 = min(b, warp * ch), j1 = min(b, j0 + ch);
-        warp_partial(Li, 1, ldi, b, g, j0, j1, 1, part + warp * W, lane);
+      __syncwarp();
+      warp_gemv(Li, 1, ldi, b, b, wg, 1, wy, lane);        // y = L_tt^{-1} g
+      __syncwarp();
+      for (int i = lane; i < b; i += 32) a.sol[beg + i] = wy[i];
+      if (m > 0) warp_gemv(L21, 1, ldr, m, b, wy, 0, a.upd + a.t_off_upd[t], lane);  // upd = L21 y
+      __syncwarp();
+    } else {
+      const int* rows = a.rows_idx + a.t_off_rows[t];
+      for (int k = lane; k < m; k += 32) wx[k] = -__ldcg(a.sol + rows[k]);
+      __syncwarp();
+      warp_gemv(L21, ldr, 1, b, m, wx, 0, wg, lane);      // -L_{rows,t}^T x_rows
+      __syncwarp();
+      for (int j = lane; j < b; j += 32) wg[j] += __ldcg(a.sol + beg + j);
+      __syncwarp();
+      warp_gemv(Li, ldi, 1, b, b, wg, -1, wy, lane);      // x = L_tt^{-T} h
+      __syncwarp();
+      for (int i = lane; i < b; i += 32) {
+        a.sol[beg + i] = wy[i];
+        correct_row(a, beg + i, wy[i]);
       }
-      __syncthreads();
-      if (tid < b) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += part[w * W + tid];
-        y[tid] = s;
-        a.sol[beg + tid] = s;
-      }
-      __syncthreads();
-      if (m > 0) {  // upd = L_{rows,t} y
-        const int ch = (b + kWarps - 1) / kWarps;
-        const int j0 = min(b, warp * ch), j1 = min(b, j0 + ch);
-        warp_partial(L21, 1, ldr, m, y, j0, j1, 0, part + warp * W, lane);
-        __syncthreads();
-        if (tid < m) {
-          double s = 0.0;
-#pragma unroll
-          for (int w = 0; w < kWarps; ++w) s += part[w * W + tid];
-          a.upd[a.t_off_upd[t] + tid] = s;
-        }
-      }
-      __syncthreads();
+      __syncwarp();
     }
-    cluster.sync();
   }
+}
 
-  // Dense top of each component (the tree levels above the ones walked):
-  // x_Z = A_Z (rhs_Z - updates from below), A_Z = (L_ZZ L_ZZ^T)^{-1}.
-  {
-    const int cb = a.grp_comp_ptr[grp], ce = a.grp_comp_ptr[grp + 1];
-    for (int ci = cb; ci < ce; ++ci) {
-      const int comp = a.grp_comps[ci], zn = a.zsize[comp], zb = a.zbase[comp];
-      const int ch = (zn + CL - 1) / CL, i0 = min(zn, crank * ch), i1 = min(zn, i0 + ch);
-      for (int i = i0 + tid; i < i1; i += kThreads) {
-        const int r = a.zrow[zb + i];
-        double s = ft * a.fxc[r];
-        for (int k = a.contrib_ptr[r]; k < a.contrib_ptr[r + 1]; ++k) s -= a.Y[a.contrib_pos[k]];
-        for (int k = a.zfwd_ptr[zb + i]; k < a.zfwd_ptr[zb + i + 1]; ++k) s -= __ldcg(a.upd + a.zfwd_pos[k]);
-        a.zg[zb + i] = s;
-      }
-    }
-    cluster.sync();
-    double* zs = part + kWarps * W;   // max_zn doubles
-    for (int ci = cb; ci < ce; ++ci) {
-      const int comp = a.grp_comps[ci], zn = a.zsize[comp], zb = a.zbase[comp];
-      if (zn == 0) continue;
-      for (int j = tid; j < zn; j += kThreads) zs[j] = __ldcg(a.zg + zb + j);
-      __syncthreads();
-      const int ch = (zn + CL - 1) / CL, i0 = min(zn, crank * ch), i1 = min(zn, i0 + ch);
-      const double* A = a.zA + a.zA_off[comp];
-      for (int i = i0 + warp; i < i1; i += kWarps) {
-        const double* Ar = A + (size_t)i * zn;
-        double s0 = 0.0, s1 = 0.0;
-        int j = lane;
-        for (; j + 32 < zn; j += 64) {
-          s0 = fma(__ldg(Ar + j), zs[j], s0);
-          s1 = fma(__ldg(Ar + j + 32), zs[j + 32], s1);
-        }
-        if (j < zn) s0 = fma(__ldg(Ar + j), zs[j], s0);
-        double v = s0 + s1;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) a.sol[a.zrow[zb + i]] = v;
-      }
-      __syncthreads();
-    }
-    cluster.sync();
+__global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
+  extern __shared__ __align__(16) double zs[];
+  const int cta = blockIdx.x;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int comp = a.cta_comp[cta], r0 = a.cta_r0[cta], r1 = a.cta_r1[cta];
+  const int zn = a.zsize[comp], zb = a.zbase[comp];
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
+  // The whole right-hand side of this component's top block (redundant per CTA).
+  for (int i = threadIdx.x; i < zn; i += kThreads) {
+    const int r = a.zrow[zb + i];
+    double v = ft * a.fxc[r];
+    const int c0 = a.contrib_ptr[r], c1 = a.contrib_ptr[r + 1];
+#pragma unroll 4
+    for (int k = c0; k < c1; ++k) v -= a.Y[a.contrib_pos[k]];
+    const int f0 = a.zfwd_ptr[zb + i], f1 = a.zfwd_ptr[zb + i + 1];
+#pragma unroll 4
+    for (int k = f0; k < f1; ++k) v -= __ldcg(a.upd + a.zfwd_pos[k]);
+    zs[i] = v;
   }
-
-  for (int l = nlev - 1; l >= 0; --l) {
-    const int qb = a.grp_level_ptr[lb + l], qe = a.grp_level_ptr[lb + l + 1];
-    for (int q = qb + crank; q < qe; q += CL) {
-      const int t = a.grp_level_nodes[q];
-      const int beg = a.t_beg[t], b = a.t_end[t] - beg, m = a.t_nrows[t];
-      const int ldi = b | 1, ldr = m | 1;
-      const double* Li = Bf + a.t_foff[t];           // read transposed below
-      const double* L21 = Li + (size_t)ldi * b;
-      const int* rows = ilist + a.t_roff[t];
-      if (tid < m) xr[tid] = __ldcg(a.sol + rows[tid]);
-      if (tid < b) y[tid] = __ldcg(a.sol + beg + tid);
-      __syncthreads();
-      if (m > 0) {  // h = y - L_{rows,t}^T x_rows
-        const int ch = (m + kWarps - 1) / kWarps;
-        const int k0 = min(m, warp * ch), k1 = min(m, k0 + ch);
-        warp_partial(L21, ldr, 1, b, xr, k0, k1, 0, part + warp * W, lane);
-        __syncthreads();
-        if (tid < b) {
-          double s = y[tid];
-#pragma unroll
-          for (int w = 0; w < kWarps; ++w) s -= part[w * W + tid];
-          g[tid] = s;
-        }
-      } else if (tid < b) {
-        g[tid] = y[tid];
-      }
-      __syncthreads();
-      {  // x = L_tt^{-T} h  (upper triangular)
-        const int ch = (b + kWarps - 1) / kWarps;
-        const int j0 = min(b, warp * ch), j1 = min(b, j0 + ch);
-        warp_partial(Li, ldi, 1, b, g, j0, j1, -1, part + warp * W, lane);
-      }
-      __syncthreads();
-      if (tid < b) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += part[w * W + tid];
-        a.sol[beg + tid] = s;
-      }
-      __syncthreads();
+  __syncthreads();
+  const double* A = a.zA + a.zA_off[comp];
+  for (int i = r0 + warp; i < r1; i += kWarps) {
+    const double* Ar = A + (size_t)i * zn;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int j = lane;
+    for (; j + 96 < zn; j += 128) {
+      s0 = fma(__ldg(Ar + j), zs[j], s0);
+      s1 = fma(__ldg(Ar + j + 32), zs[j + 32], s1);
+      s2 = fma(__ldg(Ar + j + 64), zs[j + 64], s2);
+      s3 = fma(__ldg(Ar + j + 96), zs[j + 96], s3);
     }
-    cluster.sync();
-  }
-
-  // Correction (Fig. TrapCDMIMEX) or the initial acceleration.
-  const double bdt2 = kNewmarkBeta * a.dt * a.dt, gdt = kNewmarkGamma * a.dt,
-               g1dt = (1.0 - kNewmarkGamma) * a.dt;
-  for (int ci = a.grp_comp_ptr[grp]; ci < a.grp_comp_ptr[grp + 1]; ++ci) {
-    const int comp = a.grp_comps[ci];
-    for (int r = a.comp_cbeg[comp] + crank * kThreads + threadIdx.x; r < a.comp_cend[comp];
-         r += CL * kThreads) {
-      const double acc = __ldcg(a.sol + r);
-      if (a.mode == 0) {
-        const int node = a.c_node[r];
-        const double vpred = a.v_c[r] + g1dt * a.a_c[r];
-        a.U[node] = a.U[node] + bdt2 * acc;
-        a.v_c[r] = vpred + gdt * acc;
-      }
-      a.a_c[r] = acc;
+    for (; j < zn; j += 32) s0 = fma(__ldg(Ar + j), zs[j], s0);
+    double v = (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+      const int r = a.zrow[zb + i];
+      a.sol[r] = v;
+      correct_row(a, r, v);
     }
   }
 }
@@ -560,40 +481,35 @@ struct imex_ctx {
   double *v_c = nullptr, *a_c = nullptr, *fxc = nullptr;
   int *if_cell = nullptr, *if_kidx = nullptr;
   double *if_c2 = nullptr, *cutK = nullptr, *uncutK = nullptr, *Y = nullptr;
-  int *t_beg = nullptr, *t_end = nullptr, *t_nrows = nullptr;
-  int64_t *t_off_diag = nullptr, *t_off_diagT = nullptr, *t_off_rect = nullptr, *t_off_rows = nullptr,
-          *t_off_upd = nullptr;
-  int *rows_idx = nullptr, *grp_level_nodes = nullptr, *grp_level_ptr = nullptr, *grp_level_base = nullptr;
-  int *grp_comp_ptr = nullptr, *grp_comps = nullptr;
-  int64_t* t_off_rectT = nullptr;
-  int ngroups = 0;
-  int cluster = 8;
-  int solve_width = 1;
-  int solve_smem_mode = 0;
-  int max_cta_rows = 1;
-  double *S_blob = nullptr, *M_blob = nullptr;
-  int64_t *blob_off = nullptr, *blob_len = nullptr, *t_foff = nullptr;
-  int64_t *ilist_off = nullptr, *ilist_len = nullptr, *t_roff = nullptr;
-  int* ilist = nullptr;
-  int64_t max_blob = 0;
+  int *contrib_ptr = nullptr, *contrib_pos = nullptr, *fwd_ptr = nullptr, *fwd_pos = nullptr;
+  // solve: tree metadata, per-CTA factor blobs (S and M^cc), dense tops, scratch
+  int *t_beg = nullptr, *t_end = nullptr, *t_nrows = nullptr, *rows_idx = nullptr;
+  int64_t *t_off_upd = nullptr, *t_off_rows = nullptr;
+  double *blob_S = nullptr, *blob_M = nullptr;
+  int64_t *blob_off = nullptr, *blob_len = nullptr, *node_boff = nullptr;
+  int *cta_node_ptr = nullptr, *cta_nodes = nullptr;
+  std::vector<int> lev_cta0, lev_ncta;   // per walked level: CTA range
+  int walk_smem_mode = 0;
+  size_t smem_walk = 0, smem_top = 0;
+  int walk_W = 2;
+  int ntop = 0;
+  int *top_comp = nullptr, *top_r0 = nullptr, *top_r1 = nullptr;
   int *zsize = nullptr, *zbase = nullptr, *zrow = nullptr, *zfwd_ptr = nullptr, *zfwd_pos = nullptr;
   int64_t* zA_off = nullptr;
-  double *zA_S = nullptr, *zA_M = nullptr, *zg = nullptr;
-  int max_zn = 0;
+  double *zA_S = nullptr, *zA_M = nullptr;
   int64_t nzrow = 0;
-  int* t_slot = nullptr;
-  int *comp_cbeg = nullptr, *comp_cend = nullptr;
-  int *contrib_ptr = nullptr, *contrib_pos = nullptr, *fwd_ptr = nullptr, *fwd_pos = nullptr;
   double *upd = nullptr, *sol = nullptr;
+  // host I/O
   double *ft_buf = nullptr, *rec_buf = nullptr;
   int64_t* rec_nodes = nullptr;
   int io_cap = 4096;
+  // state
   int cur = 0;              // U[cur] holds u_n
   int64_t step = 0;
   cudaStream_t stream = nullptr;
   Ops2D ops{};
   int TC = 4, ntx = 1, nty = 1;
-  size_t smem_explicit = 0, smem_solve = 0;
+  size_t smem_explicit = 0;
 };
 
 namespace {
@@ -718,104 +634,98 @@ IfaceArgs iface_args(imex_ctx* c, const double* src) {
   return ia;
 }
 
-SolveArgs solve_args(imex_ctx* c, bool use_S, double ft, int mode, double* Ubuf) {
-  SolveArgs sa{};
-  sa.vals = use_S ? c->S_blob : c->M_blob;
-  sa.blob_off = c->blob_off;
-  sa.blob_len = c->blob_len;
-  sa.t_foff = c->t_foff;
-  sa.t_roff = c->t_roff;
-  sa.ilist = c->ilist;
-  sa.ilist_off = c->ilist_off;
-  sa.ilist_len = c->ilist_len;
-  sa.max_blob = c->max_blob;
-  sa.zsize = c->zsize;
-  sa.zbase = c->zbase;
-  sa.zrow = c->zrow;
-  sa.zA = use_S ? c->zA_S : c->zA_M;
-  sa.zA_off = c->zA_off;
-  sa.zfwd_ptr = c->zfwd_ptr;
-  sa.zfwd_pos = c->zfwd_pos;
-  sa.zg = c->zg;
-  sa.max_zn = c->max_zn;
-  sa.t_slot = c->t_slot;
-  sa.max_cta_rows = c->max_cta_rows;
-  sa.t_beg = c->t_beg;
-  sa.t_end = c->t_end;
-  sa.t_nrows = c->t_nrows;
-  sa.t_off_diag = c->t_off_diag;
-  sa.t_off_diagT = c->t_off_diagT;
-  sa.t_off_rect = c->t_off_rect;
-  sa.t_off_rows = c->t_off_rows;
-  sa.t_off_upd = c->t_off_upd;
-  sa.t_off_rectT = c->t_off_rectT;
-  sa.rows_idx = c->rows_idx;
-  sa.grp_level_nodes = c->grp_level_nodes;
-  sa.grp_level_ptr = c->grp_level_ptr;
-  sa.grp_level_base = c->grp_level_base;
-  sa.grp_comp_ptr = c->grp_comp_ptr;
-  sa.grp_comps = c->grp_comps;
-  sa.comp_cbeg = c->comp_cbeg;
-  sa.comp_cend = c->comp_cend;
-  sa.contrib_ptr = c->contrib_ptr;
-  sa.contrib_pos = c->contrib_pos;
-  sa.Y = c->Y;
-  sa.fwd_ptr = c->fwd_ptr;
-  sa.fwd_pos = c->fwd_pos;
-  sa.upd = c->upd;
-  sa.sol = c->sol;
-  sa.fxc = c->fxc;
-  sa.ft = ft;
-  sa.mode = mode;
-  sa.c_node = c->c_node;
-  sa.U = Ubuf;
-  sa.v_c = c->v_c;
-  sa.a_c = c->a_c;
-  sa.dt = c->hs.dt;
-  sa.max_width = c->solve_width;
-  return sa;
-}
+constexpr int kMaxWidth = 256;                 // largest supernode / row set of the walk
+constexpr size_t kWalkSmemBudget = 200 * 1024;  // shared memory per walk CTA
 
-cudaError_t launch_solve(imex_ctx* c, const SolveArgs& sa, cudaStream_t s) {
+// The launches of the implicit solve (after k_iface): forward walk over the
+// lower levels, dense tops, backward walk with the correction.  use_S selects
+// the factor of S (step) or of M^cc (initial acceleration, mode 1).  upd/sol
+// are the solve's scratch vectors.
+cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double* ft_dev, int mode, double* Ubuf,
+                               double* upd, double* sol, cudaStream_t s) {
+  const HostSetup& hs = c->hs;
+  WalkArgs w{};
+  w.blob = use_S ? c->blob_S : c->blob_M;
+  w.blob_off = c->blob_off;
+  w.blob_len = c->blob_len;
+  w.cta_node_ptr = c->cta_node_ptr;
+  w.cta_nodes = c->cta_nodes;
+  w.node_boff = c->node_boff;
+  w.t_beg = c->t_beg;
+  w.t_end = c->t_end;
+  w.t_nrows = c->t_nrows;
+  w.t_off_upd = c->t_off_upd;
+  w.t_off_rows = c->t_off_rows;
+  w.rows_idx = c->rows_idx;
+  w.fwd_ptr = c->fwd_ptr;
+  w.fwd_pos = c->fwd_pos;
+  w.contrib_ptr = c->contrib_ptr;
+  w.contrib_pos = c->contrib_pos;
+  w.Y = c->Y;
+  w.fxc = c->fxc;
+  w.ft = ft;
+  w.ft_dev = ft_dev;
+  w.upd = upd;
+  w.sol = sol;
+  w.W = c->walk_W;
+  w.mode = mode;
+  w.c_node = c->c_node;
+  w.U = Ubuf;
+  w.v_c = c->v_c;
+  w.a_c = c->a_c;
+  w.dt = hs.dt;
+  TopArgs z{};
+  z.cta_comp = c->top_comp;
+  z.cta_r0 = c->top_r0;
+  z.cta_r1 = c->top_r1;
+  z.zsize = c->zsize;
+  z.zbase = c->zbase;
+  z.zrow = c->zrow;
+  z.zA_off = c->zA_off;
+  z.zA = use_S ? c->zA_S : c->zA_M;
+  z.zfwd_ptr = c->zfwd_ptr;
+  z.zfwd_pos = c->zfwd_pos;
+  z.contrib_ptr = c->contrib_ptr;
+  z.contrib_pos = c->contrib_pos;
+  z.Y = c->Y;
+  z.fxc = c->fxc;
+  z.ft = ft;
+  z.ft_dev = ft_dev;
+  z.upd = upd;
+  z.sol = sol;
+  z.mode = mode;
+  z.c_node = c->c_node;
+  z.U = Ubuf;
+  z.v_c = c->v_c;
+  z.a_c = c->a_c;
+  z.dt = hs.dt;
+
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(c->ngroups * c->cluster);
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = c->smem_solve;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = c->cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return c->solve_smem_mode ? cudaLaunchKernelEx(&cfg, k_solve<true>, sa)
-                            : cudaLaunchKernelEx(&cfg, k_solve<false>, sa);
-}
-
-// How many clusters of `cl` CTAs with `smem` bytes each the device co-schedules.
-int max_clusters(int cl, size_t smem) {
-  for (auto fn : {k_solve<true>, k_solve<false>}) {
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSolveSmemBudget) != cudaSuccess)
-      return 0;
-    cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  const int nlev = (int)c->lev_cta0.size();
+  auto walk = [&](int l, bool fwd) {
+    w.cta0 = c->lev_cta0[l];
+    cfg.gridDim = dim3(c->lev_ncta[l]);
+    cfg.dynamicSmemBytes = c->smem_walk;
+    if (c->walk_smem_mode)
+      return fwd ? cudaLaunchKernelEx(&cfg, k_walk<true, true>, w) : cudaLaunchKernelEx(&cfg, k_walk<false, true>, w);
+    return fwd ? cudaLaunchKernelEx(&cfg, k_walk<true, false>, w) : cudaLaunchKernelEx(&cfg, k_walk<false, false>, w);
+  };
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < nlev && e == cudaSuccess; ++l) e = walk(l, true);
+  if (e == cudaSuccess && c->ntop > 0) {
+    cfg.gridDim = dim3(c->ntop);
+    cfg.dynamicSmemBytes = c->smem_top;
+    e = cudaLaunchKernelEx(&cfg, k_top, z);
   }
-  cudaGetLastError();
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cl);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cl;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_solve<true>, &cfg) != cudaSuccess) n = 0;
-  cudaGetLastError();
-  return n;
+  for (int l = nlev - 1; l >= 0 && e == cudaSuccess; --l) e = walk(l, false);
+  return e;
 }
 
 double ft_at(const HostSetup& hs, int64_t n) {
@@ -840,34 +750,40 @@ int compute_initial(imex_ctx* c, cudaStream_t s) {
     IfaceArgs ia = iface_args(c, U0);
     k_iface<<<(nif + kWarps - 1) / kWarps, kThreads, 0, s>>>(ia);
     if (int rc = check_launch("iface (initial)")) return rc;
-    SolveArgs sa = solve_args(c, false, ft0, 1, U0);
-    if (cudaError_t e = launch_solve(c, sa, s)) return fail(IMEX_ERR_CUDA, std::string("solve (initial): ") + cudaGetErrorString(e));
+    if (cudaError_t e = launch_solve_chain(c, false, ft0, nullptr, 1, U0, c->upd, c->sol, s))
+      return fail(IMEX_ERR_CUDA, std::string("solve (initial): ") + cudaGetErrorString(e));
     if (int rc = check_launch("solve (initial)")) return rc;
   }
   return IMEX_OK;
 }
 
-// Static schedule of the implicit solve.  Components are bin-packed into
-// groups (one cluster each), largest factor first onto the lightest group;
-// each level's nodes are sorted by decreasing work and dealt to the cluster's
-// CTAs round-robin.  Every CTA gets one blob holding, in the order it visits
-// them, each of its nodes' [L_tt^{-1} (ld b|1) | L_{rows,t} (ld m|1)],
-// 16-byte aligned, for both S and M^cc.  The plan tries shared-memory budgets
-// from small (more co-resident clusters) to large and keeps the first whose
-// largest blob fits; otherwise the blobs are read from global memory.
+// Static schedule of the implicit solve.
+//  * Split level per component: the smallest level L >= 1 such that the nodes
+//    at levels >= L hold at most kZmax rows; those rows form the dense top.
+//  * Walked levels l = 0 .. max L - 1: the level's nodes of every component are
+//    packed into CTAs, largest FP64 work first onto the least-loaded CTA that
+//    still has a free warp and room in its shared-memory blob (<= 8 nodes,
+//    one warp each), aiming at one CTA per SM.  A CTA's blob holds its nodes'
+//    [L_tt^{-1} (ld b|1) | L_{rows,t} (ld m|1)], 16-byte aligned, for S and M^cc.
+//  * Dense tops: each component's rows are cut into chunks so that the whole
+//    launch has about one CTA per SM.
 struct SolvePlan {
-  std::vector<int> gl_nodes, gl_ptr, gl_base, gc_ptr, gc_list, slot, ilist;
-  std::vector<int64_t> b_off, b_len, foff, i_off, i_len, roff;
+  std::vector<int> lev_cta0, lev_ncta, cta_node_ptr, cta_nodes;
+  std::vector<int64_t> blob_off, blob_len, node_boff;
   std::vector<double> blobS, blobM;
   int64_t max_blob = 0;
-  // dense top part per component
-  std::vector<int> lz, zsize, zbase, zrow, zfwd_ptr, zfwd_pos;
+  std::vector<int> top_comp, top_r0, top_r1;
+  std::vector<int> zsize, zbase, zrow, zfwd_ptr, zfwd_pos;
   std::vector<int64_t> zA_off;
   std::vector<double> zA_S, zA_M;
   int max_zn = 0;
 };
 
-constexpr int kZmax = 400;   // largest dense top block per component
+#ifndef IMEX_DENSE_TOP_MAX
+#define IMEX_DENSE_TOP_MAX 600
+#endif
+constexpr int kZmax = IMEX_DENSE_TOP_MAX;   // largest dense top block per component
+constexpr int kTargetCTAs = 152;            // one CTA per SM
 
 // A_Z = (L_ZZ L_ZZ^T)^{-1} (row-major zn x zn) from the factor blocks of the
 // component's top nodes; Z rows are the nodes' c-indices in ascending order.
@@ -902,52 +818,47 @@ void dense_top(const HostSetup& hs, const Factor& F, const std::vector<int>& zno
     }
 }
 
-int plan_solve(imex_ctx* c, SolvePlan& best) {
+int plan_solve(imex_ctx* c, SolvePlan& P) {
   const HostSetup& hs = c->hs;
   const int64_t nt = (int64_t)hs.tree.size();
   auto node_work = [&](int t) {
     const TreeNode& T = hs.tree[t];
     const int64_t b = T.end - T.beg, m = (int64_t)T.rows.size();
-    return b * b + m * b;
+    return b * b / 2 + m * b + b;
   };
-  std::vector<int64_t> cw(hs.ncomp, 0);
-  for (int k = 0; k < hs.ncomp; ++k)
-    for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t) cw[k] += node_work(t);
   // Split level of each component: nodes at level >= lz form the dense top part.
   std::vector<int> lz(hs.ncomp, 1), zsize(hs.ncomp, 0), zbase(hs.ncomp, 0), zrow, zpos(hs.n_c, -1);
   std::vector<int64_t> zA_off(hs.ncomp, 0);
   std::vector<double> zA_S, zA_M;
   int max_zn = 0;
-  {
-    for (int k = 0; k < hs.ncomp; ++k) {
-      int maxlev = 0;
-      for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t) maxlev = std::max(maxlev, hs.tree[t].level);
-      int L = maxlev + 1;
-      for (int cand = 1; cand <= maxlev + 1; ++cand) {
-        int z = 0;
-        for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t)
-          if (hs.tree[t].level >= cand) z += hs.tree[t].end - hs.tree[t].beg;
-        if (z <= kZmax) { L = cand; break; }
-      }
-      lz[k] = L;
-      std::vector<int> znodes;
+  for (int k = 0; k < hs.ncomp; ++k) {
+    int maxlev = 0;
+    for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t) maxlev = std::max(maxlev, hs.tree[t].level);
+    int L = maxlev + 1;
+    for (int cand = 1; cand <= maxlev + 1; ++cand) {
+      int z = 0;
       for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t)
-        if (hs.tree[t].level >= L) znodes.push_back(t);
-      zbase[k] = (int)zrow.size();
-      for (int t : znodes)
-        for (int r = hs.tree[t].beg; r < hs.tree[t].end; ++r) zrow.push_back(r);
-      std::sort(zrow.begin() + zbase[k], zrow.end());
-      zsize[k] = (int)zrow.size() - zbase[k];
-      max_zn = std::max(max_zn, zsize[k]);
-      for (int i = 0; i < zsize[k]; ++i) zpos[zrow[zbase[k] + i]] = i;
-      zA_off[k] = (int64_t)zA_S.size();
-      if (zsize[k] > 0) {
-        std::vector<double> A;
-        dense_top(hs, hs.S, znodes, zpos, zsize[k], A);
-        zA_S.insert(zA_S.end(), A.begin(), A.end());
-        dense_top(hs, hs.Mcc, znodes, zpos, zsize[k], A);
-        zA_M.insert(zA_M.end(), A.begin(), A.end());
-      }
+        if (hs.tree[t].level >= cand) z += hs.tree[t].end - hs.tree[t].beg;
+      if (z <= kZmax) { L = cand; break; }
+    }
+    lz[k] = L;
+    std::vector<int> znodes;
+    for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t)
+      if (hs.tree[t].level >= L) znodes.push_back(t);
+    zbase[k] = (int)zrow.size();
+    for (int t : znodes)
+      for (int r = hs.tree[t].beg; r < hs.tree[t].end; ++r) zrow.push_back(r);
+    std::sort(zrow.begin() + zbase[k], zrow.end());
+    zsize[k] = (int)zrow.size() - zbase[k];
+    max_zn = std::max(max_zn, zsize[k]);
+    for (int i = 0; i < zsize[k]; ++i) zpos[zrow[zbase[k] + i]] = i;
+    zA_off[k] = (int64_t)zA_S.size();
+    if (zsize[k] > 0) {
+      std::vector<double> A;
+      dense_top(hs, hs.S, znodes, zpos, zsize[k], A);
+      zA_S.insert(zA_S.end(), A.begin(), A.end());
+      dense_top(hs, hs.Mcc, znodes, zpos, zsize[k], A);
+      zA_M.insert(zA_M.end(), A.begin(), A.end());
     }
   }
   // Updates into the dense rows from the walked levels only.
@@ -1036,149 +947,95 @@ int plan_solve(imex_ctx* c, SolvePlan& best) {
     if (!(std::sqrt(dn / std::max(rn, 1e-300)) < 1e-9))
       return fail(IMEX_ERR_NOT_SPD, "dense top-level solve disagrees with the tree solve");
   }
-  const size_t vec_doubles = (size_t)(3 + kWarps) * c->solve_width + (size_t)((max_zn + 1) / 2) * 2;
-  bool have = false;
-  for (int cl : {16, 8}) {
-    for (int budget_kb : {64, 96, 128, 160, 200}) {
-      const size_t budget = (size_t)budget_kb * 1024;
-      const int nclu = max_clusters(cl, budget);
-      if (nclu <= 0) continue;
-      SolvePlan P;
-      const int ngroups = std::max(1, std::min(hs.ncomp, nclu));
-      std::vector<int> order(hs.ncomp);
-      std::iota(order.begin(), order.end(), 0);
-      std::sort(order.begin(), order.end(), [&](int x, int y) { return cw[x] > cw[y]; });
-      std::vector<std::vector<int>> members(ngroups);
-      std::vector<int64_t> load(ngroups, 0);
-      for (int k : order) {
-        int gsel = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        members[gsel].push_back(k);
-        load[gsel] += cw[k];
+  // Walked levels: pack each level's nodes into CTAs.
+  int nlev = 0;
+  for (size_t t = 0; t < hs.tree.size(); ++t)
+    if (!is_top((int)t)) nlev = std::max(nlev, hs.tree[t].level + 1);
+  const size_t vec_doubles = (size_t)3 * kWarps * c->walk_W;
+  const int64_t blob_cap = (int64_t)((kWalkSmemBudget / sizeof(double)) - vec_doubles);
+  P.node_boff.assign(nt, 0);
+  P.cta_node_ptr.assign(1, 0);
+  for (int l = 0; l < nlev; ++l) {
+    std::vector<int> nodes;
+    for (size_t t = 0; t < hs.tree.size(); ++t)
+      if (!is_top((int)t) && hs.tree[t].level == l) nodes.push_back((int)t);
+    std::sort(nodes.begin(), nodes.end(), [&](int x, int y) { return node_work(x) > node_work(y); });
+    auto bytes_of = [&](int t) {
+      const TreeNode& T = hs.tree[t];
+      const int64_t b = T.end - T.beg, m = (int64_t)T.rows.size();
+      return (b | 1) * b + (m | 1) * b;
+    };
+    const int target = std::max(1, std::min<int>((int)nodes.size(), kTargetCTAs));
+    std::vector<std::vector<int>> per(target);
+    std::vector<int64_t> work(target, 0), used(target, 0);
+    for (int t : nodes) {
+      int best = -1;
+      for (int r = 0; r < (int)per.size(); ++r) {
+        if ((int)per[r].size() >= kWarps) continue;
+        if (!per[r].empty() && used[r] + bytes_of(t) > blob_cap) continue;
+        if (best < 0 || work[r] < work[best]) best = r;
       }
-      P.gc_ptr.push_back(0);
-      for (int gi = 0; gi < ngroups; ++gi) {
-        int nl = 0;
-        for (int k : members[gi]) {
-          P.gc_list.push_back(k);
-          for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t) nl = std::max(nl, hs.tree[t].level + 1);
-        }
-        P.gc_ptr.push_back((int)P.gc_list.size());
-        std::vector<std::vector<int>> byl(nl);
-        for (int k : members[gi])
-          for (int t = hs.comp_tree_ptr[k]; t < hs.comp_tree_ptr[k + 1]; ++t)
-            if (!is_top(t)) byl[hs.tree[t].level].push_back(t);
-        while (!byl.empty() && byl.back().empty()) byl.pop_back();
-        nl = (int)byl.size();
-        P.gl_base.push_back((int)P.gl_ptr.size());
-        P.gl_ptr.push_back((int)P.gl_nodes.size());
-        for (int l = 0; l < nl; ++l) {
-          std::sort(byl[l].begin(), byl[l].end(), [&](int x, int y) { return node_work(x) > node_work(y); });
-          P.gl_nodes.insert(P.gl_nodes.end(), byl[l].begin(), byl[l].end());
-          P.gl_ptr.push_back((int)P.gl_nodes.size());
-        }
+      if (best < 0) {
+        per.emplace_back();
+        work.push_back(0);
+        used.push_back(0);
+        best = (int)per.size() - 1;
       }
-      P.gl_base.push_back((int)P.gl_ptr.size());
-      P.b_off.assign((size_t)ngroups * cl, 0);
-      P.b_len.assign((size_t)ngroups * cl, 0);
-      P.foff.assign(nt, 0);
-      P.slot.assign(nt, 0);
-      P.roff.assign(nt, 0);
-      P.i_off.assign((size_t)ngroups * cl, 0);
-      P.i_len.assign((size_t)ngroups * cl, 0);
-      int max_rows = 2;
-      int64_t max_blob = 0, max_ilist = 0;
-      for (int gi = 0; gi < ngroups; ++gi) {
-        const int nlv = P.gl_base[gi + 1] - P.gl_base[gi] - 1;
-        for (int rk = 0; rk < cl; ++rk) {
-          const int cta = gi * cl + rk;
-          int rows_here = 0;
-          if (P.blobS.size() % 2) { P.blobS.push_back(0.0); P.blobM.push_back(0.0); }
-          P.b_off[cta] = (int64_t)P.blobS.size();
-          int64_t local = 0;
-          for (int l = 0; l < nlv; ++l) {
-            const int qb = P.gl_ptr[P.gl_base[gi] + l], qe = P.gl_ptr[P.gl_base[gi] + l + 1];
-            for (int q = qb + rk; q < qe; q += cl) {
-              const int t = P.gl_nodes[q];
-              const TreeNode& T = hs.tree[t];
-              const int b = T.end - T.beg, m = (int)T.rows.size();
-              const int ldi = b | 1, ldr = m | 1;
-              P.slot[t] = rows_here;
-              rows_here += b;
-              P.foff[t] = local;
-              for (const Factor* F : {&hs.S, &hs.Mcc}) {
-                std::vector<double>& out = (F == &hs.S) ? P.blobS : P.blobM;
-                const double* Li = F->vals.data() + T.off_diag;
-                const double* L21 = F->vals.data() + T.off_rect;
-                for (int j = 0; j < b; ++j)
-                  for (int i = 0; i < ldi; ++i) out.push_back(i < b ? Li[i + (size_t)b * j] : 0.0);
-                for (int j = 0; j < b; ++j)
-                  for (int i = 0; i < ldr; ++i) out.push_back(i < m ? L21[i + (size_t)m * j] : 0.0);
-              }
-              local += (int64_t)ldi * b + (int64_t)ldr * b;
-            }
-          }
-          if (local % 2) { P.blobS.push_back(0.0); P.blobM.push_back(0.0); ++local; }
-          P.b_len[cta] = local;
-          max_blob = std::max(max_blob, local);
-          max_rows = std::max(max_rows, rows_here + (rows_here & 1));
-          // Index lists of this CTA: [row ptr (rows_here + 1) | positions | ancestor rows].
-          std::vector<int> mine;
-          for (int l = 0; l < nlv; ++l) {
-            const int qb = P.gl_ptr[P.gl_base[gi] + l], qe = P.gl_ptr[P.gl_base[gi] + l + 1];
-            for (int q = qb + rk; q < qe; q += cl) mine.push_back(P.gl_nodes[q]);
-          }
-          std::vector<int> rp(1, 0), pos, anc;
-          for (int t : mine)
-            for (int r = hs.tree[t].beg; r < hs.tree[t].end; ++r) {
-              for (int k = hs.fwd_ptr[r]; k < hs.fwd_ptr[r + 1]; ++k) pos.push_back(hs.fwd_pos[k]);
-              rp.push_back((int)pos.size());
-            }
-          const int npos_base = (int)rp.size();
-          for (int& v : rp) v += npos_base;            // positions follow the row pointers
-          std::vector<int> lst = rp;
-          lst.insert(lst.end(), pos.begin(), pos.end());
-          for (int t : mine) {
-            P.roff[t] = (int64_t)lst.size();
-            lst.insert(lst.end(), hs.tree[t].rows.begin(), hs.tree[t].rows.end());
-          }
-          while (lst.size() % 4) lst.push_back(0);
-          while (P.ilist.size() % 4) P.ilist.push_back(0);
-          P.i_off[cta] = (int64_t)P.ilist.size();
-          P.i_len[cta] = (int64_t)lst.size();
-          P.ilist.insert(P.ilist.end(), lst.begin(), lst.end());
-          max_ilist = std::max(max_ilist, (int64_t)lst.size());
-        }
-      }
-      const size_t ibytes = (size_t)max_ilist * sizeof(int);
-      const size_t need = (vec_doubles + (size_t)max_rows + (size_t)max_blob) * sizeof(double) + ibytes;
-      const bool fits = need <= budget;
-      P.max_blob = max_blob;
-      P.lz = lz;
-      P.zsize = zsize;
-      P.zbase = zbase;
-      P.zrow = zrow;
-      P.zfwd_ptr = zfwd_ptr;
-      P.zfwd_pos = zfwd_pos;
-      P.zA_off = zA_off;
-      P.max_zn = max_zn;
-      if (fits || (!have && budget_kb == 200 && cl == 8)) {
-        c->max_zn = ((max_zn + 1) / 2) * 2;
-        c->cluster = cl;
-        c->ngroups = ngroups;
-        c->max_cta_rows = max_rows;
-        c->solve_smem_mode = fits ? 1 : 0;
-        c->smem_solve = fits ? need : (vec_doubles + (size_t)max_rows) * sizeof(double) + ibytes;
-        c->max_blob = fits ? max_blob : 0;
-        P.zA_S = zA_S;
-        P.zA_M = zA_M;
-        best = std::move(P);
-        have = true;
-        if (fits) return IMEX_OK;
-      }
+      per[best].push_back(t);
+      work[best] += node_work(t);
+      used[best] += bytes_of(t);
     }
-    if (have && c->solve_smem_mode) break;
+    P.lev_cta0.push_back((int)P.blob_off.size());
+    int ncta = 0;
+    for (auto& list : per) {
+      if (list.empty()) continue;
+      ++ncta;
+      if (P.blobS.size() % 2) { P.blobS.push_back(0.0); P.blobM.push_back(0.0); }
+      P.blob_off.push_back((int64_t)P.blobS.size());
+      int64_t local = 0;
+      for (int t : list) {
+        const TreeNode& T = hs.tree[t];
+        const int b = T.end - T.beg, m = (int)T.rows.size();
+        const int ldi = b | 1, ldr = m | 1;
+        P.node_boff[t] = local;
+        for (const Factor* F : {&hs.S, &hs.Mcc}) {
+          std::vector<double>& out = (F == &hs.S) ? P.blobS : P.blobM;
+          const double* Li = F->vals.data() + T.off_diag;
+          const double* L21 = F->vals.data() + T.off_rect;
+          for (int j = 0; j < b; ++j)
+            for (int i = 0; i < ldi; ++i) out.push_back(i < b ? Li[i + (size_t)b * j] : 0.0);
+          for (int j = 0; j < b; ++j)
+            for (int i = 0; i < ldr; ++i) out.push_back(i < m ? L21[i + (size_t)m * j] : 0.0);
+        }
+        local += (int64_t)ldi * b + (int64_t)ldr * b;
+        P.cta_nodes.push_back(t);
+      }
+      if (local % 2) { P.blobS.push_back(0.0); P.blobM.push_back(0.0); ++local; }
+      P.blob_len.push_back(local);
+      P.max_blob = std::max(P.max_blob, local);
+      P.cta_node_ptr.push_back((int)P.cta_nodes.size());
+    }
+    P.lev_ncta.push_back(ncta);
   }
-  if (!have) return fail(IMEX_ERR_CUDA, "no thread-block cluster configuration fits the solve kernel");
+  // Dense tops: row chunks, about one CTA per SM over the whole launch.
+  int64_t zsum = 0;
+  for (int k = 0; k < hs.ncomp; ++k) zsum += zsize[k];
+  const int chunk = (int)std::max<int64_t>(kWarps, ((zsum + kTargetCTAs - 1) / kTargetCTAs + kWarps - 1) / kWarps * kWarps);
+  for (int k = 0; k < hs.ncomp; ++k)
+    for (int r0 = 0; r0 < zsize[k]; r0 += chunk) {
+      P.top_comp.push_back(k);
+      P.top_r0.push_back(r0);
+      P.top_r1.push_back(std::min(zsize[k], r0 + chunk));
+    }
+  P.zsize = zsize;
+  P.zbase = zbase;
+  P.zrow = zrow;
+  P.zfwd_ptr = zfwd_ptr;
+  P.zfwd_pos = zfwd_pos;
+  P.zA_off = zA_off;
+  P.zA_S = std::move(zA_S);
+  P.zA_M = std::move(zA_M);
+  P.max_zn = max_zn;
   return IMEX_OK;
 }
 
@@ -1315,8 +1172,6 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     c->ntx = (hs.nn[0] + OX - 1) / OX;
     c->nty = (hs.nn[1] + OX - 1) / OX;
     c->smem_explicit = explicit_smem_doubles(P, c->TC) * sizeof(double);
-    c->solve_width = std::max(1, std::max(hs.max_block, hs.max_rows));
-    c->solve_width += c->solve_width % 2;
 
     // Operators of the explicit apply: sx = rho c^2 h_y / h_x, sy = rho c^2 h_x / h_y.
     const double sx = pb.rho * pb.c0 * pb.c0 * hs.h[1] / hs.h[0];
@@ -1350,31 +1205,35 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     std::vector<double> fxc(nc);
     for (int64_t r = 0; r < nc; ++r) fxc[r] = hs.fx[hs.c_node[r]];
     std::vector<int> tb(nt), te(nt), tn(nt);
-    std::vector<int64_t> od(nt), odT(nt), orc(nt), orw(nt), ou(nt);
+    std::vector<int64_t> orw(nt), ou(nt);
     for (int64_t t = 0; t < nt; ++t) {
       const TreeNode& T = hs.tree[t];
       tb[t] = T.beg;
       te[t] = T.end;
       tn[t] = (int)T.rows.size();
-      od[t] = T.off_diag;
-      odT[t] = T.off_diagT;
-      orc[t] = T.off_rect;
       orw[t] = T.off_rows;
       ou[t] = T.off_upd;
     }
-    std::vector<int> ccb(hs.ncomp), cce(hs.ncomp);
-    for (int k = 0; k < hs.ncomp; ++k) {
-      ccb[k] = hs.tree[hs.comp_tree_ptr[k]].beg;
-      cce[k] = hs.tree[hs.comp_tree_ptr[k + 1] - 1].end;
-    }
-    std::vector<int64_t> off_rT(nt);
-    for (int64_t t = 0; t < nt; ++t) off_rT[t] = hs.tree[t].off_rectT;
+    c->walk_W = std::max(2, std::max(hs.max_block, hs.max_rows));
+    c->walk_W += c->walk_W & 1;
     SolvePlan plan;
     if (int rc = plan_solve(c, plan)) {
-      imex_destroy(c);
+      delete c;
       return rc;
     }
+    {
+      const size_t vec = (size_t)3 * kWarps * c->walk_W * sizeof(double);
+      const size_t staged = vec + (size_t)plan.max_blob * sizeof(double);
+      c->walk_smem_mode = staged <= kWalkSmemBudget ? 1 : 0;
+      c->smem_walk = c->walk_smem_mode ? staged : vec;
+      c->smem_top = (size_t)std::max(2, plan.max_zn) * sizeof(double);
+      c->lev_cta0 = plan.lev_cta0;
+      c->lev_ncta = plan.lev_ncta;
+      c->ntop = (int)plan.top_comp.size();
+      c->nzrow = (int64_t)plan.zrow.size();
+    }
     const int64_t nif = (int64_t)hs.if_cell.size();
+    const size_t nblobcta = std::max<size_t>(plan.blob_off.size(), 1);
 
     Arena ar;
     ar.add(&c->U[0], nn);
@@ -1389,22 +1248,33 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->a_c, std::max<int64_t>(nc, 1));
     ar.add(&c->fxc, std::max<int64_t>(nc, 1));
     ar.add(&c->sol, std::max<int64_t>(nc, 1));
+    ar.add(&c->upd, std::max<int64_t>(hs.upd_size, 1));
     ar.add(&c->if_cell, std::max<int64_t>(nif, 1));
     ar.add(&c->if_kidx, std::max<int64_t>(nif, 1));
     ar.add(&c->if_c2, std::max<int64_t>(nif, 1));
     ar.add(&c->cutK, std::max<size_t>(hs.cutK.size(), 1));
     ar.add(&c->uncutK, hs.uncutK.size());
     ar.add(&c->Y, std::max<int64_t>(nif * hs.Pd, 1));
-    ar.add(&c->S_blob, std::max<size_t>(plan.blobS.size(), 2));
-    ar.add(&c->M_blob, std::max<size_t>(plan.blobM.size(), 2));
-    ar.add(&c->blob_off, std::max<size_t>(plan.b_off.size(), 1));
-    ar.add(&c->blob_len, std::max<size_t>(plan.b_len.size(), 1));
-    ar.add(&c->t_foff, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_slot, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_roff, std::max<int64_t>(nt, 1));
-    ar.add(&c->ilist, std::max<size_t>(plan.ilist.size(), 4));
-    ar.add(&c->ilist_off, std::max<size_t>(plan.i_off.size(), 1));
-    ar.add(&c->ilist_len, std::max<size_t>(plan.i_len.size(), 1));
+    ar.add(&c->contrib_ptr, hs.contrib_ptr.size());
+    ar.add(&c->contrib_pos, std::max<size_t>(hs.contrib_pos.size(), 1));
+    ar.add(&c->fwd_ptr, hs.fwd_ptr.size());
+    ar.add(&c->fwd_pos, std::max<size_t>(hs.fwd_pos.size(), 1));
+    ar.add(&c->t_beg, std::max<int64_t>(nt, 1));
+    ar.add(&c->t_end, std::max<int64_t>(nt, 1));
+    ar.add(&c->t_nrows, std::max<int64_t>(nt, 1));
+    ar.add(&c->t_off_rows, std::max<int64_t>(nt, 1));
+    ar.add(&c->t_off_upd, std::max<int64_t>(nt, 1));
+    ar.add(&c->rows_idx, std::max<size_t>(hs.rows_idx.size(), 1));
+    ar.add(&c->blob_S, std::max<size_t>(plan.blobS.size(), 2));
+    ar.add(&c->blob_M, std::max<size_t>(plan.blobM.size(), 2));
+    ar.add(&c->blob_off, nblobcta);
+    ar.add(&c->blob_len, nblobcta);
+    ar.add(&c->node_boff, std::max<int64_t>(nt, 1));
+    ar.add(&c->cta_node_ptr, plan.cta_node_ptr.size());
+    ar.add(&c->cta_nodes, std::max<size_t>(plan.cta_nodes.size(), 1));
+    ar.add(&c->top_comp, std::max<size_t>(plan.top_comp.size(), 1));
+    ar.add(&c->top_r0, std::max<size_t>(plan.top_r0.size(), 1));
+    ar.add(&c->top_r1, std::max<size_t>(plan.top_r1.size(), 1));
     ar.add(&c->zsize, std::max<size_t>(plan.zsize.size(), 1));
     ar.add(&c->zbase, std::max<size_t>(plan.zbase.size(), 1));
     ar.add(&c->zrow, std::max<size_t>(plan.zrow.size(), 1));
@@ -1413,29 +1283,6 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->zA_off, std::max<size_t>(plan.zA_off.size(), 1));
     ar.add(&c->zA_S, std::max<size_t>(plan.zA_S.size(), 1));
     ar.add(&c->zA_M, std::max<size_t>(plan.zA_M.size(), 1));
-    ar.add(&c->zg, std::max<size_t>(plan.zrow.size(), 1));
-    ar.add(&c->t_beg, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_end, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_nrows, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_off_diag, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_off_diagT, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_off_rect, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_off_rows, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_off_upd, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_off_rectT, std::max<int64_t>(nt, 1));
-    ar.add(&c->rows_idx, std::max<size_t>(hs.rows_idx.size(), 1));
-    ar.add(&c->grp_level_nodes, std::max<size_t>(plan.gl_nodes.size(), 1));
-    ar.add(&c->grp_level_ptr, std::max<size_t>(plan.gl_ptr.size(), 1));
-    ar.add(&c->grp_level_base, std::max<size_t>(plan.gl_base.size(), 1));
-    ar.add(&c->grp_comp_ptr, std::max<size_t>(plan.gc_ptr.size(), 1));
-    ar.add(&c->grp_comps, std::max<size_t>(plan.gc_list.size(), 1));
-    ar.add(&c->comp_cbeg, std::max(hs.ncomp, 1));
-    ar.add(&c->comp_cend, std::max(hs.ncomp, 1));
-    ar.add(&c->contrib_ptr, hs.contrib_ptr.size());
-    ar.add(&c->contrib_pos, std::max<size_t>(hs.contrib_pos.size(), 1));
-    ar.add(&c->fwd_ptr, hs.fwd_ptr.size());
-    ar.add(&c->fwd_pos, std::max<size_t>(hs.fwd_pos.size(), 1));
-    ar.add(&c->upd, std::max<int64_t>(hs.upd_size, 1));
     ar.add(&c->ft_buf, 2);
     ar.add(&c->rec_buf, c->io_cap);
     ar.add(&c->rec_nodes, c->io_cap);
@@ -1469,16 +1316,26 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->if_c2, hs.if_c2);
     e = e ? e : upload(c->cutK, hs.cutK);
     e = e ? e : upload(c->uncutK, hs.uncutK);
-    e = e ? e : upload(c->S_blob, plan.blobS);
-    e = e ? e : upload(c->M_blob, plan.blobM);
-    e = e ? e : upload(c->blob_off, plan.b_off);
-    e = e ? e : upload(c->blob_len, plan.b_len);
-    e = e ? e : upload(c->t_foff, plan.foff);
-    e = e ? e : upload(c->t_slot, plan.slot);
-    e = e ? e : upload(c->t_roff, plan.roff);
-    e = e ? e : upload(c->ilist, plan.ilist);
-    e = e ? e : upload(c->ilist_off, plan.i_off);
-    e = e ? e : upload(c->ilist_len, plan.i_len);
+    e = e ? e : upload(c->contrib_ptr, hs.contrib_ptr);
+    e = e ? e : upload(c->contrib_pos, hs.contrib_pos);
+    e = e ? e : upload(c->fwd_ptr, hs.fwd_ptr);
+    e = e ? e : upload(c->fwd_pos, hs.fwd_pos);
+    e = e ? e : upload(c->t_beg, tb);
+    e = e ? e : upload(c->t_end, te);
+    e = e ? e : upload(c->t_nrows, tn);
+    e = e ? e : upload(c->t_off_rows, orw);
+    e = e ? e : upload(c->t_off_upd, ou);
+    e = e ? e : upload(c->rows_idx, hs.rows_idx);
+    e = e ? e : upload(c->blob_S, plan.blobS);
+    e = e ? e : upload(c->blob_M, plan.blobM);
+    e = e ? e : upload(c->blob_off, plan.blob_off);
+    e = e ? e : upload(c->blob_len, plan.blob_len);
+    e = e ? e : upload(c->node_boff, plan.node_boff);
+    e = e ? e : upload(c->cta_node_ptr, plan.cta_node_ptr);
+    e = e ? e : upload(c->cta_nodes, plan.cta_nodes);
+    e = e ? e : upload(c->top_comp, plan.top_comp);
+    e = e ? e : upload(c->top_r0, plan.top_r0);
+    e = e ? e : upload(c->top_r1, plan.top_r1);
     e = e ? e : upload(c->zsize, plan.zsize);
     e = e ? e : upload(c->zbase, plan.zbase);
     e = e ? e : upload(c->zrow, plan.zrow);
@@ -1487,28 +1344,10 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->zA_off, plan.zA_off);
     e = e ? e : upload(c->zA_S, plan.zA_S);
     e = e ? e : upload(c->zA_M, plan.zA_M);
-    c->nzrow = (int64_t)plan.zrow.size();
-    e = e ? e : upload(c->t_beg, tb);
-    e = e ? e : upload(c->t_end, te);
-    e = e ? e : upload(c->t_nrows, tn);
-    e = e ? e : upload(c->t_off_diag, od);
-    e = e ? e : upload(c->t_off_diagT, odT);
-    e = e ? e : upload(c->t_off_rect, orc);
-    e = e ? e : upload(c->t_off_rows, orw);
-    e = e ? e : upload(c->t_off_upd, ou);
-    e = e ? e : upload(c->t_off_rectT, off_rT);
-    e = e ? e : upload(c->rows_idx, hs.rows_idx);
-    e = e ? e : upload(c->grp_level_nodes, plan.gl_nodes);
-    e = e ? e : upload(c->grp_level_ptr, plan.gl_ptr);
-    e = e ? e : upload(c->grp_level_base, plan.gl_base);
-    e = e ? e : upload(c->grp_comp_ptr, plan.gc_ptr);
-    e = e ? e : upload(c->grp_comps, plan.gc_list);
-    e = e ? e : upload(c->comp_cbeg, ccb);
-    e = e ? e : upload(c->comp_cend, cce);
-    e = e ? e : upload(c->contrib_ptr, hs.contrib_ptr);
-    e = e ? e : upload(c->contrib_pos, hs.contrib_pos);
-    e = e ? e : upload(c->fwd_ptr, hs.fwd_ptr);
-    e = e ? e : upload(c->fwd_pos, hs.fwd_pos);
+    for (auto fn : {k_walk<true, true>, k_walk<false, true>, k_walk<true, false>, k_walk<false, false>})
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWalkSmemBudget);
+    if (e == cudaSuccess && c->smem_top > 48 * 1024)
+      e = cudaFuncSetAttribute(k_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_top);
     e = e ? e : set_explicit_smem_dispatch(P, c->smem_explicit);
     if (e != cudaSuccess) {
       std::string msg = std::string("upload failed: ") + cudaGetErrorString(e);
@@ -1554,9 +1393,7 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
     IfaceArgs ia = iface_args(c, Unext);
     k_iface<<<(nif + kWarps - 1) / kWarps, kThreads, 0, s>>>(ia);
     if (ev) cudaEventRecord(ev[2], s);
-    SolveArgs sa = solve_args(c, true, ft_at(hs, step + 1), 0, Unext);
-    sa.ft_dev = ft_dev;
-    launch_solve(c, sa, s);
+    launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, c->upd, c->sol, s);
   } else if (ev) {
     cudaEventRecord(ev[2], s);
   }
@@ -1733,9 +1570,11 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   if (!c || !st) return fail(IMEX_ERR_ARG, "bad arguments");
   fill_stats(c->hs, st);
   st->step = c->step;
-  st->solve_cluster = c->cluster;
-  st->solve_groups = c->ngroups;
-  st->solve_smem_bytes = (int64_t)c->smem_solve;
+  st->solve_levels = (int64_t)c->lev_cta0.size();
+  int64_t widest = c->ntop;
+  for (int n : c->lev_ncta) widest = std::max<int64_t>(widest, n);
+  st->solve_ctas = widest;
+  st->solve_smem_bytes = (int64_t)c->smem_walk;
   st->device_bytes = (int64_t)c->bytes;
   return IMEX_OK;
 }
@@ -1757,8 +1596,8 @@ void imex_destroy(imex_ctx* c) {
 
 // ---------------------------------------------------------------------------
 // imex_step_noalloc: imex_step with the implicit solve's scratch (descendant
-// update vectors, right-hand sides of the dense top blocks, solution vector)
-// in a fixed array compiled into the library instead of context memory.
+// update vectors, solution vector) in a fixed array compiled into the library
+// instead of context memory.
 #include <mutex>
 
 namespace {
@@ -1775,10 +1614,9 @@ extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
   const HostSetup& hs = c->hs;
   auto even = [](int64_t v) { return v + (v & 1); };
   const int64_t n_upd = even(std::max<int64_t>(hs.upd_size, 1));
-  const int64_t n_zg = even(std::max<int64_t>(c->nzrow, 1));
   const int64_t n_sol = even(std::max<int64_t>(hs.n_c, 1));
-  if (n_upd + n_zg + n_sol > kStaticScratchDoubles)
-    return fail(IMEX_ERR_ARG, "imex_step_noalloc: the implicit solve needs " + std::to_string(n_upd + n_zg + n_sol) +
+  if (n_upd + n_sol > kStaticScratchDoubles)
+    return fail(IMEX_ERR_ARG, "imex_step_noalloc: the implicit solve needs " + std::to_string(n_upd + n_sol) +
                                   " doubles of scratch; the static scratch holds " +
                                   std::to_string(kStaticScratchDoubles) + " (use imex_step)");
   int dev = -1;
@@ -1798,8 +1636,7 @@ extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
     base = g_static_scratch_addr[dev];
   }
   double* upd = base;
-  double* zg = upd + n_upd;
-  double* sol = zg + n_zg;
+  double* sol = upd + n_upd;
   cudaStream_t s = (cudaStream_t)stream;
   c->stream = s;
   const double dt = hs.dt;
@@ -1813,11 +1650,7 @@ extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
     if (hs.n_c > 0) {
       IfaceArgs ia = iface_args(c, Unext);
       k_iface<<<(nif + kWarps - 1) / kWarps, kThreads, 0, s>>>(ia);
-      SolveArgs sa = solve_args(c, true, ft_at(hs, step + 1), 0, Unext);
-      sa.upd = upd;
-      sa.zg = zg;
-      sa.sol = sol;
-      launch_solve(c, sa, s);
+      launch_solve_chain(c, true, ft_at(hs, step + 1), nullptr, 0, Unext, upd, sol, s);
     }
     if (int rc = check_launch("imex_step_noalloc")) return rc;
     c->cur = 1 - c->cur;

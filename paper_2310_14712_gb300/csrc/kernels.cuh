@@ -1,6 +1,6 @@
 // Time-stepping kernels of the immersed Newmark IMEX method (sm_103a, FP64).
 //
-// One IMEX step (Fig. TrapCDMIMEX) is three launches:
+// One IMEX step (Fig. TrapCDMIMEX) is these launches:
 //   k_explicit   A1 + A2: K^d u_n over uncut cells by sum factorisation on the
 //                tensor grid (exact for every I_d row, whose cells are all
 //                uncut), fused with the CDM update on the lumped mass
@@ -9,11 +9,13 @@
 //   k_iface      A4: dense element products K_e u_pred for every cell touching
 //                I_c (stored matrices of cut cells, the uncut-cell matrix
 //                otherwise).
-//   k_solve      A4 gather + A5 + A6: right-hand side f_t(t_{n+1}) f_x^c - K^c
-//                u_pred, forward/backward solve with the supernodal
-//                nested-dissection Cholesky factor of S (inverted diagonal
-//                blocks), Newmark correction; one thread-block cluster per
-//                group of components.
+//   k_walk / k_top   A4 gather + A5 + A6: right-hand side
+//                f_t(t_{n+1}) f_x^c - K^c u_pred, forward walk over the lower
+//                levels of the supernodal nested-dissection Cholesky factor
+//                of S (inverted diagonal blocks), one dense product per
+//                component for the upper levels, backward walk, Newmark
+//                correction.  One launch per level; kernel boundaries are the
+//                level barriers, so every launch can use every SM.
 #pragma once
 #include <cstdint>
 
@@ -84,66 +86,71 @@ struct IfaceArgs {
   int nx, ny;
 };
 
-struct SolveArgs {
-  // factor, packed per CTA of the launch in consumption order
-  const double* vals;           // blob array (one blob per CTA of the launch)
-  const int64_t* blob_off;      // [cta]: offset of the CTA's blob (16-byte aligned)
-  const int64_t* blob_len;      // [cta]: length in doubles (even)
-  const int64_t* t_foff;        // node -> offset of [L_tt^{-1} (ld b|1) | L_{rows,t} (ld m|1)] in its blob
-  const int* t_slot;            // node -> first row slot in its CTA's right-hand-side array
-  int max_cta_rows;             // even
-  int64_t max_blob;             // doubles of the largest blob staged in shared memory (0: not staged)
-  const int* ilist;             // per-CTA index lists: [row ptr | update positions | ancestor rows]
-  const int64_t* ilist_off;     // [cta] (multiple of 4 ints)
-  const int64_t* ilist_len;     // [cta] (multiple of 4 ints)
-  const int64_t* t_roff;        // node -> offset of its ancestor rows in its CTA's index list
-  // dense top part of each component: x_Z = A_Z (rhs_Z - updates from the walked levels)
-  const int* zsize;             // [comp] |Z|
-  const int* zbase;             // [comp] offset into zrow / zg / zfwd_ptr
-  const int* zrow;              // c-index of each Z row
-  const double* zA;             // row-major |Z| x |Z| blocks
-  const int64_t* zA_off;        // [comp]
-  const int* zfwd_ptr;          // per Z row: update positions from the walked levels
-  const int* zfwd_pos;
-  double* zg;                   // scratch: right-hand side of the Z rows
-  int max_zn;                   // even
+// One level of the supernodal walk of A5 (forward or backward), all
+// components at once.  The level's supernodes are packed into CTAs (one warp
+// per supernode); each CTA's blocks [L_tt^{-1} (ld b|1) | L_{rows,t} (ld m|1)]
+// are stored contiguously in `blob`.
+struct WalkArgs {
+  int cta0;                     // first CTA of this level in the per-CTA arrays
+  const double* blob;
+  const int64_t* blob_off;      // [cta] (16-byte aligned)
+  const int64_t* blob_len;      // [cta] (even)
+  const int* cta_node_ptr;      // [cta] -> range in cta_nodes
+  const int* cta_nodes;
+  const int64_t* node_boff;     // tree node -> offset of its blocks in its CTA's blob
   const int* t_beg;
   const int* t_end;
   const int* t_nrows;
-  const int64_t* t_off_diag;
-  const int64_t* t_off_diagT;
-  const int64_t* t_off_rect;
-  const int64_t* t_off_rows;
-  const int64_t* t_off_upd;
-  const int64_t* t_off_rectT;
+  const int64_t* t_off_upd;     // tree node -> its update vector in `upd`
+  const int64_t* t_off_rows;    // tree node -> its ancestor rows in `rows_idx`
   const int* rows_idx;
-  // schedule: groups of components, one thread-block cluster each
-  const int* grp_level_nodes;
-  const int* grp_level_ptr;
-  const int* grp_level_base;
-  const int* grp_comp_ptr;
-  const int* grp_comps;
-  const int* comp_cbeg;
-  const int* comp_cend;
-  // right-hand side
-  const int* contrib_ptr;
+  const int* fwd_ptr;           // c-row -> positions of descendant updates in `upd`
+  const int* fwd_pos;
+  const int* contrib_ptr;       // c-row -> positions of element products in `Y`
   const int* contrib_pos;
   const double* Y;
-  const int* fwd_ptr;
-  const int* fwd_pos;
+  const double* fxc;
+  double ft;                    // f_t(t_{n+1}) (step) or f_t(0) (initial acceleration)
+  const double* ft_dev;         // if set: f_t(t_{n+1}) = ft_dev[1]
   double* upd;
   double* sol;
-  const double* fxc;
-  double ft;              // f_t(t_{n+1}) (step) or f_t(0) (init)
-  const double* ft_dev;   // if set: f_t(t_{n+1}) = ft_dev[1]
-  // state
-  int mode;               // 0: step with correction; 1: store a^c only
+  int W;                        // per-warp vector length (>= largest supernode and row set)
+  // correction of the rows this launch finalises (backward only)
+  int mode;                     // 0: Newmark correction; 1: store the acceleration only
   const int* c_node;
-  double* U;              // holds u_pred on I_c; receives u^c_{n+1}
+  double* U;                    // holds u_pred on I_c; receives u^c_{n+1}
   double* v_c;
   double* a_c;
   double dt;
-  int max_width;          // max(largest supernode, largest row set)
+};
+
+// Dense top block of every component: x_Z = A_Z (rhs_Z - updates from the
+// walked levels), A_Z = (L_ZZ L_ZZ^T)^{-1}; each CTA owns a chunk of rows.
+struct TopArgs {
+  const int* cta_comp;          // [cta] component
+  const int* cta_r0;            // [cta] first row of the chunk (within the component's Z)
+  const int* cta_r1;
+  const int* zsize;             // [comp] |Z|
+  const int* zbase;             // [comp] offset into zrow / zfwd_ptr
+  const int* zrow;              // c-index of each Z row
+  const int64_t* zA_off;        // [comp] offset of A_Z (row-major |Z| x |Z|)
+  const double* zA;
+  const int* zfwd_ptr;          // per Z row: update positions from the walked levels
+  const int* zfwd_pos;
+  const int* contrib_ptr;
+  const int* contrib_pos;
+  const double* Y;
+  const double* fxc;
+  double ft;
+  const double* ft_dev;
+  const double* upd;
+  double* sol;
+  int mode;
+  const int* c_node;
+  double* U;
+  double* v_c;
+  double* a_c;
+  double dt;
 };
 
 }  // namespace imex
