@@ -294,7 +294,7 @@ def run_gpu(args):
         "warm": {"value": ws * n_act * args.steps / (warm_ms * 1e-3), "ms_per_step": warm_ms / args.steps},
         "e2e": e2e,
         "clocks": clocks,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": st["launches_per_step"] * args.steps,
         "setup_seconds": st["setup_seconds"],
         "wall_seconds_timed_loop": wall,
     }

@@ -109,6 +109,7 @@ typedef struct {
   int64_t solve_levels;    /* tree levels walked per pass of the implicit solve (one launch each) */
   int64_t solve_ctas;      /* CTAs of the widest solve launch */
   int64_t solve_smem_bytes;/* shared memory per walk CTA (factor blocks staged when they fit) */
+  int64_t launches_per_step; /* kernel launches of one imex_step step */
 } imex_stats;
 
 /*

@@ -310,13 +310,17 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
   double* wy = wg + W;
   double* wx = wy + W;
   double* blob = sm + kWarps * 3 * W;
+  // Index lists of this CTA: per row slot {contribution begin, update begin,
+  // update end} into the position lists that follow, then ancestor rows.
+  int* il = reinterpret_cast<int*>(blob + a.max_blob);
   const int64_t boff = a.blob_off[cta];
   if (kSmem) async_copy_16(blob, a.blob + boff, a.blob_len[cta] / 2);
+  async_copy_16(il, a.ilist + a.ilist_off[cta], a.ilist_len[cta] / 4);
   const double* B = kSmem ? blob : a.blob + boff;
   // Let the next launch stage its constants; wait for the previous results.
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  if (kSmem) async_copy_wait();
+  async_copy_wait();
   const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
   for (int q = a.cta_node_ptr[cta] + warp; q < a.cta_node_ptr[cta + 1]; q += kWarps) {
     const int t = a.cta_nodes[q];
@@ -325,15 +329,14 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
     const double* Li = B + a.node_boff[t];           // L_tt^{-1}: b x b, column-major, ld ldi
     const double* L21 = Li + (size_t)ldi * b;        // L_{rows,t}: m x b, column-major, ld ldr
     if (kForward) {
+      const int* rh = il + 3 * a.node_slot[t];
       for (int i = lane; i < b; i += 32) {
-        const int r = beg + i;
-        double v = ft * a.fxc[r];
-        const int c0 = a.contrib_ptr[r], c1 = a.contrib_ptr[r + 1];
+        const int cb = rh[3 * i], fb = rh[3 * i + 1], fe = rh[3 * i + 2];
+        double v = ft * a.fxc[beg + i];
 #pragma unroll 4
-        for (int k = c0; k < c1; ++k) v -= a.Y[a.contrib_pos[k]];
-        const int f0 = a.fwd_ptr[r], f1 = a.fwd_ptr[r + 1];
+        for (int k = cb; k < fb; ++k) v -= a.Y[il[k]];
 #pragma unroll 4
-        for (int k = f0; k < f1; ++k) v -= __ldcg(a.upd + a.fwd_pos[k]);
+        for (int k = fb; k < fe; ++k) v -= __ldcg(a.upd + il[k]);
         wg[i] = v;
       }
       __syncwarp();
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
       if (m > 0) warp_gemv(L21, 1, ldr, m, b, wy, 0, a.upd + a.t_off_upd[t], lane);  // upd = L21 y
       __syncwarp();
     } else {
-      const int* rows = a.rows_idx + a.t_off_rows[t];
+      const int* rows = il + a.node_roff[t];
       for (int k = lane; k < m; k += 32) wx[k] = -__ldcg(a.sol + rows[k]);
       __syncwarp();
       warp_gemv(L21, ldr, 1, b, m, wx, 0, wg, lane);      // -L_{rows,t}^T x_rows
@@ -362,39 +365,42 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
-  extern __shared__ __align__(16) double zs[];
+  extern __shared__ __align__(16) double tsm[];
   const int cta = blockIdx.x;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int comp = a.cta_comp[cta], r0 = a.cta_r0[cta], r1 = a.cta_r1[cta];
   const int zn = a.zsize[comp], zb = a.zbase[comp];
+  double* zs = tsm;                               // max_zn (even): right-hand side of the block
+  double* Ac = zs + a.max_zn;                     // max_rows_zn: this CTA's rows of A_Z
+  int* il = reinterpret_cast<int*>(Ac + a.max_arows);  // per row {contribution begin, update begin, end}
+  async_copy_16(Ac, a.zA + a.zA_off[comp] + (size_t)r0 * zn, ((int64_t)(r1 - r0) * zn + 1) / 2);
+  async_copy_16(il, a.ilist + a.ilist_off[cta], a.ilist_len[cta] / 4);
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  async_copy_wait();
   const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
   // The whole right-hand side of this component's top block (redundant per CTA).
   for (int i = threadIdx.x; i < zn; i += kThreads) {
-    const int r = a.zrow[zb + i];
-    double v = ft * a.fxc[r];
-    const int c0 = a.contrib_ptr[r], c1 = a.contrib_ptr[r + 1];
+    const int cb = il[3 * i], fb = il[3 * i + 1], fe = il[3 * i + 2];
+    double v = ft * a.fxc[a.zrow[zb + i]];
 #pragma unroll 4
-    for (int k = c0; k < c1; ++k) v -= a.Y[a.contrib_pos[k]];
-    const int f0 = a.zfwd_ptr[zb + i], f1 = a.zfwd_ptr[zb + i + 1];
+    for (int k = cb; k < fb; ++k) v -= a.Y[il[k]];
 #pragma unroll 4
-    for (int k = f0; k < f1; ++k) v -= __ldcg(a.upd + a.zfwd_pos[k]);
+    for (int k = fb; k < fe; ++k) v -= __ldcg(a.upd + il[k]);
     zs[i] = v;
   }
   __syncthreads();
-  const double* A = a.zA + a.zA_off[comp];
   for (int i = r0 + warp; i < r1; i += kWarps) {
-    const double* Ar = A + (size_t)i * zn;
+    const double* Ar = Ac + (size_t)(i - r0) * zn;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int j = lane;
     for (; j + 96 < zn; j += 128) {
-      s0 = fma(__ldg(Ar + j), zs[j], s0);
-      s1 = fma(__ldg(Ar + j + 32), zs[j + 32], s1);
-      s2 = fma(__ldg(Ar + j + 64), zs[j + 64], s2);
-      s3 = fma(__ldg(Ar + j + 96), zs[j + 96], s3);
+      s0 = fma(Ar[j], zs[j], s0);
+      s1 = fma(Ar[j + 32], zs[j + 32], s1);
+      s2 = fma(Ar[j + 64], zs[j + 64], s2);
+      s3 = fma(Ar[j + 96], zs[j + 96], s3);
     }
-    for (; j < zn; j += 32) s0 = fma(__ldg(Ar + j), zs[j], s0);
+    for (; j < zn; j += 32) s0 = fma(Ar[j], zs[j], s0);
     double v = (s0 + s1) + (s2 + s3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -488,6 +494,13 @@ struct imex_ctx {
   double *blob_S = nullptr, *blob_M = nullptr;
   int64_t *blob_off = nullptr, *blob_len = nullptr, *node_boff = nullptr;
   int *cta_node_ptr = nullptr, *cta_nodes = nullptr;
+  int *ilist = nullptr, *node_slot = nullptr, *node_roff = nullptr;
+  int64_t *ilist_off = nullptr, *ilist_len = nullptr;
+  int64_t walk_max_blob = 0;
+  int* tlist = nullptr;
+  int64_t *tlist_off = nullptr, *tlist_len = nullptr;
+  int top_max_zn = 2;
+  int64_t top_max_arows = 0;
   std::vector<int> lev_cta0, lev_ncta;   // per walked level: CTA range
   int walk_smem_mode = 0;
   size_t smem_walk = 0, smem_top = 0;
@@ -635,7 +648,9 @@ IfaceArgs iface_args(imex_ctx* c, const double* src) {
 }
 
 constexpr int kMaxWidth = 256;                 // largest supernode / row set of the walk
-constexpr size_t kWalkSmemBudget = 200 * 1024;  // shared memory per walk CTA
+constexpr size_t kWalkSmemBudget = 200 * 1024;  // shared memory per walk CTA (staged factor)
+constexpr size_t kTopSmemBudget = 200 * 1024;   // shared memory per dense-top CTA
+constexpr size_t kMaxDynSmem = 227 * 1024;      // largest dynamic shared memory of a CTA
 
 // The launches of the implicit solve (after k_iface): forward walk over the
 // lower levels, dense tops, backward walk with the correction.  use_S selects
@@ -651,6 +666,12 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   w.cta_node_ptr = c->cta_node_ptr;
   w.cta_nodes = c->cta_nodes;
   w.node_boff = c->node_boff;
+  w.max_blob = c->walk_max_blob;
+  w.ilist = c->ilist;
+  w.ilist_off = c->ilist_off;
+  w.ilist_len = c->ilist_len;
+  w.node_slot = c->node_slot;
+  w.node_roff = c->node_roff;
   w.t_beg = c->t_beg;
   w.t_end = c->t_end;
   w.t_nrows = c->t_nrows;
@@ -683,6 +704,11 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   z.zrow = c->zrow;
   z.zA_off = c->zA_off;
   z.zA = use_S ? c->zA_S : c->zA_M;
+  z.max_zn = c->top_max_zn;
+  z.max_arows = c->top_max_arows;
+  z.ilist = c->tlist;
+  z.ilist_off = c->tlist_off;
+  z.ilist_len = c->tlist_len;
   z.zfwd_ptr = c->zfwd_ptr;
   z.zfwd_pos = c->zfwd_pos;
   z.contrib_ptr = c->contrib_ptr;
@@ -772,7 +798,15 @@ struct SolvePlan {
   std::vector<int64_t> blob_off, blob_len, node_boff;
   std::vector<double> blobS, blobM;
   int64_t max_blob = 0;
+  // Per-CTA index lists of the walk: row headers, position lists, ancestor rows.
+  std::vector<int> ilist, node_slot, node_roff;
+  std::vector<int64_t> ilist_off, ilist_len;
+  int64_t max_ilist = 0;
   std::vector<int> top_comp, top_r0, top_r1;
+  // Per-component index lists of the dense tops (one entry per top CTA).
+  std::vector<int> tlist;
+  std::vector<int64_t> tlist_off, tlist_len;
+  int64_t max_tlist = 0, max_arows = 0;
   std::vector<int> zsize, zbase, zrow, zfwd_ptr, zfwd_pos;
   std::vector<int64_t> zA_off;
   std::vector<double> zA_S, zA_M;
@@ -852,6 +886,7 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
     zsize[k] = (int)zrow.size() - zbase[k];
     max_zn = std::max(max_zn, zsize[k]);
     for (int i = 0; i < zsize[k]; ++i) zpos[zrow[zbase[k] + i]] = i;
+    if (zA_S.size() % 2) { zA_S.push_back(0.0); zA_M.push_back(0.0); }
     zA_off[k] = (int64_t)zA_S.size();
     if (zsize[k] > 0) {
       std::vector<double> A;
@@ -954,16 +989,25 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
   const size_t vec_doubles = (size_t)3 * kWarps * c->walk_W;
   const int64_t blob_cap = (int64_t)((kWalkSmemBudget / sizeof(double)) - vec_doubles);
   P.node_boff.assign(nt, 0);
+  P.node_slot.assign(nt, 0);
+  P.node_roff.assign(nt, 0);
   P.cta_node_ptr.assign(1, 0);
   for (int l = 0; l < nlev; ++l) {
     std::vector<int> nodes;
     for (size_t t = 0; t < hs.tree.size(); ++t)
       if (!is_top((int)t) && hs.tree[t].level == l) nodes.push_back((int)t);
     std::sort(nodes.begin(), nodes.end(), [&](int x, int y) { return node_work(x) > node_work(y); });
-    auto bytes_of = [&](int t) {
+    auto ints_of = [&](int t) {
+      const TreeNode& T = hs.tree[t];
+      int64_t n = 3 * (int64_t)(T.end - T.beg) + (int64_t)T.rows.size();
+      for (int r = T.beg; r < T.end; ++r)
+        n += (hs.contrib_ptr[r + 1] - hs.contrib_ptr[r]) + (hs.fwd_ptr[r + 1] - hs.fwd_ptr[r]);
+      return n;
+    };
+    auto bytes_of = [&](int t) {   // in doubles: factor blocks and index lists
       const TreeNode& T = hs.tree[t];
       const int64_t b = T.end - T.beg, m = (int64_t)T.rows.size();
-      return (b | 1) * b + (m | 1) * b;
+      return (b | 1) * b + (m | 1) * b + (ints_of(t) + 1) / 2 + 2;
     };
     const int target = std::max(1, std::min<int>((int)nodes.size(), kTargetCTAs));
     std::vector<std::vector<int>> per(target);
@@ -1012,6 +1056,35 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
       }
       if (local % 2) { P.blobS.push_back(0.0); P.blobM.push_back(0.0); ++local; }
       P.blob_len.push_back(local);
+      // Index list: {contribution begin, update begin, end} per row slot (in
+      // node order), then the position lists, then each node's ancestor rows.
+      const int64_t i0 = (int64_t)P.ilist.size();
+      int nslot = 0;
+      for (int t : list) {
+        P.node_slot[t] = nslot;
+        nslot += hs.tree[t].end - hs.tree[t].beg;
+      }
+      std::vector<int> L(3 * (size_t)nslot, 0);
+      for (int t : list) {
+        const TreeNode& T = hs.tree[t];
+        for (int r = T.beg; r < T.end; ++r) {
+          const size_t h = 3 * (size_t)(P.node_slot[t] + r - T.beg);
+          L[h] = (int)L.size();
+          for (int k = hs.contrib_ptr[r]; k < hs.contrib_ptr[r + 1]; ++k) L.push_back(hs.contrib_pos[k]);
+          L[h + 1] = (int)L.size();
+          for (int k = hs.fwd_ptr[r]; k < hs.fwd_ptr[r + 1]; ++k) L.push_back(hs.fwd_pos[k]);
+          L[h + 2] = (int)L.size();
+        }
+      }
+      for (int t : list) {
+        P.node_roff[t] = (int)L.size();
+        L.insert(L.end(), hs.tree[t].rows.begin(), hs.tree[t].rows.end());
+      }
+      while (L.size() % 4) L.push_back(0);
+      P.ilist.insert(P.ilist.end(), L.begin(), L.end());
+      P.ilist_off.push_back(i0);
+      P.ilist_len.push_back((int64_t)L.size());
+      P.max_ilist = std::max<int64_t>(P.max_ilist, (int64_t)L.size());
       P.max_blob = std::max(P.max_blob, local);
       P.cta_node_ptr.push_back((int)P.cta_nodes.size());
     }
@@ -1020,12 +1093,46 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
   // Dense tops: row chunks, about one CTA per SM over the whole launch.
   int64_t zsum = 0;
   for (int k = 0; k < hs.ncomp; ++k) zsum += zsize[k];
-  const int chunk = (int)std::max<int64_t>(kWarps, ((zsum + kTargetCTAs - 1) / kTargetCTAs + kWarps - 1) / kWarps * kWarps);
+  std::vector<std::vector<int>> tl(hs.ncomp);
+  for (int k = 0; k < hs.ncomp; ++k) {
+    const int zn = zsize[k], zb = zbase[k];
+    std::vector<int>& L = tl[k];
+    L.assign(3 * (size_t)zn, 0);
+    for (int i = 0; i < zn; ++i) {
+      const int r = zrow[zb + i];
+      L[3 * i] = (int)L.size();
+      for (int q = hs.contrib_ptr[r]; q < hs.contrib_ptr[r + 1]; ++q) L.push_back(hs.contrib_pos[q]);
+      L[3 * i + 1] = (int)L.size();
+      for (int q = zfwd_ptr[zb + i]; q < zfwd_ptr[zb + i + 1]; ++q) L.push_back(zfwd_pos[q]);
+      L[3 * i + 2] = (int)L.size();
+    }
+    while (L.size() % 4) L.push_back(0);
+    P.max_tlist = std::max<int64_t>(P.max_tlist, (int64_t)L.size());
+  }
+  const int64_t max_zn_even = std::max(2, max_zn + (max_zn & 1));
+  int chunk = (int)std::max<int64_t>(kWarps, ((zsum + kTargetCTAs - 1) / kTargetCTAs + kWarps - 1) / kWarps * kWarps);
+  auto top_smem = [&](int ch) {
+    const int64_t rows = (int64_t)std::min(ch, max_zn) * max_zn;
+    return (size_t)(max_zn_even + rows + (rows & 1)) * sizeof(double) + (size_t)P.max_tlist * sizeof(int);
+  };
+  while (chunk > kWarps && top_smem(chunk) > kTopSmemBudget) chunk -= kWarps;
+  if (top_smem(chunk) > kTopSmemBudget)
+    return fail(IMEX_ERR_ARG, "dense top block too large for shared memory (lower IMEX_DENSE_TOP_MAX)");
+  std::vector<int64_t> comp_off(hs.ncomp, 0);
+  for (int k = 0; k < hs.ncomp; ++k) {
+    comp_off[k] = (int64_t)P.tlist.size();
+    P.tlist.insert(P.tlist.end(), tl[k].begin(), tl[k].end());
+  }
   for (int k = 0; k < hs.ncomp; ++k)
     for (int r0 = 0; r0 < zsize[k]; r0 += chunk) {
+      const int r1 = std::min(zsize[k], r0 + chunk);
       P.top_comp.push_back(k);
       P.top_r0.push_back(r0);
-      P.top_r1.push_back(std::min(zsize[k], r0 + chunk));
+      P.top_r1.push_back(r1);
+      P.tlist_off.push_back(comp_off[k]);
+      P.tlist_len.push_back((int64_t)tl[k].size());
+      const int64_t rows = (int64_t)(r1 - r0) * zsize[k];
+      P.max_arows = std::max<int64_t>(P.max_arows, rows + (rows & 1));
     }
   P.zsize = zsize;
   P.zbase = zbase;
@@ -1033,6 +1140,7 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
   P.zfwd_ptr = zfwd_ptr;
   P.zfwd_pos = zfwd_pos;
   P.zA_off = zA_off;
+  for (int k = 0; k < 2; ++k) { zA_S.push_back(0.0); zA_M.push_back(0.0); }   // tail of the last 16-byte copy
   P.zA_S = std::move(zA_S);
   P.zA_M = std::move(zA_M);
   P.max_zn = max_zn;
@@ -1223,10 +1331,18 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     }
     {
       const size_t vec = (size_t)3 * kWarps * c->walk_W * sizeof(double);
-      const size_t staged = vec + (size_t)plan.max_blob * sizeof(double);
+      const size_t lists = (size_t)plan.max_ilist * sizeof(int);
+      const size_t staged = vec + (size_t)plan.max_blob * sizeof(double) + lists;
       c->walk_smem_mode = staged <= kWalkSmemBudget ? 1 : 0;
-      c->smem_walk = c->walk_smem_mode ? staged : vec;
-      c->smem_top = (size_t)std::max(2, plan.max_zn) * sizeof(double);
+      c->walk_max_blob = c->walk_smem_mode ? plan.max_blob : 0;
+      c->smem_walk = c->walk_smem_mode ? staged : vec + lists;
+      c->top_max_zn = std::max(2, plan.max_zn + (plan.max_zn & 1));
+      c->top_max_arows = plan.max_arows;
+      c->smem_top = (size_t)(c->top_max_zn + plan.max_arows) * sizeof(double) + (size_t)plan.max_tlist * sizeof(int);
+      if (c->smem_walk > kMaxDynSmem || c->smem_top > kMaxDynSmem) {
+        delete c;
+        return fail(IMEX_ERR_ARG, "solve schedule exceeds the shared memory of a CTA");
+      }
       c->lev_cta0 = plan.lev_cta0;
       c->lev_ncta = plan.lev_ncta;
       c->ntop = (int)plan.top_comp.size();
@@ -1272,6 +1388,14 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->node_boff, std::max<int64_t>(nt, 1));
     ar.add(&c->cta_node_ptr, plan.cta_node_ptr.size());
     ar.add(&c->cta_nodes, std::max<size_t>(plan.cta_nodes.size(), 1));
+    ar.add(&c->ilist, std::max<size_t>(plan.ilist.size(), 4));
+    ar.add(&c->node_slot, std::max<int64_t>(nt, 1));
+    ar.add(&c->node_roff, std::max<int64_t>(nt, 1));
+    ar.add(&c->ilist_off, nblobcta);
+    ar.add(&c->ilist_len, nblobcta);
+    ar.add(&c->tlist, std::max<size_t>(plan.tlist.size(), 4));
+    ar.add(&c->tlist_off, std::max<size_t>(plan.tlist_off.size(), 1));
+    ar.add(&c->tlist_len, std::max<size_t>(plan.tlist_len.size(), 1));
     ar.add(&c->top_comp, std::max<size_t>(plan.top_comp.size(), 1));
     ar.add(&c->top_r0, std::max<size_t>(plan.top_r0.size(), 1));
     ar.add(&c->top_r1, std::max<size_t>(plan.top_r1.size(), 1));
@@ -1333,6 +1457,14 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->node_boff, plan.node_boff);
     e = e ? e : upload(c->cta_node_ptr, plan.cta_node_ptr);
     e = e ? e : upload(c->cta_nodes, plan.cta_nodes);
+    e = e ? e : upload(c->ilist, plan.ilist);
+    e = e ? e : upload(c->node_slot, plan.node_slot);
+    e = e ? e : upload(c->node_roff, plan.node_roff);
+    e = e ? e : upload(c->ilist_off, plan.ilist_off);
+    e = e ? e : upload(c->ilist_len, plan.ilist_len);
+    e = e ? e : upload(c->tlist, plan.tlist);
+    e = e ? e : upload(c->tlist_off, plan.tlist_off);
+    e = e ? e : upload(c->tlist_len, plan.tlist_len);
     e = e ? e : upload(c->top_comp, plan.top_comp);
     e = e ? e : upload(c->top_r0, plan.top_r0);
     e = e ? e : upload(c->top_r1, plan.top_r1);
@@ -1345,9 +1477,9 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->zA_S, plan.zA_S);
     e = e ? e : upload(c->zA_M, plan.zA_M);
     for (auto fn : {k_walk<true, true>, k_walk<false, true>, k_walk<true, false>, k_walk<false, false>})
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWalkSmemBudget);
-    if (e == cudaSuccess && c->smem_top > 48 * 1024)
-      e = cudaFuncSetAttribute(k_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_top);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
     e = e ? e : set_explicit_smem_dispatch(P, c->smem_explicit);
     if (e != cudaSuccess) {
       std::string msg = std::string("upload failed: ") + cudaGetErrorString(e);
@@ -1575,6 +1707,7 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   for (int n : c->lev_ncta) widest = std::max<int64_t>(widest, n);
   st->solve_ctas = widest;
   st->solve_smem_bytes = (int64_t)c->smem_walk;
+  st->launches_per_step = 2 + 2 * (int64_t)c->lev_cta0.size() + (c->ntop > 0 ? 1 : 0);
   st->device_bytes = (int64_t)c->bytes;
   return IMEX_OK;
 }

@@ -98,6 +98,12 @@ struct WalkArgs {
   const int* cta_node_ptr;      // [cta] -> range in cta_nodes
   const int* cta_nodes;
   const int64_t* node_boff;     // tree node -> offset of its blocks in its CTA's blob
+  int64_t max_blob;             // doubles reserved for the blob in shared memory (even)
+  const int* ilist;             // per-CTA index lists (see k_walk)
+  const int64_t* ilist_off;     // [cta] (multiple of 4)
+  const int64_t* ilist_len;     // [cta] (multiple of 4)
+  const int* node_slot;         // tree node -> first row slot in its CTA's list
+  const int* node_roff;         // tree node -> offset of its ancestor rows in its CTA's list
   const int* t_beg;
   const int* t_end;
   const int* t_nrows;
@@ -133,8 +139,13 @@ struct TopArgs {
   const int* zsize;             // [comp] |Z|
   const int* zbase;             // [comp] offset into zrow / zfwd_ptr
   const int* zrow;              // c-index of each Z row
-  const int64_t* zA_off;        // [comp] offset of A_Z (row-major |Z| x |Z|)
+  const int64_t* zA_off;        // [comp] offset of A_Z (row-major |Z| x |Z|, 16-byte aligned)
   const double* zA;
+  int max_zn;                   // even
+  int64_t max_arows;            // even: largest (r1 - r0) * |Z| over the CTAs
+  const int* ilist;             // per-CTA index lists: per Z row {contribution begin, update begin, end}
+  const int64_t* ilist_off;
+  const int64_t* ilist_len;
   const int* zfwd_ptr;          // per Z row: update positions from the walked levels
   const int* zfwd_pos;
   const int* contrib_ptr;

@@ -57,7 +57,7 @@ class Stats(ctypes.Structure):
         "n_nodes", "n_d", "n_c", "n_cut", "n_uncut", "n_empty", "n_iface", "nnz_L",
         "n_components", "n_tree", "max_block", "step", "device_bytes")] + \
         [(n, ctypes.c_double) for n in ("dt", "dt_crit_uncut", "setup_seconds", "residual_S", "residual_M")] + \
-        [(n, ctypes.c_int64) for n in ("solve_levels", "solve_ctas", "solve_smem_bytes")]
+        [(n, ctypes.c_int64) for n in ("solve_levels", "solve_ctas", "solve_smem_bytes", "launches_per_step")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
