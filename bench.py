@@ -22,6 +22,7 @@ Under torchrun (N > 1) every rank runs an independent replica on its own GPU
 timed region is bracketed by barriers and the max over ranks is taken.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -46,6 +47,37 @@ UNIT = "DOF-steps/s"
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 L2_FLUSH_BYTES = 256 << 20
 PHASES = ("k_explicit2d", "k_iface", "k_walk+k_top")
+
+
+# ncu summaries that carry each phase's DRAM bytes per launch (see profiles/).
+PROFILE_FILES = {"k_explicit2d": "k_explicit2d_plate256.md", "k_walk+k_top": "solve_kernels_plate256.md"}
+
+
+def profiled_traffic(phase, workload):
+    """DRAM bytes per launch from the committed ncu summary, or None.
+
+    The figure holds only for the kernel sources it was captured from: the
+    summary records their sha256 and any change to them yields None."""
+    name = PROFILE_FILES.get(phase)
+    if workload != "plate256" or name is None:
+        return None
+    try:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        line = line.strip().lstrip("-").strip()
+        for key in ("dram_bytes_per_launch", "source_sha256"):
+            if line.startswith(key + ":"):
+                vals[key] = line.split(":", 1)[1].strip()
+    if len(vals) != 2:
+        return None
+    h = hashlib.sha256()
+    for f in ("imex.cu", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2310_14712_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return int(vals["dram_bytes_per_launch"]) if h.hexdigest() == vals["source_sha256"] else None
 
 
 def measured_peaks():
@@ -261,7 +293,8 @@ def run_gpu(args):
     hbm = peaks.get("hbm_gbs")
     ach_gflops = alg[dom]["flops"] / (per_launch_ms[dom] * 1e-3) / 1e9
     roof = {"kernel": dom, "bound": "alu", "achieved": ach_gflops / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3,
-            "unit": "TFLOP/s", "frac": ach_gflops / FP64_PEAK_GFLOPS, "traffic": None,
+            "unit": "TFLOP/s", "frac": ach_gflops / FP64_PEAK_GFLOPS,
+            "traffic": profiled_traffic(dom, args.workload), "traffic_unit": "bytes per launch (ncu)",
             "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe)"}
     kernels = {}
     for nm in PHASES:
@@ -319,7 +352,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="plate256")
-    ap.add_argument("--cpu-steps", type=int, default=200)
+    ap.add_argument("--cpu-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
