@@ -42,12 +42,21 @@ constexpr int kWarps = kThreads / 32;
 //   x pass: T1 = (sx K1)_x u, T2 = (M1)_x u, cell by cell (the two cell
 //           contributions at a vertex are added in a fix-up pass),
 //   y pass: r = (M1)_y T1 + (sy K1)_y T2, again cell by cell plus fix-up.
+// Each 1D product uses the symmetry of the GLL nodes: K1 commutes with the
+// reflection x -> -x, so it maps the even and odd parts of a vector
+// separately (P^2 -> about P^2/2 FMAs), and the exact mass is the GLL-lumped
+// mass plus a rank-one term, M1 = diag(w) + C a a^T (GLL quadrature is exact
+// to degree 2p-1; the product of two basis functions differs from a
+// polynomial it integrates exactly by a_i a_j x^{2p}, a_i the leading
+// coefficient of the i-th basis function), so M1 v costs about 3P.
 // For an I_d node every surrounding cell is uncut, so this equals its row of
 // K^d u_n (Eq. Kd).  Nodes of I_c and inactive nodes are computed but not
 // written.  Cells outside the grid contribute nothing.
 template <int P, int TC>
 __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D ops) {
   constexpr int p = P - 1;
+  constexpr int H = P / 2;                // pairs (i, P-1-i) of the even-odd split
+  constexpr bool kOdd = (P % 2) == 1;     // a centre node; then a_{P-1-i} = a_i, else -a_i
   constexpr int OX = TC * p, OY = TC * p;
   constexpr int RX = (TC + 1) * p + 1, RY = RX;
   constexpr int NC = TC + 1;
@@ -97,17 +106,37 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
 #pragma unroll
     for (int j = 0; j < P; ++j) v[j] = su[yy * RX + cc * p + j];
     const bool valid = (cx >= 0 && cx < a.ncx);
+    // Even and odd parts of v under x -> -x.
+    double e[H], o[H];
 #pragma unroll
-    for (int i = 0; i < P; ++i) {
-      double s1 = 0.0, s2 = 0.0;
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        s1 = fma(ops.kx[i * P + j], v[j], s1);
-        s2 = fma(ops.mx[i * P + j], v[j], s2);
-      }
-      o1[i] = valid ? s1 : 0.0;
-      o2[i] = valid ? s2 : 0.0;
+    for (int j = 0; j < H; ++j) {
+      e[j] = v[j] + v[P - 1 - j];
+      o[j] = v[j] - v[P - 1 - j];
     }
+    // o1 = (sx K1) v: the even part maps to the even part, odd to odd.
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      double ev = kOdd ? ops.kxc[i] * v[H] : 0.0, od = 0.0;
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        ev = fma(ops.kxe[i][j], e[j], ev);
+        od = fma(ops.kxo[i][j], o[j], od);
+      }
+      o1[i] = valid ? ev + od : 0.0;
+      o1[P - 1 - i] = valid ? ev - od : 0.0;
+    }
+    if (kOdd) {
+      double ev = ops.kxc[H] * v[H];
+#pragma unroll
+      for (int j = 0; j < H; ++j) ev = fma(ops.kxe[H][j], e[j], ev);
+      o1[H] = valid ? ev : 0.0;
+    }
+    // o2 = M1 v = w .* v + C a (a^T v).
+    double sa = kOdd ? ops.a[H] * v[H] : 0.0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? e[j] : o[j], sa);
+#pragma unroll
+    for (int i = 0; i < P; ++i) o2[i] = valid ? fma(ops.w[i], v[i], ops.ca[i] * sa) : 0.0;
     if (cc >= 1) {
 #pragma unroll
       for (int i = 1; i < p; ++i) {
@@ -139,16 +168,34 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
       vb[j] = t2[(cr * p + j) * OX + xo];
     }
     const bool valid = (cy >= 0 && cy < a.ncy);
+    // o = M1 va + (sy K1) vb, the mass in rank-one form, the stiffness even-odd.
+    double sa = kOdd ? ops.a[H] * va[H] : 0.0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? va[j] + va[P - 1 - j] : va[j] - va[P - 1 - j], sa);
+    double e[H], od_[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      e[j] = vb[j] + vb[P - 1 - j];
+      od_[j] = vb[j] - vb[P - 1 - j];
+    }
     double o[P];
 #pragma unroll
-    for (int i = 0; i < P; ++i) {
-      double s = 0.0;
+    for (int i = 0; i < H; ++i) {
+      double ev = kOdd ? ops.kyc[i] * vb[H] : 0.0, od = 0.0;
 #pragma unroll
-      for (int j = 0; j < P; ++j) {
-        s = fma(ops.my[i * P + j], va[j], s);
-        s = fma(ops.ky[i * P + j], vb[j], s);
+      for (int j = 0; j < H; ++j) {
+        ev = fma(ops.kye[i][j], e[j], ev);
+        od = fma(ops.kyo[i][j], od_[j], od);
       }
-      o[i] = valid ? s : 0.0;
+      const int k = P - 1 - i;
+      o[i] = valid ? fma(ops.w[i], va[i], fma(ops.ca[i], sa, ev + od)) : 0.0;
+      o[k] = valid ? fma(ops.w[k], va[k], fma(ops.ca[k], sa, ev - od)) : 0.0;
+    }
+    if (kOdd) {
+      double ev = ops.kyc[H] * vb[H];
+#pragma unroll
+      for (int j = 0; j < H; ++j) ev = fma(ops.kye[H][j], e[j], ev);
+      o[H] = valid ? fma(ops.w[H], va[H], fma(ops.ca[H], sa, ev)) : 0.0;
     }
     if (cr >= 1) {
 #pragma unroll
@@ -1147,6 +1194,58 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
   return IMEX_OK;
 }
 
+// Even-odd and rank-one forms of the 1D operators of the explicit apply, each
+// checked against the plain matrices it replaces.
+int explicit_ops(const HostSetup& hs, double sx, double sy, Ops2D& ops) {
+  const int P = hs.P, p = hs.p, H = P / 2;
+  const bool odd = (P % 2) == 1;
+  double kmax = 0.0, mmax = 0.0, asym = 0.0;
+  for (int i = 0; i < P * P; ++i) {
+    kmax = std::max(kmax, std::fabs(hs.K1[i]));
+    mmax = std::max(mmax, std::fabs(hs.M1[i]));
+  }
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j)
+      asym = std::max(asym, std::fabs(hs.K1[i * P + j] - hs.K1[(P - 1 - i) * P + (P - 1 - j)]));
+  if (asym > 1e-11 * kmax) return fail(IMEX_ERR_ARG, "1D stiffness is not centrosymmetric");
+  ops = Ops2D{};
+  for (int q = 0; q < 2; ++q) {
+    const double sc = q == 0 ? sx : sy;
+    double(&ke)[5][4] = q == 0 ? ops.kxe : ops.kye;
+    double(&ko)[4][4] = q == 0 ? ops.kxo : ops.kyo;
+    double(&kc)[5] = q == 0 ? ops.kxc : ops.kyc;
+    for (int i = 0; i <= (odd ? H : H - 1); ++i) {
+      for (int j = 0; j < H; ++j) {
+        ke[i][j] = 0.5 * sc * (hs.K1[i * P + j] + hs.K1[i * P + (P - 1 - j)]);
+        if (i < H) ko[i][j] = 0.5 * sc * (hs.K1[i * P + j] - hs.K1[i * P + (P - 1 - j)]);
+      }
+      if (odd) kc[i] = sc * hs.K1[i * P + H];
+    }
+  }
+  // M1 = diag(w) + C a a^T, C = int x^{2p} - sum_k w_k x_k^{2p}.
+  double C = 2.0 / (2.0 * p + 1.0);
+  for (int k = 0; k < P; ++k) C -= hs.gll_w[k] * std::pow(hs.gll_x[k], 2 * p);
+  for (int i = 0; i < P; ++i) {
+    double d = 1.0;
+    for (int k = 0; k < P; ++k)
+      if (k != i) d *= hs.gll_x[i] - hs.gll_x[k];
+    ops.a[i] = 1.0 / d;
+    ops.w[i] = hs.gll_w[i];
+    ops.ca[i] = C * ops.a[i];
+  }
+  double err = 0.0;
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j)
+      err = std::max(err, std::fabs(hs.M1[i * P + j] - ((i == j ? ops.w[i] : 0.0) + C * ops.a[i] * ops.a[j])));
+  if (err > 1e-11 * mmax) return fail(IMEX_ERR_ARG, "1D mass does not split into GLL weights plus rank one");
+  for (int i = 0; i < P; ++i) {
+    const double s = (p % 2 == 0) ? 1.0 : -1.0;   // a_{P-1-i} = (-1)^p a_i
+    if (std::fabs(ops.a[P - 1 - i] - s * ops.a[i]) > 1e-10 * std::fabs(ops.a[i]))
+      return fail(IMEX_ERR_ARG, "GLL leading coefficients are not symmetric");
+  }
+  return IMEX_OK;
+}
+
 int build_context(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src,
                   Problem& pb) {
   if (!mesh || !src) return fail(IMEX_ERR_ARG, "mesh and source must not be NULL");
@@ -1284,11 +1383,9 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     // Operators of the explicit apply: sx = rho c^2 h_y / h_x, sy = rho c^2 h_x / h_y.
     const double sx = pb.rho * pb.c0 * pb.c0 * hs.h[1] / hs.h[0];
     const double sy = pb.rho * pb.c0 * pb.c0 * hs.h[0] / hs.h[1];
-    for (int i = 0; i < P * P; ++i) {
-      c->ops.kx[i] = sx * hs.K1[i];
-      c->ops.mx[i] = hs.M1[i];
-      c->ops.my[i] = hs.M1[i];
-      c->ops.ky[i] = sy * hs.K1[i];
+    if (int rc = explicit_ops(hs, sx, sy, c->ops)) {
+      delete c;
+      return rc;
     }
     if (!pb.cell_c.empty()) {
       delete c;

@@ -43,11 +43,18 @@ __host__ __device__ inline double wavelet_value(int kind, double f0, double t) {
   }
 }
 
-// 1D operators of the explicit apply, pre-scaled (2D):
+// 1D operators of the explicit apply (2D):
 //   r = sx (M1_y (x) K1_x) u + sy (K1_y (x) M1_x) u
-// kx = sx K1, mx = M1 (x pass), my = M1, ky = sy K1 (y pass); P x P row-major.
+// K1 (stiffness) in even-odd form, pre-scaled by sx (x pass) or sy (y pass),
+// H = P/2, rows i <= (P-1)/2:
+//   ke[i][j] = (A[i][j] + A[i][P-1-j]) / 2, ko[i][j] = (A[i][j] - A[i][P-1-j]) / 2
+//   (j < H), kc[i] = A[i][H] (P odd);  then for i < H, with e_j, o_j the even
+//   and odd parts of v:  (A v)_i = Ev_i + Od_i, (A v)_{P-1-i} = Ev_i - Od_i.
+// M1 (mass, unscaled) = diag(w) + C a a^T; ca = C a.
 struct Ops2D {
-  double kx[81], mx[81], my[81], ky[81];
+  double kxe[5][4], kxo[4][4], kxc[5];
+  double kye[5][4], kyo[4][4], kyc[5];
+  double w[9], ca[9], a[9];
 };
 
 struct ExplicitArgs {
