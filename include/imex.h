@@ -110,6 +110,7 @@ typedef struct {
   int64_t solve_ctas;      /* CTAs of the widest solve launch */
   int64_t solve_smem_bytes;/* shared memory per walk CTA (factor blocks staged when they fit) */
   int64_t launches_per_step; /* kernel launches of one imex_step step */
+  int64_t rhs_pairs;       /* (c-row, interface cell) pairs of K^c u: one P^d dot product each */
 } imex_stats;
 
 /*
@@ -137,12 +138,13 @@ int imex_setup(const imex_mesh *mesh, int p, double alpha, double dt, const imex
  */
 int imex_step(imex_ctx *ctx, int64_t n, void *stream);
 
+#define IMEX_PROFILE_PHASES 3
 /*
- * imex_step_profile - imex_step() with CUDA events recorded on `stream` around
- * each of the three kernels of every step, synchronising after each step.
- * phase_ms[3] receives the summed device times (ms) of: [0] explicit apply +
- * CDM update + prediction, [1] interface element products, [2] implicit
- * solve + correction.  For measurement; results equal imex_step()'s.
+ * imex_step_profile - imex_step() with CUDA events recorded on `stream`,
+ * synchronising after each step.  phase_ms[3] receives the summed device
+ * times (ms) of: [0] explicit apply + CDM update + prediction, [1] implicit
+ * chain (right-hand sides, solve, correction), [2] whole steps.  For
+ * measurement; results equal imex_step()'s.
  */
 int imex_step_profile(imex_ctx *ctx, int64_t n, void *stream, double *phase_ms);
 

@@ -63,6 +63,9 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int ntiles = a.ntx * a.nty;
+  // The first solve launch may start staging its constant factor blocks now;
+  // it waits for this grid (griddepcontrol.wait) before it reads u.
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 
   if ((int)blockIdx.x >= ntiles) {
     // Newmark prediction on I_c (Fig. TrapCDMIMEX, "Prediction").
@@ -228,47 +231,8 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
 }
 
 // ---------------------------------------------------------------------------
-// A4: element products y_e = K_e u_pred,e for every cell touching I_c.  One
-// warp per cell; the cell's nodal block is staged in shared memory.
-__global__ void __launch_bounds__(kThreads) k_iface(IfaceArgs a) {
-  // Let the solve launch now: it stages its factor while this kernel runs and
-  // waits (griddepcontrol.wait) before it reads the products.
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-  __shared__ double ue[kWarps][128];
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int e = blockIdx.x * kWarps + warp;
-  if (e >= a.n_iface) return;
-  const int cid = a.cell[e];
-  const int cx = cid % a.ncx;
-  const int cy = (cid / a.ncx) % a.ncy;
-  const int cz = cid / (a.ncx * a.ncy);
-  const size_t base = (size_t)cx * a.p + (size_t)a.nx * ((size_t)cy * a.p) +
-                      (size_t)a.nx * a.ny * ((size_t)cz * a.p);
-  for (int l = lane; l < a.Pd; l += 32) {
-    const int i = l % a.P, j = (l / a.P) % a.P, k = l / (a.P * a.P);
-    ue[warp][l] = a.SRC[base + i + (size_t)a.nx * j + (size_t)a.nx * a.ny * k];
-  }
-  __syncwarp();
-  const int ki = a.kidx[e];
-  const double* K = ki >= 0 ? a.cutK + (size_t)ki * a.Pd * a.Pd : a.uncutK;
-  const double sc = ki >= 0 ? 1.0 : a.c2[e];
-  for (int l = lane; l < a.Pd; l += 32) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int m = 0;
-    for (; m + 4 <= a.Pd; m += 4) {
-      s0 = fma(__ldg(K + l + (size_t)a.Pd * m), ue[warp][m], s0);
-      s1 = fma(__ldg(K + l + (size_t)a.Pd * (m + 1)), ue[warp][m + 1], s1);
-      s2 = fma(__ldg(K + l + (size_t)a.Pd * (m + 2)), ue[warp][m + 2], s2);
-      s3 = fma(__ldg(K + l + (size_t)a.Pd * (m + 3)), ue[warp][m + 3], s3);
-    }
-    for (; m < a.Pd; ++m) s0 = fma(__ldg(K + l + (size_t)a.Pd * m), ue[warp][m], s0);
-    a.Y[(size_t)e * a.Pd + l] = sc * ((s0 + s1) + (s2 + s3));
-  }
-}
-
-// ---------------------------------------------------------------------------
-// A4 gather + A5 + A6: the implicit solve S a = f_t(t_{n+1}) f_x^c - K^c u_pred
-// with the supernodal nested-dissection Cholesky factor of S, and the Newmark
+// A4 + A5 + A6: the implicit solve S a = f_t(t_{n+1}) f_x^c - K^c u_pred with
+// the supernodal nested-dissection Cholesky factor of S, and the Newmark
 // correction.  Per component, the lower levels of the dissection tree are
 // walked level by level (forward: y_t = L_tt^{-1}(rhs_t - descendant updates),
 // upd_t = L_{rows,t} y_t; backward: x_t = L_tt^{-T}(y_t - L_{rows,t}^T x_rows)),
@@ -276,10 +240,14 @@ __global__ void __launch_bounds__(kThreads) k_iface(IfaceArgs a) {
 // below), A_Z = (L_ZZ L_ZZ^T)^{-1} (no lower node is an ancestor of an upper
 // one, so L_BZ = 0).  Every level is one launch over all components: kernel
 // boundaries are the barriers, so each launch spreads its FP64 work over every
-// SM.  Launches are chained with programmatic dependent launch: a kernel
-// stages its constant factor blocks (cp.async) while its predecessor runs and
-// waits (griddepcontrol.wait, a hardware wait) before it reads its results.
-// All sums run in a fixed order, so results are deterministic.
+// SM.  Within a CTA all threads share the rows of all its supernodes in each
+// phase.  The first forward launch also forms the right-hand side of every
+// implicit row: K^c u_pred row by row, one dot product of a row of K_e with the
+// cell's nodal values per (row, interface cell) pair.  Launches are chained
+// with programmatic dependent launch: a kernel stages its constant factor
+// blocks and index lists (cp.async) while its predecessor runs and waits
+// (griddepcontrol.wait, a hardware wait) before it reads its results.  All
+// sums run in a fixed order, so results are deterministic.
 
 // Start an asynchronous copy of n 16-byte chunks global -> shared with all
 // threads (cp.async, no register staging); completed by async_copy_wait().
@@ -347,19 +315,62 @@ __device__ __forceinline__ void correct_row(const Args& a, int r, double acc) {
   a.a_c[r] = acc;
 }
 
+// Per-CTA index list of a walk launch (ints, offsets relative to its start):
+//   [0] nq nodes, [1] nslot rows (sum of b), [2] nm ancestor rows (sum of m),
+//   [3] nrhs, [4] npair (first launch only), [5..7] unused
+//   node table at 8:          nq x {t, beg, b, m, slot0, moff, boff, updoff}
+//   slot table:               nslot x {q, update begin, update end, 0}
+//   ancestor table:           nm x {q, c-row}
+//   right-hand-side rows:     nrhs x {c-row, pair begin, pair end, slot or -1}
+//   pairs (row of K_e, cell): npair x {first node of the cell, K row, cell, 0}
+//   update positions (into upd).
+struct WalkList {
+  const int* h;
+  const int* node;
+  const int* slot;
+  const int* anc;
+  const int* rhs;
+  const int* pair;
+  __device__ explicit WalkList(const int* il) : h(il) {
+    node = il + 8;
+    slot = node + 8 * il[0];
+    anc = slot + 4 * il[1];
+    rhs = anc + ((2 * il[2] + 3) & ~3);
+    pair = rhs + 4 * il[3];
+  }
+};
+
+// Right-hand side of one (row, cell) pair: row l of the cell matrix times the
+// cell's nodal values (the row of K_e is stored contiguously).
+__device__ __forceinline__ double pair_product(const WalkArgs& a, const int* pr) {
+  const double* K = a.Krows + (size_t)pr[1] * a.Pd;
+  const double* u = a.SRC + pr[0];
+  double s0 = 0.0, s1 = 0.0;
+  int m = 0;
+  for (int k = 0; k < (a.dim == 3 ? a.P : 1); ++k)
+    for (int j = 0; j < a.P; ++j) {
+      const double* ur = u + (size_t)k * a.nx * a.ny + (size_t)j * a.nx;
+      int i = 0;
+      for (; i + 2 <= a.P; i += 2, m += 2) {
+        s0 = fma(__ldg(K + m), __ldcg(ur + i), s0);
+        s1 = fma(__ldg(K + m + 1), __ldcg(ur + i + 1), s1);
+      }
+      if (i < a.P) { s0 = fma(__ldg(K + m), __ldcg(ur + i), s0); ++m; }
+    }
+  return a.if_sc[pr[2]] * (s0 + s1);
+}
+
 template <bool kForward, bool kSmem>
 __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
   extern __shared__ __align__(16) double sm[];
   const int cta = a.cta0 + blockIdx.x;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int W = a.W;                            // even
-  double* wg = sm + warp * 3 * W;
-  double* wy = wg + W;
-  double* wx = wy + W;
-  double* blob = sm + kWarps * 3 * W;
-  // Index lists of this CTA: per row slot {contribution begin, update begin,
-  // update end} into the position lists that follow, then ancestor rows.
-  int* il = reinterpret_cast<int*>(blob + a.max_blob);
+  const int tid = threadIdx.x;
+  double* blob = sm;                                   // max_blob (smem mode)
+  double* vg = blob + a.max_blob;                      // max_slots: g (fwd) / y (bwd)
+  double* vy = vg + a.max_slots;                       // max_slots: y (fwd) / h (bwd)
+  double* vm = vy + a.max_slots;                       // max_m: x of the ancestor rows (bwd)
+  double* pc = vm + a.max_m;                           // max_pairs: pair products (first launch)
+  int* il = reinterpret_cast<int*>(pc + a.max_pairs);
   const int64_t boff = a.blob_off[cta];
   if (kSmem) async_copy_16(blob, a.blob + boff, a.blob_len[cta] / 2);
   async_copy_16(il, a.ilist + a.ilist_off[cta], a.ilist_len[cta] / 4);
@@ -368,45 +379,107 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
   async_copy_wait();
-  const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
-  for (int q = a.cta_node_ptr[cta] + warp; q < a.cta_node_ptr[cta + 1]; q += kWarps) {
-    const int t = a.cta_nodes[q];
-    const int beg = a.t_beg[t], b = a.t_end[t] - beg, m = a.t_nrows[t];
-    const int ldi = b | 1, ldr = m | 1;
-    const double* Li = B + a.node_boff[t];           // L_tt^{-1}: b x b, column-major, ld ldi
-    const double* L21 = Li + (size_t)ldi * b;        // L_{rows,t}: m x b, column-major, ld ldr
-    if (kForward) {
-      const int* rh = il + 3 * a.node_slot[t];
-      for (int i = lane; i < b; i += 32) {
-        const int cb = rh[3 * i], fb = rh[3 * i + 1], fe = rh[3 * i + 2];
-        double v = ft * a.fxc[beg + i];
-#pragma unroll 4
-        for (int k = cb; k < fb; ++k) v -= a.Y[il[k]];
-#pragma unroll 4
-        for (int k = fb; k < fe; ++k) v -= __ldcg(a.upd + il[k]);
-        wg[i] = v;
+  const WalkList L(il);
+  const int nslot = il[1], nm = il[2];
+  if (kForward) {
+    if (a.first) {
+      const int npair = il[4], nrhs = il[3];
+      const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
+      for (int k = tid; k < npair; k += kThreads) pc[k] = pair_product(a, L.pair + 4 * k);
+      __syncthreads();
+      for (int k = tid; k < nrhs; k += kThreads) {
+        const int* rr = L.rhs + 4 * k;
+        double v = ft * a.fxc[rr[0]];
+        for (int q = rr[1]; q < rr[2]; ++q) v -= pc[q];
+        if (rr[3] >= 0) vg[rr[3]] = v;
+        else a.rhs0[rr[0]] = v;
       }
-      __syncwarp();
-      warp_gemv(Li, 1, ldi, b, b, wg, 1, wy, lane);        // y = L_tt^{-1} g
-      __syncwarp();
-      for (int i = lane; i < b; i += 32) a.sol[beg + i] = wy[i];
-      if (m > 0) warp_gemv(L21, 1, ldr, m, b, wy, 0, a.upd + a.t_off_upd[t], lane);  // upd = L21 y
-      __syncwarp();
+      __syncthreads();
+      for (int sl = tid; sl < nslot; sl += kThreads) {
+        const int* st = L.slot + 4 * sl;
+        double v = vg[sl];
+        for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(a.upd + il[k]);
+        vg[sl] = v;
+      }
     } else {
-      const int* rows = il + a.node_roff[t];
-      for (int k = lane; k < m; k += 32) wx[k] = -__ldcg(a.sol + rows[k]);
-      __syncwarp();
-      warp_gemv(L21, ldr, 1, b, m, wx, 0, wg, lane);      // -L_{rows,t}^T x_rows
-      __syncwarp();
-      for (int j = lane; j < b; j += 32) wg[j] += __ldcg(a.sol + beg + j);
-      __syncwarp();
-      warp_gemv(Li, ldi, 1, b, b, wg, -1, wy, lane);      // x = L_tt^{-T} h
-      __syncwarp();
-      for (int i = lane; i < b; i += 32) {
-        a.sol[beg + i] = wy[i];
-        correct_row(a, beg + i, wy[i]);
+      for (int sl = tid; sl < nslot; sl += kThreads) {
+        const int* st = L.slot + 4 * sl;
+        const int* nd = L.node + 8 * st[0];
+        double v = __ldcg(a.rhs0 + nd[1] + (sl - nd[4]));
+#pragma unroll 4
+        for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(a.upd + il[k]);
+        vg[sl] = v;
       }
-      __syncwarp();
+    }
+    __syncthreads();
+    // y = L_tt^{-1} g, every row of every supernode of this CTA.
+    for (int sl = tid; sl < nslot; sl += kThreads) {
+      const int* nd = L.node + 8 * L.slot[4 * sl];
+      const int b = nd[2], s0 = nd[4], i = sl - s0, ldi = b | 1;
+      const double* Li = B + nd[6];
+      double y0 = 0.0, y1 = 0.0;
+      int j = 0;
+      for (; j + 2 <= i + 1; j += 2) {
+        y0 = fma(Li[i + ldi * j], vg[s0 + j], y0);
+        y1 = fma(Li[i + ldi * (j + 1)], vg[s0 + j + 1], y1);
+      }
+      if (j <= i) y0 = fma(Li[i + ldi * j], vg[s0 + j], y0);
+      const double y = y0 + y1;
+      vy[sl] = y;
+      a.sol[nd[1] + i] = y;
+    }
+    __syncthreads();
+    // upd_t = L_{rows,t} y_t.
+    for (int k = tid; k < nm; k += kThreads) {
+      const int* nd = L.node + 8 * L.anc[2 * k];
+      const int b = nd[2], m = nd[3], s0 = nd[4], kk = k - nd[5], ldi = b | 1, ldr = m | 1;
+      const double* L21 = B + nd[6] + (size_t)ldi * b;
+      double u0 = 0.0, u1 = 0.0;
+      int j = 0;
+      for (; j + 2 <= b; j += 2) {
+        u0 = fma(L21[kk + ldr * j], vy[s0 + j], u0);
+        u1 = fma(L21[kk + ldr * (j + 1)], vy[s0 + j + 1], u1);
+      }
+      if (j < b) u0 = fma(L21[kk + ldr * j], vy[s0 + j], u0);
+      a.upd[nd[7] + kk] = u0 + u1;
+    }
+  } else {
+    for (int k = tid; k < nm; k += kThreads) vm[k] = __ldcg(a.sol + L.anc[2 * k + 1]);
+    for (int sl = tid; sl < nslot; sl += kThreads) {
+      const int* nd = L.node + 8 * L.slot[4 * sl];
+      vg[sl] = __ldcg(a.sol + nd[1] + (sl - nd[4]));
+    }
+    __syncthreads();
+    // h = y_t - L_{rows,t}^T x_rows.
+    for (int sl = tid; sl < nslot; sl += kThreads) {
+      const int* nd = L.node + 8 * L.slot[4 * sl];
+      const int b = nd[2], m = nd[3], i = sl - nd[4], mo = nd[5], ldi = b | 1, ldr = m | 1;
+      const double* L21 = B + nd[6] + (size_t)ldi * b + (size_t)ldr * i;
+      double h0 = 0.0, h1 = 0.0;
+      int k = 0;
+      for (; k + 2 <= m; k += 2) {
+        h0 = fma(L21[k], vm[mo + k], h0);
+        h1 = fma(L21[k + 1], vm[mo + k + 1], h1);
+      }
+      if (k < m) h0 = fma(L21[k], vm[mo + k], h0);
+      vy[sl] = vg[sl] - (h0 + h1);
+    }
+    __syncthreads();
+    // x_t = L_tt^{-T} h, then the correction of the row.
+    for (int sl = tid; sl < nslot; sl += kThreads) {
+      const int* nd = L.node + 8 * L.slot[4 * sl];
+      const int b = nd[2], s0 = nd[4], i = sl - s0, ldi = b | 1;
+      const double* Lc = B + nd[6] + (size_t)ldi * i;
+      double x0 = 0.0, x1 = 0.0;
+      int j = i;
+      for (; j + 2 <= b; j += 2) {
+        x0 = fma(Lc[j], vy[s0 + j], x0);
+        x1 = fma(Lc[j + 1], vy[s0 + j + 1], x1);
+      }
+      if (j < b) x0 = fma(Lc[j], vy[s0 + j], x0);
+      const double x = x0 + x1;
+      a.sol[nd[1] + i] = x;
+      correct_row(a, nd[1] + i, x);
     }
   }
 }
@@ -419,19 +492,16 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   const int zn = a.zsize[comp], zb = a.zbase[comp];
   double* zs = tsm;                               // max_zn (even): right-hand side of the block
   double* Ac = zs + a.max_zn;                     // max_rows_zn: this CTA's rows of A_Z
-  int* il = reinterpret_cast<int*>(Ac + a.max_arows);  // per row {contribution begin, update begin, end}
+  int* il = reinterpret_cast<int*>(Ac + a.max_arows);  // per row {update begin, update end}
   async_copy_16(Ac, a.zA + a.zA_off[comp] + (size_t)r0 * zn, ((int64_t)(r1 - r0) * zn + 1) / 2);
   async_copy_16(il, a.ilist + a.ilist_off[cta], a.ilist_len[cta] / 4);
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
   async_copy_wait();
-  const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
   // The whole right-hand side of this component's top block (redundant per CTA).
   for (int i = threadIdx.x; i < zn; i += kThreads) {
-    const int cb = il[3 * i], fb = il[3 * i + 1], fe = il[3 * i + 2];
-    double v = ft * a.fxc[a.zrow[zb + i]];
-#pragma unroll 4
-    for (int k = cb; k < fb; ++k) v -= a.Y[il[k]];
+    const int fb = il[2 * i], fe = il[2 * i + 1];
+    double v = __ldcg(a.rhs0 + a.zrow[zb + i]);
 #pragma unroll 4
     for (int k = fb; k < fe; ++k) v -= __ldcg(a.upd + il[k]);
     zs[i] = v;
@@ -532,29 +602,25 @@ struct imex_ctx {
   // implicit partition
   int* c_node = nullptr;
   double *v_c = nullptr, *a_c = nullptr, *fxc = nullptr;
-  int *if_cell = nullptr, *if_kidx = nullptr;
-  double *if_c2 = nullptr, *cutK = nullptr, *uncutK = nullptr, *Y = nullptr;
-  int *contrib_ptr = nullptr, *contrib_pos = nullptr, *fwd_ptr = nullptr, *fwd_pos = nullptr;
-  // solve: tree metadata, per-CTA factor blobs (S and M^cc), dense tops, scratch
-  int *t_beg = nullptr, *t_end = nullptr, *t_nrows = nullptr, *rows_idx = nullptr;
-  int64_t *t_off_upd = nullptr, *t_off_rows = nullptr;
+  // right-hand sides: rows of the interface cell matrices, per-cell scales
+  double *Krows = nullptr, *if_sc = nullptr, *rhs0 = nullptr;
+  // solve: per-CTA factor blobs (S and M^cc) and index lists, dense tops, scratch
   double *blob_S = nullptr, *blob_M = nullptr;
-  int64_t *blob_off = nullptr, *blob_len = nullptr, *node_boff = nullptr;
-  int *cta_node_ptr = nullptr, *cta_nodes = nullptr;
-  int *ilist = nullptr, *node_slot = nullptr, *node_roff = nullptr;
+  int64_t *blob_off = nullptr, *blob_len = nullptr;
+  int* ilist = nullptr;
   int64_t *ilist_off = nullptr, *ilist_len = nullptr;
   int64_t walk_max_blob = 0;
+  int walk_max_slots = 2, walk_max_m = 2, walk_max_pairs = 2;
   int* tlist = nullptr;
   int64_t *tlist_off = nullptr, *tlist_len = nullptr;
   int top_max_zn = 2;
   int64_t top_max_arows = 0;
-  std::vector<int> lev_cta0, lev_ncta;   // per walked level: CTA range
+  std::vector<int> lev_cta0, lev_ncta, lev_has_nodes;   // per walked level: CTA range
   int walk_smem_mode = 0;
   size_t smem_walk = 0, smem_top = 0;
-  int walk_W = 2;
   int ntop = 0;
   int *top_comp = nullptr, *top_r0 = nullptr, *top_r1 = nullptr;
-  int *zsize = nullptr, *zbase = nullptr, *zrow = nullptr, *zfwd_ptr = nullptr, *zfwd_pos = nullptr;
+  int *zsize = nullptr, *zbase = nullptr, *zrow = nullptr;
   int64_t* zA_off = nullptr;
   double *zA_S = nullptr, *zA_M = nullptr;
   int64_t nzrow = 0;
@@ -569,6 +635,7 @@ struct imex_ctx {
   cudaStream_t stream = nullptr;
   Ops2D ops{};
   int TC = 4, ntx = 1, nty = 1;
+  int explicit_slots = 152;   // resident CTAs of the explicit kernel on the device
   size_t smem_explicit = 0;
 };
 
@@ -624,6 +691,26 @@ cudaError_t set_explicit_smem(size_t bytes) {
                               (int)bytes);
 }
 
+template <int P>
+cudaError_t explicit_occupancy(size_t bytes, int* per_sm) {
+  constexpr int TCs[10] = {0, 0, 16, 16, 10, 8, 6, 5, 4, 4};
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_explicit2d<P, TCs[P]>, kThreads, bytes);
+}
+
+cudaError_t explicit_occupancy_dispatch(int P, size_t bytes, int* per_sm) {
+  switch (P) {
+    case 2: return explicit_occupancy<2>(bytes, per_sm);
+    case 3: return explicit_occupancy<3>(bytes, per_sm);
+    case 4: return explicit_occupancy<4>(bytes, per_sm);
+    case 5: return explicit_occupancy<5>(bytes, per_sm);
+    case 6: return explicit_occupancy<6>(bytes, per_sm);
+    case 7: return explicit_occupancy<7>(bytes, per_sm);
+    case 8: return explicit_occupancy<8>(bytes, per_sm);
+    case 9: return explicit_occupancy<9>(bytes, per_sm);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t set_explicit_smem_dispatch(int P, size_t bytes) {
   switch (P) {
     case 2: return set_explicit_smem<2>(bytes);
@@ -667,31 +754,17 @@ ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double
   return ea;
 }
 
+// CTAs for the Newmark prediction, appended to the tiles of the explicit
+// launch: the resident slots the tiles leave free in their last wave (so the
+// launch stays one wave when the tiles fit), at least one, at most one per
+// 256 rows.
 int pred_blocks(imex_ctx* c, bool predict) {
   if (!predict || c->hs.n_c == 0) return 0;
-  return (int)std::min<int64_t>(152, (c->hs.n_c + kThreads - 1) / kThreads);
-}
-
-IfaceArgs iface_args(imex_ctx* c, const double* src) {
-  const HostSetup& hs = c->hs;
-  IfaceArgs ia{};
-  ia.SRC = src;
-  ia.cell = c->if_cell;
-  ia.kidx = c->if_kidx;
-  ia.c2 = c->if_c2;
-  ia.cutK = c->cutK;
-  ia.uncutK = c->uncutK;
-  ia.Y = c->Y;
-  ia.n_iface = (int)hs.if_cell.size();
-  ia.dim = hs.dim;
-  ia.p = hs.p;
-  ia.P = hs.P;
-  ia.Pd = hs.Pd;
-  ia.ncx = hs.pb.ncells[0];
-  ia.ncy = hs.pb.ncells[1];
-  ia.nx = hs.nn[0];
-  ia.ny = hs.nn[1];
-  return ia;
+  const int64_t tiles = (int64_t)c->ntx * c->nty;
+  const int64_t slots = std::max<int64_t>(1, c->explicit_slots);
+  int64_t spare = (slots - tiles % slots) % slots;
+  if (spare == 0) spare = 8;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(spare, (c->hs.n_c + kThreads - 1) / kThreads));
 }
 
 constexpr int kMaxWidth = 256;                 // largest supernode / row set of the walk
@@ -699,43 +772,39 @@ constexpr size_t kWalkSmemBudget = 200 * 1024;  // shared memory per walk CTA (s
 constexpr size_t kTopSmemBudget = 200 * 1024;   // shared memory per dense-top CTA
 constexpr size_t kMaxDynSmem = 227 * 1024;      // largest dynamic shared memory of a CTA
 
-// The launches of the implicit solve (after k_iface): forward walk over the
-// lower levels, dense tops, backward walk with the correction.  use_S selects
-// the factor of S (step) or of M^cc (initial acceleration, mode 1).  upd/sol
-// are the solve's scratch vectors.
+// The launches of the implicit solve: forward walk over the lower levels
+// (the first also forms every right-hand side from src), dense tops,
+// backward walk with the correction.  use_S selects the factor of S (step)
+// or of M^cc (initial acceleration, mode 1).  upd/sol/rhs0 are the solve's
+// scratch vectors.
 cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double* ft_dev, int mode, double* Ubuf,
-                               double* upd, double* sol, cudaStream_t s) {
+                               const double* src, double* upd, double* sol, double* rhs0, cudaStream_t s) {
   const HostSetup& hs = c->hs;
   WalkArgs w{};
   w.blob = use_S ? c->blob_S : c->blob_M;
   w.blob_off = c->blob_off;
   w.blob_len = c->blob_len;
-  w.cta_node_ptr = c->cta_node_ptr;
-  w.cta_nodes = c->cta_nodes;
-  w.node_boff = c->node_boff;
   w.max_blob = c->walk_max_blob;
   w.ilist = c->ilist;
   w.ilist_off = c->ilist_off;
   w.ilist_len = c->ilist_len;
-  w.node_slot = c->node_slot;
-  w.node_roff = c->node_roff;
-  w.t_beg = c->t_beg;
-  w.t_end = c->t_end;
-  w.t_nrows = c->t_nrows;
-  w.t_off_upd = c->t_off_upd;
-  w.t_off_rows = c->t_off_rows;
-  w.rows_idx = c->rows_idx;
-  w.fwd_ptr = c->fwd_ptr;
-  w.fwd_pos = c->fwd_pos;
-  w.contrib_ptr = c->contrib_ptr;
-  w.contrib_pos = c->contrib_pos;
-  w.Y = c->Y;
+  w.max_slots = c->walk_max_slots;
+  w.max_m = c->walk_max_m;
+  w.max_pairs = c->walk_max_pairs;
+  w.SRC = src;
+  w.Krows = c->Krows;
+  w.if_sc = c->if_sc;
+  w.P = hs.P;
+  w.Pd = hs.Pd;
+  w.dim = hs.dim;
+  w.nx = hs.nn[0];
+  w.ny = hs.nn[1];
   w.fxc = c->fxc;
   w.ft = ft;
   w.ft_dev = ft_dev;
+  w.rhs0 = rhs0;
   w.upd = upd;
   w.sol = sol;
-  w.W = c->walk_W;
   w.mode = mode;
   w.c_node = c->c_node;
   w.U = Ubuf;
@@ -756,14 +825,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   z.ilist = c->tlist;
   z.ilist_off = c->tlist_off;
   z.ilist_len = c->tlist_len;
-  z.zfwd_ptr = c->zfwd_ptr;
-  z.zfwd_pos = c->zfwd_pos;
-  z.contrib_ptr = c->contrib_ptr;
-  z.contrib_pos = c->contrib_pos;
-  z.Y = c->Y;
-  z.fxc = c->fxc;
-  z.ft = ft;
-  z.ft_dev = ft_dev;
+  z.rhs0 = rhs0;
   z.upd = upd;
   z.sol = sol;
   z.mode = mode;
@@ -784,6 +846,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   const int nlev = (int)c->lev_cta0.size();
   auto walk = [&](int l, bool fwd) {
     w.cta0 = c->lev_cta0[l];
+    w.first = (fwd && l == 0) ? 1 : 0;
     cfg.gridDim = dim3(c->lev_ncta[l]);
     cfg.dynamicSmemBytes = c->smem_walk;
     if (c->walk_smem_mode)
@@ -797,8 +860,19 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
     cfg.dynamicSmemBytes = c->smem_top;
     e = cudaLaunchKernelEx(&cfg, k_top, z);
   }
-  for (int l = nlev - 1; l >= 0 && e == cudaSuccess; --l) e = walk(l, false);
+  for (int l = nlev - 1; l >= 0 && e == cudaSuccess; --l)
+    if (c->lev_has_nodes[l]) e = walk(l, false);
   return e;
+}
+
+// Kernel launches of one step.
+int64_t launches_per_step(const imex_ctx* c) {
+  int64_t n = 1;   // explicit apply
+  if (c->hs.n_c > 0) {
+    n += (int64_t)c->lev_cta0.size() + (c->ntop > 0 ? 1 : 0);
+    for (int h : c->lev_has_nodes) n += h;
+  }
+  return n;
 }
 
 double ft_at(const HostSetup& hs, int64_t n) {
@@ -819,11 +893,7 @@ int compute_initial(imex_ctx* c, cudaStream_t s) {
   if (hs.n_c > 0) {
     const int nc = (int)hs.n_c;
     k_gather_c<<<(nc + 255) / 256, 256, 0, s>>>(c->v_c, c->tmp, c->c_node, nc);
-    const int nif = (int)hs.if_cell.size();
-    IfaceArgs ia = iface_args(c, U0);
-    k_iface<<<(nif + kWarps - 1) / kWarps, kThreads, 0, s>>>(ia);
-    if (int rc = check_launch("iface (initial)")) return rc;
-    if (cudaError_t e = launch_solve_chain(c, false, ft0, nullptr, 1, U0, c->upd, c->sol, s))
+    if (cudaError_t e = launch_solve_chain(c, false, ft0, nullptr, 1, U0, U0, c->upd, c->sol, c->rhs0, s))
       return fail(IMEX_ERR_CUDA, std::string("solve (initial): ") + cudaGetErrorString(e));
     if (int rc = check_launch("solve (initial)")) return rc;
   }
@@ -845,10 +915,14 @@ struct SolvePlan {
   std::vector<int64_t> blob_off, blob_len, node_boff;
   std::vector<double> blobS, blobM;
   int64_t max_blob = 0;
-  // Per-CTA index lists of the walk: row headers, position lists, ancestor rows.
-  std::vector<int> ilist, node_slot, node_roff;
+  // Per-CTA index lists of the walk (layout: WalkList).
+  std::vector<int> ilist;
   std::vector<int64_t> ilist_off, ilist_len;
   int64_t max_ilist = 0;
+  int max_slots = 2, max_m = 2, max_pairs = 2;
+  std::vector<int> lev_has_nodes;
+  // Rows of the interface cell matrices (row-major) and per-cell scale.
+  std::vector<double> Krows, if_sc;
   std::vector<int> top_comp, top_r0, top_r1;
   // Per-component index lists of the dense tops (one entry per top CTA).
   std::vector<int> tlist;
@@ -865,6 +939,7 @@ struct SolvePlan {
 #endif
 constexpr int kZmax = IMEX_DENSE_TOP_MAX;   // largest dense top block per component
 constexpr int kTargetCTAs = 152;            // one CTA per SM
+constexpr int kMaxNodesPerCTA = 32;
 
 // A_Z = (L_ZZ L_ZZ^T)^{-1} (row-major zn x zn) from the factor blocks of the
 // component's top nodes; Z rows are the nodes' c-indices in ascending order.
@@ -1029,40 +1104,75 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
     if (!(std::sqrt(dn / std::max(rn, 1e-300)) < 1e-9))
       return fail(IMEX_ERR_NOT_SPD, "dense top-level solve disagrees with the tree solve");
   }
-  // Walked levels: pack each level's nodes into CTAs.
+  // Interface cells: rows of their matrices and scales, first node of each.
+  const int Pd = hs.Pd, n_cut = (int)hs.n_cut, nif = (int)hs.if_cell.size();
+  P.Krows.assign(((size_t)n_cut + 1) * Pd * Pd, 0.0);
+  for (int k = 0; k < n_cut; ++k)
+    for (int l = 0; l < Pd; ++l)
+      for (int m = 0; m < Pd; ++m)
+        P.Krows[((size_t)k * Pd + l) * Pd + m] = hs.cutK[(size_t)k * Pd * Pd + l + (size_t)Pd * m];
+  for (int l = 0; l < Pd; ++l)
+    for (int m = 0; m < Pd; ++m) P.Krows[((size_t)n_cut * Pd + l) * Pd + m] = hs.uncutK[l + (size_t)Pd * m];
+  P.if_sc.assign(std::max(nif, 1), 1.0);
+  std::vector<int> if_base(std::max(nif, 1), 0);
+  {
+    const int ncx = hs.pb.ncells[0], ncy = hs.pb.ncells[1];
+    for (int e = 0; e < nif; ++e) {
+      const int cid = hs.if_cell[e];
+      const int cx = cid % ncx, cy = (cid / ncx) % ncy, cz = cid / (ncx * ncy);
+      const int64_t base = (int64_t)cx * hs.p + (int64_t)hs.nn[0] * cy * hs.p +
+                           (int64_t)hs.nn[0] * hs.nn[1] * cz * hs.p;
+      if (base > INT32_MAX) return fail(IMEX_ERR_ARG, "grid too large for 32-bit node indices");
+      if_base[e] = (int)base;
+      if (hs.if_kidx[e] < 0) P.if_sc[e] = hs.if_c2[e];
+    }
+  }
+  if (hs.upd_size > INT32_MAX) return fail(IMEX_ERR_ARG, "implicit partition too large for 32-bit update offsets");
+  auto npairs_of = [&](int r) { return hs.contrib_ptr[r + 1] - hs.contrib_ptr[r]; };
+
+  // Walked levels: pack each level's nodes into CTAs by longest processing
+  // time.  Level 0 always has a launch: it forms every right-hand side.
   int nlev = 0;
   for (size_t t = 0; t < hs.tree.size(); ++t)
     if (!is_top((int)t)) nlev = std::max(nlev, hs.tree[t].level + 1);
-  const size_t vec_doubles = (size_t)3 * kWarps * c->walk_W;
-  const int64_t blob_cap = (int64_t)((kWalkSmemBudget / sizeof(double)) - vec_doubles);
+  const int nlaunch = std::max(nlev, 1);
+  std::vector<char> own0(std::max<int64_t>(hs.n_c, 1), 0);
+  for (size_t t = 0; t < hs.tree.size(); ++t)
+    if (!is_top((int)t) && hs.tree[t].level == 0)
+      for (int r = hs.tree[t].beg; r < hs.tree[t].end; ++r) own0[r] = 1;
+  std::vector<int> extra_rows;
+  for (int64_t r = 0; r < hs.n_c; ++r)
+    if (!own0[r]) extra_rows.push_back((int)r);
+  const size_t vec_doubles = 0;
+  const int64_t blob_cap = (int64_t)(kWalkSmemBudget / sizeof(double));
   P.node_boff.assign(nt, 0);
-  P.node_slot.assign(nt, 0);
-  P.node_roff.assign(nt, 0);
   P.cta_node_ptr.assign(1, 0);
-  for (int l = 0; l < nlev; ++l) {
+  for (int l = 0; l < nlaunch; ++l) {
     std::vector<int> nodes;
     for (size_t t = 0; t < hs.tree.size(); ++t)
       if (!is_top((int)t) && hs.tree[t].level == l) nodes.push_back((int)t);
     std::sort(nodes.begin(), nodes.end(), [&](int x, int y) { return node_work(x) > node_work(y); });
-    auto ints_of = [&](int t) {
-      const TreeNode& T = hs.tree[t];
-      int64_t n = 3 * (int64_t)(T.end - T.beg) + (int64_t)T.rows.size();
-      for (int r = T.beg; r < T.end; ++r)
-        n += (hs.contrib_ptr[r + 1] - hs.contrib_ptr[r]) + (hs.fwd_ptr[r + 1] - hs.fwd_ptr[r]);
-      return n;
-    };
-    auto bytes_of = [&](int t) {   // in doubles: factor blocks and index lists
+    auto bytes_of = [&](int t) {   // shared memory of a node, in doubles
       const TreeNode& T = hs.tree[t];
       const int64_t b = T.end - T.beg, m = (int64_t)T.rows.size();
-      return (b | 1) * b + (m | 1) * b + (ints_of(t) + 1) / 2 + 2;
+      int64_t ints = 4 * b + 2 * m + 8;
+      int64_t pairs = 0;
+      for (int r = T.beg; r < T.end; ++r) {
+        ints += hs.fwd_ptr[r + 1] - hs.fwd_ptr[r];
+        if (l == 0) pairs += npairs_of(r);
+      }
+      ints += l == 0 ? 4 * b + 4 * pairs : 0;
+      return (b | 1) * b + (m | 1) * b + 2 * b + m + pairs + (ints + 1) / 2 + 2;
     };
-    const int target = std::max(1, std::min<int>((int)nodes.size(), kTargetCTAs));
+    int target = std::max(1, std::min<int>((int)nodes.size(), kTargetCTAs));
+    if (l == 0)
+      target = std::max(target, (int)std::min<int64_t>(kTargetCTAs, ((int64_t)extra_rows.size() + 31) / 32));
     std::vector<std::vector<int>> per(target);
     std::vector<int64_t> work(target, 0), used(target, 0);
     for (int t : nodes) {
       int best = -1;
       for (int r = 0; r < (int)per.size(); ++r) {
-        if ((int)per[r].size() >= kWarps) continue;
+        if ((int)per[r].size() >= kMaxNodesPerCTA) continue;
         if (!per[r].empty() && used[r] + bytes_of(t) > blob_cap) continue;
         if (best < 0 || work[r] < work[best]) best = r;
       }
@@ -1076,19 +1186,42 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
       work[best] += node_work(t);
       used[best] += bytes_of(t);
     }
+    // Level 0: the rows it does not solve get their right-hand side from the
+    // least loaded CTA (work of a pair: one P^d dot product).
+    std::vector<std::vector<int>> xrows(per.size());
+    if (l == 0) {
+      std::vector<int> order = extra_rows;
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return npairs_of(x) > npairs_of(y); });
+      for (int r : order) {
+        int best = 0;
+        for (int q = 1; q < (int)per.size(); ++q)
+          if (work[q] < work[best]) best = q;
+        xrows[best].push_back(r);
+        work[best] += (int64_t)Pd * npairs_of(r) + 1;
+      }
+      for (auto& xr : xrows) std::sort(xr.begin(), xr.end());
+    }
     P.lev_cta0.push_back((int)P.blob_off.size());
+    P.lev_has_nodes.push_back(nodes.empty() ? 0 : 1);
     int ncta = 0;
-    for (auto& list : per) {
-      if (list.empty()) continue;
+    for (size_t q0 = 0; q0 < per.size(); ++q0) {
+      const std::vector<int>& list = per[q0];
+      if (list.empty() && xrows[q0].empty()) continue;
       ++ncta;
       if (P.blobS.size() % 2) { P.blobS.push_back(0.0); P.blobM.push_back(0.0); }
       P.blob_off.push_back((int64_t)P.blobS.size());
       int64_t local = 0;
-      for (int t : list) {
-        const TreeNode& T = hs.tree[t];
+      int nslot = 0, nm = 0, npair = 0;
+      std::vector<int> slot0(list.size()), moff(list.size());
+      for (size_t q = 0; q < list.size(); ++q) {
+        const TreeNode& T = hs.tree[list[q]];
         const int b = T.end - T.beg, m = (int)T.rows.size();
         const int ldi = b | 1, ldr = m | 1;
-        P.node_boff[t] = local;
+        P.node_boff[list[q]] = local;
+        slot0[q] = nslot;
+        moff[q] = nm;
+        nslot += b;
+        nm += m;
         for (const Factor* F : {&hs.S, &hs.Mcc}) {
           std::vector<double>& out = (F == &hs.S) ? P.blobS : P.blobM;
           const double* Li = F->vals.data() + T.off_diag;
@@ -1099,44 +1232,89 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
             for (int i = 0; i < ldr; ++i) out.push_back(i < m ? L21[i + (size_t)m * j] : 0.0);
         }
         local += (int64_t)ldi * b + (int64_t)ldr * b;
-        P.cta_nodes.push_back(t);
+        P.cta_nodes.push_back(list[q]);
       }
       if (local % 2) { P.blobS.push_back(0.0); P.blobM.push_back(0.0); ++local; }
+      if (local > INT32_MAX) return fail(IMEX_ERR_ARG, "solve CTA blob too large");
       P.blob_len.push_back(local);
-      // Index list: {contribution begin, update begin, end} per row slot (in
-      // node order), then the position lists, then each node's ancestor rows.
-      const int64_t i0 = (int64_t)P.ilist.size();
-      int nslot = 0;
-      for (int t : list) {
-        P.node_slot[t] = nslot;
-        nslot += hs.tree[t].end - hs.tree[t].beg;
-      }
-      std::vector<int> L(3 * (size_t)nslot, 0);
-      for (int t : list) {
-        const TreeNode& T = hs.tree[t];
-        for (int r = T.beg; r < T.end; ++r) {
-          const size_t h = 3 * (size_t)(P.node_slot[t] + r - T.beg);
-          L[h] = (int)L.size();
-          for (int k = hs.contrib_ptr[r]; k < hs.contrib_ptr[r + 1]; ++k) L.push_back(hs.contrib_pos[k]);
-          L[h + 1] = (int)L.size();
-          for (int k = hs.fwd_ptr[r]; k < hs.fwd_ptr[r + 1]; ++k) L.push_back(hs.fwd_pos[k]);
-          L[h + 2] = (int)L.size();
-        }
-      }
-      for (int t : list) {
-        P.node_roff[t] = (int)L.size();
-        L.insert(L.end(), hs.tree[t].rows.begin(), hs.tree[t].rows.end());
-      }
-      while (L.size() % 4) L.push_back(0);
-      P.ilist.insert(P.ilist.end(), L.begin(), L.end());
-      P.ilist_off.push_back(i0);
-      P.ilist_len.push_back((int64_t)L.size());
-      P.max_ilist = std::max<int64_t>(P.max_ilist, (int64_t)L.size());
       P.max_blob = std::max(P.max_blob, local);
       P.cta_node_ptr.push_back((int)P.cta_nodes.size());
+      // Right-hand-side rows (level 0): own rows in slot order, then the extra rows.
+      std::vector<int> rrows, rslot;
+      if (l == 0) {
+        for (size_t q = 0; q < list.size(); ++q)
+          for (int r = hs.tree[list[q]].beg; r < hs.tree[list[q]].end; ++r) {
+            rrows.push_back(r);
+            rslot.push_back(slot0[q] + r - hs.tree[list[q]].beg);
+          }
+        for (int r : xrows[q0]) {
+          rrows.push_back(r);
+          rslot.push_back(-1);
+        }
+        for (int r : rrows) npair += npairs_of(r);
+      }
+      const int nrhs = (int)rrows.size();
+      const int o_node = 8, o_slot = o_node + 8 * (int)list.size(), o_anc = o_slot + 4 * nslot;
+      const int o_rhs = o_anc + ((2 * nm + 3) & ~3), o_pair = o_rhs + 4 * nrhs, o_pos = o_pair + 4 * npair;
+      std::vector<int> Lst(o_pos, 0);
+      Lst[0] = (int)list.size();
+      Lst[1] = nslot;
+      Lst[2] = nm;
+      Lst[3] = nrhs;
+      Lst[4] = npair;
+      for (size_t q = 0; q < list.size(); ++q) {
+        const TreeNode& T = hs.tree[list[q]];
+        const int b = T.end - T.beg, m = (int)T.rows.size();
+        int* nd = &Lst[o_node + 8 * q];
+        nd[0] = list[q];
+        nd[1] = T.beg;
+        nd[2] = b;
+        nd[3] = m;
+        nd[4] = slot0[q];
+        nd[5] = moff[q];
+        nd[6] = (int)P.node_boff[list[q]];
+        nd[7] = (int)T.off_upd;
+        for (int i = 0; i < b; ++i) {
+          const int r = T.beg + i;
+          int* st = &Lst[o_slot + 4 * (slot0[q] + i)];
+          st[0] = (int)q;
+          st[1] = (int)Lst.size();
+          for (int k = hs.fwd_ptr[r]; k < hs.fwd_ptr[r + 1]; ++k) Lst.push_back(hs.fwd_pos[k]);
+          st[2] = (int)Lst.size();
+        }
+        for (int k = 0; k < m; ++k) {
+          Lst[o_anc + 2 * (moff[q] + k)] = (int)q;
+          Lst[o_anc + 2 * (moff[q] + k) + 1] = T.rows[k];
+        }
+      }
+      int pq = 0;
+      for (int k = 0; k < nrhs; ++k) {
+        const int r = rrows[k];
+        int* rr = &Lst[o_rhs + 4 * k];
+        rr[0] = r;
+        rr[1] = pq;
+        for (int q = hs.contrib_ptr[r]; q < hs.contrib_ptr[r + 1]; ++q, ++pq) {
+          const int e = hs.contrib_pos[q] / Pd, lnode = hs.contrib_pos[q] % Pd;
+          int* pr = &Lst[o_pair + 4 * pq];
+          pr[0] = if_base[e];
+          pr[1] = (hs.if_kidx[e] >= 0 ? hs.if_kidx[e] : n_cut) * Pd + lnode;
+          pr[2] = e;
+        }
+        rr[2] = pq;
+        rr[3] = rslot[k];
+      }
+      while (Lst.size() % 4) Lst.push_back(0);
+      P.ilist_off.push_back((int64_t)P.ilist.size());
+      P.ilist_len.push_back((int64_t)Lst.size());
+      P.ilist.insert(P.ilist.end(), Lst.begin(), Lst.end());
+      P.max_ilist = std::max<int64_t>(P.max_ilist, (int64_t)Lst.size());
+      P.max_slots = std::max(P.max_slots, nslot + (nslot & 1));
+      P.max_m = std::max(P.max_m, nm + (nm & 1));
+      P.max_pairs = std::max(P.max_pairs, npair + (npair & 1));
     }
     P.lev_ncta.push_back(ncta);
   }
+  (void)vec_doubles;
   // Dense tops: row chunks, about one CTA per SM over the whole launch.
   int64_t zsum = 0;
   for (int k = 0; k < hs.ncomp; ++k) zsum += zsize[k];
@@ -1144,14 +1322,11 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
   for (int k = 0; k < hs.ncomp; ++k) {
     const int zn = zsize[k], zb = zbase[k];
     std::vector<int>& L = tl[k];
-    L.assign(3 * (size_t)zn, 0);
+    L.assign(2 * (size_t)zn, 0);
     for (int i = 0; i < zn; ++i) {
-      const int r = zrow[zb + i];
-      L[3 * i] = (int)L.size();
-      for (int q = hs.contrib_ptr[r]; q < hs.contrib_ptr[r + 1]; ++q) L.push_back(hs.contrib_pos[q]);
-      L[3 * i + 1] = (int)L.size();
+      L[2 * i] = (int)L.size();
       for (int q = zfwd_ptr[zb + i]; q < zfwd_ptr[zb + i + 1]; ++q) L.push_back(zfwd_pos[q]);
-      L[3 * i + 2] = (int)L.size();
+      L[2 * i + 1] = (int)L.size();
     }
     while (L.size() % 4) L.push_back(0);
     P.max_tlist = std::max<int64_t>(P.max_tlist, (int64_t)L.size());
@@ -1409,30 +1584,23 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     const int64_t nn = hs.nnodes, nc = hs.n_c, nt = (int64_t)hs.tree.size();
     std::vector<double> fxc(nc);
     for (int64_t r = 0; r < nc; ++r) fxc[r] = hs.fx[hs.c_node[r]];
-    std::vector<int> tb(nt), te(nt), tn(nt);
-    std::vector<int64_t> orw(nt), ou(nt);
-    for (int64_t t = 0; t < nt; ++t) {
-      const TreeNode& T = hs.tree[t];
-      tb[t] = T.beg;
-      te[t] = T.end;
-      tn[t] = (int)T.rows.size();
-      orw[t] = T.off_rows;
-      ou[t] = T.off_upd;
-    }
-    c->walk_W = std::max(2, std::max(hs.max_block, hs.max_rows));
-    c->walk_W += c->walk_W & 1;
+    (void)nt;
     SolvePlan plan;
     if (int rc = plan_solve(c, plan)) {
       delete c;
       return rc;
     }
     {
-      const size_t vec = (size_t)3 * kWarps * c->walk_W * sizeof(double);
+      c->walk_max_slots = plan.max_slots;
+      c->walk_max_m = plan.max_m;
+      c->walk_max_pairs = plan.max_pairs;
+      const size_t vec = (size_t)(2 * plan.max_slots + plan.max_m + plan.max_pairs) * sizeof(double);
       const size_t lists = (size_t)plan.max_ilist * sizeof(int);
       const size_t staged = vec + (size_t)plan.max_blob * sizeof(double) + lists;
-      c->walk_smem_mode = staged <= kWalkSmemBudget ? 1 : 0;
+      c->walk_smem_mode = staged <= kMaxDynSmem ? 1 : 0;
       c->walk_max_blob = c->walk_smem_mode ? plan.max_blob : 0;
       c->smem_walk = c->walk_smem_mode ? staged : vec + lists;
+      c->lev_has_nodes = plan.lev_has_nodes;
       c->top_max_zn = std::max(2, plan.max_zn + (plan.max_zn & 1));
       c->top_max_arows = plan.max_arows;
       c->smem_top = (size_t)(c->top_max_zn + plan.max_arows) * sizeof(double) + (size_t)plan.max_tlist * sizeof(int);
@@ -1461,33 +1629,15 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->a_c, std::max<int64_t>(nc, 1));
     ar.add(&c->fxc, std::max<int64_t>(nc, 1));
     ar.add(&c->sol, std::max<int64_t>(nc, 1));
+    ar.add(&c->rhs0, std::max<int64_t>(nc, 1));
     ar.add(&c->upd, std::max<int64_t>(hs.upd_size, 1));
-    ar.add(&c->if_cell, std::max<int64_t>(nif, 1));
-    ar.add(&c->if_kidx, std::max<int64_t>(nif, 1));
-    ar.add(&c->if_c2, std::max<int64_t>(nif, 1));
-    ar.add(&c->cutK, std::max<size_t>(hs.cutK.size(), 1));
-    ar.add(&c->uncutK, hs.uncutK.size());
-    ar.add(&c->Y, std::max<int64_t>(nif * hs.Pd, 1));
-    ar.add(&c->contrib_ptr, hs.contrib_ptr.size());
-    ar.add(&c->contrib_pos, std::max<size_t>(hs.contrib_pos.size(), 1));
-    ar.add(&c->fwd_ptr, hs.fwd_ptr.size());
-    ar.add(&c->fwd_pos, std::max<size_t>(hs.fwd_pos.size(), 1));
-    ar.add(&c->t_beg, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_end, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_nrows, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_off_rows, std::max<int64_t>(nt, 1));
-    ar.add(&c->t_off_upd, std::max<int64_t>(nt, 1));
-    ar.add(&c->rows_idx, std::max<size_t>(hs.rows_idx.size(), 1));
+    ar.add(&c->Krows, std::max<size_t>(plan.Krows.size(), 1));
+    ar.add(&c->if_sc, std::max<size_t>(plan.if_sc.size(), 1));
     ar.add(&c->blob_S, std::max<size_t>(plan.blobS.size(), 2));
     ar.add(&c->blob_M, std::max<size_t>(plan.blobM.size(), 2));
     ar.add(&c->blob_off, nblobcta);
     ar.add(&c->blob_len, nblobcta);
-    ar.add(&c->node_boff, std::max<int64_t>(nt, 1));
-    ar.add(&c->cta_node_ptr, plan.cta_node_ptr.size());
-    ar.add(&c->cta_nodes, std::max<size_t>(plan.cta_nodes.size(), 1));
     ar.add(&c->ilist, std::max<size_t>(plan.ilist.size(), 4));
-    ar.add(&c->node_slot, std::max<int64_t>(nt, 1));
-    ar.add(&c->node_roff, std::max<int64_t>(nt, 1));
     ar.add(&c->ilist_off, nblobcta);
     ar.add(&c->ilist_len, nblobcta);
     ar.add(&c->tlist, std::max<size_t>(plan.tlist.size(), 4));
@@ -1499,8 +1649,6 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->zsize, std::max<size_t>(plan.zsize.size(), 1));
     ar.add(&c->zbase, std::max<size_t>(plan.zbase.size(), 1));
     ar.add(&c->zrow, std::max<size_t>(plan.zrow.size(), 1));
-    ar.add(&c->zfwd_ptr, std::max<size_t>(plan.zfwd_ptr.size(), 1));
-    ar.add(&c->zfwd_pos, std::max<size_t>(plan.zfwd_pos.size(), 1));
     ar.add(&c->zA_off, std::max<size_t>(plan.zA_off.size(), 1));
     ar.add(&c->zA_S, std::max<size_t>(plan.zA_S.size(), 1));
     ar.add(&c->zA_M, std::max<size_t>(plan.zA_M.size(), 1));
@@ -1532,31 +1680,13 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->cls, hs.node_class);
     e = e ? e : upload(c->c_node, hs.c_node);
     e = e ? e : upload(c->fxc, fxc);
-    e = e ? e : upload(c->if_cell, hs.if_cell);
-    e = e ? e : upload(c->if_kidx, hs.if_kidx);
-    e = e ? e : upload(c->if_c2, hs.if_c2);
-    e = e ? e : upload(c->cutK, hs.cutK);
-    e = e ? e : upload(c->uncutK, hs.uncutK);
-    e = e ? e : upload(c->contrib_ptr, hs.contrib_ptr);
-    e = e ? e : upload(c->contrib_pos, hs.contrib_pos);
-    e = e ? e : upload(c->fwd_ptr, hs.fwd_ptr);
-    e = e ? e : upload(c->fwd_pos, hs.fwd_pos);
-    e = e ? e : upload(c->t_beg, tb);
-    e = e ? e : upload(c->t_end, te);
-    e = e ? e : upload(c->t_nrows, tn);
-    e = e ? e : upload(c->t_off_rows, orw);
-    e = e ? e : upload(c->t_off_upd, ou);
-    e = e ? e : upload(c->rows_idx, hs.rows_idx);
+    e = e ? e : upload(c->Krows, plan.Krows);
+    e = e ? e : upload(c->if_sc, plan.if_sc);
     e = e ? e : upload(c->blob_S, plan.blobS);
     e = e ? e : upload(c->blob_M, plan.blobM);
     e = e ? e : upload(c->blob_off, plan.blob_off);
     e = e ? e : upload(c->blob_len, plan.blob_len);
-    e = e ? e : upload(c->node_boff, plan.node_boff);
-    e = e ? e : upload(c->cta_node_ptr, plan.cta_node_ptr);
-    e = e ? e : upload(c->cta_nodes, plan.cta_nodes);
     e = e ? e : upload(c->ilist, plan.ilist);
-    e = e ? e : upload(c->node_slot, plan.node_slot);
-    e = e ? e : upload(c->node_roff, plan.node_roff);
     e = e ? e : upload(c->ilist_off, plan.ilist_off);
     e = e ? e : upload(c->ilist_len, plan.ilist_len);
     e = e ? e : upload(c->tlist, plan.tlist);
@@ -1568,8 +1698,6 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->zsize, plan.zsize);
     e = e ? e : upload(c->zbase, plan.zbase);
     e = e ? e : upload(c->zrow, plan.zrow);
-    e = e ? e : upload(c->zfwd_ptr, plan.zfwd_ptr);
-    e = e ? e : upload(c->zfwd_pos, plan.zfwd_pos);
     e = e ? e : upload(c->zA_off, plan.zA_off);
     e = e ? e : upload(c->zA_S, plan.zA_S);
     e = e ? e : upload(c->zA_M, plan.zA_M);
@@ -1578,6 +1706,12 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
     e = e ? e : set_explicit_smem_dispatch(P, c->smem_explicit);
+    if (e == cudaSuccess) {
+      int nsm = 0, per_sm = 0;
+      e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+      e = e ? e : explicit_occupancy_dispatch(P, c->smem_explicit, &per_sm);
+      c->explicit_slots = std::max(1, nsm * per_sm);
+    }
     if (e != cudaSuccess) {
       std::string msg = std::string("upload failed: ") + cudaGetErrorString(e);
       imex_destroy(c);
@@ -1604,29 +1738,22 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
   }
 }
 
-// One IMEX step n -> n+1 on stream s; events (may be NULL) are recorded before
-// the explicit kernel and after each of the three kernels.
+// One IMEX step n -> n+1 on stream s; events (may be NULL) are recorded
+// before the explicit kernel, after it, and after the implicit chain.
 static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double* ft_dev = nullptr) {
   const HostSetup& hs = c->hs;
   const double dt = hs.dt;
   double* Ucur = c->U[c->cur];
   double* Unext = c->U[1 - c->cur];
   const int64_t step = c->step;
-  const int nif = (int)hs.if_cell.size();
   if (ev) cudaEventRecord(ev[0], s);
   ExplicitArgs ea = explicit_args(c, Ucur, Unext, Unext, 2.0, -1.0, dt * dt, ft_at(hs, step), true);
   ea.ft_dev = ft_dev;
   explicit_dispatch(c, ea, c->ntx * c->nty + pred_blocks(c, true), s);
   if (ev) cudaEventRecord(ev[1], s);
-  if (hs.n_c > 0) {
-    IfaceArgs ia = iface_args(c, Unext);
-    k_iface<<<(nif + kWarps - 1) / kWarps, kThreads, 0, s>>>(ia);
-    if (ev) cudaEventRecord(ev[2], s);
-    launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, c->upd, c->sol, s);
-  } else if (ev) {
-    cudaEventRecord(ev[2], s);
-  }
-  if (ev) cudaEventRecord(ev[3], s);
+  if (hs.n_c > 0)
+    launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, c->upd, c->sol, c->rhs0, s);
+  if (ev) cudaEventRecord(ev[2], s);
   if (int rc = check_launch("imex_step")) return rc;
   c->cur = 1 - c->cur;
   c->step = step + 1;
@@ -1646,26 +1773,28 @@ int imex_step_profile(imex_ctx* c, int64_t n, void* stream, double* phase_ms) {
   if (!c || n < 0 || !phase_ms) return fail(IMEX_ERR_ARG, "bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   c->stream = s;
-  cudaEvent_t ev[4];
+  cudaEvent_t ev[3];
   for (auto& e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(IMEX_ERR_CUDA, "cudaEventCreate failed");
-  double acc[3] = {0, 0, 0};
+  // explicit apply, implicit chain, whole step
+  const int from[IMEX_PROFILE_PHASES] = {0, 1, 0}, to[IMEX_PROFILE_PHASES] = {1, 2, 2};
+  double acc[IMEX_PROFILE_PHASES] = {0, 0, 0};
   int rc = IMEX_OK;
   for (int64_t k = 0; k < n && rc == IMEX_OK; ++k) {
     rc = step_once(c, s, ev);
     if (rc) break;
-    if (cudaEventSynchronize(ev[3]) != cudaSuccess) {
+    if (cudaEventSynchronize(ev[2]) != cudaSuccess) {
       rc = fail(IMEX_ERR_CUDA, "imex_step_profile: synchronisation failed");
       break;
     }
-    for (int ph = 0; ph < 3; ++ph) {
+    for (int ph = 0; ph < IMEX_PROFILE_PHASES; ++ph) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]);
+      cudaEventElapsedTime(&ms, ev[from[ph]], ev[to[ph]]);
       acc[ph] += ms;
     }
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  for (int ph = 0; ph < 3; ++ph) phase_ms[ph] = acc[ph];
+  for (int ph = 0; ph < IMEX_PROFILE_PHASES; ++ph) phase_ms[ph] = acc[ph];
   return rc;
 }
 
@@ -1804,7 +1933,8 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   for (int n : c->lev_ncta) widest = std::max<int64_t>(widest, n);
   st->solve_ctas = widest;
   st->solve_smem_bytes = (int64_t)c->smem_walk;
-  st->launches_per_step = 2 + 2 * (int64_t)c->lev_cta0.size() + (c->ntop > 0 ? 1 : 0);
+  st->launches_per_step = launches_per_step(c);
+  st->rhs_pairs = (int64_t)c->hs.contrib_pos.size();
   st->device_bytes = (int64_t)c->bytes;
   return IMEX_OK;
 }
@@ -1845,8 +1975,8 @@ extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
   auto even = [](int64_t v) { return v + (v & 1); };
   const int64_t n_upd = even(std::max<int64_t>(hs.upd_size, 1));
   const int64_t n_sol = even(std::max<int64_t>(hs.n_c, 1));
-  if (n_upd + n_sol > kStaticScratchDoubles)
-    return fail(IMEX_ERR_ARG, "imex_step_noalloc: the implicit solve needs " + std::to_string(n_upd + n_sol) +
+  if (n_upd + 2 * n_sol > kStaticScratchDoubles)
+    return fail(IMEX_ERR_ARG, "imex_step_noalloc: the implicit solve needs " + std::to_string(n_upd + 2 * n_sol) +
                                   " doubles of scratch; the static scratch holds " +
                                   std::to_string(kStaticScratchDoubles) + " (use imex_step)");
   int dev = -1;
@@ -1867,21 +1997,17 @@ extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
   }
   double* upd = base;
   double* sol = upd + n_upd;
+  double* rhs0 = sol + n_sol;
   cudaStream_t s = (cudaStream_t)stream;
   c->stream = s;
   const double dt = hs.dt;
-  const int nif = (int)hs.if_cell.size();
   for (int64_t k = 0; k < n; ++k) {
     double* Ucur = c->U[c->cur];
     double* Unext = c->U[1 - c->cur];
     const int64_t step = c->step;
     ExplicitArgs ea = explicit_args(c, Ucur, Unext, Unext, 2.0, -1.0, dt * dt, ft_at(hs, step), true);
     explicit_dispatch(c, ea, c->ntx * c->nty + pred_blocks(c, true), s);
-    if (hs.n_c > 0) {
-      IfaceArgs ia = iface_args(c, Unext);
-      k_iface<<<(nif + kWarps - 1) / kWarps, kThreads, 0, s>>>(ia);
-      launch_solve_chain(c, true, ft_at(hs, step + 1), nullptr, 0, Unext, upd, sol, s);
-    }
+    if (hs.n_c > 0) launch_solve_chain(c, true, ft_at(hs, step + 1), nullptr, 0, Unext, Unext, upd, sol, rhs0, s);
     if (int rc = check_launch("imex_step_noalloc")) return rc;
     c->cur = 1 - c->cur;
     c->step = step + 1;

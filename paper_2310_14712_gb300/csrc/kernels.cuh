@@ -6,16 +6,14 @@
 //                uncut), fused with the CDM update on the lumped mass
 //                (Eqs. CDMacc, CDMstep); extra blocks do the Newmark
 //                prediction on I_c (A3).
-//   k_iface      A4: dense element products K_e u_pred for every cell touching
-//                I_c (stored matrices of cut cells, the uncut-cell matrix
-//                otherwise).
-//   k_walk / k_top   A4 gather + A5 + A6: right-hand side
-//                f_t(t_{n+1}) f_x^c - K^c u_pred, forward walk over the lower
-//                levels of the supernodal nested-dissection Cholesky factor
-//                of S (inverted diagonal blocks), one dense product per
-//                component for the upper levels, backward walk, Newmark
-//                correction.  One launch per level; kernel boundaries are the
-//                level barriers, so every launch can use every SM.
+//   k_walk / k_top   A4 + A5 + A6: right-hand side f_t(t_{n+1}) f_x^c -
+//                K^c u_pred (row by row from the interface cells' matrices, in
+//                the first forward launch), forward walk over the lower levels
+//                of the supernodal nested-dissection Cholesky factor of S
+//                (inverted diagonal blocks), one dense product per component
+//                for the upper levels, backward walk, Newmark correction.  One
+//                launch per level; kernel boundaries are the level barriers,
+//                so every launch can use every SM.
 #pragma once
 #include <cstdint>
 
@@ -79,55 +77,33 @@ struct ExplicitArgs {
   double dt;
 };
 
-struct IfaceArgs {
-  const double* SRC;      // u_pred (full grid)
-  const int* cell;        // interface cell ids
-  const int* kidx;        // >= 0: index into cutK; -1: uncut form
-  const double* c2;       // multiplier of the uncut form
-  const double* cutK;     // Pd x Pd column-major per cut cell
-  const double* uncutK;   // Pd x Pd column-major
-  double* Y;              // n_iface x Pd products
-  int n_iface;
-  int dim, p, P, Pd;
-  int ncx, ncy;
-  int nx, ny;
-};
-
 // One level of the supernodal walk of A5 (forward or backward), all
-// components at once.  The level's supernodes are packed into CTAs (one warp
-// per supernode); each CTA's blocks [L_tt^{-1} (ld b|1) | L_{rows,t} (ld m|1)]
-// are stored contiguously in `blob`.
+// components at once.  The level's supernodes are packed into CTAs; each
+// CTA's blocks [L_tt^{-1} (ld b|1) | L_{rows,t} (ld m|1)] are stored
+// contiguously in `blob`, its index list (layout in imex.cu, WalkList) in
+// `ilist`.  The first forward launch also forms the right-hand sides (A4).
 struct WalkArgs {
   int cta0;                     // first CTA of this level in the per-CTA arrays
   const double* blob;
   const int64_t* blob_off;      // [cta] (16-byte aligned)
   const int64_t* blob_len;      // [cta] (even)
-  const int* cta_node_ptr;      // [cta] -> range in cta_nodes
-  const int* cta_nodes;
-  const int64_t* node_boff;     // tree node -> offset of its blocks in its CTA's blob
-  int64_t max_blob;             // doubles reserved for the blob in shared memory (even)
-  const int* ilist;             // per-CTA index lists (see k_walk)
+  int64_t max_blob;             // doubles reserved for the blob in shared memory (even; 0 if not staged)
+  const int* ilist;
   const int64_t* ilist_off;     // [cta] (multiple of 4)
   const int64_t* ilist_len;     // [cta] (multiple of 4)
-  const int* node_slot;         // tree node -> first row slot in its CTA's list
-  const int* node_roff;         // tree node -> offset of its ancestor rows in its CTA's list
-  const int* t_beg;
-  const int* t_end;
-  const int* t_nrows;
-  const int64_t* t_off_upd;     // tree node -> its update vector in `upd`
-  const int64_t* t_off_rows;    // tree node -> its ancestor rows in `rows_idx`
-  const int* rows_idx;
-  const int* fwd_ptr;           // c-row -> positions of descendant updates in `upd`
-  const int* fwd_pos;
-  const int* contrib_ptr;       // c-row -> positions of element products in `Y`
-  const int* contrib_pos;
-  const double* Y;
+  int max_slots, max_m, max_pairs;  // shared-memory vector sizes (even)
+  // right-hand sides f_t f_x^c - K^c u (first forward launch)
+  int first;
+  const double* SRC;            // u_pred (step) or u_0 (initial acceleration), full grid
+  const double* Krows;          // rows of the interface cell matrices, Pd doubles each
+  const double* if_sc;          // per interface cell: 1 (stored matrix) or c_e^2 / c0^2 (uncut form)
+  int P, Pd, dim, nx, ny;
   const double* fxc;
   double ft;                    // f_t(t_{n+1}) (step) or f_t(0) (initial acceleration)
   const double* ft_dev;         // if set: f_t(t_{n+1}) = ft_dev[1]
+  double* rhs0;                 // right-hand side of every c-row not solved by the first launch
   double* upd;
   double* sol;
-  int W;                        // per-warp vector length (>= largest supernode and row set)
   // correction of the rows this launch finalises (backward only)
   int mode;                     // 0: Newmark correction; 1: store the acceleration only
   const int* c_node;
@@ -144,23 +120,16 @@ struct TopArgs {
   const int* cta_r0;            // [cta] first row of the chunk (within the component's Z)
   const int* cta_r1;
   const int* zsize;             // [comp] |Z|
-  const int* zbase;             // [comp] offset into zrow / zfwd_ptr
+  const int* zbase;             // [comp] offset into zrow
   const int* zrow;              // c-index of each Z row
   const int64_t* zA_off;        // [comp] offset of A_Z (row-major |Z| x |Z|, 16-byte aligned)
   const double* zA;
   int max_zn;                   // even
   int64_t max_arows;            // even: largest (r1 - r0) * |Z| over the CTAs
-  const int* ilist;             // per-CTA index lists: per Z row {contribution begin, update begin, end}
-  const int64_t* ilist_off;
-  const int64_t* ilist_len;
-  const int* zfwd_ptr;          // per Z row: update positions from the walked levels
-  const int* zfwd_pos;
-  const int* contrib_ptr;
-  const int* contrib_pos;
-  const double* Y;
-  const double* fxc;
-  double ft;
-  const double* ft_dev;
+  const int* ilist;             // per component: per Z row {update begin, update end}, then positions
+  const int64_t* ilist_off;     // [cta]
+  const int64_t* ilist_len;     // [cta]
+  const double* rhs0;
   const double* upd;
   double* sol;
   int mode;

@@ -57,7 +57,8 @@ class Stats(ctypes.Structure):
         "n_nodes", "n_d", "n_c", "n_cut", "n_uncut", "n_empty", "n_iface", "nnz_L",
         "n_components", "n_tree", "max_block", "step", "device_bytes")] + \
         [(n, ctypes.c_double) for n in ("dt", "dt_crit_uncut", "setup_seconds", "residual_S", "residual_M")] + \
-        [(n, ctypes.c_int64) for n in ("solve_levels", "solve_ctas", "solve_smem_bytes", "launches_per_step")]
+        [(n, ctypes.c_int64) for n in ("solve_levels", "solve_ctas", "solve_smem_bytes", "launches_per_step",
+                                    "rhs_pairs")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -236,10 +237,13 @@ class Imex:
         2 MiB device array and the call allocates nothing (see include/imex.h)."""
         _check(_lib.imex_step_noalloc(self._ctx, int(n), self._stream(stream)), "imex_step_noalloc")
 
+    PROFILE_PHASES = ("explicit", "implicit", "step")
+
     def step_profile(self, n, stream=None):
-        """Advance n steps with per-kernel CUDA events; returns summed device ms of
-        (explicit + CDM + prediction, interface products, solve + correction)."""
-        ms = (ctypes.c_double * 3)()
+        """Advance n steps with CUDA events around the kernels; returns the summed
+        device ms of (explicit + CDM + prediction, implicit chain: right-hand sides,
+        solve and correction, whole steps), in PROFILE_PHASES order."""
+        ms = (ctypes.c_double * len(self.PROFILE_PHASES))()
         _check(_lib.imex_step_profile(self._ctx, int(n), self._stream(stream), ms), "imex_step_profile")
         return tuple(ms)
 
