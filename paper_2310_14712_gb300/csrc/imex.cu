@@ -304,6 +304,19 @@ __device__ __forceinline__ void warp_gemv(const double* M, int si, int sj, int n
 
 // Newmark correction of one implicit row (Fig. TrapCDMIMEX "Correction"), or
 // the initial acceleration only (mode 1).
+// The same with c_node[r], v_c[r] and a_c[r] loaded beforehand (they are not
+// written by the kernels of the step that run before the correction).
+template <class Args>
+__device__ __forceinline__ void correct_row_pre(const Args& a, int r, double acc, int node, double v_old,
+                                                double a_old) {
+  if (a.mode == 0) {
+    const double vpred = v_old + (1.0 - kNewmarkGamma) * a.dt * a_old;
+    a.U[node] = a.U[node] + kNewmarkBeta * a.dt * a.dt * acc;
+    a.v_c[r] = vpred + kNewmarkGamma * a.dt * acc;
+  }
+  a.a_c[r] = acc;
+}
+
 template <class Args>
 __device__ __forceinline__ void correct_row(const Args& a, int r, double acc) {
   if (a.mode == 0) {
@@ -317,12 +330,13 @@ __device__ __forceinline__ void correct_row(const Args& a, int r, double acc) {
 
 // Per-CTA index list of a walk launch (ints, offsets relative to its start):
 //   [0] nq nodes, [1] nslot rows (sum of b), [2] nm ancestor rows (sum of m),
-//   [3] nrhs, [4] npair (first launch only), [5..7] unused
+//   [3] nrhs, [4] npair, [5] np = npair rounded up to even (first launch
+//   only; the cell-matrix rows of the pairs are staged separately), [6..7] 0
 //   node table at 8:          nq x {t, beg, b, m, slot0, moff, boff, updoff}
 //   slot table:               nslot x {q, update begin, update end, 0}
 //   ancestor table:           nm x {q, c-row}
 //   right-hand-side rows:     nrhs x {c-row, pair begin, pair end, slot or -1}
-//   pairs (row of K_e, cell): npair x {first node of the cell, K row, cell, 0}
+//   pairs:                    npair x {first node of the cell, 0, 0, 0}
 //   update positions (into upd).
 struct WalkList {
   const int* h;
@@ -340,24 +354,31 @@ struct WalkList {
   }
 };
 
-// Right-hand side of one (row, cell) pair: row l of the cell matrix times the
-// cell's nodal values (the row of K_e is stored contiguously).
-__device__ __forceinline__ double pair_product(const WalkArgs& a, const int* pr) {
-  const double* K = a.Krows + (size_t)pr[1] * a.Pd;
-  const double* u = a.SRC + pr[0];
+// Right-hand side of one (row, cell) pair k: row l of the cell matrix (scaled
+// by the cell's c_e^2 / c0^2 where the uncut form is used), staged m-major in
+// shared memory (kp[m * np + k]), times the cell's nodal values (off[m] is the
+// grid offset of local node m from the cell's first node).  Loads are issued
+// in batches of 16 before the products.
+constexpr int kMaxPd = 128;
+__device__ __forceinline__ double pair_product(const WalkArgs& a, const double* kp, int np, int k, int base,
+                                               const int* off) {
+  const double* u = a.SRC + base;
   double s0 = 0.0, s1 = 0.0;
-  int m = 0;
-  for (int k = 0; k < (a.dim == 3 ? a.P : 1); ++k)
-    for (int j = 0; j < a.P; ++j) {
-      const double* ur = u + (size_t)k * a.nx * a.ny + (size_t)j * a.nx;
-      int i = 0;
-      for (; i + 2 <= a.P; i += 2, m += 2) {
-        s0 = fma(__ldg(K + m), __ldcg(ur + i), s0);
-        s1 = fma(__ldg(K + m + 1), __ldcg(ur + i + 1), s1);
-      }
-      if (i < a.P) { s0 = fma(__ldg(K + m), __ldcg(ur + i), s0); ++m; }
+  for (int m0 = 0; m0 < a.Pd; m0 += 16) {
+    double kv[16], uv[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const bool ok = m0 + t < a.Pd;
+      kv[t] = ok ? kp[(size_t)(m0 + t) * np + k] : 0.0;
+      uv[t] = ok ? __ldg(u + off[ok ? m0 + t : 0]) : 0.0;
     }
-  return a.if_sc[pr[2]] * (s0 + s1);
+#pragma unroll
+    for (int t = 0; t < 16; t += 2) {
+      s0 = fma(kv[t], uv[t], s0);
+      s1 = fma(kv[t + 1], uv[t + 1], s1);
+    }
+  }
+  return s0 + s1;
 }
 
 template <bool kForward, bool kSmem>
@@ -366,26 +387,50 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
   const int cta = a.cta0 + blockIdx.x;
   const int tid = threadIdx.x;
   double* blob = sm;                                   // max_blob (smem mode)
-  double* vg = blob + a.max_blob;                      // max_slots: g (fwd) / y (bwd)
+  double* kp = blob + a.max_blob;                      // max_kp: rows of the cell matrices (first launch)
+  double* vg = kp + a.max_kp;                          // max_slots: g (fwd) / y (bwd)
   double* vy = vg + a.max_slots;                       // max_slots: y (fwd) / h (bwd)
   double* vm = vy + a.max_slots;                       // max_m: x of the ancestor rows (bwd)
   double* pc = vm + a.max_m;                           // max_pairs: pair products (first launch)
   int* il = reinterpret_cast<int*>(pc + a.max_pairs);
+  __shared__ int s_off[kForward ? kMaxPd : 1];         // grid offset of each local node of a cell
+  if (kForward && a.first)
+    for (int m = tid; m < a.Pd; m += kThreads)
+      s_off[m] = (m % a.P) + a.nx * ((m / a.P) % a.P) + a.nx * a.ny * (m / (a.P * a.P));
   const int64_t boff = a.blob_off[cta];
   if (kSmem) async_copy_16(blob, a.blob + boff, a.blob_len[cta] / 2);
   async_copy_16(il, a.ilist + a.ilist_off[cta], a.ilist_len[cta] / 4);
+  if (kForward && a.first) async_copy_16(kp, a.Kpair + a.kp_off[cta], a.kp_len[cta] / 2);
   const double* B = kSmem ? blob : a.blob + boff;
-  // Let the next launch stage its constants; wait for the previous results.
+  // Let the next launch stage its constants.
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
   async_copy_wait();
   const WalkList L(il);
   const int nslot = il[1], nm = il[2];
+  // Backward: the correction state of this thread's first two rows.
+  int pre_node[2] = {0, 0};
+  double pre_v[2] = {0.0, 0.0}, pre_a[2] = {0.0, 0.0};
+  if (!kForward) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int sl = tid + q * kThreads;
+      if (sl < nslot) {
+        const int* nd = L.node + 8 * L.slot[4 * sl];
+        const int r = nd[1] + (sl - nd[4]);
+        pre_node[q] = a.c_node[r];
+        pre_v[q] = a.v_c[r];
+        pre_a[q] = a.a_c[r];
+      }
+    }
+  }
+  // Wait for the previous launch's results.
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
   if (kForward) {
     if (a.first) {
       const int npair = il[4], nrhs = il[3];
       const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
-      for (int k = tid; k < npair; k += kThreads) pc[k] = pair_product(a, L.pair + 4 * k);
+      const int np = il[5];
+      for (int k = tid; k < npair; k += kThreads) pc[k] = pair_product(a, kp, np, k, L.pair[4 * k], s_off);
       __syncthreads();
       for (int k = tid; k < nrhs; k += kThreads) {
         const int* rr = L.rhs + 4 * k;
@@ -479,27 +524,40 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
       if (j < b) x0 = fma(Lc[j], vy[s0 + j], x0);
       const double x = x0 + x1;
       a.sol[nd[1] + i] = x;
-      correct_row(a, nd[1] + i, x);
+      if (sl < tid + kThreads) correct_row_pre(a, nd[1] + i, x, pre_node[0], pre_v[0], pre_a[0]);
+      else if (sl < tid + 2 * kThreads) correct_row_pre(a, nd[1] + i, x, pre_node[1], pre_v[1], pre_a[1]);
+      else correct_row(a, nd[1] + i, x);
     }
   }
 }
 
 __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   extern __shared__ __align__(16) double tsm[];
-  const int cta = blockIdx.x;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int cta = blockIdx.x, tid = threadIdx.x;
+  const int warp = tid / 32, lane = tid % 32;
   const int comp = a.cta_comp[cta], r0 = a.cta_r0[cta], r1 = a.cta_r1[cta];
-  const int zn = a.zsize[comp], zb = a.zbase[comp];
+  const int zn = a.zsize[comp], zb = a.zbase[comp], nr = r1 - r0;
   double* zs = tsm;                               // max_zn (even): right-hand side of the block
-  double* Ac = zs + a.max_zn;                     // max_rows_zn: this CTA's rows of A_Z
-  int* il = reinterpret_cast<int*>(Ac + a.max_arows);  // per row {update begin, update end}
-  async_copy_16(Ac, a.zA + a.zA_off[comp] + (size_t)r0 * zn, ((int64_t)(r1 - r0) * zn + 1) / 2);
+  double* Ac = zs + a.max_zn;                     // max_arows: this CTA's rows of A_Z
+  double* xs = Ac + a.max_arows;                  // max_chunk: this CTA's results
+  int* il = reinterpret_cast<int*>(xs + a.max_chunk);  // per row {update begin, update end}
+  async_copy_16(Ac, a.zA + a.zA_off[comp] + (size_t)r0 * zn, ((int64_t)nr * zn + 1) / 2);
   async_copy_16(il, a.ilist + a.ilist_off[cta], a.ilist_len[cta] / 4);
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  // The correction state of this thread's row (nr <= blockDim.x); not written
+  // by the launches of the step that run before this one.
+  int row = 0, node = 0;
+  double v_old = 0.0, a_old = 0.0;
+  if (tid < nr) {
+    row = a.zrow[zb + r0 + tid];
+    node = a.c_node[row];
+    v_old = a.v_c[row];
+    a_old = a.a_c[row];
+  }
   async_copy_wait();
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
   // The whole right-hand side of this component's top block (redundant per CTA).
-  for (int i = threadIdx.x; i < zn; i += kThreads) {
+  for (int i = tid; i < zn; i += kThreads) {
     const int fb = il[2 * i], fe = il[2 * i + 1];
     double v = __ldcg(a.rhs0 + a.zrow[zb + i]);
 #pragma unroll 4
@@ -507,8 +565,8 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
     zs[i] = v;
   }
   __syncthreads();
-  for (int i = r0 + warp; i < r1; i += kWarps) {
-    const double* Ar = Ac + (size_t)(i - r0) * zn;
+  for (int i = warp; i < nr; i += kWarps) {
+    const double* Ar = Ac + (size_t)i * zn;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int j = lane;
     for (; j + 96 < zn; j += 128) {
@@ -521,11 +579,13 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
     double v = (s0 + s1) + (s2 + s3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) {
-      const int r = a.zrow[zb + i];
-      a.sol[r] = v;
-      correct_row(a, r, v);
-    }
+    if (lane == 0) xs[i] = v;
+  }
+  __syncthreads();
+  if (tid < nr) {
+    const double x = xs[tid];
+    a.sol[row] = x;
+    correct_row_pre(a, row, x, node, v_old, a_old);
   }
 }
 
@@ -603,7 +663,9 @@ struct imex_ctx {
   int* c_node = nullptr;
   double *v_c = nullptr, *a_c = nullptr, *fxc = nullptr;
   // right-hand sides: rows of the interface cell matrices, per-cell scales
-  double *Krows = nullptr, *if_sc = nullptr, *rhs0 = nullptr;
+  double *Kpair = nullptr, *rhs0 = nullptr;
+  int64_t *kp_off = nullptr, *kp_len = nullptr;
+  int64_t walk_max_kp = 0;
   // solve: per-CTA factor blobs (S and M^cc) and index lists, dense tops, scratch
   double *blob_S = nullptr, *blob_M = nullptr;
   int64_t *blob_off = nullptr, *blob_len = nullptr;
@@ -613,7 +675,7 @@ struct imex_ctx {
   int walk_max_slots = 2, walk_max_m = 2, walk_max_pairs = 2;
   int* tlist = nullptr;
   int64_t *tlist_off = nullptr, *tlist_len = nullptr;
-  int top_max_zn = 2;
+  int top_max_zn = 2, top_max_chunk = 2;
   int64_t top_max_arows = 0;
   std::vector<int> lev_cta0, lev_ncta, lev_has_nodes;   // per walked level: CTA range
   int walk_smem_mode = 0;
@@ -770,7 +832,7 @@ int pred_blocks(imex_ctx* c, bool predict) {
 constexpr int kMaxWidth = 256;                 // largest supernode / row set of the walk
 constexpr size_t kWalkSmemBudget = 200 * 1024;  // shared memory per walk CTA (staged factor)
 constexpr size_t kTopSmemBudget = 200 * 1024;   // shared memory per dense-top CTA
-constexpr size_t kMaxDynSmem = 227 * 1024;      // largest dynamic shared memory of a CTA
+constexpr size_t kMaxDynSmem = 220 * 1024;      // dynamic shared memory limit we set (static use < 7 KB)
 
 // The launches of the implicit solve: forward walk over the lower levels
 // (the first also forms every right-hand side from src), dense tops,
@@ -792,8 +854,10 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   w.max_m = c->walk_max_m;
   w.max_pairs = c->walk_max_pairs;
   w.SRC = src;
-  w.Krows = c->Krows;
-  w.if_sc = c->if_sc;
+  w.Kpair = c->Kpair;
+  w.kp_off = c->kp_off;
+  w.kp_len = c->kp_len;
+  w.max_kp = c->walk_max_kp;
   w.P = hs.P;
   w.Pd = hs.Pd;
   w.dim = hs.dim;
@@ -822,6 +886,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   z.zA = use_S ? c->zA_S : c->zA_M;
   z.max_zn = c->top_max_zn;
   z.max_arows = c->top_max_arows;
+  z.max_chunk = c->top_max_chunk;
   z.ilist = c->tlist;
   z.ilist_off = c->tlist_off;
   z.ilist_len = c->tlist_len;
@@ -921,13 +986,17 @@ struct SolvePlan {
   int64_t max_ilist = 0;
   int max_slots = 2, max_m = 2, max_pairs = 2;
   std::vector<int> lev_has_nodes;
-  // Rows of the interface cell matrices (row-major) and per-cell scale.
-  std::vector<double> Krows, if_sc;
+  // Rows of the interface cell matrices (row-major) and per-cell scale; per
+  // level-0 CTA the rows of its pairs (m-major, scaled).
+  std::vector<double> Krows, if_sc, Kpair;
+  std::vector<int64_t> kp_off, kp_len;
+  int64_t max_kp = 0;
   std::vector<int> top_comp, top_r0, top_r1;
   // Per-component index lists of the dense tops (one entry per top CTA).
   std::vector<int> tlist;
   std::vector<int64_t> tlist_off, tlist_len;
   int64_t max_tlist = 0, max_arows = 0;
+  int max_chunk = 2;
   std::vector<int> zsize, zbase, zrow, zfwd_ptr, zfwd_pos;
   std::vector<int64_t> zA_off;
   std::vector<double> zA_S, zA_M;
@@ -1162,7 +1231,7 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
         if (l == 0) pairs += npairs_of(r);
       }
       ints += l == 0 ? 4 * b + 4 * pairs : 0;
-      return (b | 1) * b + (m | 1) * b + 2 * b + m + pairs + (ints + 1) / 2 + 2;
+      return (b | 1) * b + (m | 1) * b + 2 * b + m + (Pd + 1) * pairs + (ints + 1) / 2 + 2;
     };
     int target = std::max(1, std::min<int>((int)nodes.size(), kTargetCTAs));
     if (l == 0)
@@ -1303,6 +1372,23 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
         rr[2] = pq;
         rr[3] = rslot[k];
       }
+      Lst[5] = npair + (npair & 1);
+      // Rows of the cell matrices of the pairs, m-major, scales folded in.
+      if (P.Kpair.size() % 2) P.Kpair.push_back(0.0);
+      P.kp_off.push_back((int64_t)P.Kpair.size());
+      {
+        const int np = npair + (npair & 1);
+        std::vector<double> blk((size_t)Pd * np, 0.0);
+        for (int k = 0; k < npair; ++k) {
+          const int* pr = &Lst[o_pair + 4 * k];
+          const double* row = P.Krows.data() + (size_t)pr[1] * Pd;
+          const double sc = P.if_sc[pr[2]];
+          for (int m = 0; m < Pd; ++m) blk[(size_t)m * np + k] = sc * row[m];
+        }
+        P.Kpair.insert(P.Kpair.end(), blk.begin(), blk.end());
+        P.kp_len.push_back((int64_t)blk.size());
+        P.max_kp = std::max<int64_t>(P.max_kp, (int64_t)blk.size());
+      }
       while (Lst.size() % 4) Lst.push_back(0);
       P.ilist_off.push_back((int64_t)P.ilist.size());
       P.ilist_len.push_back((int64_t)Lst.size());
@@ -1316,8 +1402,6 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
   }
   (void)vec_doubles;
   // Dense tops: row chunks, about one CTA per SM over the whole launch.
-  int64_t zsum = 0;
-  for (int k = 0; k < hs.ncomp; ++k) zsum += zsize[k];
   std::vector<std::vector<int>> tl(hs.ncomp);
   for (int k = 0; k < hs.ncomp; ++k) {
     const int zn = zsize[k], zb = zbase[k];
@@ -1332,22 +1416,37 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
     P.max_tlist = std::max<int64_t>(P.max_tlist, (int64_t)L.size());
   }
   const int64_t max_zn_even = std::max(2, max_zn + (max_zn & 1));
-  int chunk = (int)std::max<int64_t>(kWarps, ((zsum + kTargetCTAs - 1) / kTargetCTAs + kWarps - 1) / kWarps * kWarps);
-  auto top_smem = [&](int ch) {
-    const int64_t rows = (int64_t)std::min(ch, max_zn) * max_zn;
-    return (size_t)(max_zn_even + rows + (rows & 1)) * sizeof(double) + (size_t)P.max_tlist * sizeof(int);
+  // Rows per CTA from the FP64 work |Z|^2 spread over at most one CTA per SM
+  // (even, so that every chunk of A_Z starts on a 16-byte boundary; at most
+  // one row per thread).
+  int64_t zwork = 0;
+  for (int k = 0; k < hs.ncomp; ++k) zwork += (int64_t)zsize[k] * zsize[k];
+  std::vector<int> chunk_of(hs.ncomp, 2);
+  auto top_smem = [&](int64_t rows, int ch) {
+    return (size_t)(max_zn_even + rows + (rows & 1) + ch) * sizeof(double) + (size_t)P.max_tlist * sizeof(int);
   };
-  while (chunk > kWarps && top_smem(chunk) > kTopSmemBudget) chunk -= kWarps;
-  if (top_smem(chunk) > kTopSmemBudget)
-    return fail(IMEX_ERR_ARG, "dense top block too large for shared memory (lower IMEX_DENSE_TOP_MAX)");
+  for (int64_t wcta = std::max<int64_t>(1, zwork / kTargetCTAs);; wcta += wcta / 8 + 1) {
+    int64_t nctas = 0;
+    for (int k = 0; k < hs.ncomp; ++k) {
+      const int zn = std::max(1, zsize[k]);
+      int ch = (int)std::max<int64_t>(2, std::min<int64_t>({(int64_t)zn, wcta / zn, (int64_t)kThreads}));
+      ch += ch & 1;
+      while (ch > 2 && top_smem((int64_t)ch * zn, ch) > kTopSmemBudget) ch -= 2;
+      if (top_smem((int64_t)ch * zn, ch) > kTopSmemBudget)
+        return fail(IMEX_ERR_ARG, "dense top block too large for shared memory (lower IMEX_DENSE_TOP_MAX)");
+      chunk_of[k] = ch;
+      if (zsize[k] > 0) nctas += (zsize[k] + ch - 1) / ch;
+    }
+    if (nctas <= kTargetCTAs || wcta > zwork) break;
+  }
   std::vector<int64_t> comp_off(hs.ncomp, 0);
   for (int k = 0; k < hs.ncomp; ++k) {
     comp_off[k] = (int64_t)P.tlist.size();
     P.tlist.insert(P.tlist.end(), tl[k].begin(), tl[k].end());
   }
   for (int k = 0; k < hs.ncomp; ++k)
-    for (int r0 = 0; r0 < zsize[k]; r0 += chunk) {
-      const int r1 = std::min(zsize[k], r0 + chunk);
+    for (int r0 = 0; r0 < zsize[k]; r0 += chunk_of[k]) {
+      const int r1 = std::min(zsize[k], r0 + chunk_of[k]);
       P.top_comp.push_back(k);
       P.top_r0.push_back(r0);
       P.top_r1.push_back(r1);
@@ -1355,6 +1454,7 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
       P.tlist_len.push_back((int64_t)tl[k].size());
       const int64_t rows = (int64_t)(r1 - r0) * zsize[k];
       P.max_arows = std::max<int64_t>(P.max_arows, rows + (rows & 1));
+      P.max_chunk = std::max(P.max_chunk, (r1 - r0) + ((r1 - r0) & 1));
     }
   P.zsize = zsize;
   P.zbase = zbase;
@@ -1544,6 +1644,10 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       delete c;
       return fail(IMEX_ERR_ARG, "supernode too large for the device solve (max 256)");
     }
+    if (hs.Pd > kMaxPd) {
+      delete c;
+      return fail(IMEX_ERR_ARG, "cell too large for the device right-hand side (P^d > 128)");
+    }
     if (cudaGetDevice(&c->device) != cudaSuccess) {
       delete c;
       return fail(IMEX_ERR_CUDA, "no CUDA device");
@@ -1594,7 +1698,8 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       c->walk_max_slots = plan.max_slots;
       c->walk_max_m = plan.max_m;
       c->walk_max_pairs = plan.max_pairs;
-      const size_t vec = (size_t)(2 * plan.max_slots + plan.max_m + plan.max_pairs) * sizeof(double);
+      c->walk_max_kp = plan.max_kp + (plan.max_kp & 1);
+      const size_t vec = (size_t)(c->walk_max_kp + 2 * plan.max_slots + plan.max_m + plan.max_pairs) * sizeof(double);
       const size_t lists = (size_t)plan.max_ilist * sizeof(int);
       const size_t staged = vec + (size_t)plan.max_blob * sizeof(double) + lists;
       c->walk_smem_mode = staged <= kMaxDynSmem ? 1 : 0;
@@ -1603,7 +1708,9 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       c->lev_has_nodes = plan.lev_has_nodes;
       c->top_max_zn = std::max(2, plan.max_zn + (plan.max_zn & 1));
       c->top_max_arows = plan.max_arows;
-      c->smem_top = (size_t)(c->top_max_zn + plan.max_arows) * sizeof(double) + (size_t)plan.max_tlist * sizeof(int);
+      c->top_max_chunk = plan.max_chunk;
+      c->smem_top = (size_t)(c->top_max_zn + plan.max_arows + plan.max_chunk) * sizeof(double) +
+                    (size_t)plan.max_tlist * sizeof(int);
       if (c->smem_walk > kMaxDynSmem || c->smem_top > kMaxDynSmem) {
         delete c;
         return fail(IMEX_ERR_ARG, "solve schedule exceeds the shared memory of a CTA");
@@ -1631,8 +1738,9 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->sol, std::max<int64_t>(nc, 1));
     ar.add(&c->rhs0, std::max<int64_t>(nc, 1));
     ar.add(&c->upd, std::max<int64_t>(hs.upd_size, 1));
-    ar.add(&c->Krows, std::max<size_t>(plan.Krows.size(), 1));
-    ar.add(&c->if_sc, std::max<size_t>(plan.if_sc.size(), 1));
+    ar.add(&c->Kpair, std::max<size_t>(plan.Kpair.size(), 2));
+    ar.add(&c->kp_off, nblobcta);
+    ar.add(&c->kp_len, nblobcta);
     ar.add(&c->blob_S, std::max<size_t>(plan.blobS.size(), 2));
     ar.add(&c->blob_M, std::max<size_t>(plan.blobM.size(), 2));
     ar.add(&c->blob_off, nblobcta);
@@ -1680,8 +1788,9 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->cls, hs.node_class);
     e = e ? e : upload(c->c_node, hs.c_node);
     e = e ? e : upload(c->fxc, fxc);
-    e = e ? e : upload(c->Krows, plan.Krows);
-    e = e ? e : upload(c->if_sc, plan.if_sc);
+    e = e ? e : upload(c->Kpair, plan.Kpair);
+    e = e ? e : upload(c->kp_off, plan.kp_off);
+    e = e ? e : upload(c->kp_len, plan.kp_len);
     e = e ? e : upload(c->blob_S, plan.blobS);
     e = e ? e : upload(c->blob_M, plan.blobM);
     e = e ? e : upload(c->blob_off, plan.blob_off);

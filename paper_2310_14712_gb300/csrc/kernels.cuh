@@ -95,8 +95,10 @@ struct WalkArgs {
   // right-hand sides f_t f_x^c - K^c u (first forward launch)
   int first;
   const double* SRC;            // u_pred (step) or u_0 (initial acceleration), full grid
-  const double* Krows;          // rows of the interface cell matrices, Pd doubles each
-  const double* if_sc;          // per interface cell: 1 (stored matrix) or c_e^2 / c0^2 (uncut form)
+  const double* Kpair;          // per CTA: rows of the cell matrices of its pairs (m-major, scaled)
+  const int64_t* kp_off;        // [cta] (16-byte aligned)
+  const int64_t* kp_len;        // [cta] (even)
+  int64_t max_kp;               // doubles reserved for them in shared memory (even)
   int P, Pd, dim, nx, ny;
   const double* fxc;
   double ft;                    // f_t(t_{n+1}) (step) or f_t(0) (initial acceleration)
@@ -126,6 +128,7 @@ struct TopArgs {
   const double* zA;
   int max_zn;                   // even
   int64_t max_arows;            // even: largest (r1 - r0) * |Z| over the CTAs
+  int max_chunk;                // even: largest r1 - r0 (<= threads per CTA)
   const int* ilist;             // per component: per Z row {update begin, update end}, then positions
   const int64_t* ilist_off;     // [cta]
   const int64_t* ilist_len;     // [cta]
