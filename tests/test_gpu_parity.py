@@ -199,9 +199,12 @@ def test_deterministic_runs():
 
 
 def test_plate256_full_size_sampled():
-    # The benchmarked workload at full size (256 x 128 cells, p = 4): 200 steps
-    # against the oracle on every node (the oracle handles this size in minutes).
-    _check_run(workloads.plate256(), 200)
+    # The benchmarked workload at full size (256 x 128 cells, p = 4) against the
+    # oracle on every node.  600 steps: the Ricker pulse from (0.1, 0.5) reaches
+    # the first holes after about 360 steps; before that the implicit partition
+    # only holds the scheme's exponentially small tails (|v_c| ~ 1e-16 at 200
+    # steps), where a relative norm measures nothing.
+    _check_run(workloads.plate256(), 600)
 
 
 def test_step_io_source_samples_and_receivers():
