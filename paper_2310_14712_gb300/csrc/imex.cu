@@ -697,7 +697,8 @@ struct imex_ctx {
   cudaStream_t stream = nullptr;
   Ops2D ops{};
   int TC = 4, ntx = 1, nty = 1;
-  int explicit_slots = 152;   // resident CTAs of the explicit kernel on the device
+  int explicit_per_sm = 1;    // resident CTAs of the explicit kernel per SM
+  int num_sms = 152;
   size_t smem_explicit = 0;
 };
 
@@ -817,14 +818,16 @@ ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double
 }
 
 // CTAs for the Newmark prediction, appended to the tiles of the explicit
-// launch: the resident slots the tiles leave free in their last wave (so the
-// launch stays one wave when the tiles fit), at least one, at most one per
-// 256 rows.
+// launch.  The tiles are FP64-bound and the block scheduler hands CTAs to the
+// SMs in turn, so the launch is sized to ceil(tiles / SMs) CTAs per SM: the
+// prediction fills the last round instead of adding a further CTA to some
+// SMs.  At least one, at most one per 256 rows.
 int pred_blocks(imex_ctx* c, bool predict) {
   if (!predict || c->hs.n_c == 0) return 0;
   const int64_t tiles = (int64_t)c->ntx * c->nty;
-  const int64_t slots = std::max<int64_t>(1, c->explicit_slots);
-  int64_t spare = (slots - tiles % slots) % slots;
+  const int64_t nsm = std::max(1, c->num_sms);
+  const int64_t per_sm = std::min<int64_t>((tiles + nsm - 1) / nsm, std::max(1, c->explicit_per_sm));
+  int64_t spare = (per_sm * nsm - tiles % (per_sm * nsm)) % (per_sm * nsm);
   if (spare == 0) spare = 8;
   return (int)std::max<int64_t>(1, std::min<int64_t>(spare, (c->hs.n_c + kThreads - 1) / kThreads));
 }
@@ -1819,7 +1822,8 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       int nsm = 0, per_sm = 0;
       e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
       e = e ? e : explicit_occupancy_dispatch(P, c->smem_explicit, &per_sm);
-      c->explicit_slots = std::max(1, nsm * per_sm);
+      c->num_sms = std::max(1, nsm);
+      c->explicit_per_sm = std::max(1, per_sm);
     }
     if (e != cudaSuccess) {
       std::string msg = std::string("upload failed: ") + cudaGetErrorString(e);
