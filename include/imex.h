@@ -111,6 +111,7 @@ typedef struct {
   int64_t solve_smem_bytes;/* shared memory per walk CTA (factor blocks staged when they fit) */
   int64_t launches_per_step; /* kernel launches of one imex_step step */
   int64_t rhs_pairs;       /* (c-row, interface cell) pairs of K^c u: one P^d dot product each */
+  int64_t ncols;           /* independent source columns (imex_setup_batch) */
 } imex_stats;
 
 /*
@@ -128,6 +129,24 @@ typedef struct {
  */
 int imex_setup(const imex_mesh *mesh, int p, double alpha, double dt, const imex_source *src,
                const imex_alloc *alloc, imex_ctx **out);
+
+/*
+ * imex_setup_batch - imex_setup() for ncols independent simulations that share
+ * the geometry, order, alpha, dt and source time function and differ only in
+ * the source position: column k is loaded by the bell at src->pos[k] alone
+ * (src->nsrc == ncols; with ncols == 1 the nsrc bells are summed, as in
+ * imex_setup).  One factorisation serves every column; each launch of a step
+ * covers all columns.  Every field exchanged through imex_fields,
+ * imex_set_fields and imex_set_initial then holds ncols canonical grids, one
+ * after the other (len = ncols * n_nodes).
+ *   ncols : 1 .. 256
+ * Errors: as imex_setup; IMEX_ERR_ARG if ncols is out of range or
+ * ncols > 1 and src->nsrc != ncols.
+ * No counterpart in the paper (it runs one source): independent right-hand
+ * sides are the batched form of the same method.
+ */
+int imex_setup_batch(const imex_mesh *mesh, int p, double alpha, double dt, const imex_source *src,
+                     int ncols, const imex_alloc *alloc, imex_ctx **out);
 
 /*
  * imex_step - advance n >= 0 Newmark IMEX steps (Fig. TrapCDMIMEX), each:
@@ -154,7 +173,8 @@ int imex_step_profile(imex_ctx *ctx, int64_t n, void *stream, double *phase_ms);
  *                f_t(t_{n0}), ..., f_t(t_{n0+n}) replacing it (e.g. a recorded
  *                or inverted source signature); step k reads samples k, k+1
  *   rec_nodes  : nrec canonical node indices (receivers), 0 <= nrec <= 4096
- *   traces     : n x nrec host array; row k receives u_{n0+k+1} at the receivers
+ *   traces     : n x ncols x nrec host array; entry (k, col, i) receives
+ *                u_{n0+k+1} of column col at receiver i
  * Synchronous (returns when the traces are on the host).
  * Errors: IMEX_ERR_ARG (bad sizes or node indices), IMEX_ERR_CUDA.
  */
@@ -185,7 +205,8 @@ int imex_step_noalloc(imex_ctx *ctx, int64_t n, void *stream);
 
 /*
  * imex_fields - copy one field (IMEX_FIELD_*) in canonical layout into dst.
- *   len          : number of doubles in dst; must equal imex_stats.n_nodes
+ *   len          : number of doubles in dst; must equal ncols * imex_stats.n_nodes
+ *                  (column after column)
  *   dst_on_device: nonzero if dst is device memory (copy stays on the device)
  * Synchronises the context's last stream.  Errors: IMEX_ERR_ARG, IMEX_ERR_CUDA.
  */
@@ -193,7 +214,7 @@ int imex_fields(imex_ctx *ctx, int which, double *dst, int64_t len, int dst_on_d
 
 /*
  * imex_set_fields - overwrite one state field (U, U_PREV_D, V_C or A_C) from src
- * (canonical layout, len = n_nodes); entries outside the field's partition are
+ * (canonical layout, len = ncols * n_nodes); entries outside the field's partition are
  * ignored.  With imex_set_step() this restores a checkpoint exactly.
  */
 int imex_set_fields(imex_ctx *ctx, int which, const double *src, int64_t len, int src_on_device);
@@ -202,7 +223,7 @@ int imex_set_fields(imex_ctx *ctx, int which, const double *src, int64_t len, in
 int imex_set_step(imex_ctx *ctx, int64_t n);
 
 /*
- * imex_set_initial - restart from u_0, v_0 (canonical layout, len = n_nodes) at
+ * imex_set_initial - restart from u_0, v_0 (canonical layout, len = ncols * n_nodes) at
  * n = 0: stores u_0, v^c_0, and computes on the device the CDM history
  * u^d_{-1} = u^d_0 - dt v^d_0 + dt^2/2 a^d_0 (Taylor start) and a^c_0 from
  * M^cc a^c_0 = f_t(0) f_x^c - K^c u_0.  v0 may be NULL (zero).

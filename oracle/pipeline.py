@@ -46,6 +46,15 @@ def setup(dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0,
     return s
 
 
+def setup_columns(src_pos, **kw):
+    """Independent source columns: one single-source setup per position.
+
+    Column k is the whole method run with the bell at src_pos[k] alone; the
+    columns share nothing but the inputs (a plain loop, no batching)."""
+    pos = np.asarray(src_pos, dtype=np.float64)
+    return [setup(src_pos=pos[k:k + 1], **kw) for k in range(len(pos))]
+
+
 def run(s, nsteps, u0=None, v0=None, callback=None):
     """Run `nsteps` IMEX steps from the initial state; returns the ImexState."""
     return s.imex.run(nsteps, u0=u0, v0=v0, callback=callback)

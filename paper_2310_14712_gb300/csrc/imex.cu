@@ -63,6 +63,12 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int ntiles = a.ntx * a.nty;
+  // Column of an independent-columns context (blockIdx.y).
+  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
+  const double* Uc = a.U + on;
+  const double* Wc = a.W + on;     // may alias OUTc
+  double* OUTc = a.OUT + on;
+  const double* fxc = a.fx + on;
   // The first solve launch may start staging its constant factor blocks now;
   // it waits for this grid (griddepcontrol.wait) before it reads u.
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
@@ -73,7 +79,7 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
     const int stride = (gridDim.x - ntiles) * blockDim.x;
     for (int r = (blockIdx.x - ntiles) * blockDim.x + tid; r < a.n_c; r += stride) {
       const int node = a.c_node[r];
-      a.OUT[node] = a.U[node] + c1 * a.v_c[r] + c2 * a.a_c[r];
+      OUTc[node] = Uc[node] + c1 * a.v_c[oc + r] + c2 * a.a_c[oc + r];
     }
     return;
   }
@@ -97,7 +103,7 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
   for (int idx = tid; idx < RY * RX; idx += kThreads) {
     const int yy = idx / RX, xx = idx - yy * RX;
     const int gx = X0 - p + xx, gy = Y0 - p + yy;
-    su[idx] = (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny) ? a.U[(size_t)gy * a.nx + gx] : 0.0;
+    su[idx] = (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny) ? Uc[(size_t)gy * a.nx + gx] : 0.0;
   }
   __syncthreads();
 
@@ -225,8 +231,8 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
     const double u = su[(yo + p) * RX + xo + p];
     const double minv = a.winv_x[gx] * a.winv_y[gy];
     const double ft = a.ft_dev ? a.ft_dev[0] : a.ft;
-    const double acc = minv * (ft * a.fx[g] - r);
-    a.OUT[g] = a.cu * u + a.cw * a.W[g] + a.ca * acc;
+    const double acc = minv * (ft * fxc[g] - r);
+    OUTc[g] = a.cu * u + a.cw * Wc[g] + a.ca * acc;
   }
 }
 
@@ -303,30 +309,34 @@ __device__ __forceinline__ void warp_gemv(const double* M, int si, int sj, int n
 }
 
 // Newmark correction of one implicit row (Fig. TrapCDMIMEX "Correction"), or
-// the initial acceleration only (mode 1).
-// The same with c_node[r], v_c[r] and a_c[r] loaded beforehand (they are not
-// written by the kernels of the step that run before the correction).
-template <class Args>
-__device__ __forceinline__ void correct_row_pre(const Args& a, int r, double acc, int node, double v_old,
-                                                double a_old) {
-  if (a.mode == 0) {
-    const double vpred = v_old + (1.0 - kNewmarkGamma) * a.dt * a_old;
-    a.U[node] = a.U[node] + kNewmarkBeta * a.dt * a.dt * acc;
-    a.v_c[r] = vpred + kNewmarkGamma * a.dt * acc;
+// the initial acceleration only (mode 1), on one column's fields.
+struct Corr {
+  int mode;
+  const int* c_node;
+  double* U;      // holds u_pred on I_c; receives u^c_{n+1}
+  double* v_c;
+  double* a_c;
+  double dt;
+  __device__ void row(int r, double acc) const {
+    if (mode == 0) {
+      const int node = c_node[r];
+      const double vpred = v_c[r] + (1.0 - kNewmarkGamma) * dt * a_c[r];
+      U[node] = U[node] + kNewmarkBeta * dt * dt * acc;
+      v_c[r] = vpred + kNewmarkGamma * dt * acc;
+    }
+    a_c[r] = acc;
   }
-  a.a_c[r] = acc;
-}
-
-template <class Args>
-__device__ __forceinline__ void correct_row(const Args& a, int r, double acc) {
-  if (a.mode == 0) {
-    const int node = a.c_node[r];
-    const double vpred = a.v_c[r] + (1.0 - kNewmarkGamma) * a.dt * a.a_c[r];
-    a.U[node] = a.U[node] + kNewmarkBeta * a.dt * a.dt * acc;
-    a.v_c[r] = vpred + kNewmarkGamma * a.dt * acc;
+  // The same with c_node[r], v_c[r] and a_c[r] loaded beforehand (they are not
+  // written by the kernels of the step that run before the correction).
+  __device__ void row_pre(int r, double acc, int node, double v_old, double a_old) const {
+    if (mode == 0) {
+      const double vpred = v_old + (1.0 - kNewmarkGamma) * dt * a_old;
+      U[node] = U[node] + kNewmarkBeta * dt * dt * acc;
+      v_c[r] = vpred + kNewmarkGamma * dt * acc;
+    }
+    a_c[r] = acc;
   }
-  a.a_c[r] = acc;
-}
+};
 
 // Per-CTA index list of a walk launch (ints, offsets relative to its start):
 //   [0] nq nodes, [1] nslot rows (sum of b), [2] nm ancestor rows (sum of m),
@@ -360,9 +370,9 @@ struct WalkList {
 // grid offset of local node m from the cell's first node).  Loads are issued
 // in batches of 16 before the products.
 constexpr int kMaxPd = 128;
-__device__ __forceinline__ double pair_product(const WalkArgs& a, const double* kp, int np, int k, int base,
-                                               const int* off) {
-  const double* u = a.SRC + base;
+__device__ __forceinline__ double pair_product(const WalkArgs& a, const double* src, const double* kp, int np,
+                                               int k, int base, const int* off) {
+  const double* u = src + base;
   double s0 = 0.0, s1 = 0.0;
   for (int m0 = 0; m0 < a.Pd; m0 += 16) {
     double kv[16], uv[16];
@@ -382,10 +392,18 @@ __device__ __forceinline__ double pair_product(const WalkArgs& a, const double* 
 }
 
 template <bool kForward, bool kSmem>
-__global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
   extern __shared__ __align__(16) double sm[];
   const int cta = a.cta0 + blockIdx.x;
   const int tid = threadIdx.x;
+  // Column of an independent-columns context (blockIdx.y).
+  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
+  const double* src = a.SRC + on;
+  const double* fxc = a.fxc + oc;
+  double* rhs0 = a.rhs0 + oc;
+  double* sol = a.sol + oc;
+  double* upd = a.upd + (int64_t)blockIdx.y * a.cs_upd;
+  const Corr cor{a.mode, a.c_node, a.U + on, a.v_c + oc, a.a_c + oc, a.dt};
   double* blob = sm;                                   // max_blob (smem mode)
   double* kp = blob + a.max_blob;                      // max_kp: rows of the cell matrices (first launch)
   double* vg = kp + a.max_kp;                          // max_slots: g (fwd) / y (bwd)
@@ -417,9 +435,9 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
       if (sl < nslot) {
         const int* nd = L.node + 8 * L.slot[4 * sl];
         const int r = nd[1] + (sl - nd[4]);
-        pre_node[q] = a.c_node[r];
-        pre_v[q] = a.v_c[r];
-        pre_a[q] = a.a_c[r];
+        pre_node[q] = cor.c_node[r];
+        pre_v[q] = cor.v_c[r];
+        pre_a[q] = cor.a_c[r];
       }
     }
   }
@@ -430,29 +448,29 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
       const int npair = il[4], nrhs = il[3];
       const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
       const int np = il[5];
-      for (int k = tid; k < npair; k += kThreads) pc[k] = pair_product(a, kp, np, k, L.pair[4 * k], s_off);
+      for (int k = tid; k < npair; k += kThreads) pc[k] = pair_product(a, src, kp, np, k, L.pair[4 * k], s_off);
       __syncthreads();
       for (int k = tid; k < nrhs; k += kThreads) {
         const int* rr = L.rhs + 4 * k;
-        double v = ft * a.fxc[rr[0]];
+        double v = ft * fxc[rr[0]];
         for (int q = rr[1]; q < rr[2]; ++q) v -= pc[q];
         if (rr[3] >= 0) vg[rr[3]] = v;
-        else a.rhs0[rr[0]] = v;
+        else rhs0[rr[0]] = v;
       }
       __syncthreads();
       for (int sl = tid; sl < nslot; sl += kThreads) {
         const int* st = L.slot + 4 * sl;
         double v = vg[sl];
-        for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(a.upd + il[k]);
+        for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(upd + il[k]);
         vg[sl] = v;
       }
     } else {
       for (int sl = tid; sl < nslot; sl += kThreads) {
         const int* st = L.slot + 4 * sl;
         const int* nd = L.node + 8 * st[0];
-        double v = __ldcg(a.rhs0 + nd[1] + (sl - nd[4]));
+        double v = __ldcg(rhs0 + nd[1] + (sl - nd[4]));
 #pragma unroll 4
-        for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(a.upd + il[k]);
+        for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(upd + il[k]);
         vg[sl] = v;
       }
     }
@@ -471,7 +489,7 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
       if (j <= i) y0 = fma(Li[i + ldi * j], vg[s0 + j], y0);
       const double y = y0 + y1;
       vy[sl] = y;
-      a.sol[nd[1] + i] = y;
+      sol[nd[1] + i] = y;
     }
     __syncthreads();
     // upd_t = L_{rows,t} y_t.
@@ -486,13 +504,13 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
         u1 = fma(L21[kk + ldr * (j + 1)], vy[s0 + j + 1], u1);
       }
       if (j < b) u0 = fma(L21[kk + ldr * j], vy[s0 + j], u0);
-      a.upd[nd[7] + kk] = u0 + u1;
+      upd[nd[7] + kk] = u0 + u1;
     }
   } else {
-    for (int k = tid; k < nm; k += kThreads) vm[k] = __ldcg(a.sol + L.anc[2 * k + 1]);
+    for (int k = tid; k < nm; k += kThreads) vm[k] = __ldcg(sol + L.anc[2 * k + 1]);
     for (int sl = tid; sl < nslot; sl += kThreads) {
       const int* nd = L.node + 8 * L.slot[4 * sl];
-      vg[sl] = __ldcg(a.sol + nd[1] + (sl - nd[4]));
+      vg[sl] = __ldcg(sol + nd[1] + (sl - nd[4]));
     }
     __syncthreads();
     // h = y_t - L_{rows,t}^T x_rows.
@@ -523,10 +541,10 @@ __global__ void __launch_bounds__(kThreads) k_walk(WalkArgs a) {
       }
       if (j < b) x0 = fma(Lc[j], vy[s0 + j], x0);
       const double x = x0 + x1;
-      a.sol[nd[1] + i] = x;
-      if (sl < tid + kThreads) correct_row_pre(a, nd[1] + i, x, pre_node[0], pre_v[0], pre_a[0]);
-      else if (sl < tid + 2 * kThreads) correct_row_pre(a, nd[1] + i, x, pre_node[1], pre_v[1], pre_a[1]);
-      else correct_row(a, nd[1] + i, x);
+      sol[nd[1] + i] = x;
+      if (sl < tid + kThreads) cor.row_pre(nd[1] + i, x, pre_node[0], pre_v[0], pre_a[0]);
+      else if (sl < tid + 2 * kThreads) cor.row_pre(nd[1] + i, x, pre_node[1], pre_v[1], pre_a[1]);
+      else cor.row(nd[1] + i, x);
     }
   }
 }
@@ -535,6 +553,12 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   extern __shared__ __align__(16) double tsm[];
   const int cta = blockIdx.x, tid = threadIdx.x;
   const int warp = tid / 32, lane = tid % 32;
+  // Column of an independent-columns context (blockIdx.y).
+  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
+  const double* rhs0 = a.rhs0 + oc;
+  double* sol = a.sol + oc;
+  const double* upd = a.upd + (int64_t)blockIdx.y * a.cs_upd;
+  const Corr cor{a.mode, a.c_node, a.U + on, a.v_c + oc, a.a_c + oc, a.dt};
   const int comp = a.cta_comp[cta], r0 = a.cta_r0[cta], r1 = a.cta_r1[cta];
   const int zn = a.zsize[comp], zb = a.zbase[comp], nr = r1 - r0;
   double* zs = tsm;                               // max_zn (even): right-hand side of the block
@@ -550,18 +574,18 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   double v_old = 0.0, a_old = 0.0;
   if (tid < nr) {
     row = a.zrow[zb + r0 + tid];
-    node = a.c_node[row];
-    v_old = a.v_c[row];
-    a_old = a.a_c[row];
+    node = cor.c_node[row];
+    v_old = cor.v_c[row];
+    a_old = cor.a_c[row];
   }
   async_copy_wait();
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
   // The whole right-hand side of this component's top block (redundant per CTA).
   for (int i = tid; i < zn; i += kThreads) {
     const int fb = il[2 * i], fe = il[2 * i + 1];
-    double v = __ldcg(a.rhs0 + a.zrow[zb + i]);
+    double v = __ldcg(rhs0 + a.zrow[zb + i]);
 #pragma unroll 4
-    for (int k = fb; k < fe; ++k) v -= __ldcg(a.upd + il[k]);
+    for (int k = fb; k < fe; ++k) v -= __ldcg(upd + il[k]);
     zs[i] = v;
   }
   __syncthreads();
@@ -584,8 +608,8 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   __syncthreads();
   if (tid < nr) {
     const double x = xs[tid];
-    a.sol[row] = x;
-    correct_row_pre(a, row, x, node, v_old, a_old);
+    sol[row] = x;
+    cor.row_pre(row, x, node, v_old, a_old);
   }
 }
 
@@ -692,6 +716,7 @@ struct imex_ctx {
   int64_t* rec_nodes = nullptr;
   int io_cap = 4096;
   // state
+  int ncols = 1;            // independent source columns (fields column after column)
   int cur = 0;              // U[cur] holds u_n
   int64_t step = 0;
   cudaStream_t stream = nullptr;
@@ -731,7 +756,7 @@ template <int P>
 void launch_explicit(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t s) {
   constexpr int TCs[10] = {0, 0, 16, 16, 10, 8, 6, 5, 4, 4};
   constexpr int TC = TCs[P];
-  k_explicit2d<P, TC><<<grid, kThreads, c->smem_explicit, s>>>(ea, c->ops);
+  k_explicit2d<P, TC><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
 }
 
 void explicit_dispatch(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t s) {
@@ -814,6 +839,8 @@ ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double
   ea.v_c = c->v_c;
   ea.a_c = c->a_c;
   ea.dt = hs.dt;
+  ea.cs_node = hs.nnodes;
+  ea.cs_c = hs.n_c;
   return ea;
 }
 
@@ -878,6 +905,9 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   w.v_c = c->v_c;
   w.a_c = c->a_c;
   w.dt = hs.dt;
+  w.cs_node = hs.nnodes;
+  w.cs_c = hs.n_c;
+  w.cs_upd = std::max<int64_t>(hs.upd_size, 1);
   TopArgs z{};
   z.cta_comp = c->top_comp;
   z.cta_r0 = c->top_r0;
@@ -902,6 +932,9 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   z.v_c = c->v_c;
   z.a_c = c->a_c;
   z.dt = hs.dt;
+  z.cs_node = w.cs_node;
+  z.cs_c = w.cs_c;
+  z.cs_upd = w.cs_upd;
 
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -915,7 +948,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   auto walk = [&](int l, bool fwd) {
     w.cta0 = c->lev_cta0[l];
     w.first = (fwd && l == 0) ? 1 : 0;
-    cfg.gridDim = dim3(c->lev_ncta[l]);
+    cfg.gridDim = dim3(c->lev_ncta[l], c->ncols);
     cfg.dynamicSmemBytes = c->smem_walk;
     if (c->walk_smem_mode)
       return fwd ? cudaLaunchKernelEx(&cfg, k_walk<true, true>, w) : cudaLaunchKernelEx(&cfg, k_walk<false, true>, w);
@@ -924,7 +957,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   cudaError_t e = cudaSuccess;
   for (int l = 0; l < nlev && e == cudaSuccess; ++l) e = walk(l, true);
   if (e == cudaSuccess && c->ntop > 0) {
-    cfg.gridDim = dim3(c->ntop);
+    cfg.gridDim = dim3(c->ntop, c->ncols);
     cfg.dynamicSmemBytes = c->smem_top;
     e = cudaLaunchKernelEx(&cfg, k_top, z);
   }
@@ -960,7 +993,9 @@ int compute_initial(imex_ctx* c, cudaStream_t s) {
   if (int rc = check_launch("explicit (initial)")) return rc;
   if (hs.n_c > 0) {
     const int nc = (int)hs.n_c;
-    k_gather_c<<<(nc + 255) / 256, 256, 0, s>>>(c->v_c, c->tmp, c->c_node, nc);
+    for (int col = 0; col < c->ncols; ++col)
+      k_gather_c<<<(nc + 255) / 256, 256, 0, s>>>(c->v_c + (size_t)col * nc, c->tmp + (size_t)col * hs.nnodes,
+                                                  c->c_node, nc);
     if (cudaError_t e = launch_solve_chain(c, false, ft0, nullptr, 1, U0, U0, c->upd, c->sol, c->rhs0, s))
       return fail(IMEX_ERR_CUDA, std::string("solve (initial): ") + cudaGetErrorString(e));
     if (int rc = check_launch("solve (initial)")) return rc;
@@ -1629,14 +1664,23 @@ int imex_host_setup_export(const imex_mesh* mesh, int p, double alpha, double dt
 
 int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src,
                const imex_alloc* alloc, imex_ctx** out) {
+  return imex_setup_batch(mesh, p, alpha, dt, src, 1, alloc, out);
+}
+
+int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src, int ncols,
+                     const imex_alloc* alloc, imex_ctx** out) {
   if (!out) return fail(IMEX_ERR_ARG, "out must not be NULL");
   *out = nullptr;
   imex_ctx* c = nullptr;
   try {
     Problem pb;
     if (int rc = build_context(mesh, p, alpha, dt, src, pb)) return rc;
+    if (ncols < 1 || ncols > kMaxCols) return fail(IMEX_ERR_ARG, "ncols must be in [1, 256]");
+    if (ncols > 1 && ncols != pb.nsrc) return fail(IMEX_ERR_ARG, "ncols > 1 needs one source per column");
+    pb.ncols = ncols;
     if (pb.dim != 2) return fail(IMEX_ERR_ARG, "the GPU time stepper supports dim = 2");
     c = new imex_ctx();
+    c->ncols = ncols;
     std::string err = build_setup(pb, c->hs);
     if (!err.empty()) {
       delete c;
@@ -1689,8 +1733,10 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
 
     // Compact per-c arrays and tree metadata.
     const int64_t nn = hs.nnodes, nc = hs.n_c, nt = (int64_t)hs.tree.size();
-    std::vector<double> fxc(nc);
-    for (int64_t r = 0; r < nc; ++r) fxc[r] = hs.fx[hs.c_node[r]];
+    const int ncols = c->ncols;
+    std::vector<double> fxc((size_t)nc * ncols);
+    for (int col = 0; col < ncols; ++col)
+      for (int64_t r = 0; r < nc; ++r) fxc[(size_t)col * nc + r] = hs.fx[(size_t)col * nn + hs.c_node[r]];
     (void)nt;
     SolvePlan plan;
     if (int rc = plan_solve(c, plan)) {
@@ -1727,20 +1773,20 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     const size_t nblobcta = std::max<size_t>(plan.blob_off.size(), 1);
 
     Arena ar;
-    ar.add(&c->U[0], nn);
-    ar.add(&c->U[1], nn);
-    ar.add(&c->tmp, nn);
-    ar.add(&c->fx, nn);
+    ar.add(&c->U[0], nn * ncols);
+    ar.add(&c->U[1], nn * ncols);
+    ar.add(&c->tmp, nn * ncols);
+    ar.add(&c->fx, nn * ncols);
     ar.add(&c->winv_x, hs.nn[0]);
     ar.add(&c->winv_y, hs.nn[1]);
     ar.add(&c->cls, nn);
     ar.add(&c->c_node, std::max<int64_t>(nc, 1));
-    ar.add(&c->v_c, std::max<int64_t>(nc, 1));
-    ar.add(&c->a_c, std::max<int64_t>(nc, 1));
-    ar.add(&c->fxc, std::max<int64_t>(nc, 1));
-    ar.add(&c->sol, std::max<int64_t>(nc, 1));
-    ar.add(&c->rhs0, std::max<int64_t>(nc, 1));
-    ar.add(&c->upd, std::max<int64_t>(hs.upd_size, 1));
+    ar.add(&c->v_c, std::max<int64_t>(nc, 1) * ncols);
+    ar.add(&c->a_c, std::max<int64_t>(nc, 1) * ncols);
+    ar.add(&c->fxc, std::max<int64_t>(nc, 1) * ncols);
+    ar.add(&c->sol, std::max<int64_t>(nc, 1) * ncols);
+    ar.add(&c->rhs0, std::max<int64_t>(nc, 1) * ncols);
+    ar.add(&c->upd, std::max<int64_t>(hs.upd_size, 1) * ncols);
     ar.add(&c->Kpair, std::max<size_t>(plan.Kpair.size(), 2));
     ar.add(&c->kp_off, nblobcta);
     ar.add(&c->kp_len, nblobcta);
@@ -1764,7 +1810,7 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->zA_S, std::max<size_t>(plan.zA_S.size(), 1));
     ar.add(&c->zA_M, std::max<size_t>(plan.zA_M.size(), 1));
     ar.add(&c->ft_buf, 2);
-    ar.add(&c->rec_buf, c->io_cap);
+    ar.add(&c->rec_buf, (size_t)c->io_cap * ncols);
     ar.add(&c->rec_nodes, c->io_cap);
     c->bytes = ar.total();
     void* basep = nullptr;
@@ -1931,8 +1977,11 @@ int imex_step_io(imex_ctx* c, int64_t n, const double* ft_samples, const int64_t
     }
     if (int rc = step_once(c, s, nullptr, ftd)) return rc;
     if (nrec > 0) {
-      k_gather_nodes<<<(nrec + 255) / 256, 256, 0, s>>>(c->rec_buf, c->U[c->cur], c->rec_nodes, nrec);
-      e = cudaMemcpyAsync(traces + k * nrec, c->rec_buf, nrec * sizeof(double), cudaMemcpyDeviceToHost, s);
+      for (int col = 0; col < c->ncols; ++col)
+        k_gather_nodes<<<(nrec + 255) / 256, 256, 0, s>>>(c->rec_buf + (size_t)col * nrec,
+                                                          c->U[c->cur] + (size_t)col * c->hs.nnodes, c->rec_nodes, nrec);
+      e = cudaMemcpyAsync(traces + k * nrec * c->ncols, c->rec_buf, (size_t)nrec * c->ncols * sizeof(double),
+                          cudaMemcpyDeviceToHost, s);
     }
     // ft_buf is rewritten by the next step's copy, which the stream orders
     // after this step's kernels.
@@ -1944,7 +1993,7 @@ int imex_step_io(imex_ctx* c, int64_t n, const double* ft_samples, const int64_t
 
 static int field_io_check(imex_ctx* c, int64_t len) {
   if (!c) return fail(IMEX_ERR_ARG, "NULL context");
-  if (len != c->hs.nnodes) return fail(IMEX_ERR_ARG, "len must equal n_nodes");
+  if (len != c->hs.nnodes * c->ncols) return fail(IMEX_ERR_ARG, "len must equal ncols * n_nodes");
   return IMEX_OK;
 }
 
@@ -1955,24 +2004,27 @@ int imex_fields(imex_ctx* c, int which, double* dst, int64_t len, int dst_on_dev
   const int64_t n = c->hs.nnodes;
   const int nb = (int)((n + 255) / 256);
   const int nc = (int)c->hs.n_c;
-  double* out = c->tmp;
-  switch (which) {
-    case IMEX_FIELD_U: k_masked<<<nb, 256, 0, s>>>(out, c->U[c->cur], c->cls, n, 3); break;
-    case IMEX_FIELD_U_PREV_D: k_masked<<<nb, 256, 0, s>>>(out, c->U[1 - c->cur], c->cls, n, 1); break;
-    case IMEX_FIELD_V_C:
-    case IMEX_FIELD_A_C:
-      cudaMemsetAsync(out, 0, n * sizeof(double), s);
-      if (nc > 0)
-        k_scatter_c<<<(nc + 255) / 256, 256, 0, s>>>(out, which == IMEX_FIELD_V_C ? c->v_c : c->a_c,
-                                                     c->c_node, nc);
-      break;
-    case IMEX_FIELD_FX: k_masked<<<nb, 256, 0, s>>>(out, c->fx, c->cls, n, 3); break;
-    case IMEX_FIELD_MASK_D: k_masked<<<nb, 256, 0, s>>>(out, c->fx, c->cls, n, 4); break;
-    case IMEX_FIELD_MASK_C: k_masked<<<nb, 256, 0, s>>>(out, c->fx, c->cls, n, 5); break;
-    default: return fail(IMEX_ERR_ARG, "unknown field");
+  for (int col = 0; col < c->ncols; ++col) {
+    const int64_t on = (int64_t)col * n, oc = (int64_t)col * nc;
+    double* out = c->tmp + on;
+    switch (which) {
+      case IMEX_FIELD_U: k_masked<<<nb, 256, 0, s>>>(out, c->U[c->cur] + on, c->cls, n, 3); break;
+      case IMEX_FIELD_U_PREV_D: k_masked<<<nb, 256, 0, s>>>(out, c->U[1 - c->cur] + on, c->cls, n, 1); break;
+      case IMEX_FIELD_V_C:
+      case IMEX_FIELD_A_C:
+        cudaMemsetAsync(out, 0, n * sizeof(double), s);
+        if (nc > 0)
+          k_scatter_c<<<(nc + 255) / 256, 256, 0, s>>>(out, (which == IMEX_FIELD_V_C ? c->v_c : c->a_c) + oc,
+                                                       c->c_node, nc);
+        break;
+      case IMEX_FIELD_FX: k_masked<<<nb, 256, 0, s>>>(out, c->fx + on, c->cls, n, 3); break;
+      case IMEX_FIELD_MASK_D: k_masked<<<nb, 256, 0, s>>>(out, c->fx, c->cls, n, 4); break;
+      case IMEX_FIELD_MASK_C: k_masked<<<nb, 256, 0, s>>>(out, c->fx, c->cls, n, 5); break;
+      default: return fail(IMEX_ERR_ARG, "unknown field");
+    }
   }
   if (int rc = check_launch("imex_fields")) return rc;
-  cudaError_t e = cudaMemcpyAsync(dst, out, n * sizeof(double),
+  cudaError_t e = cudaMemcpyAsync(dst, c->tmp, len * sizeof(double),
                                   dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_fields: ") + cudaGetErrorString(e));
@@ -1986,22 +2038,26 @@ int imex_set_fields(imex_ctx* c, int which, const double* src, int64_t len, int 
   const int64_t n = c->hs.nnodes;
   const int nb = (int)((n + 255) / 256);
   const int nc = (int)c->hs.n_c;
-  cudaError_t e = cudaMemcpyAsync(c->tmp, src, n * sizeof(double),
+  cudaError_t e = cudaMemcpyAsync(c->tmp, src, len * sizeof(double),
                                   src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_set_fields: ") + cudaGetErrorString(e));
-  switch (which) {
-    case IMEX_FIELD_U:
-      k_masked_set<<<nb, 256, 0, s>>>(c->U[c->cur], c->tmp, c->cls, n, NODE_D);
-      k_masked_set<<<nb, 256, 0, s>>>(c->U[c->cur], c->tmp, c->cls, n, NODE_C);
-      break;
-    case IMEX_FIELD_U_PREV_D: k_masked_set<<<nb, 256, 0, s>>>(c->U[1 - c->cur], c->tmp, c->cls, n, NODE_D); break;
-    case IMEX_FIELD_V_C:
-    case IMEX_FIELD_A_C:
-      if (nc > 0)
-        k_gather_c<<<(nc + 255) / 256, 256, 0, s>>>(which == IMEX_FIELD_V_C ? c->v_c : c->a_c, c->tmp,
-                                                    c->c_node, nc);
-      break;
-    default: return fail(IMEX_ERR_ARG, "field is not settable");
+  for (int col = 0; col < c->ncols; ++col) {
+    const int64_t on = (int64_t)col * n, oc = (int64_t)col * nc;
+    const double* in = c->tmp + on;
+    switch (which) {
+      case IMEX_FIELD_U:
+        k_masked_set<<<nb, 256, 0, s>>>(c->U[c->cur] + on, in, c->cls, n, NODE_D);
+        k_masked_set<<<nb, 256, 0, s>>>(c->U[c->cur] + on, in, c->cls, n, NODE_C);
+        break;
+      case IMEX_FIELD_U_PREV_D: k_masked_set<<<nb, 256, 0, s>>>(c->U[1 - c->cur] + on, in, c->cls, n, NODE_D); break;
+      case IMEX_FIELD_V_C:
+      case IMEX_FIELD_A_C:
+        if (nc > 0)
+          k_gather_c<<<(nc + 255) / 256, 256, 0, s>>>((which == IMEX_FIELD_V_C ? c->v_c : c->a_c) + oc, in,
+                                                      c->c_node, nc);
+        break;
+      default: return fail(IMEX_ERR_ARG, "field is not settable");
+    }
   }
   if (int rc = check_launch("imex_set_fields")) return rc;
   e = cudaStreamSynchronize(s);
@@ -2022,12 +2078,13 @@ int imex_set_initial(imex_ctx* c, const double* u0, const double* v0, int64_t le
   const int64_t n = c->hs.nnodes;
   const int nb = (int)((n + 255) / 256);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  cudaError_t e = cudaMemcpyAsync(c->tmp, u0, n * sizeof(double), kind, s);
+  cudaError_t e = cudaMemcpyAsync(c->tmp, u0, len * sizeof(double), kind, s);
   if (e == cudaSuccess) {
     c->cur = 0;
-    k_masked<<<nb, 256, 0, s>>>(c->U[0], c->tmp, c->cls, n, 3);
-    e = v0 ? cudaMemcpyAsync(c->tmp, v0, n * sizeof(double), kind, s)
-           : cudaMemsetAsync(c->tmp, 0, n * sizeof(double), s);
+    for (int col = 0; col < c->ncols; ++col)
+      k_masked<<<nb, 256, 0, s>>>(c->U[0] + (size_t)col * n, c->tmp + (size_t)col * n, c->cls, n, 3);
+    e = v0 ? cudaMemcpyAsync(c->tmp, v0, len * sizeof(double), kind, s)
+           : cudaMemsetAsync(c->tmp, 0, len * sizeof(double), s);
   }
   if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_set_initial: ") + cudaGetErrorString(e));
   c->step = 0;
@@ -2048,6 +2105,7 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   st->solve_smem_bytes = (int64_t)c->smem_walk;
   st->launches_per_step = launches_per_step(c);
   st->rhs_pairs = (int64_t)c->hs.contrib_pos.size();
+  st->ncols = c->ncols;
   st->device_bytes = (int64_t)c->bytes;
   return IMEX_OK;
 }
@@ -2086,8 +2144,8 @@ extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
   if (!c || n < 0) return fail(IMEX_ERR_ARG, "bad arguments");
   const HostSetup& hs = c->hs;
   auto even = [](int64_t v) { return v + (v & 1); };
-  const int64_t n_upd = even(std::max<int64_t>(hs.upd_size, 1));
-  const int64_t n_sol = even(std::max<int64_t>(hs.n_c, 1));
+  const int64_t n_upd = even(std::max<int64_t>(hs.upd_size, 1)) * c->ncols;
+  const int64_t n_sol = even(std::max<int64_t>(hs.n_c, 1)) * c->ncols;
   if (n_upd + 2 * n_sol > kStaticScratchDoubles)
     return fail(IMEX_ERR_ARG, "imex_step_noalloc: the implicit solve needs " + std::to_string(n_upd + 2 * n_sol) +
                                   " doubles of scratch; the static scratch holds " +

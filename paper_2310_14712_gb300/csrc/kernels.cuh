@@ -75,6 +75,8 @@ struct ExplicitArgs {
   const double* v_c;
   const double* a_c;
   double dt;
+  // independent columns (blockIdx.y): strides of full-grid and I_c fields
+  int64_t cs_node, cs_c;
 };
 
 // One level of the supernodal walk of A5 (forward or backward), all
@@ -113,6 +115,8 @@ struct WalkArgs {
   double* v_c;
   double* a_c;
   double dt;
+  // independent columns (blockIdx.y): strides of full-grid, I_c and update fields
+  int64_t cs_node, cs_c, cs_upd;
 };
 
 // Dense top block of every component: x_Z = A_Z (rhs_Z - updates from the
@@ -141,6 +145,7 @@ struct TopArgs {
   double* v_c;
   double* a_c;
   double dt;
+  int64_t cs_node, cs_c, cs_upd;  // independent columns (blockIdx.y)
 };
 
 }  // namespace imex

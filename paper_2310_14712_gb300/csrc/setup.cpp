@@ -284,9 +284,11 @@ void spacetree(const Grid& g, const Geometry& geo, const double* clo, int depth,
   visit(rlo, rhi, 0);
 }
 
-double source_value(const Problem& pb, const double* x) {
+// f_x at x: the sum of all bells, or (independent columns) bell `col` alone.
+double source_value(const Problem& pb, const double* x, int col) {
   double s = 0.0;
-  for (int k = 0; k < pb.nsrc; ++k) {
+  const int k0 = pb.ncols > 1 ? col : 0, k1 = pb.ncols > 1 ? col + 1 : pb.nsrc;
+  for (int k = k0; k < k1; ++k) {
     double r2 = 0.0;
     for (int d = 0; d < pb.dim; ++d) {
       double t = x[d] - pb.src_pos[k * pb.dim + d];
@@ -568,6 +570,9 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
   if (!(pb.alpha > 0.0) || pb.alpha > 1.0) return "alpha must be in (0, 1]";
   if (!(pb.rho > 0.0) || !(pb.c0 > 0.0)) return "rho and c0 must be positive";
   if (pb.nsrc < 1 || (int)pb.src_pos.size() != pb.nsrc * pb.dim) return "bad source positions";
+  if (pb.ncols < 1 || pb.ncols > kMaxCols || (pb.ncols > 1 && pb.ncols != pb.nsrc))
+    return "independent columns need one source per column (1 <= columns <= 256)";
+  const int ncols = pb.ncols;
   if (!(pb.sigma > 0.0)) return "source width must be positive";
   if (pb.holes.size() % (2 * pb.dim) != 0) return "holes array must be nholes x 2*dim";
   for (size_t k = 0; k < pb.holes.size() / (2 * pb.dim); ++k)
@@ -662,7 +667,7 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
   // Cut-cell element matrices by spacetree quadrature (threads over cells).
   const int64_t ncut0 = (int64_t)cut_cells.size();
   std::vector<double> cutK_all((size_t)ncut0 * Pd * Pd), cutM_all((size_t)ncut0 * Pd * Pd),
-      cutF_all((size_t)ncut0 * Pd);
+      cutF_all((size_t)ncut0 * Pd * ncols);
   std::vector<double> cut_fill(ncut0);
   parallel_for(ncut0, [&](int64_t b, int64_t e) {
     std::vector<QPoint> pts;
@@ -678,7 +683,7 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
       double wphys = 0.0, wall = 0.0;
       double* Ke = cutK_all.data() + (size_t)k * Pd * Pd;
       double* Me = cutM_all.data() + (size_t)k * Pd * Pd;
-      double* fe = cutF_all.data() + (size_t)k * Pd;
+      double* fe = cutF_all.data() + (size_t)k * Pd * ncols;
       const double c = cell_speed(cid);
       for (const QPoint& q : pts) {
         wall += q.w;
@@ -688,7 +693,8 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
         tensor_basis(g, L1, q.xr, N.data(), G.data());
         double xp[3];
         for (int d = 0; d < dim; ++d) xp[d] = clo[d] + (q.xr[d] + 1.0) * 0.5 * g.h[d];
-        const double fv = source_value(pb, xp);
+        double fv[kMaxCols];
+        for (int col = 0; col < ncols; ++col) fv[col] = source_value(pb, xp, col);
         const double kw = wq * pb.rho * c * c, mw = wq * pb.rho;
         for (int bcol = 0; bcol < Pd; ++bcol) {
           double gb[3];
@@ -700,7 +706,7 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
             Ke[a + (size_t)Pd * bcol] += s;
             Me[a + (size_t)Pd * bcol] += N[a] * nb;
           }
-          fe[bcol] += wq * fv * N[bcol];
+          for (int col = 0; col < ncols; ++col) fe[(size_t)col * Pd + bcol] += wq * fv[col] * N[bcol];
         }
       }
       cut_fill[k] = wphys / wall;
@@ -772,9 +778,9 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
   }
 
   // Source vector f_x on the full grid: uncut cells by tensor GL, cut cells by spacetree.
-  hs.fx.assign(nnode, 0.0);
+  hs.fx.assign((size_t)nnode * ncols, 0.0);
   {
-    std::vector<double> fe_uncut((size_t)ncell * Pd, 0.0);
+    std::vector<double> fe_uncut((size_t)ncell * Pd * ncols, 0.0);
     std::vector<double> Nt((size_t)Pd * Pd, 0.0), Wt(Pd, 0.0);
     std::vector<double> Xr((size_t)Pd * 3, 0.0);
     for (int q = 0; q < Pd; ++q) {
@@ -793,17 +799,23 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
         for (int q = 0; q < Pd; ++q) {
           double xp[3];
           for (int d = 0; d < dim; ++d) xp[d] = g.lo[d] + ci[d] * g.h[d] + (Xr[q * 3 + d] + 1.0) * 0.5 * g.h[d];
-          double fv = source_value(pb, xp) * Wt[q] * jac;
-          for (int a = 0; a < Pd; ++a) fe_uncut[(size_t)cid * Pd + a] += fv * Nt[(size_t)q * Pd + a];
+          for (int col = 0; col < ncols; ++col) {
+            double fv = source_value(pb, xp, col) * Wt[q] * jac;
+            double* fe = fe_uncut.data() + ((size_t)cid * ncols + col) * Pd;
+            for (int a = 0; a < Pd; ++a) fe[a] += fv * Nt[(size_t)q * Pd + a];
+          }
         }
       }
     });
     for (int64_t cid = 0; cid < ncell; ++cid) {
       if (hs.cell_type[cid] == CELL_EMPTY) continue;
       g.cell_nodes(cid, cn.data());
-      const double* fe = (hs.cell_type[cid] == CELL_CUT) ? cutF_all.data() + (size_t)cut_slot[cid] * Pd
-                                                         : fe_uncut.data() + (size_t)cid * Pd;
-      for (int l = 0; l < Pd; ++l) hs.fx[cn[l]] += fe[l];
+      for (int col = 0; col < ncols; ++col) {
+        const double* fe = (hs.cell_type[cid] == CELL_CUT)
+                               ? cutF_all.data() + ((size_t)cut_slot[cid] * ncols + col) * Pd
+                               : fe_uncut.data() + ((size_t)cid * ncols + col) * Pd;
+        for (int l = 0; l < Pd; ++l) hs.fx[(size_t)col * nnode + cn[l]] += fe[l];
+      }
     }
   }
 

@@ -17,6 +17,8 @@ namespace imex {
 enum CellType : int8_t { CELL_UNCUT = 0, CELL_CUT = 1, CELL_EMPTY = 2 };
 enum NodeClass : uint8_t { NODE_INACTIVE = 0, NODE_D = 1, NODE_C = 2 };
 
+constexpr int kMaxCols = 256;   // independent source columns of one context
+
 struct Problem {
   int dim = 2;
   double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
@@ -29,6 +31,7 @@ struct Problem {
   std::vector<double> cell_c;  // optional per-cell wave speed, flat cell order (x fastest)
   int nsrc = 1;
   std::vector<double> src_pos; // nsrc x dim
+  int ncols = 1;               // > 1: independent columns, column k loaded by source k alone
   double f0 = 1.0, sigma = 0.1, amp = 10.0;
   int wavelet = 0;
   double dt = 0.0;             // <= 0: dt_factor * uncut critical step
@@ -72,7 +75,7 @@ struct HostSetup {
   int64_t n_d = 0, n_c = 0, n_cut = 0, n_uncut = 0, n_empty = 0;
   std::vector<int> c_node;     // c-index -> grid node
   std::vector<int> node_c;     // grid node -> c-index or -1
-  std::vector<double> fx;      // full grid, canonical order
+  std::vector<double> fx;      // full grid, canonical order; ncols grids, column after column
 
   // 1D operators on [-1,1] (exact Gauss-Legendre integrals of the GLL basis).
   std::vector<double> gll_x, gll_w, K1, M1;   // K1, M1 are P x P row-major

@@ -58,7 +58,7 @@ class Stats(ctypes.Structure):
         "n_components", "n_tree", "max_block", "step", "device_bytes")] + \
         [(n, ctypes.c_double) for n in ("dt", "dt_crit_uncut", "setup_seconds", "residual_S", "residual_M")] + \
         [(n, ctypes.c_int64) for n in ("solve_levels", "solve_ctas", "solve_smem_bytes", "launches_per_step",
-                                    "rhs_pairs")]
+                                    "rhs_pairs", "ncols")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -67,6 +67,9 @@ class Stats(ctypes.Structure):
 _vp = ctypes.c_void_p
 _lib.imex_setup.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                             ctypes.POINTER(Source), ctypes.POINTER(Alloc), ctypes.POINTER(_vp)]
+_lib.imex_setup_batch.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.POINTER(Source), ctypes.c_int, ctypes.POINTER(Alloc),
+                                  ctypes.POINTER(_vp)]
 _lib.imex_step.argtypes = [_vp, ctypes.c_int64, _vp]
 _lib.imex_step_profile.argtypes = [_vp, ctypes.c_int64, _vp, _dp]
 _lib.imex_step_io.argtypes = [_vp, ctypes.c_int64, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
@@ -87,7 +90,7 @@ _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctyp
                                         ctypes.POINTER(Stats)]
 
 # Every symbol include/imex.h declares (checked by the CPU tests).
-EXPORTS = ("imex_setup", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
+EXPORTS = ("imex_setup", "imex_setup_batch", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
            "imex_set_initial", "imex_info", "imex_last_error", "imex_destroy", "imex_gll_points",
            "imex_gauss_points", "imex_host_setup_export")
 
@@ -195,12 +198,15 @@ class Imex:
     """One immersed Newmark IMEX problem on the current CUDA device.
 
     Construct from a workload (paper_2310_14712_gb300.workloads.Workload) or
-    from explicit arguments.  Device memory comes from PyTorch.
+    from explicit arguments.  Device memory comes from PyTorch.  With
+    ncols > 1 the context steps ncols independent simulations, column k
+    loaded by the source at src_pos[k] alone (imex_setup_batch); fields then
+    have ncols * n_nodes entries, column after column.
     """
 
     def __init__(self, dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0, src_sigma,
                  src_amp=10.0, wavelet=0, rho=1.0, c0=1.0, cell_c=None, dt=0.0, use_torch_alloc=True,
-                 **_):
+                 ncols=1, **_):
         import torch
         self.torch = torch
         if not torch.cuda.is_available():
@@ -211,11 +217,13 @@ class Imex:
         self._allocator = _TorchAllocator(self.device) if use_torch_alloc else None
         ctx = _vp()
         al = ctypes.byref(self._allocator.struct) if self._allocator else None
-        _check(_lib.imex_setup(ctypes.byref(m), p, alpha, dt, ctypes.byref(s), al, ctypes.byref(ctx)),
-               "imex_setup")
+        _check(_lib.imex_setup_batch(ctypes.byref(m), p, alpha, dt, ctypes.byref(s), int(ncols), al,
+                                     ctypes.byref(ctx)), "imex_setup_batch")
         self._ctx = ctx
         self.stats = self.info()
         self.n_nodes = self.stats["n_nodes"]
+        self.ncols = int(ncols)
+        self.field_len = self.n_nodes * self.ncols
         self.dim = dim
         self.shape = tuple(reversed([ncells[k] * p + 1 for k in range(dim)]))
 
@@ -249,9 +257,9 @@ class Imex:
 
     def step_io(self, n, ft_samples, rec_nodes, traces, stream=None):
         """n steps with host I/O every step: ft_samples (n+1 host doubles, or None for
-        the built-in wavelet), receivers rec_nodes (int64 node ids); traces (n x nrec
-        host doubles) receives u at the receivers after every step.  Host arrays may be
-        pinned torch CPU tensors or NumPy arrays."""
+        the built-in wavelet), receivers rec_nodes (int64 node ids); traces (n x ncols x
+        nrec host doubles) receives u at the receivers after every step.  Host arrays may
+        be pinned torch CPU tensors or NumPy arrays."""
         def ptr(a, ct):
             if a is None:
                 return None
@@ -264,28 +272,31 @@ class Imex:
                                  self._stream(stream)), "imex_step_io")
 
     def fields(self, which="u", out=None):
-        """Copy a field (canonical layout) into `out` (torch CUDA tensor or NumPy array)."""
+        """Copy a field (canonical layout; ncols grids one after the other) into `out`
+        (torch CUDA tensor or NumPy array)."""
         code = FIELDS[which] if isinstance(which, str) else int(which)
+        n = self.field_len
         if out is None:
-            out = self.torch.empty(self.n_nodes, dtype=self.torch.float64, device=self.device)
+            out = self.torch.empty(n, dtype=self.torch.float64, device=self.device)
         if isinstance(out, np.ndarray):
-            assert out.dtype == np.float64 and out.size == self.n_nodes and out.flags.c_contiguous
-            _check(_lib.imex_fields(self._ctx, code, out.ctypes.data, self.n_nodes, 0), "imex_fields")
+            assert out.dtype == np.float64 and out.size == n and out.flags.c_contiguous
+            _check(_lib.imex_fields(self._ctx, code, out.ctypes.data, n, 0), "imex_fields")
         else:
-            assert out.dtype == self.torch.float64 and out.numel() == self.n_nodes and out.is_contiguous()
-            _check(_lib.imex_fields(self._ctx, code, out.data_ptr(), self.n_nodes, 1 if out.is_cuda else 0),
+            assert out.dtype == self.torch.float64 and out.numel() == n and out.is_contiguous()
+            _check(_lib.imex_fields(self._ctx, code, out.data_ptr(), n, 1 if out.is_cuda else 0),
                    "imex_fields")
         return out
 
     def set_fields(self, which, src):
         code = FIELDS[which] if isinstance(which, str) else int(which)
+        n = self.field_len
         if isinstance(src, np.ndarray):
             src = _f64(src)
-            _check(_lib.imex_set_fields(self._ctx, code, src.ctypes.data, self.n_nodes, 0), "imex_set_fields")
+            _check(_lib.imex_set_fields(self._ctx, code, src.ctypes.data, n, 0), "imex_set_fields")
         else:
             src = src.contiguous()
-            _check(_lib.imex_set_fields(self._ctx, code, src.data_ptr(), self.n_nodes,
-                                        1 if src.is_cuda else 0), "imex_set_fields")
+            _check(_lib.imex_set_fields(self._ctx, code, src.data_ptr(), n, 1 if src.is_cuda else 0),
+                   "imex_set_fields")
 
     def set_step(self, n):
         _check(_lib.imex_set_step(self._ctx, int(n)), "imex_set_step")
@@ -296,7 +307,7 @@ class Imex:
         if v0 is not None:
             v0 = _f64(v0)
             v0p = v0.ctypes.data
-        _check(_lib.imex_set_initial(self._ctx, u0.ctypes.data, v0p, self.n_nodes, 0), "imex_set_initial")
+        _check(_lib.imex_set_initial(self._ctx, u0.ctypes.data, v0p, self.field_len, 0), "imex_set_initial")
 
     def info(self):
         st = Stats()
