@@ -4,12 +4,12 @@
 // Wave Equation", Sec. "Time integration", Fig. TrapCDMIMEX (Newmark IMEX),
 // Eqs. CDMstep / CDMacc (diagonal CDM step), Eqs. Newmark1/2 (prediction and
 // correction, beta = 1/4, gamma = 1/2), Eqs. Kd / Kc (partitioned stiffness).
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -111,10 +111,24 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
   for (int it = tid; it < RY * NC; it += kThreads) {
     const int cc = it / RY, yy = it - cc * RY;
     const int cx = cx0 + cc;
+    if (cx < 0 || cx >= a.ncx) {   // a cell outside the grid contributes nothing
+      if (cc >= 1) {
+#pragma unroll
+        for (int i = 1; i < p; ++i) {
+          t1[yy * OX + (cc - 1) * p + i] = 0.0;
+          t2[yy * OX + (cc - 1) * p + i] = 0.0;
+        }
+      }
+      tl1[yy * NC + cc] = 0.0;
+      tr1[yy * NC + cc] = 0.0;
+      tl2[yy * NC + cc] = 0.0;
+      tr2[yy * NC + cc] = 0.0;
+      continue;
+    }
     double v[P], o1[P], o2[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) v[j] = su[yy * RX + cc * p + j];
-    const bool valid = (cx >= 0 && cx < a.ncx);
+    constexpr bool valid = true;
     // Even and odd parts of v under x -> -x.
     double e[H], o[H];
 #pragma unroll
@@ -170,13 +184,22 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
   for (int it = tid; it < OX * NC; it += kThreads) {
     const int cr = it / OX, xo = it - cr * OX;
     const int cy = cy0 + cr;
+    if (cy < 0 || cy >= a.ncy) {   // a cell outside the grid contributes nothing
+      if (cr >= 1) {
+#pragma unroll
+        for (int i = 1; i < p; ++i) rr[((cr - 1) * p + i) * OX + xo] = 0.0;
+      }
+      rb[cr * OX + xo] = 0.0;
+      rt[cr * OX + xo] = 0.0;
+      continue;
+    }
     double va[P], vb[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
       va[j] = t1[(cr * p + j) * OX + xo];
       vb[j] = t2[(cr * p + j) * OX + xo];
     }
-    const bool valid = (cy >= 0 && cy < a.ncy);
+    constexpr bool valid = true;
     // o = M1 va + (sy K1) vb, the mass in rank-one form, the stiffness even-odd.
     double sa = kOdd ? ops.a[H] * va[H] : 0.0;
 #pragma unroll
@@ -648,17 +671,12 @@ __global__ void k_gather_nodes(double* out, const double* u, const int64_t* node
   if (k < n) out[k] = u[nodes[k]];
 }
 
-int tile_cells(int P) {
-  switch (P) {
-    case 2: return 16;
-    case 3: return 16;
-    case 4: return 10;
-    case 5: return 8;
-    case 6: return 6;
-    case 7: return 5;
-    default: return 4;
-  }
-}
+// Explicit-apply tile sizes (cells per tile side): two candidates per order,
+// the larger (less halo work) and half of it (finer load balance on small
+// grids); setup times both and keeps the faster (IMEX_EXPLICIT_TILE =
+// large | small overrides).
+constexpr int kTileLarge[10] = {0, 0, 16, 16, 10, 8, 6, 5, 4, 4};
+constexpr int kTileSmall[10] = {0, 0, 8, 8, 5, 4, 3, 3, 2, 2};
 
 size_t explicit_smem_doubles(int P, int TC) {
   const int p = P - 1, OX = TC * p, OY = OX, RX = (TC + 1) * p + 1, RY = RX, NC = TC + 1;
@@ -722,6 +740,8 @@ struct imex_ctx {
   cudaStream_t stream = nullptr;
   Ops2D ops{};
   int TC = 4, ntx = 1, nty = 1;
+  int tile_small = 0;             // explicit tile: 0 large, 1 small (autotuned at setup)
+  float tile_us[2] = {0.f, 0.f};  // measured explicit launch time of each candidate
   int explicit_per_sm = 1;    // resident CTAs of the explicit kernel per SM
   int num_sms = 152;
   size_t smem_explicit = 0;
@@ -754,9 +774,10 @@ int check_launch(const char* what) {
 
 template <int P>
 void launch_explicit(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t s) {
-  constexpr int TCs[10] = {0, 0, 16, 16, 10, 8, 6, 5, 4, 4};
-  constexpr int TC = TCs[P];
-  k_explicit2d<P, TC><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
+  if (c->tile_small)
+    k_explicit2d<P, kTileSmall[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
+  else
+    k_explicit2d<P, kTileLarge[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
 }
 
 void explicit_dispatch(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t s) {
@@ -772,45 +793,41 @@ void explicit_dispatch(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream
   }
 }
 
+// Shared-memory attribute and resident CTAs per SM of the explicit kernel.
 template <int P>
-cudaError_t set_explicit_smem(size_t bytes) {
-  constexpr int TCs[10] = {0, 0, 16, 16, 10, 8, 6, 5, 4, 4};
-  return cudaFuncSetAttribute(k_explicit2d<P, TCs[P]>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bytes);
+cudaError_t explicit_config(bool small, size_t bytes, int* per_sm) {
+  auto fn = small ? k_explicit2d<P, kTileSmall[P]> : k_explicit2d<P, kTileLarge[P]>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kThreads, bytes);
 }
 
-template <int P>
-cudaError_t explicit_occupancy(size_t bytes, int* per_sm) {
-  constexpr int TCs[10] = {0, 0, 16, 16, 10, 8, 6, 5, 4, 4};
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_explicit2d<P, TCs[P]>, kThreads, bytes);
-}
-
-cudaError_t explicit_occupancy_dispatch(int P, size_t bytes, int* per_sm) {
+cudaError_t explicit_config_dispatch(int P, bool small, size_t bytes, int* per_sm) {
   switch (P) {
-    case 2: return explicit_occupancy<2>(bytes, per_sm);
-    case 3: return explicit_occupancy<3>(bytes, per_sm);
-    case 4: return explicit_occupancy<4>(bytes, per_sm);
-    case 5: return explicit_occupancy<5>(bytes, per_sm);
-    case 6: return explicit_occupancy<6>(bytes, per_sm);
-    case 7: return explicit_occupancy<7>(bytes, per_sm);
-    case 8: return explicit_occupancy<8>(bytes, per_sm);
-    case 9: return explicit_occupancy<9>(bytes, per_sm);
+    case 2: return explicit_config<2>(small, bytes, per_sm);
+    case 3: return explicit_config<3>(small, bytes, per_sm);
+    case 4: return explicit_config<4>(small, bytes, per_sm);
+    case 5: return explicit_config<5>(small, bytes, per_sm);
+    case 6: return explicit_config<6>(small, bytes, per_sm);
+    case 7: return explicit_config<7>(small, bytes, per_sm);
+    case 8: return explicit_config<8>(small, bytes, per_sm);
+    case 9: return explicit_config<9>(small, bytes, per_sm);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t set_explicit_smem_dispatch(int P, size_t bytes) {
-  switch (P) {
-    case 2: return set_explicit_smem<2>(bytes);
-    case 3: return set_explicit_smem<3>(bytes);
-    case 4: return set_explicit_smem<4>(bytes);
-    case 5: return set_explicit_smem<5>(bytes);
-    case 6: return set_explicit_smem<6>(bytes);
-    case 7: return set_explicit_smem<7>(bytes);
-    case 8: return set_explicit_smem<8>(bytes);
-    case 9: return set_explicit_smem<9>(bytes);
-  }
-  return cudaErrorInvalidValue;
+// Select a tile size: tile counts, shared memory and occupancy follow it.
+cudaError_t use_tile(imex_ctx* c, bool small) {
+  const HostSetup& hs = c->hs;
+  c->tile_small = small ? 1 : 0;
+  c->TC = small ? kTileSmall[hs.P] : kTileLarge[hs.P];
+  const int OX = c->TC * hs.p;
+  c->ntx = (hs.nn[0] + OX - 1) / OX;
+  c->nty = (hs.nn[1] + OX - 1) / OX;
+  c->smem_explicit = explicit_smem_doubles(hs.P, c->TC) * sizeof(double);
+  int per_sm = 0;
+  cudaError_t e = explicit_config_dispatch(hs.P, small, c->smem_explicit, &per_sm);
+  c->explicit_per_sm = std::max(1, per_sm);
+  return e;
 }
 
 ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double* OUT, double cu, double cw,
@@ -974,6 +991,43 @@ int64_t launches_per_step(const imex_ctx* c) {
     for (int h : c->lev_has_nodes) n += h;
   }
   return n;
+}
+
+// The autotuner of the explicit tile: time both tile sizes on this problem
+// (one warm-up and five timed launches each, over all columns, writing into
+// the scratch grid) and keep the faster.  IMEX_EXPLICIT_TILE=large|small in
+// the environment fixes the choice instead.
+cudaError_t autotune_tile(imex_ctx* c) {
+  const HostSetup& hs = c->hs;
+  const char* env = std::getenv("IMEX_EXPLICIT_TILE");
+  if (env && std::string(env) == "large") return use_tile(c, false);
+  if (env && std::string(env) == "small") return use_tile(c, true);
+  cudaEvent_t ev[2];
+  cudaError_t e = cudaEventCreate(&ev[0]);
+  e = e ? e : cudaEventCreate(&ev[1]);
+  float best = 1e30f;
+  bool best_small = false;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    const bool small = k == 1;
+    e = use_tile(c, small);
+    if (e != cudaSuccess) break;
+    ExplicitArgs ea = explicit_args(c, c->U[0], c->tmp, c->tmp, 2.0, -1.0, hs.dt * hs.dt, 0.0, false);
+    explicit_dispatch(c, ea, c->ntx * c->nty, nullptr);
+    e = cudaEventRecord(ev[0], nullptr);
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) explicit_dispatch(c, ea, c->ntx * c->nty, nullptr);
+    e = e ? e : cudaEventRecord(ev[1], nullptr);
+    e = e ? e : cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    e = e ? e : cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    c->tile_us[k] = 1e3f * ms / 5.f;
+    if (e == cudaSuccess && c->tile_us[k] < best) {
+      best = c->tile_us[k];
+      best_small = small;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  return e ? e : use_tile(c, best_small);
 }
 
 double ft_at(const HostSetup& hs, int64_t n) {
@@ -1700,7 +1754,7 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
       return fail(IMEX_ERR_CUDA, "no CUDA device");
     }
     const int P = hs.P;
-    c->TC = tile_cells(P);
+    c->TC = kTileLarge[P];
     const int OX = c->TC * hs.p;
     c->ntx = (hs.nn[0] + OX - 1) / OX;
     c->nty = (hs.nn[1] + OX - 1) / OX;
@@ -1863,14 +1917,12 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
       if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
-    e = e ? e : set_explicit_smem_dispatch(P, c->smem_explicit);
     if (e == cudaSuccess) {
-      int nsm = 0, per_sm = 0;
+      int nsm = 0;
       e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-      e = e ? e : explicit_occupancy_dispatch(P, c->smem_explicit, &per_sm);
       c->num_sms = std::max(1, nsm);
-      c->explicit_per_sm = std::max(1, per_sm);
     }
+    e = e ? e : autotune_tile(c);
     if (e != cudaSuccess) {
       std::string msg = std::string("upload failed: ") + cudaGetErrorString(e);
       imex_destroy(c);
@@ -2106,6 +2158,9 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   st->launches_per_step = launches_per_step(c);
   st->rhs_pairs = (int64_t)c->hs.contrib_pos.size();
   st->ncols = c->ncols;
+  st->explicit_tile_cells = c->TC;
+  st->explicit_tile_us_large = c->tile_us[0];
+  st->explicit_tile_us_small = c->tile_us[1];
   st->device_bytes = (int64_t)c->bytes;
   return IMEX_OK;
 }

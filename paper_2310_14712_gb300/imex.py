@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
         "n_components", "n_tree", "max_block", "step", "device_bytes")] + \
         [(n, ctypes.c_double) for n in ("dt", "dt_crit_uncut", "setup_seconds", "residual_S", "residual_M")] + \
         [(n, ctypes.c_int64) for n in ("solve_levels", "solve_ctas", "solve_smem_bytes", "launches_per_step",
-                                    "rhs_pairs", "ncols")]
+                                    "rhs_pairs", "ncols", "explicit_tile_cells")] + \
+        [(n, ctypes.c_double) for n in ("explicit_tile_us_large", "explicit_tile_us_small")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -98,3 +98,20 @@ def test_batched_rejects_source_count_mismatch():
     w = workloads.multisource(nsrc=4)
     with pytest.raises(imex.ImexError):
         imex.Imex.from_workload(w, ncols=3)
+
+
+@pytest.mark.parametrize("make", [lambda: workloads.plate16(), lambda: workloads.multisource(nsrc=4)])
+def test_explicit_tile_sizes_agree_bitwise(make, monkeypatch):
+    # The autotuner picks one of two explicit tile sizes; both must give the
+    # same numbers (per node the same contractions and vertex sums in the same
+    # order), so the choice never changes a result.
+    imex = _imex()
+    out = {}
+    for tile in ("large", "small"):
+        monkeypatch.setenv("IMEX_EXPLICIT_TILE", tile)
+        w = make()
+        with imex.Imex.from_workload(w, ncols=len(w.src_pos) if w.name == "multisource" else 1) as g:
+            g.step(50)
+            out[tile] = (g.fields("u", out=np.zeros(g.field_len)), g.info()["explicit_tile_cells"])
+    assert out["large"][1] != out["small"][1]
+    assert np.array_equal(out["large"][0], out["small"][0])
