@@ -83,6 +83,39 @@ def profiled_traffic(phase, workload):
     return int(vals["dram_bytes_per_launch"]) if h.hexdigest() == vals["source_sha256"] else None
 
 
+def time_flushed(g, steps, stream, flush):
+    """Device time (ms) of `steps` single steps, each after an L2 flush."""
+    total = 0.0
+    for k in range(steps):
+        flush.fill_(float(k))
+        total += g.step_profile(1, stream)[-1]
+    return total
+
+
+def measure_batched(imex, workloads, steps, stream, flush):
+    """Independent source columns against the single-source form on the same
+    geometry: the 16x16-cell plate with 64 seeded sources (one per column)."""
+    out = {}
+    for label, ncols in (("batched", 64), ("plain", 1)):
+        w = workloads.multisource(nsrc=ncols)
+        g = imex.Imex.from_workload(w, ncols=ncols)
+        st = g.info()
+        g.step(5)
+        ms = time_flushed(g, steps, stream, flush)
+        n_act = st["n_d"] + st["n_c"]
+        out[label] = {"value": n_act * ncols * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                      "ncols": ncols, "explicit_tile_cells": st["explicit_tile_cells"]}
+        g.close()
+    b = out["batched"]
+    b.update({"workload": "multisource: [0,1]^2 minus a centred circle r=0.2, 16x16 cells, p=4, "
+                          "64 seeded sources (Ricker f0=20), one per column",
+              "unit": UNIT, "plain_value": out["plain"]["value"],
+              "plain_ms_per_step": out["plain"]["ms_per_step"],
+              "speedup_vs_plain": b["value"] / out["plain"]["value"],
+              "steps": steps, "l2": "flushed between timed steps"})
+    return b
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -340,6 +373,8 @@ def run_gpu(args):
         "setup_seconds": st["setup_seconds"],
         "wall_seconds_timed_loop": wall,
     }
+    if ws == 1:
+        line["batched"] = measure_batched(imex, workloads, min(args.steps, 200), stream, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n_act_cpu, secs = cpu_oracle_rate(w, args.cpu_steps)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",

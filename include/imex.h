@@ -207,6 +207,55 @@ int imex_step_io(imex_ctx *ctx, int64_t n, const double *ft_samples, const int64
 int imex_step_noalloc(imex_ctx *ctx, int64_t n, void *stream);
 
 /*
+ * Iterative solve of the implicit partition (no counterpart in the paper,
+ * which factorises S once; Sec. "Time integration").  With a PCG solver each
+ * step solves S a^c_{n+1} = rhs by preconditioned conjugate gradients
+ * (Saad, Algorithm 9.1) started from a^c_n and stopped at
+ * ||rhs - S a|| <= tol ||rhs||; a step whose PCG does not reach tol within
+ * maxit iterations falls back to the factorised direct solve (same step,
+ * same stream, no host round trip).  Single-column contexts only.
+ *   IMEX_SOLVER_DIRECT     : the factorised solve (default)
+ *   IMEX_SOLVER_PCG_FSAI   : M^{-1} = G G^T, G lower triangular on the pattern
+ *                            of S, learned by imex_pcg_train (initially
+ *                            diag(S)^{-1/2})
+ *   IMEX_SOLVER_PCG_JACOBI : M^{-1} = diag(S)^{-1}
+ */
+#define IMEX_SOLVER_DIRECT 0
+#define IMEX_SOLVER_PCG_FSAI 1
+#define IMEX_SOLVER_PCG_JACOBI 2
+
+/* imex_set_solver - select the solver; tol > 0, 1 <= maxit <= 100000.
+ * Errors: IMEX_ERR_ARG (bad values, or a PCG solver on a multi-column context). */
+int imex_set_solver(imex_ctx *ctx, int solver, double tol, int maxit);
+
+/*
+ * imex_pcg_train - learn G: `epochs` steps of Adam (Kingma and Ba, Algorithm 1;
+ * learning rate lr, in units of G_ij sqrt(S_ii), diagonal kept >= 1e-3) on
+ * Kaporin's functional K(G) = tr(G^T S G) - 2 sum_i log G_ii over the lower
+ * pattern of S, continuing from the current G.  loss_hist: NULL or `epochs`
+ * host doubles receiving K before each step.  Synchronous.
+ */
+int imex_pcg_train(imex_ctx *ctx, int epochs, double lr, double *loss_hist);
+
+/*
+ * imex_pcg_status - last PCG solve: iterations, relative residual, and the
+ * totals since setup (iterations, steps that fell back to the direct solve).
+ * Synchronous.  Any pointer may be NULL.
+ */
+int imex_pcg_status(imex_ctx *ctx, int64_t *iters_last, double *res_last, int64_t *iters_total,
+                    int64_t *fallbacks);
+
+/*
+ * imex_fsai_kaporin - the training kernels on caller data (device pointers):
+ * K(G) and its gradient for S (n x n CSR: s_ptr, s_col, s_val) and G (lower
+ * triangular CSR with sorted columns and a nonzero diagonal: g_ptr, g_col,
+ * g_val).  grad: nnz(G) device doubles; loss: host double.  Synchronous on
+ * `stream`.  For checking the kernels against a CPU definition.
+ */
+int imex_fsai_kaporin(int n, const int *s_ptr, const int *s_col, const double *s_val, const int *g_ptr,
+                      const int *g_col, const double *g_val, double *grad, double *loss, void *stream);
+
+/*
  * imex_fields - copy one field (IMEX_FIELD_*) in canonical layout into dst.
  *   len          : number of doubles in dst; must equal ncols * imex_stats.n_nodes
  *                  (column after column)

@@ -4,6 +4,7 @@
 // Wave Equation", Sec. "Time integration", Fig. TrapCDMIMEX (Newmark IMEX),
 // Eqs. CDMstep / CDMacc (diagonal CDM step), Eqs. Newmark1/2 (prediction and
 // correction, beta = 1/4, gamma = 1/2), Eqs. Kd / Kc (partitioned stiffness).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,6 +21,7 @@
 #include "setup.h"
 
 using namespace imex;
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -466,6 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
   }
   // Wait for the previous launch's results.
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  if (a.skip && *a.skip) return;   // the iterative solve converged: nothing to do
   if (kForward) {
     if (a.first) {
       const int npair = il[4], nrhs = il[3];
@@ -477,9 +480,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
         const int* rr = L.rhs + 4 * k;
         double v = ft * fxc[rr[0]];
         for (int q = rr[1]; q < rr[2]; ++q) v -= pc[q];
-        if (rr[3] >= 0) vg[rr[3]] = v;
+        if (rr[3] >= 0 && !a.rhs_only) vg[rr[3]] = v;
         else rhs0[rr[0]] = v;
       }
+      if (a.rhs_only) return;   // every row's right-hand side is in rhs0
       __syncthreads();
       for (int sl = tid; sl < nslot; sl += kThreads) {
         const int* st = L.slot + 4 * sl;
@@ -603,6 +607,7 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   }
   async_copy_wait();
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  if (a.skip && *a.skip) return;   // the iterative solve converged: nothing to do
   // The whole right-hand side of this component's top block (redundant per CTA).
   for (int i = tid; i < zn; i += kThreads) {
     const int fb = il[2 * i], fe = il[2 * i + 1];
@@ -634,6 +639,213 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
     sol[row] = x;
     cor.row_pre(row, x, node, v_old, a_old);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Iterative alternative for A5: preconditioned conjugate gradients (Saad,
+// Algorithm 9.1) on S a = rhs with M^{-1} = G G^T (G lower triangular on the
+// pattern of S, learned) or diag(S)^{-1}, started from the previous
+// acceleration, stopped at ||r|| <= tol ||b||.  One cooperative grid runs all
+// iterations; grid-wide barriers separate the phases that read other
+// threads' rows.  Every block sums the block partials of a dot product in the
+// same order, so all blocks take the same decisions and the result is
+// deterministic.  On convergence the kernel applies the Newmark correction;
+// otherwise it leaves the state alone and the direct solve that follows runs
+// (its launches test status[1]).
+
+// Block partial of a sum into part[slot * gridDim.x + blockIdx.x].
+__device__ __forceinline__ void block_partial(double v, double* part, int slot, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kWarps; ++w) s += red[w];
+    part[(size_t)slot * gridDim.x + blockIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Sum of the block partials of `slot`, the same bits in every thread.
+__device__ __forceinline__ double grid_total(const double* part, int slot) {
+  double s = 0.0;
+  for (int b = threadIdx.x % 32; b < (int)gridDim.x; b += 32) s += __ldcg(part + (size_t)slot * gridDim.x + b);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+__device__ __forceinline__ double csr_row_dot(const int* ptr, const int* col, const double* val, const double* v,
+                                              int i) {
+  double s0 = 0.0, s1 = 0.0;
+  int k = ptr[i];
+  const int e = ptr[i + 1];
+  for (; k + 2 <= e; k += 2) {
+    s0 = fma(val[k], __ldcg(v + col[k]), s0);
+    s1 = fma(val[k + 1], __ldcg(v + col[k + 1]), s1);
+  }
+  if (k < e) s0 = fma(val[k], __ldcg(v + col[k]), s0);
+  return s0 + s1;
+}
+
+__global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[kWarps];
+  const int n = a.n;
+  const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  // z = M^{-1} r
+  auto apply_minv = [&]() {
+    if (a.precond == 2) {
+      for (int i = g0; i < n; i += gs) a.z[i] = a.dinv[i] * a.r[i];
+    } else {
+      for (int j = g0; j < n; j += gs) {
+        double s = 0.0;
+        for (int k = a.gt_ptr[j]; k < a.gt_ptr[j + 1]; ++k) s = fma(a.g_val[a.gt_idx[k]], __ldcg(a.r + a.gt_row[k]), s);
+        a.w[j] = s;
+      }
+      grid.sync();
+      for (int i = g0; i < n; i += gs) a.z[i] = csr_row_dot(a.g_ptr, a.g_col, a.g_val, a.w, i);
+    }
+  };
+  for (int i = g0; i < n; i += gs) a.x[i] = a.a_c[i];
+  grid.sync();
+  double bb = 0.0, rr = 0.0;
+  for (int i = g0; i < n; i += gs) {
+    const double bi = a.b[i], ri = bi - csr_row_dot(a.s_ptr, a.s_col, a.s_val, a.x, i);
+    a.r[i] = ri;
+    bb = fma(bi, bi, bb);
+    rr = fma(ri, ri, rr);
+  }
+  block_partial(bb, a.part, 3, red);
+  block_partial(rr, a.part, 1, red);
+  grid.sync();
+  const double nb2 = grid_total(a.part, 3);
+  double rr_t = grid_total(a.part, 1);
+  const double tol2 = a.tol * a.tol * nb2;
+  bool conv = rr_t <= tol2;
+  int k = 0;
+  if (!conv) {
+    apply_minv();
+    double rz = 0.0;
+    for (int i = g0; i < n; i += gs) {
+      a.p[i] = a.z[i];
+      rz = fma(a.r[i], a.z[i], rz);
+    }
+    block_partial(rz, a.part, 2, red);
+    grid.sync();
+    rz = grid_total(a.part, 2);
+    for (k = 1; k <= a.maxit; ++k) {
+      double pq = 0.0;
+      for (int i = g0; i < n; i += gs) {
+        const double qi = csr_row_dot(a.s_ptr, a.s_col, a.s_val, a.p, i);
+        a.q[i] = qi;
+        pq = fma(a.p[i], qi, pq);
+      }
+      block_partial(pq, a.part, 0, red);
+      grid.sync();
+      const double alpha = rz / grid_total(a.part, 0);
+      rr = 0.0;
+      for (int i = g0; i < n; i += gs) {
+        a.x[i] = fma(alpha, a.p[i], a.x[i]);
+        const double ri = fma(-alpha, a.q[i], a.r[i]);
+        a.r[i] = ri;
+        rr = fma(ri, ri, rr);
+      }
+      block_partial(rr, a.part, 1, red);
+      grid.sync();
+      rr_t = grid_total(a.part, 1);
+      if (rr_t <= tol2) {
+        conv = true;
+        break;
+      }
+      apply_minv();
+      double rzn = 0.0;
+      for (int i = g0; i < n; i += gs) rzn = fma(a.r[i], a.z[i], rzn);
+      block_partial(rzn, a.part, 2, red);
+      grid.sync();
+      rzn = grid_total(a.part, 2);
+      const double beta = rzn / rz;
+      rz = rzn;
+      for (int i = g0; i < n; i += gs) a.p[i] = fma(beta, a.p[i], a.z[i]);
+      grid.sync();
+    }
+    if (k > a.maxit) k = a.maxit;
+  }
+  if (conv) {
+    const Corr cor{a.mode, a.c_node, a.U, a.v_c, a.a_c, a.dt};
+    for (int i = g0; i < n; i += gs) cor.row(i, a.x[i]);
+  }
+  if (g0 == 0) {
+    a.status[0] = k;
+    a.status[1] = conv ? 1 : 0;
+    a.counters[0] += k;
+    a.counters[1] += conv ? 0 : 1;
+    *a.res = nb2 > 0.0 ? sqrt(rr_t / nb2) : 0.0;
+  }
+}
+
+// Training of G (Kaporin's functional K(G) = tr(G^T S G) - 2 sum log G_ii on
+// the lower pattern; Adam).  sg = (S G) on the pattern of G: for entry
+// (i, j), sum over S's row i of S_ik G_kj (G_kj found in G's row k, k >= j).
+__global__ void k_kap_sg(int n, const int* s_ptr, const int* s_col, const double* s_val, const int* g_ptr,
+                         const int* g_col, const double* g_val, double* sg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int e = g_ptr[i]; e < g_ptr[i + 1]; ++e) {
+    const int j = g_col[e];
+    double s = 0.0;
+    for (int t = s_ptr[i]; t < s_ptr[i + 1]; ++t) {
+      const int kk = s_col[t];
+      if (kk < j) continue;
+      int lo = g_ptr[kk], hi = g_ptr[kk + 1];
+      while (lo < hi) {   // first entry of row kk with column >= j
+        const int mid = (lo + hi) / 2;
+        if (g_col[mid] < j) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < g_ptr[kk + 1] && g_col[lo] == j) s = fma(s_val[t], g_val[lo], s);
+    }
+    sg[e] = s;
+  }
+}
+
+// Gradient 2 sg - 2 delta_ij / G_ii and the per-block partials of K.
+__global__ void k_kap_grad(int n, const int* g_ptr, const int* g_col, const double* g_val, const double* sg,
+                           double* grad, double* part) {
+  __shared__ double red[kWarps];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  if (i < n) {
+    for (int e = g_ptr[i]; e < g_ptr[i + 1]; ++e) {
+      double g = 2.0 * sg[e];
+      l = fma(g_val[e], sg[e], l);
+      if (g_col[e] == i) {
+        g -= 2.0 / g_val[e];
+        l -= 2.0 * log(g_val[e]);
+      }
+      grad[e] = g;
+    }
+  }
+  block_partial(l, part, 0, red);
+}
+
+// One Adam step (Kingma and Ba, Algorithm 1) in row-scaled units theta =
+// G_ij / scale_ij; the diagonal stays >= floor.  Writes the new G values.
+__global__ void k_adam(int64_t nnz, double* theta, const double* grad, const double* scale, const uint8_t* is_diag,
+                       double* m, double* v, double b1t, double b2t, double lr, double floor_, double* g_val) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+  const double g = grad[e] * scale[e];
+  const double me = b1 * m[e] + (1.0 - b1) * g;
+  const double ve = b2 * v[e] + (1.0 - b2) * g * g;
+  m[e] = me;
+  v[e] = ve;
+  double th = theta[e] - lr * (me / (1.0 - b1t)) / (sqrt(ve / (1.0 - b2t)) + eps);
+  if (is_diag[e]) th = fmax(th, floor_);
+  theta[e] = th;
+  g_val[e] = th * scale[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -735,6 +947,23 @@ struct imex_ctx {
   int io_cap = 4096;
   // state
   int ncols = 1;            // independent source columns (fields column after column)
+  // iterative solve (PCG) and its learned preconditioner
+  int solver = IMEX_SOLVER_DIRECT;
+  double pcg_tol = 1e-10;
+  int pcg_maxit = 200;
+  int pcg_grid = 0;
+  int64_t g_nnz = 0;
+  int *s_ptr = nullptr, *s_col = nullptr;
+  double* s_val = nullptr;
+  int *g_ptr = nullptr, *g_col = nullptr, *gt_ptr = nullptr, *gt_row = nullptr, *gt_idx = nullptr;
+  double *g_val = nullptr, *g_scale = nullptr, *g_theta = nullptr, *g_m = nullptr, *g_v = nullptr;
+  double *g_grad = nullptr, *g_sg = nullptr, *dinv = nullptr;
+  uint8_t* g_isdiag = nullptr;
+  double *pcg_x = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_w = nullptr;
+  double *pcg_part = nullptr, *pcg_res = nullptr;
+  int* pcg_status = nullptr;
+  long long* pcg_counters = nullptr;
+  int64_t adam_t = 0;
   int cur = 0;              // U[cur] holds u_n
   int64_t step = 0;
   cudaStream_t stream = nullptr;
@@ -887,7 +1116,8 @@ constexpr size_t kMaxDynSmem = 220 * 1024;      // dynamic shared memory limit w
 // or of M^cc (initial acceleration, mode 1).  upd/sol/rhs0 are the solve's
 // scratch vectors.
 cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double* ft_dev, int mode, double* Ubuf,
-                               const double* src, double* upd, double* sol, double* rhs0, cudaStream_t s) {
+                               const double* src, double* upd, double* sol, double* rhs0, cudaStream_t s,
+                               const int* skip = nullptr, bool rhs_only = false) {
   const HostSetup& hs = c->hs;
   WalkArgs w{};
   w.blob = use_S ? c->blob_S : c->blob_M;
@@ -922,6 +1152,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   w.v_c = c->v_c;
   w.a_c = c->a_c;
   w.dt = hs.dt;
+  w.skip = skip;
   w.cs_node = hs.nnodes;
   w.cs_c = hs.n_c;
   w.cs_upd = std::max<int64_t>(hs.upd_size, 1);
@@ -949,6 +1180,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   z.v_c = c->v_c;
   z.a_c = c->a_c;
   z.dt = hs.dt;
+  z.skip = skip;
   z.cs_node = w.cs_node;
   z.cs_c = w.cs_c;
   z.cs_upd = w.cs_upd;
@@ -972,6 +1204,10 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
     return fwd ? cudaLaunchKernelEx(&cfg, k_walk<true, false>, w) : cudaLaunchKernelEx(&cfg, k_walk<false, false>, w);
   };
   cudaError_t e = cudaSuccess;
+  if (rhs_only) {   // the first forward launch forms every right-hand side into rhs0, nothing else
+    w.rhs_only = 1;
+    return walk(0, true);
+  }
   for (int l = 0; l < nlev && e == cudaSuccess; ++l) e = walk(l, true);
   if (e == cudaSuccess && c->ntop > 0) {
     cfg.gridDim = dim3(c->ntop, c->ncols);
@@ -989,6 +1225,7 @@ int64_t launches_per_step(const imex_ctx* c) {
   if (c->hs.n_c > 0) {
     n += (int64_t)c->lev_cta0.size() + (c->ntop > 0 ? 1 : 0);
     for (int h : c->lev_has_nodes) n += h;
+    if (c->solver != IMEX_SOLVER_DIRECT) n += 2;   // right-hand sides, PCG (the direct launches follow, skipped)
   }
   return n;
 }
@@ -1028,6 +1265,44 @@ cudaError_t autotune_tile(imex_ctx* c) {
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   return e ? e : use_tile(c, best_small);
+}
+
+cudaError_t launch_pcg(imex_ctx* c, double* Ubuf, cudaStream_t s) {
+  const HostSetup& hs = c->hs;
+  PcgArgs a{};
+  a.n = (int)hs.n_c;
+  a.s_ptr = c->s_ptr;
+  a.s_col = c->s_col;
+  a.s_val = c->s_val;
+  a.g_ptr = c->g_ptr;
+  a.g_col = c->g_col;
+  a.g_val = c->g_val;
+  a.gt_ptr = c->gt_ptr;
+  a.gt_row = c->gt_row;
+  a.gt_idx = c->gt_idx;
+  a.dinv = c->dinv;
+  a.precond = c->solver == IMEX_SOLVER_PCG_JACOBI ? 2 : 1;
+  a.b = c->rhs0;
+  a.x = c->pcg_x;
+  a.r = c->pcg_r;
+  a.z = c->pcg_z;
+  a.p = c->pcg_p;
+  a.q = c->pcg_q;
+  a.w = c->pcg_w;
+  a.part = c->pcg_part;
+  a.tol = c->pcg_tol;
+  a.maxit = c->pcg_maxit;
+  a.status = c->pcg_status;
+  a.counters = c->pcg_counters;
+  a.res = c->pcg_res;
+  a.mode = 0;
+  a.c_node = c->c_node;
+  a.U = Ubuf;
+  a.v_c = c->v_c;
+  a.a_c = c->a_c;
+  a.dt = hs.dt;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(c->pcg_grid), dim3(kThreads), args, 0, s);
 }
 
 double ft_at(const HostSetup& hs, int64_t n) {
@@ -1561,6 +1836,53 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
   return IMEX_OK;
 }
 
+// Data of the iterative solve: S (CSR), the lower pattern of G with its
+// transpose map, the per-entry row scale 1/sqrt(S_ii), and the start
+// G = diag(S)^{-1/2} (theta = G / scale: 1 on the diagonal, 0 elsewhere).
+struct PcgPlan {
+  std::vector<int> g_ptr, g_col, gt_ptr, gt_row, gt_idx;
+  std::vector<double> g_val, g_scale, g_theta, dinv;
+  std::vector<uint8_t> g_isdiag;
+};
+
+int plan_pcg(const HostSetup& hs, PcgPlan& q) {
+  const int n = (int)hs.n_c;
+  q.g_ptr.assign(1, 0);
+  q.dinv.assign(std::max(n, 1), 0.0);
+  for (int i = 0; i < n; ++i) {
+    double d = 0.0;
+    for (int k = hs.S_ptr[i]; k < hs.S_ptr[i + 1]; ++k)
+      if (hs.S_col[k] == i) d = hs.S_val[k];
+    if (!(d > 0.0)) return fail(IMEX_ERR_NOT_SPD, "S has a nonpositive diagonal entry");
+    q.dinv[i] = 1.0 / d;
+    const double sc = 1.0 / std::sqrt(d);
+    for (int k = hs.S_ptr[i]; k < hs.S_ptr[i + 1]; ++k) {
+      const int j = hs.S_col[k];
+      if (j > i) continue;
+      q.g_col.push_back(j);
+      q.g_scale.push_back(sc);
+      q.g_isdiag.push_back(j == i ? 1 : 0);
+      q.g_theta.push_back(j == i ? 1.0 : 0.0);
+      q.g_val.push_back(j == i ? sc : 0.0);
+    }
+    q.g_ptr.push_back((int)q.g_col.size());
+  }
+  // Transpose map: entries of each column j in row order.
+  q.gt_ptr.assign(n + 1, 0);
+  for (int j : q.g_col) q.gt_ptr[j + 1]++;
+  for (int j = 0; j < n; ++j) q.gt_ptr[j + 1] += q.gt_ptr[j];
+  q.gt_row.assign(q.g_col.size(), 0);
+  q.gt_idx.assign(q.g_col.size(), 0);
+  std::vector<int> fill(q.gt_ptr.begin(), q.gt_ptr.end() - 1);
+  for (int i = 0; i < n; ++i)
+    for (int e = q.g_ptr[i]; e < q.g_ptr[i + 1]; ++e) {
+      const int j = q.g_col[e];
+      q.gt_row[fill[j]] = i;
+      q.gt_idx[fill[j]++] = e;
+    }
+  return IMEX_OK;
+}
+
 // Even-odd and rank-one forms of the 1D operators of the explicit apply, each
 // checked against the plain matrices it replaces.
 int explicit_ops(const HostSetup& hs, double sx, double sy, Ops2D& ops) {
@@ -1797,6 +2119,12 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
       delete c;
       return rc;
     }
+    PcgPlan pp;
+    if (int rc = plan_pcg(hs, pp)) {
+      delete c;
+      return rc;
+    }
+    c->g_nnz = (int64_t)pp.g_col.size();
     {
       c->walk_max_slots = plan.max_slots;
       c->walk_max_m = plan.max_m;
@@ -1863,6 +2191,31 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
     ar.add(&c->zA_off, std::max<size_t>(plan.zA_off.size(), 1));
     ar.add(&c->zA_S, std::max<size_t>(plan.zA_S.size(), 1));
     ar.add(&c->zA_M, std::max<size_t>(plan.zA_M.size(), 1));
+    {
+      const int64_t ncm = std::max<int64_t>(nc, 1), gnz = std::max<int64_t>(c->g_nnz, 1);
+      ar.add(&c->s_ptr, hs.S_ptr.size());
+      ar.add(&c->s_col, std::max<size_t>(hs.S_col.size(), 1));
+      ar.add(&c->s_val, std::max<size_t>(hs.S_val.size(), 1));
+      ar.add(&c->g_ptr, pp.g_ptr.size());
+      ar.add(&c->g_col, gnz);
+      ar.add(&c->gt_ptr, ncm + 1);
+      ar.add(&c->gt_row, gnz);
+      ar.add(&c->gt_idx, gnz);
+      ar.add(&c->g_val, gnz);
+      ar.add(&c->g_scale, gnz);
+      ar.add(&c->g_theta, gnz);
+      ar.add(&c->g_m, gnz);
+      ar.add(&c->g_v, gnz);
+      ar.add(&c->g_grad, gnz);
+      ar.add(&c->g_sg, gnz);
+      ar.add(&c->g_isdiag, gnz);
+      ar.add(&c->dinv, ncm);
+      for (double** v : {&c->pcg_x, &c->pcg_r, &c->pcg_z, &c->pcg_p, &c->pcg_q, &c->pcg_w}) ar.add(v, ncm);
+      ar.add(&c->pcg_part, 4 * std::max<int64_t>(1024, (ncm + kThreads - 1) / kThreads));
+      ar.add(&c->pcg_res, 2);
+      ar.add(&c->pcg_status, 4);
+      ar.add(&c->pcg_counters, 2);
+    }
     ar.add(&c->ft_buf, 2);
     ar.add(&c->rec_buf, (size_t)c->io_cap * ncols);
     ar.add(&c->rec_nodes, c->io_cap);
@@ -1891,6 +2244,26 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
     e = e ? e : upload(c->cls, hs.node_class);
     e = e ? e : upload(c->c_node, hs.c_node);
     e = e ? e : upload(c->fxc, fxc);
+    e = e ? e : upload(c->s_ptr, hs.S_ptr);
+    e = e ? e : upload(c->s_col, hs.S_col);
+    e = e ? e : upload(c->s_val, hs.S_val);
+    e = e ? e : upload(c->g_ptr, pp.g_ptr);
+    e = e ? e : upload(c->g_col, pp.g_col);
+    e = e ? e : upload(c->gt_ptr, pp.gt_ptr);
+    e = e ? e : upload(c->gt_row, pp.gt_row);
+    e = e ? e : upload(c->gt_idx, pp.gt_idx);
+    e = e ? e : upload(c->g_val, pp.g_val);
+    e = e ? e : upload(c->g_scale, pp.g_scale);
+    e = e ? e : upload(c->g_theta, pp.g_theta);
+    e = e ? e : upload(c->g_isdiag, pp.g_isdiag);
+    e = e ? e : upload(c->dinv, pp.dinv);
+    if (e == cudaSuccess) {
+      int occ = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg, kThreads, 0);
+      int nsm = 0;
+      e = e ? e : cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+      c->pcg_grid = std::max(1, std::min(std::min(nsm, 1024), nsm * occ));
+    }
     e = e ? e : upload(c->Kpair, plan.Kpair);
     e = e ? e : upload(c->kp_off, plan.kp_off);
     e = e ? e : upload(c->kp_len, plan.kp_len);
@@ -1962,8 +2335,20 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
   ea.ft_dev = ft_dev;
   explicit_dispatch(c, ea, c->ntx * c->nty + pred_blocks(c, true), s);
   if (ev) cudaEventRecord(ev[1], s);
-  if (hs.n_c > 0)
-    launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, c->upd, c->sol, c->rhs0, s);
+  if (hs.n_c > 0) {
+    if (c->solver == IMEX_SOLVER_DIRECT) {
+      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, c->upd, c->sol, c->rhs0, s);
+    } else {
+      // Right-hand sides, PCG (correction included on convergence), then the
+      // direct solve, whose launches return at once unless PCG fell short.
+      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, c->upd, c->sol, c->rhs0, s,
+                         nullptr, true);
+      if (cudaError_t e = launch_pcg(c, Unext, s))
+        return fail(IMEX_ERR_CUDA, std::string("imex_step: PCG launch: ") + cudaGetErrorString(e));
+      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, c->upd, c->sol, c->rhs0, s,
+                         c->pcg_status + 1);
+    }
+  }
   if (ev) cudaEventRecord(ev[2], s);
   if (int rc = check_launch("imex_step")) return rc;
   c->cur = 1 - c->cur;
@@ -2143,6 +2528,95 @@ int imex_set_initial(imex_ctx* c, const double* u0, const double* v0, int64_t le
   if (int rc = compute_initial(c, s)) return rc;
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_set_initial: ") + cudaGetErrorString(e));
+  return IMEX_OK;
+}
+
+int imex_set_solver(imex_ctx* c, int solver, double tol, int maxit) {
+  if (!c) return fail(IMEX_ERR_ARG, "NULL context");
+  if (solver != IMEX_SOLVER_DIRECT && solver != IMEX_SOLVER_PCG_FSAI && solver != IMEX_SOLVER_PCG_JACOBI)
+    return fail(IMEX_ERR_ARG, "unknown solver");
+  if (!(tol > 0.0) || maxit < 1 || maxit > 100000) return fail(IMEX_ERR_ARG, "need tol > 0 and 1 <= maxit <= 100000");
+  if (solver != IMEX_SOLVER_DIRECT && c->ncols > 1)
+    return fail(IMEX_ERR_ARG, "the iterative solve serves single-column contexts");
+  c->solver = solver;
+  c->pcg_tol = tol;
+  c->pcg_maxit = maxit;
+  return IMEX_OK;
+}
+
+int imex_pcg_train(imex_ctx* c, int epochs, double lr, double* loss_hist) {
+  if (!c || epochs < 0 || !(lr > 0.0)) return fail(IMEX_ERR_ARG, "bad arguments");
+  const int n = (int)c->hs.n_c;
+  if (n == 0) return IMEX_OK;
+  const int nb = (n + kThreads - 1) / kThreads;
+  const int nbe = (int)((c->g_nnz + kThreads - 1) / kThreads);
+  std::vector<double> part(nb);
+  cudaStream_t s = c->stream;
+  for (int ep = 0; ep < epochs; ++ep) {
+    k_kap_sg<<<nb, kThreads, 0, s>>>(n, c->s_ptr, c->s_col, c->s_val, c->g_ptr, c->g_col, c->g_val, c->g_sg);
+    k_kap_grad<<<nb, kThreads, 0, s>>>(n, c->g_ptr, c->g_col, c->g_val, c->g_sg, c->g_grad, c->pcg_part);
+    if (loss_hist) {
+      cudaError_t e = cudaMemcpyAsync(part.data(), c->pcg_part, nb * sizeof(double), cudaMemcpyDeviceToHost, s);
+      e = e ? e : cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_pcg_train: ") + cudaGetErrorString(e));
+      double l = 0.0;
+      for (double v : part) l += v;
+      loss_hist[ep] = l;
+    }
+    const int64_t t = ++c->adam_t;
+    k_adam<<<nbe, kThreads, 0, s>>>(c->g_nnz, c->g_theta, c->g_grad, c->g_scale, c->g_isdiag, c->g_m, c->g_v,
+                                    std::pow(0.9, (double)t), std::pow(0.999, (double)t), lr, 1e-3, c->g_val);
+    if (int rc = check_launch("imex_pcg_train")) return rc;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_pcg_train: ") + cudaGetErrorString(e));
+  return IMEX_OK;
+}
+
+int imex_pcg_status(imex_ctx* c, int64_t* iters_last, double* res_last, int64_t* iters_total, int64_t* fallbacks) {
+  if (!c) return fail(IMEX_ERR_ARG, "NULL context");
+  int st[2] = {0, 0};
+  long long cnt[2] = {0, 0};
+  double res = 0.0;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  e = e ? e : cudaMemcpy(st, c->pcg_status, sizeof(st), cudaMemcpyDeviceToHost);
+  e = e ? e : cudaMemcpy(cnt, c->pcg_counters, sizeof(cnt), cudaMemcpyDeviceToHost);
+  e = e ? e : cudaMemcpy(&res, c->pcg_res, sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_pcg_status: ") + cudaGetErrorString(e));
+  if (iters_last) *iters_last = st[0];
+  if (res_last) *res_last = res;
+  if (iters_total) *iters_total = cnt[0];
+  if (fallbacks) *fallbacks = cnt[1];
+  return IMEX_OK;
+}
+
+int imex_fsai_kaporin(int n, const int* s_ptr, const int* s_col, const double* s_val, const int* g_ptr,
+                      const int* g_col, const double* g_val, double* grad, double* loss, void* stream) {
+  if (n < 1 || !s_ptr || !s_col || !s_val || !g_ptr || !g_col || !g_val || !grad || !loss)
+    return fail(IMEX_ERR_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  int nnz = 0;
+  cudaError_t e = cudaMemcpyAsync(&nnz, g_ptr + n, sizeof(int), cudaMemcpyDeviceToHost, s);
+  e = e ? e : cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_fsai_kaporin: ") + cudaGetErrorString(e));
+  const int nb = (n + kThreads - 1) / kThreads;
+  double *sg = nullptr, *part = nullptr;
+  e = cudaMalloc(&sg, std::max(nnz, 1) * sizeof(double));
+  e = e ? e : cudaMalloc(&part, nb * sizeof(double));
+  if (e == cudaSuccess) {
+    k_kap_sg<<<nb, kThreads, 0, s>>>(n, s_ptr, s_col, s_val, g_ptr, g_col, g_val, sg);
+    k_kap_grad<<<nb, kThreads, 0, s>>>(n, g_ptr, g_col, g_val, sg, grad, part);
+    e = cudaGetLastError();
+  }
+  std::vector<double> hp(nb);
+  e = e ? e : cudaMemcpyAsync(hp.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = e ? e : cudaStreamSynchronize(s);
+  cudaFree(sg);
+  cudaFree(part);
+  if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_fsai_kaporin: ") + cudaGetErrorString(e));
+  double l = 0.0;
+  for (double v : hp) l += v;
+  *loss = l;
   return IMEX_OK;
 }
 

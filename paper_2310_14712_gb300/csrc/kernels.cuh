@@ -96,6 +96,8 @@ struct WalkArgs {
   int max_slots, max_m, max_pairs;  // shared-memory vector sizes (even)
   // right-hand sides f_t f_x^c - K^c u (first forward launch)
   int first;
+  int rhs_only;                 // first launch: only form the right-hand sides (into rhs0)
+  const int* skip;              // if set and *skip != 0: the launch does nothing (PCG converged)
   const double* SRC;            // u_pred (step) or u_0 (initial acceleration), full grid
   const double* Kpair;          // per CTA: rows of the cell matrices of its pairs (m-major, scaled)
   const int64_t* kp_off;        // [cta] (16-byte aligned)
@@ -133,6 +135,7 @@ struct TopArgs {
   int max_zn;                   // even
   int64_t max_arows;            // even: largest (r1 - r0) * |Z| over the CTAs
   int max_chunk;                // even: largest r1 - r0 (<= threads per CTA)
+  const int* skip;              // if set and *skip != 0: the launch does nothing (PCG converged)
   const int* ilist;             // per component: per Z row {update begin, update end}, then positions
   const int64_t* ilist_off;     // [cta]
   const int64_t* ilist_len;     // [cta]
@@ -146,6 +149,38 @@ struct TopArgs {
   double* a_c;
   double dt;
   int64_t cs_node, cs_c, cs_upd;  // independent columns (blockIdx.y)
+};
+
+// Preconditioned conjugate gradients for S a = rhs (the iterative alternative
+// to A5), one cooperative grid, single column.
+struct PcgArgs {
+  int n;                          // implicit rows (c-order)
+  const int* s_ptr;               // S, CSR, full symmetric pattern
+  const int* s_col;
+  const double* s_val;
+  const int* g_ptr;               // G, CSR, lower triangle of S's pattern
+  const int* g_col;
+  const double* g_val;
+  const int* gt_ptr;              // G^T: per column j the entries (row, index into g_val)
+  const int* gt_row;
+  const int* gt_idx;
+  const double* dinv;             // 1 / S_ii
+  int precond;                    // 1: M^{-1} = G G^T; 2: M^{-1} = diag(S)^{-1}
+  const double* b;                // right-hand side
+  double *x, *r, *z, *p, *q, *w;  // n each
+  double* part;                   // 4 x gridDim.x block partial sums
+  double tol;                     // stop when ||r|| <= tol ||b||
+  int maxit;
+  int* status;                    // [0] iterations of the last solve, [1] 1: converged, 0: fallback
+  long long* counters;            // [0] iterations summed, [1] fallbacks
+  double* res;                    // relative residual of the last solve
+  // Newmark correction on convergence (as in the direct solve)
+  int mode;
+  const int* c_node;
+  double* U;
+  double* v_c;
+  double* a_c;
+  double dt;
 };
 
 }  // namespace imex

@@ -1034,6 +1034,9 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
     }
     Smat = coo_to_csr(nc, es);
     Mmat = coo_to_csr(nc, em);
+    hs.S_ptr = Smat.ptr;
+    hs.S_col = Smat.col;
+    hs.S_val = Smat.val;
   }
 
   // ---------------------------------------------------------------- symbolic

@@ -101,6 +101,10 @@ struct HostSetup {
   int64_t upd_size = 0;
   int max_block = 0, max_rows = 0, ncomp = 0, max_comp = 0;
   Factor S, Mcc;
+  // S itself (c-order, full symmetric pattern, CSR): the operator of the
+  // iterative solve and of preconditioner training.
+  std::vector<int> S_ptr, S_col;
+  std::vector<double> S_val;
   int64_t nnz_L = 0;
   double residual_S = 0, residual_M = 0;  // ||A x - b|| / ||b|| of a host replay of the device solve
 

@@ -72,6 +72,11 @@ _lib.imex_setup_batch.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_d
                                   ctypes.POINTER(Source), ctypes.c_int, ctypes.POINTER(Alloc),
                                   ctypes.POINTER(_vp)]
 _lib.imex_step.argtypes = [_vp, ctypes.c_int64, _vp]
+_lib.imex_set_solver.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+_lib.imex_pcg_train.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _dp]
+_lib.imex_pcg_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), _dp, ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_int64)]
+_lib.imex_fsai_kaporin.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _dp, _vp]
 _lib.imex_step_profile.argtypes = [_vp, ctypes.c_int64, _vp, _dp]
 _lib.imex_step_io.argtypes = [_vp, ctypes.c_int64, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                               _dp, _vp]
@@ -91,7 +96,8 @@ _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctyp
                                         ctypes.POINTER(Stats)]
 
 # Every symbol include/imex.h declares (checked by the CPU tests).
-EXPORTS = ("imex_setup", "imex_setup_batch", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
+EXPORTS = ("imex_setup", "imex_setup_batch", "imex_set_solver", "imex_pcg_train", "imex_pcg_status",
+           "imex_fsai_kaporin", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
            "imex_set_initial", "imex_info", "imex_last_error", "imex_destroy", "imex_gll_points",
            "imex_gauss_points", "imex_host_setup_export")
 
@@ -140,6 +146,24 @@ def _mesh_source(dim, lo, hi, ncells, depth, holes, rho, c0, cell_c, src_pos, f0
     s.pos = pos.ctypes.data_as(_dp)
     s.f0, s.sigma, s.amp, s.wavelet = f0, sigma, amp, wavelet
     return m, s, keep
+
+
+SOLVERS = {"direct": 0, "pcg_fsai": 1, "pcg_jacobi": 2}
+
+
+def fsai_kaporin(s_ptr, s_col, s_val, g_ptr, g_col, g_val, stream=None):
+    """K(G) = tr(G^T S G) - 2 sum log G_ii and its gradient with the library's
+    training kernels; all arguments are CUDA torch tensors (int32 / float64,
+    CSR).  Returns (loss, grad tensor)."""
+    import torch
+    n = int(s_ptr.numel()) - 1
+    grad = torch.empty_like(g_val)
+    loss = ctypes.c_double(0.0)
+    st = torch.cuda.current_stream() if stream is None else stream
+    _check(_lib.imex_fsai_kaporin(n, s_ptr.data_ptr(), s_col.data_ptr(), s_val.data_ptr(), g_ptr.data_ptr(),
+                                  g_col.data_ptr(), g_val.data_ptr(), grad.data_ptr(), ctypes.byref(loss),
+                                  ctypes.c_void_p(st.cuda_stream)), "imex_fsai_kaporin")
+    return loss.value, grad
 
 
 def gll_points(p):
@@ -240,6 +264,23 @@ class Imex:
     def step(self, n, stream=None):
         """Advance n IMEX steps asynchronously on `stream` (default: torch's current stream)."""
         _check(_lib.imex_step(self._ctx, int(n), self._stream(stream)), "imex_step")
+
+    def set_solver(self, solver="direct", tol=1e-10, maxit=200):
+        """'direct' (factorised), 'pcg_fsai' (learned G G^T) or 'pcg_jacobi'."""
+        _check(_lib.imex_set_solver(self._ctx, SOLVERS[solver], float(tol), int(maxit)), "imex_set_solver")
+
+    def pcg_train(self, epochs, lr=3e-2):
+        """Adam steps on Kaporin's functional for G; returns the loss before each step."""
+        hist = np.zeros(int(epochs))
+        _check(_lib.imex_pcg_train(self._ctx, int(epochs), float(lr), hist.ctypes.data_as(_dp)), "imex_pcg_train")
+        return hist
+
+    def pcg_status(self):
+        it, tot, fb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        res = ctypes.c_double()
+        _check(_lib.imex_pcg_status(self._ctx, ctypes.byref(it), ctypes.byref(res), ctypes.byref(tot),
+                                    ctypes.byref(fb)), "imex_pcg_status")
+        return {"iters_last": it.value, "res_last": res.value, "iters_total": tot.value, "fallbacks": fb.value}
 
     def step_noalloc(self, n, stream=None):
         """Like step(), but the implicit solve's scratch lives in the library's fixed
