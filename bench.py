@@ -116,6 +116,34 @@ def measure_batched(imex, workloads, steps, stream, flush):
     return b
 
 
+def measure_learned_pcg(imex, w, steps, stream, flush, epochs=300):
+    """The implicit solve by PCG (tol 1e-10) with the learned FSAI preconditioner
+    and with Jacobi, against the factorised solve, on the bench workload."""
+    g = imex.Imex.from_workload(w)
+    st = g.info()
+    n_act = st["n_d"] + st["n_c"]
+    t0 = time.perf_counter()
+    hist = g.pcg_train(epochs)
+    train_s = time.perf_counter() - t0
+    out = {"workload": workload_name(w), "unit": UNIT, "tol": 1e-10, "train_epochs": epochs,
+           "train_seconds": train_s, "kaporin_loss": [float(hist[0]), float(hist[-1])],
+           "l2": "flushed between timed steps", "steps": steps}
+    for solver in ("direct", "pcg_fsai", "pcg_jacobi"):
+        g.set_solver(solver, 1e-10, 5000)
+        g.step(3)
+        s0 = g.pcg_status()
+        ms = time_flushed(g, steps, stream, flush)
+        s1 = g.pcg_status()
+        out[solver] = {"value": n_act * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                       "iterations_per_step": (s1["iters_total"] - s0["iters_total"]) / steps,
+                       "fallbacks": s1["fallbacks"] - s0["fallbacks"]}
+    out["learned_vs_jacobi_iterations"] = (out["pcg_fsai"]["iterations_per_step"] /
+                                           max(out["pcg_jacobi"]["iterations_per_step"], 1e-30))
+    out["learned_vs_direct_value"] = out["pcg_fsai"]["value"] / out["direct"]["value"]
+    g.close()
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -375,6 +403,7 @@ def run_gpu(args):
     }
     if ws == 1:
         line["batched"] = measure_batched(imex, workloads, min(args.steps, 200), stream, flush)
+        line["learned_pcg"] = measure_learned_pcg(imex, w, min(args.steps, 20), stream, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n_act_cpu, secs = cpu_oracle_rate(w, args.cpu_steps)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -676,17 +676,22 @@ __device__ __forceinline__ double grid_total(const double* part, int slot) {
   return s;
 }
 
+// One row of a CSR product; four independent gathers in flight per thread.
 __device__ __forceinline__ double csr_row_dot(const int* ptr, const int* col, const double* val, const double* v,
                                               int i) {
-  double s0 = 0.0, s1 = 0.0;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int k = ptr[i];
   const int e = ptr[i + 1];
-  for (; k + 2 <= e; k += 2) {
-    s0 = fma(val[k], __ldcg(v + col[k]), s0);
-    s1 = fma(val[k + 1], __ldcg(v + col[k + 1]), s1);
+  for (; k + 4 <= e; k += 4) {
+    const int c0 = col[k], c1 = col[k + 1], c2 = col[k + 2], c3 = col[k + 3];
+    const double x0 = __ldcg(v + c0), x1 = __ldcg(v + c1), x2 = __ldcg(v + c2), x3 = __ldcg(v + c3);
+    s0 = fma(val[k], x0, s0);
+    s1 = fma(val[k + 1], x1, s1);
+    s2 = fma(val[k + 2], x2, s2);
+    s3 = fma(val[k + 3], x3, s3);
   }
-  if (k < e) s0 = fma(val[k], __ldcg(v + col[k]), s0);
-  return s0 + s1;
+  for (; k < e; ++k) s0 = fma(val[k], __ldcg(v + col[k]), s0);
+  return (s0 + s1) + (s2 + s3);
 }
 
 __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
@@ -2262,7 +2267,10 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg, kThreads, 0);
       int nsm = 0;
       e = e ? e : cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-      c->pcg_grid = std::max(1, std::min(std::min(nsm, 1024), nsm * occ));
+      // About one row per thread, at most one CTA per SM: fewer CTAs make the
+      // grid barriers cheaper on small partitions.
+      const int rows_ctas = (int)std::max<int64_t>(1, (hs.n_c + kThreads - 1) / kThreads);
+      c->pcg_grid = std::max(1, std::min({nsm, 1024, nsm * occ, rows_ctas}));
     }
     e = e ? e : upload(c->Kpair, plan.Kpair);
     e = e ? e : upload(c->kp_off, plan.kp_off);
