@@ -228,25 +228,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
-
-
-def reduce_max(x, ws, device):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def barrier(ws):
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+from paper_2310_14712_gb300.replicas import barrier, dist_env, reduce_max  # noqa: E402
 
 
 def cpu_oracle_rate(w, nsteps, warmup=1):
