@@ -262,6 +262,253 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
 }
 
 // ---------------------------------------------------------------------------
+// A1 + A2 (+ A3) in 3D: the same tensor-grid scheme with three passes.  A
+// tile owns OX^3 nodes (TC^3 cells); u is staged with one halo cell on the
+// low side of each axis.
+//   x pass: TK = (sx K1)_x u, TM = (M1)_x u          (every staged (z, y) row)
+//   y pass: AB = (M1)_y TK + (sy K1)_y TM, C = (M1)_y TM   (staged z, owned x)
+//   z pass: r = (M1)_z AB + (sz K1)_z C              (owned y, x)
+// each pass cell by cell, the two cell contributions at a vertex plane added
+// in a fix-up pass.  For an I_d node every surrounding cell is uncut, so r is
+// its row of K^d u_n (Eq. Kd).  The 1D products use the even-odd form of K1
+// and the rank-one form of M1, as in 2D.
+
+// o = (s K1) v on axis ax (even-odd form).
+template <int P>
+__device__ __forceinline__ void k1d3(const Ops3D& ops, int ax, const double (&v)[P], double (&o)[P]) {
+  constexpr int H = P / 2;
+  constexpr bool kOdd = (P % 2) == 1;
+  double e[H], od[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = v[j] + v[P - 1 - j];
+    od[j] = v[j] - v[P - 1 - j];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    double ev = kOdd ? ops.kc[ax][i] * v[H] : 0.0, odd = 0.0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      ev = fma(ops.ke[ax][i][j], e[j], ev);
+      odd = fma(ops.ko[ax][i][j], od[j], odd);
+    }
+    o[i] = ev + odd;
+    o[P - 1 - i] = ev - odd;
+  }
+  if (kOdd) {
+    double ev = ops.kc[ax][H] * v[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) ev = fma(ops.ke[ax][H][j], e[j], ev);
+    o[H] = ev;
+  }
+}
+
+// a^T v for the rank-one part of M1.
+template <int P>
+__device__ __forceinline__ double m1d3_sa(const Ops3D& ops, const double (&v)[P]) {
+  constexpr int H = P / 2;
+  constexpr bool kOdd = (P % 2) == 1;
+  double sa = kOdd ? ops.a[H] * v[H] : 0.0;
+#pragma unroll
+  for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? v[j] + v[P - 1 - j] : v[j] - v[P - 1 - j], sa);
+  return sa;
+}
+
+template <int P, int TC>
+__global__ void __launch_bounds__(kThreads) k_explicit3d(ExplicitArgs a, Ops3D ops) {
+  constexpr int p = P - 1;
+  constexpr int OX = TC * p;
+  constexpr int R = (TC + 1) * p + 1;   // staged nodes per axis
+  constexpr int NC = TC + 1;            // staged cells per axis
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x;
+  const int ntiles = a.ntx * a.nty * a.ntz;
+  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
+  const double* Uc = a.U + on;
+  const double* Wc = a.W + on;     // may alias OUTc
+  double* OUTc = a.OUT + on;
+  const double* fxc = a.fx + on;
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+
+  if ((int)blockIdx.x >= ntiles) {
+    // Newmark prediction on I_c (Fig. TrapCDMIMEX, "Prediction").
+    const double c1 = a.dt, c2 = (0.5 - kNewmarkBeta) * a.dt * a.dt;
+    const int stride = (gridDim.x - ntiles) * blockDim.x;
+    for (int r = (blockIdx.x - ntiles) * blockDim.x + tid; r < a.n_c; r += stride) {
+      const int node = a.c_node[r];
+      OUTc[node] = Uc[node] + c1 * a.v_c[oc + r] + c2 * a.a_c[oc + r];
+    }
+    return;
+  }
+
+  double* su = sm;                          // R^3
+  double* TK = su + R * R * R;              // R x R x OX
+  double* TM = TK + R * R * OX;
+  double* reg = TM + R * R * OX;            // x-pass partials, then y-pass arrays
+  double* xlk = reg;                        // R*R x NC each
+  double* xrk = xlk + R * R * NC;
+  double* xlm = xrk + R * R * NC;
+  double* xrm = xlm + R * R * NC;
+  double* AB = reg;                         // R x OX(y) x OX(x)
+  double* CC = AB + R * OX * OX;
+  double* ylab = CC + R * OX * OX;          // R x NC x OX each
+  double* yrab = ylab + R * NC * OX;
+  double* ylc = yrab + R * NC * OX;
+  double* yrc = ylc + R * NC * OX;
+  double* rr = TK;                          // OX^3 (aliases TK/TM after the y pass)
+  double* zl = rr + OX * OX * OX;           // NC x OX x OX each
+  double* zr = zl + NC * OX * OX;
+
+  const int tile = blockIdx.x;
+  const int tx = tile % a.ntx, ty = (tile / a.ntx) % a.nty, tz = tile / (a.ntx * a.nty);
+  const int X0 = tx * OX, Y0 = ty * OX, Z0 = tz * OX;
+  const int cx0 = X0 / p - 1, cy0 = Y0 / p - 1, cz0 = Z0 / p - 1;
+  const int64_t nxy = (int64_t)a.nx * a.ny;
+
+  for (int idx = tid; idx < R * R * R; idx += kThreads) {
+    const int zz = idx / (R * R), yy = (idx / R) % R, xx = idx % R;
+    const int gx = X0 - p + xx, gy = Y0 - p + yy, gz = Z0 - p + zz;
+    su[idx] = (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz)
+                  ? Uc[(int64_t)gz * nxy + (int64_t)gy * a.nx + gx]
+                  : 0.0;
+  }
+  __syncthreads();
+
+  // x pass: item = (row zy, cell cc), rows fastest.
+  for (int it = tid; it < R * R * NC; it += kThreads) {
+    const int cc = it / (R * R), zy = it - cc * (R * R);
+    const int cx = cx0 + cc;
+    double ok[P], om[P];
+    if (cx < 0 || cx >= a.ncx) {
+#pragma unroll
+      for (int i = 0; i < P; ++i) ok[i] = om[i] = 0.0;
+    } else {
+      double v[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) v[j] = su[zy * R + cc * p + j];
+      k1d3<P>(ops, 0, v, ok);
+      const double sa = m1d3_sa<P>(ops, v);
+#pragma unroll
+      for (int i = 0; i < P; ++i) om[i] = fma(ops.w[i], v[i], ops.ca[i] * sa);
+    }
+    if (cc >= 1) {
+#pragma unroll
+      for (int i = 1; i < p; ++i) {
+        TK[zy * OX + (cc - 1) * p + i] = ok[i];
+        TM[zy * OX + (cc - 1) * p + i] = om[i];
+      }
+    }
+    xlk[zy * NC + cc] = ok[0];
+    xrk[zy * NC + cc] = ok[p];
+    xlm[zy * NC + cc] = om[0];
+    xrm[zy * NC + cc] = om[p];
+  }
+  __syncthreads();
+  for (int it = tid; it < R * R * TC; it += kThreads) {
+    const int k = it / (R * R), zy = it - k * (R * R);
+    TK[zy * OX + k * p] = xrk[zy * NC + k] + xlk[zy * NC + k + 1];
+    TM[zy * OX + k * p] = xrm[zy * NC + k] + xlm[zy * NC + k + 1];
+  }
+  __syncthreads();
+
+  // y pass: item = (z, x, cell row cr), x fastest.
+  for (int it = tid; it < R * OX * NC; it += kThreads) {
+    const int cr = it / (R * OX), rem = it - cr * (R * OX);
+    const int z = rem / OX, x = rem - z * OX;
+    const int cy = cy0 + cr;
+    double ab[P], cm[P];
+    if (cy < 0 || cy >= a.ncy) {
+#pragma unroll
+      for (int i = 0; i < P; ++i) ab[i] = cm[i] = 0.0;
+    } else {
+      double va[P], vb[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        va[j] = TK[(z * R + cr * p + j) * OX + x];
+        vb[j] = TM[(z * R + cr * p + j) * OX + x];
+      }
+      double kb[P];
+      k1d3<P>(ops, 1, vb, kb);
+      const double sa = m1d3_sa<P>(ops, va), sb = m1d3_sa<P>(ops, vb);
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        ab[i] = fma(ops.w[i], va[i], fma(ops.ca[i], sa, kb[i]));
+        cm[i] = fma(ops.w[i], vb[i], ops.ca[i] * sb);
+      }
+    }
+    if (cr >= 1) {
+#pragma unroll
+      for (int i = 1; i < p; ++i) {
+        AB[(z * OX + (cr - 1) * p + i) * OX + x] = ab[i];
+        CC[(z * OX + (cr - 1) * p + i) * OX + x] = cm[i];
+      }
+    }
+    ylab[(z * NC + cr) * OX + x] = ab[0];
+    yrab[(z * NC + cr) * OX + x] = ab[p];
+    ylc[(z * NC + cr) * OX + x] = cm[0];
+    yrc[(z * NC + cr) * OX + x] = cm[p];
+  }
+  __syncthreads();
+  for (int it = tid; it < R * TC * OX; it += kThreads) {
+    const int k = it / (R * OX), rem = it - k * (R * OX);
+    const int z = rem / OX, x = rem - z * OX;
+    AB[(z * OX + k * p) * OX + x] = yrab[(z * NC + k) * OX + x] + ylab[(z * NC + k + 1) * OX + x];
+    CC[(z * OX + k * p) * OX + x] = yrc[(z * NC + k) * OX + x] + ylc[(z * NC + k + 1) * OX + x];
+  }
+  __syncthreads();
+
+  // z pass: item = (y, x, cell layer cl), x fastest.
+  for (int it = tid; it < OX * OX * NC; it += kThreads) {
+    const int cl = it / (OX * OX), yx = it - cl * (OX * OX);
+    const int cz = cz0 + cl;
+    double o[P];
+    if (cz < 0 || cz >= a.ncz) {
+#pragma unroll
+      for (int i = 0; i < P; ++i) o[i] = 0.0;
+    } else {
+      double va[P], vb[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        va[j] = AB[(cl * p + j) * OX * OX + yx];
+        vb[j] = CC[(cl * p + j) * OX * OX + yx];
+      }
+      double kb[P];
+      k1d3<P>(ops, 2, vb, kb);
+      const double sa = m1d3_sa<P>(ops, va);
+#pragma unroll
+      for (int i = 0; i < P; ++i) o[i] = fma(ops.w[i], va[i], fma(ops.ca[i], sa, kb[i]));
+    }
+    if (cl >= 1) {
+#pragma unroll
+      for (int i = 1; i < p; ++i) rr[((cl - 1) * p + i) * OX * OX + yx] = o[i];
+    }
+    zl[cl * OX * OX + yx] = o[0];
+    zr[cl * OX * OX + yx] = o[p];
+  }
+  __syncthreads();
+  for (int it = tid; it < TC * OX * OX; it += kThreads) {
+    const int k = it / (OX * OX), yx = it - k * (OX * OX);
+    rr[(k * p) * OX * OX + yx] = zr[k * OX * OX + yx] + zl[(k + 1) * OX * OX + yx];
+  }
+  __syncthreads();
+
+  // CDM update of the owned I_d nodes (Eqs. CDMacc, CDMstep).
+  const double ft = a.ft_dev ? a.ft_dev[0] : a.ft;
+  for (int it = tid; it < OX * OX * OX; it += kThreads) {
+    const int zo = it / (OX * OX), yo = (it / OX) % OX, xo = it % OX;
+    const int gx = X0 + xo, gy = Y0 + yo, gz = Z0 + zo;
+    if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
+    const int64_t g = (int64_t)gz * nxy + (int64_t)gy * a.nx + gx;
+    if (a.cls[g] != NODE_D) continue;
+    const double r = rr[it];
+    const double u = su[((zo + p) * R + yo + p) * R + xo + p];
+    const double minv = a.winv_x[gx] * a.winv_y[gy] * a.winv_z[gz];
+    const double acc = minv * (ft * fxc[g] - r);
+    OUTc[g] = a.cu * u + a.cw * Wc[g] + a.ca * acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // A4 + A5 + A6: the implicit solve S a = f_t(t_{n+1}) f_x^c - K^c u_pred with
 // the supernodal nested-dissection Cholesky factor of S, and the Newmark
 // correction.  Per component, the lower levels of the dissection tree are
@@ -443,7 +690,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
   const int64_t boff = a.blob_off[cta];
   if (kSmem) async_copy_16(blob, a.blob + boff, a.blob_len[cta] / 2);
   async_copy_16(il, a.ilist + a.ilist_off[cta], a.ilist_len[cta] / 4);
-  if (kForward && a.first) async_copy_16(kp, a.Kpair + a.kp_off[cta], a.kp_len[cta] / 2);
+  if (kForward && a.first && a.kp_smem) async_copy_16(kp, a.Kpair + a.kp_off[cta], a.kp_len[cta] / 2);
+  const double* KP = (kForward && a.first && !a.kp_smem) ? a.Kpair + a.kp_off[cta] : kp;
   const double* B = kSmem ? blob : a.blob + boff;
   // Let the next launch stage its constants.
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
@@ -474,7 +722,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
       const int npair = il[4], nrhs = il[3];
       const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
       const int np = il[5];
-      for (int k = tid; k < npair; k += kThreads) pc[k] = pair_product(a, src, kp, np, k, L.pair[4 * k], s_off);
+      for (int k = tid; k < npair; k += kThreads) pc[k] = pair_product(a, src, KP, np, k, L.pair[4 * k], s_off);
       __syncthreads();
       for (int k = tid; k < nrhs; k += kThreads) {
         const int* rr = L.rhs + 4 * k;
@@ -894,6 +1142,14 @@ __global__ void k_gather_nodes(double* out, const double* u, const int64_t* node
 // large | small overrides).
 constexpr int kTileLarge[10] = {0, 0, 16, 16, 10, 8, 6, 5, 4, 4};
 constexpr int kTileSmall[10] = {0, 0, 8, 8, 5, 4, 3, 3, 2, 2};
+// 3D (P <= 5): tiles of TC^3 cells.
+constexpr int kTileLarge3[6] = {0, 0, 8, 4, 3, 3};
+constexpr int kTileSmall3[6] = {0, 0, 4, 2, 2, 2};
+
+size_t explicit_smem_doubles3(int P, int TC) {
+  const size_t p = P - 1, OX = TC * p, R = (TC + 1) * p + 1, NC = TC + 1;
+  return R * R * R + 2 * R * R * OX + std::max(4 * R * R * NC, 2 * R * OX * OX + 4 * R * NC * OX);
+}
 
 size_t explicit_smem_doubles(int P, int TC) {
   const int p = P - 1, OX = TC * p, OY = OX, RX = (TC + 1) * p + 1, RY = RX, NC = TC + 1;
@@ -916,7 +1172,7 @@ struct imex_ctx {
   double *U[2] = {nullptr, nullptr};
   double* tmp = nullptr;    // full grid scratch (initial velocity, exports)
   double* fx = nullptr;
-  double *winv_x = nullptr, *winv_y = nullptr;
+  double *winv_x = nullptr, *winv_y = nullptr, *winv_z = nullptr;
   uint8_t* cls = nullptr;
   // implicit partition
   int* c_node = nullptr;
@@ -925,6 +1181,7 @@ struct imex_ctx {
   double *Kpair = nullptr, *rhs0 = nullptr;
   int64_t *kp_off = nullptr, *kp_len = nullptr;
   int64_t walk_max_kp = 0;
+  int walk_kp_smem = 1;   // cell-matrix rows of the pairs staged in shared memory
   // solve: per-CTA factor blobs (S and M^cc) and index lists, dense tops, scratch
   double *blob_S = nullptr, *blob_M = nullptr;
   int64_t *blob_off = nullptr, *blob_len = nullptr;
@@ -973,7 +1230,8 @@ struct imex_ctx {
   int64_t step = 0;
   cudaStream_t stream = nullptr;
   Ops2D ops{};
-  int TC = 4, ntx = 1, nty = 1;
+  int TC = 4, ntx = 1, nty = 1, ntz = 1;
+  Ops3D ops3{};
   int tile_small = 0;             // explicit tile: 0 large, 1 small (autotuned at setup)
   float tile_us[2] = {0.f, 0.f};  // measured explicit launch time of each candidate
   int explicit_per_sm = 1;    // resident CTAs of the explicit kernel per SM
@@ -1014,7 +1272,24 @@ void launch_explicit(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t
     k_explicit2d<P, kTileLarge[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
 }
 
+template <int P>
+void launch_explicit3(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t s) {
+  if (c->tile_small)
+    k_explicit3d<P, kTileSmall3[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops3);
+  else
+    k_explicit3d<P, kTileLarge3[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops3);
+}
+
 void explicit_dispatch(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t s) {
+  if (c->hs.dim == 3) {
+    switch (c->hs.P) {
+      case 2: launch_explicit3<2>(c, ea, grid, s); break;
+      case 3: launch_explicit3<3>(c, ea, grid, s); break;
+      case 4: launch_explicit3<4>(c, ea, grid, s); break;
+      case 5: launch_explicit3<5>(c, ea, grid, s); break;
+    }
+    return;
+  }
   switch (c->hs.P) {
     case 2: launch_explicit<2>(c, ea, grid, s); break;
     case 3: launch_explicit<3>(c, ea, grid, s); break;
@@ -1035,7 +1310,23 @@ cudaError_t explicit_config(bool small, size_t bytes, int* per_sm) {
   return e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kThreads, bytes);
 }
 
-cudaError_t explicit_config_dispatch(int P, bool small, size_t bytes, int* per_sm) {
+template <int P>
+cudaError_t explicit_config3(bool small, size_t bytes, int* per_sm) {
+  auto fn = small ? k_explicit3d<P, kTileSmall3[P]> : k_explicit3d<P, kTileLarge3[P]>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kThreads, bytes);
+}
+
+cudaError_t explicit_config_dispatch(int dim, int P, bool small, size_t bytes, int* per_sm) {
+  if (dim == 3) {
+    switch (P) {
+      case 2: return explicit_config3<2>(small, bytes, per_sm);
+      case 3: return explicit_config3<3>(small, bytes, per_sm);
+      case 4: return explicit_config3<4>(small, bytes, per_sm);
+      case 5: return explicit_config3<5>(small, bytes, per_sm);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (P) {
     case 2: return explicit_config<2>(small, bytes, per_sm);
     case 3: return explicit_config<3>(small, bytes, per_sm);
@@ -1053,16 +1344,20 @@ cudaError_t explicit_config_dispatch(int P, bool small, size_t bytes, int* per_s
 cudaError_t use_tile(imex_ctx* c, bool small) {
   const HostSetup& hs = c->hs;
   c->tile_small = small ? 1 : 0;
-  c->TC = small ? kTileSmall[hs.P] : kTileLarge[hs.P];
+  const bool d3 = hs.dim == 3;
+  c->TC = d3 ? (small ? kTileSmall3[hs.P] : kTileLarge3[hs.P]) : (small ? kTileSmall[hs.P] : kTileLarge[hs.P]);
   const int OX = c->TC * hs.p;
   c->ntx = (hs.nn[0] + OX - 1) / OX;
   c->nty = (hs.nn[1] + OX - 1) / OX;
-  c->smem_explicit = explicit_smem_doubles(hs.P, c->TC) * sizeof(double);
+  c->ntz = d3 ? (hs.nn[2] + OX - 1) / OX : 1;
+  c->smem_explicit = (d3 ? explicit_smem_doubles3(hs.P, c->TC) : explicit_smem_doubles(hs.P, c->TC)) * sizeof(double);
   int per_sm = 0;
-  cudaError_t e = explicit_config_dispatch(hs.P, small, c->smem_explicit, &per_sm);
+  cudaError_t e = explicit_config_dispatch(hs.dim, hs.P, small, c->smem_explicit, &per_sm);
   c->explicit_per_sm = std::max(1, per_sm);
   return e;
 }
+
+int ntiles(const imex_ctx* c) { return c->ntx * c->nty * c->ntz; }
 
 ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double* OUT, double cu, double cw,
                            double ca, double ft, bool predict) {
@@ -1075,12 +1370,16 @@ ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double
   ea.fx = c->fx;
   ea.winv_x = c->winv_x;
   ea.winv_y = c->winv_y;
+  ea.winv_z = c->winv_z;
   ea.nx = hs.nn[0];
   ea.ny = hs.nn[1];
+  ea.nz = hs.dim == 3 ? hs.nn[2] : 1;
   ea.ncx = hs.pb.ncells[0];
   ea.ncy = hs.pb.ncells[1];
+  ea.ncz = hs.dim == 3 ? hs.pb.ncells[2] : 1;
   ea.ntx = c->ntx;
   ea.nty = c->nty;
+  ea.ntz = c->ntz;
   ea.cu = cu;
   ea.cw = cw;
   ea.ca = ca;
@@ -1102,7 +1401,7 @@ ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double
 // SMs.  At least one, at most one per 256 rows.
 int pred_blocks(imex_ctx* c, bool predict) {
   if (!predict || c->hs.n_c == 0) return 0;
-  const int64_t tiles = (int64_t)c->ntx * c->nty;
+  const int64_t tiles = (int64_t)ntiles(c);
   const int64_t nsm = std::max(1, c->num_sms);
   const int64_t per_sm = std::min<int64_t>((tiles + nsm - 1) / nsm, std::max(1, c->explicit_per_sm));
   int64_t spare = (per_sm * nsm - tiles % (per_sm * nsm)) % (per_sm * nsm);
@@ -1140,6 +1439,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   w.kp_off = c->kp_off;
   w.kp_len = c->kp_len;
   w.max_kp = c->walk_max_kp;
+  w.kp_smem = c->walk_kp_smem;
   w.P = hs.P;
   w.Pd = hs.Pd;
   w.dim = hs.dim;
@@ -1254,9 +1554,9 @@ cudaError_t autotune_tile(imex_ctx* c) {
     e = use_tile(c, small);
     if (e != cudaSuccess) break;
     ExplicitArgs ea = explicit_args(c, c->U[0], c->tmp, c->tmp, 2.0, -1.0, hs.dt * hs.dt, 0.0, false);
-    explicit_dispatch(c, ea, c->ntx * c->nty, nullptr);
+    explicit_dispatch(c, ea, ntiles(c), nullptr);
     e = cudaEventRecord(ev[0], nullptr);
-    for (int r = 0; r < 5 && e == cudaSuccess; ++r) explicit_dispatch(c, ea, c->ntx * c->nty, nullptr);
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) explicit_dispatch(c, ea, ntiles(c), nullptr);
     e = e ? e : cudaEventRecord(ev[1], nullptr);
     e = e ? e : cudaEventSynchronize(ev[1]);
     float ms = 0.f;
@@ -1323,7 +1623,7 @@ int compute_initial(imex_ctx* c, cudaStream_t s) {
   const double dt = hs.dt;
   const double ft0 = wavelet_value(hs.pb.wavelet, hs.pb.f0, 0.0);
   ExplicitArgs ea = explicit_args(c, U0, c->tmp, Uo, 1.0, -dt, 0.5 * dt * dt, ft0, false);
-  explicit_dispatch(c, ea, c->ntx * c->nty, s);
+  explicit_dispatch(c, ea, ntiles(c), s);
   if (int rc = check_launch("explicit (initial)")) return rc;
   if (hs.n_c > 0) {
     const int nc = (int)hs.n_c;
@@ -1606,8 +1906,14 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
       return (b | 1) * b + (m | 1) * b + 2 * b + m + (Pd + 1) * pairs + (ints + 1) / 2 + 2;
     };
     int target = std::max(1, std::min<int>((int)nodes.size(), kTargetCTAs));
-    if (l == 0)
-      target = std::max(target, (int)std::min<int64_t>(kTargetCTAs, ((int64_t)extra_rows.size() + 31) / 32));
+    if (l == 0) {
+      int64_t extra_pairs = 0;
+      for (int r : extra_rows) extra_pairs += npairs_of(r);
+      // at most 32 extra rows and about 48 KB of their cell-matrix rows per CTA
+      const int64_t by_pairs = (extra_pairs * (Pd + 1) * (int64_t)sizeof(double) + 49151) / 49152;
+      target = std::max(target, (int)std::min<int64_t>(kTargetCTAs, std::max<int64_t>(
+                                                                          ((int64_t)extra_rows.size() + 31) / 32, by_pairs)));
+    }
     std::vector<std::vector<int>> per(target);
     std::vector<int64_t> work(target, 0), used(target, 0);
     for (int t : nodes) {
@@ -1940,6 +2246,28 @@ int explicit_ops(const HostSetup& hs, double sx, double sy, Ops2D& ops) {
   return IMEX_OK;
 }
 
+// 3D: even-odd stiffness per axis (scales s3) and the rank-one mass, from
+// the 2D routine (whose checks apply to the same 1D matrices).
+int explicit_ops3(const HostSetup& hs, const double* s3, Ops3D& ops) {
+  Ops2D a{}, b{};
+  if (int rc = explicit_ops(hs, s3[0], s3[1], a)) return rc;
+  if (int rc = explicit_ops(hs, s3[2], s3[2], b)) return rc;
+  ops = Ops3D{};
+  std::memcpy(ops.ke[0], a.kxe, sizeof(a.kxe));
+  std::memcpy(ops.ko[0], a.kxo, sizeof(a.kxo));
+  std::memcpy(ops.kc[0], a.kxc, sizeof(a.kxc));
+  std::memcpy(ops.ke[1], a.kye, sizeof(a.kye));
+  std::memcpy(ops.ko[1], a.kyo, sizeof(a.kyo));
+  std::memcpy(ops.kc[1], a.kyc, sizeof(a.kyc));
+  std::memcpy(ops.ke[2], b.kxe, sizeof(b.kxe));
+  std::memcpy(ops.ko[2], b.kxo, sizeof(b.kxo));
+  std::memcpy(ops.kc[2], b.kxc, sizeof(b.kxc));
+  std::memcpy(ops.w, a.w, sizeof(a.w));
+  std::memcpy(ops.ca, a.ca, sizeof(a.ca));
+  std::memcpy(ops.a, a.a, sizeof(a.a));
+  return IMEX_OK;
+}
+
 int build_context(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src,
                   Problem& pb) {
   if (!mesh || !src) return fail(IMEX_ERR_ARG, "mesh and source must not be NULL");
@@ -2059,7 +2387,7 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
     if (ncols < 1 || ncols > kMaxCols) return fail(IMEX_ERR_ARG, "ncols must be in [1, 256]");
     if (ncols > 1 && ncols != pb.nsrc) return fail(IMEX_ERR_ARG, "ncols > 1 needs one source per column");
     pb.ncols = ncols;
-    if (pb.dim != 2) return fail(IMEX_ERR_ARG, "the GPU time stepper supports dim = 2");
+    if (pb.dim == 3 && pb.p > 4) return fail(IMEX_ERR_ARG, "the 3D GPU time stepper supports p <= 4");
     c = new imex_ctx();
     c->ncols = ncols;
     std::string err = build_setup(pb, c->hs);
@@ -2087,19 +2415,29 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
     c->nty = (hs.nn[1] + OX - 1) / OX;
     c->smem_explicit = explicit_smem_doubles(P, c->TC) * sizeof(double);
 
-    // Operators of the explicit apply: sx = rho c^2 h_y / h_x, sy = rho c^2 h_x / h_y.
-    const double sx = pb.rho * pb.c0 * pb.c0 * hs.h[1] / hs.h[0];
-    const double sy = pb.rho * pb.c0 * pb.c0 * hs.h[0] / hs.h[1];
-    if (int rc = explicit_ops(hs, sx, sy, c->ops)) {
-      delete c;
-      return rc;
+    // Operators of the explicit apply: in 2D sx = rho c^2 h_y / h_x,
+    // sy = rho c^2 h_x / h_y (|J| (2/h_d)^2 with |J| = h_x h_y / 4); in 3D
+    // sx = rho c^2 h_y h_z / (2 h_x) and cyclic (|J| = h_x h_y h_z / 8).
+    const double rc2 = pb.rho * pb.c0 * pb.c0;
+    if (hs.dim == 2) {
+      if (int rc = explicit_ops(hs, rc2 * hs.h[1] / hs.h[0], rc2 * hs.h[0] / hs.h[1], c->ops)) {
+        delete c;
+        return rc;
+      }
+    } else {
+      const double s3[3] = {0.5 * rc2 * hs.h[1] * hs.h[2] / hs.h[0], 0.5 * rc2 * hs.h[0] * hs.h[2] / hs.h[1],
+                            0.5 * rc2 * hs.h[0] * hs.h[1] / hs.h[2]};
+      if (int rc = explicit_ops3(hs, s3, c->ops3)) {
+        delete c;
+        return rc;
+      }
     }
     if (!pb.cell_c.empty()) {
       delete c;
       return fail(IMEX_ERR_ARG, "per-cell wave speed is not supported by the 2D explicit kernel");
     }
     // Assembled GLL weights per node column/row; lumped mass = rho |J| W_x W_y.
-    std::vector<double> wx(hs.nn[0]), wy(hs.nn[1]);
+    std::vector<double> wx(hs.nn[0]), wy(hs.nn[1]), wz(hs.dim == 3 ? hs.nn[2] : 1, 1.0);
     auto assembled = [&](int i, int n) {
       const int loc = i % hs.p;
       if (loc != 0) return hs.gll_w[loc];
@@ -2108,9 +2446,16 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
       if (i < n - 1) w += hs.gll_w[0];
       return w;
     };
-    const double jac = 0.25 * hs.h[0] * hs.h[1];
-    for (int i = 0; i < hs.nn[0]; ++i) wx[i] = 1.0 / assembled(i, hs.nn[0]);
-    for (int i = 0; i < hs.nn[1]; ++i) wy[i] = 1.0 / (assembled(i, hs.nn[1]) * pb.rho * jac);
+    if (hs.dim == 2) {
+      const double jac = 0.25 * hs.h[0] * hs.h[1];
+      for (int i = 0; i < hs.nn[0]; ++i) wx[i] = 1.0 / assembled(i, hs.nn[0]);
+      for (int i = 0; i < hs.nn[1]; ++i) wy[i] = 1.0 / (assembled(i, hs.nn[1]) * pb.rho * jac);
+    } else {
+      const double jac = 0.125 * hs.h[0] * hs.h[1] * hs.h[2];
+      for (int i = 0; i < hs.nn[0]; ++i) wx[i] = 1.0 / assembled(i, hs.nn[0]);
+      for (int i = 0; i < hs.nn[1]; ++i) wy[i] = 1.0 / assembled(i, hs.nn[1]);
+      for (int i = 0; i < hs.nn[2]; ++i) wz[i] = 1.0 / (assembled(i, hs.nn[2]) * pb.rho * jac);
+    }
 
     // Compact per-c arrays and tree metadata.
     const int64_t nn = hs.nnodes, nc = hs.n_c, nt = (int64_t)hs.tree.size();
@@ -2134,13 +2479,19 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
       c->walk_max_slots = plan.max_slots;
       c->walk_max_m = plan.max_m;
       c->walk_max_pairs = plan.max_pairs;
-      c->walk_max_kp = plan.max_kp + (plan.max_kp & 1);
-      const size_t vec = (size_t)(c->walk_max_kp + 2 * plan.max_slots + plan.max_m + plan.max_pairs) * sizeof(double);
-      const size_t lists = (size_t)plan.max_ilist * sizeof(int);
-      const size_t staged = vec + (size_t)plan.max_blob * sizeof(double) + lists;
-      c->walk_smem_mode = staged <= kMaxDynSmem ? 1 : 0;
+      // Shared memory of a walk CTA: vectors and index lists always; the
+      // cell-matrix rows of the pairs and the factor blocks when they fit
+      // (otherwise they are read from global memory).
+      const size_t kp = (size_t)(plan.max_kp + (plan.max_kp & 1)) * sizeof(double);
+      const size_t blob = (size_t)plan.max_blob * sizeof(double);
+      const size_t base = (size_t)(2 * plan.max_slots + plan.max_m + plan.max_pairs) * sizeof(double) +
+                          (size_t)plan.max_ilist * sizeof(int);
+      c->walk_kp_smem = base + kp <= kMaxDynSmem ? 1 : 0;
+      c->walk_max_kp = c->walk_kp_smem ? (plan.max_kp + (plan.max_kp & 1)) : 0;
+      const size_t used = base + (c->walk_kp_smem ? kp : 0);
+      c->walk_smem_mode = used + blob <= kMaxDynSmem ? 1 : 0;
       c->walk_max_blob = c->walk_smem_mode ? plan.max_blob : 0;
-      c->smem_walk = c->walk_smem_mode ? staged : vec + lists;
+      c->smem_walk = used + (c->walk_smem_mode ? blob : 0);
       c->lev_has_nodes = plan.lev_has_nodes;
       c->top_max_zn = std::max(2, plan.max_zn + (plan.max_zn & 1));
       c->top_max_arows = plan.max_arows;
@@ -2166,6 +2517,7 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
     ar.add(&c->fx, nn * ncols);
     ar.add(&c->winv_x, hs.nn[0]);
     ar.add(&c->winv_y, hs.nn[1]);
+    ar.add(&c->winv_z, wz.size());
     ar.add(&c->cls, nn);
     ar.add(&c->c_node, std::max<int64_t>(nc, 1));
     ar.add(&c->v_c, std::max<int64_t>(nc, 1) * ncols);
@@ -2246,6 +2598,7 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
     e = e ? e : upload(c->fx, hs.fx);
     e = e ? e : upload(c->winv_x, wx);
     e = e ? e : upload(c->winv_y, wy);
+    e = e ? e : upload(c->winv_z, wz);
     e = e ? e : upload(c->cls, hs.node_class);
     e = e ? e : upload(c->c_node, hs.c_node);
     e = e ? e : upload(c->fxc, fxc);
@@ -2341,7 +2694,7 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
   if (ev) cudaEventRecord(ev[0], s);
   ExplicitArgs ea = explicit_args(c, Ucur, Unext, Unext, 2.0, -1.0, dt * dt, ft_at(hs, step), true);
   ea.ft_dev = ft_dev;
-  explicit_dispatch(c, ea, c->ntx * c->nty + pred_blocks(c, true), s);
+  explicit_dispatch(c, ea, ntiles(c) + pred_blocks(c, true), s);
   if (ev) cudaEventRecord(ev[1], s);
   if (hs.n_c > 0) {
     if (c->solver == IMEX_SOLVER_DIRECT) {
@@ -2714,7 +3067,7 @@ extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
     double* Unext = c->U[1 - c->cur];
     const int64_t step = c->step;
     ExplicitArgs ea = explicit_args(c, Ucur, Unext, Unext, 2.0, -1.0, dt * dt, ft_at(hs, step), true);
-    explicit_dispatch(c, ea, c->ntx * c->nty + pred_blocks(c, true), s);
+    explicit_dispatch(c, ea, ntiles(c) + pred_blocks(c, true), s);
     if (hs.n_c > 0) launch_solve_chain(c, true, ft_at(hs, step + 1), nullptr, 0, Unext, Unext, upd, sol, rhs0, s);
     if (int rc = check_launch("imex_step_noalloc")) return rc;
     c->cur = 1 - c->cur;

@@ -55,6 +55,15 @@ struct Ops2D {
   double w[9], ca[9], a[9];
 };
 
+// 1D operators of the 3D explicit apply:
+//   r = sx (M1_z (x) M1_y (x) K1_x) u + sy (M1_z (x) K1_y (x) M1_x) u
+//     + sz (K1_z (x) M1_y (x) M1_x) u
+// K1 in even-odd form per axis (scaled by sx, sy, sz), M1 = diag(w) + C a a^T.
+struct Ops3D {
+  double ke[3][5][4], ko[3][4][4], kc[3][5];
+  double w[9], ca[9], a[9];
+};
+
 struct ExplicitArgs {
   const double* U;        // u_n (full grid)
   const double* W;        // u_{n-1} (step) or v_0 (init), full grid
@@ -62,10 +71,11 @@ struct ExplicitArgs {
   const uint8_t* cls;     // node class (0 inactive, 1 I_d, 2 I_c)
   const double* fx;       // f_x, full grid
   const double* winv_x;   // 1 / assembled GLL weight along x, per node column
-  const double* winv_y;   // idem along y, scaled by dt-independent 1/(rho |J|)
-  int nx, ny;             // nodes per axis
-  int ncx, ncy;           // cells per axis
-  int ntx, nty;           // tiles per axis
+  const double* winv_y;   // idem along y (2D: scaled by dt-independent 1/(rho |J|))
+  const double* winv_z;   // 3D: idem along z, scaled by 1/(rho |J|)
+  int nx, ny, nz;         // nodes per axis (nz = 1 in 2D)
+  int ncx, ncy, ncz;      // cells per axis
+  int ntx, nty, ntz;      // tiles per axis
   double cu, cw, ca;      // out = cu u + cw w + ca minv (ft fx - r)
   double ft;              // f_t(t_n)
   const double* ft_dev;   // if set: f_t(t_n) = ft_dev[0] (user-supplied samples)
@@ -103,6 +113,7 @@ struct WalkArgs {
   const int64_t* kp_off;        // [cta] (16-byte aligned)
   const int64_t* kp_len;        // [cta] (even)
   int64_t max_kp;               // doubles reserved for them in shared memory (even)
+  int kp_smem;                  // 1: staged in shared memory; 0: read from global memory
   int P, Pd, dim, nx, ny;
   const double* fxc;
   double ft;                    // f_t(t_{n+1}) (step) or f_t(0) (initial acceleration)
