@@ -41,7 +41,7 @@ def setup(dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0,
         dt = dt_factor * uncut_critical_dt(p, grid.h, rho, cmax)
     ft = sources.wavelet(wavelet, f0)
     s = Setup()
-    s.grid, s.disc, s.dt, s.ft = grid, disc, dt, ft
+    s.grid, s.disc, s.dt, s.ft, s.geom = grid, disc, dt, ft, geom
     s.imex = NewmarkImex(disc.M, disc.K, disc.fx, ft, dt, disc.is_c, disc.is_d)
     return s
 
