@@ -256,6 +256,27 @@ int imex_fsai_kaporin(int n, const int *s_ptr, const int *s_col, const double *s
                       const int *g_col, const double *g_val, double *grad, double *loss, void *stream);
 
 /*
+ * imex_adjoint - misfit J = 1/2 sum_{n=1..N} sum_cols sum_r (u_n[rec_r] - d)^2
+ * of the next N = nsteps steps and its gradient dJ/dc_e with respect to the
+ * wave speed of every cell, by the discrete adjoint of the IMEX step (no
+ * counterpart in the paper, which names full-waveform inversion as the use).
+ *   rec_nodes : nrec canonical node indices (host)
+ *   data      : N x ncols x nrec observed traces (host), entry (n-1, col, r)
+ *               compared with u_n of column col at receiver r
+ *   checkpoint_every : forward states kept every that many steps; each
+ *               segment is recomputed once in the reverse sweep
+ *   grad      : ncells (product of mesh->ncells) host doubles, overwritten
+ *               (0 for empty cells); misfit: host double
+ * Runs forward from the current state and leaves the context N steps later.
+ * The dependence of the starting state on c is not differentiated (it has
+ * none when it is the setup's state u_0 = v_0 = 0).  Uses the factorised
+ * solve; temporary device memory (about (N / checkpoint_every + checkpoint_every)
+ * ncols n_nodes doubles) is allocated for the call.  Synchronous.
+ */
+int imex_adjoint(imex_ctx *ctx, int64_t nsteps, const int64_t *rec_nodes, int nrec, const double *data,
+                 int checkpoint_every, double *grad, double *misfit);
+
+/*
  * imex_fields - copy one field (IMEX_FIELD_*) in canonical layout into dst.
  *   len          : number of doubles in dst; must equal ncols * imex_stats.n_nodes
  *                  (column after column)

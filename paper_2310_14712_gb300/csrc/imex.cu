@@ -590,6 +590,7 @@ struct Corr {
   double* a_c;
   double dt;
   __device__ void row(int r, double acc) const {
+    if (mode == 2) return;   // solve only: the solution stays in sol
     if (mode == 0) {
       const int node = c_node[r];
       const double vpred = v_c[r] + (1.0 - kNewmarkGamma) * dt * a_c[r];
@@ -601,6 +602,7 @@ struct Corr {
   // The same with c_node[r], v_c[r] and a_c[r] loaded beforehand (they are not
   // written by the kernels of the step that run before the correction).
   __device__ void row_pre(int r, double acc, int node, double v_old, double a_old) const {
+    if (mode == 2) return;
     if (mode == 0) {
       const double vpred = v_old + (1.0 - kNewmarkGamma) * dt * a_old;
       U[node] = U[node] + kNewmarkBeta * dt * dt * acc;
@@ -718,7 +720,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
   if (a.skip && *a.skip) return;   // the iterative solve converged: nothing to do
   if (kForward) {
-    if (a.first) {
+    if (a.first && a.rhs_given) {
+      for (int sl = tid; sl < nslot; sl += kThreads) {
+        const int* st = L.slot + 4 * sl;
+        const int* nd = L.node + 8 * st[0];
+        double v = rhs0[nd[1] + (sl - nd[4])];
+        for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(upd + il[k]);
+        vg[sl] = v;
+      }
+    } else if (a.first) {
       const int npair = il[4], nrhs = il[3];
       const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
       const int np = il[5];
@@ -1102,6 +1112,191 @@ __global__ void k_adam(int64_t nnz, double* theta, const double* grad, const dou
 }
 
 // ---------------------------------------------------------------------------
+// Cell-by-cell K (HetArgs): the explicit step for per-cell wave speed, and the
+// adjoint.  off: grid offsets of the local nodes of a cell.
+
+__device__ __forceinline__ int local_offset(const HetArgs& h, int m) {
+  return (m % h.P) + h.nx * ((m / h.P) % h.P) + h.nx * h.ny * (m / (h.P * h.P));
+}
+
+// (K x)_i: the cells of node i in list order.
+__device__ __forceinline__ double het_row(const HetArgs& h, const double* x, int64_t i) {
+  double s = 0.0;
+  for (int t = h.nc_ptr[i]; t < h.nc_ptr[i + 1]; ++t) {
+    const int e = h.nc_cell[t], l = h.nc_local[t];
+    const double* K = h.Kall + ((size_t)h.cell_koff[e] * h.Pd + l) * h.Pd;
+    const double* xe = x + h.cell_base[e];
+    double d0 = 0.0, d1 = 0.0;
+    int m = 0;
+    for (; m + 2 <= h.Pd; m += 2) {
+      d0 = fma(K[m], xe[local_offset(h, m)], d0);
+      d1 = fma(K[m + 1], xe[local_offset(h, m + 1)], d1);
+    }
+    if (m < h.Pd) d0 = fma(K[m], xe[local_offset(h, m)], d0);
+    s = fma(h.cell_w[e], d0 + d1, s);
+  }
+  return s;
+}
+
+// A1 + A2 (+ A3) with cell-by-cell K (any dimension).
+__global__ void __launch_bounds__(kThreads) k_explicit_het(ExplicitArgs a, HetArgs h) {
+  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
+  const double* Uc = a.U + on;
+  const double* Wc = a.W + on;
+  double* OUTc = a.OUT + on;
+  const double* fxc = a.fx + on;
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  const int nb = (int)((h.nnodes + kThreads - 1) / kThreads);
+  if ((int)blockIdx.x >= nb) {
+    const double c1 = a.dt, c2 = (0.5 - kNewmarkBeta) * a.dt * a.dt;
+    const int stride = (gridDim.x - nb) * blockDim.x;
+    for (int r = (blockIdx.x - nb) * blockDim.x + threadIdx.x; r < a.n_c; r += stride) {
+      const int node = a.c_node[r];
+      OUTc[node] = Uc[node] + c1 * a.v_c[oc + r] + c2 * a.a_c[oc + r];
+    }
+    return;
+  }
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= h.nnodes || a.cls[g] != NODE_D) return;
+  const int gx = (int)(g % a.nx), gy = (int)((g / a.nx) % a.ny), gz = (int)(g / ((int64_t)a.nx * a.ny));
+  double minv = a.winv_x[gx] * a.winv_y[gy];
+  if (h.dim == 3) minv *= a.winv_z[gz];
+  const double ft = a.ft_dev ? a.ft_dev[0] : a.ft;
+  const double r = het_row(h, Uc, g);
+  const double acc = minv * (ft * fxc[g] - r);
+  OUTc[g] = a.cu * Uc[g] + a.cw * Wc[g] + a.ca * acc;
+}
+
+// out = K x on every active node (0 elsewhere), per column (blockIdx.y).
+__global__ void k_applyK(HetArgs h, const uint8_t* cls, const double* x, double* out, int64_t cs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= h.nnodes) return;
+  const int64_t o = (int64_t)blockIdx.y * cs;
+  out[o + i] = cls[i] ? het_row(h, x + o, i) : 0.0;
+}
+
+// grad[cell_id[e]] -= sum over columns of (2 / c_e) (hv_e . K_e un_e + gv_e . K_e un1_e)
+// (dK/dc_e = 2 c_e K_e(1) = (2 / c_e) K_e); one thread per cell, columns in order.
+__global__ void k_grad_cells(HetArgs h, int ncols, int64_t cs, const double* hv, const double* un,
+                             const double* gv, const double* un1, double* grad) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= h.ncell) return;
+  const double* K = h.Kall + (size_t)h.cell_koff[e] * h.Pd * h.Pd;
+  double total = 0.0;
+  for (int col = 0; col < ncols; ++col) {
+    const int64_t b = (int64_t)col * cs + h.cell_base[e];
+    double s = 0.0;
+    for (int l = 0; l < h.Pd; ++l) {
+      const int ol = local_offset(h, l);
+      const double hl = hv[b + ol], gl = gv[b + ol];
+      if (hl == 0.0 && gl == 0.0) continue;
+      double ku = 0.0, ku1 = 0.0;
+      for (int m = 0; m < h.Pd; ++m) {
+        const int om = local_offset(h, m);
+        ku = fma(K[l * h.Pd + m], un[b + om], ku);
+        ku1 = fma(K[l * h.Pd + m], un1[b + om], ku1);
+      }
+      s = fma(hl, ku, fma(gl, ku1, s));
+    }
+    total = fma(h.cell_w[e], s, total);
+  }
+  grad[h.cell_id[e]] -= 2.0 / h.cell_c[e] * total;
+}
+
+// Adjoint step, part 1 (c rows): rhs0 = abar + beta dt^2 ubar^c + gamma dt vbar;
+// ucp = ubar^c, vcp = vbar.
+__global__ void k_adj_pre(int n_c, int64_t cs_node, int64_t cs_c, const int* c_node, const double* ubar,
+                          const double* vbar, const double* abar, double* rhs0, double* ucp, double* vcp,
+                          double dt) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_c) return;
+  const int64_t oc = (int64_t)blockIdx.y * cs_c + r;
+  const double ub = ubar[(int64_t)blockIdx.y * cs_node + c_node[r]];
+  rhs0[oc] = abar[oc] + kNewmarkBeta * dt * dt * ub + kNewmarkGamma * dt * vbar[oc];
+  ucp[oc] = ub;
+  vcp[oc] = vbar[oc];
+}
+
+// z[c_node[r]] = v[r] per column (z zeroed beforehand).
+__global__ void k_c_to_grid_set(int n_c, int64_t cs_node, int64_t cs_c, const int* c_node, const double* v,
+                                double* z) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_c) return;
+  z[(int64_t)blockIdx.y * cs_node + c_node[r]] = v[(int64_t)blockIdx.y * cs_c + r];
+}
+
+// Adjoint step, part 2 (all nodes): with wbar = -K[:, I_c] g (kg = K z1):
+// I_d: T = ubar + wbar, h = dt^2 M^{-1} T (into z2), I_c: ucp += wbar.
+__global__ void k_adj_mid(ExplicitArgs a, int64_t nnodes, const double* ubar, const double* kg, double* T,
+                          double* z2, const int* node_c, double* ucp, double dt) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nnodes) return;
+  const int64_t o = (int64_t)blockIdx.y * a.cs_node + g;
+  z2[o] = 0.0;
+  T[o] = 0.0;
+  if (a.cls[g] == NODE_D) {
+    const int gx = (int)(g % a.nx), gy = (int)((g / a.nx) % a.ny), gz = (int)(g / ((int64_t)a.nx * a.ny));
+    double minv = a.winv_x[gx] * a.winv_y[gy];
+    if (a.nz > 1) minv *= a.winv_z[gz];
+    const double t = ubar[o] - kg[o];
+    T[o] = t;
+    z2[o] = dt * dt * minv * t;
+  } else if (a.cls[g] == NODE_C) {
+    ucp[(int64_t)blockIdx.y * a.cs_c + node_c[g]] -= kg[o];
+  }
+}
+
+// Adjoint step, part 3: ubar_n = -K[:, I_d] h (kh = K z2) + 2 T + ubar_prev (I_d),
+// + ucp (I_c); ubar_prev = -T (I_d); vbar, abar of step n (I_c).
+__global__ void k_adj_post(ExplicitArgs a, int64_t nnodes, const double* kh, const double* T, double* ubar,
+                           double* ubar_prev, const int* node_c, const double* ucp, const double* vcp, double* vbar,
+                           double* abar, double dt) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nnodes) return;
+  const int64_t o = (int64_t)blockIdx.y * a.cs_node + g;
+  double ub = -kh[o];
+  if (a.cls[g] == NODE_D) {
+    ub += 2.0 * T[o] + ubar_prev[o];
+    ubar_prev[o] = -T[o];
+  } else if (a.cls[g] == NODE_C) {
+    const int64_t r = (int64_t)blockIdx.y * a.cs_c + node_c[g];
+    const double uc = ucp[r], vc = vcp[r];
+    ub += uc;
+    vbar[r] = dt * uc + vc;
+    abar[r] = (0.5 - kNewmarkBeta) * dt * dt * uc + (1.0 - kNewmarkGamma) * dt * vc;
+    ubar_prev[o] = 0.0;
+  } else {
+    ub = 0.0;
+    ubar_prev[o] = 0.0;
+  }
+  ubar[o] = ub;
+}
+
+// Misfit at the receivers: ubar[rec] += u[rec] - d (per column), and the
+// per-column partial 1/2 sum (u[rec] - d)^2 into jpart[col].
+__global__ void k_misfit(int nrec, int64_t cs_node, const int64_t* rec, const double* u, const double* data,
+                         double* ubar, double* jpart, int add_adjoint) {
+  // one block per column, data: (ncols x nrec) for this step
+  __shared__ double red[kWarps];
+  const int col = blockIdx.x;
+  double j = 0.0;
+  for (int k = threadIdx.x; k < nrec; k += blockDim.x) {
+    const int64_t o = (int64_t)col * cs_node + rec[k];
+    const double e = u[o] - data[(int64_t)col * nrec + k];
+    j = fma(0.5 * e, e, j);
+    if (add_adjoint) ubar[o] += e;
+  }
+  for (int o = 16; o > 0; o >>= 1) j += __shfl_xor_sync(0xffffffffu, j, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = j;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += red[w];
+    jpart[col] += t;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Small field kernels (layout conversion only).
 __global__ void k_gather_c(double* dst, const double* src, const int* c_node, int n_c) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1209,6 +1404,12 @@ struct imex_ctx {
   int io_cap = 4096;
   // state
   int ncols = 1;            // independent source columns (fields column after column)
+  // cell-by-cell K (per-cell wave speed; the adjoint)
+  int hetero = 0;
+  int het_ncell = 0;
+  int *het_base = nullptr, *het_koff = nullptr, *het_id = nullptr, *het_ptr = nullptr, *het_cell = nullptr,
+      *het_local = nullptr, *node_c_dev = nullptr;
+  double *het_w = nullptr, *het_c = nullptr, *Kall = nullptr;
   // iterative solve (PCG) and its learned preconditioner
   int solver = IMEX_SOLVER_DIRECT;
   double pcg_tol = 1e-10;
@@ -1280,7 +1481,36 @@ void launch_explicit3(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_
     k_explicit3d<P, kTileLarge3[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops3);
 }
 
+int ntiles(const imex_ctx* c) { return c->ntx * c->nty * c->ntz; }
+
+HetArgs het_args(const imex_ctx* c) {
+  const HostSetup& hs = c->hs;
+  HetArgs h{};
+  h.ncell = c->het_ncell;
+  h.cell_base = c->het_base;
+  h.cell_koff = c->het_koff;
+  h.cell_w = c->het_w;
+  h.cell_c = c->het_c;
+  h.cell_id = c->het_id;
+  h.Kall = c->Kall;
+  h.nc_ptr = c->het_ptr;
+  h.nc_cell = c->het_cell;
+  h.nc_local = c->het_local;
+  h.P = hs.P;
+  h.Pd = hs.Pd;
+  h.dim = hs.dim;
+  h.nx = hs.nn[0];
+  h.ny = hs.nn[1];
+  h.nnodes = hs.nnodes;
+  return h;
+}
+
 void explicit_dispatch(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t s) {
+  if (c->hetero) {   // grid = tiles + prediction blocks; the cell-by-cell kernel takes nodes instead of tiles
+    const int nb = (int)((c->hs.nnodes + kThreads - 1) / kThreads);
+    k_explicit_het<<<dim3(nb + (grid - ntiles(c)), c->ncols), kThreads, 0, s>>>(ea, het_args(c));
+    return;
+  }
   if (c->hs.dim == 3) {
     switch (c->hs.P) {
       case 2: launch_explicit3<2>(c, ea, grid, s); break;
@@ -1357,8 +1587,6 @@ cudaError_t use_tile(imex_ctx* c, bool small) {
   return e;
 }
 
-int ntiles(const imex_ctx* c) { return c->ntx * c->nty * c->ntz; }
-
 ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double* OUT, double cu, double cw,
                            double ca, double ft, bool predict) {
   const HostSetup& hs = c->hs;
@@ -1421,7 +1649,7 @@ constexpr size_t kMaxDynSmem = 220 * 1024;      // dynamic shared memory limit w
 // scratch vectors.
 cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double* ft_dev, int mode, double* Ubuf,
                                const double* src, double* upd, double* sol, double* rhs0, cudaStream_t s,
-                               const int* skip = nullptr, bool rhs_only = false) {
+                               const int* skip = nullptr, bool rhs_only = false, bool rhs_given = false) {
   const HostSetup& hs = c->hs;
   WalkArgs w{};
   w.blob = use_S ? c->blob_S : c->blob_M;
@@ -1458,6 +1686,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   w.a_c = c->a_c;
   w.dt = hs.dt;
   w.skip = skip;
+  w.rhs_given = rhs_given ? 1 : 0;
   w.cs_node = hs.nnodes;
   w.cs_c = hs.n_c;
   w.cs_upd = std::max<int64_t>(hs.upd_size, 1);
@@ -2432,10 +2661,7 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
         return rc;
       }
     }
-    if (!pb.cell_c.empty()) {
-      delete c;
-      return fail(IMEX_ERR_ARG, "per-cell wave speed is not supported by the 2D explicit kernel");
-    }
+    c->hetero = pb.cell_c.empty() ? 0 : 1;   // per-cell speed: cell-by-cell explicit apply
     // Assembled GLL weights per node column/row; lumped mass = rho |J| W_x W_y.
     std::vector<double> wx(hs.nn[0]), wy(hs.nn[1]), wz(hs.dim == 3 ? hs.nn[2] : 1, 1.0);
     auto assembled = [&](int i, int n) {
@@ -2475,6 +2701,53 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
       return rc;
     }
     c->g_nnz = (int64_t)pp.g_col.size();
+    // Cell-by-cell K: every non-empty cell, and each node's cells.
+    std::vector<int> hb, hk, hid, hptr, hcell, hloc;
+    std::vector<double> hw, hc;
+    {
+      std::vector<int> cut_k(hs.ncell_total, -1);
+      for (size_t e = 0; e < hs.if_cell.size(); ++e)
+        if (hs.if_kidx[e] >= 0) cut_k[hs.if_cell[e]] = hs.if_kidx[e];
+      const int ncx = pb.ncells[0], ncy = pb.ncells[1];
+      std::vector<int> cnt(hs.nnodes + 1, 0);
+      for (int cid = 0; cid < hs.ncell_total; ++cid) {
+        if (hs.cell_type[cid] == CELL_EMPTY) continue;
+        const int cx = cid % ncx, cy = (cid / ncx) % ncy, cz = cid / (ncx * ncy);
+        hb.push_back(cx * hs.p + hs.nn[0] * cy * hs.p + hs.nn[0] * hs.nn[1] * cz * hs.p);
+        const double ce = pb.cell_c.empty() ? pb.c0 : pb.cell_c[cid];
+        if (hs.cell_type[cid] == CELL_CUT) {
+          hk.push_back(cut_k[cid]);
+          hw.push_back(1.0);
+        } else {
+          hk.push_back((int)hs.n_cut);
+          hw.push_back((ce / pb.c0) * (ce / pb.c0));
+        }
+        hc.push_back(ce);
+        hid.push_back(cid);
+      }
+      auto loc = [&](int m) {
+        return (m % hs.P) + hs.nn[0] * ((m / hs.P) % hs.P) + hs.nn[0] * hs.nn[1] * (m / (hs.P * hs.P));
+      };
+      for (size_t e = 0; e < hb.size(); ++e)
+        for (int l = 0; l < hs.Pd; ++l) cnt[hb[e] + loc(l) + 1]++;
+      for (int64_t i = 0; i < hs.nnodes; ++i) cnt[i + 1] += cnt[i];
+      hptr = cnt;
+      hcell.assign(cnt[hs.nnodes], 0);
+      hloc.assign(cnt[hs.nnodes], 0);
+      std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+      for (size_t e = 0; e < hb.size(); ++e)
+        for (int l = 0; l < hs.Pd; ++l) {
+          const int node = hb[e] + loc(l);
+          hcell[fill[node]] = (int)e;
+          hloc[fill[node]++] = l;
+        }
+      for (int k : hk)
+        if (k < 0) {
+          delete c;
+          return fail(IMEX_ERR_GEOM, "a cut cell without a stored matrix");
+        }
+      c->het_ncell = (int)hb.size();
+    }
     {
       c->walk_max_slots = plan.max_slots;
       c->walk_max_m = plan.max_m;
@@ -2573,6 +2846,16 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
       ar.add(&c->pcg_status, 4);
       ar.add(&c->pcg_counters, 2);
     }
+    ar.add(&c->het_base, std::max<size_t>(hb.size(), 1));
+    ar.add(&c->het_koff, std::max<size_t>(hk.size(), 1));
+    ar.add(&c->het_id, std::max<size_t>(hid.size(), 1));
+    ar.add(&c->het_w, std::max<size_t>(hw.size(), 1));
+    ar.add(&c->het_c, std::max<size_t>(hc.size(), 1));
+    ar.add(&c->het_ptr, hptr.size());
+    ar.add(&c->het_cell, std::max<size_t>(hcell.size(), 1));
+    ar.add(&c->het_local, std::max<size_t>(hloc.size(), 1));
+    ar.add(&c->Kall, std::max<size_t>(plan.Krows.size(), 1));
+    ar.add(&c->node_c_dev, std::max<int64_t>(nn, 1));
     ar.add(&c->ft_buf, 2);
     ar.add(&c->rec_buf, (size_t)c->io_cap * ncols);
     ar.add(&c->rec_nodes, c->io_cap);
@@ -2625,6 +2908,16 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
       const int rows_ctas = (int)std::max<int64_t>(1, (hs.n_c + kThreads - 1) / kThreads);
       c->pcg_grid = std::max(1, std::min({nsm, 1024, nsm * occ, rows_ctas}));
     }
+    e = e ? e : upload(c->het_base, hb);
+    e = e ? e : upload(c->het_koff, hk);
+    e = e ? e : upload(c->het_id, hid);
+    e = e ? e : upload(c->het_w, hw);
+    e = e ? e : upload(c->het_c, hc);
+    e = e ? e : upload(c->het_ptr, hptr);
+    e = e ? e : upload(c->het_cell, hcell);
+    e = e ? e : upload(c->het_local, hloc);
+    e = e ? e : upload(c->Kall, plan.Krows);
+    e = e ? e : upload(c->node_c_dev, hs.node_c);
     e = e ? e : upload(c->Kpair, plan.Kpair);
     e = e ? e : upload(c->kp_off, plan.kp_off);
     e = e ? e : upload(c->kp_len, plan.kp_len);
@@ -2656,7 +2949,7 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
       e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
       c->num_sms = std::max(1, nsm);
     }
-    e = e ? e : autotune_tile(c);
+    e = e ? e : (c->hetero ? use_tile(c, false) : autotune_tile(c));
     if (e != cudaSuccess) {
       std::string msg = std::string("upload failed: ") + cudaGetErrorString(e);
       imex_destroy(c);
@@ -2978,6 +3271,148 @@ int imex_fsai_kaporin(int n, const int* s_ptr, const int* s_col, const double* s
   double l = 0.0;
   for (double v : hp) l += v;
   *loss = l;
+  return IMEX_OK;
+}
+
+int imex_adjoint(imex_ctx* c, int64_t nsteps, const int64_t* rec_nodes, int nrec, const double* data,
+                 int checkpoint_every, double* grad, double* misfit) {
+  if (!c || nsteps < 1 || nrec < 1 || !rec_nodes || !data || !grad || !misfit || checkpoint_every < 1)
+    return fail(IMEX_ERR_ARG, "bad arguments");
+  const HostSetup& hs = c->hs;
+  for (int k = 0; k < nrec; ++k)
+    if (rec_nodes[k] < 0 || rec_nodes[k] >= hs.nnodes) return fail(IMEX_ERR_ARG, "receiver node out of range");
+  cudaStream_t s = c->stream;
+  const int ncols = c->ncols;
+  const int64_t nn = hs.nnodes, nc = std::max<int64_t>(hs.n_c, 1), N = nsteps, Kc = checkpoint_every;
+  const int64_t nseg = (N + Kc - 1) / Kc;
+  const int64_t ck_len = (int64_t)ncols * (2 * nn + 2 * nc);
+  std::vector<void*> bufs;
+  auto dalloc = [&](size_t bytes) -> double* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    return static_cast<double*>(p);
+  };
+  auto cleanup = [&]() {
+    for (void* p : bufs) cudaFree(p);
+  };
+  double* ck = dalloc((size_t)(nseg + 1) * ck_len * sizeof(double));
+  double* fin = dalloc((size_t)ck_len * sizeof(double));
+  double* seg = dalloc((size_t)(Kc + 1) * ncols * nn * sizeof(double));
+  double* ubar = dalloc((size_t)ncols * nn * sizeof(double));
+  double* ubar_prev = dalloc((size_t)ncols * nn * sizeof(double));
+  double* T = dalloc((size_t)ncols * nn * sizeof(double));
+  double* z1 = dalloc((size_t)ncols * nn * sizeof(double));
+  double* z2 = dalloc((size_t)ncols * nn * sizeof(double));
+  double* kg = dalloc((size_t)ncols * nn * sizeof(double));
+  double* kh = dalloc((size_t)ncols * nn * sizeof(double));
+  double* vbar = dalloc((size_t)ncols * nc * sizeof(double));
+  double* abar = dalloc((size_t)ncols * nc * sizeof(double));
+  double* ucp = dalloc((size_t)ncols * nc * sizeof(double));
+  double* vcp = dalloc((size_t)ncols * nc * sizeof(double));
+  double* dgrad = dalloc((size_t)hs.ncell_total * sizeof(double));
+  double* jpart = dalloc((size_t)ncols * 2 * sizeof(double));
+  double* ddata = dalloc((size_t)N * ncols * nrec * sizeof(double));
+  int64_t* drec = reinterpret_cast<int64_t*>(dalloc((size_t)nrec * sizeof(int64_t)));
+  for (void* p : bufs)
+    if (!p) {
+      cleanup();
+      return fail(IMEX_ERR_ALLOC, "imex_adjoint: device buffers");
+    }
+  if (std::count(bufs.begin(), bufs.end(), nullptr) || bufs.size() != 18) {
+    cleanup();
+    return fail(IMEX_ERR_ALLOC, "imex_adjoint: device buffers");
+  }
+  cudaError_t e = cudaMemcpyAsync(ddata, data, (size_t)N * ncols * nrec * sizeof(double), cudaMemcpyHostToDevice, s);
+  e = e ? e : cudaMemcpyAsync(drec, rec_nodes, nrec * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  e = e ? e : cudaMemsetAsync(jpart, 0, ncols * 2 * sizeof(double), s);
+  e = e ? e : cudaMemsetAsync(dgrad, 0, hs.ncell_total * sizeof(double), s);
+  // State copies: U[cur], U[1-cur], v_c, a_c of every column.
+  auto save = [&](double* dst) {
+    cudaError_t r = cudaMemcpyAsync(dst, c->U[c->cur], ncols * nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    r = r ? r : cudaMemcpyAsync(dst + ncols * nn, c->U[1 - c->cur], ncols * nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    r = r ? r : cudaMemcpyAsync(dst + 2 * ncols * nn, c->v_c, ncols * nc * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    r = r ? r : cudaMemcpyAsync(dst + 2 * ncols * nn + ncols * nc, c->a_c, ncols * nc * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s);
+    return r;
+  };
+  auto restore = [&](const double* src) {
+    cudaError_t r = cudaMemcpyAsync(c->U[c->cur], src, ncols * nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    r = r ? r : cudaMemcpyAsync(c->U[1 - c->cur], src + ncols * nn, ncols * nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    r = r ? r : cudaMemcpyAsync(c->v_c, src + 2 * ncols * nn, ncols * nc * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    r = r ? r : cudaMemcpyAsync(c->a_c, src + 2 * ncols * nn + ncols * nc, ncols * nc * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s);
+    return r;
+  };
+  const int64_t n0 = c->step;
+  const int nbn = (int)((nn + kThreads - 1) / kThreads), nbc = (int)((nc + kThreads - 1) / kThreads);
+  const dim3 gn(nbn, ncols), gc(nbc, ncols);
+  const HetArgs ha = het_args(c);
+  // Forward with checkpoints and the misfit.
+  e = e ? e : save(ck);
+  for (int64_t n = 0; n < N && e == cudaSuccess; ++n) {
+    if (int rc = step_once(c, s, nullptr)) {
+      cleanup();
+      return rc;
+    }
+    k_misfit<<<ncols, kThreads, 0, s>>>(nrec, nn, drec, c->U[c->cur], ddata + n * ncols * nrec, nullptr, jpart, 0);
+    if ((n + 1) % Kc == 0) e = save(ck + ((n + 1) / Kc) * ck_len);
+  }
+  e = e ? e : save(fin);
+  // Reverse over the segments, each recomputed from its checkpoint.
+  e = e ? e : cudaMemsetAsync(ubar, 0, ncols * nn * sizeof(double), s);
+  e = e ? e : cudaMemsetAsync(ubar_prev, 0, ncols * nn * sizeof(double), s);
+  e = e ? e : cudaMemsetAsync(vbar, 0, ncols * nc * sizeof(double), s);
+  e = e ? e : cudaMemsetAsync(abar, 0, ncols * nc * sizeof(double), s);
+  const double dt = hs.dt;
+  ExplicitArgs ea = explicit_args(c, c->U[0], c->U[0], c->U[0], 0.0, 0.0, 0.0, 0.0, false);
+  for (int64_t sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
+    const int64_t nb = sg * Kc, ne = std::min(N, nb + Kc);
+    e = restore(ck + sg * ck_len);
+    c->step = n0 + nb;
+    e = e ? e : cudaMemcpyAsync(seg, c->U[c->cur], ncols * nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    for (int64_t n = nb; n < ne && e == cudaSuccess; ++n) {
+      if (int rc = step_once(c, s, nullptr)) {
+        cleanup();
+        return rc;
+      }
+      e = cudaMemcpyAsync(seg + (n - nb + 1) * ncols * nn, c->U[c->cur], ncols * nn * sizeof(double),
+                          cudaMemcpyDeviceToDevice, s);
+    }
+    for (int64_t n = ne - 1; n >= nb && e == cudaSuccess; --n) {
+      const double* un = seg + (n - nb) * ncols * nn;
+      const double* un1 = seg + (n - nb + 1) * ncols * nn;
+      k_misfit<<<ncols, kThreads, 0, s>>>(nrec, nn, drec, un1, ddata + n * ncols * nrec, ubar, jpart + ncols, 1);
+      if (hs.n_c > 0) {
+        k_adj_pre<<<gc, kThreads, 0, s>>>((int)hs.n_c, nn, nc, c->c_node, ubar, vbar, abar, c->rhs0, ucp, vcp, dt);
+        e = launch_solve_chain(c, true, 0.0, nullptr, 2, c->U[c->cur], c->U[c->cur], c->upd, c->sol, c->rhs0, s,
+                               nullptr, false, true);
+      }
+      e = e ? e : cudaMemsetAsync(z1, 0, ncols * nn * sizeof(double), s);
+      if (hs.n_c > 0) k_c_to_grid_set<<<gc, kThreads, 0, s>>>((int)hs.n_c, nn, nc, c->c_node, c->sol, z1);
+      k_applyK<<<gn, kThreads, 0, s>>>(ha, c->cls, z1, kg, nn);
+      k_adj_mid<<<gn, kThreads, 0, s>>>(ea, nn, ubar, kg, T, z2, c->node_c_dev, ucp, dt);
+      k_applyK<<<gn, kThreads, 0, s>>>(ha, c->cls, z2, kh, nn);
+      k_grad_cells<<<(ha.ncell + kThreads - 1) / kThreads, kThreads, 0, s>>>(ha, ncols, nn, z2, un, z1, un1, dgrad);
+      k_adj_post<<<gn, kThreads, 0, s>>>(ea, nn, kh, T, ubar, ubar_prev, c->node_c_dev, ucp, vcp, vbar, abar, dt);
+      if (int rc = check_launch("imex_adjoint")) {
+        cleanup();
+        return rc;
+      }
+    }
+  }
+  // Leave the context at the end of the forward run.
+  e = e ? e : restore(fin);
+  c->step = n0 + N;
+  std::vector<double> jp(ncols * 2);
+  e = e ? e : cudaMemcpyAsync(grad, dgrad, hs.ncell_total * sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = e ? e : cudaMemcpyAsync(jp.data(), jpart, ncols * 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = e ? e : cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_adjoint: ") + cudaGetErrorString(e));
+  double J = 0.0;
+  for (int col = 0; col < ncols; ++col) J += jp[col];
+  *misfit = J;
   return IMEX_OK;
 }
 

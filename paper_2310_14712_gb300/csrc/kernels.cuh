@@ -107,6 +107,7 @@ struct WalkArgs {
   // right-hand sides f_t f_x^c - K^c u (first forward launch)
   int first;
   int rhs_only;                 // first launch: only form the right-hand sides (into rhs0)
+  int rhs_given;                // first launch: every right-hand side is already in rhs0
   const int* skip;              // if set and *skip != 0: the launch does nothing (PCG converged)
   const double* SRC;            // u_pred (step) or u_0 (initial acceleration), full grid
   const double* Kpair;          // per CTA: rows of the cell matrices of its pairs (m-major, scaled)
@@ -192,6 +193,28 @@ struct PcgArgs {
   double* v_c;
   double* a_c;
   double dt;
+};
+
+// Cell-by-cell form of K used where the tensor-grid apply does not apply
+// (per-cell wave speed, the adjoint): every non-empty cell e has its nodal
+// block at cell_base[e] (+ the local offsets of a cell), its matrix row-major
+// in Kall (cut cells: their stored matrix; uncut cells: the uncut matrix),
+// and weight w[e] (c_e^2 / c0^2 for uncut cells, 1 for cut cells, whose
+// stored matrices carry c_e^2).  Each node lists its cells (CSR), so a row
+// of K x is gathered in a fixed order.
+struct HetArgs {
+  int ncell;                      // non-empty cells
+  const int* cell_base;
+  const int* cell_koff;           // matrix index into Kall (Pd x Pd each)
+  const double* cell_w;
+  const double* cell_c;           // wave speed c_e
+  const int* cell_id;             // flat cell id (gradient index)
+  const double* Kall;
+  const int* nc_ptr;              // node -> its (cell, local node) entries
+  const int* nc_cell;
+  const int* nc_local;
+  int P, Pd, dim, nx, ny;
+  int64_t nnodes;
 };
 
 }  // namespace imex

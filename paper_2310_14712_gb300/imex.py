@@ -72,6 +72,8 @@ _lib.imex_setup_batch.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_d
                                   ctypes.POINTER(Source), ctypes.c_int, ctypes.POINTER(Alloc),
                                   ctypes.POINTER(_vp)]
 _lib.imex_step.argtypes = [_vp, ctypes.c_int64, _vp]
+_lib.imex_adjoint.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, _dp,
+                              ctypes.c_int, _dp, _dp]
 _lib.imex_set_solver.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
 _lib.imex_pcg_train.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _dp]
 _lib.imex_pcg_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), _dp, ctypes.POINTER(ctypes.c_int64),
@@ -96,7 +98,7 @@ _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctyp
                                         ctypes.POINTER(Stats)]
 
 # Every symbol include/imex.h declares (checked by the CPU tests).
-EXPORTS = ("imex_setup", "imex_setup_batch", "imex_set_solver", "imex_pcg_train", "imex_pcg_status",
+EXPORTS = ("imex_setup", "imex_setup_batch", "imex_adjoint", "imex_set_solver", "imex_pcg_train", "imex_pcg_status",
            "imex_fsai_kaporin", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
            "imex_set_initial", "imex_info", "imex_last_error", "imex_destroy", "imex_gll_points",
            "imex_gauss_points", "imex_host_setup_export")
@@ -251,6 +253,7 @@ class Imex:
         self.field_len = self.n_nodes * self.ncols
         self.dim = dim
         self.shape = tuple(reversed([ncells[k] * p + 1 for k in range(dim)]))
+        self._ncells = tuple(ncells[:dim])
 
     @classmethod
     def from_workload(cls, w, **kw):
@@ -274,6 +277,19 @@ class Imex:
         hist = np.zeros(int(epochs))
         _check(_lib.imex_pcg_train(self._ctx, int(epochs), float(lr), hist.ctypes.data_as(_dp)), "imex_pcg_train")
         return hist
+
+    def adjoint(self, nsteps, rec_nodes, data, checkpoint_every=100):
+        """Misfit of the next nsteps steps at the receivers against data
+        (nsteps x ncols x nrec) and its gradient in the per-cell wave speed."""
+        rec = np.ascontiguousarray(np.asarray(rec_nodes, dtype=np.int64))
+        d = _f64(data).reshape(int(nsteps), self.ncols, len(rec))
+        ncell = int(np.prod(self._ncells))
+        grad = np.zeros(ncell)
+        J = ctypes.c_double()
+        _check(_lib.imex_adjoint(self._ctx, int(nsteps), rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 len(rec), d.ctypes.data_as(_dp), int(checkpoint_every),
+                                 grad.ctypes.data_as(_dp), ctypes.byref(J)), "imex_adjoint")
+        return J.value, grad
 
     def pcg_status(self):
         it, tot, fb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
