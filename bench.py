@@ -144,6 +144,43 @@ def measure_learned_pcg(imex, w, steps, stream, flush, epochs=300):
     return out
 
 
+def measure_adjoint(imex, workloads, nrec=64, checkpoint_every=100):
+    """Misfit gradient in the per-cell wave speed by the discrete adjoint, on
+    the adjoint workload (16x16-cell plate, smooth seeded speed, 16 sources as
+    columns, 64 receivers, 2000 steps, checkpoint every 100), against the
+    forward run of the same steps.  Host wall clock around the calls."""
+    import numpy as np
+    import torch
+    w = workloads.adjoint()
+    rec = workloads.receiver_nodes(w, nrec)
+    ncols = len(w.src_pos)
+    data = np.zeros((w.steps, ncols, nrec))
+    out = {"workload": "adjoint: [0,1]^2 minus a centred circle r=0.2, 16x16 cells, p=4, per-cell "
+                       f"speed in [0.8,1.2], {ncols} sources (columns), {nrec} receivers, "
+                       f"{w.steps} steps, checkpoint every {checkpoint_every}",
+           "unit": "s"}
+    with imex.Imex.from_workload(w, ncols=ncols) as g:
+        st = g.info()
+        g.step(20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(w.steps)
+        torch.cuda.synchronize()
+        out["forward_seconds"] = time.perf_counter() - t0
+    with imex.Imex.from_workload(w, ncols=ncols) as g:
+        g.adjoint(50, rec, data[:50], 10)          # warm-up (allocations, code paths)
+    with imex.Imex.from_workload(w, ncols=ncols) as g:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, grad = g.adjoint(w.steps, rec, data, checkpoint_every)
+        out["gradient_seconds"] = time.perf_counter() - t0
+    n_act = st["n_d"] + st["n_c"]
+    out["gradient_over_forward"] = out["gradient_seconds"] / out["forward_seconds"]
+    out["gradient_dof_steps_per_s"] = n_act * ncols * w.steps / out["gradient_seconds"]
+    out["finite"] = bool(np.isfinite(J) and np.isfinite(grad).all())
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -386,6 +423,7 @@ def run_gpu(args):
     if ws == 1:
         line["batched"] = measure_batched(imex, workloads, min(args.steps, 200), stream, flush)
         line["learned_pcg"] = measure_learned_pcg(imex, w, min(args.steps, 20), stream, flush)
+        line["adjoint"] = measure_adjoint(imex, workloads)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n_act_cpu, secs = cpu_oracle_rate(w, args.cpu_steps)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
