@@ -115,6 +115,9 @@ typedef struct {
   int64_t explicit_tile_cells;   /* cells per side of an explicit-apply tile (autotuned) */
   double explicit_tile_us_large; /* setup timing of one explicit launch, larger tile (0: not timed) */
   double explicit_tile_us_small; /* the same, smaller tile */
+  int64_t scheme;                /* IMEX_SCHEME_* of the context */
+  double dt_crit_cut_min;        /* smallest cut-cell critical step for the scheme's mass
+                                    (central-difference schemes; 0 otherwise) */
 } imex_stats;
 
 /*
@@ -150,6 +153,48 @@ int imex_setup(const imex_mesh *mesh, int p, double alpha, double dt, const imex
  */
 int imex_setup_batch(const imex_mesh *mesh, int p, double alpha, double dt, const imex_source *src,
                      int ncols, const imex_alloc *alloc, imex_ctx **out);
+
+/*
+ * Time integration schemes on the same discretisation: the method and the
+ * paper's comparison schemes (Sec. "Lumping of Cut Cells", Table
+ * criticaltimestepsizes, the runtime comparisons).
+ *   IMEX_SCHEME_IMEX        : Newmark IMEX (Fig. TrapCDMIMEX)
+ *   IMEX_SCHEME_CDM         : central differences on every DOF (Eqs. CDMstep,
+ *                             CDMacc) with the consistent SCM mass: diagonal on
+ *                             I_d, the consistent cut-cell blocks on I_c, so a
+ *                             step is the diagonal update of I_d and a solve
+ *                             with M^cc for a^c_n
+ *   IMEX_SCHEME_CDM_HRZ     : the same with every cut-cell mass HRZ-lumped
+ *                             (Eqs. HRZ: the diagonal scaled to the element
+ *                             mass, off-diagonal entries dropped)
+ *   IMEX_SCHEME_TRAPEZOIDAL : trapezoidal Newmark (beta = 1/4, gamma = 1/2) on
+ *                             every DOF (I_d empty, S = M + beta dt^2 K)
+ */
+#define IMEX_SCHEME_IMEX 0
+#define IMEX_SCHEME_CDM 1
+#define IMEX_SCHEME_CDM_HRZ 2
+#define IMEX_SCHEME_TRAPEZOIDAL 3
+
+/*
+ * imex_setup_scheme - imex_setup_batch() with a time integration scheme.
+ *   scheme : IMEX_SCHEME_*
+ *   dt     : <= 0 selects 0.9 x the scheme's cell-wise critical step: that of
+ *            one uncut cell (IMEX, trapezoidal), or the smaller of that and the
+ *            smallest cut-cell value 2 / sqrt(lambda_max(K_e, M_e)) for the
+ *            scheme's cut-cell mass (central differences; the assembled
+ *            lambda_max is bounded by the largest cell-wise one)
+ * State: the central-difference schemes keep (u_n, u_{n-1}) on every active DOF:
+ * IMEX_FIELD_U_PREV_D then holds u_{n-1} on I_c too, IMEX_FIELD_A_C the
+ * acceleration a^c_{n-1} of the last step (a^c_0 before the first) and
+ * IMEX_FIELD_V_C the initial velocity.  The trapezoidal scheme has every
+ * active DOF in I_c.
+ * Errors: as imex_setup_batch; IMEX_ERR_ARG for an unknown scheme;
+ * IMEX_ERR_NOT_SPD if a cut-cell mass is not positive definite.  The
+ * iterative solvers (imex_set_solver) and imex_adjoint take the IMEX scheme
+ * only (the iterative solvers also the trapezoidal one).
+ */
+int imex_setup_scheme(const imex_mesh *mesh, int p, double alpha, double dt, const imex_source *src,
+                      int ncols, int scheme, const imex_alloc *alloc, imex_ctx **out);
 
 /*
  * imex_step - advance n >= 0 Newmark IMEX steps (Fig. TrapCDMIMEX), each:

@@ -46,14 +46,15 @@ def _is_diagonal(A):
     return bool(np.all(A.row == A.col) or A.nnz == 0)
 
 
-def cdm(M, K, fx, ft, dt, nsteps, u0, v0, callback=None):
-    """Central difference method (Eqs. CDMstep, CDMacc). Returns (u_n, u_{n-1})."""
+def cdm(M, K, fx, ft, dt, nsteps, u0, v0, callback=None, permc_spec="COLAMD"):
+    """Central difference method (Eqs. CDMstep, CDMacc). Returns (u_n, u_{n-1}).
+    permc_spec: column ordering of the sparse LU of a non-diagonal M."""
     n = M.shape[0]
     if _is_diagonal(M):
         md = np.asarray(M.diagonal())
         solve = lambda b: b / md
     else:
-        lu = spla.splu(_csc(M))
+        lu = spla.splu(_csc(M), permc_spec=permc_spec)
         solve = lu.solve
     u = np.array(u0, dtype=np.float64)
     a0 = solve(ft(0.0) * fx - K @ u)
@@ -68,13 +69,13 @@ def cdm(M, K, fx, ft, dt, nsteps, u0, v0, callback=None):
     return u, u_prev
 
 
-def trapezoidal_newmark(M, K, fx, ft, dt, nsteps, u0, v0, callback=None):
+def trapezoidal_newmark(M, K, fx, ft, dt, nsteps, u0, v0, callback=None, permc_spec="COLAMD"):
     """Trapezoidal Newmark, predictor-corrector form (Fig. implicitNewmark).
-    Returns (u, v, a)."""
+    Returns (u, v, a).  permc_spec: column ordering of the sparse LUs."""
     u = np.array(u0, dtype=np.float64)
     v = np.array(v0, dtype=np.float64)
-    a = spla.splu(_csc(M)).solve(ft(0.0) * fx - K @ u)
-    S = spla.splu(_csc(M + BETA * dt * dt * K))
+    a = spla.splu(_csc(M), permc_spec=permc_spec).solve(ft(0.0) * fx - K @ u)
+    S = spla.splu(_csc(M + BETA * dt * dt * K), permc_spec=permc_spec)
     for k in range(nsteps):
         t1 = (k + 1) * dt
         u_pred = u + dt * v + (0.5 - BETA) * dt * dt * a

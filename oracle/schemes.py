@@ -104,9 +104,10 @@ class SchemeState:
         self.u, self.u_prev, self.v, self.a = u, u_prev, v, a
 
 
-def run(s, scheme, nsteps, u0=None, v0=None, M_hrz=None):
+def run(s, scheme, nsteps, u0=None, v0=None, M_hrz=None, permc_spec="COLAMD"):
     """nsteps of `scheme` from (u0, v0) (default zero) with the setup's dt,
-    force and masks; the system is restricted to the active DOFs."""
+    force and masks; the system is restricted to the active DOFs.  permc_spec:
+    column ordering of the sparse LUs (the IMEX scheme uses the setup's own)."""
     d = s.disc
     n = d.grid.nnodes
     act = np.flatnonzero(d.active)
@@ -119,7 +120,7 @@ def run(s, scheme, nsteps, u0=None, v0=None, M_hrz=None):
     fx = np.asarray(d.fx)[act]
     if scheme == "trapezoidal":
         M = sp.csr_matrix(d.M)[act][:, act]
-        u, v, a = trapezoidal_newmark(M, K, fx, s.ft, s.dt, nsteps, u0[act], v0[act])
+        u, v, a = trapezoidal_newmark(M, K, fx, s.ft, s.dt, nsteps, u0[act], v0[act], permc_spec=permc_spec)
         out = [np.zeros(n) for _ in range(3)]
         for o, x in zip(out, (u, v, a)):
             o[act] = x
@@ -130,7 +131,7 @@ def run(s, scheme, nsteps, u0=None, v0=None, M_hrz=None):
         M = (hrz_mass(s) if M_hrz is None else M_hrz)[act][:, act]
     else:
         raise ValueError(f"unknown scheme {scheme!r}")
-    u, u_prev = cdm(M, K, fx, s.ft, s.dt, nsteps, u0[act], v0[act])
+    u, u_prev = cdm(M, K, fx, s.ft, s.dt, nsteps, u0[act], v0[act], permc_spec=permc_spec)
     uf, pf = np.zeros(n), np.zeros(n)
     uf[act], pf[act] = u, u_prev
     return SchemeState(uf, pf)

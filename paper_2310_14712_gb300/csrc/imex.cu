@@ -585,13 +585,17 @@ __device__ __forceinline__ void warp_gemv(const double* M, int si, int sj, int n
 struct Corr {
   int mode;
   const int* c_node;
-  double* U;      // holds u_pred on I_c; receives u^c_{n+1}
+  double* U;      // holds u_pred on I_c (mode 0) or u^c_{n-1} (mode 3); receives u^c_{n+1}
   double* v_c;
   double* a_c;
   double dt;
+  const double* Un;  // u_n (mode 3)
   __device__ void row(int r, double acc) const {
     if (mode == 2) return;   // solve only: the solution stays in sol
-    if (mode == 0) {
+    if (mode == 3) {         // central differences on I_c (Eq. CDMstep): acc = a^c_n
+      const int node = c_node[r];
+      U[node] = 2.0 * Un[node] - U[node] + dt * dt * acc;
+    } else if (mode == 0) {
       const int node = c_node[r];
       const double vpred = v_c[r] + (1.0 - kNewmarkGamma) * dt * a_c[r];
       U[node] = U[node] + kNewmarkBeta * dt * dt * acc;
@@ -603,7 +607,9 @@ struct Corr {
   // written by the kernels of the step that run before the correction).
   __device__ void row_pre(int r, double acc, int node, double v_old, double a_old) const {
     if (mode == 2) return;
-    if (mode == 0) {
+    if (mode == 3) {
+      U[node] = 2.0 * Un[node] - U[node] + dt * dt * acc;
+    } else if (mode == 0) {
       const double vpred = v_old + (1.0 - kNewmarkGamma) * dt * a_old;
       U[node] = U[node] + kNewmarkBeta * dt * dt * acc;
       v_c[r] = vpred + kNewmarkGamma * dt * acc;
@@ -677,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
   double* rhs0 = a.rhs0 + oc;
   double* sol = a.sol + oc;
   double* upd = a.upd + (int64_t)blockIdx.y * a.cs_upd;
-  const Corr cor{a.mode, a.c_node, a.U + on, a.v_c + oc, a.a_c + oc, a.dt};
+  const Corr cor{a.mode, a.c_node, a.U + on, a.v_c + oc, a.a_c + oc, a.dt, src};
   double* blob = sm;                                   // max_blob (smem mode)
   double* kp = blob + a.max_blob;                      // max_kp: rows of the cell matrices (first launch)
   double* vg = kp + a.max_kp;                          // max_slots: g (fwd) / y (bwd)
@@ -730,7 +736,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
       }
     } else if (a.first) {
       const int npair = il[4], nrhs = il[3];
-      const double ft = a.ft_dev ? a.ft_dev[1] : a.ft;
+      // f_t at t_{n+1}, or at t_n for the central-difference form (mode 3).
+      const double ft = a.ft_dev ? a.ft_dev[a.mode == 3 ? 0 : 1] : a.ft;
       const int np = il[5];
       for (int k = tid; k < npair; k += kThreads) pc[k] = pair_product(a, src, KP, np, k, L.pair[4 * k], s_off);
       __syncthreads();
@@ -843,7 +850,7 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   const double* rhs0 = a.rhs0 + oc;
   double* sol = a.sol + oc;
   const double* upd = a.upd + (int64_t)blockIdx.y * a.cs_upd;
-  const Corr cor{a.mode, a.c_node, a.U + on, a.v_c + oc, a.a_c + oc, a.dt};
+  const Corr cor{a.mode, a.c_node, a.U + on, a.v_c + oc, a.a_c + oc, a.dt, a.Un ? a.Un + on : nullptr};
   const int comp = a.cta_comp[cta], r0 = a.cta_r0[cta], r1 = a.cta_r1[cta];
   const int zn = a.zsize[comp], zb = a.zbase[comp], nr = r1 - r0;
   double* zs = tsm;                               // max_zn (even): right-hand side of the block
@@ -1036,7 +1043,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
     if (k > a.maxit) k = a.maxit;
   }
   if (conv) {
-    const Corr cor{a.mode, a.c_node, a.U, a.v_c, a.a_c, a.dt};
+    const Corr cor{a.mode, a.c_node, a.U, a.v_c, a.a_c, a.dt, nullptr};
     for (int i = g0; i < n; i += gs) cor.row(i, a.x[i]);
   }
   if (g0 == 0) {
@@ -1301,6 +1308,16 @@ __global__ void k_misfit(int nrec, int64_t cs_node, const int64_t* rec, const do
 __global__ void k_gather_c(double* dst, const double* src, const int* c_node, int n_c) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n_c) dst[r] = src[c_node[r]];
+}
+// Central-difference start on I_c (column blockIdx.y):
+// u^c_{-1} = u^c_0 - dt v^c_0 + dt^2/2 a^c_0 into Uo.
+__global__ void k_cdm_start_c(double* Uo, const double* U0, const double* v_c, const double* a_c,
+                              const int* c_node, int n_c, int64_t cs_node, double dt) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_c) return;
+  const int64_t on = (int64_t)blockIdx.y * cs_node, oc = (int64_t)blockIdx.y * n_c;
+  const int node = c_node[r];
+  Uo[on + node] = U0[on + node] - dt * v_c[oc + r] + 0.5 * dt * dt * a_c[oc + r];
 }
 __global__ void k_scatter_c(double* dst, const double* src, const int* c_node, int n_c) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1711,6 +1728,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   z.mode = mode;
   z.c_node = c->c_node;
   z.U = Ubuf;
+  z.Un = src;
   z.v_c = c->v_c;
   z.a_c = c->a_c;
   z.dt = hs.dt;
@@ -1862,6 +1880,11 @@ int compute_initial(imex_ctx* c, cudaStream_t s) {
     if (cudaError_t e = launch_solve_chain(c, false, ft0, nullptr, 1, U0, U0, c->upd, c->sol, c->rhs0, s))
       return fail(IMEX_ERR_CUDA, std::string("solve (initial): ") + cudaGetErrorString(e));
     if (int rc = check_launch("solve (initial)")) return rc;
+    if (scheme_is_cdm(hs.pb.scheme)) {   // the central-difference history of I_c as well
+      k_cdm_start_c<<<dim3((nc + 255) / 256, c->ncols), 256, 0, s>>>(Uo, U0, c->v_c, c->a_c, c->c_node, nc,
+                                                                       hs.nnodes, dt);
+      if (int rc = check_launch("central-difference start")) return rc;
+    }
   }
   return IMEX_OK;
 }
@@ -2251,12 +2274,13 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
         nd[6] = (int)P.node_boff[list[q]];
         nd[7] = (int)T.off_upd;
         for (int i = 0; i < b; ++i) {
+          // Indices, not pointers: the appends below may reallocate Lst.
           const int r = T.beg + i;
-          int* st = &Lst[o_slot + 4 * (slot0[q] + i)];
-          st[0] = (int)q;
-          st[1] = (int)Lst.size();
+          const size_t st = (size_t)o_slot + 4 * (size_t)(slot0[q] + i);
+          Lst[st] = (int)q;
+          Lst[st + 1] = (int)Lst.size();
           for (int k = hs.fwd_ptr[r]; k < hs.fwd_ptr[r + 1]; ++k) Lst.push_back(hs.fwd_pos[k]);
-          st[2] = (int)Lst.size();
+          Lst[st + 2] = (int)Lst.size();
         }
         for (int k = 0; k < m; ++k) {
           Lst[o_anc + 2 * (moff[q] + k)] = (int)q;
@@ -2581,6 +2605,8 @@ static void fill_stats(const HostSetup& hs, imex_stats* st) {
   st->setup_seconds = hs.setup_seconds;
   st->residual_S = hs.residual_S;
   st->residual_M = hs.residual_M;
+  st->scheme = hs.pb.scheme;
+  st->dt_crit_cut_min = hs.dt_crit_cut_min;
 }
 
 int imex_host_setup_export(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src,
@@ -2607,6 +2633,15 @@ int imex_setup(const imex_mesh* mesh, int p, double alpha, double dt, const imex
 
 int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src, int ncols,
                      const imex_alloc* alloc, imex_ctx** out) {
+  return imex_setup_scheme(mesh, p, alpha, dt, src, ncols, IMEX_SCHEME_IMEX, alloc, out);
+}
+
+static_assert(IMEX_SCHEME_IMEX == kSchemeImex && IMEX_SCHEME_CDM == kSchemeCdm &&
+                  IMEX_SCHEME_CDM_HRZ == kSchemeCdmHrz && IMEX_SCHEME_TRAPEZOIDAL == kSchemeTrapezoidal,
+              "scheme codes");
+
+int imex_setup_scheme(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src, int ncols,
+                      int scheme, const imex_alloc* alloc, imex_ctx** out) {
   if (!out) return fail(IMEX_ERR_ARG, "out must not be NULL");
   *out = nullptr;
   imex_ctx* c = nullptr;
@@ -2615,7 +2650,9 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
     if (int rc = build_context(mesh, p, alpha, dt, src, pb)) return rc;
     if (ncols < 1 || ncols > kMaxCols) return fail(IMEX_ERR_ARG, "ncols must be in [1, 256]");
     if (ncols > 1 && ncols != pb.nsrc) return fail(IMEX_ERR_ARG, "ncols > 1 needs one source per column");
+    if (scheme < IMEX_SCHEME_IMEX || scheme > IMEX_SCHEME_TRAPEZOIDAL) return fail(IMEX_ERR_ARG, "unknown scheme");
     pb.ncols = ncols;
+    pb.scheme = scheme;
     if (pb.dim == 3 && pb.p > 4) return fail(IMEX_ERR_ARG, "the 3D GPU time stepper supports p <= 4");
     c = new imex_ctx();
     c->ncols = ncols;
@@ -2976,30 +3013,58 @@ int imex_setup_batch(const imex_mesh* mesh, int p, double alpha, double dt, cons
   }
 }
 
-// One IMEX step n -> n+1 on stream s; events (may be NULL) are recorded
-// before the explicit kernel, after it, and after the implicit chain.
-static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double* ft_dev = nullptr) {
+// CTAs of an explicit launch that only predicts (no explicit DOFs).
+int pred_only_blocks(const imex_ctx* c) {
+  const int64_t nb = (c->hs.n_c + kThreads - 1) / kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(nb, 4LL * std::max(1, c->num_sms)));
+}
+
+// One step n -> n+1 on stream s; events (may be NULL) are recorded before
+// the explicit kernel, after it, and after the implicit chain.  Scratch
+// (upd, sol, rhs0) defaults to the context's own; given scratch takes the
+// direct solve.
+//   IMEX / trapezoidal: diagonal CDM step on I_d with the prediction of I_c,
+//     then S a^c_{n+1} = f_t(t_{n+1}) f^c - K^c u_pred and the correction.
+//   Central differences (consistent or HRZ mass): the same explicit kernel
+//     without prediction, then M^cc a^c_n = f_t(t_n) f^c - K^c u_n and
+//     u^c_{n+1} = 2 u^c_n - u^c_{n-1} + dt^2 a^c_n (Eqs. CDMstep, CDMacc).
+static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double* ft_dev = nullptr,
+                     double* upd = nullptr, double* sol = nullptr, double* rhs0 = nullptr) {
   const HostSetup& hs = c->hs;
+  const bool own = upd == nullptr;
+  if (own) {
+    upd = c->upd;
+    sol = c->sol;
+    rhs0 = c->rhs0;
+  }
   const double dt = hs.dt;
   double* Ucur = c->U[c->cur];
   double* Unext = c->U[1 - c->cur];
   const int64_t step = c->step;
+  const bool cdm = scheme_is_cdm(hs.pb.scheme);
   if (ev) cudaEventRecord(ev[0], s);
-  ExplicitArgs ea = explicit_args(c, Ucur, Unext, Unext, 2.0, -1.0, dt * dt, ft_at(hs, step), true);
+  ExplicitArgs ea = explicit_args(c, Ucur, Unext, Unext, 2.0, -1.0, dt * dt, ft_at(hs, step), !cdm);
   ea.ft_dev = ft_dev;
-  explicit_dispatch(c, ea, ntiles(c) + pred_blocks(c, true), s);
+  int grid = ntiles(c) + pred_blocks(c, !cdm);
+  if (hs.n_d == 0 && !c->hetero) {   // no explicit DOFs: prediction CTAs only
+    ea.ntx = ea.nty = ea.ntz = 0;
+    grid = pred_only_blocks(c);
+  }
+  explicit_dispatch(c, ea, grid, s);
   if (ev) cudaEventRecord(ev[1], s);
   if (hs.n_c > 0) {
-    if (c->solver == IMEX_SOLVER_DIRECT) {
-      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, c->upd, c->sol, c->rhs0, s);
+    if (cdm) {
+      launch_solve_chain(c, false, ft_at(hs, step), ft_dev, 3, Unext, Ucur, upd, sol, rhs0, s);
+    } else if (c->solver == IMEX_SOLVER_DIRECT || !own) {
+      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, s);
     } else {
       // Right-hand sides, PCG (correction included on convergence), then the
       // direct solve, whose launches return at once unless PCG fell short.
-      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, c->upd, c->sol, c->rhs0, s,
+      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, s,
                          nullptr, true);
       if (cudaError_t e = launch_pcg(c, Unext, s))
         return fail(IMEX_ERR_CUDA, std::string("imex_step: PCG launch: ") + cudaGetErrorString(e));
-      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, c->upd, c->sol, c->rhs0, s,
+      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, s,
                          c->pcg_status + 1);
     }
   }
@@ -3100,7 +3165,9 @@ int imex_fields(imex_ctx* c, int which, double* dst, int64_t len, int dst_on_dev
     double* out = c->tmp + on;
     switch (which) {
       case IMEX_FIELD_U: k_masked<<<nb, 256, 0, s>>>(out, c->U[c->cur] + on, c->cls, n, 3); break;
-      case IMEX_FIELD_U_PREV_D: k_masked<<<nb, 256, 0, s>>>(out, c->U[1 - c->cur] + on, c->cls, n, 1); break;
+      case IMEX_FIELD_U_PREV_D:   // u_{n-1} on I_d; on every active DOF for central differences
+        k_masked<<<nb, 256, 0, s>>>(out, c->U[1 - c->cur] + on, c->cls, n, scheme_is_cdm(c->hs.pb.scheme) ? 3 : 1);
+        break;
       case IMEX_FIELD_V_C:
       case IMEX_FIELD_A_C:
         cudaMemsetAsync(out, 0, n * sizeof(double), s);
@@ -3140,7 +3207,10 @@ int imex_set_fields(imex_ctx* c, int which, const double* src, int64_t len, int 
         k_masked_set<<<nb, 256, 0, s>>>(c->U[c->cur] + on, in, c->cls, n, NODE_D);
         k_masked_set<<<nb, 256, 0, s>>>(c->U[c->cur] + on, in, c->cls, n, NODE_C);
         break;
-      case IMEX_FIELD_U_PREV_D: k_masked_set<<<nb, 256, 0, s>>>(c->U[1 - c->cur] + on, in, c->cls, n, NODE_D); break;
+      case IMEX_FIELD_U_PREV_D:
+        k_masked_set<<<nb, 256, 0, s>>>(c->U[1 - c->cur] + on, in, c->cls, n, NODE_D);
+        if (scheme_is_cdm(c->hs.pb.scheme)) k_masked_set<<<nb, 256, 0, s>>>(c->U[1 - c->cur] + on, in, c->cls, n, NODE_C);
+        break;
       case IMEX_FIELD_V_C:
       case IMEX_FIELD_A_C:
         if (nc > 0)
@@ -3192,6 +3262,8 @@ int imex_set_solver(imex_ctx* c, int solver, double tol, int maxit) {
   if (!(tol > 0.0) || maxit < 1 || maxit > 100000) return fail(IMEX_ERR_ARG, "need tol > 0 and 1 <= maxit <= 100000");
   if (solver != IMEX_SOLVER_DIRECT && c->ncols > 1)
     return fail(IMEX_ERR_ARG, "the iterative solve serves single-column contexts");
+  if (solver != IMEX_SOLVER_DIRECT && scheme_is_cdm(c->hs.pb.scheme))
+    return fail(IMEX_ERR_ARG, "the iterative solve is of S; central differences solve with M^cc");
   c->solver = solver;
   c->pcg_tol = tol;
   c->pcg_maxit = maxit;
@@ -3279,6 +3351,7 @@ int imex_adjoint(imex_ctx* c, int64_t nsteps, const int64_t* rec_nodes, int nrec
   if (!c || nsteps < 1 || nrec < 1 || !rec_nodes || !data || !grad || !misfit || checkpoint_every < 1)
     return fail(IMEX_ERR_ARG, "bad arguments");
   const HostSetup& hs = c->hs;
+  if (hs.pb.scheme != kSchemeImex) return fail(IMEX_ERR_ARG, "the adjoint is of the Newmark IMEX scheme");
   for (int k = 0; k < nrec; ++k)
     if (rec_nodes[k] < 0 || rec_nodes[k] >= hs.nnodes) return fail(IMEX_ERR_ARG, "receiver node out of range");
   cudaStream_t s = c->stream;
@@ -3496,18 +3569,8 @@ extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
   double* rhs0 = sol + n_sol;
   cudaStream_t s = (cudaStream_t)stream;
   c->stream = s;
-  const double dt = hs.dt;
-  for (int64_t k = 0; k < n; ++k) {
-    double* Ucur = c->U[c->cur];
-    double* Unext = c->U[1 - c->cur];
-    const int64_t step = c->step;
-    ExplicitArgs ea = explicit_args(c, Ucur, Unext, Unext, 2.0, -1.0, dt * dt, ft_at(hs, step), true);
-    explicit_dispatch(c, ea, ntiles(c) + pred_blocks(c, true), s);
-    if (hs.n_c > 0) launch_solve_chain(c, true, ft_at(hs, step + 1), nullptr, 0, Unext, Unext, upd, sol, rhs0, s);
-    if (int rc = check_launch("imex_step_noalloc")) return rc;
-    c->cur = 1 - c->cur;
-    c->step = step + 1;
-  }
+  for (int64_t k = 0; k < n; ++k)
+    if (int rc = step_once(c, s, nullptr, nullptr, upd, sol, rhs0)) return rc;
   return IMEX_OK;
 }
 

@@ -109,7 +109,7 @@ struct WalkArgs {
   int rhs_only;                 // first launch: only form the right-hand sides (into rhs0)
   int rhs_given;                // first launch: every right-hand side is already in rhs0
   const int* skip;              // if set and *skip != 0: the launch does nothing (PCG converged)
-  const double* SRC;            // u_pred (step) or u_0 (initial acceleration), full grid
+  const double* SRC;            // u_pred (step), u_n (mode 3) or u_0 (initial acceleration), full grid
   const double* Kpair;          // per CTA: rows of the cell matrices of its pairs (m-major, scaled)
   const int64_t* kp_off;        // [cta] (16-byte aligned)
   const int64_t* kp_len;        // [cta] (even)
@@ -117,15 +117,16 @@ struct WalkArgs {
   int kp_smem;                  // 1: staged in shared memory; 0: read from global memory
   int P, Pd, dim, nx, ny;
   const double* fxc;
-  double ft;                    // f_t(t_{n+1}) (step) or f_t(0) (initial acceleration)
-  const double* ft_dev;         // if set: f_t(t_{n+1}) = ft_dev[1]
+  double ft;                    // f_t(t_{n+1}) (step; t_n in mode 3) or f_t(0) (initial acceleration)
+  const double* ft_dev;         // if set: f_t(t_{n+1}) = ft_dev[1] (mode 3: f_t(t_n) = ft_dev[0])
   double* rhs0;                 // right-hand side of every c-row not solved by the first launch
   double* upd;
   double* sol;
   // correction of the rows this launch finalises (backward only)
-  int mode;                     // 0: Newmark correction; 1: store the acceleration only
+  int mode;                     // 0: Newmark correction; 1: store the acceleration only;
+                                // 2: nothing (solution left in sol); 3: central-difference update
   const int* c_node;
-  double* U;                    // holds u_pred on I_c; receives u^c_{n+1}
+  double* U;                    // holds u_pred (mode 0) or u^c_{n-1} (mode 3) on I_c; receives u^c_{n+1}
   double* v_c;
   double* a_c;
   double dt;
@@ -157,6 +158,7 @@ struct TopArgs {
   int mode;
   const int* c_node;
   double* U;
+  const double* Un;             // u_n for the central-difference update (mode 3)
   double* v_c;
   double* a_c;
   double dt;

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <limits>
 #include <numeric>
 #include <thread>
 
@@ -327,6 +328,79 @@ double sym_max_eig(std::vector<double> A, int n) {
   }
   double m = -1e300;
   for (int i = 0; i < n; ++i) m = std::max(m, A[i * n + i]);
+  return m;
+}
+
+// Largest eigenvalue of the symmetric-definite pencil (K, M), both n x n
+// symmetric with M positive definite: lambda_max(L^{-1} K L^{-T}) with
+// M = L L^T.  Cyclic Jacobi rotations until the off-diagonal mass is below
+// (1e-15)^2 of the diagonal's.  Returns NaN when M is not positive definite.
+double gen_max_eig(const double* K, const double* M, int n) {
+  std::vector<double> L((size_t)n * n, 0.0), A((size_t)n * n), y(n);
+  for (int j = 0; j < n; ++j) {
+    double d = M[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(d > 0.0)) return std::numeric_limits<double>::quiet_NaN();
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double v = M[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) v -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = v / ljj;
+    }
+  }
+  auto lsolve = [&](double* v) {   // v <- L^{-1} v
+    for (int i = 0; i < n; ++i) {
+      double t = v[i];
+      for (int k = 0; k < i; ++k) t -= L[(size_t)i * n + k] * v[k];
+      v[i] = t / L[(size_t)i * n + i];
+    }
+  };
+  std::vector<double> Y((size_t)n * n);   // Y = L^{-1} K, column j at Y[j*n ..]
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < n; ++i) y[i] = K[(size_t)j * n + i];
+    lsolve(y.data());
+    for (int i = 0; i < n; ++i) Y[(size_t)j * n + i] = y[i];
+  }
+  // A = L^{-1} Y^T: column j of Y^T is row j of Y.
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < n; ++i) y[i] = Y[(size_t)i * n + j];
+    lsolve(y.data());
+    for (int i = 0; i < n; ++i) A[(size_t)i * n + j] = y[i];
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      const double v = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+      A[(size_t)i * n + j] = A[(size_t)j * n + i] = v;
+    }
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int i = 0; i < n; ++i) {
+      dia += A[(size_t)i * n + i] * A[(size_t)i * n + i];
+      for (int j = i + 1; j < n; ++j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+    }
+    if (off <= 1e-30 * dia) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[(size_t)p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double theta = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = cs * akp - sn * akq;
+          A[(size_t)k * n + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = cs * apk - sn * aqk;
+          A[(size_t)q * n + k] = sn * apk + cs * aqk;
+        }
+      }
+  }
+  double m = -1e300;
+  for (int i = 0; i < n; ++i) m = std::max(m, A[(size_t)i * n + i]);
   return m;
 }
 
@@ -668,7 +742,8 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
   const int64_t ncut0 = (int64_t)cut_cells.size();
   std::vector<double> cutK_all((size_t)ncut0 * Pd * Pd), cutM_all((size_t)ncut0 * Pd * Pd),
       cutF_all((size_t)ncut0 * Pd * ncols);
-  std::vector<double> cut_fill(ncut0);
+  std::vector<double> cut_fill(ncut0), cut_lam(ncut0, 0.0);
+  if (pb.scheme < kSchemeImex || pb.scheme > kSchemeTrapezoidal) return "unknown time integration scheme";
   parallel_for(ncut0, [&](int64_t b, int64_t e) {
     std::vector<QPoint> pts;
     std::vector<double> N(Pd), G(3 * Pd);
@@ -710,6 +785,17 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
         }
       }
       cut_fill[k] = wphys / wall;
+      if (pb.scheme == kSchemeCdmHrz) {
+        // HRZ: the diagonal scaled to the element mass, off-diagonals dropped (Eqs. HRZ).
+        double tot = 0.0, dsum = 0.0;
+        for (size_t q = 0; q < (size_t)Pd * Pd; ++q) tot += Me[q];
+        for (int a = 0; a < Pd; ++a) dsum += Me[a + (size_t)Pd * a];
+        for (int a = 0; a < Pd; ++a)
+          for (int b2 = 0; b2 < Pd; ++b2)
+            if (a != b2) Me[a + (size_t)Pd * b2] = 0.0;
+        for (int a = 0; a < Pd; ++a) Me[a + (size_t)Pd * a] *= tot / dsum;
+      }
+      if (scheme_is_cdm(pb.scheme)) cut_lam[k] = gen_max_eig(Ke, Me, Pd);
     }
   });
   // Fill-ratio test: cells with eta < 1e-10 are empty.
@@ -739,7 +825,7 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
     g.cell_nodes(cid, cn.data());
     for (int l = 0; l < Pd; ++l) {
       uint8_t& nc = hs.node_class[cn[l]];
-      if (hs.cell_type[cid] == CELL_CUT) nc = NODE_C;
+      if (hs.cell_type[cid] == CELL_CUT || pb.scheme == kSchemeTrapezoidal) nc = NODE_C;
       else if (nc == NODE_INACTIVE) nc = NODE_D;
     }
   }
@@ -774,7 +860,21 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
                         std::sqrt(uncutM[a] * uncutM[b]);
     double lam = sym_max_eig(A, Pd);
     hs.dt_crit_uncut = 2.0 / std::sqrt(lam);
-    hs.dt = (pb.dt > 0.0) ? pb.dt : pb.dt_factor * hs.dt_crit_uncut;
+    double dt_stable = hs.dt_crit_uncut;
+    if (scheme_is_cdm(pb.scheme)) {
+      // Central differences on the cut cells too: the smallest cell-wise step
+      // (the assembled lambda_max is bounded by the largest cell-wise one).
+      double lam_c = 0.0;
+      for (int64_t k : kept) {
+        if (!(cut_lam[k] > 0.0)) return "cut-cell mass matrix is not positive definite";
+        lam_c = std::max(lam_c, cut_lam[k]);
+      }
+      if (lam_c > 0.0) {
+        hs.dt_crit_cut_min = 2.0 / std::sqrt(lam_c);
+        dt_stable = std::min(dt_stable, hs.dt_crit_cut_min);
+      }
+    }
+    hs.dt = (pb.dt > 0.0) ? pb.dt : pb.dt_factor * dt_stable;
   }
 
   // Source vector f_x on the full grid: uncut cells by tensor GL, cut cells by spacetree.

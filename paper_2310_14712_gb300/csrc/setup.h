@@ -34,9 +34,18 @@ struct Problem {
   int ncols = 1;               // > 1: independent columns, column k loaded by source k alone
   double f0 = 1.0, sigma = 0.1, amp = 10.0;
   int wavelet = 0;
-  double dt = 0.0;             // <= 0: dt_factor * uncut critical step
+  double dt = 0.0;             // <= 0: dt_factor * the scheme's cell-wise critical step
   double dt_factor = 0.9;
+  int scheme = 0;              // kScheme*
 };
+
+// Time integration schemes on the same discretisation (the method and the
+// paper's comparison schemes).  The values are the public IMEX_SCHEME_* codes.
+constexpr int kSchemeImex = 0;         // Newmark IMEX (Fig. TrapCDMIMEX)
+constexpr int kSchemeCdm = 1;          // central differences, consistent cut-cell masses
+constexpr int kSchemeCdmHrz = 2;       // central differences, HRZ-lumped cut-cell masses (Eqs. HRZ)
+constexpr int kSchemeTrapezoidal = 3;  // trapezoidal Newmark on every DOF
+inline bool scheme_is_cdm(int s) { return s == kSchemeCdm || s == kSchemeCdmHrz; }
 
 // One node of the nested-dissection tree of the implicit partition.  Its DOFs
 // are the contiguous c-index range [beg, end); `rows` are the ancestor
@@ -109,6 +118,9 @@ struct HostSetup {
   double residual_S = 0, residual_M = 0;  // ||A x - b|| / ||b|| of a host replay of the device solve
 
   double dt = 0, dt_crit_uncut = 0;
+  // Smallest cell-wise critical step of the cut cells for the mass the scheme
+  // uses (central-difference schemes only; 0 when not computed).
+  double dt_crit_cut_min = 0;
   double setup_seconds = 0;
 };
 

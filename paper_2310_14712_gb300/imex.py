@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
         [(n, ctypes.c_double) for n in ("dt", "dt_crit_uncut", "setup_seconds", "residual_S", "residual_M")] + \
         [(n, ctypes.c_int64) for n in ("solve_levels", "solve_ctas", "solve_smem_bytes", "launches_per_step",
                                     "rhs_pairs", "ncols", "explicit_tile_cells")] + \
-        [(n, ctypes.c_double) for n in ("explicit_tile_us_large", "explicit_tile_us_small")]
+        [(n, ctypes.c_double) for n in ("explicit_tile_us_large", "explicit_tile_us_small")] + \
+        [("scheme", ctypes.c_int64), ("dt_crit_cut_min", ctypes.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -71,6 +72,9 @@ _lib.imex_setup.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double,
 _lib.imex_setup_batch.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                   ctypes.POINTER(Source), ctypes.c_int, ctypes.POINTER(Alloc),
                                   ctypes.POINTER(_vp)]
+_lib.imex_setup_scheme.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(Source), ctypes.c_int, ctypes.c_int, ctypes.POINTER(Alloc),
+                                   ctypes.POINTER(_vp)]
 _lib.imex_step.argtypes = [_vp, ctypes.c_int64, _vp]
 _lib.imex_adjoint.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, _dp,
                               ctypes.c_int, _dp, _dp]
@@ -98,7 +102,7 @@ _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctyp
                                         ctypes.POINTER(Stats)]
 
 # Every symbol include/imex.h declares (checked by the CPU tests).
-EXPORTS = ("imex_setup", "imex_setup_batch", "imex_adjoint", "imex_set_solver", "imex_pcg_train", "imex_pcg_status",
+EXPORTS = ("imex_setup", "imex_setup_batch", "imex_setup_scheme", "imex_adjoint", "imex_set_solver", "imex_pcg_train", "imex_pcg_status",
            "imex_fsai_kaporin", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
            "imex_set_initial", "imex_info", "imex_last_error", "imex_destroy", "imex_gll_points",
            "imex_gauss_points", "imex_host_setup_export")
@@ -151,6 +155,8 @@ def _mesh_source(dim, lo, hi, ncells, depth, holes, rho, c0, cell_c, src_pos, f0
 
 
 SOLVERS = {"direct": 0, "pcg_fsai": 1, "pcg_jacobi": 2}
+# Time integration schemes (IMEX_SCHEME_*): the method and the paper's comparison schemes.
+SCHEMES = {"imex": 0, "cdm": 1, "cdm_hrz": 2, "trapezoidal": 3}
 
 
 def fsai_kaporin(s_ptr, s_col, s_val, g_ptr, g_col, g_val, stream=None):
@@ -228,12 +234,14 @@ class Imex:
     from explicit arguments.  Device memory comes from PyTorch.  With
     ncols > 1 the context steps ncols independent simulations, column k
     loaded by the source at src_pos[k] alone (imex_setup_batch); fields then
-    have ncols * n_nodes entries, column after column.
+    have ncols * n_nodes entries, column after column.  `scheme` picks the
+    time integration (SCHEMES; imex_setup_scheme): the method itself or one of
+    the paper's comparison schemes on the same discretisation.
     """
 
     def __init__(self, dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0, src_sigma,
                  src_amp=10.0, wavelet=0, rho=1.0, c0=1.0, cell_c=None, dt=0.0, use_torch_alloc=True,
-                 ncols=1, **_):
+                 ncols=1, scheme="imex", **_):
         import torch
         self.torch = torch
         if not torch.cuda.is_available():
@@ -244,8 +252,8 @@ class Imex:
         self._allocator = _TorchAllocator(self.device) if use_torch_alloc else None
         ctx = _vp()
         al = ctypes.byref(self._allocator.struct) if self._allocator else None
-        _check(_lib.imex_setup_batch(ctypes.byref(m), p, alpha, dt, ctypes.byref(s), int(ncols), al,
-                                     ctypes.byref(ctx)), "imex_setup_batch")
+        _check(_lib.imex_setup_scheme(ctypes.byref(m), p, alpha, dt, ctypes.byref(s), int(ncols),
+                                      SCHEMES[scheme], al, ctypes.byref(ctx)), "imex_setup_scheme")
         self._ctx = ctx
         self.stats = self.info()
         self.n_nodes = self.stats["n_nodes"]

@@ -151,6 +151,17 @@ def test_many_holes_and_components():
     assert info["n_components"] > 5
 
 
+def test_multilevel_solve_schedule():
+    # A 6 x 6 lattice of holes (r = 0.07) on 16 x 16 cells, p = 4: one implicit
+    # component of about 4000 DOFs whose dissection tree is walked in several
+    # launches per direction below the dense top (descendant updates gathered
+    # across launches).
+    centres = (np.arange(6) + 0.5) / 6.0
+    w = _box(16, 4, [[x, y, 0.07, 0.07] for x in centres for y in centres])
+    e_phys, e_all, info = _check_run(w, 100)
+    assert info["solve_levels"] >= 2
+
+
 def test_standing_mode_against_oracle_and_closed_form():
     # alpha = 1 everywhere: u = cos(pi x) cos(pi y) cos(sqrt(2) pi t) on the box.
     w = _box(8, 4, [[0.5, 0.5, 0.13, 0.13]], alpha=1.0)

@@ -1,0 +1,135 @@
+"""GPU parity of the paper's comparison schemes (central differences with the
+consistent and the HRZ-lumped cut-cell masses, trapezoidal Newmark) against
+the oracle (oracle/schemes.py), through the C-ABI.
+
+Gates as for the method: physical DOFs relative L2 <= 1e-11; all active DOFs
+<= max(1e-11, FLOOR_FACTOR x the spread of oracle runs that differ only in
+the sparse ordering of their solves)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import pipeline, schemes
+from paper_2310_14712_gb300 import workloads
+
+from parity_util import FLOOR_FACTOR, ORDERINGS, phys_mask
+
+pytestmark = pytest.mark.gpu
+
+
+def _imex():
+    from paper_2310_14712_gb300 import imex
+    return imex
+
+
+def _gpu_run(w, scheme, nsteps, u0=None):
+    imex = _imex()
+    with imex.Imex.from_workload(w, scheme=scheme) as g:
+        if u0 is not None:
+            g.set_initial(u0)
+        g.step(nsteps)
+        st = {k: g.fields(k, out=np.zeros(g.n_nodes)) for k in ("u", "u_prev_d", "v_c", "a_c")}
+        info = g.info()
+    return st, info
+
+
+def _floor(s, scheme, nsteps, ref, u0):
+    fl = 0.0
+    for spec in ORDERINGS:
+        alt = schemes.run(s, scheme, nsteps, u0=u0, permc_spec=spec)
+        fl = max(fl, pipeline.relative_l2(alt.u, ref.u, s.disc.active))
+    return fl
+
+
+def _check(w, scheme, nsteps, u0=None):
+    st, info = _gpu_run(w, scheme, nsteps, u0)
+    w2 = dataclasses.replace(w, dt=info["dt"])
+    s = pipeline.setup(**w2.kwargs())
+    ref = schemes.run(s, scheme, nsteps, u0=u0)
+    act = s.disc.active
+    phys = phys_mask(s, w.holes)
+    e_phys = pipeline.relative_l2(st["u"], ref.u, phys)
+    e_all = pipeline.relative_l2(st["u"], ref.u, act)
+    tol_all = max(1e-11, FLOOR_FACTOR * _floor(s, scheme, nsteps, ref, u0))
+    assert e_phys <= 1e-11, (e_phys, e_all)
+    assert e_all <= tol_all, (e_all, tol_all)
+    if ref.u_prev is not None:
+        assert pipeline.relative_l2(st["u_prev_d"], ref.u_prev, phys) <= 1e-11
+    if ref.v is not None:
+        assert pipeline.relative_l2(st["v_c"], ref.v, phys) <= 1e-10
+        assert pipeline.relative_l2(st["a_c"], ref.a, phys) <= 1e-10
+    return s, info
+
+
+def _standing(w):
+    s = pipeline.setup(**w.kwargs())
+    X = s.grid.node_coords()
+    return np.cos(np.pi * X[:, 0]) * np.cos(np.pi * X[:, 1])
+
+
+@pytest.mark.parametrize("scheme", ["cdm", "cdm_hrz"])
+def test_central_difference_time_step_is_the_cellwise_minimum(scheme):
+    w = workloads.plate16()
+    _, info = _gpu_run(w, scheme, 0)
+    s = pipeline.setup(**w.kwargs())
+    dt_u, dt_c = schemes.cellwise_critical_dt(s, "consistent" if scheme == "cdm" else "hrz")
+    assert info["scheme"] == _imex().SCHEMES[scheme]
+    assert info["dt_crit_uncut"] == pytest.approx(dt_u, rel=1e-12)
+    assert info["dt_crit_cut_min"] == pytest.approx(dt_c, rel=1e-10)
+    assert info["dt"] == pytest.approx(0.9 * min(dt_u, dt_c), rel=1e-10)
+
+
+@pytest.mark.parametrize("scheme", ["cdm", "cdm_hrz", "trapezoidal"])
+def test_schemes_plate16_match_oracle(scheme):
+    w = workloads.plate16()
+    s, info = _check(w, scheme, 300, u0=_standing(w))
+    if scheme == "trapezoidal":
+        assert info["n_d"] == 0 and info["n_c"] == int(s.disc.active.sum())
+    else:
+        assert info["n_d"] > 0 and info["n_c"] > 0
+
+
+@pytest.mark.parametrize("scheme", ["cdm", "cdm_hrz", "trapezoidal"])
+@pytest.mark.parametrize("p", [2, 5])
+def test_schemes_ragged_grid(scheme, p):
+    w = workloads.Workload("box", 2, (0.0, 0.0), (1.3, 0.7), (13, 7), p, 1e-5, 3,
+                           np.array([[0.55, 0.45, 0.21, 0.21]]), np.array([[0.23, 0.31]]), 3.0, 0.08, 0)
+    _check(w, scheme, 60)
+
+
+def test_central_differences_without_cut_cells_are_imex_bitwise():
+    w = workloads.Workload("box", 2, (0.0, 0.0), (1.0, 1.0), (9, 9), 4, 1e-5, 3,
+                           np.zeros((0, 4)), np.array([[0.23, 0.31]]), 3.0, 0.08, 0)
+    ref, _ = _gpu_run(w, "imex", 80)
+    for scheme in ("cdm", "cdm_hrz"):
+        st, info = _gpu_run(w, scheme, 80)
+        assert info["n_c"] == 0
+        assert np.array_equal(st["u"], ref["u"]) and np.array_equal(st["u_prev_d"], ref["u_prev_d"])
+
+
+@pytest.mark.parametrize("scheme", ["cdm_hrz", "trapezoidal"])
+def test_schemes_with_independent_columns(scheme):
+    imex = _imex()
+    w = workloads.multisource(nsrc=3)
+    n = 80
+    with imex.Imex.from_workload(w, ncols=3, scheme=scheme) as g:
+        g.step(n)
+        u = g.fields("u", out=np.zeros(g.field_len)).reshape(3, -1)
+        dt = g.info()["dt"]
+    kw = w.kwargs()
+    pos = kw.pop("src_pos")
+    kw["dt"] = dt
+    for k, s in enumerate(pipeline.setup_columns(pos, **kw)):
+        ref = schemes.run(s, scheme, n)
+        assert pipeline.relative_l2(u[k], ref.u, phys_mask(s, w.holes)) <= 1e-11
+
+
+def test_scheme_restrictions():
+    imex = _imex()
+    w = workloads.plate16()
+    with imex.Imex.from_workload(w, scheme="cdm") as g:
+        with pytest.raises(imex.ImexError):
+            g.set_solver("pcg_jacobi")
+        with pytest.raises(imex.ImexError):
+            g.adjoint(4, np.array([5]), np.zeros((4, 1, 1)))
