@@ -1182,32 +1182,70 @@ __global__ void k_applyK(HetArgs h, const uint8_t* cls, const double* x, double*
   out[o + i] = cls[i] ? het_row(h, x + o, i) : 0.0;
 }
 
-// grad[cell_id[e]] -= sum over columns of (2 / c_e) (hv_e . K_e un_e + gv_e . K_e un1_e)
-// (dK/dc_e = 2 c_e K_e(1) = (2 / c_e) K_e); one thread per cell, columns in order.
-__global__ void k_grad_cells(HetArgs h, int ncols, int64_t cs, const double* hv, const double* un,
-                             const double* gv, const double* un1, double* grad) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= h.ncell) return;
-  const double* K = h.Kall + (size_t)h.cell_koff[e] * h.Pd * h.Pd;
-  double total = 0.0;
-  for (int col = 0; col < ncols; ++col) {
-    const int64_t b = (int64_t)col * cs + h.cell_base[e];
-    double s = 0.0;
-    for (int l = 0; l < h.Pd; ++l) {
-      const int ol = local_offset(h, l);
-      const double hl = hv[b + ol], gl = gv[b + ol];
-      if (hl == 0.0 && gl == 0.0) continue;
-      double ku = 0.0, ku1 = 0.0;
-      for (int m = 0; m < h.Pd; ++m) {
-        const int om = local_offset(h, m);
-        ku = fma(K[l * h.Pd + m], un[b + om], ku);
-        ku1 = fma(K[l * h.Pd + m], un1[b + om], ku1);
-      }
-      s = fma(hl, ku, fma(gl, ku1, s));
+// grad[cell_id[e]] -= (2 / c_e) sum over columns of (hv_e . K_e un_e + gv_e . K_e un1_e)
+// (dK/dc_e = 2 c_e K_e(1) = (2 / c_e) K_e, K_e = w_e times the stored matrix).
+// One CTA per cell.  The cell matrix is staged in
+// shared memory when it fits (kGradKSmem), the cell's values kGradCols
+// columns at a time; threads take (column, row) items in a fixed assignment
+// and the block sums in a fixed tree, so results are deterministic.
+constexpr int kGradThreads = 128;
+constexpr int kGradCols = 16;
+constexpr int kGradKSmem = 4096;   // doubles of K_e staged (P^d <= 64)
+__global__ void __launch_bounds__(kGradThreads) k_grad_cells(HetArgs h, int ncols, int64_t cs, const double* hv,
+                                                             const double* un, const double* gv, const double* un1,
+                                                             double* grad) {
+  extern __shared__ double sgc[];
+  const int e = blockIdx.x;
+  const int tid = threadIdx.x, Pd = h.Pd;
+  const bool kin = Pd * Pd <= kGradKSmem;
+  double* Ks = sgc;                                   // Pd x Pd when it fits
+  double* vh = sgc + (kin ? Pd * Pd : 0);             // kGradCols x Pd each
+  double* vu = vh + kGradCols * Pd;
+  double* vg = vu + kGradCols * Pd;
+  double* vu1 = vg + kGradCols * Pd;
+  double* red = vu1 + kGradCols * Pd;                 // kGradThreads
+  const double* Kg = h.Kall + (size_t)h.cell_koff[e] * Pd * Pd;
+  if (kin)
+    for (int i = tid; i < Pd * Pd; i += kGradThreads) Ks[i] = Kg[i];
+  const double* K = kin ? Ks : Kg;
+  const int64_t base = h.cell_base[e];
+  double part = 0.0;
+  for (int c0 = 0; c0 < ncols; c0 += kGradCols) {
+    const int ncl = min(kGradCols, ncols - c0);
+    for (int i = tid; i < ncl * Pd; i += kGradThreads) {
+      const int64_t b = (int64_t)(c0 + i / Pd) * cs + base + local_offset(h, i % Pd);
+      vh[i] = hv[b];
+      vu[i] = un[b];
+      vg[i] = gv[b];
+      vu1[i] = un1[b];
     }
-    total = fma(h.cell_w[e], s, total);
+    __syncthreads();
+    for (int i = tid; i < ncl * Pd; i += kGradThreads) {
+      const double hl = vh[i], gl = vg[i];
+      if (hl == 0.0 && gl == 0.0) continue;
+      const int l = i % Pd, o = i - l;
+      double ku = 0.0, ku1 = 0.0;
+      for (int m = 0; m < Pd; ++m) {
+        const double k = K[l * Pd + m];
+        ku = fma(k, vu[o + m], ku);
+        ku1 = fma(k, vu1[o + m], ku1);
+      }
+      part = fma(hl, ku, fma(gl, ku1, part));
+    }
+    __syncthreads();
   }
-  grad[h.cell_id[e]] -= 2.0 / h.cell_c[e] * total;
+  red[tid] = part;
+  __syncthreads();
+  for (int w = kGradThreads / 2; w > 0; w >>= 1) {
+    if (tid < w) red[tid] += red[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) grad[h.cell_id[e]] -= 2.0 / h.cell_c[e] * (h.cell_w[e] * red[0]);
+}
+
+size_t grad_cells_smem(int Pd) {
+  return ((Pd * Pd <= kGradKSmem ? (size_t)Pd * Pd : 0) + 4 * (size_t)kGradCols * Pd + kGradThreads) *
+         sizeof(double);
 }
 
 // Adjoint step, part 1 (c rows): rhs0 = abar + beta dt^2 ubar^c + gamma dt vbar;
@@ -3439,6 +3477,8 @@ int imex_adjoint(imex_ctx* c, int64_t nsteps, const int64_t* rec_nodes, int nrec
   e = e ? e : cudaMemsetAsync(abar, 0, ncols * nc * sizeof(double), s);
   const double dt = hs.dt;
   ExplicitArgs ea = explicit_args(c, c->U[0], c->U[0], c->U[0], 0.0, 0.0, 0.0, 0.0, false);
+  e = e ? e : cudaFuncSetAttribute(k_grad_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)grad_cells_smem(hs.Pd));
   for (int64_t sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
     const int64_t nb = sg * Kc, ne = std::min(N, nb + Kc);
     e = restore(ck + sg * ck_len);
@@ -3466,7 +3506,7 @@ int imex_adjoint(imex_ctx* c, int64_t nsteps, const int64_t* rec_nodes, int nrec
       k_applyK<<<gn, kThreads, 0, s>>>(ha, c->cls, z1, kg, nn);
       k_adj_mid<<<gn, kThreads, 0, s>>>(ea, nn, ubar, kg, T, z2, c->node_c_dev, ucp, dt);
       k_applyK<<<gn, kThreads, 0, s>>>(ha, c->cls, z2, kh, nn);
-      k_grad_cells<<<(ha.ncell + kThreads - 1) / kThreads, kThreads, 0, s>>>(ha, ncols, nn, z2, un, z1, un1, dgrad);
+      k_grad_cells<<<ha.ncell, kGradThreads, grad_cells_smem(hs.Pd), s>>>(ha, ncols, nn, z2, un, z1, un1, dgrad);
       k_adj_post<<<gn, kThreads, 0, s>>>(ea, nn, kh, T, ubar, ubar_prev, c->node_c_dev, ucp, vcp, vbar, abar, dt);
       if (int rc = check_launch("imex_adjoint")) {
         cleanup();
