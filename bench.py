@@ -77,7 +77,7 @@ def profiled_traffic(phase, workload):
     if len(vals) != 2:
         return None
     h = hashlib.sha256()
-    for f in ("imex.cu", "kernels.cuh"):
+    for f in ("step_kernels.cuh", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_2310_14712_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return int(vals["dram_bytes_per_launch"]) if h.hexdigest() == vals["source_sha256"] else None
@@ -141,6 +141,35 @@ def measure_learned_pcg(imex, w, steps, stream, flush, epochs=300):
                                            max(out["pcg_jacobi"]["iterations_per_step"], 1e-30))
     out["learned_vs_direct_value"] = out["pcg_fsai"]["value"] / out["direct"]["value"]
     g.close()
+    return out
+
+
+def measure_schemes(imex, workloads, steps, stream, flush):
+    """The paper's comparison schemes against the method on the same
+    discretisation, each at its own default step (0.9 x its cell-wise critical
+    step): per-step time, and simulated time advanced per second of device
+    time, which is what the schemes' different stable steps trade against.
+    The all-implicit trapezoidal scheme runs on the 16x16-cell plate only (on
+    the 256x128 plate its dissection separators exceed the device solve's
+    256-row supernodes)."""
+    out = {"l2": "flushed between timed steps", "steps": steps, "unit": "DOF-steps/s"}
+    for wname, w, names in (("plate16", workloads.plate16(), ("imex", "cdm", "cdm_hrz", "trapezoidal")),
+                            ("plate256", workloads.plate256(), ("imex", "cdm", "cdm_hrz"))):
+        res = {"workload": workload_name(w)}
+        for sch in names:
+            with imex.Imex.from_workload(w, scheme=sch) as g:
+                st = g.info()
+                n_act = st["n_d"] + st["n_c"]
+                g.step(3)
+                ms = time_flushed(g, steps, stream, flush)
+            res[sch] = {"dt": st["dt"], "dt_crit_uncut": st["dt_crit_uncut"],
+                        "dt_crit_cut_min": st["dt_crit_cut_min"] or None, "n_d": st["n_d"], "n_c": st["n_c"],
+                        "ms_per_step": ms / steps, "value": n_act * steps / (ms * 1e-3),
+                        "sim_time_per_s": st["dt"] * steps / (ms * 1e-3)}
+        ref = res["imex"]["sim_time_per_s"]
+        for sch in names:
+            res[sch]["sim_time_vs_imex"] = res[sch]["sim_time_per_s"] / ref
+        out[wname] = res
     return out
 
 
@@ -305,7 +334,8 @@ def run_reference(args):
 
 
 def workload_name(w):
-    return (f"{w.name}: [0,2]x[0,1] minus {len(w.holes)} circles, {w.ncells[0]}x{w.ncells[1]} cells, "
+    box = "x".join(f"[{a:g},{b:g}]" for a, b in zip(w.lo, w.hi))
+    return (f"{w.name}: {box} minus {len(w.holes)} circles, {w.ncells[0]}x{w.ncells[1]} cells, "
             f"p={w.p}, alpha={w.alpha:g}, quadtree depth {w.depth}, Ricker f0={w.f0:g}")
 
 
@@ -420,10 +450,11 @@ def run_gpu(args):
         "setup_seconds": st["setup_seconds"],
         "wall_seconds_timed_loop": wall,
     }
-    if ws == 1:
+    if ws == 1 and not args.no_extras:
         line["batched"] = measure_batched(imex, workloads, min(args.steps, 200), stream, flush)
         line["learned_pcg"] = measure_learned_pcg(imex, w, min(args.steps, 20), stream, flush)
         line["adjoint"] = measure_adjoint(imex, workloads)
+        line["schemes"] = measure_schemes(imex, workloads, min(args.steps, 200), stream, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n_act_cpu, secs = cpu_oracle_rate(w, args.cpu_steps)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -447,6 +478,8 @@ def main():
     ap.add_argument("--workload", default="plate256")
     ap.add_argument("--cpu-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the headline measurement (no batched, PCG, adjoint or scheme lines)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

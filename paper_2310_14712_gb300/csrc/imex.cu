@@ -35,876 +35,7 @@ int fail(int code, const std::string& msg) {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-// ---------------------------------------------------------------------------
-// A1 + A2 (+ A3): explicit apply on the tensor grid, CDM update, prediction.
-//
-// A tile owns OX x OY nodes (TC x TC cells).  With u staged in shared memory
-// together with one halo cell on the low side, the stiffness rows of the
-// owned nodes are formed by sum factorisation:
-//   x pass: T1 = (sx K1)_x u, T2 = (M1)_x u, cell by cell (the two cell
-//           contributions at a vertex are added in a fix-up pass),
-//   y pass: r = (M1)_y T1 + (sy K1)_y T2, again cell by cell plus fix-up.
-// Each 1D product uses the symmetry of the GLL nodes: K1 commutes with the
-// reflection x -> -x, so it maps the even and odd parts of a vector
-// separately (P^2 -> about P^2/2 FMAs), and the exact mass is the GLL-lumped
-// mass plus a rank-one term, M1 = diag(w) + C a a^T (GLL quadrature is exact
-// to degree 2p-1; the product of two basis functions differs from a
-// polynomial it integrates exactly by a_i a_j x^{2p}, a_i the leading
-// coefficient of the i-th basis function), so M1 v costs about 3P.
-// For an I_d node every surrounding cell is uncut, so this equals its row of
-// K^d u_n (Eq. Kd).  Nodes of I_c and inactive nodes are computed but not
-// written.  Cells outside the grid contribute nothing.
-template <int P, int TC>
-__global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D ops) {
-  constexpr int p = P - 1;
-  constexpr int H = P / 2;                // pairs (i, P-1-i) of the even-odd split
-  constexpr bool kOdd = (P % 2) == 1;     // a centre node; then a_{P-1-i} = a_i, else -a_i
-  constexpr int OX = TC * p, OY = TC * p;
-  constexpr int RX = (TC + 1) * p + 1, RY = RX;
-  constexpr int NC = TC + 1;
-  extern __shared__ double sm[];
-  const int tid = threadIdx.x;
-  const int ntiles = a.ntx * a.nty;
-  // Column of an independent-columns context (blockIdx.y).
-  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
-  const double* Uc = a.U + on;
-  const double* Wc = a.W + on;     // may alias OUTc
-  double* OUTc = a.OUT + on;
-  const double* fxc = a.fx + on;
-  // The first solve launch may start staging its constant factor blocks now;
-  // it waits for this grid (griddepcontrol.wait) before it reads u.
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-
-  if ((int)blockIdx.x >= ntiles) {
-    // Newmark prediction on I_c (Fig. TrapCDMIMEX, "Prediction").
-    const double c1 = a.dt, c2 = (0.5 - kNewmarkBeta) * a.dt * a.dt;
-    const int stride = (gridDim.x - ntiles) * blockDim.x;
-    for (int r = (blockIdx.x - ntiles) * blockDim.x + tid; r < a.n_c; r += stride) {
-      const int node = a.c_node[r];
-      OUTc[node] = Uc[node] + c1 * a.v_c[oc + r] + c2 * a.a_c[oc + r];
-    }
-    return;
-  }
-
-  double* su = sm;                 // RY x RX
-  double* t1 = su + RY * RX;       // RY x OX
-  double* t2 = t1 + RY * OX;       // RY x OX
-  double* scr = t2 + RY * OX;
-  double* tl1 = scr;               // RY x NC vertex partials (x pass)
-  double* tr1 = tl1 + RY * NC;
-  double* tl2 = tr1 + RY * NC;
-  double* tr2 = tl2 + RY * NC;
-  double* rr = scr;                // OY x OX (aliases the x-pass partials)
-  double* rb = rr + OY * OX;       // NC x OX vertex partials (y pass)
-  double* rt = rb + NC * OX;
-
-  const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
-  const int X0 = tx * OX, Y0 = ty * OY;
-  const int cx0 = X0 / p - 1, cy0 = Y0 / p - 1;
-
-  for (int idx = tid; idx < RY * RX; idx += kThreads) {
-    const int yy = idx / RX, xx = idx - yy * RX;
-    const int gx = X0 - p + xx, gy = Y0 - p + yy;
-    su[idx] = (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny) ? Uc[(size_t)gy * a.nx + gx] : 0.0;
-  }
-  __syncthreads();
-
-  // x pass: item = (row yy, cell cc), rows fastest.
-  for (int it = tid; it < RY * NC; it += kThreads) {
-    const int cc = it / RY, yy = it - cc * RY;
-    const int cx = cx0 + cc;
-    if (cx < 0 || cx >= a.ncx) {   // a cell outside the grid contributes nothing
-      if (cc >= 1) {
-#pragma unroll
-        for (int i = 1; i < p; ++i) {
-          t1[yy * OX + (cc - 1) * p + i] = 0.0;
-          t2[yy * OX + (cc - 1) * p + i] = 0.0;
-        }
-      }
-      tl1[yy * NC + cc] = 0.0;
-      tr1[yy * NC + cc] = 0.0;
-      tl2[yy * NC + cc] = 0.0;
-      tr2[yy * NC + cc] = 0.0;
-      continue;
-    }
-    double v[P], o1[P], o2[P];
-#pragma unroll
-    for (int j = 0; j < P; ++j) v[j] = su[yy * RX + cc * p + j];
-    constexpr bool valid = true;
-    // Even and odd parts of v under x -> -x.
-    double e[H], o[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-      e[j] = v[j] + v[P - 1 - j];
-      o[j] = v[j] - v[P - 1 - j];
-    }
-    // o1 = (sx K1) v: the even part maps to the even part, odd to odd.
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-      double ev = kOdd ? ops.kxc[i] * v[H] : 0.0, od = 0.0;
-#pragma unroll
-      for (int j = 0; j < H; ++j) {
-        ev = fma(ops.kxe[i][j], e[j], ev);
-        od = fma(ops.kxo[i][j], o[j], od);
-      }
-      o1[i] = valid ? ev + od : 0.0;
-      o1[P - 1 - i] = valid ? ev - od : 0.0;
-    }
-    if (kOdd) {
-      double ev = ops.kxc[H] * v[H];
-#pragma unroll
-      for (int j = 0; j < H; ++j) ev = fma(ops.kxe[H][j], e[j], ev);
-      o1[H] = valid ? ev : 0.0;
-    }
-    // o2 = M1 v = w .* v + C a (a^T v).
-    double sa = kOdd ? ops.a[H] * v[H] : 0.0;
-#pragma unroll
-    for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? e[j] : o[j], sa);
-#pragma unroll
-    for (int i = 0; i < P; ++i) o2[i] = valid ? fma(ops.w[i], v[i], ops.ca[i] * sa) : 0.0;
-    if (cc >= 1) {
-#pragma unroll
-      for (int i = 1; i < p; ++i) {
-        t1[yy * OX + (cc - 1) * p + i] = o1[i];
-        t2[yy * OX + (cc - 1) * p + i] = o2[i];
-      }
-    }
-    tl1[yy * NC + cc] = o1[0];
-    tr1[yy * NC + cc] = o1[p];
-    tl2[yy * NC + cc] = o2[0];
-    tr2[yy * NC + cc] = o2[p];
-  }
-  __syncthreads();
-  for (int it = tid; it < RY * TC; it += kThreads) {
-    const int k = it / RY, yy = it - k * RY;
-    t1[yy * OX + k * p] = tr1[yy * NC + k] + tl1[yy * NC + k + 1];
-    t2[yy * OX + k * p] = tr2[yy * NC + k] + tl2[yy * NC + k + 1];
-  }
-  __syncthreads();
-
-  // y pass: item = (column xo, cell row cr), columns fastest.
-  for (int it = tid; it < OX * NC; it += kThreads) {
-    const int cr = it / OX, xo = it - cr * OX;
-    const int cy = cy0 + cr;
-    if (cy < 0 || cy >= a.ncy) {   // a cell outside the grid contributes nothing
-      if (cr >= 1) {
-#pragma unroll
-        for (int i = 1; i < p; ++i) rr[((cr - 1) * p + i) * OX + xo] = 0.0;
-      }
-      rb[cr * OX + xo] = 0.0;
-      rt[cr * OX + xo] = 0.0;
-      continue;
-    }
-    double va[P], vb[P];
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      va[j] = t1[(cr * p + j) * OX + xo];
-      vb[j] = t2[(cr * p + j) * OX + xo];
-    }
-    constexpr bool valid = true;
-    // o = M1 va + (sy K1) vb, the mass in rank-one form, the stiffness even-odd.
-    double sa = kOdd ? ops.a[H] * va[H] : 0.0;
-#pragma unroll
-    for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? va[j] + va[P - 1 - j] : va[j] - va[P - 1 - j], sa);
-    double e[H], od_[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-      e[j] = vb[j] + vb[P - 1 - j];
-      od_[j] = vb[j] - vb[P - 1 - j];
-    }
-    double o[P];
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-      double ev = kOdd ? ops.kyc[i] * vb[H] : 0.0, od = 0.0;
-#pragma unroll
-      for (int j = 0; j < H; ++j) {
-        ev = fma(ops.kye[i][j], e[j], ev);
-        od = fma(ops.kyo[i][j], od_[j], od);
-      }
-      const int k = P - 1 - i;
-      o[i] = valid ? fma(ops.w[i], va[i], fma(ops.ca[i], sa, ev + od)) : 0.0;
-      o[k] = valid ? fma(ops.w[k], va[k], fma(ops.ca[k], sa, ev - od)) : 0.0;
-    }
-    if (kOdd) {
-      double ev = ops.kyc[H] * vb[H];
-#pragma unroll
-      for (int j = 0; j < H; ++j) ev = fma(ops.kye[H][j], e[j], ev);
-      o[H] = valid ? fma(ops.w[H], va[H], fma(ops.ca[H], sa, ev)) : 0.0;
-    }
-    if (cr >= 1) {
-#pragma unroll
-      for (int i = 1; i < p; ++i) rr[((cr - 1) * p + i) * OX + xo] = o[i];
-    }
-    rb[cr * OX + xo] = o[0];
-    rt[cr * OX + xo] = o[p];
-  }
-  __syncthreads();
-  for (int it = tid; it < TC * OX; it += kThreads) {
-    const int k = it / OX, xo = it - k * OX;
-    rr[(k * p) * OX + xo] = rt[k * OX + xo] + rb[(k + 1) * OX + xo];
-  }
-  __syncthreads();
-
-  // CDM update of the owned I_d nodes (Eqs. CDMacc, CDMstep).
-  for (int it = tid; it < OY * OX; it += kThreads) {
-    const int yo = it / OX, xo = it - yo * OX;
-    const int gx = X0 + xo, gy = Y0 + yo;
-    if (gx >= a.nx || gy >= a.ny) continue;
-    const size_t g = (size_t)gy * a.nx + gx;
-    if (a.cls[g] != NODE_D) continue;
-    const double r = rr[yo * OX + xo];
-    const double u = su[(yo + p) * RX + xo + p];
-    const double minv = a.winv_x[gx] * a.winv_y[gy];
-    const double ft = a.ft_dev ? a.ft_dev[0] : a.ft;
-    const double acc = minv * (ft * fxc[g] - r);
-    OUTc[g] = a.cu * u + a.cw * Wc[g] + a.ca * acc;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// A1 + A2 (+ A3) in 3D: the same tensor-grid scheme with three passes.  A
-// tile owns OX^3 nodes (TC^3 cells); u is staged with one halo cell on the
-// low side of each axis.
-//   x pass: TK = (sx K1)_x u, TM = (M1)_x u          (every staged (z, y) row)
-//   y pass: AB = (M1)_y TK + (sy K1)_y TM, C = (M1)_y TM   (staged z, owned x)
-//   z pass: r = (M1)_z AB + (sz K1)_z C              (owned y, x)
-// each pass cell by cell, the two cell contributions at a vertex plane added
-// in a fix-up pass.  For an I_d node every surrounding cell is uncut, so r is
-// its row of K^d u_n (Eq. Kd).  The 1D products use the even-odd form of K1
-// and the rank-one form of M1, as in 2D.
-
-// o = (s K1) v on axis ax (even-odd form).
-template <int P>
-__device__ __forceinline__ void k1d3(const Ops3D& ops, int ax, const double (&v)[P], double (&o)[P]) {
-  constexpr int H = P / 2;
-  constexpr bool kOdd = (P % 2) == 1;
-  double e[H], od[H];
-#pragma unroll
-  for (int j = 0; j < H; ++j) {
-    e[j] = v[j] + v[P - 1 - j];
-    od[j] = v[j] - v[P - 1 - j];
-  }
-#pragma unroll
-  for (int i = 0; i < H; ++i) {
-    double ev = kOdd ? ops.kc[ax][i] * v[H] : 0.0, odd = 0.0;
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-      ev = fma(ops.ke[ax][i][j], e[j], ev);
-      odd = fma(ops.ko[ax][i][j], od[j], odd);
-    }
-    o[i] = ev + odd;
-    o[P - 1 - i] = ev - odd;
-  }
-  if (kOdd) {
-    double ev = ops.kc[ax][H] * v[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) ev = fma(ops.ke[ax][H][j], e[j], ev);
-    o[H] = ev;
-  }
-}
-
-// a^T v for the rank-one part of M1.
-template <int P>
-__device__ __forceinline__ double m1d3_sa(const Ops3D& ops, const double (&v)[P]) {
-  constexpr int H = P / 2;
-  constexpr bool kOdd = (P % 2) == 1;
-  double sa = kOdd ? ops.a[H] * v[H] : 0.0;
-#pragma unroll
-  for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? v[j] + v[P - 1 - j] : v[j] - v[P - 1 - j], sa);
-  return sa;
-}
-
-template <int P, int TC>
-__global__ void __launch_bounds__(kThreads) k_explicit3d(ExplicitArgs a, Ops3D ops) {
-  constexpr int p = P - 1;
-  constexpr int OX = TC * p;
-  constexpr int R = (TC + 1) * p + 1;   // staged nodes per axis
-  constexpr int NC = TC + 1;            // staged cells per axis
-  extern __shared__ double sm[];
-  const int tid = threadIdx.x;
-  const int ntiles = a.ntx * a.nty * a.ntz;
-  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
-  const double* Uc = a.U + on;
-  const double* Wc = a.W + on;     // may alias OUTc
-  double* OUTc = a.OUT + on;
-  const double* fxc = a.fx + on;
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-
-  if ((int)blockIdx.x >= ntiles) {
-    // Newmark prediction on I_c (Fig. TrapCDMIMEX, "Prediction").
-    const double c1 = a.dt, c2 = (0.5 - kNewmarkBeta) * a.dt * a.dt;
-    const int stride = (gridDim.x - ntiles) * blockDim.x;
-    for (int r = (blockIdx.x - ntiles) * blockDim.x + tid; r < a.n_c; r += stride) {
-      const int node = a.c_node[r];
-      OUTc[node] = Uc[node] + c1 * a.v_c[oc + r] + c2 * a.a_c[oc + r];
-    }
-    return;
-  }
-
-  double* su = sm;                          // R^3
-  double* TK = su + R * R * R;              // R x R x OX
-  double* TM = TK + R * R * OX;
-  double* reg = TM + R * R * OX;            // x-pass partials, then y-pass arrays
-  double* xlk = reg;                        // R*R x NC each
-  double* xrk = xlk + R * R * NC;
-  double* xlm = xrk + R * R * NC;
-  double* xrm = xlm + R * R * NC;
-  double* AB = reg;                         // R x OX(y) x OX(x)
-  double* CC = AB + R * OX * OX;
-  double* ylab = CC + R * OX * OX;          // R x NC x OX each
-  double* yrab = ylab + R * NC * OX;
-  double* ylc = yrab + R * NC * OX;
-  double* yrc = ylc + R * NC * OX;
-  double* rr = TK;                          // OX^3 (aliases TK/TM after the y pass)
-  double* zl = rr + OX * OX * OX;           // NC x OX x OX each
-  double* zr = zl + NC * OX * OX;
-
-  const int tile = blockIdx.x;
-  const int tx = tile % a.ntx, ty = (tile / a.ntx) % a.nty, tz = tile / (a.ntx * a.nty);
-  const int X0 = tx * OX, Y0 = ty * OX, Z0 = tz * OX;
-  const int cx0 = X0 / p - 1, cy0 = Y0 / p - 1, cz0 = Z0 / p - 1;
-  const int64_t nxy = (int64_t)a.nx * a.ny;
-
-  for (int idx = tid; idx < R * R * R; idx += kThreads) {
-    const int zz = idx / (R * R), yy = (idx / R) % R, xx = idx % R;
-    const int gx = X0 - p + xx, gy = Y0 - p + yy, gz = Z0 - p + zz;
-    su[idx] = (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz)
-                  ? Uc[(int64_t)gz * nxy + (int64_t)gy * a.nx + gx]
-                  : 0.0;
-  }
-  __syncthreads();
-
-  // x pass: item = (row zy, cell cc), rows fastest.
-  for (int it = tid; it < R * R * NC; it += kThreads) {
-    const int cc = it / (R * R), zy = it - cc * (R * R);
-    const int cx = cx0 + cc;
-    double ok[P], om[P];
-    if (cx < 0 || cx >= a.ncx) {
-#pragma unroll
-      for (int i = 0; i < P; ++i) ok[i] = om[i] = 0.0;
-    } else {
-      double v[P];
-#pragma unroll
-      for (int j = 0; j < P; ++j) v[j] = su[zy * R + cc * p + j];
-      k1d3<P>(ops, 0, v, ok);
-      const double sa = m1d3_sa<P>(ops, v);
-#pragma unroll
-      for (int i = 0; i < P; ++i) om[i] = fma(ops.w[i], v[i], ops.ca[i] * sa);
-    }
-    if (cc >= 1) {
-#pragma unroll
-      for (int i = 1; i < p; ++i) {
-        TK[zy * OX + (cc - 1) * p + i] = ok[i];
-        TM[zy * OX + (cc - 1) * p + i] = om[i];
-      }
-    }
-    xlk[zy * NC + cc] = ok[0];
-    xrk[zy * NC + cc] = ok[p];
-    xlm[zy * NC + cc] = om[0];
-    xrm[zy * NC + cc] = om[p];
-  }
-  __syncthreads();
-  for (int it = tid; it < R * R * TC; it += kThreads) {
-    const int k = it / (R * R), zy = it - k * (R * R);
-    TK[zy * OX + k * p] = xrk[zy * NC + k] + xlk[zy * NC + k + 1];
-    TM[zy * OX + k * p] = xrm[zy * NC + k] + xlm[zy * NC + k + 1];
-  }
-  __syncthreads();
-
-  // y pass: item = (z, x, cell row cr), x fastest.
-  for (int it = tid; it < R * OX * NC; it += kThreads) {
-    const int cr = it / (R * OX), rem = it - cr * (R * OX);
-    const int z = rem / OX, x = rem - z * OX;
-    const int cy = cy0 + cr;
-    double ab[P], cm[P];
-    if (cy < 0 || cy >= a.ncy) {
-#pragma unroll
-      for (int i = 0; i < P; ++i) ab[i] = cm[i] = 0.0;
-    } else {
-      double va[P], vb[P];
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        va[j] = TK[(z * R + cr * p + j) * OX + x];
-        vb[j] = TM[(z * R + cr * p + j) * OX + x];
-      }
-      double kb[P];
-      k1d3<P>(ops, 1, vb, kb);
-      const double sa = m1d3_sa<P>(ops, va), sb = m1d3_sa<P>(ops, vb);
-#pragma unroll
-      for (int i = 0; i < P; ++i) {
-        ab[i] = fma(ops.w[i], va[i], fma(ops.ca[i], sa, kb[i]));
-        cm[i] = fma(ops.w[i], vb[i], ops.ca[i] * sb);
-      }
-    }
-    if (cr >= 1) {
-#pragma unroll
-      for (int i = 1; i < p; ++i) {
-        AB[(z * OX + (cr - 1) * p + i) * OX + x] = ab[i];
-        CC[(z * OX + (cr - 1) * p + i) * OX + x] = cm[i];
-      }
-    }
-    ylab[(z * NC + cr) * OX + x] = ab[0];
-    yrab[(z * NC + cr) * OX + x] = ab[p];
-    ylc[(z * NC + cr) * OX + x] = cm[0];
-    yrc[(z * NC + cr) * OX + x] = cm[p];
-  }
-  __syncthreads();
-  for (int it = tid; it < R * TC * OX; it += kThreads) {
-    const int k = it / (R * OX), rem = it - k * (R * OX);
-    const int z = rem / OX, x = rem - z * OX;
-    AB[(z * OX + k * p) * OX + x] = yrab[(z * NC + k) * OX + x] + ylab[(z * NC + k + 1) * OX + x];
-    CC[(z * OX + k * p) * OX + x] = yrc[(z * NC + k) * OX + x] + ylc[(z * NC + k + 1) * OX + x];
-  }
-  __syncthreads();
-
-  // z pass: item = (y, x, cell layer cl), x fastest.
-  for (int it = tid; it < OX * OX * NC; it += kThreads) {
-    const int cl = it / (OX * OX), yx = it - cl * (OX * OX);
-    const int cz = cz0 + cl;
-    double o[P];
-    if (cz < 0 || cz >= a.ncz) {
-#pragma unroll
-      for (int i = 0; i < P; ++i) o[i] = 0.0;
-    } else {
-      double va[P], vb[P];
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        va[j] = AB[(cl * p + j) * OX * OX + yx];
-        vb[j] = CC[(cl * p + j) * OX * OX + yx];
-      }
-      double kb[P];
-      k1d3<P>(ops, 2, vb, kb);
-      const double sa = m1d3_sa<P>(ops, va);
-#pragma unroll
-      for (int i = 0; i < P; ++i) o[i] = fma(ops.w[i], va[i], fma(ops.ca[i], sa, kb[i]));
-    }
-    if (cl >= 1) {
-#pragma unroll
-      for (int i = 1; i < p; ++i) rr[((cl - 1) * p + i) * OX * OX + yx] = o[i];
-    }
-    zl[cl * OX * OX + yx] = o[0];
-    zr[cl * OX * OX + yx] = o[p];
-  }
-  __syncthreads();
-  for (int it = tid; it < TC * OX * OX; it += kThreads) {
-    const int k = it / (OX * OX), yx = it - k * (OX * OX);
-    rr[(k * p) * OX * OX + yx] = zr[k * OX * OX + yx] + zl[(k + 1) * OX * OX + yx];
-  }
-  __syncthreads();
-
-  // CDM update of the owned I_d nodes (Eqs. CDMacc, CDMstep).
-  const double ft = a.ft_dev ? a.ft_dev[0] : a.ft;
-  for (int it = tid; it < OX * OX * OX; it += kThreads) {
-    const int zo = it / (OX * OX), yo = (it / OX) % OX, xo = it % OX;
-    const int gx = X0 + xo, gy = Y0 + yo, gz = Z0 + zo;
-    if (gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
-    const int64_t g = (int64_t)gz * nxy + (int64_t)gy * a.nx + gx;
-    if (a.cls[g] != NODE_D) continue;
-    const double r = rr[it];
-    const double u = su[((zo + p) * R + yo + p) * R + xo + p];
-    const double minv = a.winv_x[gx] * a.winv_y[gy] * a.winv_z[gz];
-    const double acc = minv * (ft * fxc[g] - r);
-    OUTc[g] = a.cu * u + a.cw * Wc[g] + a.ca * acc;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// A4 + A5 + A6: the implicit solve S a = f_t(t_{n+1}) f_x^c - K^c u_pred with
-// the supernodal nested-dissection Cholesky factor of S, and the Newmark
-// correction.  Per component, the lower levels of the dissection tree are
-// walked level by level (forward: y_t = L_tt^{-1}(rhs_t - descendant updates),
-// upd_t = L_{rows,t} y_t; backward: x_t = L_tt^{-T}(y_t - L_{rows,t}^T x_rows)),
-// and the upper levels are one dense product x_Z = A_Z (rhs_Z - updates from
-// below), A_Z = (L_ZZ L_ZZ^T)^{-1} (no lower node is an ancestor of an upper
-// one, so L_BZ = 0).  Every level is one launch over all components: kernel
-// boundaries are the barriers, so each launch spreads its FP64 work over every
-// SM.  Within a CTA all threads share the rows of all its supernodes in each
-// phase.  The first forward launch also forms the right-hand side of every
-// implicit row: K^c u_pred row by row, one dot product of a row of K_e with the
-// cell's nodal values per (row, interface cell) pair.  Launches are chained
-// with programmatic dependent launch: a kernel stages its constant factor
-// blocks and index lists (cp.async) while its predecessor runs and waits
-// (griddepcontrol.wait, a hardware wait) before it reads its results.  All
-// sums run in a fixed order, so results are deterministic.
-
-// Start an asynchronous copy of n 16-byte chunks global -> shared with all
-// threads (cp.async, no register staging); completed by async_copy_wait().
-__device__ __forceinline__ void async_copy_16(void* dst, const void* src, int64_t nchunks) {
-  const char* s8 = reinterpret_cast<const char*>(src);
-  char* d8 = reinterpret_cast<char*>(dst);
-  for (int64_t k = threadIdx.x; k < nchunks; k += blockDim.x) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(d8 + 16 * k);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(s8 + 16 * k) : "memory");
-  }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void async_copy_wait() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-  __syncthreads();
-}
-
-// One warp, one supernode product: lanes own rows.  out[i] = sum_j M[i si + j sj] v[j]
-// for i < nrows, restricted to j <= i (tri > 0) or j >= i (tri < 0).
-// (si, sj) = (1, ld) reads a column-major block, (ld, 1) its transpose; with an
-// odd ld both are free of shared-memory bank conflicts.
-template <int R>
-__device__ __forceinline__ void warp_gemv_r(const double* M, int si, int sj, int nrows, int ncols,
-                                            const double* v, int tri, double* out, int lane) {
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int i = lane + 32 * r;
-    if (i >= nrows) break;
-    int j0 = 0, j1 = ncols;
-    if (tri > 0) j1 = min(ncols, i + 1);
-    if (tri < 0) j0 = i;
-    double s0 = 0.0, s1 = 0.0;
-    int j = j0;
-    for (; j + 2 <= j1; j += 2) {
-      s0 = fma(M[(size_t)i * si + (size_t)j * sj], v[j], s0);
-      s1 = fma(M[(size_t)i * si + (size_t)(j + 1) * sj], v[j + 1], s1);
-    }
-    if (j < j1) s0 = fma(M[(size_t)i * si + (size_t)j * sj], v[j], s0);
-    out[i] = s0 + s1;
-  }
-}
-
-__device__ __forceinline__ void warp_gemv(const double* M, int si, int sj, int nrows, int ncols,
-                                          const double* v, int tri, double* out, int lane) {
-  switch ((nrows + 31) / 32) {
-    case 0: break;
-    case 1: warp_gemv_r<1>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
-    case 2: warp_gemv_r<2>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
-    case 3: warp_gemv_r<3>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
-    case 4: warp_gemv_r<4>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
-    default: warp_gemv_r<8>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
-  }
-}
-
-// Newmark correction of one implicit row (Fig. TrapCDMIMEX "Correction"), or
-// the initial acceleration only (mode 1), on one column's fields.
-struct Corr {
-  int mode;
-  const int* c_node;
-  double* U;      // holds u_pred on I_c (mode 0) or u^c_{n-1} (mode 3); receives u^c_{n+1}
-  double* v_c;
-  double* a_c;
-  double dt;
-  const double* Un;  // u_n (mode 3)
-  __device__ void row(int r, double acc) const {
-    if (mode == 2) return;   // solve only: the solution stays in sol
-    if (mode == 3) {         // central differences on I_c (Eq. CDMstep): acc = a^c_n
-      const int node = c_node[r];
-      U[node] = 2.0 * Un[node] - U[node] + dt * dt * acc;
-    } else if (mode == 0) {
-      const int node = c_node[r];
-      const double vpred = v_c[r] + (1.0 - kNewmarkGamma) * dt * a_c[r];
-      U[node] = U[node] + kNewmarkBeta * dt * dt * acc;
-      v_c[r] = vpred + kNewmarkGamma * dt * acc;
-    }
-    a_c[r] = acc;
-  }
-  // The same with c_node[r], v_c[r] and a_c[r] loaded beforehand (they are not
-  // written by the kernels of the step that run before the correction).
-  __device__ void row_pre(int r, double acc, int node, double v_old, double a_old) const {
-    if (mode == 2) return;
-    if (mode == 3) {
-      U[node] = 2.0 * Un[node] - U[node] + dt * dt * acc;
-    } else if (mode == 0) {
-      const double vpred = v_old + (1.0 - kNewmarkGamma) * dt * a_old;
-      U[node] = U[node] + kNewmarkBeta * dt * dt * acc;
-      v_c[r] = vpred + kNewmarkGamma * dt * acc;
-    }
-    a_c[r] = acc;
-  }
-};
-
-// Per-CTA index list of a walk launch (ints, offsets relative to its start):
-//   [0] nq nodes, [1] nslot rows (sum of b), [2] nm ancestor rows (sum of m),
-//   [3] nrhs, [4] npair, [5] np = npair rounded up to even (first launch
-//   only; the cell-matrix rows of the pairs are staged separately), [6..7] 0
-//   node table at 8:          nq x {t, beg, b, m, slot0, moff, boff, updoff}
-//   slot table:               nslot x {q, update begin, update end, 0}
-//   ancestor table:           nm x {q, c-row}
-//   right-hand-side rows:     nrhs x {c-row, pair begin, pair end, slot or -1}
-//   pairs:                    npair x {first node of the cell, 0, 0, 0}
-//   update positions (into upd).
-struct WalkList {
-  const int* h;
-  const int* node;
-  const int* slot;
-  const int* anc;
-  const int* rhs;
-  const int* pair;
-  __device__ explicit WalkList(const int* il) : h(il) {
-    node = il + 8;
-    slot = node + 8 * il[0];
-    anc = slot + 4 * il[1];
-    rhs = anc + ((2 * il[2] + 3) & ~3);
-    pair = rhs + 4 * il[3];
-  }
-};
-
-// Right-hand side of one (row, cell) pair k: row l of the cell matrix (scaled
-// by the cell's c_e^2 / c0^2 where the uncut form is used), staged m-major in
-// shared memory (kp[m * np + k]), times the cell's nodal values (off[m] is the
-// grid offset of local node m from the cell's first node).  Loads are issued
-// in batches of 16 before the products.
-constexpr int kMaxPd = 128;
-__device__ __forceinline__ double pair_product(const WalkArgs& a, const double* src, const double* kp, int np,
-                                               int k, int base, const int* off) {
-  const double* u = src + base;
-  double s0 = 0.0, s1 = 0.0;
-  for (int m0 = 0; m0 < a.Pd; m0 += 16) {
-    double kv[16], uv[16];
-#pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      const bool ok = m0 + t < a.Pd;
-      kv[t] = ok ? kp[(size_t)(m0 + t) * np + k] : 0.0;
-      uv[t] = ok ? __ldg(u + off[ok ? m0 + t : 0]) : 0.0;
-    }
-#pragma unroll
-    for (int t = 0; t < 16; t += 2) {
-      s0 = fma(kv[t], uv[t], s0);
-      s1 = fma(kv[t + 1], uv[t + 1], s1);
-    }
-  }
-  return s0 + s1;
-}
-
-template <bool kForward, bool kSmem>
-__global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
-  extern __shared__ __align__(16) double sm[];
-  const int cta = a.cta0 + blockIdx.x;
-  const int tid = threadIdx.x;
-  // Column of an independent-columns context (blockIdx.y).
-  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
-  const double* src = a.SRC + on;
-  const double* fxc = a.fxc + oc;
-  double* rhs0 = a.rhs0 + oc;
-  double* sol = a.sol + oc;
-  double* upd = a.upd + (int64_t)blockIdx.y * a.cs_upd;
-  const Corr cor{a.mode, a.c_node, a.U + on, a.v_c + oc, a.a_c + oc, a.dt, src};
-  double* blob = sm;                                   // max_blob (smem mode)
-  double* kp = blob + a.max_blob;                      // max_kp: rows of the cell matrices (first launch)
-  double* vg = kp + a.max_kp;                          // max_slots: g (fwd) / y (bwd)
-  double* vy = vg + a.max_slots;                       // max_slots: y (fwd) / h (bwd)
-  double* vm = vy + a.max_slots;                       // max_m: x of the ancestor rows (bwd)
-  double* pc = vm + a.max_m;                           // max_pairs: pair products (first launch)
-  int* il = reinterpret_cast<int*>(pc + a.max_pairs);
-  __shared__ int s_off[kForward ? kMaxPd : 1];         // grid offset of each local node of a cell
-  if (kForward && a.first)
-    for (int m = tid; m < a.Pd; m += kThreads)
-      s_off[m] = (m % a.P) + a.nx * ((m / a.P) % a.P) + a.nx * a.ny * (m / (a.P * a.P));
-  const int64_t boff = a.blob_off[cta];
-  if (kSmem) async_copy_16(blob, a.blob + boff, a.blob_len[cta] / 2);
-  async_copy_16(il, a.ilist + a.ilist_off[cta], a.ilist_len[cta] / 4);
-  if (kForward && a.first && a.kp_smem) async_copy_16(kp, a.Kpair + a.kp_off[cta], a.kp_len[cta] / 2);
-  const double* KP = (kForward && a.first && !a.kp_smem) ? a.Kpair + a.kp_off[cta] : kp;
-  const double* B = kSmem ? blob : a.blob + boff;
-  // Let the next launch stage its constants.
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-  async_copy_wait();
-  const WalkList L(il);
-  const int nslot = il[1], nm = il[2];
-  // Backward: the correction state of this thread's first two rows.
-  int pre_node[2] = {0, 0};
-  double pre_v[2] = {0.0, 0.0}, pre_a[2] = {0.0, 0.0};
-  if (!kForward) {
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int sl = tid + q * kThreads;
-      if (sl < nslot) {
-        const int* nd = L.node + 8 * L.slot[4 * sl];
-        const int r = nd[1] + (sl - nd[4]);
-        pre_node[q] = cor.c_node[r];
-        pre_v[q] = cor.v_c[r];
-        pre_a[q] = cor.a_c[r];
-      }
-    }
-  }
-  // Wait for the previous launch's results.
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  if (a.skip && *a.skip) return;   // the iterative solve converged: nothing to do
-  if (kForward) {
-    if (a.first && a.rhs_given) {
-      for (int sl = tid; sl < nslot; sl += kThreads) {
-        const int* st = L.slot + 4 * sl;
-        const int* nd = L.node + 8 * st[0];
-        double v = rhs0[nd[1] + (sl - nd[4])];
-        for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(upd + il[k]);
-        vg[sl] = v;
-      }
-    } else if (a.first) {
-      const int npair = il[4], nrhs = il[3];
-      // f_t at t_{n+1}, or at t_n for the central-difference form (mode 3).
-      const double ft = a.ft_dev ? a.ft_dev[a.mode == 3 ? 0 : 1] : a.ft;
-      const int np = il[5];
-      for (int k = tid; k < npair; k += kThreads) pc[k] = pair_product(a, src, KP, np, k, L.pair[4 * k], s_off);
-      __syncthreads();
-      for (int k = tid; k < nrhs; k += kThreads) {
-        const int* rr = L.rhs + 4 * k;
-        double v = ft * fxc[rr[0]];
-        for (int q = rr[1]; q < rr[2]; ++q) v -= pc[q];
-        if (rr[3] >= 0 && !a.rhs_only) vg[rr[3]] = v;
-        else rhs0[rr[0]] = v;
-      }
-      if (a.rhs_only) return;   // every row's right-hand side is in rhs0
-      __syncthreads();
-      for (int sl = tid; sl < nslot; sl += kThreads) {
-        const int* st = L.slot + 4 * sl;
-        double v = vg[sl];
-        for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(upd + il[k]);
-        vg[sl] = v;
-      }
-    } else {
-      for (int sl = tid; sl < nslot; sl += kThreads) {
-        const int* st = L.slot + 4 * sl;
-        const int* nd = L.node + 8 * st[0];
-        double v = __ldcg(rhs0 + nd[1] + (sl - nd[4]));
-#pragma unroll 4
-        for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(upd + il[k]);
-        vg[sl] = v;
-      }
-    }
-    __syncthreads();
-    // y = L_tt^{-1} g, every row of every supernode of this CTA.
-    for (int sl = tid; sl < nslot; sl += kThreads) {
-      const int* nd = L.node + 8 * L.slot[4 * sl];
-      const int b = nd[2], s0 = nd[4], i = sl - s0, ldi = b | 1;
-      const double* Li = B + nd[6];
-      double y0 = 0.0, y1 = 0.0;
-      int j = 0;
-      for (; j + 2 <= i + 1; j += 2) {
-        y0 = fma(Li[i + ldi * j], vg[s0 + j], y0);
-        y1 = fma(Li[i + ldi * (j + 1)], vg[s0 + j + 1], y1);
-      }
-      if (j <= i) y0 = fma(Li[i + ldi * j], vg[s0 + j], y0);
-      const double y = y0 + y1;
-      vy[sl] = y;
-      sol[nd[1] + i] = y;
-    }
-    __syncthreads();
-    // upd_t = L_{rows,t} y_t.
-    for (int k = tid; k < nm; k += kThreads) {
-      const int* nd = L.node + 8 * L.anc[2 * k];
-      const int b = nd[2], m = nd[3], s0 = nd[4], kk = k - nd[5], ldi = b | 1, ldr = m | 1;
-      const double* L21 = B + nd[6] + (size_t)ldi * b;
-      double u0 = 0.0, u1 = 0.0;
-      int j = 0;
-      for (; j + 2 <= b; j += 2) {
-        u0 = fma(L21[kk + ldr * j], vy[s0 + j], u0);
-        u1 = fma(L21[kk + ldr * (j + 1)], vy[s0 + j + 1], u1);
-      }
-      if (j < b) u0 = fma(L21[kk + ldr * j], vy[s0 + j], u0);
-      upd[nd[7] + kk] = u0 + u1;
-    }
-  } else {
-    for (int k = tid; k < nm; k += kThreads) vm[k] = __ldcg(sol + L.anc[2 * k + 1]);
-    for (int sl = tid; sl < nslot; sl += kThreads) {
-      const int* nd = L.node + 8 * L.slot[4 * sl];
-      vg[sl] = __ldcg(sol + nd[1] + (sl - nd[4]));
-    }
-    __syncthreads();
-    // h = y_t - L_{rows,t}^T x_rows.
-    for (int sl = tid; sl < nslot; sl += kThreads) {
-      const int* nd = L.node + 8 * L.slot[4 * sl];
-      const int b = nd[2], m = nd[3], i = sl - nd[4], mo = nd[5], ldi = b | 1, ldr = m | 1;
-      const double* L21 = B + nd[6] + (size_t)ldi * b + (size_t)ldr * i;
-      double h0 = 0.0, h1 = 0.0;
-      int k = 0;
-      for (; k + 2 <= m; k += 2) {
-        h0 = fma(L21[k], vm[mo + k], h0);
-        h1 = fma(L21[k + 1], vm[mo + k + 1], h1);
-      }
-      if (k < m) h0 = fma(L21[k], vm[mo + k], h0);
-      vy[sl] = vg[sl] - (h0 + h1);
-    }
-    __syncthreads();
-    // x_t = L_tt^{-T} h, then the correction of the row.
-    for (int sl = tid; sl < nslot; sl += kThreads) {
-      const int* nd = L.node + 8 * L.slot[4 * sl];
-      const int b = nd[2], s0 = nd[4], i = sl - s0, ldi = b | 1;
-      const double* Lc = B + nd[6] + (size_t)ldi * i;
-      double x0 = 0.0, x1 = 0.0;
-      int j = i;
-      for (; j + 2 <= b; j += 2) {
-        x0 = fma(Lc[j], vy[s0 + j], x0);
-        x1 = fma(Lc[j + 1], vy[s0 + j + 1], x1);
-      }
-      if (j < b) x0 = fma(Lc[j], vy[s0 + j], x0);
-      const double x = x0 + x1;
-      sol[nd[1] + i] = x;
-      if (sl < tid + kThreads) cor.row_pre(nd[1] + i, x, pre_node[0], pre_v[0], pre_a[0]);
-      else if (sl < tid + 2 * kThreads) cor.row_pre(nd[1] + i, x, pre_node[1], pre_v[1], pre_a[1]);
-      else cor.row(nd[1] + i, x);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
-  extern __shared__ __align__(16) double tsm[];
-  const int cta = blockIdx.x, tid = threadIdx.x;
-  const int warp = tid / 32, lane = tid % 32;
-  // Column of an independent-columns context (blockIdx.y).
-  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
-  const double* rhs0 = a.rhs0 + oc;
-  double* sol = a.sol + oc;
-  const double* upd = a.upd + (int64_t)blockIdx.y * a.cs_upd;
-  const Corr cor{a.mode, a.c_node, a.U + on, a.v_c + oc, a.a_c + oc, a.dt, a.Un ? a.Un + on : nullptr};
-  const int comp = a.cta_comp[cta], r0 = a.cta_r0[cta], r1 = a.cta_r1[cta];
-  const int zn = a.zsize[comp], zb = a.zbase[comp], nr = r1 - r0;
-  double* zs = tsm;                               // max_zn (even): right-hand side of the block
-  double* Ac = zs + a.max_zn;                     // max_arows: this CTA's rows of A_Z
-  double* xs = Ac + a.max_arows;                  // max_chunk: this CTA's results
-  int* il = reinterpret_cast<int*>(xs + a.max_chunk);  // per row {update begin, update end}
-  async_copy_16(Ac, a.zA + a.zA_off[comp] + (size_t)r0 * zn, ((int64_t)nr * zn + 1) / 2);
-  async_copy_16(il, a.ilist + a.ilist_off[cta], a.ilist_len[cta] / 4);
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-  // The correction state of this thread's row (nr <= blockDim.x); not written
-  // by the launches of the step that run before this one.
-  int row = 0, node = 0;
-  double v_old = 0.0, a_old = 0.0;
-  if (tid < nr) {
-    row = a.zrow[zb + r0 + tid];
-    node = cor.c_node[row];
-    v_old = cor.v_c[row];
-    a_old = cor.a_c[row];
-  }
-  async_copy_wait();
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  if (a.skip && *a.skip) return;   // the iterative solve converged: nothing to do
-  // The whole right-hand side of this component's top block (redundant per CTA).
-  for (int i = tid; i < zn; i += kThreads) {
-    const int fb = il[2 * i], fe = il[2 * i + 1];
-    double v = __ldcg(rhs0 + a.zrow[zb + i]);
-#pragma unroll 4
-    for (int k = fb; k < fe; ++k) v -= __ldcg(upd + il[k]);
-    zs[i] = v;
-  }
-  __syncthreads();
-  for (int i = warp; i < nr; i += kWarps) {
-    const double* Ar = Ac + (size_t)i * zn;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int j = lane;
-    for (; j + 96 < zn; j += 128) {
-      s0 = fma(Ar[j], zs[j], s0);
-      s1 = fma(Ar[j + 32], zs[j + 32], s1);
-      s2 = fma(Ar[j + 64], zs[j + 64], s2);
-      s3 = fma(Ar[j + 96], zs[j + 96], s3);
-    }
-    for (; j < zn; j += 32) s0 = fma(Ar[j], zs[j], s0);
-    double v = (s0 + s1) + (s2 + s3);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) xs[i] = v;
-  }
-  __syncthreads();
-  if (tid < nr) {
-    const double x = xs[tid];
-    sol[row] = x;
-    cor.row_pre(row, x, node, v_old, a_old);
-  }
-}
+#include "step_kernels.cuh"
 
 // ---------------------------------------------------------------------------
 // Iterative alternative for A5: preconditioned conjugate gradients (Saad,
