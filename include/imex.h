@@ -118,6 +118,7 @@ typedef struct {
   int64_t scheme;                /* IMEX_SCHEME_* of the context */
   double dt_crit_cut_min;        /* smallest cut-cell critical step for the scheme's mass
                                     (central-difference schemes; 0 otherwise) */
+  int64_t factorized;            /* 1: factorised implicit solve available; 0: imex_setup_pcg */
 } imex_stats;
 
 /*
@@ -195,6 +196,27 @@ int imex_setup_batch(const imex_mesh *mesh, int p, double alpha, double dt, cons
  */
 int imex_setup_scheme(const imex_mesh *mesh, int p, double alpha, double dt, const imex_source *src,
                       int ncols, int scheme, const imex_alloc *alloc, imex_ctx **out);
+
+/*
+ * imex_setup_pcg - a single-column context without a factorisation: no
+ * nested dissection, no Cholesky factor, no solve schedule.  Every implicit
+ * solve of S (Fig. TrapCDMIMEX "Acceleration calculation") is preconditioned
+ * CG (imex_set_solver: IMEX_SOLVER_PCG_JACOBI, the default, with maxit 5000,
+ * or IMEX_SOLVER_PCG_FSAI after imex_pcg_train); the right-hand sides come
+ * from one warp-per-row kernel over the same (row, interface cell) pairs; the
+ * initial acceleration solves M^cc a^c_0 = f_t(0) f^c - K^c u_0 by
+ * Jacobi-preconditioned CG to 1e-12.  For partitions whose factor does not
+ * fit the device solve (3D voids, where dissection separators exceed 256
+ * rows).  With no direct solve to fall back on, a solve that misses the
+ * tolerance still applies its last iterate and counts as a fallback in
+ * imex_pcg_status.  The implicit DOFs are in grid order.
+ *   scheme : IMEX_SCHEME_IMEX or IMEX_SCHEME_TRAPEZOIDAL
+ * Not available on such a context: IMEX_SOLVER_DIRECT, imex_adjoint,
+ * imex_step_noalloc (IMEX_ERR_ARG).
+ * Errors: as imex_setup.
+ */
+int imex_setup_pcg(const imex_mesh *mesh, int p, double alpha, double dt, const imex_source *src, int scheme,
+                   const imex_alloc *alloc, imex_ctx **out);
 
 /*
  * imex_step - advance n >= 0 Newmark IMEX steps (Fig. TrapCDMIMEX), each:

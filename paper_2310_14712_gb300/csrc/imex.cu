@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
     }
     if (k > a.maxit) k = a.maxit;
   }
-  if (conv) {
+  if (conv || a.always_correct) {
     const Corr cor{a.mode, a.c_node, a.U, a.v_c, a.a_c, a.dt, nullptr};
     for (int i = g0; i < n; i += gs) cor.row(i, a.x[i]);
   }
@@ -184,6 +184,32 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
     a.counters[1] += conv ? 0 : 1;
     *a.res = nb2 > 0.0 ? sqrt(rr_t / nb2) : 0.0;
   }
+}
+
+// Right-hand sides of the implicit rows without a solve plan (one warp per
+// row): rhs_r = f_t f^c_r - sum over the row's (interface cell, local row)
+// pairs of sc_e (row of the cell matrix) . (the cell's nodal values of src),
+// the same pairs and cell matrices as the first walk launch uses (Eq. Kc).
+__global__ void __launch_bounds__(kThreads) k_rhs_c(int n_c, const int* pr_ptr, const int* pr_pos,
+                                                    const int* if_base, const int* if_koff, const double* if_sc,
+                                                    const double* Krows, int P, int Pd, int nx, int ny,
+                                                    const double* fxc, double ft, const double* ft_dev,
+                                                    const double* src, double* rhs) {
+  const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32), lane = threadIdx.x % 32;
+  if (r >= n_c) return;
+  double acc = 0.0;
+  for (int q = pr_ptr[r]; q < pr_ptr[r + 1]; ++q) {
+    const int e = pr_pos[q] / Pd, l = pr_pos[q] % Pd;
+    const double* row = Krows + ((size_t)if_koff[e] * Pd + l) * Pd;
+    const double* u = src + if_base[e];
+    double t = 0.0;
+    for (int m = lane; m < Pd; m += 32)
+      t = fma(row[m], __ldg(u + (m % P) + nx * ((m / P) % P) + nx * ny * (m / (P * P))), t);
+    acc = fma(if_sc[e], t, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) rhs[r] = (ft_dev ? ft_dev[1] : ft) * fxc[r] - acc;   // ft_dev[1] = f_t(t_{n+1})
 }
 
 // Training of G (Kaporin's functional K(G) = tr(G^T S G) - 2 sum log G_ii on
@@ -608,6 +634,11 @@ struct imex_ctx {
   double *g_val = nullptr, *g_scale = nullptr, *g_theta = nullptr, *g_m = nullptr, *g_v = nullptr;
   double *g_grad = nullptr, *g_sg = nullptr, *dinv = nullptr;
   uint8_t* g_isdiag = nullptr;
+  // no factorisation (imex_setup_pcg): M^cc on S's pattern for the initial
+  // acceleration, and the (row, interface cell) pairs of K^c u per row
+  int factorized = 1;
+  double *m_val = nullptr, *dinv_m = nullptr, *if_sc_dev = nullptr;
+  int *pr_ptr = nullptr, *pr_pos = nullptr, *if_base_dev = nullptr, *if_koff_dev = nullptr;
   double *pcg_x = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_w = nullptr;
   double *pcg_part = nullptr, *pcg_res = nullptr;
   int* pcg_status = nullptr;
@@ -943,6 +974,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
 // Kernel launches of one step.
 int64_t launches_per_step(const imex_ctx* c) {
   int64_t n = 1;   // explicit apply
+  if (c->hs.n_c > 0 && !c->factorized) return n + 2;   // right-hand sides, PCG
   if (c->hs.n_c > 0) {
     n += (int64_t)c->lev_cta0.size() + (c->ntop > 0 ? 1 : 0);
     for (int h : c->lev_has_nodes) n += h;
@@ -988,21 +1020,23 @@ cudaError_t autotune_tile(imex_ctx* c) {
   return e ? e : use_tile(c, best_small);
 }
 
-cudaError_t launch_pcg(imex_ctx* c, double* Ubuf, cudaStream_t s) {
+// PCG on S (the step; Newmark correction) or, for the initial acceleration
+// of a context without a factorisation, on M^cc with Jacobi (mode 1).
+cudaError_t launch_pcg(imex_ctx* c, double* Ubuf, cudaStream_t s, bool on_M = false) {
   const HostSetup& hs = c->hs;
   PcgArgs a{};
   a.n = (int)hs.n_c;
   a.s_ptr = c->s_ptr;
   a.s_col = c->s_col;
-  a.s_val = c->s_val;
+  a.s_val = on_M ? c->m_val : c->s_val;
   a.g_ptr = c->g_ptr;
   a.g_col = c->g_col;
   a.g_val = c->g_val;
   a.gt_ptr = c->gt_ptr;
   a.gt_row = c->gt_row;
   a.gt_idx = c->gt_idx;
-  a.dinv = c->dinv;
-  a.precond = c->solver == IMEX_SOLVER_PCG_JACOBI ? 2 : 1;
+  a.dinv = on_M ? c->dinv_m : c->dinv;
+  a.precond = (on_M || c->solver == IMEX_SOLVER_PCG_JACOBI) ? 2 : 1;
   a.b = c->rhs0;
   a.x = c->pcg_x;
   a.r = c->pcg_r;
@@ -1011,12 +1045,13 @@ cudaError_t launch_pcg(imex_ctx* c, double* Ubuf, cudaStream_t s) {
   a.q = c->pcg_q;
   a.w = c->pcg_w;
   a.part = c->pcg_part;
-  a.tol = c->pcg_tol;
-  a.maxit = c->pcg_maxit;
+  a.tol = on_M ? 1e-12 : c->pcg_tol;
+  a.maxit = on_M ? 100000 : c->pcg_maxit;
+  a.always_correct = c->factorized ? 0 : 1;   // no direct solve to fall back on
   a.status = c->pcg_status;
   a.counters = c->pcg_counters;
   a.res = c->pcg_res;
-  a.mode = 0;
+  a.mode = on_M ? 1 : 0;
   a.c_node = c->c_node;
   a.U = Ubuf;
   a.v_c = c->v_c;
@@ -1024,6 +1059,16 @@ cudaError_t launch_pcg(imex_ctx* c, double* Ubuf, cudaStream_t s) {
   a.dt = hs.dt;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(c->pcg_grid), dim3(kThreads), args, 0, s);
+}
+
+// Right-hand sides rhs0 = f_t f^c - K^c src of a context without a solve plan.
+void launch_rhs_c(imex_ctx* c, double ft, const double* src, cudaStream_t s, const double* ft_dev = nullptr) {
+  const HostSetup& hs = c->hs;
+  const int nc = (int)hs.n_c;
+  const int64_t blocks = ((int64_t)nc * 32 + kThreads - 1) / kThreads;
+  k_rhs_c<<<(unsigned)blocks, kThreads, 0, s>>>(nc, c->pr_ptr, c->pr_pos, c->if_base_dev, c->if_koff_dev,
+                                                c->if_sc_dev, c->Kall, hs.P, hs.Pd, hs.nn[0], hs.nn[1], c->fxc,
+                                                ft, ft_dev, src, c->rhs0);
 }
 
 double ft_at(const HostSetup& hs, int64_t n) {
@@ -1046,7 +1091,11 @@ int compute_initial(imex_ctx* c, cudaStream_t s) {
     for (int col = 0; col < c->ncols; ++col)
       k_gather_c<<<(nc + 255) / 256, 256, 0, s>>>(c->v_c + (size_t)col * nc, c->tmp + (size_t)col * hs.nnodes,
                                                   c->c_node, nc);
-    if (cudaError_t e = launch_solve_chain(c, false, ft0, nullptr, 1, U0, U0, c->upd, c->sol, c->rhs0, s))
+    if (!c->factorized) {   // M^cc a^c_0 = f_t(0) f^c - K^c u_0 by Jacobi-PCG
+      launch_rhs_c(c, ft0, U0, s);
+      if (cudaError_t e = launch_pcg(c, U0, s, true))
+        return fail(IMEX_ERR_CUDA, std::string("PCG (initial): ") + cudaGetErrorString(e));
+    } else if (cudaError_t e = launch_solve_chain(c, false, ft0, nullptr, 1, U0, U0, c->upd, c->sol, c->rhs0, s))
       return fail(IMEX_ERR_CUDA, std::string("solve (initial): ") + cudaGetErrorString(e));
     if (int rc = check_launch("solve (initial)")) return rc;
     if (scheme_is_cdm(hs.pb.scheme)) {   // the central-difference history of I_c as well
@@ -1134,6 +1183,33 @@ void dense_top(const HostSetup& hs, const Factor& F, const std::vector<int>& zno
       A[(size_t)i * zn + j] = sum;
       A[(size_t)j * zn + i] = sum;
     }
+}
+
+// Rows of the interface-cell matrices (the stored cut-cell matrices, then the
+// uncut one at index n_cut; row-major), the scale of each interface cell
+// (c_e^2 / c0^2 for the uncut form, 1 for cut cells) and its first grid node.
+int interface_rows(const HostSetup& hs, std::vector<double>& Krows, std::vector<double>& if_sc,
+                   std::vector<int>& if_base) {
+  const int Pd = hs.Pd, n_cut = (int)hs.n_cut, nif = (int)hs.if_cell.size();
+  Krows.assign(((size_t)n_cut + 1) * Pd * Pd, 0.0);
+  for (int k = 0; k < n_cut; ++k)
+    for (int l = 0; l < Pd; ++l)
+      for (int m = 0; m < Pd; ++m)
+        Krows[((size_t)k * Pd + l) * Pd + m] = hs.cutK[(size_t)k * Pd * Pd + l + (size_t)Pd * m];
+  for (int l = 0; l < Pd; ++l)
+    for (int m = 0; m < Pd; ++m) Krows[((size_t)n_cut * Pd + l) * Pd + m] = hs.uncutK[l + (size_t)Pd * m];
+  if_sc.assign(std::max(nif, 1), 1.0);
+  if_base.assign(std::max(nif, 1), 0);
+  const int ncx = hs.pb.ncells[0], ncy = hs.pb.ncells[1];
+  for (int e = 0; e < nif; ++e) {
+    const int cid = hs.if_cell[e];
+    const int cx = cid % ncx, cy = (cid / ncx) % ncy, cz = cid / (ncx * ncy);
+    const int64_t base = (int64_t)cx * hs.p + (int64_t)hs.nn[0] * cy * hs.p + (int64_t)hs.nn[0] * hs.nn[1] * cz * hs.p;
+    if (base > INT32_MAX) return fail(IMEX_ERR_ARG, "grid too large for 32-bit node indices");
+    if_base[e] = (int)base;
+    if (hs.if_kidx[e] < 0) if_sc[e] = hs.if_c2[e];
+  }
+  return IMEX_OK;
 }
 
 int plan_solve(imex_ctx* c, SolvePlan& P) {
@@ -1267,28 +1343,9 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
       return fail(IMEX_ERR_NOT_SPD, "dense top-level solve disagrees with the tree solve");
   }
   // Interface cells: rows of their matrices and scales, first node of each.
-  const int Pd = hs.Pd, n_cut = (int)hs.n_cut, nif = (int)hs.if_cell.size();
-  P.Krows.assign(((size_t)n_cut + 1) * Pd * Pd, 0.0);
-  for (int k = 0; k < n_cut; ++k)
-    for (int l = 0; l < Pd; ++l)
-      for (int m = 0; m < Pd; ++m)
-        P.Krows[((size_t)k * Pd + l) * Pd + m] = hs.cutK[(size_t)k * Pd * Pd + l + (size_t)Pd * m];
-  for (int l = 0; l < Pd; ++l)
-    for (int m = 0; m < Pd; ++m) P.Krows[((size_t)n_cut * Pd + l) * Pd + m] = hs.uncutK[l + (size_t)Pd * m];
-  P.if_sc.assign(std::max(nif, 1), 1.0);
-  std::vector<int> if_base(std::max(nif, 1), 0);
-  {
-    const int ncx = hs.pb.ncells[0], ncy = hs.pb.ncells[1];
-    for (int e = 0; e < nif; ++e) {
-      const int cid = hs.if_cell[e];
-      const int cx = cid % ncx, cy = (cid / ncx) % ncy, cz = cid / (ncx * ncy);
-      const int64_t base = (int64_t)cx * hs.p + (int64_t)hs.nn[0] * cy * hs.p +
-                           (int64_t)hs.nn[0] * hs.nn[1] * cz * hs.p;
-      if (base > INT32_MAX) return fail(IMEX_ERR_ARG, "grid too large for 32-bit node indices");
-      if_base[e] = (int)base;
-      if (hs.if_kidx[e] < 0) P.if_sc[e] = hs.if_c2[e];
-    }
-  }
+  const int Pd = hs.Pd, n_cut = (int)hs.n_cut;
+  std::vector<int> if_base;
+  if (int rc = interface_rows(hs, P.Krows, P.if_sc, if_base)) return rc;
   if (hs.upd_size > INT32_MAX) return fail(IMEX_ERR_ARG, "implicit partition too large for 32-bit update offsets");
   auto npairs_of = [&](int r) { return hs.contrib_ptr[r + 1] - hs.contrib_ptr[r]; };
 
@@ -1732,6 +1789,9 @@ int setup_error_code(const std::string& e) {
   return IMEX_ERR_ARG;
 }
 
+int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src, int ncols, int scheme,
+               bool factorize, const imex_alloc* alloc, imex_ctx** out);
+
 }  // namespace
 
 extern "C" {
@@ -1811,6 +1871,22 @@ static_assert(IMEX_SCHEME_IMEX == kSchemeImex && IMEX_SCHEME_CDM == kSchemeCdm &
 
 int imex_setup_scheme(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src, int ncols,
                       int scheme, const imex_alloc* alloc, imex_ctx** out) {
+  return setup_impl(mesh, p, alpha, dt, src, ncols, scheme, true, alloc, out);
+}
+
+int imex_setup_pcg(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src, int scheme,
+                   const imex_alloc* alloc, imex_ctx** out) {
+  if (scheme != IMEX_SCHEME_IMEX && scheme != IMEX_SCHEME_TRAPEZOIDAL)
+    return fail(IMEX_ERR_ARG, "without a factorisation the scheme must be IMEX or trapezoidal");
+  return setup_impl(mesh, p, alpha, dt, src, 1, scheme, false, alloc, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src, int ncols, int scheme,
+               bool factorize, const imex_alloc* alloc, imex_ctx** out) {
   if (!out) return fail(IMEX_ERR_ARG, "out must not be NULL");
   *out = nullptr;
   imex_ctx* c = nullptr;
@@ -1822,6 +1898,7 @@ int imex_setup_scheme(const imex_mesh* mesh, int p, double alpha, double dt, con
     if (scheme < IMEX_SCHEME_IMEX || scheme > IMEX_SCHEME_TRAPEZOIDAL) return fail(IMEX_ERR_ARG, "unknown scheme");
     pb.ncols = ncols;
     pb.scheme = scheme;
+    pb.factorize = factorize;
     if (pb.dim == 3 && pb.p > 4) return fail(IMEX_ERR_ARG, "the 3D GPU time stepper supports p <= 4");
     c = new imex_ctx();
     c->ncols = ncols;
@@ -1897,10 +1974,22 @@ int imex_setup_scheme(const imex_mesh* mesh, int p, double alpha, double dt, con
       for (int64_t r = 0; r < nc; ++r) fxc[(size_t)col * nc + r] = hs.fx[(size_t)col * nn + hs.c_node[r]];
     (void)nt;
     SolvePlan plan;
-    if (int rc = plan_solve(c, plan)) {
-      delete c;
-      return rc;
+    std::vector<int> if_base_h, if_koff_h;
+    if (factorize) {
+      if (int rc = plan_solve(c, plan)) {
+        delete c;
+        return rc;
+      }
+    } else {   // no solve plan: the rows of the cell matrices and the pairs only
+      if (int rc = interface_rows(hs, plan.Krows, plan.if_sc, if_base_h)) {
+        delete c;
+        return rc;
+      }
+      for (size_t e = 0; e < hs.if_cell.size(); ++e)
+        if_koff_h.push_back(hs.if_kidx[e] >= 0 ? hs.if_kidx[e] : (int)hs.n_cut);
+      if (if_koff_h.empty()) if_koff_h.push_back(0);
     }
+    c->factorized = factorize ? 1 : 0;
     PcgPlan pp;
     if (int rc = plan_pcg(hs, pp)) {
       delete c;
@@ -2062,6 +2151,16 @@ int imex_setup_scheme(const imex_mesh* mesh, int p, double alpha, double dt, con
     ar.add(&c->het_local, std::max<size_t>(hloc.size(), 1));
     ar.add(&c->Kall, std::max<size_t>(plan.Krows.size(), 1));
     ar.add(&c->node_c_dev, std::max<int64_t>(nn, 1));
+    {
+      const bool nf = !factorize;
+      ar.add(&c->m_val, nf ? std::max<size_t>(hs.M_val.size(), 1) : 1);
+      ar.add(&c->dinv_m, nf ? std::max<int64_t>(nc, 1) : 1);
+      ar.add(&c->pr_ptr, nf ? hs.contrib_ptr.size() : 1);
+      ar.add(&c->pr_pos, nf ? std::max<size_t>(hs.contrib_pos.size(), 1) : 1);
+      ar.add(&c->if_base_dev, nf ? if_base_h.size() : 1);
+      ar.add(&c->if_koff_dev, nf ? if_koff_h.size() : 1);
+      ar.add(&c->if_sc_dev, nf ? plan.if_sc.size() : 1);
+    }
     ar.add(&c->ft_buf, 2);
     ar.add(&c->rec_buf, (size_t)c->io_cap * ncols);
     ar.add(&c->rec_nodes, c->io_cap);
@@ -2124,6 +2223,21 @@ int imex_setup_scheme(const imex_mesh* mesh, int p, double alpha, double dt, con
     e = e ? e : upload(c->het_local, hloc);
     e = e ? e : upload(c->Kall, plan.Krows);
     e = e ? e : upload(c->node_c_dev, hs.node_c);
+    if (!factorize && e == cudaSuccess) {
+      std::vector<double> dm(std::max<int64_t>(nc, 1), 0.0);
+      for (int64_t r = 0; r < nc; ++r)
+        for (int k = hs.S_ptr[r]; k < hs.S_ptr[r + 1]; ++k)
+          if (hs.S_col[k] == r) dm[r] = 1.0 / hs.M_val[k];
+      e = upload(c->m_val, hs.M_val);
+      e = e ? e : upload(c->dinv_m, dm);
+      e = e ? e : upload(c->pr_ptr, hs.contrib_ptr);
+      e = e ? e : upload(c->pr_pos, hs.contrib_pos);
+      e = e ? e : upload(c->if_base_dev, if_base_h);
+      e = e ? e : upload(c->if_koff_dev, if_koff_h);
+      e = e ? e : upload(c->if_sc_dev, plan.if_sc);
+      c->solver = IMEX_SOLVER_PCG_JACOBI;
+      c->pcg_maxit = 5000;
+    }
     e = e ? e : upload(c->Kpair, plan.Kpair);
     e = e ? e : upload(c->kp_off, plan.kp_off);
     e = e ? e : upload(c->kp_len, plan.kp_len);
@@ -2182,6 +2296,10 @@ int imex_setup_scheme(const imex_mesh* mesh, int p, double alpha, double dt, con
   }
 }
 
+}  // namespace
+
+extern "C" {
+
 // CTAs of an explicit launch that only predicts (no explicit DOFs).
 int pred_only_blocks(const imex_ctx* c) {
   const int64_t nb = (c->hs.n_c + kThreads - 1) / kThreads;
@@ -2222,7 +2340,11 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
   explicit_dispatch(c, ea, grid, s);
   if (ev) cudaEventRecord(ev[1], s);
   if (hs.n_c > 0) {
-    if (cdm) {
+    if (!c->factorized) {   // right-hand sides, then PCG with the correction
+      launch_rhs_c(c, ft_at(hs, step + 1), Unext, s, ft_dev);
+      if (cudaError_t e = launch_pcg(c, Unext, s))
+        return fail(IMEX_ERR_CUDA, std::string("imex_step: PCG launch: ") + cudaGetErrorString(e));
+    } else if (cdm) {
       launch_solve_chain(c, false, ft_at(hs, step), ft_dev, 3, Unext, Ucur, upd, sol, rhs0, s);
     } else if (c->solver == IMEX_SOLVER_DIRECT || !own) {
       launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, s);
@@ -2431,6 +2553,8 @@ int imex_set_solver(imex_ctx* c, int solver, double tol, int maxit) {
   if (!(tol > 0.0) || maxit < 1 || maxit > 100000) return fail(IMEX_ERR_ARG, "need tol > 0 and 1 <= maxit <= 100000");
   if (solver != IMEX_SOLVER_DIRECT && c->ncols > 1)
     return fail(IMEX_ERR_ARG, "the iterative solve serves single-column contexts");
+  if (solver == IMEX_SOLVER_DIRECT && !c->factorized)
+    return fail(IMEX_ERR_ARG, "the context has no factorisation (imex_setup_pcg)");
   if (solver != IMEX_SOLVER_DIRECT && scheme_is_cdm(c->hs.pb.scheme))
     return fail(IMEX_ERR_ARG, "the iterative solve is of S; central differences solve with M^cc");
   c->solver = solver;
@@ -2521,6 +2645,7 @@ int imex_adjoint(imex_ctx* c, int64_t nsteps, const int64_t* rec_nodes, int nrec
     return fail(IMEX_ERR_ARG, "bad arguments");
   const HostSetup& hs = c->hs;
   if (hs.pb.scheme != kSchemeImex) return fail(IMEX_ERR_ARG, "the adjoint is of the Newmark IMEX scheme");
+  if (!c->factorized) return fail(IMEX_ERR_ARG, "the adjoint needs a factorised context");
   for (int k = 0; k < nrec; ++k)
     if (rec_nodes[k] < 0 || rec_nodes[k] >= hs.nnodes) return fail(IMEX_ERR_ARG, "receiver node out of range");
   cudaStream_t s = c->stream;
@@ -2676,6 +2801,7 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   st->explicit_tile_us_large = c->tile_us[0];
   st->explicit_tile_us_small = c->tile_us[1];
   st->device_bytes = (int64_t)c->bytes;
+  st->factorized = c->factorized;
   return IMEX_OK;
 }
 
@@ -2711,6 +2837,7 @@ static __device__ __align__(256) double g_static_solve_scratch[kStaticScratchDou
 
 extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
   if (!c || n < 0) return fail(IMEX_ERR_ARG, "bad arguments");
+  if (c && !c->factorized) return fail(IMEX_ERR_ARG, "imex_step_noalloc needs a factorised context");
   const HostSetup& hs = c->hs;
   auto even = [](int64_t v) { return v + (v & 1); };
   const int64_t n_upd = even(std::max<int64_t>(hs.upd_size, 1)) * c->ncols;

@@ -188,7 +188,9 @@ struct PcgArgs {
   int* status;                    // [0] iterations of the last solve, [1] 1: converged, 0: fallback
   long long* counters;            // [0] iterations summed, [1] fallbacks
   double* res;                    // relative residual of the last solve
-  // Newmark correction on convergence (as in the direct solve)
+  // Newmark correction on convergence (as in the direct solve), or always
+  // (always_correct: no direct solve to fall back on; misses are counted)
+  int always_correct;
   int mode;
   const int* c_node;
   double* U;

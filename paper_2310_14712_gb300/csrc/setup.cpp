@@ -1044,7 +1044,7 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
     }
     return roots;
   };
-  {
+  if (pb.factorize) {
     auto comps = pieces(cnodes);
     hs.ncomp = (int)comps.size();
     hs.comp_tree_ptr.assign(1, 0);
@@ -1052,6 +1052,16 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
       hs.max_comp = std::max(hs.max_comp, (int)comps[k].size());
       dissect(comps[k], k);
       hs.comp_tree_ptr.push_back((int)hs.tree.size());
+    }
+  } else {
+    // Iterative solve only: the implicit DOFs in grid order, no tree.
+    auto comps = pieces(cnodes);
+    hs.ncomp = (int)comps.size();
+    for (auto& cp : comps) hs.max_comp = std::max(hs.max_comp, (int)cp.size());
+    hs.comp_tree_ptr.assign(1, 0);
+    for (int v : cnodes) {
+      hs.c_node[next_c] = v;
+      hs.node_c[v] = next_c++;
     }
   }
   if (next_c != hs.n_c) return "internal error: nested dissection lost DOFs";
@@ -1108,7 +1118,69 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
 
   // ---------------------------------------------------------------- implicit matrices
   CsrMat Smat, Mmat;
-  {
+  if (!pb.factorize) {
+    // Row by row (threads over rows): row r of S = M^cc + beta dt^2 K^cc and
+    // of M^cc from its (interface cell, local node) contributions, entries of
+    // equal column summed in contribution order.
+    const int nc = (int)hs.n_c;
+    const double bdt2 = kBeta * hs.dt * hs.dt;
+    const int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>(nc, 4096));
+    std::vector<std::vector<int>> ccol(nchunk), ccnt(nchunk);
+    std::vector<std::vector<double>> cs(nchunk), cm(nchunk);
+    parallel_for(nchunk, [&](int64_t b0, int64_t e0) {
+      std::vector<int> cn2(Pd);
+      std::vector<std::pair<int, std::pair<double, double>>> ent;
+      for (int64_t ch = b0; ch < e0; ++ch) {
+        const int64_t r0 = ch * nc / nchunk, r1 = (ch + 1) * nc / nchunk;
+        for (int64_t r = r0; r < r1; ++r) {
+          ent.clear();
+          for (int q = hs.contrib_ptr[r]; q < hs.contrib_ptr[r + 1]; ++q) {
+            const int e = hs.contrib_pos[q] / Pd, la = hs.contrib_pos[q] % Pd;
+            const int64_t cid = hs.if_cell[e];
+            g.cell_nodes(cid, cn2.data());
+            const bool is_cut = hs.cell_type[cid] == CELL_CUT;
+            const double* Ke = is_cut ? hs.cutK.data() + (size_t)hs.if_kidx[e] * Pd * Pd : hs.uncutK.data();
+            const double ks = is_cut ? 1.0 : hs.if_c2[e];
+            const double* Me = is_cut ? cutM_all.data() + (size_t)cut_slot[cid] * Pd * Pd : nullptr;
+            for (int lb = 0; lb < Pd; ++lb) {
+              const int j = hs.node_c[cn2[lb]];
+              if (j < 0) continue;
+              const double kv = ks * Ke[la + (size_t)Pd * lb];
+              const double mv = is_cut ? Me[la + (size_t)Pd * lb] : (la == lb ? uncutM[la] : 0.0);
+              ent.push_back({j, {mv + bdt2 * kv, mv}});
+            }
+          }
+          std::stable_sort(ent.begin(), ent.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+          int cnt = 0;
+          for (size_t k = 0; k < ent.size();) {
+            const int j = ent[k].first;
+            double sv = 0.0, mv = 0.0;
+            while (k < ent.size() && ent[k].first == j) {
+              sv += ent[k].second.first;
+              mv += ent[k].second.second;
+              ++k;
+            }
+            ccol[ch].push_back(j);
+            cs[ch].push_back(sv);
+            cm[ch].push_back(mv);
+            ++cnt;
+          }
+          ccnt[ch].push_back(cnt);
+        }
+      }
+    });
+    hs.S_ptr.assign(1, 0);
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+      for (int k : ccnt[ch]) hs.S_ptr.push_back(hs.S_ptr.back() + k);
+      hs.S_col.insert(hs.S_col.end(), ccol[ch].begin(), ccol[ch].end());
+      hs.S_val.insert(hs.S_val.end(), cs[ch].begin(), cs[ch].end());
+      hs.M_val.insert(hs.M_val.end(), cm[ch].begin(), cm[ch].end());
+      std::vector<int>().swap(ccol[ch]);
+      std::vector<double>().swap(cs[ch]);
+      std::vector<double>().swap(cm[ch]);
+    }
+    if ((int64_t)hs.S_ptr.size() != nc + 1) return "internal error: row assembly lost rows";
+  } else {
     const int nc = (int)hs.n_c;
     std::vector<std::pair<int64_t, double>> es, em;
     const double bdt2 = kBeta * hs.dt * hs.dt;
@@ -1137,6 +1209,17 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
     hs.S_ptr = Smat.ptr;
     hs.S_col = Smat.col;
     hs.S_val = Smat.val;
+    // M^cc on the pattern of S (a subset of it).
+    hs.M_val.assign(hs.S_val.size(), 0.0);
+    for (int i = 0; i < nc; ++i) {
+      int q = Mmat.ptr[i];
+      for (int k = Smat.ptr[i]; k < Smat.ptr[i + 1] && q < Mmat.ptr[i + 1]; ++k)
+        if (Smat.col[k] == Mmat.col[q]) hs.M_val[k] = Mmat.val[q++];
+    }
+  }
+  if (!pb.factorize) {
+    hs.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return "";
   }
 
   // ---------------------------------------------------------------- symbolic

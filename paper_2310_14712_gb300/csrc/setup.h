@@ -37,6 +37,7 @@ struct Problem {
   double dt = 0.0;             // <= 0: dt_factor * the scheme's cell-wise critical step
   double dt_factor = 0.9;
   int scheme = 0;              // kScheme*
+  bool factorize = true;       // false: no dissection and no factorisation (iterative solve only)
 };
 
 // Time integration schemes on the same discretisation (the method and the
@@ -114,6 +115,7 @@ struct HostSetup {
   // iterative solve and of preconditioner training.
   std::vector<int> S_ptr, S_col;
   std::vector<double> S_val;
+  std::vector<double> M_val;   // M^cc on the pattern of S (zeros where M^cc has none)
   int64_t nnz_L = 0;
   double residual_S = 0, residual_M = 0;  // ||A x - b|| / ||b|| of a host replay of the device solve
 

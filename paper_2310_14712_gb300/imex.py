@@ -60,7 +60,7 @@ class Stats(ctypes.Structure):
         [(n, ctypes.c_int64) for n in ("solve_levels", "solve_ctas", "solve_smem_bytes", "launches_per_step",
                                     "rhs_pairs", "ncols", "explicit_tile_cells")] + \
         [(n, ctypes.c_double) for n in ("explicit_tile_us_large", "explicit_tile_us_small")] + \
-        [("scheme", ctypes.c_int64), ("dt_crit_cut_min", ctypes.c_double)]
+        [("scheme", ctypes.c_int64), ("dt_crit_cut_min", ctypes.c_double), ("factorized", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -75,6 +75,8 @@ _lib.imex_setup_batch.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_d
 _lib.imex_setup_scheme.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(Source), ctypes.c_int, ctypes.c_int, ctypes.POINTER(Alloc),
                                    ctypes.POINTER(_vp)]
+_lib.imex_setup_pcg.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                ctypes.POINTER(Source), ctypes.c_int, ctypes.POINTER(Alloc), ctypes.POINTER(_vp)]
 _lib.imex_step.argtypes = [_vp, ctypes.c_int64, _vp]
 _lib.imex_adjoint.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, _dp,
                               ctypes.c_int, _dp, _dp]
@@ -102,7 +104,7 @@ _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctyp
                                         ctypes.POINTER(Stats)]
 
 # Every symbol include/imex.h declares (checked by the CPU tests).
-EXPORTS = ("imex_setup", "imex_setup_batch", "imex_setup_scheme", "imex_adjoint", "imex_set_solver", "imex_pcg_train", "imex_pcg_status",
+EXPORTS = ("imex_setup", "imex_setup_batch", "imex_setup_scheme", "imex_setup_pcg", "imex_adjoint", "imex_set_solver", "imex_pcg_train", "imex_pcg_status",
            "imex_fsai_kaporin", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
            "imex_set_initial", "imex_info", "imex_last_error", "imex_destroy", "imex_gll_points",
            "imex_gauss_points", "imex_host_setup_export")
@@ -236,12 +238,13 @@ class Imex:
     loaded by the source at src_pos[k] alone (imex_setup_batch); fields then
     have ncols * n_nodes entries, column after column.  `scheme` picks the
     time integration (SCHEMES; imex_setup_scheme): the method itself or one of
-    the paper's comparison schemes on the same discretisation.
+    the paper's comparison schemes on the same discretisation.  With
+    factorize=False the implicit solve is PCG only (imex_setup_pcg).
     """
 
     def __init__(self, dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0, src_sigma,
                  src_amp=10.0, wavelet=0, rho=1.0, c0=1.0, cell_c=None, dt=0.0, use_torch_alloc=True,
-                 ncols=1, scheme="imex", **_):
+                 ncols=1, scheme="imex", factorize=True, **_):
         import torch
         self.torch = torch
         if not torch.cuda.is_available():
@@ -252,8 +255,14 @@ class Imex:
         self._allocator = _TorchAllocator(self.device) if use_torch_alloc else None
         ctx = _vp()
         al = ctypes.byref(self._allocator.struct) if self._allocator else None
-        _check(_lib.imex_setup_scheme(ctypes.byref(m), p, alpha, dt, ctypes.byref(s), int(ncols),
-                                      SCHEMES[scheme], al, ctypes.byref(ctx)), "imex_setup_scheme")
+        if factorize:
+            _check(_lib.imex_setup_scheme(ctypes.byref(m), p, alpha, dt, ctypes.byref(s), int(ncols),
+                                          SCHEMES[scheme], al, ctypes.byref(ctx)), "imex_setup_scheme")
+        else:   # no factorisation: PCG only (imex_setup_pcg), one column
+            if int(ncols) != 1:
+                raise ValueError("a context without a factorisation has one column")
+            _check(_lib.imex_setup_pcg(ctypes.byref(m), p, alpha, dt, ctypes.byref(s), SCHEMES[scheme], al,
+                                       ctypes.byref(ctx)), "imex_setup_pcg")
         self._ctx = ctx
         self.stats = self.info()
         self.n_nodes = self.stats["n_nodes"]

@@ -115,3 +115,76 @@ def test_pcg_solver_rejected_for_several_columns():
     with imex.Imex.from_workload(w, ncols=2) as g:
         with pytest.raises(imex.ImexError):
             g.set_solver("pcg_jacobi")
+
+
+# Contexts without a factorisation (imex_setup_pcg): PCG is the only solve.
+
+def _run_nf(w, nsteps, solver="pcg_jacobi", train=0, tol=1e-10, maxit=5000):
+    imex = _imex()
+    with imex.Imex.from_workload(w, factorize=False) as g:
+        info = g.info()
+        a0 = g.fields("a_c", out=np.zeros(g.n_nodes))
+        if train:
+            g.pcg_train(train)
+        g.set_solver(solver, tol, maxit)
+        g.step(nsteps)
+        u = g.fields("u", out=np.zeros(g.n_nodes))
+        status = g.pcg_status()
+    return u, a0, status, info
+
+
+@pytest.mark.parametrize("solver,train", [("pcg_jacobi", 0), ("pcg_fsai", 400)])
+def test_pcg_without_factorisation_matches_oracle(solver, train):
+    w = workloads.plate16()
+    nsteps = 120
+    u, a0, status, info = _run_nf(w, nsteps, solver, train)
+    assert info["factorized"] == 0 and info["nnz_L"] == 0 and info["launches_per_step"] == 3
+    assert status["fallbacks"] == 0
+    s = pipeline.setup(**w.kwargs())
+    st0 = s.imex.initial_state()
+    phys = phys_mask(s, w.holes)
+    # a^c_0 by Jacobi-CG on M^cc to 1e-12 (M^cc is far worse conditioned than S).
+    assert pipeline.relative_l2(a0, st0.a_c, phys & s.disc.is_c) <= 1e-8
+    ref = s.imex.run(nsteps)
+    # Same bounds as the PCG stepping of a factorised context (cond(S) x tol).
+    assert pipeline.relative_l2(u, ref.u, phys) <= 1e-8
+    assert pipeline.relative_l2(u, ref.u, s.disc.active) <= 1e-6
+
+
+def test_pcg_without_factorisation_3d_voids():
+    # Six seeded ellipsoidal voids on 6 x 6 x 3 cells, p = 3, octree depth 2.
+    w = workloads.voids3d(ncells=(6, 6, 3))
+    w.holes = w.holes[:6]
+    nsteps = 40
+    u, _, status, info = _run_nf(w, nsteps)
+    assert status["fallbacks"] == 0 and info["n_c"] > 0
+    s = pipeline.setup(**w.kwargs())
+    ref = s.imex.run(nsteps)
+    assert pipeline.relative_l2(u, ref.u, phys_mask(s, w.holes)) <= 1e-8
+    assert pipeline.relative_l2(u, ref.u, s.disc.active) <= 1e-6
+
+
+def test_pcg_without_factorisation_trapezoidal():
+    from oracle import schemes
+    w = workloads.plate16()
+    imex = _imex()
+    with imex.Imex.from_workload(w, factorize=False, scheme="trapezoidal") as g:
+        g.set_solver("pcg_jacobi", 1e-11, 5000)
+        g.step(60)
+        u = g.fields("u", out=np.zeros(g.n_nodes))
+        assert g.pcg_status()["fallbacks"] == 0
+    s = pipeline.setup(**w.kwargs())
+    ref = schemes.run(s, "trapezoidal", 60)
+    assert pipeline.relative_l2(u, ref.u, phys_mask(s, w.holes)) <= 1e-8
+
+
+def test_context_without_factorisation_restrictions():
+    imex = _imex()
+    w = workloads.plate16()
+    with imex.Imex.from_workload(w, factorize=False) as g:
+        with pytest.raises(imex.ImexError):
+            g.set_solver("direct")
+        with pytest.raises(imex.ImexError):
+            g.step_noalloc(1)
+    with pytest.raises(ValueError):
+        imex.Imex.from_workload(workloads.multisource(nsrc=2), ncols=2, factorize=False)
