@@ -173,6 +173,56 @@ def measure_schemes(imex, workloads, steps, stream, flush):
     return out
 
 
+def measure_voids3d(imex, workloads, stream, flush, steps=10, epochs=100):
+    """The 3D voided solid at full size (64x64x32 cells, p=3, 40 ellipsoidal
+    voids, octree depth 2): its dissection separators exceed the device
+    solve's 256-row supernodes, so the context has no factorisation
+    (imex_setup_pcg) and every implicit solve is PCG to 1e-10, first with
+    Jacobi, then with the learned FSAI preconditioner."""
+    import time as _t
+    w = workloads.voids3d()
+    t0 = _t.perf_counter()
+    g = imex.Imex.from_workload(w, factorize=False)
+    setup_s = _t.perf_counter() - t0
+    st = g.info()
+    n_act = st["n_d"] + st["n_c"]
+    out = {"workload": (f"voids3d: [0,1]x[0,1]x[0,0.5] minus {len(w.holes)} ellipsoids, "
+                        f"{w.ncells[0]}x{w.ncells[1]}x{w.ncells[2]} cells, p={w.p}, alpha={w.alpha:g}, "
+                        f"octree depth {w.depth}, Ricker f0={w.f0:g}"),
+           "unit": UNIT, "n_nodes": st["n_nodes"], "n_d": st["n_d"], "n_c": st["n_c"], "n_cut": st["n_cut"],
+           "components": st["n_components"], "dt": st["dt"], "factorized": st["factorized"],
+           "setup_seconds": setup_s, "device_bytes": st["device_bytes"], "tol": 1e-10,
+           "l2": "flushed between timed steps", "steps": steps}
+
+    def timed(solver, nsteps):
+        g.set_solver(solver, 1e-10, 5000)
+        g.step(2)
+        a = g.pcg_status()
+        ph = [0.0, 0.0, 0.0]
+        for k in range(nsteps):
+            flush.fill_(float(k))
+            for q, v in enumerate(g.step_profile(1, stream)):
+                ph[q] += v
+        b = g.pcg_status()
+        return {"value": n_act * nsteps / (ph[2] * 1e-3), "ms_per_step": ph[2] / nsteps,
+                "explicit_ms": ph[0] / nsteps, "implicit_ms": ph[1] / nsteps,
+                "iterations_per_step": (b["iters_total"] - a["iters_total"]) / nsteps,
+                "fallbacks": b["fallbacks"] - a["fallbacks"]}
+
+    out["pcg_jacobi"] = timed("pcg_jacobi", max(2, steps // 2))
+    t0 = _t.perf_counter()
+    hist = g.pcg_train(epochs)
+    out["train_epochs"] = epochs
+    out["train_seconds"] = _t.perf_counter() - t0
+    out["kaporin_loss"] = [float(hist[0]), float(hist[-1])]
+    out["pcg_fsai"] = timed("pcg_fsai", steps)
+    out["value"] = out["pcg_fsai"]["value"]
+    out["learned_vs_jacobi_iterations"] = (out["pcg_fsai"]["iterations_per_step"] /
+                                           max(out["pcg_jacobi"]["iterations_per_step"], 1e-30))
+    g.close()
+    return out
+
+
 def measure_adjoint(imex, workloads, nrec=64, checkpoint_every=100):
     """Misfit gradient in the per-cell wave speed by the discrete adjoint, on
     the adjoint workload (16x16-cell plate, smooth seeded speed, 16 sources as
@@ -455,6 +505,7 @@ def run_gpu(args):
         line["learned_pcg"] = measure_learned_pcg(imex, w, min(args.steps, 20), stream, flush)
         line["adjoint"] = measure_adjoint(imex, workloads)
         line["schemes"] = measure_schemes(imex, workloads, min(args.steps, 200), stream, flush)
+        line["voids3d"] = measure_voids3d(imex, workloads, stream, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n_act_cpu, secs = cpu_oracle_rate(w, args.cpu_steps)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",

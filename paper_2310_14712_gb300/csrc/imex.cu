@@ -72,51 +72,76 @@ __device__ __forceinline__ double grid_total(const double* part, int slot) {
   return s;
 }
 
-// One row of a CSR product; four independent gathers in flight per thread.
-__device__ __forceinline__ double csr_row_dot(const int* ptr, const int* col, const double* val, const double* v,
-                                              int i) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int k = ptr[i];
-  const int e = ptr[i + 1];
-  for (; k + 4 <= e; k += 4) {
-    const int c0 = col[k], c1 = col[k + 1], c2 = col[k + 2], c3 = col[k + 3];
-    const double x0 = __ldcg(v + c0), x1 = __ldcg(v + c1), x2 = __ldcg(v + c2), x3 = __ldcg(v + c3);
-    s0 = fma(val[k], x0, s0);
-    s1 = fma(val[k + 1], x1, s1);
-    s2 = fma(val[k + 2], x2, s2);
-    s3 = fma(val[k + 3], x3, s3);
-  }
-  for (; k < e; ++k) s0 = fma(val[k], __ldcg(v + col[k]), s0);
-  return (s0 + s1) + (s2 + s3);
-}
+// Values of G in the column order of its transpose lists (gt_val[k] =
+// g_val[gt_idx[k]]), refreshed whenever G changes: G^T r then streams them.
+struct PcgCols {
+  const double* gt_val;
+};
 
-__global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
+__global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a, PcgCols t2) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[kWarps];
   const int n = a.n;
   const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  // Sparse products one warp per row: lanes stride the row (coalesced column
+  // and value loads), a fixed xor tree sums them; every lane gets the value.
+  const int lane = threadIdx.x & 31, w0 = g0 >> 5, ws = gs >> 5;
+  auto warp_dot = [&](const int* ptr, const int* col, const double* val, const double* v, int i) {
+    const int end = ptr[i + 1];
+    double t0 = 0.0, t1 = 0.0;
+    int k = ptr[i] + lane;
+    for (; k + 32 < end; k += 64) {   // two independent gathers in flight per lane
+      const int c0 = col[k], c1 = col[k + 32];
+      const double v0 = val[k], v1 = val[k + 32];
+      t0 = fma(v0, __ldcg(v + c0), t0);
+      t1 = fma(v1, __ldcg(v + c1), t1);
+    }
+    if (k < end) t0 = fma(val[k], __ldcg(v + col[k]), t0);
+    double t = t0 + t1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+  };
   // z = M^{-1} r
   auto apply_minv = [&]() {
     if (a.precond == 2) {
       for (int i = g0; i < n; i += gs) a.z[i] = a.dinv[i] * a.r[i];
     } else {
-      for (int j = g0; j < n; j += gs) {
-        double s = 0.0;
-        for (int k = a.gt_ptr[j]; k < a.gt_ptr[j + 1]; ++k) s = fma(a.g_val[a.gt_idx[k]], __ldcg(a.r + a.gt_row[k]), s);
-        a.w[j] = s;
+      for (int j = w0; j < n; j += ws) {   // w = G^T r, column j of G
+        const int end = a.gt_ptr[j + 1];
+        double t0 = 0.0, t1 = 0.0;
+        int k = a.gt_ptr[j] + lane;
+        for (; k + 32 < end; k += 64) {
+          const int r0 = a.gt_row[k], r1 = a.gt_row[k + 32];
+          const double g0v = t2.gt_val[k], g1v = t2.gt_val[k + 32];
+          t0 = fma(g0v, __ldcg(a.r + r0), t0);
+          t1 = fma(g1v, __ldcg(a.r + r1), t1);
+        }
+        if (k < end) t0 = fma(t2.gt_val[k], __ldcg(a.r + a.gt_row[k]), t0);
+        double t = t0 + t1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) a.w[j] = t;
       }
       grid.sync();
-      for (int i = g0; i < n; i += gs) a.z[i] = csr_row_dot(a.g_ptr, a.g_col, a.g_val, a.w, i);
+      for (int i = w0; i < n; i += ws) {
+        const double zi = warp_dot(a.g_ptr, a.g_col, a.g_val, a.w, i);
+        if (lane == 0) a.z[i] = zi;
+      }
+      grid.sync();   // z is read below by other threads than its writers
     }
   };
   for (int i = g0; i < n; i += gs) a.x[i] = a.a_c[i];
   grid.sync();
   double bb = 0.0, rr = 0.0;
-  for (int i = g0; i < n; i += gs) {
-    const double bi = a.b[i], ri = bi - csr_row_dot(a.s_ptr, a.s_col, a.s_val, a.x, i);
-    a.r[i] = ri;
-    bb = fma(bi, bi, bb);
-    rr = fma(ri, ri, rr);
+  for (int i = w0; i < n; i += ws) {
+    const double ri0 = warp_dot(a.s_ptr, a.s_col, a.s_val, a.x, i);
+    if (lane == 0) {
+      const double bi = a.b[i], ri = bi - ri0;
+      a.r[i] = ri;
+      bb = fma(bi, bi, bb);
+      rr = fma(ri, ri, rr);
+    }
   }
   block_partial(bb, a.part, 3, red);
   block_partial(rr, a.part, 1, red);
@@ -138,10 +163,12 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
     rz = grid_total(a.part, 2);
     for (k = 1; k <= a.maxit; ++k) {
       double pq = 0.0;
-      for (int i = g0; i < n; i += gs) {
-        const double qi = csr_row_dot(a.s_ptr, a.s_col, a.s_val, a.p, i);
-        a.q[i] = qi;
-        pq = fma(a.p[i], qi, pq);
+      for (int i = w0; i < n; i += ws) {
+        const double qi = warp_dot(a.s_ptr, a.s_col, a.s_val, a.p, i);
+        if (lane == 0) {
+          a.q[i] = qi;
+          pq = fma(a.p[i], qi, pq);
+        }
       }
       block_partial(pq, a.part, 0, red);
       grid.sync();
@@ -273,6 +300,12 @@ __global__ void k_adam(int64_t nnz, double* theta, const double* grad, const dou
   if (is_diag[e]) th = fmax(th, floor_);
   theta[e] = th;
   g_val[e] = th * scale[e];
+}
+
+// gt_val[k] = g_val[gt_idx[k]] (G's values in transpose order).
+__global__ void k_gt_vals(int64_t nnz, const double* g_val, const int* gt_idx, double* gt_val) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nnz) gt_val[k] = g_val[gt_idx[k]];
 }
 
 // ---------------------------------------------------------------------------
@@ -634,6 +667,7 @@ struct imex_ctx {
   double *g_val = nullptr, *g_scale = nullptr, *g_theta = nullptr, *g_m = nullptr, *g_v = nullptr;
   double *g_grad = nullptr, *g_sg = nullptr, *dinv = nullptr;
   uint8_t* g_isdiag = nullptr;
+  double* gt_val = nullptr;   // G's values in transpose order
   // no factorisation (imex_setup_pcg): M^cc on S's pattern for the initial
   // acceleration, and the (row, interface cell) pairs of K^c u per row
   int factorized = 1;
@@ -1057,7 +1091,8 @@ cudaError_t launch_pcg(imex_ctx* c, double* Ubuf, cudaStream_t s, bool on_M = fa
   a.v_c = c->v_c;
   a.a_c = c->a_c;
   a.dt = hs.dt;
-  void* args[] = {&a};
+  PcgCols t2{c->gt_val};
+  void* args[] = {&a, &t2};
   return cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(c->pcg_grid), dim3(kThreads), args, 0, s);
 }
 
@@ -2127,6 +2162,7 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       ar.add(&c->gt_row, gnz);
       ar.add(&c->gt_idx, gnz);
       ar.add(&c->g_val, gnz);
+      ar.add(&c->gt_val, gnz);
       ar.add(&c->g_scale, gnz);
       ar.add(&c->g_theta, gnz);
       ar.add(&c->g_m, gnz);
@@ -2199,6 +2235,11 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->gt_row, pp.gt_row);
     e = e ? e : upload(c->gt_idx, pp.gt_idx);
     e = e ? e : upload(c->g_val, pp.g_val);
+    {
+      std::vector<double> gtv(pp.gt_idx.size());
+      for (size_t k = 0; k < gtv.size(); ++k) gtv[k] = pp.g_val[pp.gt_idx[k]];
+      e = e ? e : upload(c->gt_val, gtv);
+    }
     e = e ? e : upload(c->g_scale, pp.g_scale);
     e = e ? e : upload(c->g_theta, pp.g_theta);
     e = e ? e : upload(c->g_isdiag, pp.g_isdiag);
@@ -2208,10 +2249,12 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg, kThreads, 0);
       int nsm = 0;
       e = e ? e : cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-      // About one row per thread, at most one CTA per SM: fewer CTAs make the
-      // grid barriers cheaper on small partitions.
-      const int rows_ctas = (int)std::max<int64_t>(1, (hs.n_c + kThreads - 1) / kThreads);
-      c->pcg_grid = std::max(1, std::min({nsm, 1024, nsm * occ, rows_ctas}));
+      // Sparse products take one warp per row.  Small partitions: at most one
+      // CTA per SM (fewer CTAs make the grid barriers cheaper); large ones
+      // (3D): every co-resident CTA, about four rows per warp.
+      const int64_t rows_ctas = std::max<int64_t>(1, (hs.n_c + 4 * kWarps - 1) / (4 * kWarps));
+      const int cap = hs.n_c >= 65536 ? nsm * occ : nsm;
+      c->pcg_grid = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)cap, 1024, (int64_t)nsm * occ, rows_ctas}));
     }
     e = e ? e : upload(c->het_base, hb);
     e = e ? e : upload(c->het_koff, hk);
@@ -2587,6 +2630,9 @@ int imex_pcg_train(imex_ctx* c, int epochs, double lr, double* loss_hist) {
                                     std::pow(0.9, (double)t), std::pow(0.999, (double)t), lr, 1e-3, c->g_val);
     if (int rc = check_launch("imex_pcg_train")) return rc;
   }
+  if (epochs > 0 && c->g_nnz > 0)
+    k_gt_vals<<<(unsigned)((c->g_nnz + kThreads - 1) / kThreads), kThreads, 0, s>>>(c->g_nnz, c->g_val, c->gt_idx,
+                                                                                      c->gt_val);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_pcg_train: ") + cudaGetErrorString(e));
   return IMEX_OK;
