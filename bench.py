@@ -190,6 +190,7 @@ def measure_voids3d(imex, workloads, stream, flush, steps=10, epochs=100):
                         f"{w.ncells[0]}x{w.ncells[1]}x{w.ncells[2]} cells, p={w.p}, alpha={w.alpha:g}, "
                         f"octree depth {w.depth}, Ricker f0={w.f0:g}"),
            "unit": UNIT, "n_nodes": st["n_nodes"], "n_d": st["n_d"], "n_c": st["n_c"], "n_cut": st["n_cut"],
+           "n_uncut": st["n_uncut"],
            "components": st["n_components"], "dt": st["dt"], "factorized": st["factorized"],
            "setup_seconds": setup_s, "device_bytes": st["device_bytes"], "tol": 1e-10,
            "l2": "flushed between timed steps", "steps": steps}
@@ -204,8 +205,10 @@ def measure_voids3d(imex, workloads, stream, flush, steps=10, epochs=100):
             for q, v in enumerate(g.step_profile(1, stream)):
                 ph[q] += v
         b = g.pcg_status()
+        P = w.p + 1
         return {"value": n_act * nsteps / (ph[2] * 1e-3), "ms_per_step": ph[2] / nsteps,
                 "explicit_ms": ph[0] / nsteps, "implicit_ms": ph[1] / nsteps,
+                "explicit_fp64_tflops": 14 * P ** 4 * st["n_uncut"] / (ph[0] / nsteps * 1e-3) / 1e12,
                 "iterations_per_step": (b["iters_total"] - a["iters_total"]) / nsteps,
                 "fallbacks": b["fallbacks"] - a["fallbacks"]}
 
