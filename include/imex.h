@@ -43,7 +43,8 @@ extern "C" {
 #define IMEX_ERR_ALLOC (-3)    /* allocation failed */
 #define IMEX_ERR_CUDA (-4)     /* CUDA runtime error */
 #define IMEX_ERR_NOT_SPD (-5)  /* S or M^cc not positive definite */
-#define IMEX_ERR_TIMEOUT (-6)  /* a bounded device wait gave up */
+#define IMEX_ERR_TIMEOUT (-6)  /* reserved: a bounded device wait gave up (no kernel of this
+                                  library waits on a flag; none returns it) */
 #define IMEX_ERR_DIVERGED (-7) /* non-finite field values */
 
 /* Source time functions f_t (Sec. Spatial discretization: f(t) = f_t(t) f_x). */
@@ -372,6 +373,16 @@ int imex_set_initial(imex_ctx *ctx, const double *u0, const double *v0, int64_t 
 
 /* imex_info - sizes, counts and the time step. */
 int imex_info(imex_ctx *ctx, imex_stats *out);
+
+/*
+ * imex_check_finite - health check of the state after the steps issued so far
+ * (synchronises the context's stream): *max_abs_u receives max |u_n| over the
+ * active DOFs of every column.  Returns IMEX_ERR_DIVERGED if u_n, u_{n-1} or
+ * the c-partition velocity or acceleration holds a non-finite value (an
+ * unstable step, e.g. a central-difference scheme above its critical step),
+ * else IMEX_OK.  max_abs_u may be NULL.
+ */
+int imex_check_finite(imex_ctx *ctx, double *max_abs_u);
 
 /* imex_last_error - message of the calling thread's last failure ("" if none). */
 const char *imex_last_error(void);

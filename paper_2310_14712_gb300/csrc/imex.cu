@@ -302,6 +302,38 @@ __global__ void k_adam(int64_t nnz, double* theta, const double* grad, const dou
   g_val[e] = th * scale[e];
 }
 
+// Health check: per block max |x| over the entries whose class is nonzero
+// (out[b]) and whether any of the n entries (class-masked) is non-finite
+// (flag[b] = 1).  Grid-stride, kHealthBlocks blocks.
+constexpr int kHealthBlocks = 1024;
+__global__ void __launch_bounds__(kThreads) k_health(const double* x, int64_t n, const uint8_t* cls,
+                                                     int64_t cs, double* out, int* flag, int accumulate) {
+  __shared__ double smax[kThreads];
+  __shared__ int sbad[kThreads];
+  double m = 0.0;
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (cls && cls[i % cs] == 0) continue;
+    const double v = x[i];
+    if (!isfinite(v)) bad = 1;
+    else m = fmax(m, fabs(v));
+  }
+  smax[threadIdx.x] = m;
+  sbad[threadIdx.x] = bad;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + w]);
+      sbad[threadIdx.x] |= sbad[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[blockIdx.x] = accumulate ? fmax(out[blockIdx.x], smax[0]) : smax[0];
+    flag[blockIdx.x] = accumulate ? (flag[blockIdx.x] | sbad[0]) : sbad[0];
+  }
+}
+
 // gt_val[k] = g_val[gt_idx[k]] (G's values in transpose order).
 __global__ void k_gt_vals(int64_t nnz, const double* g_val, const int* gt_idx, double* gt_val) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2848,6 +2880,37 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   st->explicit_tile_us_small = c->tile_us[1];
   st->device_bytes = (int64_t)c->bytes;
   st->factorized = c->factorized;
+  return IMEX_OK;
+}
+
+int imex_check_finite(imex_ctx* c, double* max_abs_u) {
+  if (!c) return fail(IMEX_ERR_ARG, "NULL context");
+  const HostSetup& hs = c->hs;
+  cudaStream_t s = c->stream;
+  const int64_t nn = hs.nnodes * c->ncols, nc = hs.n_c * c->ncols;
+  double* out = c->pcg_part;                          // kHealthBlocks maxima
+  int* flag = reinterpret_cast<int*>(c->pcg_part + kHealthBlocks);
+  k_health<<<kHealthBlocks, kThreads, 0, s>>>(c->U[c->cur], nn, c->cls, hs.nnodes, out, flag, 0);
+  k_health<<<kHealthBlocks, kThreads, 0, s>>>(c->U[1 - c->cur], nn, c->cls, hs.nnodes, c->pcg_part + 2 * kHealthBlocks,
+                                              flag, 1);
+  if (nc > 0) {
+    k_health<<<kHealthBlocks, kThreads, 0, s>>>(c->v_c, nc, nullptr, 1, c->pcg_part + 2 * kHealthBlocks, flag, 1);
+    k_health<<<kHealthBlocks, kThreads, 0, s>>>(c->a_c, nc, nullptr, 1, c->pcg_part + 2 * kHealthBlocks, flag, 1);
+  }
+  std::vector<double> m(kHealthBlocks);
+  std::vector<int> f(kHealthBlocks);
+  cudaError_t e = cudaMemcpyAsync(m.data(), out, kHealthBlocks * sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = e ? e : cudaMemcpyAsync(f.data(), flag, kHealthBlocks * sizeof(int), cudaMemcpyDeviceToHost, s);
+  e = e ? e : cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_check_finite: ") + cudaGetErrorString(e));
+  double mx = 0.0;
+  int bad = 0;
+  for (int b = 0; b < kHealthBlocks; ++b) {
+    mx = std::max(mx, m[b]);
+    bad |= f[b];
+  }
+  if (max_abs_u) *max_abs_u = mx;
+  if (bad) return fail(IMEX_ERR_DIVERGED, "non-finite values in the state");
   return IMEX_OK;
 }
 

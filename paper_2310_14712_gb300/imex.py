@@ -78,6 +78,7 @@ _lib.imex_setup_scheme.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_
 _lib.imex_setup_pcg.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                 ctypes.POINTER(Source), ctypes.c_int, ctypes.POINTER(Alloc), ctypes.POINTER(_vp)]
 _lib.imex_step.argtypes = [_vp, ctypes.c_int64, _vp]
+_lib.imex_check_finite.argtypes = [_vp, _dp]
 _lib.imex_adjoint.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, _dp,
                               ctypes.c_int, _dp, _dp]
 _lib.imex_set_solver.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
@@ -106,7 +107,7 @@ _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctyp
 # Every symbol include/imex.h declares (checked by the CPU tests).
 EXPORTS = ("imex_setup", "imex_setup_batch", "imex_setup_scheme", "imex_setup_pcg", "imex_adjoint", "imex_set_solver", "imex_pcg_train", "imex_pcg_status",
            "imex_fsai_kaporin", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
-           "imex_set_initial", "imex_info", "imex_last_error", "imex_destroy", "imex_gll_points",
+           "imex_set_initial", "imex_info", "imex_check_finite", "imex_last_error", "imex_destroy", "imex_gll_points",
            "imex_gauss_points", "imex_host_setup_export")
 
 
@@ -383,6 +384,13 @@ class Imex:
             v0 = _f64(v0)
             v0p = v0.ctypes.data
         _check(_lib.imex_set_initial(self._ctx, u0.ctypes.data, v0p, self.field_len, 0), "imex_set_initial")
+
+    def check_finite(self):
+        """max |u_n| over the active DOFs; raises ImexError (IMEX_ERR_DIVERGED) if
+        the state holds a non-finite value."""
+        m = ctypes.c_double()
+        _check(_lib.imex_check_finite(self._ctx, ctypes.byref(m)), "imex_check_finite")
+        return m.value
 
     def info(self):
         st = Stats()

@@ -133,3 +133,35 @@ def test_scheme_restrictions():
             g.set_solver("pcg_jacobi")
         with pytest.raises(imex.ImexError):
             g.adjoint(4, np.array([5]), np.zeros((4, 1, 1)))
+
+
+def test_health_check_reports_divergence_above_the_critical_step():
+    # Central differences at 1.5 x the global critical step of a small plate
+    # grow by about 2x per step until the state overflows; the health check
+    # reports it (IMEX_ERR_DIVERGED).  Below the step it returns max |u|.
+    import scipy.linalg as sla
+    import scipy.sparse as sp
+    imex = _imex()
+    w = workloads.Workload("box", 2, (0.0, 0.0), (1.0, 1.0), (4, 4), 2, 1e-3, 2,
+                           np.array([[0.5, 0.5, 0.2, 0.2]]), np.array([[0.27, 0.31]]), 3.0, 0.08, 0)
+    s = pipeline.setup(**w.kwargs())
+    act = np.flatnonzero(s.disc.active)
+    K = sp.csr_matrix(s.disc.K)[act][:, act].toarray()
+    M = sp.csr_matrix(s.disc.M)[act][:, act].toarray()
+    dt_crit = 2.0 / np.sqrt(sla.eigh(K, M, eigvals_only=True)[-1])
+    X = s.grid.node_coords()
+    u0 = np.cos(np.pi * X[:, 0]) * np.cos(np.pi * X[:, 1])
+    stable = dataclasses.replace(w, dt=0.9 * dt_crit)
+    with imex.Imex.from_workload(stable, scheme="cdm") as g:
+        g.set_initial(u0)
+        g.step(300)
+        u = g.fields("u", out=np.zeros(g.n_nodes))
+        assert g.check_finite() == pytest.approx(np.abs(u[s.disc.active]).max(), rel=0, abs=0)
+    unstable = dataclasses.replace(w, dt=1.5 * dt_crit)
+    with imex.Imex.from_workload(unstable, scheme="cdm") as g:
+        g.set_initial(u0)
+        g.step(20)
+        assert np.isfinite(g.check_finite())
+        g.step(3000)
+        with pytest.raises(imex.ImexError, match="DIVERGED"):
+            g.check_finite()
