@@ -116,19 +116,38 @@ def measure_batched(imex, workloads, steps, stream, flush):
     return b
 
 
-def measure_learned_pcg(imex, w, steps, stream, flush, epochs=300):
+def snapshot(g):
+    """State (u, u_{n-1} on I_d, v^c, a^c) and step counter of a context."""
+    return ({k: g.fields(k, out=np.zeros(g.field_len)) for k in ("u", "u_prev_d", "v_c", "a_c")},
+            g.info()["step"])
+
+
+def restore(g, snap):
+    for k, v in snap[0].items():
+        g.set_fields(k, v)
+    g.set_step(snap[1])
+
+
+def measure_learned_pcg(imex, w, steps, stream, flush, epochs=300, lr=0.1, t_active=600):
     """The implicit solve by PCG (tol 1e-10) with the learned FSAI preconditioner
-    and with Jacobi, against the factorised solve, on the bench workload."""
+    and with Jacobi, against the factorised solve, on the bench workload.  All
+    three run the same steps from one snapshot taken after t_active steps, when
+    the pulse has reached the holes (before that the implicit right-hand sides
+    are exactly zero and PCG takes no iteration)."""
     g = imex.Imex.from_workload(w)
     st = g.info()
     n_act = st["n_d"] + st["n_c"]
+    g.step(t_active)
+    snap = snapshot(g)
     t0 = time.perf_counter()
-    hist = g.pcg_train(epochs)
+    hist = g.pcg_train(epochs, lr)
     train_s = time.perf_counter() - t0
-    out = {"workload": workload_name(w), "unit": UNIT, "tol": 1e-10, "train_epochs": epochs,
+    out = {"workload": workload_name(w), "unit": UNIT, "tol": 1e-10, "train_epochs": epochs, "lr": lr,
            "train_seconds": train_s, "kaporin_loss": [float(hist[0]), float(hist[-1])],
-           "l2": "flushed between timed steps", "steps": steps}
+           "l2": "flushed between timed steps", "steps": steps,
+           "window": f"steps {t_active + 3}..{t_active + 3 + steps} from one snapshot"}
     for solver in ("direct", "pcg_fsai", "pcg_jacobi"):
+        restore(g, snap)
         g.set_solver(solver, 1e-10, 5000)
         g.step(3)
         s0 = g.pcg_status()
@@ -173,12 +192,13 @@ def measure_schemes(imex, workloads, steps, stream, flush):
     return out
 
 
-def measure_voids3d(imex, workloads, stream, flush, steps=10, epochs=100):
+def measure_voids3d(imex, workloads, stream, flush, steps=10, epochs=300, lr=0.2, t_active=20):
     """The 3D voided solid at full size (64x64x32 cells, p=3, 40 ellipsoidal
     voids, octree depth 2): its dissection separators exceed the device
     solve's 256-row supernodes, so the context has no factorisation
-    (imex_setup_pcg) and every implicit solve is PCG to 1e-10, first with
-    Jacobi, then with the learned FSAI preconditioner."""
+    (imex_setup_pcg) and every implicit solve is PCG to 1e-10: with the
+    learned FSAI preconditioner (trained first, then stepped to t_active) and
+    with Jacobi, both from the same snapshot."""
     import time as _t
     w = workloads.voids3d()
     t0 = _t.perf_counter()
@@ -212,13 +232,19 @@ def measure_voids3d(imex, workloads, stream, flush, steps=10, epochs=100):
                 "iterations_per_step": (b["iters_total"] - a["iters_total"]) / nsteps,
                 "fallbacks": b["fallbacks"] - a["fallbacks"]}
 
-    out["pcg_jacobi"] = timed("pcg_jacobi", max(2, steps // 2))
     t0 = _t.perf_counter()
-    hist = g.pcg_train(epochs)
+    hist = g.pcg_train(epochs, lr)
     out["train_epochs"] = epochs
+    out["lr"] = lr
     out["train_seconds"] = _t.perf_counter() - t0
     out["kaporin_loss"] = [float(hist[0]), float(hist[-1])]
+    g.set_solver("pcg_fsai", 1e-10, 5000)
+    g.step(t_active)
+    snap = snapshot(g)
+    out["window"] = f"steps {t_active + 2}.. from one snapshot"
     out["pcg_fsai"] = timed("pcg_fsai", steps)
+    restore(g, snap)
+    out["pcg_jacobi"] = timed("pcg_jacobi", max(2, steps // 2))
     out["value"] = out["pcg_fsai"]["value"]
     out["learned_vs_jacobi_iterations"] = (out["pcg_fsai"]["iterations_per_step"] /
                                            max(out["pcg_jacobi"]["iterations_per_step"], 1e-30))
