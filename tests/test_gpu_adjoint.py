@@ -119,3 +119,24 @@ def test_adjoint_full_size_against_central_differences():
         cm = c.copy(); cm[e] -= h
         fd = (Jof(cp) - Jof(cm)) / (2 * h)
         assert abs(fd - g[e]) <= 1e-4 * abs(fd), (e, fd, g[e])
+
+
+def test_adjoint_3d_matches_oracle():
+    # 4 x 3 x 3 cells, p = 2, one void, per-cell speed, 2 sources, 25 steps.
+    from paper_2310_14712_gb300 import adjoint
+    rng = np.random.default_rng(3)
+    w = workloads.Workload("adj3", 3, (0.0, 0.0, 0.0), (1.0, 0.8, 0.6), (4, 3, 3), 2, 1e-4, 2,
+                           np.array([[0.55, 0.4, 0.3, 0.22, 0.18, 0.15]]),
+                           np.array([[0.2, 0.25, 0.2], [0.8, 0.55, 0.35]]), 3.0, 0.1, 0)
+    c = 1.0 + 0.1 * rng.standard_normal(4 * 3 * 3)
+    w.cell_c = c
+    s = pipeline.setup(**dict(w.kwargs(), src_pos=w.src_pos[:1]))
+    w.dt = s.dt
+    nn = s.grid.nnodes
+    rec = np.arange(nn - 12, nn, 2, dtype=np.int64)
+    nsteps = 25
+    data = 1e-3 * rng.standard_normal((nsteps, 2, len(rec)))
+    J, g = adjoint.misfit_and_gradient(w, c, rec, data, nsteps, checkpoint_every=7)
+    Jr, gr = _oracle(w, c, rec, data, nsteps)
+    assert J == pytest.approx(Jr, rel=1e-10)
+    assert np.linalg.norm(g - gr) <= 1e-8 * np.linalg.norm(gr)

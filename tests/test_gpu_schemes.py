@@ -165,3 +165,12 @@ def test_health_check_reports_divergence_above_the_critical_step():
         g.step(3000)
         with pytest.raises(imex.ImexError, match="DIVERGED"):
             g.check_finite()
+
+
+@pytest.mark.parametrize("scheme", ["cdm", "cdm_hrz", "trapezoidal"])
+def test_schemes_3d(scheme):
+    # 4 x 3 x 3 cells, p = 2, one ellipsoidal void, octree depth 2.
+    w = workloads.Workload("box3", 3, (0.0, 0.0, 0.0), (1.0, 0.8, 0.6), (4, 3, 3), 2, 1e-5, 2,
+                           np.array([[0.55, 0.4, 0.3, 0.22, 0.18, 0.15]]), np.array([[0.21, 0.27, 0.22]]),
+                           3.0, 0.1, 0)
+    _check(w, scheme, 40)
