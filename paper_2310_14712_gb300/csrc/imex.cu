@@ -1883,7 +1883,22 @@ int imex_gauss_points(int n, double* x, double* w) {
   return IMEX_OK;
 }
 
-static void fill_stats(const HostSetup& hs, imex_stats* st) {
+static // IMEX_LOG=1 in the environment: one JSON line of setup statistics on stderr.
+void log_setup(const HostSetup& hs, const char* where) {
+  const char* v = std::getenv("IMEX_LOG");
+  if (!v || std::strcmp(v, "1") != 0) return;
+  std::fprintf(stderr,
+               "{\"imex_setup\": \"%s\", \"dim\": %d, \"p\": %d, \"n_nodes\": %lld, \"n_d\": %lld, "
+               "\"n_c\": %lld, \"n_uncut\": %lld, \"n_cut\": %lld, \"n_empty\": %lld, \"components\": %d, "
+               "\"nnz_L\": %lld, \"max_block\": %d, \"dt\": %.17g, \"dt_crit_uncut\": %.17g, "
+               "\"dt_crit_cut_min\": %.17g, \"scheme\": %d, \"factorized\": %d, \"setup_seconds\": %.6f}\n",
+               where, hs.dim, hs.p, (long long)hs.nnodes, (long long)hs.n_d, (long long)hs.n_c,
+               (long long)hs.n_uncut, (long long)hs.n_cut, (long long)hs.n_empty, hs.ncomp, (long long)hs.nnz_L,
+               hs.max_block, hs.dt, hs.dt_crit_uncut, hs.dt_crit_cut_min, hs.pb.scheme, hs.pb.factorize ? 1 : 0,
+               hs.setup_seconds);
+}
+
+void fill_stats(const HostSetup& hs, imex_stats* st) {
   std::memset(st, 0, sizeof(*st));
   st->n_nodes = hs.nnodes;
   st->n_d = hs.n_d;
@@ -1916,6 +1931,7 @@ int imex_host_setup_export(const imex_mesh* mesh, int p, double alpha, double dt
     if (node_class) std::memcpy(node_class, hs.node_class.data(), hs.node_class.size());
     if (fx) std::memcpy(fx, hs.fx.data(), hs.fx.size() * sizeof(double));
     if (stats) fill_stats(hs, stats);
+    log_setup(hs, "host");
     return IMEX_OK;
   } catch (const std::exception& ex) {
     return fail(IMEX_ERR_ALLOC, std::string("host setup failed: ") + ex.what());
@@ -2363,6 +2379,7 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       imex_destroy(c);
       return fail(IMEX_ERR_CUDA, msg);
     }
+    log_setup(c->hs, "device");
     *out = c;
     return IMEX_OK;
   } catch (const std::exception& ex) {

@@ -188,3 +188,28 @@ def test_context_without_factorisation_restrictions():
             g.step_noalloc(1)
     with pytest.raises(ValueError):
         imex.Imex.from_workload(workloads.multisource(nsrc=2), ncols=2, factorize=False)
+
+
+def test_failing_allocator_is_reported():
+    # Fault injection on the host: an allocator hook that returns NULL.
+    import ctypes
+    imex = _imex()
+    kw = workloads.plate16().kwargs()
+    m, s, keep = imex._mesh_source(kw["dim"], kw["lo"], kw["hi"], kw["ncells"], kw["depth"], kw["holes"],
+                                   kw["rho"], kw["c0"], kw["cell_c"], kw["src_pos"], kw["f0"], kw["src_sigma"],
+                                   kw["src_amp"], kw["wavelet"])
+    calls = []
+
+    def alloc(nbytes, user):
+        calls.append(nbytes)
+        return None
+
+    def release(ptr, user):
+        pass
+
+    al = imex.Alloc(imex._ALLOC_FN(alloc), imex._RELEASE_FN(release), None)
+    ctx = ctypes.c_void_p()
+    rc = imex._lib.imex_setup_scheme(ctypes.byref(m), kw["p"], kw["alpha"], 0.0, ctypes.byref(s), 1, 0,
+                                     ctypes.byref(al), ctypes.byref(ctx))
+    assert rc == -3 and calls and not ctx.value   # IMEX_ERR_ALLOC, nothing returned
+    assert b"allocator" in imex._lib.imex_last_error()

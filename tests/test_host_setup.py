@@ -77,3 +77,25 @@ def test_host_setup_rejects_bad_arguments():
     kw["alpha"] = 0.0
     with pytest.raises(imex.ImexError):
         imex.host_setup_export(**kw)
+
+
+def test_setup_statistics_log_line():
+    # IMEX_LOG=1: one JSON line of setup statistics on stderr (a child process,
+    # so that the variable is read by a fresh library).
+    import json
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2310_14712_gb300 import imex, workloads\n"
+            "imex.host_setup_export(**workloads.plate16().kwargs())\n") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                       env=dict(os.environ, IMEX_LOG="1"), timeout=300)
+    assert r.returncode == 0, r.stderr
+    lines = [json.loads(l) for l in r.stderr.splitlines() if l.startswith('{"imex_setup"')]
+    assert len(lines) == 1
+    st = imex.host_setup_export(**workloads.plate16().kwargs())[2]
+    rec = lines[0]
+    assert rec["imex_setup"] == "host"
+    for k in ("n_d", "n_c", "n_cut", "n_uncut", "n_empty", "nnz_L"):
+        assert rec[k] == st[k], k
+    assert rec["dt"] == st["dt"] and rec["factorized"] == 1
