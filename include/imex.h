@@ -114,7 +114,9 @@ typedef struct {
   int64_t rhs_pairs;       /* (c-row, interface cell) pairs of K^c u: one P^d dot product each */
   int64_t ncols;           /* independent source columns (imex_setup_batch) */
   int64_t explicit_tile_cells;   /* cells per side of an explicit-apply tile (autotuned) */
-  double explicit_tile_us_large; /* setup timing of one explicit launch, larger tile (0: not timed) */
+  double explicit_tile_us_large; /* setup timing with the larger tile: one whole step (factorised
+                                    contexts with implicit DOFs) or one explicit launch (others);
+                                    0: not timed */
   double explicit_tile_us_small; /* the same, smaller tile */
   int64_t scheme;                /* IMEX_SCHEME_* of the context */
   double dt_crit_cut_min;        /* smallest cut-cell critical step for the scheme's mass

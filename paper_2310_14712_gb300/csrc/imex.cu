@@ -1952,9 +1952,16 @@ static_assert(IMEX_SCHEME_IMEX == kSchemeImex && IMEX_SCHEME_CDM == kSchemeCdm &
                   IMEX_SCHEME_CDM_HRZ == kSchemeCdmHrz && IMEX_SCHEME_TRAPEZOIDAL == kSchemeTrapezoidal,
               "scheme codes");
 
+static int autotune_tile_steps(imex_ctx* c);
+
 int imex_setup_scheme(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src, int ncols,
                       int scheme, const imex_alloc* alloc, imex_ctx** out) {
-  return setup_impl(mesh, p, alpha, dt, src, ncols, scheme, true, alloc, out);
+  int rc = setup_impl(mesh, p, alpha, dt, src, ncols, scheme, true, alloc, out);
+  if (rc == IMEX_OK && (rc = autotune_tile_steps(*out)) != IMEX_OK) {
+    imex_destroy(*out);
+    *out = nullptr;
+  }
+  return rc;
 }
 
 int imex_setup_pcg(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src, int scheme,
@@ -2455,6 +2462,76 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
   if (int rc = check_launch("imex_step")) return rc;
   c->cur = 1 - c->cur;
   c->step = step + 1;
+  return IMEX_OK;
+}
+
+// Tile choice of a factorised context with implicit DOFs, by whole steps: the
+// solve chain's first launch stages its constants while the tail of the
+// explicit kernel runs, so the tile that makes the explicit kernel fastest
+// alone is not the one that makes the step fastest (on the 256x128 plate,
+// p = 4: 8-cell tiles 80.8 us per step, 4-cell tiles 89.6, although the
+// 4-cell kernel alone can time faster).  Four steps with each tile after one
+// warm-up step; the state (both field buffers, v^c, a^c, the step counter) is
+// saved before and restored after.  IMEX_EXPLICIT_TILE = large | small keeps
+// the forced tile.
+static int autotune_tile_steps(imex_ctx* c) {
+  const HostSetup& hs = c->hs;
+  if (c->hetero || !c->factorized || hs.n_c == 0) return IMEX_OK;
+  const char* env = std::getenv("IMEX_EXPLICIT_TILE");
+  if (env && (std::string(env) == "large" || std::string(env) == "small")) return IMEX_OK;
+  const size_t nn = (size_t)hs.nnodes * c->ncols, ncv = (size_t)hs.n_c * c->ncols;
+  double* save = nullptr;
+  if (cudaMalloc(&save, (2 * nn + 2 * ncv) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IMEX_ERR_ALLOC, "tile tuning: device buffer");
+  }
+  double* const dst[4] = {save, save + nn, save + 2 * nn, save + 2 * nn + ncv};
+  double* const src[4] = {c->U[0], c->U[1], c->v_c, c->a_c};
+  const size_t len[4] = {nn, nn, ncv, ncv};
+  const int cur0 = c->cur;
+  const int64_t step0 = c->step;
+  auto copy_state = [&](bool to_save) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+      e = to_save ? cudaMemcpy(dst[k], src[k], len[k] * sizeof(double), cudaMemcpyDeviceToDevice)
+                  : cudaMemcpy(src[k], dst[k], len[k] * sizeof(double), cudaMemcpyDeviceToDevice);
+    c->cur = cur0;
+    c->step = step0;
+    return e;
+  };
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = copy_state(true);
+  e = e ? e : cudaEventCreate(&ev[0]);
+  e = e ? e : cudaEventCreate(&ev[1]);
+  float best = 1e30f;
+  bool best_small = c->tile_small != 0;
+  int rc = IMEX_OK;
+  for (int k = 0; k < 2 && e == cudaSuccess && rc == IMEX_OK; ++k) {
+    const bool small = k == 1;
+    e = use_tile(c, small);
+    e = e ? e : copy_state(false);
+    if (e != cudaSuccess) break;
+    rc = step_once(c, nullptr, nullptr);
+    e = cudaEventRecord(ev[0], nullptr);
+    for (int r = 0; r < 4 && rc == IMEX_OK && e == cudaSuccess; ++r) rc = step_once(c, nullptr, nullptr);
+    e = e ? e : cudaEventRecord(ev[1], nullptr);
+    e = e ? e : cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    e = e ? e : cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    c->tile_us[k] = 1e3f * ms / 4.f;
+    if (e == cudaSuccess && c->tile_us[k] < best) {
+      best = c->tile_us[k];
+      best_small = small;
+    }
+  }
+  if (ev[0]) cudaEventDestroy(ev[0]);
+  if (ev[1]) cudaEventDestroy(ev[1]);
+  e = e ? e : use_tile(c, best_small);
+  e = e ? e : copy_state(false);
+  e = e ? e : cudaDeviceSynchronize();
+  cudaFree(save);
+  if (rc != IMEX_OK) return rc;
+  if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("tile tuning: ") + cudaGetErrorString(e));
   return IMEX_OK;
 }
 
