@@ -248,7 +248,12 @@ int imex_step_profile(imex_ctx *ctx, int64_t n, void *stream, double *phase_ms);
  *   rec_nodes  : nrec canonical node indices (receivers), 0 <= nrec <= 4096
  *   traces     : n x ncols x nrec host array; entry (k, col, i) receives
  *                u_{n0+k+1} of column col at receiver i
- * Synchronous (returns when the traces are on the host).
+ * Every step copies its two samples in and its receiver values out; the
+ * copies run on two copy streams of the context, ordered by events against
+ * the steps on `stream` (ring buffers of 8 slots), so that the step kernels
+ * do not wait for them.  Pinned host arrays make the copies asynchronous;
+ * pageable ones work too.  Synchronous (returns when the traces are on the
+ * host); the host arrays must stay valid until then.
  * Errors: IMEX_ERR_ARG (bad sizes or node indices), IMEX_ERR_CUDA.
  */
 int imex_step_io(imex_ctx *ctx, int64_t n, const double *ft_samples, const int64_t *rec_nodes,

@@ -33,6 +33,7 @@ int fail(int code, const std::string& msg) {
 }
 
 constexpr int kThreads = 256;
+constexpr int kIoRing = 8;   // slots of the host-I/O rings (imex_step_io)
 constexpr int kWarps = kThreads / 32;
 
 #include "step_kernels.cuh"
@@ -675,10 +676,14 @@ struct imex_ctx {
   double *zA_S = nullptr, *zA_M = nullptr;
   int64_t nzrow = 0;
   double *upd = nullptr, *sol = nullptr;
-  // host I/O
+  // host I/O (imex_step_io): rings of kIoRing slots for the source samples
+  // (2 doubles each) and the receiver values (io_cap * ncols each), filled and
+  // drained on two copy streams, with events guarding slot reuse
   double *ft_buf = nullptr, *rec_buf = nullptr;
   int64_t* rec_nodes = nullptr;
   int io_cap = 4096;
+  cudaStream_t io_h2d = nullptr, io_d2h = nullptr;
+  cudaEvent_t io_ev[3][kIoRing] = {};   // [h2d done | step and gather done | d2h done][slot]
   // state
   int ncols = 1;            // independent source columns (fields column after column)
   // cell-by-cell K (per-cell wave speed; the adjoint)
@@ -2252,8 +2257,8 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       ar.add(&c->if_koff_dev, nf ? if_koff_h.size() : 1);
       ar.add(&c->if_sc_dev, nf ? plan.if_sc.size() : 1);
     }
-    ar.add(&c->ft_buf, 2);
-    ar.add(&c->rec_buf, (size_t)c->io_cap * ncols);
+    ar.add(&c->ft_buf, 2 * kIoRing);
+    ar.add(&c->rec_buf, (size_t)kIoRing * c->io_cap * ncols);
     ar.add(&c->rec_nodes, c->io_cap);
     c->bytes = ar.total();
     void* basep = nullptr;
@@ -2583,25 +2588,52 @@ int imex_step_io(imex_ctx* c, int64_t n, const double* ft_samples, const int64_t
   cudaStream_t s = (cudaStream_t)stream;
   c->stream = s;
   cudaError_t e = cudaSuccess;
+  // Copies run on two streams of their own so that the step kernels do not
+  // wait for them: the source samples of step k go into ring slot k % kIoRing
+  // ahead of the step (the slot is reused once step k - kIoRing has run), the
+  // receiver values of step k are gathered into a ring slot on the compute
+  // stream and copied out behind an event (the slot is reused once that copy
+  // is done).  Every step still copies its own inputs in and results out.
+  if (!c->io_h2d) {
+    e = cudaStreamCreateWithFlags(&c->io_h2d, cudaStreamNonBlocking);
+    e = e ? e : cudaStreamCreateWithFlags(&c->io_d2h, cudaStreamNonBlocking);
+    for (auto& row : c->io_ev)
+      for (cudaEvent_t& ev : row)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_step_io: ") + cudaGetErrorString(e));
+  }
   if (nrec > 0) e = cudaMemcpyAsync(c->rec_nodes, rec_nodes, nrec * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+  const size_t slot_len = (size_t)c->io_cap * c->ncols, rec_len = (size_t)nrec * c->ncols;
   for (int64_t k = 0; k < n && e == cudaSuccess; ++k) {
+    const int j = (int)(k % kIoRing);
     const double* ftd = nullptr;
     if (ft_samples) {
-      e = cudaMemcpyAsync(c->ft_buf, ft_samples + k, 2 * sizeof(double), cudaMemcpyHostToDevice, s);
+      if (k >= kIoRing) e = cudaStreamWaitEvent(c->io_h2d, c->io_ev[1][j], 0);
+      e = e ? e : cudaMemcpyAsync(c->ft_buf + 2 * j, ft_samples + k, 2 * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->io_h2d);
+      e = e ? e : cudaEventRecord(c->io_ev[0][j], c->io_h2d);
+      e = e ? e : cudaStreamWaitEvent(s, c->io_ev[0][j], 0);
       if (e != cudaSuccess) break;
-      ftd = c->ft_buf;
+      ftd = c->ft_buf + 2 * j;
     }
     if (int rc = step_once(c, s, nullptr, ftd)) return rc;
+    double* slot = c->rec_buf + (size_t)j * slot_len;
     if (nrec > 0) {
+      if (k >= kIoRing) e = cudaStreamWaitEvent(s, c->io_ev[2][j], 0);
       for (int col = 0; col < c->ncols; ++col)
-        k_gather_nodes<<<(nrec + 255) / 256, 256, 0, s>>>(c->rec_buf + (size_t)col * nrec,
+        k_gather_nodes<<<(nrec + 255) / 256, 256, 0, s>>>(slot + (size_t)col * nrec,
                                                           c->U[c->cur] + (size_t)col * c->hs.nnodes, c->rec_nodes, nrec);
-      e = cudaMemcpyAsync(traces + k * nrec * c->ncols, c->rec_buf, (size_t)nrec * c->ncols * sizeof(double),
-                          cudaMemcpyDeviceToHost, s);
     }
-    // ft_buf is rewritten by the next step's copy, which the stream orders
-    // after this step's kernels.
+    e = e ? e : cudaEventRecord(c->io_ev[1][j], s);
+    if (nrec > 0) {
+      e = e ? e : cudaStreamWaitEvent(c->io_d2h, c->io_ev[1][j], 0);
+      e = e ? e : cudaMemcpyAsync(traces + k * rec_len, slot, rec_len * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->io_d2h);
+      e = e ? e : cudaEventRecord(c->io_ev[2][j], c->io_d2h);
+    }
   }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->io_h2d);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->io_d2h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_step_io: ") + cudaGetErrorString(e));
   return IMEX_OK;
@@ -3012,6 +3044,11 @@ void imex_destroy(imex_ctx* c) {
   if (!c) return;
   if (c->base) {
     cudaDeviceSynchronize();
+    for (auto& row : c->io_ev)
+      for (cudaEvent_t& ev : row)
+        if (ev) cudaEventDestroy(ev);
+    if (c->io_h2d) cudaStreamDestroy(c->io_h2d);
+    if (c->io_d2h) cudaStreamDestroy(c->io_d2h);
     if (c->has_hooks) {
       if (c->hooks.release) c->hooks.release(c->base, c->hooks.user);
     } else {
