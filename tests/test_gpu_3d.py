@@ -68,3 +68,106 @@ def test_3d_tile_sizes_agree_bitwise(monkeypatch):
         out[tile] = (st["u"], info["explicit_tile_cells"])
     assert out["large"][1] != out["small"][1]
     assert np.array_equal(out["large"][0], out["small"][0])
+
+
+def test_voids3d_full_size_first_steps_sampled():
+    # The benchmarked solid at full size (64 x 64 x 32 cells, p = 3, 40 voids,
+    # 3.6 M nodes) in a context without a factorisation, against values the
+    # oracle computes node by node.  From the zero state an explicit node i
+    # (every cell around it uncut) has u_1 = dt^2/2 f_t(0) f_i / M_ii, and if the
+    # nodes of its cells are explicit too,
+    # u_2 = 2 u_1 + dt^2 (f_t(dt) f_i - (K u_1)_i) / M_ii,
+    # with K, M and f assembled from the oracle's element matrices of those
+    # cells alone.  Checked on every such node within 3 cells of the source.
+    import itertools
+    from oracle import sources
+    from oracle.discretize import Grid, uncut_critical_dt, uncut_element
+    from oracle.geometry import UNCUT, Holes
+    imex = _imex()
+    w = workloads.voids3d()
+    grid = Grid(w.lo, w.hi, w.ncells, w.p)
+    holes = Holes(w.holes, 3)
+    p, P = w.p, w.p + 1
+    nn = [n * p + 1 for n in w.ncells]
+    dt = 0.9 * uncut_critical_dt(p, grid.h, w.rho, w.c0)
+    fx = sources.bell(w.src_pos, w.src_sigma, w.src_amp)
+    ft = sources.wavelet(w.wavelet, w.f0)
+    cells = {}
+
+    def cell(ci):            # (node ids, K_e, diag M_e, f_e) of an uncut cell, None otherwise
+        if ci not in cells:
+            lo, hi = grid.cell_box(ci)
+            if holes.classify_box(lo, hi) != UNCUT:
+                cells[ci] = None
+            else:
+                Ke, Me, fe = uncut_element(p, grid.h, w.rho, w.c0, lo, fx)
+                cells[ci] = (grid.cell_nodes(ci), Ke, np.diag(Me), fe)
+        return cells[ci]
+
+    def cells_of(node):      # (cell index, local index) pairs of the cells around a node
+        idx = [node % nn[0], (node // nn[0]) % nn[1], node // (nn[0] * nn[1])]
+        per_axis = []
+        for k in range(3):
+            c, r = divmod(idx[k], p)
+            opts = [(c - 1, p), (c, 0)] if r == 0 else [(c, r)]
+            per_axis.append([(cc, ll) for cc, ll in opts if 0 <= cc < w.ncells[k]])
+        out = []
+        for (cx, lx), (cy, ly), (cz, lz) in itertools.product(*per_axis):
+            out.append(((cx, cy, cz), lx + P * ly + P * P * lz))
+        return out
+
+    def explicit(node):
+        return all(cell(ci) is not None for ci, _ in cells_of(node))
+
+    def f_and_m(node):
+        f = m = 0.0
+        for ci, l in cells_of(node):
+            _, _, md, fe = cell(ci)
+            f += fe[l]
+            m += md[l]
+        return f, m
+
+    u1 = {}
+
+    def u1_of(node):
+        if node not in u1:
+            f, m = f_and_m(node)
+            u1[node] = 0.5 * dt * dt * ft(0.0) * f / m
+        return u1[node]
+
+    src_cell = [int((w.src_pos[0][k] - w.lo[k]) / grid.h[k]) for k in range(3)]
+    lo_n = [max(0, (src_cell[k] - 3) * p) for k in range(3)]
+    hi_n = [min(nn[k] - 1, (src_cell[k] + 4) * p) for k in range(3)]
+    want1, want2 = {}, {}
+    for z in range(lo_n[2], hi_n[2] + 1):
+        for y in range(lo_n[1], hi_n[1] + 1):
+            for x in range(lo_n[0], hi_n[0] + 1):
+                i = x + nn[0] * (y + nn[1] * z)
+                if not explicit(i):
+                    continue
+                want1[i] = u1_of(i)
+                ring = set()
+                for ci, _ in cells_of(i):
+                    ring.update(int(j) for j in cell(ci)[0])
+                if not all(explicit(j) for j in ring):
+                    continue
+                f, m = f_and_m(i)
+                ku = 0.0
+                for ci, l in cells_of(i):
+                    ids, Ke, _, _ = cell(ci)
+                    ku += Ke[l] @ np.array([u1_of(int(j)) for j in ids])
+                want2[i] = 2.0 * u1_of(i) + dt * dt * (ft(dt) * f - ku) / m
+    assert len(want2) > 1000
+    with imex.Imex.from_workload(w, factorize=False) as g:
+        assert g.info()["dt"] == pytest.approx(dt, rel=1e-13)
+        g.step(1)
+        got1 = g.fields("u", out=np.zeros(g.n_nodes))
+        g.step(1)
+        got2 = g.fields("u", out=np.zeros(g.n_nodes))
+        assert g.pcg_status()["fallbacks"] == 0
+    for want, got in ((want1, got1), (want2, got2)):
+        ids = np.fromiter(want.keys(), dtype=np.int64)
+        ref = np.fromiter(want.values(), dtype=np.float64)
+        scale = np.abs(ref).max()
+        assert scale > 0
+        assert np.abs(got[ids] - ref).max() <= 1e-12 * scale, np.abs(got[ids] - ref).max() / scale
