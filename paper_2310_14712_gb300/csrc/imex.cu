@@ -664,7 +664,7 @@ struct imex_ctx {
   int walk_max_slots = 2, walk_max_m = 2, walk_max_pairs = 2;
   int* tlist = nullptr;
   int64_t *tlist_off = nullptr, *tlist_len = nullptr;
-  int top_max_zn = 2, top_max_chunk = 2;
+  int top_max_zn = 2;
   int64_t top_max_arows = 0;
   std::vector<int> lev_cta0, lev_ncta, lev_has_nodes;   // per walked level: CTA range
   int walk_smem_mode = 0;
@@ -989,7 +989,6 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   z.zA = use_S ? c->zA_S : c->zA_M;
   z.max_zn = c->top_max_zn;
   z.max_arows = c->top_max_arows;
-  z.max_chunk = c->top_max_chunk;
   z.ilist = c->tlist;
   z.ilist_off = c->tlist_off;
   z.ilist_len = c->tlist_len;
@@ -1210,7 +1209,6 @@ struct SolvePlan {
   std::vector<int> tlist;
   std::vector<int64_t> tlist_off, tlist_len;
   int64_t max_tlist = 0, max_arows = 0;
-  int max_chunk = 2;
   std::vector<int> zsize, zbase, zrow, zfwd_ptr, zfwd_pos;
   std::vector<int64_t> zA_off;
   std::vector<double> zA_S, zA_M;
@@ -1651,8 +1649,8 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
   int64_t zwork = 0;
   for (int k = 0; k < hs.ncomp; ++k) zwork += (int64_t)zsize[k] * zsize[k];
   std::vector<int> chunk_of(hs.ncomp, 2);
-  auto top_smem = [&](int64_t rows, int ch) {
-    return (size_t)(max_zn_even + rows + (rows & 1) + ch) * sizeof(double) + (size_t)P.max_tlist * sizeof(int);
+  auto top_smem = [&](int64_t rows, int) {
+    return (size_t)(max_zn_even + rows + (rows & 1) + kThreads) * sizeof(double) + (size_t)P.max_tlist * sizeof(int);
   };
   for (int64_t wcta = std::max<int64_t>(1, zwork / kTargetCTAs);; wcta += wcta / 8 + 1) {
     int64_t nctas = 0;
@@ -1683,7 +1681,6 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
       P.tlist_len.push_back((int64_t)tl[k].size());
       const int64_t rows = (int64_t)(r1 - r0) * zsize[k];
       P.max_arows = std::max<int64_t>(P.max_arows, rows + (rows & 1));
-      P.max_chunk = std::max(P.max_chunk, (r1 - r0) + ((r1 - r0) & 1));
     }
   P.zsize = zsize;
   P.zbase = zbase;
@@ -1691,6 +1688,18 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
   P.zfwd_ptr = zfwd_ptr;
   P.zfwd_pos = zfwd_pos;
   P.zA_off = zA_off;
+  // Each CTA's chunk of rows [r0, r1) of A_Z^{-1} column-major in place (the
+  // kernel's column slices read consecutive words); the check above used the
+  // row-major form.
+  for (size_t q = 0; q < P.top_comp.size(); ++q) {
+    const int k = P.top_comp[q], zn = zsize[k], r0 = P.top_r0[q], nr = P.top_r1[q] - r0;
+    const int64_t off = zA_off[k] + (int64_t)r0 * zn;
+    for (std::vector<double>* A : {&zA_S, &zA_M}) {
+      std::vector<double> blk(A->begin() + off, A->begin() + off + (int64_t)nr * zn);
+      for (int i = 0; i < nr; ++i)
+        for (int j = 0; j < zn; ++j) (*A)[off + (int64_t)j * nr + i] = blk[(size_t)i * zn + j];
+    }
+  }
   for (int k = 0; k < 2; ++k) { zA_S.push_back(0.0); zA_M.push_back(0.0); }   // tail of the last 16-byte copy
   P.zA_S = std::move(zA_S);
   P.zA_M = std::move(zA_M);
@@ -2158,8 +2167,7 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       c->lev_has_nodes = plan.lev_has_nodes;
       c->top_max_zn = std::max(2, plan.max_zn + (plan.max_zn & 1));
       c->top_max_arows = plan.max_arows;
-      c->top_max_chunk = plan.max_chunk;
-      c->smem_top = (size_t)(c->top_max_zn + plan.max_arows + plan.max_chunk) * sizeof(double) +
+      c->smem_top = (size_t)(c->top_max_zn + plan.max_arows + kThreads) * sizeof(double) +
                     (size_t)plan.max_tlist * sizeof(int);
       if (c->smem_walk > kMaxDynSmem || c->smem_top > kMaxDynSmem) {
         delete c;

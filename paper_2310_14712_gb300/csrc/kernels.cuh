@@ -143,11 +143,10 @@ struct TopArgs {
   const int* zsize;             // [comp] |Z|
   const int* zbase;             // [comp] offset into zrow
   const int* zrow;              // c-index of each Z row
-  const int64_t* zA_off;        // [comp] offset of A_Z (row-major |Z| x |Z|, 16-byte aligned)
+  const int64_t* zA_off;        // [comp] offset of A_Z (|Z| x |Z|, 16-byte aligned; each CTA's chunk of rows column-major)
   const double* zA;
   int max_zn;                   // even
   int64_t max_arows;            // even: largest (r1 - r0) * |Z| over the CTAs
-  int max_chunk;                // even: largest r1 - r0 (<= threads per CTA)
   const int* skip;              // if set and *skip != 0: the launch does nothing (PCG converged)
   const int* ilist;             // per component: per Z row {update begin, update end}, then positions
   const int64_t* ilist_off;     // [cta]

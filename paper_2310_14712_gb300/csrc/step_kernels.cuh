@@ -586,6 +586,19 @@ struct Corr {
     }
     a_c[r] = acc;
   }
+  // The same with U[node] (u_in) and, in mode 3, Un[node] (un_in) loaded too.
+  __device__ void row_in(int r, double acc, double v_old, double a_old, int node, double u_in,
+                         double un_in) const {
+    if (mode == 2) return;
+    if (mode == 3) {
+      U[node] = 2.0 * un_in - u_in + dt * dt * acc;
+    } else if (mode == 0) {
+      const double vpred = v_old + (1.0 - kNewmarkGamma) * dt * a_old;
+      U[node] = u_in + kNewmarkBeta * dt * dt * acc;
+      v_c[r] = vpred + kNewmarkGamma * dt * acc;
+    }
+    a_c[r] = acc;
+  }
 };
 
 // Per-CTA index list of a walk launch (ints, offsets relative to its start):
@@ -814,7 +827,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
 __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   extern __shared__ __align__(16) double tsm[];
   const int cta = blockIdx.x, tid = threadIdx.x;
-  const int warp = tid / 32, lane = tid % 32;
   // Column of an independent-columns context (blockIdx.y).
   const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
   const double* rhs0 = a.rhs0 + oc;
@@ -825,10 +837,17 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   const int zn = a.zsize[comp], zb = a.zbase[comp], nr = r1 - r0;
   double* zs = tsm;                               // max_zn (even): right-hand side of the block
   double* Ac = zs + a.max_zn;                     // max_arows: this CTA's rows of A_Z
-  double* xs = Ac + a.max_arows;                  // max_chunk: this CTA's results
-  int* il = reinterpret_cast<int*>(xs + a.max_chunk);  // per row {update begin, update end}
+  double* xs = Ac + a.max_arows;                  // kThreads: partial dot products
+  int* il = reinterpret_cast<int*>(xs + kThreads);  // per row {update begin, update end}, positions
   async_copy_16(Ac, a.zA + a.zA_off[comp] + (size_t)r0 * zn, ((int64_t)nr * zn + 1) / 2);
   async_copy_16(il, a.ilist + a.ilist_off[cta], a.ilist_len[cta] / 4);
+  // c-index of this thread's first kZr rows of the block (registers: the
+  // shared memory of this kernel is kept small enough to share an SM with
+  // the walk launches that run before it).
+  constexpr int kZr = 3;
+  int zr[kZr];
+#pragma unroll
+  for (int q = 0; q < kZr; ++q) zr[q] = tid + q * kThreads < zn ? a.zrow[zb + tid + q * kThreads] : 0;
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   // The correction state of this thread's row (nr <= blockDim.x); not written
   // by the launches of the step that run before this one.
@@ -843,36 +862,50 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   async_copy_wait();
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
   if (a.skip && *a.skip) return;   // the iterative solve converged: nothing to do
+  // Inputs of the correction written by the earlier launches of the step,
+  // loaded now so that their latency overlaps the gather.
+  double u_in = 0.0, un_in = 0.0;
+  if (tid < nr && cor.mode != 2) {
+    u_in = __ldcg(cor.U + node);
+    if (cor.mode == 3) un_in = __ldcg(cor.Un + node);
+  }
   // The whole right-hand side of this component's top block (redundant per CTA).
-  for (int i = tid; i < zn; i += kThreads) {
+  auto gather = [&](int i, int zri) {
     const int fb = il[2 * i], fe = il[2 * i + 1];
-    double v = __ldcg(rhs0 + a.zrow[zb + i]);
+    double v = __ldcg(rhs0 + zri);
 #pragma unroll 4
     for (int k = fb; k < fe; ++k) v -= __ldcg(upd + il[k]);
     zs[i] = v;
-  }
-  __syncthreads();
-  for (int i = warp; i < nr; i += kWarps) {
-    const double* Ar = Ac + (size_t)i * zn;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int j = lane;
-    for (; j + 96 < zn; j += 128) {
-      s0 = fma(Ar[j], zs[j], s0);
-      s1 = fma(Ar[j + 32], zs[j + 32], s1);
-      s2 = fma(Ar[j + 64], zs[j + 64], s2);
-      s3 = fma(Ar[j + 96], zs[j + 96], s3);
-    }
-    for (; j < zn; j += 32) s0 = fma(Ar[j], zs[j], s0);
-    double v = (s0 + s1) + (s2 + s3);
+  };
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) xs[i] = v;
+  for (int q = 0; q < kZr; ++q)
+    if (tid + q * kThreads < zn) gather(tid + q * kThreads, zr[q]);
+  for (int i = tid + kZr * kThreads; i < zn; i += kThreads) gather(i, a.zrow[zb + i]);
+  __syncthreads();
+  // Rows of A_Z^{-1} times z. The chunk is stored column-major (row i, column
+  // j at j * nr + i); thread (s, i) takes row i over the s-th of S column
+  // slices, so a warp reads consecutive words and the FP64 pipe does no
+  // reduction work beyond S - 1 additions per row.
+  const int nslice = min(kThreads / max(nr, 1), max(zn, 1));
+  if (tid < nslice * nr) {
+    const int s = tid / nr, i = tid - s * nr;
+    const int j0 = zn * s / nslice, j1 = zn * (s + 1) / nslice;
+    const double* Ai = Ac + i;
+    double s0 = 0.0, s1 = 0.0;
+    int j = j0;
+    for (; j + 2 <= j1; j += 2) {
+      s0 = fma(Ai[(size_t)j * nr], zs[j], s0);
+      s1 = fma(Ai[(size_t)(j + 1) * nr], zs[j + 1], s1);
+    }
+    if (j < j1) s0 = fma(Ai[(size_t)j * nr], zs[j], s0);
+    xs[tid] = s0 + s1;
   }
   __syncthreads();
   if (tid < nr) {
-    const double x = xs[tid];
+    double x = xs[tid];
+    for (int q = 1; q < nslice; ++q) x += xs[q * nr + tid];
     sol[row] = x;
-    cor.row_pre(row, x, node, v_old, a_old);
+    cor.row_in(row, x, v_old, a_old, node, u_in, un_in);
   }
 }
 
