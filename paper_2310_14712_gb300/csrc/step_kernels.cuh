@@ -884,9 +884,9 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   __syncthreads();
   // Rows of A_Z^{-1} times z. The chunk is stored column-major (row i, column
   // j at j * nr + i); thread (s, i) takes row i over the s-th of S column
-  // slices, so a warp reads consecutive words and the FP64 pipe does no
-  // reduction work beyond S - 1 additions per row.
-  const int nslice = min(kThreads / max(nr, 1), max(zn, 1));
+  // slices, so a warp reads consecutive words, and the slices are summed
+  // pairwise (S - 1 additions per row, spread over the threads).
+  const int nslice = min(kThreads / max(nr, 1), max(zn / 2, 1));
   if (tid < nslice * nr) {
     const int s = tid / nr, i = tid - s * nr;
     const int j0 = zn * s / nslice, j1 = zn * (s + 1) / nslice;
@@ -901,9 +901,14 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
     xs[tid] = s0 + s1;
   }
   __syncthreads();
+  for (int h = nslice; h > 1;) {
+    const int h2 = (h + 1) / 2;   // slice s < h - h2 takes in slice s + h2
+    if (tid < (h - h2) * nr) xs[tid] += xs[tid + h2 * nr];
+    h = h2;
+    __syncthreads();
+  }
   if (tid < nr) {
-    double x = xs[tid];
-    for (int q = 1; q < nslice; ++q) x += xs[q * nr + tid];
+    const double x = xs[tid];
     sol[row] = x;
     cor.row_in(row, x, v_old, a_old, node, u_in, un_in);
   }
