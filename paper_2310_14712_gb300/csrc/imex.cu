@@ -1688,7 +1688,7 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
   P.zfwd_ptr = zfwd_ptr;
   P.zfwd_pos = zfwd_pos;
   P.zA_off = zA_off;
-  // Each CTA's chunk of rows [r0, r1) of A_Z^{-1} column-major in place (the
+  // Each CTA's chunk of rows [r0, r1) of A_Z column-major in place (the
   // kernel's column slices read consecutive words); the check above used the
   // row-major form.
   for (size_t q = 0; q < P.top_comp.size(); ++q) {

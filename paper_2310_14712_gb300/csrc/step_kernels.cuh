@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
     if (tid + q * kThreads < zn) gather(tid + q * kThreads, zr[q]);
   for (int i = tid + kZr * kThreads; i < zn; i += kThreads) gather(i, a.zrow[zb + i]);
   __syncthreads();
-  // Rows of A_Z^{-1} times z. The chunk is stored column-major (row i, column
+  // Rows of A_Z times z.  The chunk is stored column-major (row i, column
   // j at j * nr + i); thread (s, i) takes row i over the s-th of S column
   // slices, so a warp reads consecutive words, and the slices are summed
   // pairwise (S - 1 additions per row, spread over the threads).
