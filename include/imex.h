@@ -113,7 +113,8 @@ typedef struct {
   int64_t launches_per_step; /* kernel launches of one imex_step step */
   int64_t rhs_pairs;       /* (c-row, interface cell) pairs of K^c u: one P^d dot product each */
   int64_t ncols;           /* independent source columns (imex_setup_batch) */
-  int64_t explicit_tile_cells;   /* cells per side of an explicit-apply tile (autotuned) */
+  int64_t explicit_tile_cells;   /* cells per side of an explicit-apply tile, or strip width of the
+                                    sweep (autotuned) */
   double explicit_tile_us_large; /* setup timing with the larger tile: one whole step (factorised
                                     contexts with implicit DOFs) or one explicit launch (others);
                                     0: not timed */
@@ -122,6 +123,11 @@ typedef struct {
   double dt_crit_cut_min;        /* smallest cut-cell critical step for the scheme's mass
                                     (central-difference schemes; 0 otherwise) */
   int64_t factorized;            /* 1: factorised implicit solve available; 0: imex_setup_pcg */
+  int64_t explicit_variant;      /* explicit apply in use: 0 larger tiles, 1 smaller tiles,
+                                    2 persistent strip sweep, 3 the sweep in shorter chunks with
+                                    more CTAs per SM (2D; autotuned at setup) */
+  double explicit_sweep_us;      /* setup timing of variant 2 (as the tile timings) */
+  double explicit_sweep_short_us;/* setup timing of variant 3 */
 } imex_stats;
 
 /*
@@ -262,12 +268,22 @@ int imex_step_io(imex_ctx *ctx, int64_t n, const double *ft_samples, const int64
 /*
  * imex_step_noalloc - the same n steps as imex_step(), for callers that must
  * not allocate device memory while they run: it makes no allocation of any
- * kind, and the scratch of the implicit solve (update vectors and the
- * solution vector) is not taken from the
- * context but from one fixed 2 MiB array (262,144 doubles) compiled into the
- * library, which every GPU that loads the library keeps until the process
- * exits.  Typical callers run under a device-memory budget fixed at start-up
- * or inside code regions where allocation calls are not permitted.
+ * kind.  The scratch of the factorised implicit solve (the descendant update
+ * vectors, the solution vector and the right-hand sides, each column after
+ * column) is not taken from the context but from one fixed 2 MiB array
+ * (262,144 doubles) compiled into the library, which every GPU that loads
+ * the library keeps until the process exits.  Typical callers run under a
+ * device-memory budget fixed at start-up or inside code regions where
+ * allocation calls are not permitted.
+ *   - Capacity: with U = the context's update-vector length and n_c its
+ *     implicit DOFs, each rounded up to even, a problem fits when
+ *     (U + 2 n_c) x ncols <= 262,144; larger problems are rejected with
+ *     IMEX_ERR_ARG before anything is launched.
+ *   - Contexts only: factorised (not imex_setup_pcg) and with the direct
+ *     solver (imex_set_solver: IMEX_SOLVER_DIRECT, the default); the PCG
+ *     solvers keep their vectors in context memory, so a context set to
+ *     PCG is rejected with IMEX_ERR_ARG (use imex_step).  Every scheme
+ *     (imex_setup_scheme) and every column count is accepted.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
@@ -275,8 +291,7 @@ int imex_step_io(imex_ctx *ctx, int64_t n, const double *ft_samples, const int64
  *     Nothing in it needs to start at zero: each entry is written before it
  *     is read within a step.  Calls that overlap on the GPU (other streams,
  *     other contexts, at the same time) race on the array.
- *   - Problems whose solve needs more scratch than the array holds are
- *     rejected with IMEX_ERR_ARG before anything is launched.
+ * Results are bit-identical to imex_step() on the same context state.
  * No counterpart in the paper: this is an interface choice of the library.
  */
 int imex_step_noalloc(imex_ctx *ctx, int64_t n, void *stream);
@@ -390,6 +405,22 @@ int imex_info(imex_ctx *ctx, imex_stats *out);
  * else IMEX_OK.  max_abs_u may be NULL.
  */
 int imex_check_finite(imex_ctx *ctx, double *max_abs_u);
+
+/*
+ * imex_probe_fp64 - throughput of the current device's FP64 pipe, the
+ * denominator of the roofline of the FP64-bound step kernels (no counterpart
+ * in the paper; a measurement helper).  One launch of 4 x SMs CTAs x 256
+ * threads, each thread running eight independent chains of `iters`
+ * instructions of one kind: 0 fused multiply-add, 1 add, 2 multiply (runtime
+ * operands, values kept in normal range), timed with CUDA events after a
+ * warm-up launch on the legacy default stream (synchronises the device).
+ *   lane_ops_per_s : receives thread-level instructions per second (an FMA
+ *                    counts as one; 2 flops)
+ *   seconds        : receives the timed launch's duration (may be NULL)
+ * Errors: IMEX_ERR_ARG (kind, iters < 1, NULL output), IMEX_ERR_ALLOC,
+ * IMEX_ERR_CUDA.
+ */
+int imex_probe_fp64(int kind, int iters, double *lane_ops_per_s, double *seconds);
 
 /* imex_last_error - message of the calling thread's last failure ("" if none). */
 const char *imex_last_error(void);

@@ -2,8 +2,8 @@
 
     python -m paper_2310_14712_gb300.build [-v] [--ptxas-info]
 
-Two translation units are compiled in parallel (g++ for the host setup, nvcc
-for the kernels and the C-ABI) and linked with nvcc into
+Three translation units are compiled in parallel (g++ for the host setup,
+nvcc for the step kernels with the C-ABI and for the FP64 pipe probe) and linked with nvcc into
 paper_2310_14712_gb300/libimex.so.  Object files go to
 paper_2310_14712_gb300/_build/.  No GPU is needed to build.
 """
@@ -41,22 +41,25 @@ def build(verbose=False, ptxas_info=False):
           os.path.join(CSRC, "imex.cu"), "-o", os.path.join(OUT, "imex.o")]
     if ptxas_info:
         cu.insert(1, "-Xptxas=-v")
+    probe = [nvcc, *ARCH, "-lineinfo", *common, "-Xcompiler", "-fPIC", "-c",
+             os.path.join(CSRC, "probe.cu"), "-o", os.path.join(OUT, "probe.o")]
     cpp = ["g++", *common, "-fPIC", "-pthread", "-Wall", "-Wno-unused-variable", "-c",
            os.path.join(CSRC, "setup.cpp"), "-o", os.path.join(OUT, "setup.o")]
     results = {}
     threads = [threading.Thread(target=_run, args=(cmd, results, k, verbose))
-               for k, cmd in (("cu", cu), ("cpp", cpp))]
+               for k, cmd in (("cu", cu), ("probe", probe), ("cpp", cpp))]
     for t in threads:
         t.start()
     for t in threads:
         t.join()
-    for k in ("cu", "cpp"):
+    for k in ("cu", "probe", "cpp"):
         r = results[k]
         if r.returncode != 0 or (verbose and (r.stdout or r.stderr)) or (ptxas_info and k == "cu"):
             sys.stderr.write(r.stdout + r.stderr)
         if r.returncode != 0:
             raise RuntimeError(f"compilation of {k} failed")
-    link = [nvcc, *ARCH, "-shared", os.path.join(OUT, "imex.o"), os.path.join(OUT, "setup.o"),
+    link = [nvcc, *ARCH, "-shared", os.path.join(OUT, "imex.o"), os.path.join(OUT, "probe.o"),
+            os.path.join(OUT, "setup.o"),
             "-o", LIB + ".tmp", "-lpthread"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:

@@ -609,12 +609,22 @@ __global__ void k_gather_nodes(double* out, const double* u, const int64_t* node
   if (k < n) out[k] = u[nodes[k]];
 }
 
-// Explicit-apply tile sizes (cells per tile side): two candidates per order,
-// the larger (less halo work) and half of it (finer load balance on small
-// grids); setup times both and keeps the faster (IMEX_EXPLICIT_TILE =
-// large | small overrides).
+// Explicit-apply variants, the candidates of the setup autotuner (the
+// environment variable IMEX_EXPLICIT_TILE = large | small | sweep fixes one):
+//   0 tiles of kTileLarge[P] cells per side (less halo work),
+//   1 tiles of kTileSmall[P] (finer load balance on small grids),
+//   2 (2D) the persistent strip sweep, strips of kSweepCells[P] cells and
+//     chunks of as many cell rows, up to kSweepMinBlocks[0][P] CTAs per SM.
 constexpr int kTileLarge[10] = {0, 0, 16, 16, 10, 8, 6, 5, 4, 4};
 constexpr int kTileSmall[10] = {0, 0, 8, 8, 5, 4, 3, 3, 2, 2};
+constexpr int kSweepCells[10] = {0, 0, 32, 16, 10, 8, 6, 5, 4, 4};
+//   3 (2D) the same strips in chunks of half as many cell rows, with more
+//     resident CTAs per SM (kSweepMinBlocks[1][P]).
+constexpr int kSweepMinBlocks[2][10] = {{0, 0, 3, 3, 3, 3, 2, 2, 2, 1}, {0, 0, 4, 4, 4, 4, 3, 3, 3, 2}};
+constexpr int kExplicitSweep = 2, kExplicitSweepShort = 3;
+const char* const kExplicitNames[4] = {"large", "small", "sweep", "sweep_short"};
+template <int P>
+constexpr int sweep_chunk(int short_chunks) { return short_chunks ? (kSweepCells[P] + 1) / 2 : kSweepCells[P]; }
 // 3D (P <= 5): tiles of TC^3 cells.
 constexpr int kTileLarge3[6] = {0, 0, 8, 4, 3, 3};
 constexpr int kTileSmall3[6] = {0, 0, 4, 2, 2, 2};
@@ -721,8 +731,8 @@ struct imex_ctx {
   Ops2D ops{};
   int TC = 4, ntx = 1, nty = 1, ntz = 1;
   Ops3D ops3{};
-  int tile_small = 0;             // explicit tile: 0 large, 1 small (autotuned at setup)
-  float tile_us[2] = {0.f, 0.f};  // measured explicit launch time of each candidate
+  int xvar = 0;                   // explicit variant: 0 large tile, 1 small tile, 2/3 sweep (autotuned)
+  float tile_us[4] = {0.f, 0.f, 0.f, 0.f};  // measured time of each candidate (0: not timed)
   int explicit_per_sm = 1;    // resident CTAs of the explicit kernel per SM
   int num_sms = 152;
   size_t smem_explicit = 0;
@@ -755,7 +765,13 @@ int check_launch(const char* what) {
 
 template <int P>
 void launch_explicit(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t s) {
-  if (c->tile_small)
+  if (c->xvar == kExplicitSweep)
+    k_sweep2d<P, kSweepCells[P], sweep_chunk<P>(0), kSweepMinBlocks[0][P]>
+        <<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
+  else if (c->xvar == kExplicitSweepShort)
+    k_sweep2d<P, kSweepCells[P], sweep_chunk<P>(1), kSweepMinBlocks[1][P]>
+        <<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
+  else if (c->xvar == 1)
     k_explicit2d<P, kTileSmall[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
   else
     k_explicit2d<P, kTileLarge[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
@@ -763,7 +779,7 @@ void launch_explicit(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t
 
 template <int P>
 void launch_explicit3(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t s) {
-  if (c->tile_small)
+  if (c->xvar == 1)
     k_explicit3d<P, kTileSmall3[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops3);
   else
     k_explicit3d<P, kTileLarge3[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops3);
@@ -822,20 +838,23 @@ void explicit_dispatch(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream
 
 // Shared-memory attribute and resident CTAs per SM of the explicit kernel.
 template <int P>
-cudaError_t explicit_config(bool small, size_t bytes, int* per_sm) {
-  auto fn = small ? k_explicit2d<P, kTileSmall[P]> : k_explicit2d<P, kTileLarge[P]>;
+cudaError_t explicit_config(int var, size_t bytes, int* per_sm) {
+  auto fn = var == kExplicitSweep      ? k_sweep2d<P, kSweepCells[P], sweep_chunk<P>(0), kSweepMinBlocks[0][P]>
+            : var == kExplicitSweepShort ? k_sweep2d<P, kSweepCells[P], sweep_chunk<P>(1), kSweepMinBlocks[1][P]>
+            : var == 1                   ? k_explicit2d<P, kTileSmall[P]>
+                                         : k_explicit2d<P, kTileLarge[P]>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kThreads, bytes);
 }
 
 template <int P>
-cudaError_t explicit_config3(bool small, size_t bytes, int* per_sm) {
-  auto fn = small ? k_explicit3d<P, kTileSmall3[P]> : k_explicit3d<P, kTileLarge3[P]>;
+cudaError_t explicit_config3(int var, size_t bytes, int* per_sm) {
+  auto fn = var == 1 ? k_explicit3d<P, kTileSmall3[P]> : k_explicit3d<P, kTileLarge3[P]>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kThreads, bytes);
 }
 
-cudaError_t explicit_config_dispatch(int dim, int P, bool small, size_t bytes, int* per_sm) {
+cudaError_t explicit_config_dispatch(int dim, int P, int small, size_t bytes, int* per_sm) {
   if (dim == 3) {
     switch (P) {
       case 2: return explicit_config3<2>(small, bytes, per_sm);
@@ -858,21 +877,70 @@ cudaError_t explicit_config_dispatch(int dim, int P, bool small, size_t bytes, i
   return cudaErrorInvalidValue;
 }
 
-// Select a tile size: tile counts, shared memory and occupancy follow it.
-cudaError_t use_tile(imex_ctx* c, bool small) {
+// Shared memory (doubles) of the sweep kernel of order P (SweepShape).
+size_t sweep_smem_doubles(int P, int short_chunks) {
+  switch (P) {
+#define IMEX_SWEEP_SHAPE(PP)                                                                           \
+  case PP:                                                                                             \
+    return short_chunks ? SweepShape<PP, kSweepCells[PP], sweep_chunk<PP>(1)>::DOUBLES                 \
+                        : SweepShape<PP, kSweepCells[PP], sweep_chunk<PP>(0)>::DOUBLES;
+    IMEX_SWEEP_SHAPE(2) IMEX_SWEEP_SHAPE(3) IMEX_SWEEP_SHAPE(4) IMEX_SWEEP_SHAPE(5)
+    IMEX_SWEEP_SHAPE(6) IMEX_SWEEP_SHAPE(7) IMEX_SWEEP_SHAPE(8) IMEX_SWEEP_SHAPE(9)
+#undef IMEX_SWEEP_SHAPE
+  }
+  return 0;
+}
+
+// Number of explicit variants of a context: tiles (large, small) and, in 2D,
+// the sweep.
+int explicit_variants(const imex_ctx* c) { return c->hs.dim == 3 ? 2 : 4; }
+
+// Select an explicit variant: tile counts (for the sweep: ntx = its CTAs),
+// shared memory and occupancy follow it.
+cudaError_t use_explicit(imex_ctx* c, int var) {
   const HostSetup& hs = c->hs;
-  c->tile_small = small ? 1 : 0;
   const bool d3 = hs.dim == 3;
-  c->TC = d3 ? (small ? kTileSmall3[hs.P] : kTileLarge3[hs.P]) : (small ? kTileSmall[hs.P] : kTileLarge[hs.P]);
-  const int OX = c->TC * hs.p;
-  c->ntx = (hs.nn[0] + OX - 1) / OX;
-  c->nty = (hs.nn[1] + OX - 1) / OX;
-  c->ntz = d3 ? (hs.nn[2] + OX - 1) / OX : 1;
-  c->smem_explicit = (d3 ? explicit_smem_doubles3(hs.P, c->TC) : explicit_smem_doubles(hs.P, c->TC)) * sizeof(double);
+  if (var < 0 || var >= explicit_variants(c)) var = 0;
+  c->xvar = var;
+  if (var == kExplicitSweep || var == kExplicitSweepShort) {
+    c->TC = kSweepCells[hs.P];
+    c->nty = c->ntz = 1;
+    c->smem_explicit = sweep_smem_doubles(hs.P, var == kExplicitSweepShort) * sizeof(double);
+    int per_sm = 0;
+    cudaError_t e = explicit_config_dispatch(hs.dim, hs.P, var, c->smem_explicit, &per_sm);
+    c->explicit_per_sm = std::max(1, per_sm);
+    // As many sweep CTAs as are resident at once (up to three per SM), never
+    // more than work units; IMEX_SWEEP_CTAS = n fixes the number (tests:
+    // segments that cross strip boundaries on small grids).
+    const int64_t units = (int64_t)((hs.pb.ncells[0] + c->TC - 1) / c->TC) * hs.pb.ncells[1];
+    int64_t n = std::min<int64_t>(units, (int64_t)std::max(1, c->num_sms) *
+                                             std::min(kSweepMinBlocks[var - kExplicitSweep][hs.P], c->explicit_per_sm));
+    if (const char* env = std::getenv("IMEX_SWEEP_CTAS")) n = std::min<int64_t>(units, std::atoll(env));
+    c->ntx = (int)std::max<int64_t>(1, n);
+    return e;
+  } else {
+    const bool small = var == 1;
+    c->TC = d3 ? (small ? kTileSmall3[hs.P] : kTileLarge3[hs.P]) : (small ? kTileSmall[hs.P] : kTileLarge[hs.P]);
+    const int OX = c->TC * hs.p;
+    c->ntx = (hs.nn[0] + OX - 1) / OX;
+    c->nty = (hs.nn[1] + OX - 1) / OX;
+    c->ntz = d3 ? (hs.nn[2] + OX - 1) / OX : 1;
+    c->smem_explicit =
+        (d3 ? explicit_smem_doubles3(hs.P, c->TC) : explicit_smem_doubles(hs.P, c->TC)) * sizeof(double);
+  }
   int per_sm = 0;
-  cudaError_t e = explicit_config_dispatch(hs.dim, hs.P, small, c->smem_explicit, &per_sm);
+  cudaError_t e = explicit_config_dispatch(hs.dim, hs.P, var, c->smem_explicit, &per_sm);
   c->explicit_per_sm = std::max(1, per_sm);
   return e;
+}
+
+// Index of the variant named by IMEX_EXPLICIT_TILE, or -1.
+int explicit_env_variant(const imex_ctx* c) {
+  const char* env = std::getenv("IMEX_EXPLICIT_TILE");
+  if (!env) return -1;
+  for (int k = 0; k < explicit_variants(c); ++k)
+    if (std::string(env) == kExplicitNames[k]) return k;
+  return -1;
 }
 
 ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double* OUT, double cu, double cw,
@@ -917,6 +985,7 @@ ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double
 // SMs.  At least one, at most one per 256 rows.
 int pred_blocks(imex_ctx* c, bool predict) {
   if (!predict || c->hs.n_c == 0) return 0;
+  if (c->xvar >= kExplicitSweep) return 0;   // the sweep CTAs predict their share themselves
   const int64_t tiles = (int64_t)ntiles(c);
   const int64_t nsm = std::max(1, c->num_sms);
   const int64_t per_sm = std::min<int64_t>((tiles + nsm - 1) / nsm, std::max(1, c->explicit_per_sm));
@@ -1053,23 +1122,20 @@ int64_t launches_per_step(const imex_ctx* c) {
   return n;
 }
 
-// The autotuner of the explicit tile: time both tile sizes on this problem
+// The autotuner of the explicit variant: time every candidate on this problem
 // (one warm-up and five timed launches each, over all columns, writing into
-// the scratch grid) and keep the faster.  IMEX_EXPLICIT_TILE=large|small in
-// the environment fixes the choice instead.
+// the scratch grid) and keep the fastest.  IMEX_EXPLICIT_TILE = large |
+// small | sweep in the environment fixes the choice instead.
 cudaError_t autotune_tile(imex_ctx* c) {
   const HostSetup& hs = c->hs;
-  const char* env = std::getenv("IMEX_EXPLICIT_TILE");
-  if (env && std::string(env) == "large") return use_tile(c, false);
-  if (env && std::string(env) == "small") return use_tile(c, true);
+  if (int v = explicit_env_variant(c); v >= 0) return use_explicit(c, v);
   cudaEvent_t ev[2];
   cudaError_t e = cudaEventCreate(&ev[0]);
   e = e ? e : cudaEventCreate(&ev[1]);
   float best = 1e30f;
-  bool best_small = false;
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-    const bool small = k == 1;
-    e = use_tile(c, small);
+  int best_var = 0;
+  for (int k = 0; k < explicit_variants(c) && e == cudaSuccess; ++k) {
+    e = use_explicit(c, k);
     if (e != cudaSuccess) break;
     ExplicitArgs ea = explicit_args(c, c->U[0], c->tmp, c->tmp, 2.0, -1.0, hs.dt * hs.dt, 0.0, false);
     explicit_dispatch(c, ea, ntiles(c), nullptr);
@@ -1082,12 +1148,12 @@ cudaError_t autotune_tile(imex_ctx* c) {
     c->tile_us[k] = 1e3f * ms / 5.f;
     if (e == cudaSuccess && c->tile_us[k] < best) {
       best = c->tile_us[k];
-      best_small = small;
+      best_var = k;
     }
   }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
-  return e ? e : use_tile(c, best_small);
+  return e ? e : use_explicit(c, best_var);
 }
 
 // PCG on S (the step; Newmark correction) or, for the initial acceleration
@@ -1897,8 +1963,8 @@ int imex_gauss_points(int n, double* x, double* w) {
   return IMEX_OK;
 }
 
-static // IMEX_LOG=1 in the environment: one JSON line of setup statistics on stderr.
-void log_setup(const HostSetup& hs, const char* where) {
+// IMEX_LOG=1 in the environment: one JSON line of setup statistics on stderr.
+static void log_setup(const HostSetup& hs, const char* where) {
   const char* v = std::getenv("IMEX_LOG");
   if (!v || std::strcmp(v, "1") != 0) return;
   std::fprintf(stderr,
@@ -2380,7 +2446,7 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
       c->num_sms = std::max(1, nsm);
     }
-    e = e ? e : (c->hetero ? use_tile(c, false) : autotune_tile(c));
+    e = e ? e : (c->hetero ? use_explicit(c, 0) : autotune_tile(c));
     if (e != cudaSuccess) {
       std::string msg = std::string("upload failed: ") + cudaGetErrorString(e);
       imex_destroy(c);
@@ -2420,8 +2486,9 @@ int pred_only_blocks(const imex_ctx* c) {
 
 // One step n -> n+1 on stream s; events (may be NULL) are recorded before
 // the explicit kernel, after it, and after the implicit chain.  Scratch
-// (upd, sol, rhs0) defaults to the context's own; given scratch takes the
-// direct solve.
+// (upd, sol, rhs0) of the factorised solve defaults to the context's own
+// (imex_step_noalloc passes its fixed array and accepts direct-solver
+// contexts only).
 //   IMEX / trapezoidal: diagonal CDM step on I_d with the prediction of I_c,
 //     then S a^c_{n+1} = f_t(t_{n+1}) f^c - K^c u_pred and the correction.
 //   Central differences (consistent or HRZ mass): the same explicit kernel
@@ -2458,7 +2525,7 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
         return fail(IMEX_ERR_CUDA, std::string("imex_step: PCG launch: ") + cudaGetErrorString(e));
     } else if (cdm) {
       launch_solve_chain(c, false, ft_at(hs, step), ft_dev, 3, Unext, Ucur, upd, sol, rhs0, s);
-    } else if (c->solver == IMEX_SOLVER_DIRECT || !own) {
+    } else if (c->solver == IMEX_SOLVER_DIRECT) {
       launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, s);
     } else {
       // Right-hand sides, PCG (correction included on convergence), then the
@@ -2490,8 +2557,7 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
 static int autotune_tile_steps(imex_ctx* c) {
   const HostSetup& hs = c->hs;
   if (c->hetero || !c->factorized || hs.n_c == 0) return IMEX_OK;
-  const char* env = std::getenv("IMEX_EXPLICIT_TILE");
-  if (env && (std::string(env) == "large" || std::string(env) == "small")) return IMEX_OK;
+  if (explicit_env_variant(c) >= 0) return IMEX_OK;
   const size_t nn = (size_t)hs.nnodes * c->ncols, ncv = (size_t)hs.n_c * c->ncols;
   double* save = nullptr;
   if (cudaMalloc(&save, (2 * nn + 2 * ncv) * sizeof(double)) != cudaSuccess) {
@@ -2517,11 +2583,10 @@ static int autotune_tile_steps(imex_ctx* c) {
   e = e ? e : cudaEventCreate(&ev[0]);
   e = e ? e : cudaEventCreate(&ev[1]);
   float best = 1e30f;
-  bool best_small = c->tile_small != 0;
+  int best_var = c->xvar;
   int rc = IMEX_OK;
-  for (int k = 0; k < 2 && e == cudaSuccess && rc == IMEX_OK; ++k) {
-    const bool small = k == 1;
-    e = use_tile(c, small);
+  for (int k = 0; k < explicit_variants(c) && e == cudaSuccess && rc == IMEX_OK; ++k) {
+    e = use_explicit(c, k);
     e = e ? e : copy_state(false);
     if (e != cudaSuccess) break;
     rc = step_once(c, nullptr, nullptr);
@@ -2534,12 +2599,12 @@ static int autotune_tile_steps(imex_ctx* c) {
     c->tile_us[k] = 1e3f * ms / 4.f;
     if (e == cudaSuccess && c->tile_us[k] < best) {
       best = c->tile_us[k];
-      best_small = small;
+      best_var = k;
     }
   }
   if (ev[0]) cudaEventDestroy(ev[0]);
   if (ev[1]) cudaEventDestroy(ev[1]);
-  e = e ? e : use_tile(c, best_small);
+  e = e ? e : use_explicit(c, best_var);
   e = e ? e : copy_state(false);
   e = e ? e : cudaDeviceSynchronize();
   cudaFree(save);
@@ -3012,6 +3077,9 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   st->explicit_tile_cells = c->TC;
   st->explicit_tile_us_large = c->tile_us[0];
   st->explicit_tile_us_small = c->tile_us[1];
+  st->explicit_variant = c->xvar;
+  st->explicit_sweep_us = c->tile_us[2];
+  st->explicit_sweep_short_us = c->tile_us[3];
   st->device_bytes = (int64_t)c->bytes;
   st->factorized = c->factorized;
   return IMEX_OK;
@@ -3070,8 +3138,8 @@ void imex_destroy(imex_ctx* c) {
 
 // ---------------------------------------------------------------------------
 // imex_step_noalloc: imex_step with the implicit solve's scratch (descendant
-// update vectors, solution vector) in a fixed array compiled into the library
-// instead of context memory.
+// update vectors, solution vector, right-hand sides) in a fixed array
+// compiled into the library instead of context memory.
 #include <mutex>
 
 namespace {
@@ -3085,7 +3153,11 @@ static __device__ __align__(256) double g_static_solve_scratch[kStaticScratchDou
 
 extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
   if (!c || n < 0) return fail(IMEX_ERR_ARG, "bad arguments");
-  if (c && !c->factorized) return fail(IMEX_ERR_ARG, "imex_step_noalloc needs a factorised context");
+  if (!c->factorized) return fail(IMEX_ERR_ARG, "imex_step_noalloc needs a factorised context");
+  // The PCG solvers keep their right-hand side and iterates in context
+  // memory; only the factorised solve runs on the fixed array.
+  if (c->solver != IMEX_SOLVER_DIRECT)
+    return fail(IMEX_ERR_ARG, "imex_step_noalloc runs the factorised direct solve only (imex_set_solver: direct)");
   const HostSetup& hs = c->hs;
   auto even = [](int64_t v) { return v + (v & 1); };
   const int64_t n_upd = even(std::max<int64_t>(hs.upd_size, 1)) * c->ncols;

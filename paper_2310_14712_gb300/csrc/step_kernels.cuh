@@ -7,6 +7,18 @@
 
 // ---------------------------------------------------------------------------
 // A1 + A2 (+ A3): explicit apply on the tensor grid, CDM update, prediction.
+
+// CDM update of one explicit node (Eqs. CDMacc, CDMstep):
+//   out = cu u + cw w + (ca / M_ii) (f_t f_x - r),
+// ca / M_ii = winv_x (ca winv_y) from the per-axis inverse lumped weights.
+// With cw = -1 (the step) cu u - w is one FMA.  Every 2D explicit kernel
+// uses this helper, so they agree bit for bit.
+__device__ __forceinline__ double cdm_node(double u, double w, double r, double fx, double ft, double wx,
+                                           double ca_wy, double cu, double cw) {
+  const double t = fma(ft, fx, -r);
+  const double s = cw == -1.0 ? fma(cu, u, -w) : fma(cu, u, cw * w);
+  return fma(wx * ca_wy, t, s);
+}
 //
 // A tile owns OX x OY nodes (TC x TC cells).  With u staged in shared memory
 // together with one halo cell on the low side, the stiffness rows of the
@@ -24,11 +36,136 @@
 // For an I_d node every surrounding cell is uncut, so this equals its row of
 // K^d u_n (Eq. Kd).  Nodes of I_c and inactive nodes are computed but not
 // written.  Cells outside the grid contribute nothing.
+// The 1D products of the 2D explicit apply, on the P nodal values of one
+// cell along one grid line.  Each uses the symmetry of the GLL nodes: K1
+// commutes with the reflection x -> -x, so it maps the even and odd parts of
+// a vector separately (P^2 -> about P^2/2 FMAs), and the exact mass is the
+// GLL-lumped mass plus a rank-one term, M1 = diag(w) + C a a^T (GLL
+// quadrature is exact to degree 2p-1; the product of two basis functions
+// differs from a polynomial it integrates exactly by a_i a_j x^{2p}, a_i the
+// leading coefficient of the i-th basis function), so M1 v costs about 3P.
+// Every 2D explicit kernel calls these, so their results agree bit for bit.
+
+// x pass: o1 = (sx K1) v, o2 = M1 v.
+template <int P>
+__device__ __forceinline__ void x_item(const Ops2D& ops, const double (&v)[P], double (&o1)[P], double (&o2)[P]) {
+  constexpr int H = P / 2;
+  constexpr bool kOdd = (P % 2) == 1;
+  double e[H], o[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = v[j] + v[P - 1 - j];
+    o[j] = v[j] - v[P - 1 - j];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    double ev = kOdd ? ops.kxc[i] * v[H] : 0.0, od = 0.0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      ev = fma(ops.kxe[i][j], e[j], ev);
+      od = fma(ops.kxo[i][j], o[j], od);
+    }
+    o1[i] = ev + od;
+    o1[P - 1 - i] = ev - od;
+  }
+  if (kOdd) {
+    double ev = ops.kxc[H] * v[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) ev = fma(ops.kxe[H][j], e[j], ev);
+    o1[H] = ev;
+  }
+  double sa = kOdd ? ops.a[H] * v[H] : 0.0;
+#pragma unroll
+  for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? e[j] : o[j], sa);
+#pragma unroll
+  for (int i = 0; i < P; ++i) o2[i] = fma(ops.w[i], v[i], ops.ca[i] * sa);
+}
+
+// The same, last node only (o1[P-1], o2[P-1]): the right vertex of a cell
+// whose other outputs are not needed.  Same operations as x_item for them.
+template <int P>
+__device__ __forceinline__ void x_item_last(const Ops2D& ops, const double (&v)[P], double& o1p, double& o2p) {
+  constexpr int H = P / 2;
+  constexpr bool kOdd = (P % 2) == 1;
+  double e[H], o[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = v[j] + v[P - 1 - j];
+    o[j] = v[j] - v[P - 1 - j];
+  }
+  double ev = kOdd ? ops.kxc[0] * v[H] : 0.0, od = 0.0;
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    ev = fma(ops.kxe[0][j], e[j], ev);
+    od = fma(ops.kxo[0][j], o[j], od);
+  }
+  o1p = ev - od;
+  double sa = kOdd ? ops.a[H] * v[H] : 0.0;
+#pragma unroll
+  for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? e[j] : o[j], sa);
+  o2p = fma(ops.w[P - 1], v[P - 1], ops.ca[P - 1] * sa);
+}
+
+// y pass: o = M1 va + (sy K1) vb.
+template <int P>
+__device__ __forceinline__ void y_item(const Ops2D& ops, const double (&va)[P], const double (&vb)[P], double (&o)[P]) {
+  constexpr int H = P / 2;
+  constexpr bool kOdd = (P % 2) == 1;
+  double sa = kOdd ? ops.a[H] * va[H] : 0.0;
+#pragma unroll
+  for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? va[j] + va[P - 1 - j] : va[j] - va[P - 1 - j], sa);
+  double e[H], od_[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = vb[j] + vb[P - 1 - j];
+    od_[j] = vb[j] - vb[P - 1 - j];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    double ev = kOdd ? ops.kyc[i] * vb[H] : 0.0, od = 0.0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      ev = fma(ops.kye[i][j], e[j], ev);
+      od = fma(ops.kyo[i][j], od_[j], od);
+    }
+    const int k = P - 1 - i;
+    o[i] = fma(ops.w[i], va[i], fma(ops.ca[i], sa, ev + od));
+    o[k] = fma(ops.w[k], va[k], fma(ops.ca[k], sa, ev - od));
+  }
+  if (kOdd) {
+    double ev = ops.kyc[H] * vb[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) ev = fma(ops.kye[H][j], e[j], ev);
+    o[H] = fma(ops.w[H], va[H], fma(ops.ca[H], sa, ev));
+  }
+}
+
+// The same, last node only (o[P-1]).
+template <int P>
+__device__ __forceinline__ double y_item_last(const Ops2D& ops, const double (&va)[P], const double (&vb)[P]) {
+  constexpr int H = P / 2;
+  constexpr bool kOdd = (P % 2) == 1;
+  double sa = kOdd ? ops.a[H] * va[H] : 0.0;
+#pragma unroll
+  for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? va[j] + va[P - 1 - j] : va[j] - va[P - 1 - j], sa);
+  double e[H], od_[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = vb[j] + vb[P - 1 - j];
+    od_[j] = vb[j] - vb[P - 1 - j];
+  }
+  double ev = kOdd ? ops.kyc[0] * vb[H] : 0.0, od = 0.0;
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    ev = fma(ops.kye[0][j], e[j], ev);
+    od = fma(ops.kyo[0][j], od_[j], od);
+  }
+  return fma(ops.w[P - 1], va[P - 1], fma(ops.ca[P - 1], sa, ev - od));
+}
+
 template <int P, int TC>
 __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D ops) {
   constexpr int p = P - 1;
-  constexpr int H = P / 2;                // pairs (i, P-1-i) of the even-odd split
-  constexpr bool kOdd = (P % 2) == 1;     // a centre node; then a_{P-1-i} = a_i, else -a_i
   constexpr int OX = TC * p, OY = TC * p;
   constexpr int RX = (TC + 1) * p + 1, RY = RX;
   constexpr int NC = TC + 1;
@@ -100,38 +237,7 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
     double v[P], o1[P], o2[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) v[j] = su[yy * RX + cc * p + j];
-    constexpr bool valid = true;
-    // Even and odd parts of v under x -> -x.
-    double e[H], o[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-      e[j] = v[j] + v[P - 1 - j];
-      o[j] = v[j] - v[P - 1 - j];
-    }
-    // o1 = (sx K1) v: the even part maps to the even part, odd to odd.
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-      double ev = kOdd ? ops.kxc[i] * v[H] : 0.0, od = 0.0;
-#pragma unroll
-      for (int j = 0; j < H; ++j) {
-        ev = fma(ops.kxe[i][j], e[j], ev);
-        od = fma(ops.kxo[i][j], o[j], od);
-      }
-      o1[i] = valid ? ev + od : 0.0;
-      o1[P - 1 - i] = valid ? ev - od : 0.0;
-    }
-    if (kOdd) {
-      double ev = ops.kxc[H] * v[H];
-#pragma unroll
-      for (int j = 0; j < H; ++j) ev = fma(ops.kxe[H][j], e[j], ev);
-      o1[H] = valid ? ev : 0.0;
-    }
-    // o2 = M1 v = w .* v + C a (a^T v).
-    double sa = kOdd ? ops.a[H] * v[H] : 0.0;
-#pragma unroll
-    for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? e[j] : o[j], sa);
-#pragma unroll
-    for (int i = 0; i < P; ++i) o2[i] = valid ? fma(ops.w[i], v[i], ops.ca[i] * sa) : 0.0;
+    x_item<P>(ops, v, o1, o2);
     if (cc >= 1) {
 #pragma unroll
       for (int i = 1; i < p; ++i) {
@@ -171,36 +277,8 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
       va[j] = t1[(cr * p + j) * OX + xo];
       vb[j] = t2[(cr * p + j) * OX + xo];
     }
-    constexpr bool valid = true;
-    // o = M1 va + (sy K1) vb, the mass in rank-one form, the stiffness even-odd.
-    double sa = kOdd ? ops.a[H] * va[H] : 0.0;
-#pragma unroll
-    for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? va[j] + va[P - 1 - j] : va[j] - va[P - 1 - j], sa);
-    double e[H], od_[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-      e[j] = vb[j] + vb[P - 1 - j];
-      od_[j] = vb[j] - vb[P - 1 - j];
-    }
     double o[P];
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-      double ev = kOdd ? ops.kyc[i] * vb[H] : 0.0, od = 0.0;
-#pragma unroll
-      for (int j = 0; j < H; ++j) {
-        ev = fma(ops.kye[i][j], e[j], ev);
-        od = fma(ops.kyo[i][j], od_[j], od);
-      }
-      const int k = P - 1 - i;
-      o[i] = valid ? fma(ops.w[i], va[i], fma(ops.ca[i], sa, ev + od)) : 0.0;
-      o[k] = valid ? fma(ops.w[k], va[k], fma(ops.ca[k], sa, ev - od)) : 0.0;
-    }
-    if (kOdd) {
-      double ev = ops.kyc[H] * vb[H];
-#pragma unroll
-      for (int j = 0; j < H; ++j) ev = fma(ops.kye[H][j], e[j], ev);
-      o[H] = valid ? fma(ops.w[H], va[H], fma(ops.ca[H], sa, ev)) : 0.0;
-    }
+    y_item<P>(ops, va, vb, o);
     if (cr >= 1) {
 #pragma unroll
       for (int i = 1; i < p; ++i) rr[((cr - 1) * p + i) * OX + xo] = o[i];
@@ -216,6 +294,7 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
   __syncthreads();
 
   // CDM update of the owned I_d nodes (Eqs. CDMacc, CDMstep).
+  const double ft = a.ft_dev ? a.ft_dev[0] : a.ft;
   for (int it = tid; it < OY * OX; it += kThreads) {
     const int yo = it / OX, xo = it - yo * OX;
     const int gx = X0 + xo, gy = Y0 + yo;
@@ -224,10 +303,342 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
     if (a.cls[g] != NODE_D) continue;
     const double r = rr[yo * OX + xo];
     const double u = su[(yo + p) * RX + xo + p];
-    const double minv = a.winv_x[gx] * a.winv_y[gy];
-    const double ft = a.ft_dev ? a.ft_dev[0] : a.ft;
-    const double acc = minv * (ft * fxc[g] - r);
-    OUTc[g] = a.cu * u + a.cw * Wc[g] + a.ca * acc;
+    OUTc[g] = cdm_node(u, Wc[g], r, fxc[g], ft, a.winv_x[gx], a.ca * a.winv_y[gy], a.cu, a.cw);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A1 + A2 (+ A3) in 2D, persistent sweep form.  The grid is cut into strips
+// of TCX cells (OX = TCX p owned node columns); the work units are (strip,
+// cell row) pairs, strip-major, and CTA b of the nsweep = a.ntx sweep CTAs
+// takes the contiguous units [b U / nsweep, (b+1) U / nsweep), so every CTA has the same
+// number of cell rows within one.  A CTA walks each of its strip segments
+// upwards in chunks of CH cell rows.  Between chunks it keeps the top node
+// row of the chunk: its staged u, its x-pass products (T1 = (sx K1)_x u,
+// T2 = (M1)_x u) and its partial stiffness row from the cell row below, so
+// no row of the strip is staged or contracted twice except the cell row
+// below a segment's start (its top output only).  The left halo cell of the
+// strip contributes only its right vertex column (x_item_last).  The next
+// chunk's rows of u are copied into the other of two buffers (cp.async)
+// while the current chunk is contracted.  Same products and sums as
+// k_explicit2d, in the same order: the two kernels agree bit for bit.
+// Shared memory (doubles): u 2 x SR x RX, T1 and T2 SR x OXP each, x-pass
+// vertex partials or y-pass rows (aliased), the carried partial row.
+template <int P, int TCX, int CH>
+struct SweepShape {
+  static constexpr int p = P - 1;
+  static constexpr int OX = TCX * p;        // owned node columns of a full strip
+  static constexpr int OXP = OX + 1;        // + the grid's last column in the last strip
+  static constexpr int RX = OX + p + 1;     // staged columns: halo cell, strip cells
+  static constexpr int NC = TCX + 1;        // staged cells per row (halo first)
+  static constexpr int NR = CH * p;         // new node rows per chunk
+  static constexpr int SR = NR + 1;         // staged rows (carried row first)
+  static constexpr int XR = NR > P ? NR : P;  // rows of x-pass partials
+  static constexpr int SCR = (4 * XR * NC > SR * OXP + 2 * CH * OXP) ? 4 * XR * NC : SR * OXP + 2 * CH * OXP;
+  static constexpr int KF = (SR * OXP + kThreads - 1) / kThreads;  // CDM nodes per thread per chunk
+  // u (2 buffers), T1, T2, scratch, carried row (2 buffers), winv_x of the
+  // strip, winv_y (2 buffers)
+  static constexpr int DOUBLES = 2 * SR * RX + 2 * SR * OXP + SCR + 2 * OXP + OXP + 2 * SR;
+};
+
+// Stage rows [gy0, gy0 + nrows) of u (columns X0 - p ... X0 + OX) into su
+// rows [r0, r0 + nrows): cp.async of 8 bytes per node inside the grid,
+// zeros outside.
+template <int RX>
+__device__ __forceinline__ void sweep_stage(double* su, int r0, const double* Uc, int gy0, int nrows, int X0, int p,
+                                            int nx) {
+  for (int idx = threadIdx.x; idx < nrows * RX; idx += blockDim.x) {
+    const int yy = idx / RX, xx = idx - yy * RX;
+    const int gx = X0 - p + xx;
+    double* d = su + (r0 + yy) * RX + xx;
+    if (gx >= 0 && gx < nx) {
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(d);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa),
+                   "l"(Uc + (size_t)(gy0 + yy) * nx + gx)
+                   : "memory");
+    } else {
+      *d = 0.0;
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Stage n consecutive doubles src[i0 + k] (k < n, zero where i0 + k >= lim)
+// into dst[k] (cp.async, 8 bytes each); not committed.
+__device__ __forceinline__ void sweep_stage_vec(double* dst, const double* src, int i0, int n, int lim) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    if (i0 + k < lim) {
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + k);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src + i0 + k) : "memory");
+    } else {
+      dst[k] = 0.0;
+    }
+  }
+}
+
+template <int P, int TCX, int CH, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_sweep2d(ExplicitArgs a, Ops2D ops) {
+  using S = SweepShape<P, TCX, CH>;
+  constexpr int p = S::p, OX = S::OX, OXP = S::OXP, RX = S::RX, NC = S::NC, NR = S::NR, SR = S::SR;
+  constexpr int XR = S::XR, KF = S::KF;
+  extern __shared__ __align__(16) double sm[];
+  const int tid = threadIdx.x;
+  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
+  const double* Uc = a.U + on;
+  const double* Wc = a.W + on;     // may alias OUTc
+  double* OUTc = a.OUT + on;
+  const double* fxc = a.fx + on;
+  // The first solve launch may start staging its constant factor blocks now;
+  // it waits for this grid (griddepcontrol.wait) before it reads u.
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+
+  const int nsweep = a.ntx;        // sweep CTAs; the rest of the grid (if any) predicts
+  const double c1p = a.dt, c2p = (0.5 - kNewmarkBeta) * a.dt * a.dt;
+  if ((int)blockIdx.x >= nsweep) {
+    // Newmark prediction on I_c (Fig. TrapCDMIMEX, "Prediction").
+    const int stride = (gridDim.x - nsweep) * blockDim.x;
+    for (int r = (blockIdx.x - nsweep) * blockDim.x + tid; r < a.n_c; r += stride) {
+      const int node = a.c_node[r];
+      OUTc[node] = Uc[node] + c1p * a.v_c[oc + r] + c2p * a.a_c[oc + r];
+    }
+    return;
+  }
+  // No prediction CTAs (gridDim.x == nsweep): each sweep CTA predicts its
+  // share of I_c while its first rows arrive (a CTA launched after the
+  // sweep CTAs would only start once one of them has finished).
+  bool predict = (int)gridDim.x == nsweep && a.n_c > 0;
+  auto predict_share = [&]() {
+    const int r0 = (int)((int64_t)a.n_c * blockIdx.x / nsweep);
+    const int r1 = (int)((int64_t)a.n_c * (blockIdx.x + 1) / nsweep);
+    for (int r = r0 + tid; r < r1; r += kThreads) {
+      const int node = a.c_node[r];
+      OUTc[node] = Uc[node] + c1p * a.v_c[oc + r] + c2p * a.a_c[oc + r];
+    }
+    predict = false;
+  };
+
+  double* const ub0 = sm;                    // u, two buffers of SR x RX
+  double* const ub1 = sm + SR * RX;
+  double* t1 = sm + 2 * SR * RX;             // SR x OXP
+  double* t2 = t1 + SR * OXP;
+  double* scr = t2 + SR * OXP;
+  double* tl1 = scr;                         // XR x NC vertex partials (x pass)
+  double* tr1 = tl1 + XR * NC;
+  double* tl2 = tr1 + XR * NC;
+  double* tr2 = tl2 + XR * NC;
+  double* rr = scr;                          // SR x OXP rows of K^d u (aliases the x partials)
+  double* rb = rr + SR * OXP;                // CH x OXP bottom-vertex partials (y pass)
+  double* rt = rb + CH * OXP;                // CH x OXP top-vertex partials
+  double* const carry0 = scr + S::SCR;       // OXP: partial row from the cell row below,
+  double* const carry1 = carry0 + OXP;       //   two buffers (read, then written, in one phase)
+  double* wxs = carry1 + OXP;                // OXP: winv_x of the strip's columns
+  double* const wy0 = wxs + OXP;             // SR: winv_y of a chunk's rows, two buffers
+  double* const wy1 = wy0 + SR;
+
+  const int ncy = a.ncy;
+  const int nstrip = (a.ncx + TCX - 1) / TCX;
+  const int64_t units = (int64_t)nstrip * ncy;
+  int64_t u0 = units * blockIdx.x / nsweep;
+  const int64_t u1 = units * (blockIdx.x + 1) / nsweep;
+  const double ft = a.ft_dev ? a.ft_dev[0] : a.ft;
+
+  // x pass over staged rows [r_lo, r_lo + nrows) of su into T1/T2 rows
+  // [r_lo, ...): cell by cell, then the vertex columns.
+  auto xpass = [&](const double* su, int r_lo, int nrows, int cx0) {
+    for (int it = tid; it < nrows * NC; it += kThreads) {
+      const int cc = it / nrows, yl = it - cc * nrows, yy = r_lo + yl;
+      const int cx = cx0 + cc;
+      double* T1 = t1 + yy * OXP + (cc - 1) * p;
+      double* T2 = t2 + yy * OXP + (cc - 1) * p;
+      if (cx < 0 || cx >= a.ncx) {   // a cell outside the grid contributes nothing
+        if (cc >= 1) {
+#pragma unroll
+          for (int i = 1; i < p; ++i) {
+            T1[i] = 0.0;
+            T2[i] = 0.0;
+          }
+        }
+        tl1[yl * NC + cc] = 0.0;
+        tr1[yl * NC + cc] = 0.0;
+        tl2[yl * NC + cc] = 0.0;
+        tr2[yl * NC + cc] = 0.0;
+        continue;
+      }
+      double v[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) v[j] = su[yy * RX + cc * p + j];
+      if (cc == 0) {   // halo cell: its right vertex only
+        double o1p, o2p;
+        x_item_last<P>(ops, v, o1p, o2p);
+        tr1[yl * NC] = o1p;
+        tr2[yl * NC] = o2p;
+        continue;
+      }
+      double o1[P], o2[P];
+      x_item<P>(ops, v, o1, o2);
+#pragma unroll
+      for (int i = 1; i < p; ++i) {
+        T1[i] = o1[i];
+        T2[i] = o2[i];
+      }
+      tl1[yl * NC + cc] = o1[0];
+      tr1[yl * NC + cc] = o1[p];
+      tl2[yl * NC + cc] = o2[0];
+      tr2[yl * NC + cc] = o2[p];
+    }
+    __syncthreads();
+    for (int it = tid; it < nrows * NC; it += kThreads) {   // vertex columns k p, k = 0..TCX
+      const int k = it / nrows, yl = it - k * nrows, yy = r_lo + yl;
+      const double r1 = k < TCX ? tl1[yl * NC + k + 1] : 0.0;
+      const double r2 = k < TCX ? tl2[yl * NC + k + 1] : 0.0;
+      t1[yy * OXP + k * p] = tr1[yl * NC + k] + r1;
+      t2[yy * OXP + k * p] = tr2[yl * NC + k] + r2;
+    }
+    __syncthreads();
+  };
+
+  while (u0 < u1) {
+    // One segment: strip sx, cell rows [ra, rb).
+    const int sx = (int)(u0 / ncy);
+    const int ra = (int)(u0 - (int64_t)sx * ncy);
+    const int64_t rlim = ra + (u1 - u0);
+    const int rb_ = rlim < ncy ? (int)rlim : ncy;
+    u0 += rb_ - ra;
+    const int X0 = sx * OX;
+    const int cx0 = sx * TCX - 1;                 // the halo cell
+    const int oxe = min(OXP, a.nx - X0);          // owned columns (the last strip also owns column nx - 1)
+    const int ocols = (sx == nstrip - 1) ? oxe : min(OX, oxe);
+    int cur = 0;
+    int c0 = ra;
+    int ch = min(CH, rb_ - c0);
+    __syncthreads();   // the previous segment's reads of winv_x are done
+    // Everything the segment's start needs, in one round trip: winv_x of the
+    // strip, winv_y and u of the first chunk's rows and, below a segment
+    // that does not start at the grid's bottom, the P rows of the cell row
+    // below (buffer 1).
+    sweep_stage_vec(wxs, a.winv_x, X0, OXP, a.nx);
+    sweep_stage_vec(wy0, a.winv_y, c0 * p, SR, a.ny);
+    if (ra == 0) sweep_stage<RX>(ub0, 0, Uc, 0, ch * p + 1, X0, p, a.nx);
+    else {
+      sweep_stage<RX>(ub1, 0, Uc, (ra - 1) * p, P, X0, p, a.nx);
+      sweep_stage<RX>(ub0, 1, Uc, c0 * p + 1, ch * p, X0, p, a.nx);
+    }
+    if (predict) predict_share();
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    // Prologue: node row ra p (staged u, T1, T2 in row 0 of buffer 0) and
+    // the partial of that row from the cell row below.
+    if (ra == 0) {
+      xpass(ub0, 0, 1, cx0);
+      for (int xo = tid; xo < OXP; xo += kThreads) carry0[xo] = 0.0;
+    } else {
+      // x pass on the P rows of the cell row below, its top output; then row
+      // ra p moves to row 0 of buffer 0.
+      xpass(ub1, 0, P, cx0);
+      for (int xo = tid; xo < ocols; xo += kThreads) {
+        double va[P], vb[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          va[j] = t1[j * OXP + xo];
+          vb[j] = t2[j * OXP + xo];
+        }
+        carry0[xo] = y_item_last<P>(ops, va, vb);
+      }
+      __syncthreads();
+      for (int xx = tid; xx < RX; xx += kThreads) ub0[xx] = ub1[p * RX + xx];
+      for (int xo = tid; xo < OXP; xo += kThreads) {
+        t1[xo] = t1[p * OXP + xo];
+        t2[xo] = t2[p * OXP + xo];
+      }
+      __syncthreads();
+    }
+    while (ch > 0) {
+      double* const su = cur ? ub1 : ub0;
+      double* const sn = cur ? ub0 : ub1;
+      const double* const wyc = cur ? wy1 : wy0;
+      const double* const carry = cur ? carry1 : carry0;
+      double* const carry_next = cur ? carry0 : carry1;
+      const int c1 = c0 + ch;
+      const int chn = min(CH, rb_ - c1);         // next chunk's cell rows
+      const bool top = c1 == ncy;                 // the grid's top row is final too
+      const int nfin = ch * p + (top ? 1 : 0);
+      // The CDM update's inputs of this thread's nodes (u_{n-1}, f_x, class),
+      // loaded now so that they arrive while the passes run.
+      double pw[KF], pf[KF];
+      int pcl[KF];
+#pragma unroll
+      for (int q = 0; q < KF; ++q) {
+        const int it = tid + q * kThreads;
+        pcl[q] = NODE_INACTIVE;
+        pw[q] = pf[q] = 0.0;
+        if (it < ocols * nfin) {
+          const int yl = it / ocols, xo = it - yl * ocols;
+          const size_t g = (size_t)(c0 * p + yl) * a.nx + X0 + xo;
+          pcl[q] = a.cls[g];
+          pw[q] = Wc[g];
+          pf[q] = fxc[g];
+        }
+      }
+      if (chn > 0) {
+        sweep_stage_vec(cur ? wy0 : wy1, a.winv_y, c1 * p, SR, a.ny);
+        sweep_stage<RX>(sn, 1, Uc, c1 * p + 1, chn * p, X0, p, a.nx);
+      }
+      xpass(su, 1, ch * p, cx0);
+      // y pass: item = (column xo, cell row k), columns fastest.
+      for (int it = tid; it < ocols * ch; it += kThreads) {
+        const int k = it / ocols, xo = it - k * ocols;
+        double va[P], vb[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          va[j] = t1[(k * p + j) * OXP + xo];
+          vb[j] = t2[(k * p + j) * OXP + xo];
+        }
+        double o[P];
+        y_item<P>(ops, va, vb, o);
+#pragma unroll
+        for (int i = 1; i < p; ++i) rr[(k * p + i) * OXP + xo] = o[i];
+        rb[k * OXP + xo] = o[0];
+        rt[k * OXP + xo] = o[p];
+      }
+      __syncthreads();
+      // CDM update of the finished rows (Eqs. CDMacc, CDMstep).  A vertex
+      // row k p adds the contributions of the cell rows below and above it
+      // here (rows are warp-uniform for full strips).
+#pragma unroll
+      for (int q = 0; q < KF; ++q) {
+        const int it = tid + q * kThreads;
+        if (pcl[q] != NODE_D) continue;   // also every it >= ocols * nfin
+        const int yl = it / ocols, xo = it - yl * ocols;
+        const size_t g = (size_t)(c0 * p + yl) * a.nx + X0 + xo;
+        const int k = yl / p;
+        double r;
+        if (yl != k * p) {
+          r = rr[yl * OXP + xo];
+        } else if (k < ch) {
+          const double below = k == 0 ? carry[xo] : rt[(k - 1) * OXP + xo];
+          r = below + rb[k * OXP + xo];
+        } else {   // the grid's top row: nothing above
+          r = rt[(k - 1) * OXP + xo];
+        }
+        const double u = su[yl * RX + xo + p];
+        OUTc[g] = cdm_node(u, pw[q], r, pf[q], ft, wxs[xo], a.ca * wyc[yl], a.cu, a.cw);
+      }
+      if (!top)
+        for (int xo = tid; xo < ocols; xo += kThreads) carry_next[xo] = rt[(ch - 1) * OXP + xo];
+      // Carry the top row (u, T1, T2) to row 0 of the next buffer.
+      if (chn > 0) {
+        for (int xx = tid; xx < RX; xx += kThreads) sn[xx] = su[(ch * p) * RX + xx];
+        for (int xo = tid; xo < OXP; xo += kThreads) {
+          t1[xo] = t1[(ch * p) * OXP + xo];
+          t2[xo] = t2[(ch * p) * OXP + xo];
+        }
+      }
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      __syncthreads();
+      cur = 1 - cur;
+      c0 = c1;
+      ch = chn;
+    }
   }
 }
 

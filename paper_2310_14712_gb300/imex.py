@@ -60,7 +60,9 @@ class Stats(ctypes.Structure):
         [(n, ctypes.c_int64) for n in ("solve_levels", "solve_ctas", "solve_smem_bytes", "launches_per_step",
                                     "rhs_pairs", "ncols", "explicit_tile_cells")] + \
         [(n, ctypes.c_double) for n in ("explicit_tile_us_large", "explicit_tile_us_small")] + \
-        [("scheme", ctypes.c_int64), ("dt_crit_cut_min", ctypes.c_double), ("factorized", ctypes.c_int64)]
+        [("scheme", ctypes.c_int64), ("dt_crit_cut_min", ctypes.c_double), ("factorized", ctypes.c_int64),
+         ("explicit_variant", ctypes.c_int64), ("explicit_sweep_us", ctypes.c_double),
+         ("explicit_sweep_short_us", ctypes.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -95,6 +97,7 @@ _lib.imex_set_fields.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int64, ctypes.
 _lib.imex_set_step.argtypes = [_vp, ctypes.c_int64]
 _lib.imex_set_initial.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int]
 _lib.imex_info.argtypes = [_vp, ctypes.POINTER(Stats)]
+_lib.imex_probe_fp64.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
 _lib.imex_last_error.restype = ctypes.c_char_p
 _lib.imex_destroy.argtypes = [_vp]
 _lib.imex_destroy.restype = None
@@ -108,7 +111,7 @@ _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctyp
 EXPORTS = ("imex_setup", "imex_setup_batch", "imex_setup_scheme", "imex_setup_pcg", "imex_adjoint", "imex_set_solver", "imex_pcg_train", "imex_pcg_status",
            "imex_fsai_kaporin", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
            "imex_set_initial", "imex_info", "imex_check_finite", "imex_last_error", "imex_destroy", "imex_gll_points",
-           "imex_gauss_points", "imex_host_setup_export")
+           "imex_gauss_points", "imex_host_setup_export", "imex_probe_fp64")
 
 
 class ImexError(RuntimeError):
@@ -175,6 +178,18 @@ def fsai_kaporin(s_ptr, s_col, s_val, g_ptr, g_col, g_val, stream=None):
                                   g_col.data_ptr(), g_val.data_ptr(), grad.data_ptr(), ctypes.byref(loss),
                                   ctypes.c_void_p(st.cuda_stream)), "imex_fsai_kaporin")
     return loss.value, grad
+
+
+PROBE_KINDS = {"fma": 0, "add": 1, "mul": 2}
+
+
+def probe_fp64(kind="fma", iters=40000):
+    """Measured FP64 thread-instruction rate of the current device (imex_probe_fp64):
+    returns (instructions per second, seconds of the timed launch)."""
+    rate, secs = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.imex_probe_fp64(PROBE_KINDS[kind], int(iters), ctypes.byref(rate), ctypes.byref(secs)),
+           "imex_probe_fp64")
+    return rate.value, secs.value
 
 
 def gll_points(p):

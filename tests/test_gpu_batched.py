@@ -101,17 +101,25 @@ def test_batched_rejects_source_count_mismatch():
 
 
 @pytest.mark.parametrize("make", [lambda: workloads.plate16(), lambda: workloads.multisource(nsrc=4)])
-def test_explicit_tile_sizes_agree_bitwise(make, monkeypatch):
-    # The autotuner picks one of two explicit tile sizes; both must give the
-    # same numbers (per node the same contractions and vertex sums in the same
-    # order), so the choice never changes a result.
+def test_explicit_variants_agree_bitwise(make, monkeypatch):
+    # The autotuner picks one of four explicit variants (two tile sizes, the
+    # persistent strip sweep in long or short chunks); all must give the same
+    # numbers (per node the same contractions and vertex sums in the same
+    # order), so the choice never changes a result.  Each sweep runs twice:
+    # one CTA per unit, and a few CTAs whose unit ranges cross strips.
     imex = _imex()
     out = {}
-    for tile in ("large", "small"):
+    for tile, ctas in (("large", None), ("small", None), ("sweep", None), ("sweep", "7"),
+                       ("sweep_short", None), ("sweep_short", "5")):
         monkeypatch.setenv("IMEX_EXPLICIT_TILE", tile)
+        if ctas:
+            monkeypatch.setenv("IMEX_SWEEP_CTAS", ctas)
         w = make()
         with imex.Imex.from_workload(w, ncols=len(w.src_pos) if w.name == "multisource" else 1) as g:
             g.step(50)
-            out[tile] = (g.fields("u", out=np.zeros(g.field_len)), g.info()["explicit_tile_cells"])
-    assert out["large"][1] != out["small"][1]
-    assert np.array_equal(out["large"][0], out["small"][0])
+            info = g.info()
+            out[(tile, ctas)] = (g.fields("u", out=np.zeros(g.field_len)), info["explicit_variant"])
+    assert [v[1] for v in out.values()] == [0, 1, 2, 2, 3, 3]
+    ref = out[("large", None)][0]
+    for key, (u, _) in out.items():
+        assert np.array_equal(u, ref), key
