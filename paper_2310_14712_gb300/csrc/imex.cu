@@ -655,6 +655,7 @@ struct imex_ctx {
   double *U[2] = {nullptr, nullptr};
   double* tmp = nullptr;    // full grid scratch (initial velocity, exports)
   double* fx = nullptr;
+  double* fxs = nullptr;    // 2D: dt^2 M^{-1} f_x (the explicit kernels' source term)
   double *winv_x = nullptr, *winv_y = nullptr, *winv_z = nullptr;
   uint8_t* cls = nullptr;
   // implicit partition
@@ -952,6 +953,8 @@ ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double
   ea.OUT = OUT;
   ea.cls = c->cls;
   ea.fx = c->fx;
+  ea.fxs = c->fxs;
+  ea.kappa2 = ca / (hs.dt * hs.dt);
   ea.winv_x = c->winv_x;
   ea.winv_y = c->winv_y;
   ea.winv_z = c->winv_z;
@@ -1874,6 +1877,35 @@ int explicit_ops(const HostSetup& hs, double sx, double sy, Ops2D& ops) {
 
 // 3D: even-odd stiffness per axis (scales s3) and the rank-one mass, from
 // the 2D routine (whose checks apply to the same 1D matrices).
+// Fold dt^2 M^{-1} into the 2D operators (Ops2D): x rows scaled by f_i, y
+// rows by kappa f_i, f_i = 1 / (assembled GLL weight of local node i for an
+// interior vertex: w_i, or w_0 + w_p at a vertex), kappa = dt^2 / (rho |J|).
+void mass_scaled_ops(const HostSetup& hs, double kappa, Ops2D& ops) {
+  const int P = hs.P, p = hs.p, H = P / 2;
+  const bool odd = (P % 2) == 1;
+  double f[9];
+  for (int i = 0; i < P; ++i) f[i] = (i == 0 || i == p) ? 1.0 / (hs.gll_w[0] + hs.gll_w[p]) : 1.0 / hs.gll_w[i];
+  for (int i = 0; i <= (odd ? H : H - 1); ++i) {   // row i (and P-1-i, f symmetric)
+    for (int j = 0; j < H; ++j) {
+      ops.kxe[i][j] *= f[i];
+      ops.kye[i][j] *= kappa * f[i];
+      if (i < H) {
+        ops.kxo[i][j] *= f[i];
+        ops.kyo[i][j] *= kappa * f[i];
+      }
+    }
+    if (odd) {
+      ops.kxc[i] *= f[i];
+      ops.kyc[i] *= kappa * f[i];
+    }
+  }
+  for (int i = 0; i < P; ++i) {
+    ops.cax[i] = f[i] * ops.ca[i];
+    ops.wy[i] = kappa * f[i] * ops.w[i];
+    ops.cay[i] = kappa * f[i] * ops.ca[i];
+  }
+}
+
 int explicit_ops3(const HostSetup& hs, const double* s3, Ops3D& ops) {
   Ops2D a{}, b{};
   if (int rc = explicit_ops(hs, s3[0], s3[1], a)) return rc;
@@ -2106,6 +2138,7 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
         delete c;
         return rc;
       }
+      mass_scaled_ops(hs, hs.dt * hs.dt / (pb.rho * 0.25 * hs.h[0] * hs.h[1]), c->ops);
     } else {
       const double s3[3] = {0.5 * rc2 * hs.h[1] * hs.h[2] / hs.h[0], 0.5 * rc2 * hs.h[0] * hs.h[2] / hs.h[1],
                             0.5 * rc2 * hs.h[0] * hs.h[1] / hs.h[2]};
@@ -2252,6 +2285,7 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->U[1], nn * ncols);
     ar.add(&c->tmp, nn * ncols);
     ar.add(&c->fx, nn * ncols);
+    ar.add(&c->fxs, hs.dim == 2 ? nn * ncols : 1);
     ar.add(&c->winv_x, hs.nn[0]);
     ar.add(&c->winv_y, hs.nn[1]);
     ar.add(&c->winv_z, wz.size());
@@ -2354,6 +2388,16 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
 
     cudaError_t e = cudaMemset(c->base, 0, c->bytes);
     e = e ? e : upload(c->fx, hs.fx);
+    if (hs.dim == 2) {   // dt^2 M^{-1} f_x with the per-axis inverse lumped weights
+      std::vector<double> fxs(hs.fx.size());
+      const double dt2 = hs.dt * hs.dt;
+      for (size_t g = 0; g < fxs.size(); ++g) {
+        const int64_t gl = (int64_t)(g % (size_t)nn);
+        const int gx = (int)(gl % hs.nn[0]), gy = (int)(gl / hs.nn[0]);
+        fxs[g] = dt2 * (wx[gx] * wy[gy]) * hs.fx[g];
+      }
+      e = e ? e : upload(c->fxs, fxs);
+    }
     e = e ? e : upload(c->winv_x, wx);
     e = e ? e : upload(c->winv_y, wy);
     e = e ? e : upload(c->winv_z, wz);

@@ -43,16 +43,27 @@ __host__ __device__ inline double wavelet_value(int kind, double f0, double t) {
 
 // 1D operators of the explicit apply (2D):
 //   r = sx (M1_y (x) K1_x) u + sy (K1_y (x) M1_x) u
-// K1 (stiffness) in even-odd form, pre-scaled by sx (x pass) or sy (y pass),
-// H = P/2, rows i <= (P-1)/2:
+// K1 (stiffness) in even-odd form, rows i <= (P-1)/2:
 //   ke[i][j] = (A[i][j] + A[i][P-1-j]) / 2, ko[i][j] = (A[i][j] - A[i][P-1-j]) / 2
-//   (j < H), kc[i] = A[i][H] (P odd);  then for i < H, with e_j, o_j the even
-//   and odd parts of v:  (A v)_i = Ev_i + Od_i, (A v)_{P-1-i} = Ev_i - Od_i.
-// M1 (mass, unscaled) = diag(w) + C a a^T; ca = C a.
+//   (j < H = P/2), kc[i] = A[i][H] (P odd);  then for i < H, with e_j, o_j the
+//   even and odd parts of v:  (A v)_i = Ev_i + Od_i, (A v)_{P-1-i} = Ev_i - Od_i.
+// M1 (mass) = diag(w) + C a a^T; ca = C a.
+// The 2D kernels apply dt^2 M^{-1} K with the inverse lumped mass folded in:
+// on a uniform grid M^{-1} of an explicit node is (1/W_x)(1/W_y)/(rho |J|)
+// with per-axis assembled GLL weights W, which per local node are w_i
+// (interior) or 2 w_0 (a vertex shared by two cells; w_0 at the grid's edge,
+// where the kernels double the vertex sum exactly).  So with f_i = 1/w_i or
+// 1/(2 w_0) and kappa = dt^2 / (rho |J|):
+//   x pass  A = f (x) sx K1 (kxe, kxo, kxc),  M1 -> f M1: interior rows
+//           v_i + cax_i (a^T v), vertex rows v_i / 2 + cax_i (a^T v),
+//   y pass  A = kappa f (x) sy K1 (kye, kyo, kyc),  M1 -> kappa f M1:
+//           wy_i v_i + cay_i (a^T v).
+// (3D builds its Ops3D from the unscaled form: w, ca.)
 struct Ops2D {
   double kxe[5][4], kxo[4][4], kxc[5];
   double kye[5][4], kyo[4][4], kyc[5];
   double w[9], ca[9], a[9];
+  double cax[9], wy[9], cay[9];
 };
 
 // 1D operators of the 3D explicit apply:
@@ -77,6 +88,8 @@ struct ExplicitArgs {
   int ncx, ncy, ncz;      // cells per axis
   int ntx, nty, ntz;      // tiles per axis
   double cu, cw, ca;      // out = cu u + cw w + ca minv (ft fx - r)
+  const double* fxs;      // 2D: dt^2 M^{-1} f_x per node (explicit nodes), full grid
+  double kappa2;          // 2D: ca / dt^2 (the kernels form dt^2 M^{-1} (ft fx - r))
   double ft;              // f_t(t_n)
   const double* ft_dev;   // if set: f_t(t_n) = ft_dev[0] (user-supplied samples)
   // Newmark prediction on I_c (blocks after the tiles); n_c = 0 disables it.

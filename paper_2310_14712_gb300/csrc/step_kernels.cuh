@@ -9,15 +9,17 @@
 // A1 + A2 (+ A3): explicit apply on the tensor grid, CDM update, prediction.
 
 // CDM update of one explicit node (Eqs. CDMacc, CDMstep):
-//   out = cu u + cw w + (ca / M_ii) (f_t f_x - r),
-// ca / M_ii = winv_x (ca winv_y) from the per-axis inverse lumped weights.
-// With cw = -1 (the step) cu u - w is one FMA.  Every 2D explicit kernel
-// uses this helper, so they agree bit for bit.
-__device__ __forceinline__ double cdm_node(double u, double w, double r, double fx, double ft, double wx,
-                                           double ca_wy, double cu, double cw) {
-  const double t = fma(ft, fx, -r);
-  const double s = cw == -1.0 ? fma(cu, u, -w) : fma(cu, u, cw * w);
-  return fma(wx * ca_wy, t, s);
+//   out = cu u + cw w + ca M_ii^{-1} (f_t f_x - (K u)_i)
+//       = cu u + cw w + kappa2 (f_t g - r),
+// with g = dt^2 M_ii^{-1} f_x (stored), r = dt^2 M_ii^{-1} (K u)_i (the
+// mass-scaled apply) and kappa2 = ca / dt^2.  The step (cu = 2, cw = -1,
+// kappa2 = 1) costs three FP64 operations.  Every 2D explicit kernel uses
+// this helper, so they agree bit for bit.
+__device__ __forceinline__ double cdm_node(double u, double w, double r, double g, double ft, double cu,
+                                           double cw, double kappa2) {
+  const double t = fma(ft, g, -r);
+  if (cw == -1.0 && kappa2 == 1.0) return fma(cu, u, -w) + t;
+  return fma(kappa2, t, fma(cu, u, cw * w));
 }
 //
 // A tile owns OX x OY nodes (TC x TC cells).  With u staged in shared memory
@@ -44,7 +46,9 @@ __device__ __forceinline__ double cdm_node(double u, double w, double r, double 
 // quadrature is exact to degree 2p-1; the product of two basis functions
 // differs from a polynomial it integrates exactly by a_i a_j x^{2p}, a_i the
 // leading coefficient of the i-th basis function), so M1 v costs about 3P.
-// Every 2D explicit kernel calls these, so their results agree bit for bit.
+// The coefficients carry the inverse lumped mass and dt^2 (Ops2D), so r is
+// dt^2 M^{-1} K u at explicit nodes.  Every 2D explicit kernel calls these,
+// so their results agree bit for bit.
 
 // x pass: o1 = (sx K1) v, o2 = M1 v.
 template <int P>
@@ -78,7 +82,8 @@ __device__ __forceinline__ void x_item(const Ops2D& ops, const double (&v)[P], d
 #pragma unroll
   for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? e[j] : o[j], sa);
 #pragma unroll
-  for (int i = 0; i < P; ++i) o2[i] = fma(ops.w[i], v[i], ops.ca[i] * sa);
+  for (int i = 0; i < P; ++i)
+    o2[i] = (i == 0 || i == P - 1) ? fma(0.5, v[i], ops.cax[i] * sa) : fma(ops.cax[i], sa, v[i]);
 }
 
 // The same, last node only (o1[P-1], o2[P-1]): the right vertex of a cell
@@ -103,7 +108,7 @@ __device__ __forceinline__ void x_item_last(const Ops2D& ops, const double (&v)[
   double sa = kOdd ? ops.a[H] * v[H] : 0.0;
 #pragma unroll
   for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? e[j] : o[j], sa);
-  o2p = fma(ops.w[P - 1], v[P - 1], ops.ca[P - 1] * sa);
+  o2p = fma(0.5, v[P - 1], ops.cax[P - 1] * sa);
 }
 
 // y pass: o = M1 va + (sy K1) vb.
@@ -128,15 +133,19 @@ __device__ __forceinline__ void y_item(const Ops2D& ops, const double (&va)[P], 
       ev = fma(ops.kye[i][j], e[j], ev);
       od = fma(ops.kyo[i][j], od_[j], od);
     }
+    // The rank-one mass term of the pair: cay_{P-1-i} = cay_i (p even) or
+    // -cay_i (p odd), so it joins the even or the odd accumulator.
+    if (kOdd) ev = fma(ops.cay[i], sa, ev);
+    else od = fma(ops.cay[i], sa, od);
     const int k = P - 1 - i;
-    o[i] = fma(ops.w[i], va[i], fma(ops.ca[i], sa, ev + od));
-    o[k] = fma(ops.w[k], va[k], fma(ops.ca[k], sa, ev - od));
+    o[i] = fma(ops.wy[i], va[i], ev + od);
+    o[k] = fma(ops.wy[k], va[k], ev - od);
   }
   if (kOdd) {
     double ev = ops.kyc[H] * vb[H];
 #pragma unroll
     for (int j = 0; j < H; ++j) ev = fma(ops.kye[H][j], e[j], ev);
-    o[H] = fma(ops.w[H], va[H], fma(ops.ca[H], sa, ev));
+    o[H] = fma(ops.wy[H], va[H], fma(ops.cay[H], sa, ev));
   }
 }
 
@@ -160,7 +169,9 @@ __device__ __forceinline__ double y_item_last(const Ops2D& ops, const double (&v
     ev = fma(ops.kye[0][j], e[j], ev);
     od = fma(ops.kyo[0][j], od_[j], od);
   }
-  return fma(ops.w[P - 1], va[P - 1], fma(ops.ca[P - 1], sa, ev - od));
+  if (kOdd) ev = fma(ops.cay[0], sa, ev);
+  else od = fma(ops.cay[0], sa, od);
+  return fma(ops.wy[P - 1], va[P - 1], ev - od);
 }
 
 template <int P, int TC>
@@ -177,7 +188,6 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
   const double* Uc = a.U + on;
   const double* Wc = a.W + on;     // may alias OUTc
   double* OUTc = a.OUT + on;
-  const double* fxc = a.fx + on;
   // The first solve launch may start staging its constant factor blocks now;
   // it waits for this grid (griddepcontrol.wait) before it reads u.
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
@@ -253,8 +263,15 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
   __syncthreads();
   for (int it = tid; it < RY * TC; it += kThreads) {
     const int k = it / RY, yy = it - k * RY;
-    t1[yy * OX + k * p] = tr1[yy * NC + k] + tl1[yy * NC + k + 1];
-    t2[yy * OX + k * p] = tr2[yy * NC + k] + tl2[yy * NC + k + 1];
+    const int gx = X0 + k * p;
+    double v1 = tr1[yy * NC + k] + tl1[yy * NC + k + 1];
+    double v2 = tr2[yy * NC + k] + tl2[yy * NC + k + 1];
+    if (gx == 0 || gx == a.nx - 1) {   // one cell at the grid's edge: its weight is w_0, not 2 w_0
+      v1 *= 2.0;
+      v2 *= 2.0;
+    }
+    t1[yy * OX + k * p] = v1;
+    t2[yy * OX + k * p] = v2;
   }
   __syncthreads();
 
@@ -289,12 +306,16 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
   __syncthreads();
   for (int it = tid; it < TC * OX; it += kThreads) {
     const int k = it / OX, xo = it - k * OX;
-    rr[(k * p) * OX + xo] = rt[k * OX + xo] + rb[(k + 1) * OX + xo];
+    const int gy = Y0 + k * p;
+    double v = rt[k * OX + xo] + rb[(k + 1) * OX + xo];
+    if (gy == 0 || gy == a.ny - 1) v *= 2.0;   // one cell at the grid's edge
+    rr[(k * p) * OX + xo] = v;
   }
   __syncthreads();
 
   // CDM update of the owned I_d nodes (Eqs. CDMacc, CDMstep).
   const double ft = a.ft_dev ? a.ft_dev[0] : a.ft;
+  const double* gxs = a.fxs + on;
   for (int it = tid; it < OY * OX; it += kThreads) {
     const int yo = it / OX, xo = it - yo * OX;
     const int gx = X0 + xo, gy = Y0 + yo;
@@ -303,7 +324,7 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
     if (a.cls[g] != NODE_D) continue;
     const double r = rr[yo * OX + xo];
     const double u = su[(yo + p) * RX + xo + p];
-    OUTc[g] = cdm_node(u, Wc[g], r, fxc[g], ft, a.winv_x[gx], a.ca * a.winv_y[gy], a.cu, a.cw);
+    OUTc[g] = cdm_node(u, Wc[g], r, gxs[g], ft, a.cu, a.cw, a.kappa2);
   }
 }
 
@@ -336,9 +357,8 @@ struct SweepShape {
   static constexpr int XR = NR > P ? NR : P;  // rows of x-pass partials
   static constexpr int SCR = (4 * XR * NC > SR * OXP + 2 * CH * OXP) ? 4 * XR * NC : SR * OXP + 2 * CH * OXP;
   static constexpr int KF = (SR * OXP + kThreads - 1) / kThreads;  // CDM nodes per thread per chunk
-  // u (2 buffers), T1, T2, scratch, carried row (2 buffers), winv_x of the
-  // strip, winv_y (2 buffers)
-  static constexpr int DOUBLES = 2 * SR * RX + 2 * SR * OXP + SCR + 2 * OXP + OXP + 2 * SR;
+  // u (2 buffers), T1, T2, scratch, carried row (2 buffers)
+  static constexpr int DOUBLES = 2 * SR * RX + 2 * SR * OXP + SCR + 2 * OXP;
 };
 
 // Stage rows [gy0, gy0 + nrows) of u (columns X0 - p ... X0 + OX) into su
@@ -363,19 +383,6 @@ __device__ __forceinline__ void sweep_stage(double* su, int r0, const double* Uc
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// Stage n consecutive doubles src[i0 + k] (k < n, zero where i0 + k >= lim)
-// into dst[k] (cp.async, 8 bytes each); not committed.
-__device__ __forceinline__ void sweep_stage_vec(double* dst, const double* src, int i0, int n, int lim) {
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    if (i0 + k < lim) {
-      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + k);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src + i0 + k) : "memory");
-    } else {
-      dst[k] = 0.0;
-    }
-  }
-}
-
 template <int P, int TCX, int CH, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_sweep2d(ExplicitArgs a, Ops2D ops) {
   using S = SweepShape<P, TCX, CH>;
@@ -387,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep2d(ExplicitArgs a, Ops2
   const double* Uc = a.U + on;
   const double* Wc = a.W + on;     // may alias OUTc
   double* OUTc = a.OUT + on;
-  const double* fxc = a.fx + on;
+  const double* gxs = a.fxs + on;   // dt^2 M^{-1} f_x
   // The first solve launch may start staging its constant factor blocks now;
   // it waits for this grid (griddepcontrol.wait) before it reads u.
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
@@ -431,9 +438,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep2d(ExplicitArgs a, Ops2
   double* rt = rb + CH * OXP;                // CH x OXP top-vertex partials
   double* const carry0 = scr + S::SCR;       // OXP: partial row from the cell row below,
   double* const carry1 = carry0 + OXP;       //   two buffers (read, then written, in one phase)
-  double* wxs = carry1 + OXP;                // OXP: winv_x of the strip's columns
-  double* const wy0 = wxs + OXP;             // SR: winv_y of a chunk's rows, two buffers
-  double* const wy1 = wy0 + SR;
 
   const int ncy = a.ncy;
   const int nstrip = (a.ncx + TCX - 1) / TCX;
@@ -491,8 +495,15 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep2d(ExplicitArgs a, Ops2
       const int k = it / nrows, yl = it - k * nrows, yy = r_lo + yl;
       const double r1 = k < TCX ? tl1[yl * NC + k + 1] : 0.0;
       const double r2 = k < TCX ? tl2[yl * NC + k + 1] : 0.0;
-      t1[yy * OXP + k * p] = tr1[yl * NC + k] + r1;
-      t2[yy * OXP + k * p] = tr2[yl * NC + k] + r2;
+      const int gx = cx0 * p + p + k * p;
+      double v1 = tr1[yl * NC + k] + r1;
+      double v2 = tr2[yl * NC + k] + r2;
+      if (gx == 0 || gx == a.nx - 1) {   // one cell at the grid's edge: its weight is w_0, not 2 w_0
+        v1 *= 2.0;
+        v2 *= 2.0;
+      }
+      t1[yy * OXP + k * p] = v1;
+      t2[yy * OXP + k * p] = v2;
     }
     __syncthreads();
   };
@@ -511,13 +522,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep2d(ExplicitArgs a, Ops2
     int cur = 0;
     int c0 = ra;
     int ch = min(CH, rb_ - c0);
-    __syncthreads();   // the previous segment's reads of winv_x are done
-    // Everything the segment's start needs, in one round trip: winv_x of the
-    // strip, winv_y and u of the first chunk's rows and, below a segment
-    // that does not start at the grid's bottom, the P rows of the cell row
-    // below (buffer 1).
-    sweep_stage_vec(wxs, a.winv_x, X0, OXP, a.nx);
-    sweep_stage_vec(wy0, a.winv_y, c0 * p, SR, a.ny);
+    // Everything the segment's start needs, in one round trip: u of the
+    // first chunk's rows and, below a segment that does not start at the
+    // grid's bottom, the P rows of the cell row below (buffer 1).
     if (ra == 0) sweep_stage<RX>(ub0, 0, Uc, 0, ch * p + 1, X0, p, a.nx);
     else {
       sweep_stage<RX>(ub1, 0, Uc, (ra - 1) * p, P, X0, p, a.nx);
@@ -555,14 +562,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep2d(ExplicitArgs a, Ops2
     while (ch > 0) {
       double* const su = cur ? ub1 : ub0;
       double* const sn = cur ? ub0 : ub1;
-      const double* const wyc = cur ? wy1 : wy0;
       const double* const carry = cur ? carry1 : carry0;
       double* const carry_next = cur ? carry0 : carry1;
       const int c1 = c0 + ch;
       const int chn = min(CH, rb_ - c1);         // next chunk's cell rows
       const bool top = c1 == ncy;                 // the grid's top row is final too
       const int nfin = ch * p + (top ? 1 : 0);
-      // The CDM update's inputs of this thread's nodes (u_{n-1}, f_x, class),
+      // The CDM update's inputs of this thread's nodes (u_{n-1}, scaled f_x, class),
       // loaded now so that they arrive while the passes run.
       double pw[KF], pf[KF];
       int pcl[KF];
@@ -576,13 +582,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep2d(ExplicitArgs a, Ops2
           const size_t g = (size_t)(c0 * p + yl) * a.nx + X0 + xo;
           pcl[q] = a.cls[g];
           pw[q] = Wc[g];
-          pf[q] = fxc[g];
+          pf[q] = gxs[g];
         }
       }
-      if (chn > 0) {
-        sweep_stage_vec(cur ? wy0 : wy1, a.winv_y, c1 * p, SR, a.ny);
-        sweep_stage<RX>(sn, 1, Uc, c1 * p + 1, chn * p, X0, p, a.nx);
-      }
+      if (chn > 0) sweep_stage<RX>(sn, 1, Uc, c1 * p + 1, chn * p, X0, p, a.nx);
       xpass(su, 1, ch * p, cx0);
       // y pass: item = (column xo, cell row k), columns fastest.
       for (int it = tid; it < ocols * ch; it += kThreads) {
@@ -617,11 +620,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep2d(ExplicitArgs a, Ops2
         } else if (k < ch) {
           const double below = k == 0 ? carry[xo] : rt[(k - 1) * OXP + xo];
           r = below + rb[k * OXP + xo];
-        } else {   // the grid's top row: nothing above
-          r = rt[(k - 1) * OXP + xo];
+          if (c0 == 0 && k == 0) r *= 2.0;   // one cell at the grid's bottom edge
+        } else {   // the grid's top row: nothing above (one cell: doubled)
+          r = 2.0 * rt[(k - 1) * OXP + xo];
         }
         const double u = su[yl * RX + xo + p];
-        OUTc[g] = cdm_node(u, pw[q], r, pf[q], ft, wxs[xo], a.ca * wyc[yl], a.cu, a.cw);
+        OUTc[g] = cdm_node(u, pw[q], r, pf[q], ft, a.cu, a.cw, a.kappa2);
       }
       if (!top)
         for (int xo = tid; xo < ocols; xo += kThreads) carry_next[xo] = rt[(ch - 1) * OXP + xo];
