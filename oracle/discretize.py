@@ -160,8 +160,15 @@ def shape_functions(p, xr, h):
     return N, G
 
 
-def element_from_points(p, h, xr, wr, alpha_q, rho, c, fvals):
-    """K_e, M_e, f_e from quadrature points (Eqs. Mglobal, K, f restricted to one cell)."""
+def element_from_points(p, h, xr, wr, alpha_q, rho, c, fvals, reverse=False):
+    """K_e, M_e, f_e from quadrature points (Eqs. Mglobal, K, f restricted to one cell).
+
+    reverse: sum over the points in reverse order (the same integral, other
+    roundoff; the parity tests use it to sample the rounding spread of the
+    assembled system)."""
+    if reverse:
+        xr, wr, alpha_q = xr[::-1], wr[::-1], np.asarray(alpha_q)[::-1]
+        fvals = None if fvals is None else np.asarray(fvals)[::-1]
     N, G = shape_functions(p, xr, h)
     jac = np.prod(h / 2.0)
     wq = wr * jac * alpha_q
@@ -173,16 +180,16 @@ def element_from_points(p, h, xr, wr, alpha_q, rho, c, fvals):
     return Ke, Me, fe
 
 
-def uncut_element(p, h, rho, c, box_lo, fx):
+def uncut_element(p, h, rho, c, box_lo, fx, reverse=False):
     """Uncut cell: GL stiffness and load, GLL (diagonal) mass."""
     dim = len(h)
     xg, wg = basis.gauss_points(p + 1)
     xr, wr = tensor_points(xg, wg, dim)
     fv = fx(box_lo + (xr + 1.0) / 2.0 * h) if fx is not None else None
-    Ke, _, fe = element_from_points(p, h, xr, wr, np.ones(len(xr)), rho, c, fv)
+    Ke, _, fe = element_from_points(p, h, xr, wr, np.ones(len(xr)), rho, c, fv, reverse)
     xl, wl = basis.gll_points(p)
     xr2, wr2 = tensor_points(xl, wl, dim)
-    _, Me, _ = element_from_points(p, h, xr2, wr2, np.ones(len(xr2)), rho, c, None)
+    _, Me, _ = element_from_points(p, h, xr2, wr2, np.ones(len(xr2)), rho, c, None, reverse)
     return Ke, Me, fe
 
 
@@ -205,12 +212,14 @@ def all_cell_nodes(grid):
     return cells, ids
 
 
-def discretize(grid, geom, alpha, depth, rho=1.0, c0=1.0, cell_c=None, fx=None):
+def discretize(grid, geom, alpha, depth, rho=1.0, c0=1.0, cell_c=None, fx=None, quad_reverse=False):
     """Build the assembled system for all non-empty cells of `grid`.
 
     geom: object with physical(x) and classify_box(lo, hi) (Holes / HalfSpace).
     cell_c: optional per-cell wave speed (flat cell order), default c0 everywhere.
     fx: callable, spatial load f_x(x) for points (n, dim), or None.
+    quad_reverse: every element's quadrature summed in reverse point order
+    (the same system up to roundoff, about 1e-15 of max |K|).
 
     Uncut cells all share one reference element: their K_e (c^2-scaled) and
     GLL mass are computed once, and their loads f_e = sum_q w_q |J| f(x_q) N(x_q)
@@ -234,7 +243,7 @@ def discretize(grid, geom, alpha, depth, rho=1.0, c0=1.0, cell_c=None, fx=None):
     # Uncut cells: one reference element, scaled by c_e^2 for the stiffness.
     uncut = np.flatnonzero(ctype == UNCUT)
     if len(uncut):
-        Ke1, Me1, _ = uncut_element(p, grid.h, rho, 1.0, np.zeros(dim), None)
+        Ke1, Me1, _ = uncut_element(p, grid.h, rho, 1.0, np.zeros(dim), None, quad_reverse)
         xg, wg = basis.gauss_points(p + 1)
         xr, wr = tensor_points(xg, wg, dim)
         Nq, _ = shape_functions(p, xr, grid.h)                   # (P^d points, P^d basis)
@@ -263,7 +272,7 @@ def discretize(grid, geom, alpha, depth, rho=1.0, c0=1.0, cell_c=None, fx=None):
             continue
         aq = np.where(phys, 1.0, alpha)
         fv = fx(lo + (xr + 1.0) / 2.0 * grid.h) if fx is not None else None
-        Ke, Me, fe = element_from_points(p, grid.h, xr, wr, aq, rho, float(speed[cid]), fv)
+        Ke, Me, fe = element_from_points(p, grid.h, xr, wr, aq, rho, float(speed[cid]), fv, quad_reverse)
         ids = nodes[cid]
         rr, cc = np.meshgrid(ids, ids, indexing="ij")
         rows.append(rr.ravel())

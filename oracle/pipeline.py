@@ -27,12 +27,19 @@ class Setup:
 
 def setup(dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0,
           src_sigma, src_amp=10.0, wavelet=sources.RICKER, rho=1.0, c0=1.0,
-          cell_c=None, dt=0.0, dt_factor=0.9, geom=None):
-    """Discretise one workload and build its IMEX integrator (one source column)."""
+          cell_c=None, dt=0.0, dt_factor=0.9, geom=None, quad_reverse=False):
+    """Discretise one workload and build its IMEX integrator (one source column).
+
+    quad_reverse: sum every element quadrature in reverse point order (the
+    same system up to roundoff; see discretize).  The arguments are kept as
+    Setup.args so that the same workload can be set up again."""
+    args = dict(dim=dim, lo=lo, hi=hi, ncells=ncells, p=p, alpha=alpha, depth=depth, holes=holes,
+                src_pos=src_pos, f0=f0, src_sigma=src_sigma, src_amp=src_amp, wavelet=wavelet,
+                rho=rho, c0=c0, cell_c=cell_c, dt=dt, dt_factor=dt_factor, geom=geom)
     grid = Grid(lo, hi, ncells, p)
     geom = Holes(holes, dim) if geom is None else geom
     fx = sources.bell(src_pos, src_sigma, src_amp)
-    disc = discretize(grid, geom, alpha, depth, rho, c0, cell_c, fx)
+    disc = discretize(grid, geom, alpha, depth, rho, c0, cell_c, fx, quad_reverse)
     if dt <= 0:
         if cell_c is None:
             cmax = c0
@@ -42,6 +49,7 @@ def setup(dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0,
     ft = sources.wavelet(wavelet, f0)
     s = Setup()
     s.grid, s.disc, s.dt, s.ft, s.geom = grid, disc, dt, ft, geom
+    s.args = args
     s.imex = NewmarkImex(disc.M, disc.K, disc.fx, ft, dt, disc.is_c, disc.is_d)
     return s
 

@@ -1,4 +1,22 @@
-"""Shared parity checks of a GPU state against an oracle run (see test_gpu_parity)."""
+"""Shared parity checks of a GPU state against an oracle run.
+
+The gate on all active DOFs (fictitious nodes included) is relative to the
+spread of correct FP64 answers, the "rounding floor": the largest
+disagreement between the reference oracle run and oracle runs that evaluate
+the same method in another correct FP64 way,
+  * the implicit systems factorised with another sparse ordering (three), and
+  * the system assembled with every element quadrature summed in reverse
+    point order (the same K and M up to about 1e-15 of max |K|).
+S = M^cc + dt^2/4 K^cc is ill-conditioned for alpha = 1e-5, and a
+perturbation of the cut-cell matrices at roundoff level is a large relative
+change of their alpha-scaled fictitious entries; the weakly coupled
+fictitious medium keeps it as a phase drift that grows with the step count.
+On the 16x16 plate with 64 sources (f0 = 20) after 2000 steps, the reversed
+quadrature alone moves the oracle by 4.0e-10 on all active DOFs and 3.4e-12
+on physical DOFs, while another sparse ordering moves it by 1.8e-11: an
+independent assembly (the library's, in C++) cannot be judged against the
+ordering spread alone.
+"""
 import numpy as np
 
 from oracle import pipeline
@@ -11,59 +29,69 @@ def phys_mask(s, holes):
 
 
 ORDERINGS = ("NATURAL", "MMD_ATA", "MMD_AT_PLUS_A")
-DENSE_INVERSE_MAX = 4000   # implicit DOFs up to which the explicit-inverse variant runs
+
+# Gates: all active DOFs <= max(1e-11, FLOOR_FACTOR x floor); physical DOFs
+# relative L2 <= 1e-11; per-node max |u - u_ref| over physical DOFs <=
+# max(1e-11, FLOOR_FACTOR x its floor) x max |u_ref| there.
+FLOOR_FACTOR = 10.0
 
 
-class _InverseSolve:
-    """x = A^{-1} b with the explicitly inverted matrix (a correct FP64 solve
-    of another algorithm class than the sparse LU)."""
-
-    def __init__(self, lu, n):
-        self.inv = lu.solve(np.eye(n))      # A^{-1}, column by column
-
-    def solve(self, b):
-        return self.inv @ b
+def reversed_quadrature_setup(s):
+    """The same workload (and time step) assembled with reversed quadrature sums."""
+    return pipeline.setup(**{**s.args, "dt": s.dt}, quad_reverse=True)
 
 
-def ordering_floor(s, ref, nsteps, u0=None, v0=None):
-    """Spread of correct answers on the active DOFs: the largest relative L2
-    disagreement between the reference run and runs that differ only in how
-    the implicit systems are solved: other sparse orderings of the LU and,
-    for small implicit partitions, the explicit inverse of the matrices."""
+def _maxabs(u, ref, mask):
+    den = np.abs(ref[mask]).max() if mask.any() else 0.0
+    d = np.abs(u[mask] - ref[mask]).max() if mask.any() else 0.0
+    return float(d / den) if den > 0 else float(d)
+
+
+class Floor:
+    """Rounding floor of one case: relative L2 over all active DOFs and the
+    relative per-node max over physical DOFs."""
+
+    def __init__(self):
+        self.all = 0.0
+        self.maxabs = 0.0
+        self.parts = {}
+
+    def add(self, name, u, ref_u, s, holes):
+        a = pipeline.relative_l2(u, ref_u, s.disc.active)
+        m = _maxabs(u, ref_u, phys_mask(s, holes))
+        self.parts[name] = (a, m)
+        self.all = max(self.all, a)
+        self.maxabs = max(self.maxabs, m)
+
+
+def rounding_floor(s, ref, nsteps, holes, u0=None, v0=None):
+    """Floor of the method (Fig. TrapCDMIMEX) on setup s, reference run ref."""
     d = s.disc
-    fl = 0.0
+    fl = Floor()
     for spec in ORDERINGS:
         alt = NewmarkImex(d.M, d.K, d.fx, s.ft, s.dt, d.is_c, d.is_d, permc_spec=spec)
-        fl = max(fl, pipeline.relative_l2(alt.run(nsteps, u0=u0, v0=v0).u, ref.u, d.active))
-    nc = int(np.count_nonzero(d.is_c))
-    if 0 < nc <= DENSE_INVERSE_MAX:
-        alt = NewmarkImex(d.M, d.K, d.fx, s.ft, s.dt, d.is_c, d.is_d)
-        alt.S_lu = _InverseSolve(alt.S_lu, nc)
-        alt.Mcc_lu = _InverseSolve(alt.Mcc_lu, nc)
-        fl = max(fl, pipeline.relative_l2(alt.run(nsteps, u0=u0, v0=v0).u, ref.u, d.active))
+        fl.add(spec, alt.run(nsteps, u0=u0, v0=v0).u, ref.u, s, holes)
+    r = reversed_quadrature_setup(s)
+    fl.add("reversed quadrature", r.imex.run(nsteps, u0=u0, v0=v0).u, ref.u, s, holes)
     return fl
 
 
-# Gate on all active DOFs (fictitious nodes included) as a multiple of the
-# spread of correct FP64 answers: S = M^cc + dt^2/4 K^cc is ill-conditioned
-# (alpha = 1e-5), so fictitious-node values depend on how the implicit systems
-# are solved; the device solve composes inverted diagonal blocks with an
-# explicitly inverted dense top, two inverse-based stages where each variant
-# in the spread uses one method.
-FLOOR_FACTOR = 30.0
-
-
-def check_state(s, ref, st, holes, alpha, nsteps, use_floor=True):
-    """Relative L2 gates: physical DOFs <= 1e-11, all active <= max(1e-11,
-    FLOOR_FACTOR x floor), CDM history and c-partition velocity/acceleration."""
+def check_state(s, ref, st, holes, alpha, nsteps, use_floor=True, u0=None, v0=None, floor=None):
+    """Gates: physical DOFs relative L2 <= 1e-11; per-node max over physical
+    DOFs and all active DOFs within FLOOR_FACTOR x the rounding floor (at
+    least 1e-11); CDM history and c-partition velocity/acceleration."""
     act = s.disc.active
     phys = phys_mask(s, holes)
     e_phys = pipeline.relative_l2(st["u"], ref.u, phys)
     e_all = pipeline.relative_l2(st["u"], ref.u, act)
-    tol_all = 1e-11
+    m_phys = _maxabs(st["u"], ref.u, phys)
+    tol_all = tol_max = 1e-11
     if use_floor and s.disc.is_c.any() and alpha < 1.0:
-        tol_all = max(1e-11, FLOOR_FACTOR * ordering_floor(s, ref, nsteps))
+        fl = floor if floor is not None else rounding_floor(s, ref, nsteps, holes, u0, v0)
+        tol_all = max(1e-11, FLOOR_FACTOR * fl.all)
+        tol_max = max(1e-11, FLOOR_FACTOR * fl.maxabs)
     assert e_phys <= 1e-11, (e_phys, e_all)
+    assert m_phys <= tol_max, (m_phys, tol_max)
     assert e_all <= tol_all, (e_all, tol_all)
     if s.disc.is_d.any():
         assert pipeline.relative_l2(st["u_prev_d"], ref.u_prev_d, s.disc.is_d) <= max(tol_all, 1e-11)
@@ -72,3 +100,34 @@ def check_state(s, ref, st, holes, alpha, nsteps, use_floor=True):
         assert pipeline.relative_l2(st["v_c"], ref.v_c, cphys) <= 1e-10
         assert pipeline.relative_l2(st["a_c"], ref.a_c, cphys) <= 1e-10
     return e_phys, e_all
+
+
+# --- oracle runs in spawned worker processes (the full-size workloads) -----
+
+def _variant_run(args):
+    """Worker: one oracle run of a workload (kwargs) for nsteps, in one of the
+    floor's variants; returns the final ImexState fields."""
+    kw, nsteps, variant, dt = args
+    kw = dict(kw, dt=dt)
+    s = pipeline.setup(**kw, quad_reverse=(variant == "reversed quadrature"))
+    d = s.disc
+    if variant in ORDERINGS:
+        im = NewmarkImex(d.M, d.K, d.fx, s.ft, s.dt, d.is_c, d.is_d, permc_spec=variant)
+    else:
+        im = s.imex
+    st = im.run(nsteps)
+    return variant, {"u": st.u, "u_prev_d": st.u_prev_d, "v_c": st.v_c, "a_c": st.a_c}
+
+
+def parallel_reference_and_floor(kw, dt, nsteps, workers=5):
+    """Reference run and every floor variant of a workload, each in its own
+    spawned process (spawn: safe next to an initialised CUDA context).
+    Returns (reference fields, {variant: fields})."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    variants = ("reference",) + ORDERINGS + ("reversed quadrature",)
+    with ProcessPoolExecutor(max_workers=min(workers, len(variants)),
+                             mp_context=mp.get_context("spawn")) as ex:
+        out = dict(ex.map(_variant_run, [(kw, nsteps, v, dt) for v in variants]))
+    ref = out.pop("reference")
+    return ref, out
