@@ -1904,6 +1904,7 @@ void mass_scaled_ops(const HostSetup& hs, double kappa, Ops2D& ops) {
     ops.wy[i] = kappa * f[i] * ops.w[i];
     ops.cay[i] = kappa * f[i] * ops.ca[i];
   }
+  ops.wyv = kappa;
 }
 
 int explicit_ops3(const HostSetup& hs, const double* s3, Ops3D& ops) {

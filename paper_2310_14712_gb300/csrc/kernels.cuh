@@ -58,12 +58,15 @@ __host__ __device__ inline double wavelet_value(int kind, double f0, double t) {
 //           v_i + cax_i (a^T v), vertex rows v_i / 2 + cax_i (a^T v),
 //   y pass  A = kappa f (x) sy K1 (kye, kyo, kyc),  M1 -> kappa f M1:
 //           wy_i v_i + cay_i (a^T v).
+// At a vertex the two cells' halves of the nodal term go to one cell (the
+// x pass's last node: v; the y pass's last node: wyv = kappa times v).
 // (3D builds its Ops3D from the unscaled form: w, ca.)
 struct Ops2D {
   double kxe[5][4], kxo[4][4], kxc[5];
   double kye[5][4], kyo[4][4], kyc[5];
   double w[9], ca[9], a[9];
   double cax[9], wy[9], cay[9];
+  double wyv;   // kappa: the whole nodal mass share of a vertex in y (split asymmetrically)
 };
 
 // 1D operators of the 3D explicit apply:

@@ -47,8 +47,14 @@ __device__ __forceinline__ double cdm_node(double u, double w, double r, double 
 // differs from a polynomial it integrates exactly by a_i a_j x^{2p}, a_i the
 // leading coefficient of the i-th basis function), so M1 v costs about 3P.
 // The coefficients carry the inverse lumped mass and dt^2 (Ops2D), so r is
-// dt^2 M^{-1} K u at explicit nodes.  Every 2D explicit kernel calls these,
-// so their results agree bit for bit.
+// dt^2 M^{-1} K u at explicit nodes.  The diagonal (nodal) mass term of a
+// vertex shared by two cells is split asymmetrically: the cell on the low
+// side adds all of it (its last node: v, or kappa va in y), the cell on the
+// high side none (its first node: only the rank-one term), so each vertex
+// output costs one FP64 operation less; at the grid's edge, where one cell
+// holds the vertex, the fix-ups restore twice the half share exactly
+// (2 sum + v at the low edge, 2 sum - v at the high edge).  Every 2D
+// explicit kernel calls these, so their results agree bit for bit.
 
 // x pass: o1 = (sx K1) v, o2 = M1 v.
 template <int P>
@@ -83,7 +89,7 @@ __device__ __forceinline__ void x_item(const Ops2D& ops, const double (&v)[P], d
   for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? e[j] : o[j], sa);
 #pragma unroll
   for (int i = 0; i < P; ++i)
-    o2[i] = (i == 0 || i == P - 1) ? fma(0.5, v[i], ops.cax[i] * sa) : fma(ops.cax[i], sa, v[i]);
+    o2[i] = i == 0 ? ops.cax[0] * sa : fma(ops.cax[i], sa, v[i]);   // vertex mass split, see below
 }
 
 // The same, last node only (o1[P-1], o2[P-1]): the right vertex of a cell
@@ -108,7 +114,7 @@ __device__ __forceinline__ void x_item_last(const Ops2D& ops, const double (&v)[
   double sa = kOdd ? ops.a[H] * v[H] : 0.0;
 #pragma unroll
   for (int j = 0; j < H; ++j) sa = fma(ops.a[j], kOdd ? e[j] : o[j], sa);
-  o2p = fma(0.5, v[P - 1], ops.cax[P - 1] * sa);
+  o2p = fma(ops.cax[P - 1], sa, v[P - 1]);
 }
 
 // y pass: o = M1 va + (sy K1) vb.
@@ -138,8 +144,13 @@ __device__ __forceinline__ void y_item(const Ops2D& ops, const double (&va)[P], 
     if (kOdd) ev = fma(ops.cay[i], sa, ev);
     else od = fma(ops.cay[i], sa, od);
     const int k = P - 1 - i;
-    o[i] = fma(ops.wy[i], va[i], ev + od);
-    o[k] = fma(ops.wy[k], va[k], ev - od);
+    if (i == 0) {   // vertex mass split, see below
+      o[0] = ev + od;
+      o[k] = fma(ops.wyv, va[k], ev - od);
+    } else {
+      o[i] = fma(ops.wy[i], va[i], ev + od);
+      o[k] = fma(ops.wy[k], va[k], ev - od);
+    }
   }
   if (kOdd) {
     double ev = ops.kyc[H] * vb[H];
@@ -171,7 +182,7 @@ __device__ __forceinline__ double y_item_last(const Ops2D& ops, const double (&v
   }
   if (kOdd) ev = fma(ops.cay[0], sa, ev);
   else od = fma(ops.cay[0], sa, od);
-  return fma(ops.wy[P - 1], va[P - 1], ev - od);
+  return fma(ops.wyv, va[P - 1], ev - od);
 }
 
 template <int P, int TC>
@@ -267,8 +278,9 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
     double v1 = tr1[yy * NC + k] + tl1[yy * NC + k + 1];
     double v2 = tr2[yy * NC + k] + tl2[yy * NC + k + 1];
     if (gx == 0 || gx == a.nx - 1) {   // one cell at the grid's edge: its weight is w_0, not 2 w_0
+      const double u = su[yy * RX + k * p + p];
       v1 *= 2.0;
-      v2 *= 2.0;
+      v2 = gx == 0 ? fma(2.0, v2, u) : fma(2.0, v2, -u);
     }
     t1[yy * OX + k * p] = v1;
     t2[yy * OX + k * p] = v2;
@@ -308,7 +320,10 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
     const int k = it / OX, xo = it - k * OX;
     const int gy = Y0 + k * p;
     double v = rt[k * OX + xo] + rb[(k + 1) * OX + xo];
-    if (gy == 0 || gy == a.ny - 1) v *= 2.0;   // one cell at the grid's edge
+    if (gy == 0 || gy == a.ny - 1) {   // one cell at the grid's edge
+      const double ka = ops.wyv * t1[((k + 1) * p) * OX + xo];
+      v = gy == 0 ? fma(2.0, v, ka) : fma(2.0, v, -ka);
+    }
     rr[(k * p) * OX + xo] = v;
   }
   __syncthreads();
@@ -499,8 +514,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep2d(ExplicitArgs a, Ops2
       double v1 = tr1[yl * NC + k] + r1;
       double v2 = tr2[yl * NC + k] + r2;
       if (gx == 0 || gx == a.nx - 1) {   // one cell at the grid's edge: its weight is w_0, not 2 w_0
+        const double u = su[yy * RX + k * p + p];
         v1 *= 2.0;
-        v2 *= 2.0;
+        v2 = gx == 0 ? fma(2.0, v2, u) : fma(2.0, v2, -u);
       }
       t1[yy * OXP + k * p] = v1;
       t2[yy * OXP + k * p] = v2;
@@ -620,9 +636,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep2d(ExplicitArgs a, Ops2
         } else if (k < ch) {
           const double below = k == 0 ? carry[xo] : rt[(k - 1) * OXP + xo];
           r = below + rb[k * OXP + xo];
-          if (c0 == 0 && k == 0) r *= 2.0;   // one cell at the grid's bottom edge
-        } else {   // the grid's top row: nothing above (one cell: doubled)
-          r = 2.0 * rt[(k - 1) * OXP + xo];
+          if (c0 == 0 && k == 0) r = fma(2.0, r, ops.wyv * t1[xo]);   // one cell at the grid's bottom edge
+        } else {   // the grid's top row: nothing above (one cell)
+          r = fma(2.0, rt[(k - 1) * OXP + xo], -(ops.wyv * t1[(k * p) * OXP + xo]));
         }
         const double u = su[yl * RX + xo + p];
         OUTc[g] = cdm_node(u, pw[q], r, pf[q], ft, a.cu, a.cw, a.kappa2);
