@@ -128,6 +128,9 @@ typedef struct {
                                     more CTAs per SM (2D; autotuned at setup) */
   double explicit_sweep_us;      /* setup timing of variant 2 (as the tile timings) */
   double explicit_sweep_short_us;/* setup timing of variant 3 */
+  int64_t large_supernodes;      /* walked supernodes of more than 256 diagonal or ancestor rows,
+                                    solved by row chunks over many CTAs */
+  int64_t max_rows;              /* largest ancestor row set of a supernode */
 } imex_stats;
 
 /*
@@ -270,14 +273,16 @@ int imex_step_io(imex_ctx *ctx, int64_t n, const double *ft_samples, const int64
  * not allocate device memory while they run: it makes no allocation of any
  * kind.  The scratch of the factorised implicit solve (the descendant update
  * vectors, the solution vector and the right-hand sides, each column after
- * column) is not taken from the context but from one fixed 2 MiB array
+ * column; with supernodes of more than 256 rows also the backward products)
+ * is not taken from the context but from one fixed 2 MiB array
  * (262,144 doubles) compiled into the library, which every GPU that loads
  * the library keeps until the process exits.  Typical callers run under a
  * device-memory budget fixed at start-up or inside code regions where
  * allocation calls are not permitted.
  *   - Capacity: with U = the context's update-vector length and n_c its
  *     implicit DOFs, each rounded up to even, a problem fits when
- *     (U + 2 n_c) x ncols <= 262,144; larger problems are rejected with
+ *     (U + 2 n_c) x ncols <= 262,144 ((U + 3 n_c) x ncols when the factor has
+ *     supernodes of more than 256 rows); larger problems are rejected with
  *     IMEX_ERR_ARG before anything is launched.
  *   - Contexts only: factorised (not imex_setup_pcg) and with the direct
  *     solver (imex_set_solver: IMEX_SOLVER_DIRECT, the default); the PCG

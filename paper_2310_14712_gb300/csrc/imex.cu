@@ -687,6 +687,15 @@ struct imex_ctx {
   double *zA_S = nullptr, *zA_M = nullptr;
   int64_t nzrow = 0;
   double *upd = nullptr, *sol = nullptr;
+  // large supernodes of the walked levels (k_panel)
+  int *pan_desc = nullptr, *pan_idx = nullptr;
+  int64_t* pan_aoff = nullptr;
+  double *panS = nullptr, *panM = nullptr, *hbuf = nullptr;
+  std::vector<int> pan_cta0, pan_ncta;   // [4 level + phase]
+  int64_t pan_max_chunk = 2;
+  int pan_max_nv = 2;
+  size_t smem_panel = 0;
+  int64_t n_large = 0;   // supernodes walked by k_panel
   // host I/O (imex_step_io): rings of kIoRing slots for the source samples
   // (2 doubles each) and the receiver values (io_cap * ncols each), filled and
   // drained on two copy streams, with events guarding slot reuse
@@ -997,7 +1006,8 @@ int pred_blocks(imex_ctx* c, bool predict) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(spare, (c->hs.n_c + kThreads - 1) / kThreads));
 }
 
-constexpr int kMaxWidth = 256;                 // largest supernode / row set of the walk
+constexpr int kMaxWidth = 256;                 // largest supernode / row set one walk CTA takes
+constexpr int64_t kPanelChunk = 12288;         // doubles of a k_panel chunk (96 KB of shared memory)
 constexpr size_t kWalkSmemBudget = 200 * 1024;  // shared memory per walk CTA (staged factor)
 constexpr size_t kTopSmemBudget = 200 * 1024;   // shared memory per dense-top CTA
 constexpr size_t kMaxDynSmem = 220 * 1024;      // dynamic shared memory limit we set (static use < 7 KB)
@@ -1008,8 +1018,9 @@ constexpr size_t kMaxDynSmem = 220 * 1024;      // dynamic shared memory limit w
 // or of M^cc (initial acceleration, mode 1).  upd/sol/rhs0 are the solve's
 // scratch vectors.
 cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double* ft_dev, int mode, double* Ubuf,
-                               const double* src, double* upd, double* sol, double* rhs0, cudaStream_t s,
-                               const int* skip = nullptr, bool rhs_only = false, bool rhs_given = false) {
+                               const double* src, double* upd, double* sol, double* rhs0, double* hbuf,
+                               cudaStream_t s, const int* skip = nullptr, bool rhs_only = false,
+                               bool rhs_given = false) {
   const HostSetup& hs = c->hs;
   WalkArgs w{};
   w.blob = use_S ? c->blob_S : c->blob_M;
@@ -1097,19 +1108,56 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
       return fwd ? cudaLaunchKernelEx(&cfg, k_walk<true, true>, w) : cudaLaunchKernelEx(&cfg, k_walk<false, true>, w);
     return fwd ? cudaLaunchKernelEx(&cfg, k_walk<true, false>, w) : cudaLaunchKernelEx(&cfg, k_walk<false, false>, w);
   };
+  PanelArgs pa{};
+  pa.desc = c->pan_desc;
+  pa.a_off = c->pan_aoff;
+  pa.A = use_S ? c->panS : c->panM;
+  pa.idx = c->pan_idx;
+  pa.max_chunk = c->pan_max_chunk;
+  pa.max_nv = c->pan_max_nv;
+  pa.skip = skip;
+  pa.rhs0 = rhs0;
+  pa.upd = upd;
+  pa.sol = sol;
+  pa.hbuf = hbuf;
+  pa.mode = mode;
+  pa.c_node = c->c_node;
+  pa.U = Ubuf;
+  pa.Un = src;
+  pa.v_c = c->v_c;
+  pa.a_c = c->a_c;
+  pa.dt = hs.dt;
+  pa.cs_node = w.cs_node;
+  pa.cs_c = w.cs_c;
+  pa.cs_upd = w.cs_upd;
+  auto panel = [&](int l, int phase) {
+    const int n = c->pan_ncta.empty() ? 0 : c->pan_ncta[4 * l + phase];
+    if (n == 0) return cudaSuccess;
+    pa.cta0 = c->pan_cta0[4 * l + phase];
+    cfg.gridDim = dim3(n, c->ncols);
+    cfg.dynamicSmemBytes = c->smem_panel;
+    return cudaLaunchKernelEx(&cfg, k_panel, pa);
+  };
   cudaError_t e = cudaSuccess;
   if (rhs_only) {   // the first forward launch forms every right-hand side into rhs0, nothing else
     w.rhs_only = 1;
     return walk(0, true);
   }
-  for (int l = 0; l < nlev && e == cudaSuccess; ++l) e = walk(l, true);
+  // Per walked level: the walk of its small supernodes, then the two
+  // forward phases of its large ones (k_panel); backwards in reverse.
+  for (int l = 0; l < nlev && e == cudaSuccess; ++l) {
+    if (l == 0 || c->lev_ncta[l] > 0) e = walk(l, true);
+    for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph) e = panel(l, ph);
+  }
   if (e == cudaSuccess && c->ntop > 0) {
     cfg.gridDim = dim3(c->ntop, c->ncols);
     cfg.dynamicSmemBytes = c->smem_top;
     e = cudaLaunchKernelEx(&cfg, k_top, z);
   }
-  for (int l = nlev - 1; l >= 0 && e == cudaSuccess; --l)
-    if (c->lev_has_nodes[l]) e = walk(l, false);
+  for (int l = nlev - 1; l >= 0 && e == cudaSuccess; --l) {
+    for (int ph = 2; ph < 4 && e == cudaSuccess; ++ph) e = panel(l, ph);
+    if (e == cudaSuccess && c->lev_has_nodes[l]) e = walk(l, false);
+  }
   return e;
 }
 
@@ -1118,8 +1166,10 @@ int64_t launches_per_step(const imex_ctx* c) {
   int64_t n = 1;   // explicit apply
   if (c->hs.n_c > 0 && !c->factorized) return n + 2;   // right-hand sides, PCG
   if (c->hs.n_c > 0) {
-    n += (int64_t)c->lev_cta0.size() + (c->ntop > 0 ? 1 : 0);
+    for (size_t l = 0; l < c->lev_cta0.size(); ++l) n += (l == 0 || c->lev_ncta[l] > 0) ? 1 : 0;
+    n += c->ntop > 0 ? 1 : 0;
     for (int h : c->lev_has_nodes) n += h;
+    for (int k : c->pan_ncta) n += k > 0 ? 1 : 0;
     if (c->solver != IMEX_SOLVER_DIRECT) n += 2;   // right-hand sides, PCG (the direct launches follow, skipped)
   }
   return n;
@@ -1235,7 +1285,7 @@ int compute_initial(imex_ctx* c, cudaStream_t s) {
       launch_rhs_c(c, ft0, U0, s);
       if (cudaError_t e = launch_pcg(c, U0, s, true))
         return fail(IMEX_ERR_CUDA, std::string("PCG (initial): ") + cudaGetErrorString(e));
-    } else if (cudaError_t e = launch_solve_chain(c, false, ft0, nullptr, 1, U0, U0, c->upd, c->sol, c->rhs0, s))
+    } else if (cudaError_t e = launch_solve_chain(c, false, ft0, nullptr, 1, U0, U0, c->upd, c->sol, c->rhs0, c->hbuf, s))
       return fail(IMEX_ERR_CUDA, std::string("solve (initial): ") + cudaGetErrorString(e));
     if (int rc = check_launch("solve (initial)")) return rc;
     if (scheme_is_cdm(hs.pb.scheme)) {   // the central-difference history of I_c as well
@@ -1282,6 +1332,16 @@ struct SolvePlan {
   std::vector<int64_t> zA_off;
   std::vector<double> zA_S, zA_M;
   int max_zn = 0;
+  // Large supernodes of the walked levels (k_panel): per CTA a descriptor
+  // (8 ints), the offset of its chunk in panS / panM, and its index list;
+  // per level and phase (0..3) the CTA range.
+  std::vector<int> pan_desc, pan_idx;
+  std::vector<int64_t> pan_aoff;
+  std::vector<double> panS, panM;
+  std::vector<int> pan_cta0, pan_ncta;   // [4 level + phase]
+  int64_t pan_max_chunk = 2;
+  int pan_max_nv = 2;
+  int64_t n_large = 0;
 };
 
 #ifndef IMEX_DENSE_TOP_MAX
@@ -1348,6 +1408,73 @@ int interface_rows(const HostSetup& hs, std::vector<double>& Krows, std::vector<
     if_base[e] = (int)base;
     if (hs.if_kidx[e] < 0) if_sc[e] = hs.if_c2[e];
   }
+  return IMEX_OK;
+}
+
+// Row chunks of the large supernodes `big` of walked level l, for both
+// factors (S and M^cc), in the four k_panel phases (PanelArgs): forward
+// y = L_tt^{-1} g and upd = L_{rows,t} y, backward h = y - L_{rows,t}^T x_rows
+// and x = L_tt^{-T} h.  Chunks hold at most kPanelChunk doubles and at most
+// kThreads rows; the triangular blocks keep only their nonzero columns.
+int plan_panels(const HostSetup& hs, const std::vector<int>& big, int l, SolvePlan& P) {
+  auto rows_per = [](int64_t nv) { return (int)std::max<int64_t>(1, std::min<int64_t>(kThreads, kPanelChunk / std::max<int64_t>(nv, 1))); };
+  for (int phase = 0; phase < 4; ++phase) {
+    P.pan_cta0[4 * l + phase] = (int)P.pan_aoff.size();
+    int ncta = 0;
+    for (int t : big) {
+      const TreeNode& T = hs.tree[t];
+      const int b = T.end - T.beg, m = (int)T.rows.size();
+      const int nout = phase == 1 ? m : b;
+      const int step = rows_per(phase == 2 ? m : b);
+      for (int r0 = 0; r0 < nout; r0 += step) {
+        const int r1 = std::min(nout, r0 + step), nr = r1 - r0;
+        const int nv = phase == 0 ? r1 : phase == 1 ? b : phase == 2 ? m : b - r0;
+        // index list
+        std::vector<int> il;
+        for (int j = 0; j < nv; ++j)
+          il.push_back(phase == 0 || phase == 1 ? T.beg + j : phase == 2 ? T.rows[j] : T.beg + r0 + j);
+        if (phase == 0) {
+          il.resize((size_t)3 * nv + nr, 0);
+          for (int j = 0; j < nv; ++j) {
+            const int r = T.beg + j;
+            il[nv + 2 * j] = (int)il.size();
+            for (int k = hs.fwd_ptr[r]; k < hs.fwd_ptr[r + 1]; ++k) il.push_back(hs.fwd_pos[k]);
+            il[nv + 2 * j + 1] = (int)il.size();
+          }
+          for (int i = 0; i < nr; ++i) il[3 * nv + i] = T.beg + r0 + i;
+        } else {
+          for (int i = 0; i < nr; ++i) il.push_back(phase == 1 ? (int)T.off_upd + r0 + i : T.beg + r0 + i);
+        }
+        P.pan_desc.insert(P.pan_desc.end(), {phase, nr, nv, (int)P.pan_idx.size(), t, r0, 0, 0});
+        P.pan_idx.insert(P.pan_idx.end(), il.begin(), il.end());
+        // chunk, column-major: element (i, j) at j nr + i
+        for (const Factor* F : {&hs.S, &hs.Mcc}) {
+          std::vector<double>& out = (F == &hs.S) ? P.panS : P.panM;
+          if (out.size() % 2) out.push_back(0.0);
+          if (F == &hs.S) P.pan_aoff.push_back((int64_t)out.size());
+          const double* Li = F->vals.data() + T.off_diag;    // L_tt^{-1}[i][j] = Li[i + b j]
+          const double* L21 = F->vals.data() + T.off_rect;   // L_{rows,t}[k][j] = L21[k + m j]
+          for (int j = 0; j < nv; ++j)
+            for (int i = 0; i < nr; ++i) {
+              double v;
+              if (phase == 0) v = (j <= r0 + i) ? Li[(r0 + i) + (size_t)b * j] : 0.0;
+              else if (phase == 1) v = L21[(r0 + i) + (size_t)m * j];
+              else if (phase == 2) v = L21[j + (size_t)m * (r0 + i)];
+              else v = (r0 + j >= r0 + i) ? Li[(r0 + j) + (size_t)b * (r0 + i)] : 0.0;
+              out.push_back(v);
+            }
+          if (out.size() % 2) out.push_back(0.0);
+        }
+        const int64_t n = (int64_t)nr * nv;
+        P.pan_max_chunk = std::max<int64_t>(P.pan_max_chunk, n + (n & 1));
+        P.pan_max_nv = std::max(P.pan_max_nv, nv + (nv & 1));
+        ++ncta;
+      }
+    }
+    P.pan_ncta[4 * l + phase] = ncta;
+  }
+  if (P.panS.size() != P.panM.size()) return fail(IMEX_ERR_ARG, "internal error: panel chunks of S and M differ");
+  if (P.pan_idx.size() > (size_t)INT32_MAX) return fail(IMEX_ERR_ARG, "panel index lists too large");
   return IMEX_OK;
 }
 
@@ -1505,11 +1632,21 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
   const int64_t blob_cap = (int64_t)(kWalkSmemBudget / sizeof(double));
   P.node_boff.assign(nt, 0);
   P.cta_node_ptr.assign(1, 0);
+  // Supernodes with more than kMaxWidth diagonal or ancestor rows are
+  // walked by k_panel (row chunks over many CTAs) instead of one walk CTA.
+  auto is_big = [&](int t) {
+    const TreeNode& T = hs.tree[t];
+    return T.end - T.beg > kMaxWidth || (int)T.rows.size() > kMaxWidth;
+  };
+  P.pan_cta0.assign(4 * (size_t)nlaunch, 0);
+  P.pan_ncta.assign(4 * (size_t)nlaunch, 0);
   for (int l = 0; l < nlaunch; ++l) {
-    std::vector<int> nodes;
+    std::vector<int> nodes, big;
     for (size_t t = 0; t < hs.tree.size(); ++t)
-      if (!is_top((int)t) && hs.tree[t].level == l) nodes.push_back((int)t);
+      if (!is_top((int)t) && hs.tree[t].level == l) (is_big((int)t) ? big : nodes).push_back((int)t);
     std::sort(nodes.begin(), nodes.end(), [&](int x, int y) { return node_work(x) > node_work(y); });
+    if (int rc = plan_panels(hs, big, l, P)) return rc;
+    P.n_large += (int64_t)big.size();
     auto bytes_of = [&](int t) {   // shared memory of a node, in doubles
       const TreeNode& T = hs.tree[t];
       const int64_t b = T.end - T.beg, m = (int64_t)T.rows.size();
@@ -2111,10 +2248,6 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       return fail(setup_error_code(err), err);
     }
     HostSetup& hs = c->hs;
-    if (hs.max_block > kMaxWidth || hs.max_rows > kMaxWidth) {
-      delete c;
-      return fail(IMEX_ERR_ARG, "supernode too large for the device solve (max 256)");
-    }
     if (hs.Pd > kMaxPd) {
       delete c;
       return fail(IMEX_ERR_ARG, "cell too large for the device right-hand side (P^d > 128)");
@@ -2273,6 +2406,16 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
         delete c;
         return fail(IMEX_ERR_ARG, "solve schedule exceeds the shared memory of a CTA");
       }
+      c->n_large = plan.n_large;
+      c->pan_cta0 = plan.pan_cta0;
+      c->pan_ncta = plan.pan_ncta;
+      c->pan_max_chunk = plan.pan_max_chunk;
+      c->pan_max_nv = plan.pan_max_nv;
+      c->smem_panel = (size_t)(plan.pan_max_chunk + plan.pan_max_nv + kThreads) * sizeof(double);
+      if (c->smem_panel > kMaxDynSmem) {
+        delete c;
+        return fail(IMEX_ERR_ARG, "large-supernode chunk exceeds the shared memory of a CTA");
+      }
       c->lev_cta0 = plan.lev_cta0;
       c->lev_ncta = plan.lev_ncta;
       c->ntop = (int)plan.top_comp.size();
@@ -2298,6 +2441,12 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->sol, std::max<int64_t>(nc, 1) * ncols);
     ar.add(&c->rhs0, std::max<int64_t>(nc, 1) * ncols);
     ar.add(&c->upd, std::max<int64_t>(hs.upd_size, 1) * ncols);
+    ar.add(&c->hbuf, std::max<int64_t>(nc, 1) * ncols);
+    ar.add(&c->pan_desc, std::max<size_t>(plan.pan_desc.size(), 8));
+    ar.add(&c->pan_idx, std::max<size_t>(plan.pan_idx.size(), 4));
+    ar.add(&c->pan_aoff, std::max<size_t>(plan.pan_aoff.size(), 1));
+    ar.add(&c->panS, std::max<size_t>(plan.panS.size(), 2));
+    ar.add(&c->panM, std::max<size_t>(plan.panM.size(), 2));
     ar.add(&c->Kpair, std::max<size_t>(plan.Kpair.size(), 2));
     ar.add(&c->kp_off, nblobcta);
     ar.add(&c->kp_len, nblobcta);
@@ -2482,10 +2631,17 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->zA_off, plan.zA_off);
     e = e ? e : upload(c->zA_S, plan.zA_S);
     e = e ? e : upload(c->zA_M, plan.zA_M);
+    e = e ? e : upload(c->pan_desc, plan.pan_desc);
+    e = e ? e : upload(c->pan_idx, plan.pan_idx);
+    e = e ? e : upload(c->pan_aoff, plan.pan_aoff);
+    e = e ? e : upload(c->panS, plan.panS);
+    e = e ? e : upload(c->panM, plan.panM);
     for (auto fn : {k_walk<true, true>, k_walk<false, true>, k_walk<true, false>, k_walk<false, false>})
       if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
     if (e == cudaSuccess) {
       int nsm = 0;
       e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
@@ -2540,13 +2696,14 @@ int pred_only_blocks(const imex_ctx* c) {
 //     without prediction, then M^cc a^c_n = f_t(t_n) f^c - K^c u_n and
 //     u^c_{n+1} = 2 u^c_n - u^c_{n-1} + dt^2 a^c_n (Eqs. CDMstep, CDMacc).
 static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double* ft_dev = nullptr,
-                     double* upd = nullptr, double* sol = nullptr, double* rhs0 = nullptr) {
+                     double* upd = nullptr, double* sol = nullptr, double* rhs0 = nullptr, double* hbuf = nullptr) {
   const HostSetup& hs = c->hs;
   const bool own = upd == nullptr;
   if (own) {
     upd = c->upd;
     sol = c->sol;
     rhs0 = c->rhs0;
+    hbuf = c->hbuf;
   }
   const double dt = hs.dt;
   double* Ucur = c->U[c->cur];
@@ -2569,17 +2726,17 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
       if (cudaError_t e = launch_pcg(c, Unext, s))
         return fail(IMEX_ERR_CUDA, std::string("imex_step: PCG launch: ") + cudaGetErrorString(e));
     } else if (cdm) {
-      launch_solve_chain(c, false, ft_at(hs, step), ft_dev, 3, Unext, Ucur, upd, sol, rhs0, s);
+      launch_solve_chain(c, false, ft_at(hs, step), ft_dev, 3, Unext, Ucur, upd, sol, rhs0, hbuf, s);
     } else if (c->solver == IMEX_SOLVER_DIRECT) {
-      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, s);
+      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, hbuf, s);
     } else {
       // Right-hand sides, PCG (correction included on convergence), then the
       // direct solve, whose launches return at once unless PCG fell short.
-      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, s,
+      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, hbuf, s,
                          nullptr, true);
       if (cudaError_t e = launch_pcg(c, Unext, s))
         return fail(IMEX_ERR_CUDA, std::string("imex_step: PCG launch: ") + cudaGetErrorString(e));
-      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, s,
+      launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, hbuf, s,
                          c->pcg_status + 1);
     }
   }
@@ -3076,7 +3233,7 @@ int imex_adjoint(imex_ctx* c, int64_t nsteps, const int64_t* rec_nodes, int nrec
       k_misfit<<<ncols, kThreads, 0, s>>>(nrec, nn, drec, un1, ddata + n * ncols * nrec, ubar, jpart + ncols, 1);
       if (hs.n_c > 0) {
         k_adj_pre<<<gc, kThreads, 0, s>>>((int)hs.n_c, nn, nc, c->c_node, ubar, vbar, abar, c->rhs0, ucp, vcp, dt);
-        e = launch_solve_chain(c, true, 0.0, nullptr, 2, c->U[c->cur], c->U[c->cur], c->upd, c->sol, c->rhs0, s,
+        e = launch_solve_chain(c, true, 0.0, nullptr, 2, c->U[c->cur], c->U[c->cur], c->upd, c->sol, c->rhs0, c->hbuf, s,
                                nullptr, false, true);
       }
       e = e ? e : cudaMemsetAsync(z1, 0, ncols * nn * sizeof(double), s);
@@ -3125,6 +3282,8 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   st->explicit_variant = c->xvar;
   st->explicit_sweep_us = c->tile_us[2];
   st->explicit_sweep_short_us = c->tile_us[3];
+  st->large_supernodes = c->n_large;
+  st->max_rows = c->hs.max_rows;
   st->device_bytes = (int64_t)c->bytes;
   st->factorized = c->factorized;
   return IMEX_OK;
@@ -3207,8 +3366,12 @@ extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
   auto even = [](int64_t v) { return v + (v & 1); };
   const int64_t n_upd = even(std::max<int64_t>(hs.upd_size, 1)) * c->ncols;
   const int64_t n_sol = even(std::max<int64_t>(hs.n_c, 1)) * c->ncols;
-  if (n_upd + 2 * n_sol > kStaticScratchDoubles)
-    return fail(IMEX_ERR_ARG, "imex_step_noalloc: the implicit solve needs " + std::to_string(n_upd + 2 * n_sol) +
+  // A third vector for the backward products of supernodes above 256 rows.
+  bool panels = false;
+  for (int k : c->pan_ncta) panels = panels || k > 0;
+  const int64_t need = n_upd + (panels ? 3 : 2) * n_sol;
+  if (need > kStaticScratchDoubles)
+    return fail(IMEX_ERR_ARG, "imex_step_noalloc: the implicit solve needs " + std::to_string(need) +
                                   " doubles of scratch; the static scratch holds " +
                                   std::to_string(kStaticScratchDoubles) + " (use imex_step)");
   int dev = -1;
@@ -3230,10 +3393,11 @@ extern "C" int imex_step_noalloc(imex_ctx* c, int64_t n, void* stream) {
   double* upd = base;
   double* sol = upd + n_upd;
   double* rhs0 = sol + n_sol;
+  double* hbuf = panels ? rhs0 + n_sol : nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   c->stream = s;
   for (int64_t k = 0; k < n; ++k)
-    if (int rc = step_once(c, s, nullptr, nullptr, upd, sol, rhs0)) return rc;
+    if (int rc = step_once(c, s, nullptr, nullptr, upd, sol, rhs0, hbuf)) return rc;
   return IMEX_OK;
 }
 

@@ -180,6 +180,41 @@ struct TopArgs {
   int64_t cs_node, cs_c, cs_upd;  // independent columns (blockIdx.y)
 };
 
+// Large supernodes of the walked levels (more than 256 diagonal or ancestor
+// rows), one launch per level and phase, each CTA one chunk of rows of a
+// dense block times a gathered vector:
+//   kind 0 (forward)   y_t = L_tt^{-1} g_t, g_t = rhs - descendant updates -> sol
+//   kind 1 (forward)   upd_t = L_{rows,t} y_t                               -> upd
+//   kind 2 (backward)  h_t = y_t - L_{rows,t}^T x_rows                      -> hbuf
+//   kind 3 (backward)  x_t = L_tt^{-T} h_t, then the correction of the row -> sol
+// Per CTA: desc[8 cta + 0..3] = kind, nr (rows), nv (vector length), index
+// list offset; the chunk is nr x nv, column-major (row i, column j at
+// j nr + i), at a_off[cta] in A.  Index list: nv input c-indices (kind 0:
+// then 2 nv update ranges into the list itself), nr output indices (c-rows;
+// kind 1: update positions), then kind 0's update positions.
+struct PanelArgs {
+  int cta0;
+  const int* desc;
+  const int64_t* a_off;
+  const double* A;
+  const int* idx;
+  int64_t max_chunk;            // doubles reserved for a chunk in shared memory (even)
+  int max_nv;                   // doubles reserved for the vector (even)
+  const int* skip;              // if set and *skip != 0: the launch does nothing (PCG converged)
+  const double* rhs0;
+  double* upd;
+  double* sol;
+  double* hbuf;
+  int mode;                     // correction mode (WalkArgs)
+  const int* c_node;
+  double* U;
+  const double* Un;
+  double* v_c;
+  double* a_c;
+  double dt;
+  int64_t cs_node, cs_c, cs_upd;
+};
+
 // Preconditioned conjugate gradients for S a = rhs (the iterative alternative
 // to A5), one cooperative grid, single column.
 struct PcgArgs {

@@ -1345,3 +1345,85 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Large supernodes of the walked levels (PanelArgs): each CTA multiplies one
+// chunk of rows of a dense block (the inverted diagonal block, its
+// transpose, the block below it or its transpose) by a gathered vector.  The
+// chunk is staged (cp.async) before the grid-dependency wait; threads (s, i)
+// take row i over the s-th column slice and the slices are summed pairwise,
+// as in k_top.  Fixed-order sums: results do not depend on timing.
+__global__ void __launch_bounds__(kThreads) k_panel(PanelArgs a) {
+  extern __shared__ __align__(16) double psm[];
+  const int cta = a.cta0 + blockIdx.x, tid = threadIdx.x;
+  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
+  const double* rhs0 = a.rhs0 + oc;
+  double* sol = a.sol + oc;
+  double* hbuf = a.hbuf + oc;
+  double* upd = a.upd + (int64_t)blockIdx.y * a.cs_upd;
+  const Corr cor{a.mode, a.c_node, a.U + on, a.v_c + oc, a.a_c + oc, a.dt, a.Un ? a.Un + on : nullptr};
+  const int* d = a.desc + 8 * cta;
+  const int kind = d[0], nr = d[1], nv = d[2];
+  const int* il = a.idx + d[3];
+  const int* vin = il;                                  // nv input indices
+  const int* vrng = il + nv;                            // kind 0: 2 nv update ranges
+  const int* vout = il + (kind == 0 ? 3 * nv : nv);     // nr output indices
+  double* Ac = psm;                                     // max_chunk: the chunk, column-major
+  double* vs = Ac + a.max_chunk;                        // max_nv: the gathered vector
+  double* xs = vs + a.max_nv;                           // kThreads: partial sums
+  const int64_t n = (int64_t)nr * nv;
+  async_copy_16(Ac, a.A + a.a_off[cta], (n + 1) / 2);
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  async_copy_wait();
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  if (a.skip && *a.skip) return;   // the iterative solve converged: nothing to do
+  for (int j = tid; j < nv; j += kThreads) {
+    const int c = vin[j];
+    double v;
+    if (kind == 0) {
+      v = __ldcg(rhs0 + c);
+      for (int q = vrng[2 * j]; q < vrng[2 * j + 1]; ++q) v -= __ldcg(upd + il[q]);
+    } else if (kind == 3) {
+      v = __ldcg(hbuf + c);
+    } else {
+      v = __ldcg(sol + c);
+    }
+    vs[j] = v;
+  }
+  __syncthreads();
+  const int nslice = min(kThreads / max(nr, 1), max(nv / 2, 1));
+  if (tid < nslice * nr) {
+    const int s = tid / nr, i = tid - s * nr;
+    const int j0 = (int)((int64_t)nv * s / nslice), j1 = (int)((int64_t)nv * (s + 1) / nslice);
+    const double* Ai = Ac + i;
+    double s0 = 0.0, s1 = 0.0;
+    int j = j0;
+    for (; j + 2 <= j1; j += 2) {
+      s0 = fma(Ai[(size_t)j * nr], vs[j], s0);
+      s1 = fma(Ai[(size_t)(j + 1) * nr], vs[j + 1], s1);
+    }
+    if (j < j1) s0 = fma(Ai[(size_t)j * nr], vs[j], s0);
+    xs[tid] = s0 + s1;
+  }
+  __syncthreads();
+  for (int h = nslice; h > 1;) {
+    const int h2 = (h + 1) / 2;   // slice s < h - h2 takes in slice s + h2
+    if (tid < (h - h2) * nr) xs[tid] += xs[tid + h2 * nr];
+    h = h2;
+    __syncthreads();
+  }
+  if (tid < nr) {
+    const double acc = xs[tid];
+    const int c = vout[tid];
+    if (kind == 0) {
+      sol[c] = acc;
+    } else if (kind == 1) {
+      upd[c] = acc;
+    } else if (kind == 2) {
+      hbuf[c] = __ldcg(sol + c) - acc;
+    } else {
+      sol[c] = acc;
+      cor.row(c, acc);
+    }
+  }
+}

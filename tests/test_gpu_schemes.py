@@ -178,3 +178,14 @@ def test_schemes_3d(scheme):
                            np.array([[0.55, 0.4, 0.3, 0.22, 0.18, 0.15]]), np.array([[0.21, 0.27, 0.22]]),
                            3.0, 0.1, 0)
     _check(w, scheme, 40)
+
+
+def test_trapezoidal_with_large_supernodes():
+    # Every active DOF implicit on a 96 x 48-cell perforated plate (p = 4, the
+    # 24 seeded holes): 70k implicit DOFs whose top dissection supernodes carry
+    # more than 256 ancestor rows, walked as row chunks over many CTAs.
+    w = workloads.plate256()
+    w.ncells = (96, 48)
+    s, info = _check(w, "trapezoidal", 100)
+    assert info["large_supernodes"] > 0 and info["max_rows"] > 256
+    assert info["n_d"] == 0

@@ -53,6 +53,16 @@ def test_noalloc_cdm_scheme_matches_step():
     _side_by_side(workloads.plate16(), scheme="cdm")
 
 
+def test_noalloc_large_supernodes_match_step():
+    # A 3D solid whose factor has supernodes of more than 256 rows: the
+    # array also holds the backward products of their row chunks.
+    w = workloads.voids3d(ncells=(8, 8, 4), steps=40)
+    imex = _imex()
+    with imex.Imex.from_workload(w) as g:
+        assert g.info()["large_supernodes"] > 0
+    _side_by_side(w, calls=(5, 7))
+
+
 def test_noalloc_rejects_pcg_context_and_oversized_problem():
     imex = _imex()
     with imex.Imex.from_workload(workloads.plate16()) as g:
