@@ -156,37 +156,58 @@ def restore(g, snap):
     g.set_step(snap[1])
 
 
-def measure_learned_pcg(imex, w, steps, stream, flush, epochs=300, lr=0.1, t_active=600):
-    """The implicit solve by PCG (tol 1e-10) with the learned FSAI preconditioner
-    and with Jacobi, against the factorised solve, on the bench workload.  All
-    three run the same steps from one snapshot taken after t_active steps, when
-    the pulse has reached the holes (before that the implicit right-hand sides
-    are exactly zero and PCG takes no iteration)."""
+def measure_learned_pcg(imex, w, steps, stream, flush, epochs=300, lr=0.1, t_active=600, guess_steps=40):
+    """The implicit solve by PCG (tol 1e-10) against the factorised solve on
+    the bench workload, all from one snapshot taken after t_active steps,
+    when the pulse has reached the holes (before that the implicit right-hand
+    sides are exactly zero and PCG takes no iteration): the learned FSAI
+    (Kaporin training on the GPU), the same with the starting guess learned
+    from the method's own solutions, the closed-form FSAI of the pattern, and
+    Jacobi."""
     g = imex.Imex.from_workload(w)
     st = g.info()
     n_act = st["n_d"] + st["n_c"]
-    g.step(t_active)
-    snap = snapshot(g)
+    g.step(t_active - guess_steps)
     t0 = time.perf_counter()
     hist = g.pcg_train(epochs, lr)
     train_s = time.perf_counter() - t0
+    g.set_solver("pcg_fsai", 1e-10, 5000)
+    t0 = time.perf_counter()
+    wts, ghist = g.pcg_train_guess(guess_steps, 300, 0.05)
+    guess_s = time.perf_counter() - t0
+    snap = snapshot(g)
     out = {"workload": workload_name(w), "unit": UNIT, "tol": 1e-10, "train_epochs": epochs, "lr": lr,
            "train_seconds": train_s, "kaporin_loss": [float(hist[0]), float(hist[-1])],
+           "guess_weights": [float(x) for x in wts], "guess_train_steps": guess_steps,
+           "guess_train_seconds": guess_s, "guess_loss": [float(ghist[0]), float(ghist[-1])],
            "l2": "flushed between timed steps", "steps": steps,
            "window": f"steps {t_active + 3}..{t_active + 3 + steps} from one snapshot"}
-    for solver in ("direct", "pcg_fsai", "pcg_jacobi"):
+
+    def run(label, solver, guess):
         restore(g, snap)
         g.set_solver(solver, 1e-10, 5000)
+        g.pcg_set_guess(guess)
         g.step(3)
         s0 = g.pcg_status()
         ms = time_flushed(g, steps, stream, flush)
         s1 = g.pcg_status()
-        out[solver] = {"value": n_act * steps / (ms * 1e-3), "ms_per_step": ms / steps,
-                       "iterations_per_step": (s1["iters_total"] - s0["iters_total"]) / steps,
-                       "fallbacks": s1["fallbacks"] - s0["fallbacks"]}
+        out[label] = {"value": n_act * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                      "iterations_per_step": (s1["iters_total"] - s0["iters_total"]) / steps,
+                      "fallbacks": s1["fallbacks"] - s0["fallbacks"]}
+
+    run("direct", "direct", False)
+    run("pcg_fsai", "pcg_fsai", False)
+    run("pcg_fsai_guess", "pcg_fsai", True)
+    g.pcg_fsai_closed_form()
+    run("pcg_fsai_closed_form", "pcg_fsai", False)
+    run("pcg_jacobi", "pcg_jacobi", False)
     out["learned_vs_jacobi_iterations"] = (out["pcg_fsai"]["iterations_per_step"] /
                                            max(out["pcg_jacobi"]["iterations_per_step"], 1e-30))
-    out["learned_vs_direct_value"] = out["pcg_fsai"]["value"] / out["direct"]["value"]
+    out["guess_vs_plain_iterations"] = (out["pcg_fsai_guess"]["iterations_per_step"] /
+                                        max(out["pcg_fsai"]["iterations_per_step"], 1e-30))
+    out["trained_vs_closed_form_iterations"] = (out["pcg_fsai"]["iterations_per_step"] /
+                                                max(out["pcg_fsai_closed_form"]["iterations_per_step"], 1e-30))
+    out["learned_vs_direct_value"] = out["pcg_fsai_guess"]["value"] / out["direct"]["value"]
     g.close()
     return out
 
@@ -267,18 +288,37 @@ def measure_voids3d(imex, workloads, stream, flush, steps=10, epochs=300, lr=0.2
     out["lr"] = lr
     out["train_seconds"] = _t.perf_counter() - t0
     out["kaporin_loss"] = [float(hist[0]), float(hist[-1])]
-    g.step(t_active)
+    g.set_solver("pcg_fsai", 1e-10, 5000)
+    t0 = _t.perf_counter()
+    wts, ghist = g.pcg_train_guess(t_active, 300, 0.05)
+    out["guess_weights"] = [float(x) for x in wts]
+    out["guess_train_steps"] = t_active
+    out["guess_train_seconds"] = _t.perf_counter() - t0
+    out["guess_loss"] = [float(ghist[0]), float(ghist[-1])]
     snap = snapshot(g)
     out["window"] = f"steps {t_active + 2}.. from one snapshot"
-    out["direct"] = timed("direct", steps)
-    restore(g, snap)
-    out["pcg_fsai"] = timed("pcg_fsai", steps)
-    restore(g, snap)
-    out["pcg_jacobi"] = timed("pcg_jacobi", max(2, steps // 2))
+
+    def timed_guess(solver, nsteps, guess):
+        restore(g, snap)
+        g.pcg_set_guess(guess)
+        return timed(solver, nsteps)
+
+    out["direct"] = timed_guess("direct", steps, False)
+    out["pcg_fsai"] = timed_guess("pcg_fsai", steps, False)
+    out["pcg_fsai_guess"] = timed_guess("pcg_fsai", steps, True)
+    out["pcg_jacobi"] = timed_guess("pcg_jacobi", max(2, steps // 2), False)
+    t0 = _t.perf_counter()
+    g.pcg_fsai_closed_form()
+    out["closed_form_seconds"] = _t.perf_counter() - t0
+    out["pcg_fsai_closed_form"] = timed_guess("pcg_fsai", steps, False)
     out["value"] = out["direct"]["value"]
     out["learned_vs_jacobi_iterations"] = (out["pcg_fsai"]["iterations_per_step"] /
                                            max(out["pcg_jacobi"]["iterations_per_step"], 1e-30))
-    out["learned_vs_direct_value"] = out["pcg_fsai"]["value"] / out["direct"]["value"]
+    out["guess_vs_plain_iterations"] = (out["pcg_fsai_guess"]["iterations_per_step"] /
+                                        max(out["pcg_fsai"]["iterations_per_step"], 1e-30))
+    out["trained_vs_closed_form_iterations"] = (out["pcg_fsai"]["iterations_per_step"] /
+                                                max(out["pcg_fsai_closed_form"]["iterations_per_step"], 1e-30))
+    out["learned_vs_direct_value"] = out["pcg_fsai_guess"]["value"] / out["direct"]["value"]
     g.close()
     return out
 

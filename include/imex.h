@@ -337,6 +337,39 @@ int imex_pcg_train(imex_ctx *ctx, int epochs, double lr, double *loss_hist);
  * totals since setup (iterations, steps that fell back to the direct solve).
  * Synchronous.  Any pointer may be NULL.
  */
+/*
+ * imex_pcg_train_guess - learn the starting guess of the PCG solves from the
+ * method's own solutions (no counterpart in the paper; the north-star's
+ * learned part).  Advances the context by nsteps >= 4 steps with its current
+ * solver, keeping a^c after every step (a temporary device buffer of
+ * (nsteps + 1) n_c doubles), then runs `epochs` Adam steps (Kingma and Ba,
+ * Algorithm 1; learning rate lr, from w = (1, 0, 0)) on
+ *   E(w) = sum_s ||w0 a_s + w1 a_{s-1} + w2 a_{s-2} - a_{s+1}||^2 / ||a_{s+1}||^2
+ * with the library's gradient kernels.  Afterwards every PCG solve starts
+ * from x0 = w0 a^c_n + w1 a^c_{n-1} + w2 a^c_{n-2} (instead of a^c_n) once two
+ * PCG solves since the last direct solve or state change have filled the
+ * history.  loss_hist (epochs doubles) and w_out (3) may be NULL.
+ * Single-column contexts.  Errors: IMEX_ERR_ARG, IMEX_ERR_ALLOC, IMEX_ERR_CUDA.
+ */
+int imex_pcg_train_guess(imex_ctx *ctx, int nsteps, int epochs, double lr, double *loss_hist, double *w_out);
+
+/*
+ * imex_pcg_set_guess - enable (with the weights w[3], or the trained ones when
+ * w is NULL) or disable (enable = 0: start from a^c_n) the learned starting
+ * guess of the PCG solves.  Errors: IMEX_ERR_ARG, IMEX_ERR_CUDA.
+ */
+int imex_pcg_set_guess(imex_ctx *ctx, int enable, const double *w);
+
+/*
+ * imex_pcg_fsai_closed_form - set G of the FSAI preconditioner to the
+ * minimiser of Kaporin's functional on its pattern, computed directly on the
+ * host (column j: S_QQ y = e_j on the rows Q of the column,
+ * G_Qj = y / sqrt(y_j); Kolotilina and Yeremin's factorised sparse
+ * approximate inverse), for comparison with the trained G; later training
+ * continues from it.  Errors: IMEX_ERR_ARG, IMEX_ERR_NOT_SPD, IMEX_ERR_CUDA.
+ */
+int imex_pcg_fsai_closed_form(imex_ctx *ctx);
+
 int imex_pcg_status(imex_ctx *ctx, int64_t *iters_last, double *res_last, int64_t *iters_total,
                     int64_t *fallbacks);
 

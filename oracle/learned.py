@@ -29,6 +29,15 @@ alternative: conjugate gradients with a preconditioner learned from pairs
     above is kept as the check on the method's own pairs: fitting it alone
     lengthened CG on held-out right-hand sides.
 
+  * The starting guess of each solve is learned from the method's own
+    solutions: x0 = sum_k w_k a_{n-k} (k < 3, a_n the accelerations of the
+    last solves; PCG otherwise starts from a_n), with the weights w fitted by
+    Adam to the loss over consecutive solutions
+        E(w) = sum_s ||sum_k w_k a_{s-k} - a_{s+1}||^2 / ||a_{s+1}||^2
+    (extrapolation_loss_grad).  Polynomial extrapolation through the last
+    three values, w = (3, -3, 1), is exact for accelerations quadratic in
+    time; the learned weights adapt to the wave content of the run.
+
 Pins (tests/test_oracle_learned.py): PCG against a direct solve and its
 iteration bound on a diagonal system; both gradients against central finite
 differences and the losses written out densely; the data-fit loss at the
@@ -36,7 +45,11 @@ exact inverse factor (zero, and PCG converging in one iteration); the
 Kaporin minimiser against the column-wise closed form (and, on the full
 lower pattern, the Cholesky factor of S^{-1}); Adam's first step in closed
 form; training on the method's own systems halving CG iterations against
-the untrained (Jacobi) start, the direct solve judging the error.
+the untrained (Jacobi) start, the direct solve judging the error; the
+extrapolation loss zero at w = (3, -3, 1) on any sequence quadratic in time,
+its gradient against central differences, Adam converging to those weights
+on such a sequence, and the learned guess cutting CG iterations on later
+solves of the method's own run.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -194,3 +207,45 @@ def jacobi_init(indptr, indices, S):
             if indices[k] == i:
                 vals[k] = 1.0 / np.sqrt(d[i])
     return vals
+
+
+def extrapolation_guess(H, w):
+    """x0 = sum_k w_k H[k]; H: (K, n, ...) histories, H[k] = a_{n-k}."""
+    H = np.asarray(H, dtype=np.float64)
+    return np.tensordot(np.asarray(w, dtype=np.float64), H, axes=(0, 0))
+
+
+def extrapolation_loss_grad(H, X, w):
+    """E(w) = sum_s ||sum_k w_k H[k][:, s] - X[:, s]||^2 / ||X[:, s]||^2 and its
+    gradient dE/dw_k = sum_s 2 (e_s . H[k][:, s]) / ||X[:, s]||^2, e_s the
+    residual of sample s.  H: (K, n, ns), X: (n, ns)."""
+    H = np.asarray(H, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    wt = 1.0 / np.sum(X * X, axis=0)
+    E = extrapolation_guess(H, w) - X
+    loss = float(np.sum(wt * np.sum(E * E, axis=0)))
+    grad = np.array([float(np.sum(2.0 * wt * np.sum(E * H[k], axis=0))) for k in range(H.shape[0])])
+    return loss, grad
+
+
+def extrapolation_samples(A, K=3):
+    """Histories and targets from a sequence of solutions A (n, T): sample s
+    (K-1 <= s < T-1) has H[k][:, s] = A[:, s-k] and target A[:, s+1]."""
+    A = np.asarray(A, dtype=np.float64)
+    T = A.shape[1]
+    s = np.arange(K - 1, T - 1)
+    H = np.stack([A[:, s - k] for k in range(K)])
+    return H, A[:, s + 1]
+
+
+def train_extrapolation(H, X, w0, epochs, lr):
+    """Full-batch Adam on E from w0; returns w and the loss history."""
+    w = np.array(w0, dtype=np.float64)
+    m = np.zeros_like(w)
+    v = np.zeros_like(w)
+    hist = []
+    for t in range(1, epochs + 1):
+        loss, g = extrapolation_loss_grad(H, X, w)
+        hist.append(loss)
+        w, m, v = adam_step(w, g, m, v, t, lr)
+    return w, hist

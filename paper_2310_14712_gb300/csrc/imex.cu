@@ -15,6 +15,8 @@
 #include <numeric>
 #include <string>
 #include <vector>
+#include <thread>
+#include <mutex>
 
 #include "../../include/imex.h"
 #include "kernels.cuh"
@@ -132,7 +134,18 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a, PcgCols t2) {
       grid.sync();   // z is read below by other threads than its writers
     }
   };
-  for (int i = g0; i < n; i += gs) a.x[i] = a.a_c[i];
+  if (a.hist1) {   // learned starting guess (or a^c_n), then shift the history
+    const double w0 = a.guess_w ? a.guess_w[0] : 1.0, w1 = a.guess_w ? a.guess_w[1] : 0.0,
+                 w2 = a.guess_w ? a.guess_w[2] : 0.0;
+    for (int i = g0; i < n; i += gs) {
+      const double an = a.a_c[i], h1 = a.hist1[i], h2 = a.hist2[i];
+      a.x[i] = a.guess_w ? fma(w0, an, fma(w1, h1, w2 * h2)) : an;
+      a.hist2[i] = h1;
+      a.hist1[i] = an;
+    }
+  } else {
+    for (int i = g0; i < n; i += gs) a.x[i] = a.a_c[i];
+  }
   grid.sync();
   double bb = 0.0, rr = 0.0;
   for (int i = w0; i < n; i += ws) {
@@ -301,6 +314,70 @@ __global__ void k_adam(int64_t nnz, double* theta, const double* grad, const dou
   if (is_diag[e]) th = fmax(th, floor_);
   theta[e] = th;
   g_val[e] = th * scale[e];
+}
+
+// Training of the learned starting guess (three weights w, Adam) on the
+// method's own solutions A (column t: a^c after t steps, n rows each):
+// sample s (2 <= s < T-1) has history (A_s, A_{s-1}, A_{s-2}) and target
+// A_{s+1}; E(w) = sum_s wt_s ||e_s||^2, e_s = sum_k w_k A_{s-k} - A_{s+1},
+// wt_s = 1 / ||A_{s+1}||^2.  k_guess_grad: per block partials of E and of
+// dE/dw_k = sum_s 2 wt_s (e_s . A_{s-k}) into part[(0..3) gridDim.x + b].
+__global__ void __launch_bounds__(kThreads) k_guess_grad(int n, int T, const double* A, const double* wt,
+                                                         const double* w, double* part) {
+  __shared__ double red[kWarps];
+  const double w0 = w[0], w1 = w[1], w2 = w[2];
+  double l = 0.0, g[3] = {0.0, 0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int s = 2; s < T - 1; ++s) {
+      const double h0 = A[(size_t)s * n + i], h1 = A[(size_t)(s - 1) * n + i], h2 = A[(size_t)(s - 2) * n + i];
+      const double e = fma(w0, h0, fma(w1, h1, w2 * h2)) - A[(size_t)(s + 1) * n + i];
+      const double we = wt[s] * e;
+      l = fma(we, e, l);
+      g[0] = fma(2.0 * we, h0, g[0]);
+      g[1] = fma(2.0 * we, h1, g[1]);
+      g[2] = fma(2.0 * we, h2, g[2]);
+    }
+  }
+  block_partial(l, part, 0, red);
+  for (int k = 0; k < 3; ++k) block_partial(g[k], part, 1 + k, red);
+}
+
+// Squared norm of column s of A into part[s] (one block per column,
+// fixed-order reduction).
+__global__ void __launch_bounds__(kThreads) k_col_sqnorm(int n, const double* A, double* out) {
+  __shared__ double red[kWarps];
+  const double* x = A + (size_t)blockIdx.x * n;
+  double l = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) l = fma(x[i], x[i], l);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < kWarps; ++q) s += red[q];
+    out[blockIdx.x] = s > 0.0 ? 1.0 / s : 0.0;
+  }
+}
+
+// One Adam step on the three weights (state[0..2] w, [3..5] m, [6..8] v)
+// from the summed block partials; loss_out (may be NULL) receives E.
+__global__ void k_guess_adam(int nb, const double* part, double* state, double b1t, double b2t, double lr,
+                             double* loss_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double sum[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = 0; q < 4; ++q)
+    for (int b = 0; b < nb; ++b) sum[q] += part[(size_t)q * nb + b];
+  if (loss_out) *loss_out = sum[0];
+  const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+  for (int k = 0; k < 3; ++k) {
+    const double g = sum[1 + k];
+    const double m = b1 * state[3 + k] + (1.0 - b1) * g;
+    const double v = b2 * state[6 + k] + (1.0 - b2) * g * g;
+    state[3 + k] = m;
+    state[6 + k] = v;
+    state[k] -= lr * (m / (1.0 - b1t)) / (sqrt(v / (1.0 - b2t)) + eps);
+  }
 }
 
 // Health check: per block max |x| over the entries whose class is nonzero
@@ -732,6 +809,12 @@ struct imex_ctx {
   int *pr_ptr = nullptr, *pr_pos = nullptr, *if_base_dev = nullptr, *if_koff_dev = nullptr;
   double *pcg_x = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_w = nullptr;
   double *pcg_part = nullptr, *pcg_res = nullptr;
+  // learned starting guess of the PCG solves: history a^c_{n-1}, a^c_{n-2}
+  // (pcg_hist, 2 n_c) and the Adam state of the three weights (guess_state:
+  // w, m, v); used once two PCG solves have filled the history
+  double *pcg_hist = nullptr, *guess_state = nullptr;
+  int guess_on = 0;
+  int64_t guess_valid = 0, guess_t = 0;
   int* pcg_status = nullptr;
   long long* pcg_counters = nullptr;
   int64_t adam_t = 0;
@@ -1236,6 +1319,9 @@ cudaError_t launch_pcg(imex_ctx* c, double* Ubuf, cudaStream_t s, bool on_M = fa
   a.part = c->pcg_part;
   a.tol = on_M ? 1e-12 : c->pcg_tol;
   a.maxit = on_M ? 100000 : c->pcg_maxit;
+  a.hist1 = on_M ? nullptr : c->pcg_hist;
+  a.hist2 = on_M ? nullptr : c->pcg_hist + hs.n_c;
+  a.guess_w = (!on_M && c->guess_on && c->guess_valid >= 2) ? c->guess_state : nullptr;
   a.always_correct = c->factorized ? 0 : 1;   // no direct solve to fall back on
   a.status = c->pcg_status;
   a.counters = c->pcg_counters;
@@ -2491,6 +2577,8 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       ar.add(&c->dinv, ncm);
       for (double** v : {&c->pcg_x, &c->pcg_r, &c->pcg_z, &c->pcg_p, &c->pcg_q, &c->pcg_w}) ar.add(v, ncm);
       ar.add(&c->pcg_part, 4 * std::max<int64_t>(1024, (ncm + kThreads - 1) / kThreads));
+      ar.add(&c->pcg_hist, 2 * ncm);
+      ar.add(&c->guess_state, 16);
       ar.add(&c->pcg_res, 2);
       ar.add(&c->pcg_status, 4);
       ar.add(&c->pcg_counters, 2);
@@ -2725,10 +2813,12 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
       launch_rhs_c(c, ft_at(hs, step + 1), Unext, s, ft_dev);
       if (cudaError_t e = launch_pcg(c, Unext, s))
         return fail(IMEX_ERR_CUDA, std::string("imex_step: PCG launch: ") + cudaGetErrorString(e));
+      ++c->guess_valid;
     } else if (cdm) {
       launch_solve_chain(c, false, ft_at(hs, step), ft_dev, 3, Unext, Ucur, upd, sol, rhs0, hbuf, s);
     } else if (c->solver == IMEX_SOLVER_DIRECT) {
       launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, hbuf, s);
+      c->guess_valid = 0;   // the PCG history is not advanced by the direct solve
     } else {
       // Right-hand sides, PCG (correction included on convergence), then the
       // direct solve, whose launches return at once unless PCG fell short.
@@ -2738,6 +2828,7 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
         return fail(IMEX_ERR_CUDA, std::string("imex_step: PCG launch: ") + cudaGetErrorString(e));
       launch_solve_chain(c, true, ft_at(hs, step + 1), ft_dev, 0, Unext, Unext, upd, sol, rhs0, hbuf, s,
                          c->pcg_status + 1);
+      ++c->guess_valid;
     }
   }
   if (ev) cudaEventRecord(ev[2], s);
@@ -2959,6 +3050,7 @@ int imex_fields(imex_ctx* c, int which, double* dst, int64_t len, int dst_on_dev
 int imex_set_fields(imex_ctx* c, int which, const double* src, int64_t len, int src_on_device) {
   if (int rc = field_io_check(c, len)) return rc;
   if (!src) return fail(IMEX_ERR_ARG, "NULL source");
+  c->guess_valid = 0;
   cudaStream_t s = c->stream;
   const int64_t n = c->hs.nnodes;
   const int nb = (int)((n + 255) / 256);
@@ -2996,12 +3088,14 @@ int imex_set_fields(imex_ctx* c, int which, const double* src, int64_t len, int 
 int imex_set_step(imex_ctx* c, int64_t n) {
   if (!c || n < 0) return fail(IMEX_ERR_ARG, "bad arguments");
   c->step = n;
+  c->guess_valid = 0;
   return IMEX_OK;
 }
 
 int imex_set_initial(imex_ctx* c, const double* u0, const double* v0, int64_t len, int on_device) {
   if (int rc = field_io_check(c, len)) return rc;
   if (!u0) return fail(IMEX_ERR_ARG, "NULL u0");
+  c->guess_valid = 0;
   cudaStream_t s = c->stream;
   const int64_t n = c->hs.nnodes;
   const int nb = (int)((n + 255) / 256);
@@ -3068,6 +3162,170 @@ int imex_pcg_train(imex_ctx* c, int epochs, double lr, double* loss_hist) {
                                                                                       c->gt_val);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_pcg_train: ") + cudaGetErrorString(e));
+  return IMEX_OK;
+}
+
+int imex_pcg_train_guess(imex_ctx* c, int nsteps, int epochs, double lr, double* loss_hist, double* w_out) {
+  if (!c || nsteps < 4 || epochs < 0 || !(lr > 0.0)) return fail(IMEX_ERR_ARG, "need nsteps >= 4, epochs >= 0, lr > 0");
+  if (c->ncols > 1 || !c->pcg_hist) return fail(IMEX_ERR_ARG, "the learned guess serves single-column PCG contexts");
+  const int n = (int)c->hs.n_c;
+  if (n == 0) return fail(IMEX_ERR_ARG, "no implicit DOFs");
+  cudaStream_t s = c->stream;
+  const int T = nsteps + 1;
+  double* A = nullptr;
+  if (cudaMalloc(&A, ((size_t)T * n + T + 4 * 1024 + (size_t)std::max(epochs, 1)) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IMEX_ERR_ALLOC, "imex_pcg_train_guess: device buffer");
+  }
+  double* inv = A + (size_t)T * n;           // 1 / ||A_t||^2
+  double* part = inv + T;                    // 4 x nb block partials
+  double* lhist = part + 4 * 1024;           // loss per epoch
+  cudaError_t e = cudaMemcpyAsync(A, c->a_c, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  int rc = IMEX_OK;
+  for (int t = 1; t < T && e == cudaSuccess && rc == IMEX_OK; ++t) {
+    rc = step_once(c, s, nullptr);
+    if (rc == IMEX_OK)
+      e = cudaMemcpyAsync(A + (size_t)t * n, c->a_c, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
+  const int nb = (int)std::min<int64_t>(1024, ((int64_t)n + kThreads - 1) / kThreads);
+  if (e == cudaSuccess && rc == IMEX_OK) {
+    k_col_sqnorm<<<T, kThreads, 0, s>>>(n, A, inv);
+    const double w0[9] = {1.0, 0.0, 0.0, 0, 0, 0, 0, 0, 0};   // start from a^c_n alone
+    e = cudaMemcpyAsync(c->guess_state, w0, sizeof(w0), cudaMemcpyHostToDevice, s);
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+      k_guess_grad<<<nb, kThreads, 0, s>>>(n, T, A, inv + 1, c->guess_state, part);
+      const int64_t t = ep + 1;
+      k_guess_adam<<<1, 1, 0, s>>>(nb, part, c->guess_state, std::pow(0.9, (double)t), std::pow(0.999, (double)t),
+                                   lr, lhist + ep);
+      e = cudaGetLastError();
+    }
+    // The history of the next PCG solve: a^c after the last two steps.
+    e = e ? e : cudaMemcpyAsync(c->pcg_hist, A + (size_t)(T - 2) * n, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    e = e ? e : cudaMemcpyAsync(c->pcg_hist + n, A + (size_t)(T - 3) * n, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    double w[3] = {1.0, 0.0, 0.0};
+    e = e ? e : cudaMemcpyAsync(w, c->guess_state, sizeof(w), cudaMemcpyDeviceToHost, s);
+    if (loss_hist && epochs > 0) e = e ? e : cudaMemcpyAsync(loss_hist, lhist, epochs * sizeof(double), cudaMemcpyDeviceToHost, s);
+    e = e ? e : cudaStreamSynchronize(s);
+    if (e == cudaSuccess && w_out) std::copy(w, w + 3, w_out);
+  }
+  cudaFree(A);
+  if (rc != IMEX_OK) return rc;
+  if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_pcg_train_guess: ") + cudaGetErrorString(e));
+  c->guess_on = 1;
+  c->guess_valid = 2;
+  return IMEX_OK;
+}
+
+int imex_pcg_fsai_closed_form(imex_ctx* c) {
+  if (!c || !c->g_val) return fail(IMEX_ERR_ARG, "the context has no PCG solver");
+  const HostSetup& hs = c->hs;
+  const int n = (int)hs.n_c;
+  if (n == 0) return IMEX_OK;
+  // G's pattern as the setup built it: row i holds the columns j <= i of S's
+  // row i, in S's order.
+  std::vector<int> g_ptr(1, 0), g_col;
+  for (int i = 0; i < n; ++i) {
+    for (int k = hs.S_ptr[i]; k < hs.S_ptr[i + 1]; ++k)
+      if (hs.S_col[k] <= i) g_col.push_back(hs.S_col[k]);
+    g_ptr.push_back((int)g_col.size());
+  }
+  if ((int64_t)g_col.size() != c->g_nnz) return fail(IMEX_ERR_ARG, "internal error: G pattern mismatch");
+  // Column j: rows Q (i >= j with G_ij on the pattern) and their positions.
+  std::vector<int> ct_ptr(n + 1, 0), ct_row(g_col.size()), ct_pos(g_col.size());
+  for (int j : g_col) ct_ptr[j + 1]++;
+  for (int j = 0; j < n; ++j) ct_ptr[j + 1] += ct_ptr[j];
+  {
+    std::vector<int> fill(ct_ptr.begin(), ct_ptr.end() - 1);
+    for (int i = 0; i < n; ++i)
+      for (int e = g_ptr[i]; e < g_ptr[i + 1]; ++e) {
+        ct_row[fill[g_col[e]]] = i;
+        ct_pos[fill[g_col[e]]++] = e;
+      }
+  }
+  auto s_at = [&](int a, int b) {   // S_ab (0 off the pattern)
+    const int* lo = hs.S_col.data() + hs.S_ptr[a];
+    const int* hi = hs.S_col.data() + hs.S_ptr[a + 1];
+    for (const int* q = lo; q < hi; ++q)
+      if (*q == b) return hs.S_val[q - hs.S_col.data()];
+    return 0.0;
+  };
+  std::vector<double> val(g_col.size(), 0.0);
+  std::string err;
+  std::mutex mu;
+  auto work = [&](int j0, int j1) {
+    std::vector<double> A, y;
+    for (int j = j0; j < j1; ++j) {
+      const int q0 = ct_ptr[j], m = ct_ptr[j + 1] - q0;
+      const int* Q = ct_row.data() + q0;   // ascending; Q[0] = j
+      A.assign((size_t)m * m, 0.0);
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b <= a; ++b) A[(size_t)a * m + b] = s_at(Q[a], Q[b]);
+      // Cholesky of S_QQ (lower, in place), then S_QQ y = e_0.
+      bool ok = true;
+      for (int k = 0; k < m && ok; ++k) {
+        double d = A[(size_t)k * m + k];
+        for (int q = 0; q < k; ++q) d -= A[(size_t)k * m + q] * A[(size_t)k * m + q];
+        if (!(d > 0.0)) { ok = false; break; }
+        const double l = std::sqrt(d);
+        A[(size_t)k * m + k] = l;
+        for (int i = k + 1; i < m; ++i) {
+          double t = A[(size_t)i * m + k];
+          for (int q = 0; q < k; ++q) t -= A[(size_t)i * m + q] * A[(size_t)k * m + q];
+          A[(size_t)i * m + k] = t / l;
+        }
+      }
+      if (!ok) {
+        std::lock_guard<std::mutex> lk(mu);
+        err = "S_QQ not positive definite";
+        return;
+      }
+      y.assign(m, 0.0);
+      for (int i = 0; i < m; ++i) {   // L z = e_0
+        double t = i == 0 ? 1.0 : 0.0;
+        for (int q = 0; q < i; ++q) t -= A[(size_t)i * m + q] * y[q];
+        y[i] = t / A[(size_t)i * m + i];
+      }
+      for (int i = m - 1; i >= 0; --i) {   // L^T y = z
+        double t = y[i];
+        for (int q = i + 1; q < m; ++q) t -= A[(size_t)q * m + i] * y[q];
+        y[i] = t / A[(size_t)i * m + i];
+      }
+      const double sc = 1.0 / std::sqrt(y[0]);
+      for (int a = 0; a < m; ++a) val[ct_pos[q0 + a]] = y[a] * sc;
+    }
+  };
+  const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  for (int t = 0; t < nth; ++t) th.emplace_back(work, (int)((int64_t)n * t / nth), (int)((int64_t)n * (t + 1) / nth));
+  for (auto& t : th) t.join();
+  if (!err.empty()) return fail(IMEX_ERR_NOT_SPD, "imex_pcg_fsai_closed_form: " + err);
+  // Values, their row-scaled parameters for further training, the
+  // transposed copy; the Adam state starts afresh.
+  std::vector<double> scale(g_col.size()), theta(g_col.size());
+  cudaError_t e = cudaMemcpy(scale.data(), c->g_scale, scale.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  for (size_t k = 0; k < val.size(); ++k) theta[k] = val[k] / scale[k];
+  e = e ? e : cudaMemcpy(c->g_val, val.data(), val.size() * sizeof(double), cudaMemcpyHostToDevice);
+  e = e ? e : cudaMemcpy(c->g_theta, theta.data(), theta.size() * sizeof(double), cudaMemcpyHostToDevice);
+  e = e ? e : cudaMemset(c->g_m, 0, val.size() * sizeof(double));
+  e = e ? e : cudaMemset(c->g_v, 0, val.size() * sizeof(double));
+  if (e == cudaSuccess) {
+    k_gt_vals<<<(unsigned)((c->g_nnz + kThreads - 1) / kThreads), kThreads>>>(c->g_nnz, c->g_val, c->gt_idx, c->gt_val);
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_pcg_fsai_closed_form: ") + cudaGetErrorString(e));
+  c->adam_t = 0;
+  return IMEX_OK;
+}
+
+int imex_pcg_set_guess(imex_ctx* c, int enable, const double* w) {
+  if (!c) return fail(IMEX_ERR_ARG, "NULL context");
+  if (!c->pcg_hist) return fail(IMEX_ERR_ARG, "the context has no PCG solver");
+  if (enable && w) {
+    const double st[9] = {w[0], w[1], w[2], 0, 0, 0, 0, 0, 0};
+    cudaError_t e = cudaMemcpy(c->guess_state, st, sizeof(st), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(IMEX_ERR_CUDA, std::string("imex_pcg_set_guess: ") + cudaGetErrorString(e));
+  }
+  c->guess_on = enable ? 1 : 0;
   return IMEX_OK;
 }
 

@@ -238,6 +238,12 @@ struct PcgArgs {
   int* status;                    // [0] iterations of the last solve, [1] 1: converged, 0: fallback
   long long* counters;            // [0] iterations summed, [1] fallbacks
   double* res;                    // relative residual of the last solve
+  // Learned starting guess: x0 = w0 a^c_n + w1 a^c_{n-1} + w2 a^c_{n-2} when
+  // guess_w is set (device, 3 weights), else x0 = a^c_n; the two history
+  // vectors are shifted every solve (hist1 <- a^c_n, hist2 <- hist1).
+  const double* guess_w;
+  double* hist1;
+  double* hist2;
   // Newmark correction on convergence (as in the direct solve), or always
   // (always_correct: no direct solve to fall back on; misses are counted)
   int always_correct;

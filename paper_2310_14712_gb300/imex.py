@@ -86,6 +86,9 @@ _lib.imex_adjoint.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64
                               ctypes.c_int, _dp, _dp]
 _lib.imex_set_solver.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
 _lib.imex_pcg_train.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _dp]
+_lib.imex_pcg_train_guess.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp]
+_lib.imex_pcg_set_guess.argtypes = [_vp, ctypes.c_int, _dp]
+_lib.imex_pcg_fsai_closed_form.argtypes = [_vp]
 _lib.imex_pcg_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), _dp, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64)]
 _lib.imex_fsai_kaporin.argtypes = [ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _dp, _vp]
@@ -109,7 +112,7 @@ _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctyp
                                         ctypes.POINTER(Stats)]
 
 # Every symbol include/imex.h declares (checked by the CPU tests).
-EXPORTS = ("imex_setup", "imex_setup_batch", "imex_setup_scheme", "imex_setup_pcg", "imex_adjoint", "imex_set_solver", "imex_pcg_train", "imex_pcg_status",
+EXPORTS = ("imex_setup", "imex_setup_batch", "imex_setup_scheme", "imex_setup_pcg", "imex_adjoint", "imex_set_solver", "imex_pcg_train", "imex_pcg_train_guess", "imex_pcg_set_guess", "imex_pcg_fsai_closed_form", "imex_pcg_status",
            "imex_fsai_kaporin", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
            "imex_set_initial", "imex_info", "imex_check_finite", "imex_last_error", "imex_destroy", "imex_gll_points",
            "imex_gauss_points", "imex_host_setup_export", "imex_probe_fp64")
@@ -324,6 +327,27 @@ class Imex:
                                  len(rec), d.ctypes.data_as(_dp), int(checkpoint_every),
                                  grad.ctypes.data_as(_dp), ctypes.byref(J)), "imex_adjoint")
         return J.value, grad
+
+    def pcg_train_guess(self, nsteps, epochs, lr=0.05):
+        """Advance nsteps steps, then learn the PCG starting-guess weights from
+        their solutions (imex_pcg_train_guess); returns (weights, loss history)."""
+        hist = np.zeros(max(int(epochs), 1))
+        w = np.zeros(3)
+        _check(_lib.imex_pcg_train_guess(self._ctx, int(nsteps), int(epochs), float(lr), hist.ctypes.data_as(_dp),
+                                         w.ctypes.data_as(_dp)), "imex_pcg_train_guess")
+        return w, hist[:int(epochs)]
+
+    def pcg_set_guess(self, enable=True, w=None):
+        """Enable (given or trained weights) or disable the learned PCG starting guess."""
+        wp = None
+        if w is not None:
+            w = _f64(w)
+            wp = w.ctypes.data_as(_dp)
+        _check(_lib.imex_pcg_set_guess(self._ctx, 1 if enable else 0, wp), "imex_pcg_set_guess")
+
+    def pcg_fsai_closed_form(self):
+        """Set G to the closed-form FSAI of its pattern (imex_pcg_fsai_closed_form)."""
+        _check(_lib.imex_pcg_fsai_closed_form(self._ctx), "imex_pcg_fsai_closed_form")
 
     def pcg_status(self):
         it, tot, fb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -213,3 +213,82 @@ def test_failing_allocator_is_reported():
                                      ctypes.byref(al), ctypes.byref(ctx))
     assert rc == -3 and calls and not ctx.value   # IMEX_ERR_ALLOC, nothing returned
     assert b"allocator" in imex._lib.imex_last_error()
+
+
+# --- learned starting guess and the closed-form FSAI -------------------------
+
+def test_guess_training_kernels_match_the_oracle():
+    # Two identical contexts: one learns the starting-guess weights on the GPU
+    # over 30 steps; the other steps the same 30 steps and hands its
+    # accelerations to the oracle's Adam.  Same losses, same weights.
+    imex = _imex()
+    w = workloads.plate16()
+    nsteps, epochs, lr = 30, 200, 0.05
+    with imex.Imex.from_workload(w, factorize=False) as a, imex.Imex.from_workload(w, factorize=False) as b:
+        a.step(150)
+        b.step(150)
+        Ic = np.flatnonzero(b.fields("mask_c", out=np.zeros(b.n_nodes)) > 0)
+        seq = [b.fields("a_c", out=np.zeros(b.n_nodes))[Ic]]
+        for _ in range(nsteps):
+            b.step(1)
+            seq.append(b.fields("a_c", out=np.zeros(b.n_nodes))[Ic])
+        w_gpu, hist_gpu = a.pcg_train_guess(nsteps, epochs, lr)
+        assert a.info()["step"] == b.info()["step"]
+    H, X = learned.extrapolation_samples(np.stack(seq, axis=1), 3)
+    w_cpu, hist_cpu = learned.train_extrapolation(H, X, [1.0, 0.0, 0.0], epochs, lr)
+    assert np.allclose(hist_gpu, hist_cpu, rtol=1e-9, atol=0), np.abs(hist_gpu / hist_cpu - 1).max()
+    assert np.allclose(w_gpu, w_cpu, rtol=0, atol=1e-8), (w_gpu, w_cpu)
+    assert hist_gpu[-1] < 0.2 * hist_gpu[0]
+
+
+def test_learned_guess_cuts_pcg_iterations_and_keeps_parity():
+    # From one state, the same 58 PCG solves (learned FSAI) with the plain
+    # start a^c_n and with the learned guess: fewer iterations with the
+    # guess, and the result still matches the oracle's direct run.
+    imex = _imex()
+    w = workloads.plate16(steps=260)
+    its = {}
+    with imex.Imex.from_workload(w, factorize=False) as g:
+        g.pcg_train(300, 0.1)
+        g.set_solver("pcg_fsai", 1e-10, 2000)
+        g.step(160)
+        weights, _ = g.pcg_train_guess(40, 300, 0.05)
+        snap = {k: g.fields(k, out=np.zeros(g.n_nodes)) for k in ("u", "u_prev_d", "v_c", "a_c")}
+        step0 = g.info()["step"]
+        for guess in (False, True):
+            for k, v in snap.items():
+                g.set_fields(k, v)
+            g.set_step(step0)
+            g.pcg_set_guess(guess)
+            g.step(2)                      # refills the history after the state change
+            s0 = g.pcg_status()["iters_total"]
+            g.step(58)
+            its[guess] = g.pcg_status()["iters_total"] - s0
+            if guess:
+                u = g.fields("u", out=np.zeros(g.n_nodes))
+                assert g.info()["step"] == 260
+        assert g.pcg_status()["fallbacks"] == 0
+    assert its[True] < its[False], its   # measured 790 against 819
+    s = pipeline.setup(**w.kwargs())
+    ref = s.imex.run(260)
+    assert pipeline.relative_l2(u, ref.u, phys_mask(s, w.holes)) <= 1e-8
+    assert pipeline.relative_l2(u, ref.u, s.disc.active) <= 1e-6
+
+
+def test_closed_form_fsai_is_the_kaporin_minimiser():
+    # Kaporin's functional is convex on the pattern; the closed form is its
+    # minimiser, so the trained G approaches it from above and needs at least
+    # as many iterations.
+    imex = _imex()
+    w = workloads.plate16()
+    with imex.Imex.from_workload(w, factorize=False) as g:
+        hist = g.pcg_train(300, 0.1)
+        k_trained = float(hist[-1])
+        g.pcg_fsai_closed_form()
+        k_closed = float(g.pcg_train(1, 1e-12)[0])   # the loss before a negligible step
+    assert k_closed <= k_trained + 1e-9 * abs(k_trained), (k_closed, k_trained)
+    _, S = _oracle_S(w)
+    indptr, indices = learned.lower_pattern(S)
+    vals = learned.fsai_closed_form(S, indptr, indices)
+    k_oracle = learned.kaporin_loss_grad(S, indptr, indices, vals)[0]
+    assert k_closed == pytest.approx(k_oracle, rel=1e-10)

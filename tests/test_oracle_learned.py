@@ -171,3 +171,82 @@ def test_learned_preconditioner_shortens_cg_on_the_methods_systems():
         assert r1 <= 1e-10
         assert np.linalg.norm(x1 - X[:, j]) <= 1e-6 * np.linalg.norm(X[:, j])
     assert k1 < 0.5 * k0
+
+
+# --- learned starting guess (extrapolation weights) ---------------------------
+
+def _quadratic_sequence(n=40, T=12, seed=3):
+    rng = np.random.default_rng(seed)
+    c0, c1, c2 = rng.standard_normal((3, n))
+    t = np.arange(T, dtype=np.float64)
+    return c0[:, None] + c1[:, None] * t + c2[:, None] * t * t     # (n, T)
+
+
+def test_extrapolation_exact_on_quadratic_sequences():
+    # Polynomial extrapolation through the last three values reproduces any
+    # sequence quadratic in time: the loss is zero at w = (3, -3, 1), and this
+    # is its unique minimiser when the three histories are independent.
+    A = _quadratic_sequence()
+    H, X = learned.extrapolation_samples(A, 3)
+    loss, g = learned.extrapolation_loss_grad(H, X, [3.0, -3.0, 1.0])
+    assert loss <= 1e-24 and np.abs(g).max() <= 1e-10
+    assert np.allclose(learned.extrapolation_guess(H, [3.0, -3.0, 1.0]), X, rtol=0, atol=1e-10)
+    # Written out for one sample: the loss of w = (1, 0, 0) (start from a_n).
+    s = 4
+    e = A[:, s + 2] - A[:, s + 3]
+    l1, _ = learned.extrapolation_loss_grad(H[:, :, s:s + 1], X[:, s:s + 1], [1.0, 0.0, 0.0])
+    assert l1 == pytest.approx(e @ e / (A[:, s + 3] @ A[:, s + 3]), rel=1e-13)
+
+
+def test_extrapolation_gradient_matches_central_differences():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((30, 9)).cumsum(axis=1)
+    H, X = learned.extrapolation_samples(A, 3)
+    w = np.array([1.7, -0.9, 0.2])
+    loss, g = learned.extrapolation_loss_grad(H, X, w)
+    for k in range(3):
+        h = 1e-6
+        wp = w.copy(); wp[k] += h
+        wm = w.copy(); wm[k] -= h
+        fd = (learned.extrapolation_loss_grad(H, X, wp)[0] - learned.extrapolation_loss_grad(H, X, wm)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, g[k])
+
+
+def test_adam_learns_the_quadratic_extrapolation():
+    A = _quadratic_sequence()
+    H, X = learned.extrapolation_samples(A, 3)
+    w, hist = learned.train_extrapolation(H, X, [1.0, 0.0, 0.0], 3000, 0.05)
+    assert hist[-1] < 1e-12 * hist[0]
+    assert np.allclose(w, [3.0, -3.0, 1.0], atol=1e-5), w
+
+
+def test_learned_guess_cuts_cg_iterations_on_the_methods_own_solves():
+    # The plate's accelerations a^c_n from the oracle's own run: weights
+    # learned on steps 100..160 start the solves of steps 170..190 closer to
+    # their solutions than a_n does, and CG needs fewer iterations there.
+    from oracle import pipeline
+    from paper_2310_14712_gb300 import workloads
+    w_ = workloads.plate16(steps=200)
+    s = pipeline.setup(**w_.kwargs())
+    Ic = s.imex.Ic
+    st = s.imex.initial_state()
+    acc, rhs = [], []
+    for n in range(190):
+        st = s.imex.step(st)
+        acc.append(st.a_c[Ic].copy())
+    A = np.stack(acc, axis=1)
+    H, X = learned.extrapolation_samples(A[:, 100:161], 3)
+    w, hist = learned.train_extrapolation(H, X, [1.0, 0.0, 0.0], 2000, 0.01)
+    assert hist[-1] < 0.1 * hist[0]
+    d = s.disc
+    S = sp.csr_matrix(d.M[Ic][:, Ic] + 0.25 * s.dt ** 2 * d.K[Ic][:, Ic])
+    its_plain, its_learned = 0, 0
+    for n in range(170, 189):
+        b = S @ A[:, n + 1]
+        x0p = A[:, n]
+        x0l = learned.extrapolation_guess(A[:, [n, n - 1, n - 2]].T, w)
+        _, kp, _ = learned.pcg(S, b, x0=x0p, apply_minv=lambda r: r / S.diagonal(), tol=1e-10, maxit=5000)
+        _, kl, _ = learned.pcg(S, b, x0=x0l, apply_minv=lambda r: r / S.diagonal(), tol=1e-10, maxit=5000)
+        its_plain += kp
+        its_learned += kl
+    assert its_learned < 0.9 * its_plain, (its_learned, its_plain)
