@@ -109,7 +109,9 @@ typedef struct {
   double residual_S, residual_M; /* relative residuals of a host replay of the device solve */
   int64_t solve_levels;    /* tree levels walked per pass of the implicit solve (one launch each) */
   int64_t solve_ctas;      /* CTAs of the widest solve launch */
-  int64_t solve_smem_bytes;/* shared memory per walk CTA (factor blocks staged when they fit) */
+  int64_t solve_smem_bytes;/* shared memory requested per walk CTA: at least solve_smem_needed,
+                              raised by the setup autotuner when a larger request (fewer CTAs of
+                              the explicit launch beside a walk CTA) measured faster */
   int64_t launches_per_step; /* kernel launches of one imex_step step */
   int64_t rhs_pairs;       /* (c-row, interface cell) pairs of K^c u: one P^d dot product each */
   int64_t ncols;           /* independent source columns (imex_setup_batch) */
@@ -131,6 +133,8 @@ typedef struct {
   int64_t large_supernodes;      /* walked supernodes of more than 256 diagonal or ancestor rows,
                                     solved by row chunks over many CTAs */
   int64_t max_rows;              /* largest ancestor row set of a supernode */
+  int64_t solve_smem_needed;     /* shared memory a walk CTA needs (factor blocks staged when
+                                    they fit) */
 } imex_stats;
 
 /*

@@ -757,6 +757,10 @@ struct imex_ctx {
   std::vector<int> lev_cta0, lev_ncta, lev_has_nodes;   // per walked level: CTA range
   int walk_smem_mode = 0;
   size_t smem_walk = 0, smem_top = 0;
+  // Dynamic shared memory requested per walk launch (>= smem_walk).  A
+  // larger request changes which CTAs of the neighbouring launches share an
+  // SM with a walk CTA; the setup autotuner times a few requests.
+  size_t smem_walk_req = 0;
   int ntop = 0;
   int *top_comp = nullptr, *top_r0 = nullptr, *top_r1 = nullptr;
   int *zsize = nullptr, *zbase = nullptr, *zrow = nullptr;
@@ -1186,7 +1190,7 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
     w.cta0 = c->lev_cta0[l];
     w.first = (fwd && l == 0) ? 1 : 0;
     cfg.gridDim = dim3(c->lev_ncta[l], c->ncols);
-    cfg.dynamicSmemBytes = c->smem_walk;
+    cfg.dynamicSmemBytes = c->smem_walk_req;
     if (c->walk_smem_mode)
       return fwd ? cudaLaunchKernelEx(&cfg, k_walk<true, true>, w) : cudaLaunchKernelEx(&cfg, k_walk<false, true>, w);
     return fwd ? cudaLaunchKernelEx(&cfg, k_walk<true, false>, w) : cudaLaunchKernelEx(&cfg, k_walk<false, false>, w);
@@ -1567,10 +1571,18 @@ int plan_panels(const HostSetup& hs, const std::vector<int>& big, int l, SolvePl
 int plan_solve(imex_ctx* c, SolvePlan& P) {
   const HostSetup& hs = c->hs;
   const int64_t nt = (int64_t)hs.tree.size();
+  // FP64 work of a supernode in a walk CTA: its triangular and rectangular
+  // products and, at level 0 (which forms the right-hand sides), one P^d dot
+  // product per (row, interface cell) pair of its rows, issued in batches
+  // of 16 (the kernel's pair_product).
+  const int64_t pair_cost = ((int64_t)hs.Pd + 15) / 16 * 16;
   auto node_work = [&](int t) {
     const TreeNode& T = hs.tree[t];
     const int64_t b = T.end - T.beg, m = (int64_t)T.rows.size();
-    return b * b / 2 + m * b + b;
+    int64_t w = b * b / 2 + m * b + b;
+    if (T.level == 0)
+      for (int r = T.beg; r < T.end; ++r) w += pair_cost * (hs.contrib_ptr[r + 1] - hs.contrib_ptr[r]);
+    return w;
   };
   // Split level of each component: nodes at level >= lz form the dense top part.
   std::vector<int> lz(hs.ncomp, 1), zsize(hs.ncomp, 0), zbase(hs.ncomp, 0), zrow, zpos(hs.n_c, -1);
@@ -1743,7 +1755,7 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
         if (l == 0) pairs += npairs_of(r);
       }
       ints += l == 0 ? 4 * b + 4 * pairs : 0;
-      return (b | 1) * b + (m | 1) * b + 2 * b + m + (Pd + 1) * pairs + (ints + 1) / 2 + 2;
+      return b * (b + 1) / 2 + (m | 1) * b + 2 * b + m + (Pd + 1) * pairs + (ints + 1) / 2 + 2;
     };
     int target = std::max(1, std::min<int>((int)nodes.size(), kTargetCTAs));
     if (l == 0) {
@@ -1784,7 +1796,7 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
         for (int q = 1; q < (int)per.size(); ++q)
           if (work[q] < work[best]) best = q;
         xrows[best].push_back(r);
-        work[best] += (int64_t)Pd * npairs_of(r) + 1;
+        work[best] += pair_cost * npairs_of(r) + 1;
       }
       for (auto& xr : xrows) std::sort(xr.begin(), xr.end());
     }
@@ -1800,10 +1812,13 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
       int64_t local = 0;
       int nslot = 0, nm = 0, npair = 0;
       std::vector<int> slot0(list.size()), moff(list.size());
+      // Per supernode: L_tt^{-1} packed by diagonals (diagonal d: entries
+      // (d + i, i), i < b - d), then L_{rows,t} column-major with an odd
+      // leading dimension.
       for (size_t q = 0; q < list.size(); ++q) {
         const TreeNode& T = hs.tree[list[q]];
         const int b = T.end - T.beg, m = (int)T.rows.size();
-        const int ldi = b | 1, ldr = m | 1;
+        const int ldr = m | 1;
         P.node_boff[list[q]] = local;
         slot0[q] = nslot;
         moff[q] = nm;
@@ -1813,12 +1828,12 @@ int plan_solve(imex_ctx* c, SolvePlan& P) {
           std::vector<double>& out = (F == &hs.S) ? P.blobS : P.blobM;
           const double* Li = F->vals.data() + T.off_diag;
           const double* L21 = F->vals.data() + T.off_rect;
-          for (int j = 0; j < b; ++j)
-            for (int i = 0; i < ldi; ++i) out.push_back(i < b ? Li[i + (size_t)b * j] : 0.0);
+          for (int d = 0; d < b; ++d)
+            for (int i = 0; i + d < b; ++i) out.push_back(Li[(i + d) + (size_t)b * i]);
           for (int j = 0; j < b; ++j)
             for (int i = 0; i < ldr; ++i) out.push_back(i < m ? L21[i + (size_t)m * j] : 0.0);
         }
-        local += (int64_t)ldi * b + (int64_t)ldr * b;
+        local += (int64_t)b * (b + 1) / 2 + (int64_t)ldr * b;
         P.cta_nodes.push_back(list[q]);
       }
       if (local % 2) { P.blobS.push_back(0.0); P.blobM.push_back(0.0); ++local; }
@@ -2483,6 +2498,7 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       c->walk_smem_mode = used + blob <= kMaxDynSmem ? 1 : 0;
       c->walk_max_blob = c->walk_smem_mode ? plan.max_blob : 0;
       c->smem_walk = used + (c->walk_smem_mode ? blob : 0);
+      c->smem_walk_req = c->smem_walk;
       c->lev_has_nodes = plan.lev_has_nodes;
       c->top_max_zn = std::max(2, plan.max_zn + (plan.max_zn & 1));
       c->top_max_arows = plan.max_arows;
@@ -2850,7 +2866,7 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
 static int autotune_tile_steps(imex_ctx* c) {
   const HostSetup& hs = c->hs;
   if (c->hetero || !c->factorized || hs.n_c == 0) return IMEX_OK;
-  if (explicit_env_variant(c) >= 0) return IMEX_OK;
+  const bool pinned = explicit_env_variant(c) >= 0;
   const size_t nn = (size_t)hs.nnodes * c->ncols, ncv = (size_t)hs.n_c * c->ncols;
   double* save = nullptr;
   if (cudaMalloc(&save, (2 * nn + 2 * ncv) * sizeof(double)) != cudaSuccess) {
@@ -2878,7 +2894,7 @@ static int autotune_tile_steps(imex_ctx* c) {
   float best = 1e30f;
   int best_var = c->xvar;
   int rc = IMEX_OK;
-  for (int k = 0; k < explicit_variants(c) && e == cudaSuccess && rc == IMEX_OK; ++k) {
+  for (int k = 0; k < explicit_variants(c) && !pinned && e == cudaSuccess && rc == IMEX_OK; ++k) {
     e = use_explicit(c, k);
     e = e ? e : copy_state(false);
     if (e != cudaSuccess) break;
@@ -2895,9 +2911,36 @@ static int autotune_tile_steps(imex_ctx* c) {
       best_var = k;
     }
   }
+  if (!pinned) e = e ? e : use_explicit(c, best_var);
+  // Shared memory requested per walk launch: what the walk needs, or enough
+  // that at most one, or no, CTA of the explicit launch can share an SM with
+  // it (140 and 184 KB); one whole step each, the fastest kept.
+  {
+    const size_t cand[3] = {c->smem_walk, std::max<size_t>(c->smem_walk, 140 * 1024),
+                            std::max<size_t>(c->smem_walk, 184 * 1024)};
+    float wbest = 1e30f;
+    size_t req = c->smem_walk;
+    for (int k = 0; k < 3 && e == cudaSuccess && rc == IMEX_OK; ++k) {
+      if (cand[k] > kMaxDynSmem || (k > 0 && cand[k] == cand[k - 1])) continue;
+      c->smem_walk_req = cand[k];
+      e = copy_state(false);
+      if (e != cudaSuccess) break;
+      rc = step_once(c, nullptr, nullptr);
+      e = cudaEventRecord(ev[0], nullptr);
+      for (int r = 0; r < 4 && rc == IMEX_OK && e == cudaSuccess; ++r) rc = step_once(c, nullptr, nullptr);
+      e = e ? e : cudaEventRecord(ev[1], nullptr);
+      e = e ? e : cudaEventSynchronize(ev[1]);
+      float ms = 0.f;
+      e = e ? e : cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (e == cudaSuccess && ms < wbest) {
+        wbest = ms;
+        req = cand[k];
+      }
+    }
+    c->smem_walk_req = req;
+  }
   if (ev[0]) cudaEventDestroy(ev[0]);
   if (ev[1]) cudaEventDestroy(ev[1]);
-  e = e ? e : use_explicit(c, best_var);
   e = e ? e : copy_state(false);
   e = e ? e : cudaDeviceSynchronize();
   cudaFree(save);
@@ -3530,7 +3573,8 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   int64_t widest = c->ntop;
   for (int n : c->lev_ncta) widest = std::max<int64_t>(widest, n);
   st->solve_ctas = widest;
-  st->solve_smem_bytes = (int64_t)c->smem_walk;
+  st->solve_smem_bytes = (int64_t)c->smem_walk_req;
+  st->solve_smem_needed = (int64_t)c->smem_walk;
   st->launches_per_step = launches_per_step(c);
   st->rhs_pairs = (int64_t)c->hs.contrib_pos.size();
   st->ncols = c->ncols;

@@ -107,9 +107,9 @@ struct ExplicitArgs {
 
 // One level of the supernodal walk of A5 (forward or backward), all
 // components at once.  The level's supernodes are packed into CTAs; each
-// CTA's blocks [L_tt^{-1} (ld b|1) | L_{rows,t} (ld m|1)] are stored
-// contiguously in `blob`, its index list (layout in imex.cu, WalkList) in
-// `ilist`.  The first forward launch also forms the right-hand sides (A4).
+// CTA's blocks [L_tt^{-1} packed by diagonals | L_{rows,t} (ld m|1)] are
+// stored contiguously in `blob`, its index list (layout in imex.cu,
+// WalkList) in `ilist`.  The first forward launch also forms the right-hand sides (A4).
 struct WalkArgs {
   int cta0;                     // first CTA of this level in the per-CTA arrays
   const double* blob;

@@ -944,43 +944,6 @@ __device__ __forceinline__ void async_copy_wait() {
   __syncthreads();
 }
 
-// One warp, one supernode product: lanes own rows.  out[i] = sum_j M[i si + j sj] v[j]
-// for i < nrows, restricted to j <= i (tri > 0) or j >= i (tri < 0).
-// (si, sj) = (1, ld) reads a column-major block, (ld, 1) its transpose; with an
-// odd ld both are free of shared-memory bank conflicts.
-template <int R>
-__device__ __forceinline__ void warp_gemv_r(const double* M, int si, int sj, int nrows, int ncols,
-                                            const double* v, int tri, double* out, int lane) {
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int i = lane + 32 * r;
-    if (i >= nrows) break;
-    int j0 = 0, j1 = ncols;
-    if (tri > 0) j1 = min(ncols, i + 1);
-    if (tri < 0) j0 = i;
-    double s0 = 0.0, s1 = 0.0;
-    int j = j0;
-    for (; j + 2 <= j1; j += 2) {
-      s0 = fma(M[(size_t)i * si + (size_t)j * sj], v[j], s0);
-      s1 = fma(M[(size_t)i * si + (size_t)(j + 1) * sj], v[j + 1], s1);
-    }
-    if (j < j1) s0 = fma(M[(size_t)i * si + (size_t)j * sj], v[j], s0);
-    out[i] = s0 + s1;
-  }
-}
-
-__device__ __forceinline__ void warp_gemv(const double* M, int si, int sj, int nrows, int ncols,
-                                          const double* v, int tri, double* out, int lane) {
-  switch ((nrows + 31) / 32) {
-    case 0: break;
-    case 1: warp_gemv_r<1>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
-    case 2: warp_gemv_r<2>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
-    case 3: warp_gemv_r<3>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
-    case 4: warp_gemv_r<4>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
-    default: warp_gemv_r<8>(M, si, sj, nrows, ncols, v, tri, out, lane); break;
-  }
-}
-
 // Newmark correction of one implicit row (Fig. TrapCDMIMEX "Correction"), or
 // the initial acceleration only (mode 1), on one column's fields.
 struct Corr {
@@ -1085,6 +1048,15 @@ __device__ __forceinline__ double pair_product(const WalkArgs& a, const double* 
   return s0 + s1;
 }
 
+// Diagonal blocks L_tt^{-1} (b x b, lower triangular) are stored packed by
+// diagonals: diagonal d (entries (d + i, i), i < b - d) starts at
+// d b - d (d - 1) / 2, and L_{rows,t} follows at tri_size(b).  Row i of the
+// forward product reads entry (i, i - d) and column i of the backward
+// product entry (i + d, i) at step d: in both, the lanes of a warp
+// (consecutive i of one block) read consecutive words, and only the
+// triangle is stored, staged and read.
+__device__ __forceinline__ int tri_size(int b) { return b * (b + 1) / 2; }
+
 template <bool kForward, bool kSmem>
 __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
   extern __shared__ __align__(16) double sm[];
@@ -1181,18 +1153,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
       }
     }
     __syncthreads();
-    // y = L_tt^{-1} g, every row of every supernode of this CTA.
+    // y = L_tt^{-1} g, every row of every supernode of this CTA; row i
+    // reads entry (i, i - d) at d = 0, 1, ..., i (see tri_size).
     for (int sl = tid; sl < nslot; sl += kThreads) {
       const int* nd = L.node + 8 * L.slot[4 * sl];
-      const int b = nd[2], s0 = nd[4], i = sl - s0, ldi = b | 1;
-      const double* Li = B + nd[6];
+      const int b = nd[2], s0 = nd[4], i = sl - s0;
+      const double* Lp = B + nd[6];
+      const double* g = vg + s0 + i;   // g[-d] = g_{i-d}
       double y0 = 0.0, y1 = 0.0;
-      int j = 0;
-      for (; j + 2 <= i + 1; j += 2) {
-        y0 = fma(Li[i + ldi * j], vg[s0 + j], y0);
-        y1 = fma(Li[i + ldi * (j + 1)], vg[s0 + j + 1], y1);
+      int d = 0, q = i;
+      for (; d + 2 <= i + 1; d += 2) {
+        y0 = fma(Lp[q], g[-d], y0);
+        q += b - d - 1;
+        y1 = fma(Lp[q], g[-d - 1], y1);
+        q += b - d - 2;
       }
-      if (j <= i) y0 = fma(Li[i + ldi * j], vg[s0 + j], y0);
+      if (d <= i) y0 = fma(Lp[q], g[-d], y0);
       const double y = y0 + y1;
       vy[sl] = y;
       sol[nd[1] + i] = y;
@@ -1201,8 +1177,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
     // upd_t = L_{rows,t} y_t.
     for (int k = tid; k < nm; k += kThreads) {
       const int* nd = L.node + 8 * L.anc[2 * k];
-      const int b = nd[2], m = nd[3], s0 = nd[4], kk = k - nd[5], ldi = b | 1, ldr = m | 1;
-      const double* L21 = B + nd[6] + (size_t)ldi * b;
+      const int b = nd[2], m = nd[3], s0 = nd[4], kk = k - nd[5], ldr = m | 1;
+      const double* L21 = B + nd[6] + tri_size(b);
       double u0 = 0.0, u1 = 0.0;
       int j = 0;
       for (; j + 2 <= b; j += 2) {
@@ -1222,8 +1198,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
     // h = y_t - L_{rows,t}^T x_rows.
     for (int sl = tid; sl < nslot; sl += kThreads) {
       const int* nd = L.node + 8 * L.slot[4 * sl];
-      const int b = nd[2], m = nd[3], i = sl - nd[4], mo = nd[5], ldi = b | 1, ldr = m | 1;
-      const double* L21 = B + nd[6] + (size_t)ldi * b + (size_t)ldr * i;
+      const int b = nd[2], m = nd[3], i = sl - nd[4], mo = nd[5], ldr = m | 1;
+      const double* L21 = B + nd[6] + tri_size(b) + (size_t)ldr * i;
       double h0 = 0.0, h1 = 0.0;
       int k = 0;
       for (; k + 2 <= m; k += 2) {
@@ -1234,18 +1210,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
       vy[sl] = vg[sl] - (h0 + h1);
     }
     __syncthreads();
-    // x_t = L_tt^{-T} h, then the correction of the row.
+    // x_t = L_tt^{-T} h, then the correction of the row; column i reads
+    // entry (i + d, i) at d = 0, 1, ..., b - 1 - i.
     for (int sl = tid; sl < nslot; sl += kThreads) {
       const int* nd = L.node + 8 * L.slot[4 * sl];
-      const int b = nd[2], s0 = nd[4], i = sl - s0, ldi = b | 1;
-      const double* Lc = B + nd[6] + (size_t)ldi * i;
+      const int b = nd[2], s0 = nd[4], i = sl - s0, n = b - i;
+      const double* Lp = B + nd[6];
+      const double* h = vy + s0 + i;   // h[d] = h_{i+d}
       double x0 = 0.0, x1 = 0.0;
-      int j = i;
-      for (; j + 2 <= b; j += 2) {
-        x0 = fma(Lc[j], vy[s0 + j], x0);
-        x1 = fma(Lc[j + 1], vy[s0 + j + 1], x1);
+      int d = 0, q = i;
+      for (; d + 2 <= n; d += 2) {
+        x0 = fma(Lp[q], h[d], x0);
+        q += b - d;
+        x1 = fma(Lp[q], h[d + 1], x1);
+        q += b - d - 1;
       }
-      if (j < b) x0 = fma(Lc[j], vy[s0 + j], x0);
+      if (d < n) x0 = fma(Lp[q], h[d], x0);
       const double x = x0 + x1;
       sol[nd[1] + i] = x;
       if (sl < tid + kThreads) cor.row_pre(nd[1] + i, x, pre_node[0], pre_v[0], pre_a[0]);

@@ -117,8 +117,9 @@ def test_orders_ragged_grid(p, variant, monkeypatch):
     monkeypatch.setenv("IMEX_EXPLICIT_TILE", variant)
     if variant.startswith("sweep"):
         monkeypatch.setenv("IMEX_SWEEP_CTAS", "3")
-    w = _box(13, p, [[0.55, 0.95, 0.21, 0.21]], ncy=7, hi=(1.3, 0.7))
-    _check_run(w, 40)
+    w = _box(13, p, [[0.55, 0.62, 0.21, 0.21]], ncy=7, hi=(1.3, 0.7))
+    e_phys, e_all, info = _check_run(w, 40)
+    assert info["n_c"] > 0
 
 
 def test_no_holes_all_explicit():
