@@ -52,7 +52,15 @@ L2_FLUSH_BYTES = 256 << 20
 # the first walk also forming the right-hand sides).
 PHASES = ("k_explicit2d", "k_walk+k_top")
 # Explicit-apply variants of the setup autotuner (imex_info explicit_variant).
-EXPLICIT_VARIANTS = ("tiles_large", "tiles_small", "sweep", "sweep_short")
+EXPLICIT_VARIANTS = ("tiles_large", "tiles_small", "sweep", "sweep_short", "tiles_large_split1",
+                     "tiles_large_split2", "tiles_small_split2", "tiles_small_split4")
+
+
+def explicit_autotune_us(st):
+    """Setup timing of every explicit candidate (one whole step, us; None: not timed)."""
+    us = [st["explicit_tile_us_large"], st["explicit_tile_us_small"], st["explicit_sweep_us"],
+          st["explicit_sweep_short_us"]] + list(st["explicit_split_us"])
+    return {n: (v or None) for n, v in zip(EXPLICIT_VARIANTS, us)}
 
 
 # ncu summaries that carry each phase's DRAM bytes per launch (see profiles/).
@@ -130,9 +138,7 @@ def measure_batched(imex, workloads, steps, stream, flush):
         n_act = st["n_d"] + st["n_c"]
         out[label] = {"value": n_act * ncols * steps / (ms * 1e-3), "ms_per_step": ms / steps,
                       "ncols": ncols, "explicit_variant": EXPLICIT_VARIANTS[st["explicit_variant"]],
-                      "explicit_autotune_us": {n: st[k] or None for n, k in zip(EXPLICIT_VARIANTS, (
-                          "explicit_tile_us_large", "explicit_tile_us_small", "explicit_sweep_us",
-                          "explicit_sweep_short_us"))}}
+                      "explicit_autotune_us": explicit_autotune_us(st)}
         g.close()
     b = out["batched"]
     b.update({"workload": "multisource: [0,1]^2 minus a centred circle r=0.2, 16x16 cells, p=4, "
@@ -577,7 +583,7 @@ def run_gpu(args):
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     ach_gflops = alg[dom]["flops"] / (per_launch_ms[dom] * 1e-3) / 1e9
-    xkern = "k_sweep2d" if st["explicit_variant"] >= 2 else "k_explicit2d"
+    xkern = "k_sweep2d" if st["explicit_variant"] in (2, 3) else "k_explicit2d"
     roof = {"kernel": xkern if dom == "k_explicit2d" else dom, "bound": "alu", "achieved": ach_gflops / 1e3, "peak": peak_gflops / 1e3,
             "unit": "TFLOP/s", "frac": ach_gflops / peak_gflops,
             "traffic": profiled_traffic(dom, args.workload), "traffic_unit": "bytes per launch (ncu)",
@@ -604,10 +610,10 @@ def run_gpu(args):
                    "dt": st["dt"], "solve_levels": st["solve_levels"], "solve_ctas": st["solve_ctas"],
                    "solve_smem_bytes": st["solve_smem_bytes"],
                    "explicit_variant": EXPLICIT_VARIANTS[st["explicit_variant"]],
-                   "explicit_autotune_us": {n: st[k] or None for n, k in zip(EXPLICIT_VARIANTS, (
-                       "explicit_tile_us_large", "explicit_tile_us_small", "explicit_sweep_us",
-                       "explicit_sweep_short_us"))},
-                   "explicit_autotune_basis": "one whole step per candidate at setup (state restored)",
+                   "explicit_autotune_us": explicit_autotune_us(st),
+                   "explicit_autotune_basis": ("one whole step per candidate at setup (state restored), "
+                                               "best over the walk launches' shared-memory requests"),
+                   "solve_smem_request": st["solve_smem_bytes"], "solve_smem_needed": st["solve_smem_needed"],
                    "warm_kernel_ms": None,
                    "l2": "flushed (256 MB write) between timed steps",
                    "step_timing": "CUDA events on the launching stream at the boundaries of each timed step",

@@ -127,7 +127,10 @@ typedef struct {
   int64_t factorized;            /* 1: factorised implicit solve available; 0: imex_setup_pcg */
   int64_t explicit_variant;      /* explicit apply in use: 0 larger tiles, 1 smaller tiles,
                                     2 persistent strip sweep, 3 the sweep in shorter chunks with
-                                    more CTAs per SM (2D; autotuned at setup) */
+                                    more CTAs per SM, 4..7 the split launch (explicit_split_us)
+                                    (2D; autotuned at setup, IMEX_EXPLICIT_TILE=large|small|sweep|
+                                    sweep_short|large_split1|large_split2|small_split2|
+                                    small_split4 pins it) */
   double explicit_sweep_us;      /* setup timing of variant 2 (as the tile timings) */
   double explicit_sweep_short_us;/* setup timing of variant 3 */
   int64_t large_supernodes;      /* walked supernodes of more than 256 diagonal or ancestor rows,
@@ -135,6 +138,11 @@ typedef struct {
   int64_t max_rows;              /* largest ancestor row set of a supernode */
   int64_t solve_smem_needed;     /* shared memory a walk CTA needs (factor blocks staged when
                                     they fit) */
+  double explicit_split_us[4];   /* setup timings of variants 4..7: the split launch (the tiles
+                                    owning nodes the implicit solve reads and the prediction, then
+                                    the solve, while the other tiles run on a second stream with
+                                    1 or 2 CTAs per SM (larger tiles) or 2 or 4 (smaller tiles);
+                                    2D factorised contexts, direct solve; 0: not timed) */
 } imex_stats;
 
 /*

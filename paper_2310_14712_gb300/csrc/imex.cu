@@ -699,7 +699,16 @@ constexpr int kSweepCells[10] = {0, 0, 32, 16, 10, 8, 6, 5, 4, 4};
 //     resident CTAs per SM (kSweepMinBlocks[1][P]).
 constexpr int kSweepMinBlocks[2][10] = {{0, 0, 3, 3, 3, 3, 2, 2, 2, 1}, {0, 0, 4, 4, 4, 4, 3, 3, 3, 2}};
 constexpr int kExplicitSweep = 2, kExplicitSweepShort = 3;
-const char* const kExplicitNames[4] = {"large", "small", "sweep", "sweep_short"};
+// Explicit candidates of the autotuner: the kernel form (tiles, strip sweep)
+// and, for tiles, the split launch: the tiles whose nodes the implicit solve
+// reads (with the prediction), then the solve, while the other tiles run on
+// a second stream with a fixed number of CTAs per SM.  Split candidate s
+// (variant 4 + s) uses tile form kSplitTile[s] with kSplitPerSM[s] CTAs.
+constexpr int kExplicitSplit = 4, kSplitVariants = 4;
+constexpr int kSplitTile[kSplitVariants] = {0, 0, 1, 1};
+constexpr int kSplitPerSM[kSplitVariants] = {1, 2, 2, 4};
+const char* const kExplicitNames[8] = {"large",        "small",        "sweep",        "sweep_short",
+                                       "large_split1", "large_split2", "small_split2", "small_split4"};
 template <int P>
 constexpr int sweep_chunk(int short_chunks) { return short_chunks ? (kSweepCells[P] + 1) / 2 : kSweepCells[P]; }
 // 3D (P <= 5): tiles of TC^3 cells.
@@ -828,8 +837,18 @@ struct imex_ctx {
   Ops2D ops{};
   int TC = 4, ntx = 1, nty = 1, ntz = 1;
   Ops3D ops3{};
-  int xvar = 0;                   // explicit variant: 0 large tile, 1 small tile, 2/3 sweep (autotuned)
-  float tile_us[4] = {0.f, 0.f, 0.f, 0.f};  // measured time of each candidate (0: not timed)
+  int xvar = 0;                   // explicit kernel form: 0 large tile, 1 small tile, 2/3 sweep (autotuned)
+  int xsplit = 0;                 // split launch in use (variant 4 + split candidate; autotuned)
+  int split_per_sm = 1;           // CTAs per SM of the split launch's second half
+  float tile_us[8] = {};          // measured time of each candidate (0: not timed)
+  // Split explicit launch (2D tiles): per tile size, the tiles owning an I_d
+  // node of an interface cell (read by the implicit solve) and the others,
+  // which run on the stream `side` beside the solve.
+  int split_ok = 0;
+  int *tile_near[2] = {nullptr, nullptr}, *tile_far[2] = {nullptr, nullptr};
+  int n_near[2] = {0, 0}, n_far[2] = {0, 0};
+  cudaStream_t side = nullptr;
+  cudaEvent_t ov_fork = nullptr, ov_join = nullptr;
   int explicit_per_sm = 1;    // resident CTAs of the explicit kernel per SM
   int num_sms = 152;
   size_t smem_explicit = 0;
@@ -862,16 +881,17 @@ int check_launch(const char* what) {
 
 template <int P>
 void launch_explicit(imex_ctx* c, const ExplicitArgs& ea, int grid, cudaStream_t s) {
+  const dim3 g(grid, ea.persistent ? 1 : c->ncols);   // a persistent launch loops over the columns
   if (c->xvar == kExplicitSweep)
     k_sweep2d<P, kSweepCells[P], sweep_chunk<P>(0), kSweepMinBlocks[0][P]>
-        <<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
+        <<<g, kThreads, c->smem_explicit, s>>>(ea, c->ops);
   else if (c->xvar == kExplicitSweepShort)
     k_sweep2d<P, kSweepCells[P], sweep_chunk<P>(1), kSweepMinBlocks[1][P]>
-        <<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
+        <<<g, kThreads, c->smem_explicit, s>>>(ea, c->ops);
   else if (c->xvar == 1)
-    k_explicit2d<P, kTileSmall[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
+    k_explicit2d<P, kTileSmall[P]><<<g, kThreads, c->smem_explicit, s>>>(ea, c->ops);
   else
-    k_explicit2d<P, kTileLarge[P]><<<dim3(grid, c->ncols), kThreads, c->smem_explicit, s>>>(ea, c->ops);
+    k_explicit2d<P, kTileLarge[P]><<<g, kThreads, c->smem_explicit, s>>>(ea, c->ops);
 }
 
 template <int P>
@@ -990,7 +1010,9 @@ size_t sweep_smem_doubles(int P, int short_chunks) {
 
 // Number of explicit variants of a context: tiles (large, small) and, in 2D,
 // the sweep.
-int explicit_variants(const imex_ctx* c) { return c->hs.dim == 3 ? 2 : 4; }
+int explicit_variants(const imex_ctx* c) {
+  return c->hs.dim == 3 ? 2 : (c->split_ok ? kExplicitSplit + kSplitVariants : 4);
+}
 
 // Select an explicit variant: tile counts (for the sweep: ntx = its CTAs),
 // shared memory and occupancy follow it.
@@ -998,6 +1020,11 @@ cudaError_t use_explicit(imex_ctx* c, int var) {
   const HostSetup& hs = c->hs;
   const bool d3 = hs.dim == 3;
   if (var < 0 || var >= explicit_variants(c)) var = 0;
+  c->xsplit = var >= kExplicitSplit ? 1 : 0;
+  if (c->xsplit) {
+    c->split_per_sm = kSplitPerSM[var - kExplicitSplit];
+    var = kSplitTile[var - kExplicitSplit];
+  }
   c->xvar = var;
   if (var == kExplicitSweep || var == kExplicitSweepShort) {
     c->TC = kSweepCells[hs.P];
@@ -1074,6 +1101,7 @@ ExplicitArgs explicit_args(imex_ctx* c, const double* U, const double* W, double
   ea.dt = hs.dt;
   ea.cs_node = hs.nnodes;
   ea.cs_c = hs.n_c;
+  ea.ncols = c->ncols;
   return ea;
 }
 
@@ -1246,6 +1274,19 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
     if (e == cudaSuccess && c->lev_has_nodes[l]) e = walk(l, false);
   }
   return e;
+}
+
+// The split candidate in use (index into kSplitTile / kSplitPerSM).
+int split_index(const imex_ctx* c) {
+  for (int s = 0; s < kSplitVariants; ++s)
+    if (kSplitTile[s] == c->xvar && kSplitPerSM[s] == c->split_per_sm) return s;
+  return 0;
+}
+
+// The split explicit launch is in use (see step_once): direct solve by the
+// launch chain, whose launches are not cooperative.
+bool split_active(const imex_ctx* c) {
+  return c->xsplit && c->split_ok && c->hs.n_d > 0 && c->solver == IMEX_SOLVER_DIRECT;
 }
 
 // Kernel launches of one step.
@@ -2525,6 +2566,36 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     }
     const int64_t nif = (int64_t)hs.if_cell.size();
     const size_t nblobcta = std::max<size_t>(plan.blob_off.size(), 1);
+    // Split explicit launch (2D tiles): per tile size, the tiles owning an
+    // I_d node of an interface cell (the solve reads its u_pred) and the others.
+    std::vector<int> tile_lists[2][2];   // [tile size][near, far]
+    bool split_tiles = false;
+    if (hs.dim == 2 && factorize && !c->hetero && hs.n_c > 0 && hs.n_d > 0) {
+      std::vector<uint8_t> need(hs.nnodes, 0);
+      const int ncx = hs.pb.ncells[0], nx = hs.nn[0], ny = hs.nn[1], p = hs.p;
+      for (int cid : hs.if_cell) {
+        const int cx = cid % ncx, cy = cid / ncx;
+        for (int j = 0; j <= p; ++j)
+          for (int i = 0; i <= p; ++i) {
+            const int64_t g = (int64_t)(cy * p + j) * nx + cx * p + i;
+            if (hs.node_class[g] == NODE_D) need[g] = 1;
+          }
+      }
+      for (int v = 0; v < 2; ++v) {
+        const int OX = (v ? kTileSmall[hs.P] : kTileLarge[hs.P]) * p;
+        const int ntx = (nx + OX - 1) / OX, nty = (ny + OX - 1) / OX;
+        for (int ty = 0; ty < nty; ++ty)
+          for (int tx = 0; tx < ntx; ++tx) {
+            bool near = false;
+            for (int y = ty * OX; y < std::min(ny, ty * OX + OX) && !near; ++y)
+              for (int x = tx * OX; x < std::min(nx, tx * OX + OX) && !near; ++x) near = need[(int64_t)y * nx + x];
+            tile_lists[v][near ? 0 : 1].push_back(ty * ntx + tx);
+          }
+        c->n_near[v] = (int)tile_lists[v][0].size();
+        c->n_far[v] = (int)tile_lists[v][1].size();
+      }
+      split_tiles = c->n_far[0] > 0 && c->n_far[1] > 0;
+    }
 
     Arena ar;
     ar.add(&c->U[0], nn * ncols);
@@ -2571,6 +2642,10 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     ar.add(&c->zA_off, std::max<size_t>(plan.zA_off.size(), 1));
     ar.add(&c->zA_S, std::max<size_t>(plan.zA_S.size(), 1));
     ar.add(&c->zA_M, std::max<size_t>(plan.zA_M.size(), 1));
+    for (int v = 0; v < 2; ++v) {
+      ar.add(&c->tile_near[v], std::max<size_t>(tile_lists[v][0].size(), 1));
+      ar.add(&c->tile_far[v], std::max<size_t>(tile_lists[v][1].size(), 1));
+    }
     {
       const int64_t ncm = std::max<int64_t>(nc, 1), gnz = std::max<int64_t>(c->g_nnz, 1);
       ar.add(&c->s_ptr, hs.S_ptr.size());
@@ -2740,6 +2815,10 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->pan_aoff, plan.pan_aoff);
     e = e ? e : upload(c->panS, plan.panS);
     e = e ? e : upload(c->panM, plan.panM);
+    for (int v = 0; v < 2; ++v) {
+      e = e ? e : upload(c->tile_near[v], tile_lists[v][0]);
+      e = e ? e : upload(c->tile_far[v], tile_lists[v][1]);
+    }
     for (auto fn : {k_walk<true, true>, k_walk<false, true>, k_walk<true, false>, k_walk<false, false>})
       if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
     if (e == cudaSuccess)
@@ -2750,6 +2829,15 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       int nsm = 0;
       e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
       c->num_sms = std::max(1, nsm);
+    }
+    // The side stream and events of the split explicit launch.
+    if (e == cudaSuccess && split_tiles) {
+      int lo = 0, hi = 0;
+      e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+      e = e ? e : cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, lo);
+      e = e ? e : cudaEventCreateWithFlags(&c->ov_fork, cudaEventDisableTiming);
+      e = e ? e : cudaEventCreateWithFlags(&c->ov_join, cudaEventDisableTiming);
+      c->split_ok = e == cudaSuccess ? 1 : 0;
     }
     e = e ? e : (c->hetero ? use_explicit(c, 0) : autotune_tile(c));
     if (e != cudaSuccess) {
@@ -2822,7 +2910,35 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
     ea.ntx = ea.nty = ea.ntz = 0;
     grid = pred_only_blocks(c);
   }
-  explicit_dispatch(c, ea, grid, s);
+  // Split launch (2D tiles, IMEX scheme, direct solve, not in a per-phase
+  // timing): the tiles owning I_d nodes of interface cells, and the
+  // prediction, on s; the other tiles on the side stream, beside the solve.
+  // Neither half reads what the other writes (owned nodes are disjoint; both
+  // read u_n, which nothing writes during the step); the solve reads only the
+  // first half's nodes (u_pred of the interface cells) and writes only I_c
+  // rows, which the second half neither reads nor writes; the step ends on s
+  // once both streams have.
+  const bool split = split_active(c) && !cdm && !ev;
+  if (split) {
+    const int v = c->xvar;
+    cudaEventRecord(c->ov_fork, s);
+    ExplicitArgs en = ea;
+    en.tiles = c->tile_near[v];
+    en.ntl = c->n_near[v];
+    const int npred = (int)std::max<int64_t>(1, std::min<int64_t>((hs.n_c + kThreads - 1) / kThreads, c->num_sms));
+    explicit_dispatch(c, en, en.ntl + npred, s);
+    cudaStreamWaitEvent(c->side, c->ov_fork, 0);
+    ExplicitArgs ef = ea;
+    ef.tiles = c->tile_far[v];
+    ef.ntl = c->n_far[v];
+    ef.persistent = 1;
+    ef.n_c = 0;
+    explicit_dispatch(c, ef, (int)std::min<int64_t>((int64_t)ef.ntl * c->ncols, (int64_t)c->num_sms * c->split_per_sm),
+                      c->side);
+    cudaEventRecord(c->ov_join, c->side);
+  } else {
+    explicit_dispatch(c, ea, grid, s);
+  }
   if (ev) cudaEventRecord(ev[1], s);
   if (hs.n_c > 0) {
     if (!c->factorized) {   // right-hand sides, then PCG with the correction
@@ -2847,6 +2963,7 @@ static int step_once(imex_ctx* c, cudaStream_t s, cudaEvent_t* ev, const double*
       ++c->guess_valid;
     }
   }
+  if (split) cudaStreamWaitEvent(s, c->ov_join, 0);
   if (ev) cudaEventRecord(ev[2], s);
   if (int rc = check_launch("imex_step")) return rc;
   c->cur = 1 - c->cur;
@@ -2891,38 +3008,27 @@ static int autotune_tile_steps(imex_ctx* c) {
   cudaError_t e = copy_state(true);
   e = e ? e : cudaEventCreate(&ev[0]);
   e = e ? e : cudaEventCreate(&ev[1]);
+  // Candidates: every explicit variant (or the pinned one) with each shared
+  // memory request of the walk launches: what the walk needs, or enough that
+  // fewer CTAs of other launches share its SM (140 and 184 KB).  A larger
+  // request changes which CTAs of neighbouring launches (the explicit
+  // tiles, the dense tops, the split launch's second half) can be resident
+  // beside a walk CTA.  One untimed and four timed whole steps each, from
+  // the saved state; the fastest pair is kept.
+  const size_t wreq[3] = {c->smem_walk, std::max<size_t>(c->smem_walk, 140 * 1024),
+                          std::max<size_t>(c->smem_walk, 184 * 1024)};
   float best = 1e30f;
-  int best_var = c->xvar;
+  int best_var = c->xvar + (c->xsplit ? kExplicitSplit + split_index(c) : 0);
+  size_t best_req = c->smem_walk;
   int rc = IMEX_OK;
-  for (int k = 0; k < explicit_variants(c) && !pinned && e == cudaSuccess && rc == IMEX_OK; ++k) {
+  for (int k = 0; k < explicit_variants(c) && e == cudaSuccess && rc == IMEX_OK; ++k) {
+    if (pinned && k != explicit_env_variant(c)) continue;
     e = use_explicit(c, k);
-    e = e ? e : copy_state(false);
     if (e != cudaSuccess) break;
-    rc = step_once(c, nullptr, nullptr);
-    e = cudaEventRecord(ev[0], nullptr);
-    for (int r = 0; r < 4 && rc == IMEX_OK && e == cudaSuccess; ++r) rc = step_once(c, nullptr, nullptr);
-    e = e ? e : cudaEventRecord(ev[1], nullptr);
-    e = e ? e : cudaEventSynchronize(ev[1]);
-    float ms = 0.f;
-    e = e ? e : cudaEventElapsedTime(&ms, ev[0], ev[1]);
-    c->tile_us[k] = 1e3f * ms / 4.f;
-    if (e == cudaSuccess && c->tile_us[k] < best) {
-      best = c->tile_us[k];
-      best_var = k;
-    }
-  }
-  if (!pinned) e = e ? e : use_explicit(c, best_var);
-  // Shared memory requested per walk launch: what the walk needs, or enough
-  // that at most one, or no, CTA of the explicit launch can share an SM with
-  // it (140 and 184 KB); one whole step each, the fastest kept.
-  {
-    const size_t cand[3] = {c->smem_walk, std::max<size_t>(c->smem_walk, 140 * 1024),
-                            std::max<size_t>(c->smem_walk, 184 * 1024)};
-    float wbest = 1e30f;
-    size_t req = c->smem_walk;
-    for (int k = 0; k < 3 && e == cudaSuccess && rc == IMEX_OK; ++k) {
-      if (cand[k] > kMaxDynSmem || (k > 0 && cand[k] == cand[k - 1])) continue;
-      c->smem_walk_req = cand[k];
+    float kbest = 1e30f;
+    for (int w = 0; w < 3 && e == cudaSuccess && rc == IMEX_OK; ++w) {
+      if (wreq[w] > kMaxDynSmem || (w > 0 && wreq[w] == wreq[w - 1])) continue;
+      c->smem_walk_req = wreq[w];
       e = copy_state(false);
       if (e != cudaSuccess) break;
       rc = step_once(c, nullptr, nullptr);
@@ -2932,13 +3038,19 @@ static int autotune_tile_steps(imex_ctx* c) {
       e = e ? e : cudaEventSynchronize(ev[1]);
       float ms = 0.f;
       e = e ? e : cudaEventElapsedTime(&ms, ev[0], ev[1]);
-      if (e == cudaSuccess && ms < wbest) {
-        wbest = ms;
-        req = cand[k];
+      const float us = 1e3f * ms / 4.f;
+      if (e != cudaSuccess) break;
+      kbest = std::min(kbest, us);
+      if (us < best) {
+        best = us;
+        best_var = k;
+        best_req = wreq[w];
       }
     }
-    c->smem_walk_req = req;
+    c->tile_us[k] = kbest < 1e30f ? kbest : 0.f;
   }
+  e = e ? e : use_explicit(c, best_var);
+  c->smem_walk_req = best_req;
   if (ev[0]) cudaEventDestroy(ev[0]);
   if (ev[1]) cudaEventDestroy(ev[1]);
   e = e ? e : copy_state(false);
@@ -3581,7 +3693,8 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   st->explicit_tile_cells = c->TC;
   st->explicit_tile_us_large = c->tile_us[0];
   st->explicit_tile_us_small = c->tile_us[1];
-  st->explicit_variant = c->xvar;
+  st->explicit_variant = c->xsplit ? kExplicitSplit + split_index(c) : c->xvar;
+  for (int s = 0; s < kSplitVariants; ++s) st->explicit_split_us[s] = c->tile_us[kExplicitSplit + s];
   st->explicit_sweep_us = c->tile_us[2];
   st->explicit_sweep_short_us = c->tile_us[3];
   st->large_supernodes = c->n_large;
@@ -3631,6 +3744,9 @@ void imex_destroy(imex_ctx* c) {
         if (ev) cudaEventDestroy(ev);
     if (c->io_h2d) cudaStreamDestroy(c->io_h2d);
     if (c->io_d2h) cudaStreamDestroy(c->io_d2h);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ov_fork) cudaEventDestroy(c->ov_fork);
+    if (c->ov_join) cudaEventDestroy(c->ov_join);
     if (c->has_hooks) {
       if (c->hooks.release) c->hooks.release(c->base, c->hooks.user);
     } else {

@@ -103,6 +103,13 @@ struct ExplicitArgs {
   double dt;
   // independent columns (blockIdx.y): strides of full-grid and I_c fields
   int64_t cs_node, cs_c;
+  // 2D tiles: if set, CTA b takes tile tiles[b] (b < ntl; the CTAs after
+  // them predict); persistent: a fixed grid loops over the ntl x ncols
+  // (tile, column) items of the list instead, without prediction.
+  const int* tiles;
+  int ntl;
+  int persistent;
+  int ncols;
 };
 
 // One level of the supernodal walk of A5 (forward or backward), all

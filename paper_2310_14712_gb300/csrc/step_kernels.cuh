@@ -185,34 +185,19 @@ __device__ __forceinline__ double y_item_last(const Ops2D& ops, const double (&v
   return fma(ops.wyv, va[P - 1], ev - od);
 }
 
+// One tile of the 2D explicit apply (owned nodes of tile `tile`, column col).
 template <int P, int TC>
-__global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D ops) {
+__device__ __forceinline__ void explicit_tile(const ExplicitArgs& a, const Ops2D& ops, int tile, int col,
+                                              double* sm) {
   constexpr int p = P - 1;
   constexpr int OX = TC * p, OY = TC * p;
   constexpr int RX = (TC + 1) * p + 1, RY = RX;
   constexpr int NC = TC + 1;
-  extern __shared__ double sm[];
   const int tid = threadIdx.x;
-  const int ntiles = a.ntx * a.nty;
-  // Column of an independent-columns context (blockIdx.y).
-  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
+  const int64_t on = (int64_t)col * a.cs_node;
   const double* Uc = a.U + on;
   const double* Wc = a.W + on;     // may alias OUTc
   double* OUTc = a.OUT + on;
-  // The first solve launch may start staging its constant factor blocks now;
-  // it waits for this grid (griddepcontrol.wait) before it reads u.
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-
-  if ((int)blockIdx.x >= ntiles) {
-    // Newmark prediction on I_c (Fig. TrapCDMIMEX, "Prediction").
-    const double c1 = a.dt, c2 = (0.5 - kNewmarkBeta) * a.dt * a.dt;
-    const int stride = (gridDim.x - ntiles) * blockDim.x;
-    for (int r = (blockIdx.x - ntiles) * blockDim.x + tid; r < a.n_c; r += stride) {
-      const int node = a.c_node[r];
-      OUTc[node] = Uc[node] + c1 * a.v_c[oc + r] + c2 * a.a_c[oc + r];
-    }
-    return;
-  }
 
   double* su = sm;                 // RY x RX
   double* t1 = su + RY * RX;       // RY x OX
@@ -226,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
   double* rb = rr + OY * OX;       // NC x OX vertex partials (y pass)
   double* rt = rb + NC * OX;
 
-  const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
+  const int tx = tile % a.ntx, ty = tile / a.ntx;
   const int X0 = tx * OX, Y0 = ty * OY;
   const int cx0 = X0 / p - 1, cy0 = Y0 / p - 1;
 
@@ -341,6 +326,42 @@ __global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D o
     const double u = su[(yo + p) * RX + xo + p];
     OUTc[g] = cdm_node(u, Wc[g], r, gxs[g], ft, a.cu, a.cw, a.kappa2);
   }
+}
+
+// The 2D explicit apply: one CTA per tile (of the list a.tiles, if given),
+// then the prediction CTAs; or (a.persistent) a fixed grid looping over the
+// listed tiles of every column, without prediction.
+template <int P, int TC>
+__global__ void __launch_bounds__(kThreads) k_explicit2d(ExplicitArgs a, Ops2D ops) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x;
+  const int ntl = a.tiles ? a.ntl : a.ntx * a.nty;
+  // The first solve launch may start staging its constant factor blocks now;
+  // it waits for this grid (griddepcontrol.wait) before it reads u.
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  if (a.persistent) {
+    const int nitem = ntl * a.ncols;
+    for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+      const int col = it / ntl;
+      explicit_tile<P, TC>(a, ops, a.tiles[it - col * ntl], col, sm);
+      __syncthreads();
+    }
+    return;
+  }
+  if ((int)blockIdx.x >= ntl) {
+    // Newmark prediction on I_c (Fig. TrapCDMIMEX, "Prediction").
+    const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
+    const double* Uc = a.U + on;
+    double* OUTc = a.OUT + on;
+    const double c1 = a.dt, c2 = (0.5 - kNewmarkBeta) * a.dt * a.dt;
+    const int stride = (gridDim.x - ntl) * blockDim.x;
+    for (int r = (blockIdx.x - ntl) * blockDim.x + tid; r < a.n_c; r += stride) {
+      const int node = a.c_node[r];
+      OUTc[node] = Uc[node] + c1 * a.v_c[oc + r] + c2 * a.a_c[oc + r];
+    }
+    return;
+  }
+  explicit_tile<P, TC>(a, ops, a.tiles ? a.tiles[blockIdx.x] : (int)blockIdx.x, blockIdx.y, sm);
 }
 
 // ---------------------------------------------------------------------------

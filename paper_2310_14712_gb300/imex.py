@@ -63,10 +63,13 @@ class Stats(ctypes.Structure):
         [("scheme", ctypes.c_int64), ("dt_crit_cut_min", ctypes.c_double), ("factorized", ctypes.c_int64),
          ("explicit_variant", ctypes.c_int64), ("explicit_sweep_us", ctypes.c_double),
          ("explicit_sweep_short_us", ctypes.c_double), ("large_supernodes", ctypes.c_int64),
-         ("max_rows", ctypes.c_int64), ("solve_smem_needed", ctypes.c_int64)]
+         ("max_rows", ctypes.c_int64), ("solve_smem_needed", ctypes.c_int64),
+         ("explicit_split_us", ctypes.c_double * 4)]
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_}
+        out = {n: getattr(self, n) for n, _ in self._fields_}
+        out["explicit_split_us"] = list(out["explicit_split_us"])
+        return out
 
 
 _vp = ctypes.c_void_p

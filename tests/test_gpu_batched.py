@@ -102,15 +102,18 @@ def test_batched_rejects_source_count_mismatch():
 
 @pytest.mark.parametrize("make", [lambda: workloads.plate16(), lambda: workloads.multisource(nsrc=4)])
 def test_explicit_variants_agree_bitwise(make, monkeypatch):
-    # The autotuner picks one of four explicit variants (two tile sizes, the
-    # persistent strip sweep in long or short chunks); all must give the same
-    # numbers (per node the same contractions and vertex sums in the same
-    # order), so the choice never changes a result.  Each sweep runs twice:
-    # one CTA per unit, and a few CTAs whose unit ranges cross strips.
+    # The autotuner picks one of eight explicit variants (two tile sizes, the
+    # persistent strip sweep in long or short chunks, the split launch: the
+    # tiles the solve reads first, the others on a second stream beside the
+    # solve, with a few CTAs per SM); all must give the same numbers (per
+    # node the same contractions and vertex sums in the same order), so the
+    # choice never changes a result.  Each sweep runs twice: one CTA per
+    # unit, and a few CTAs whose unit ranges cross strips.
     imex = _imex()
     out = {}
     for tile, ctas in (("large", None), ("small", None), ("sweep", None), ("sweep", "7"),
-                       ("sweep_short", None), ("sweep_short", "5")):
+                       ("sweep_short", None), ("sweep_short", "5"), ("large_split1", None),
+                       ("large_split2", None), ("small_split2", None), ("small_split4", None)):
         monkeypatch.setenv("IMEX_EXPLICIT_TILE", tile)
         if ctas:
             monkeypatch.setenv("IMEX_SWEEP_CTAS", ctas)
@@ -119,7 +122,7 @@ def test_explicit_variants_agree_bitwise(make, monkeypatch):
             g.step(50)
             info = g.info()
             out[(tile, ctas)] = (g.fields("u", out=np.zeros(g.field_len)), info["explicit_variant"])
-    assert [v[1] for v in out.values()] == [0, 1, 2, 2, 3, 3]
+    assert [v[1] for v in out.values()] == [0, 1, 2, 2, 3, 3, 4, 5, 6, 7]
     ref = out[("large", None)][0]
     for key, (u, _) in out.items():
         assert np.array_equal(u, ref), key

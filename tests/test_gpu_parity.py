@@ -108,12 +108,13 @@ def _box(n, p, holes, alpha=1e-5, depth=3, ncy=None, lo=(0.0, 0.0), hi=(1.0, 1.0
                               np.array([[0.23, 0.31]]), 3.0, 0.08, 0)
 
 
-@pytest.mark.parametrize("variant", ["large", "sweep", "sweep_short"])
+@pytest.mark.parametrize("variant", ["large", "sweep", "sweep_short", "small_split2"])
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_orders_ragged_grid(p, variant, monkeypatch):
     # 13 x 7 cells: not a multiple of any tile or strip width; one hole
-    # crossing the top edge.  Both explicit forms (tiles; the strip sweep with
-    # 3 CTAs, whose unit ranges start mid-strip and cross strips).
+    # crossing the top edge.  Every explicit form (tiles; the strip sweep with
+    # 3 CTAs, whose unit ranges start mid-strip and cross strips; small tiles
+    # with the split launch beside the solve).
     monkeypatch.setenv("IMEX_EXPLICIT_TILE", variant)
     if variant.startswith("sweep"):
         monkeypatch.setenv("IMEX_SWEEP_CTAS", "3")
