@@ -125,16 +125,26 @@ def time_flushed_phases(g, steps, stream, flush):
     return total
 
 
-def measure_batched(imex, workloads, steps, stream, flush):
+def measure_batched(imex, workloads, steps, stream, flush, rank=0, ws=1):
     """Independent source columns against the single-source form on the same
-    geometry: the 16x16-cell plate with 64 seeded sources (one per column)."""
+    geometry: the 16x16-cell plate with 64 seeded sources (one per column).
+    With ws ranks the 64 columns are split between them (replicas.shard_columns:
+    contiguous blocks, no collective on the data path); the value is all 64
+    columns over the slowest rank's time.  The single-column comparison runs
+    on one rank only."""
     out = {}
+    full = workloads.multisource(nsrc=64)
     for label, ncols in (("batched", 64), ("plain", 1)):
+        if label == "plain" and ws > 1:
+            continue
         w = workloads.multisource(nsrc=ncols)
-        g = imex.Imex.from_workload(w, ncols=ncols)
+        mine = shard_columns(ncols, rank, ws) if label == "batched" else range(ncols)
+        if label == "batched":
+            w.src_pos = full.src_pos[mine.start:mine.stop]
+        g = imex.Imex.from_workload(w, ncols=len(mine))
         st = g.info()
         g.step(5)
-        ms = time_flushed(g, steps, stream, flush)
+        ms = reduce_max(time_flushed(g, steps, stream, flush), ws)
         n_act = st["n_d"] + st["n_c"]
         out[label] = {"value": n_act * ncols * steps / (ms * 1e-3), "ms_per_step": ms / steps,
                       "ncols": ncols, "explicit_variant": EXPLICIT_VARIANTS[st["explicit_variant"]],
@@ -143,10 +153,11 @@ def measure_batched(imex, workloads, steps, stream, flush):
     b = out["batched"]
     b.update({"workload": "multisource: [0,1]^2 minus a centred circle r=0.2, 16x16 cells, p=4, "
                           "64 seeded sources (Ricker f0=20), one per column",
-              "unit": UNIT, "plain_value": out["plain"]["value"],
-              "plain_ms_per_step": out["plain"]["ms_per_step"],
-              "speedup_vs_plain": b["value"] / out["plain"]["value"],
-              "steps": steps, "l2": "flushed between timed steps"})
+              "unit": UNIT, "steps": steps, "l2": "flushed between timed steps",
+              "columns_per_rank": [len(shard_columns(64, r, ws)) for r in range(ws)]})
+    if "plain" in out:
+        b.update({"plain_value": out["plain"]["value"], "plain_ms_per_step": out["plain"]["ms_per_step"],
+                  "speedup_vs_plain": b["value"] / out["plain"]["value"]})
     return b
 
 
@@ -466,7 +477,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-from paper_2310_14712_gb300.replicas import barrier, dist_env, reduce_max  # noqa: E402
+from paper_2310_14712_gb300.replicas import barrier, dist_env, reduce_max, shard_columns  # noqa: E402
 
 
 def cpu_oracle_rate(w, nsteps, warmup=1):
@@ -635,6 +646,8 @@ def run_gpu(args):
         "setup_seconds": st["setup_seconds"],
         "wall_seconds_timed_loop": wall,
     }
+    if ws > 1 and not args.no_extras:   # the batched columns split across the ranks
+        line["batched"] = measure_batched(imex, workloads, min(args.steps, 200), stream, flush, rank, ws)
     if ws == 1 and not args.no_extras:
         line["batched"] = measure_batched(imex, workloads, min(args.steps, 200), stream, flush)
         line["learned_pcg"] = measure_learned_pcg(imex, w, min(args.steps, 20), stream, flush)

@@ -496,6 +496,22 @@ int imex_host_setup_export(const imex_mesh *mesh, int p, double alpha, double dt
                            const imex_source *src, uint8_t *node_class, double *fx,
                            imex_stats *stats);
 
+/*
+ * imex_host_element_matrices - run the host discretisation only (no GPU, no
+ * factorisation) and return the element matrices of `ncell` cells (flat cell
+ * ids, x fastest) as the library assembles them (Sec. Spatial
+ * discretization): cut cells K_e, M_e by the spacetree quadrature with the
+ * fictitious domain scaled by alpha; uncut cells the reference stiffness
+ * scaled by c_e^2 / c0^2 and the GLL-lumped (diagonal) mass; empty cells
+ * zero.  K and M receive ncell x P^d x P^d doubles (cell after cell,
+ * column-major; both symmetric); cell_type (may be NULL) receives 0 uncut,
+ * 1 cut, 2 empty.  Errors: IMEX_ERR_ARG (bad sizes, cell id out of range),
+ * IMEX_ERR_GEOM.
+ */
+int imex_host_element_matrices(const imex_mesh *mesh, int p, double alpha, const imex_source *src,
+                               int ncell, const int64_t *cells, double *K, double *M,
+                               int8_t *cell_type);
+
 #ifdef __cplusplus
 }
 #endif

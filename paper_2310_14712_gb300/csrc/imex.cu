@@ -2312,6 +2312,27 @@ void fill_stats(const HostSetup& hs, imex_stats* st) {
   st->dt_crit_cut_min = hs.dt_crit_cut_min;
 }
 
+int imex_host_element_matrices(const imex_mesh* mesh, int p, double alpha, const imex_source* src, int ncell,
+                               const int64_t* cells, double* K, double* M, int8_t* cell_type) {
+  if (ncell < 0 || (ncell > 0 && (!cells || !K || !M))) return fail(IMEX_ERR_ARG, "bad arguments");
+  try {
+    Problem pb;
+    if (int rc = build_context(mesh, p, alpha, 0.0, src, pb)) return rc;
+    pb.factorize = false;
+    pb.export_cells.assign(cells, cells + ncell);
+    HostSetup hs;
+    std::string err = build_setup(pb, hs);
+    if (!err.empty()) return fail(setup_error_code(err), err);
+    std::memcpy(K, hs.export_K.data(), hs.export_K.size() * sizeof(double));
+    std::memcpy(M, hs.export_M.data(), hs.export_M.size() * sizeof(double));
+    if (cell_type)
+      for (int q = 0; q < ncell; ++q) cell_type[q] = hs.cell_type[cells[q]];
+    return IMEX_OK;
+  } catch (const std::exception& ex) {
+    return fail(IMEX_ERR_ALLOC, std::string("host setup failed: ") + ex.what());
+  }
+}
+
 int imex_host_setup_export(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src,
                            uint8_t* node_class, double* fx, imex_stats* stats) {
   try {

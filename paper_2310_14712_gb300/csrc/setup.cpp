@@ -1087,6 +1087,25 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
     hs.if_c2.push_back((c * c) / (pb.c0 * pb.c0));
     hs.if_kidx.push_back(hs.cell_type[cid] == CELL_CUT ? -2 : -1);
   }
+  // Element matrices of the requested cells, as the assembly uses them.
+  hs.export_K.assign(pb.export_cells.size() * Pd * Pd, 0.0);
+  hs.export_M.assign(pb.export_cells.size() * Pd * Pd, 0.0);
+  for (size_t q = 0; q < pb.export_cells.size(); ++q) {
+    const int64_t cid = pb.export_cells[q];
+    if (cid < 0 || cid >= ncell) return "export cell out of range";
+    double* K = hs.export_K.data() + q * Pd * Pd;
+    double* M = hs.export_M.data() + q * Pd * Pd;
+    if (hs.cell_type[cid] == CELL_CUT) {
+      std::copy(cutK_all.begin() + (size_t)cut_slot[cid] * Pd * Pd,
+                cutK_all.begin() + (size_t)(cut_slot[cid] + 1) * Pd * Pd, K);
+      std::copy(cutM_all.begin() + (size_t)cut_slot[cid] * Pd * Pd,
+                cutM_all.begin() + (size_t)(cut_slot[cid] + 1) * Pd * Pd, M);
+    } else if (hs.cell_type[cid] == CELL_UNCUT) {
+      const double c = cell_speed(cid), s = (c * c) / (pb.c0 * pb.c0);
+      for (size_t k = 0; k < (size_t)Pd * Pd; ++k) K[k] = s * hs.uncutK[k];
+      for (int a = 0; a < Pd; ++a) M[a + (size_t)Pd * a] = uncutM[a];
+    }
+  }
   // Pack cut-cell stiffness in interface order.
   hs.cutK.clear();
   {

@@ -38,6 +38,7 @@ struct Problem {
   double dt_factor = 0.9;
   int scheme = 0;              // kScheme*
   bool factorize = true;       // false: no dissection and no factorisation (iterative solve only)
+  std::vector<int64_t> export_cells;  // cells whose element matrices are kept (HostSetup::export_K/M)
 };
 
 // Time integration schemes on the same discretisation (the method and the
@@ -96,6 +97,11 @@ struct HostSetup {
   std::vector<int> if_kidx;    // index into cutK (>= 0) or -1 (uncut form)
   std::vector<double> if_c2;   // c^2 multiplier for the uncut form (c_e^2 / c0^2)
   std::vector<double> cutK;    // n_cut x Pd x Pd, column-major per cell
+  // Element matrices of Problem::export_cells as assembled (Pd x Pd each,
+  // column-major): cut cells by spacetree quadrature, uncut cells the
+  // reference form (stiffness scaled by c_e^2 / c0^2, GLL-lumped mass),
+  // empty cells zero.
+  std::vector<double> export_K, export_M;
   // For each c-index r: list of positions (if_cell * Pd + local node) whose
   // element products add into row r of K^c u.
   std::vector<int> contrib_ptr, contrib_pos;

@@ -113,12 +113,14 @@ _lib.imex_gauss_points.argtypes = [ctypes.c_int, _dp, _dp]
 _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double,
                                         ctypes.c_double, ctypes.POINTER(Source), _vp, _dp,
                                         ctypes.POINTER(Stats)]
+_lib.imex_host_element_matrices.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double,
+                                            ctypes.POINTER(Source), ctypes.c_int, _vp, _dp, _dp, _vp]
 
 # Every symbol include/imex.h declares (checked by the CPU tests).
 EXPORTS = ("imex_setup", "imex_setup_batch", "imex_setup_scheme", "imex_setup_pcg", "imex_adjoint", "imex_set_solver", "imex_pcg_train", "imex_pcg_train_guess", "imex_pcg_set_guess", "imex_pcg_fsai_closed_form", "imex_pcg_status",
            "imex_fsai_kaporin", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
            "imex_set_initial", "imex_info", "imex_check_finite", "imex_last_error", "imex_destroy", "imex_gll_points",
-           "imex_gauss_points", "imex_host_setup_export", "imex_probe_fp64")
+           "imex_gauss_points", "imex_host_setup_export", "imex_host_element_matrices", "imex_probe_fp64")
 
 
 class ImexError(RuntimeError):
@@ -226,6 +228,25 @@ def host_setup_export(dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0, 
                                        cls.ctypes.data, fx.ctypes.data_as(_dp), ctypes.byref(st)),
            "imex_host_setup_export")
     return cls, fx, st.as_dict()
+
+
+def host_element_matrices(cells, dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0, src_sigma,
+                          src_amp=10.0, wavelet=0, rho=1.0, c0=1.0, cell_c=None, **_):
+    """Host discretisation only (no GPU): element matrices K_e, M_e of the
+    given flat cell ids as the library assembles them, shape (n, P^d, P^d),
+    and the cell types (0 uncut, 1 cut, 2 empty)."""
+    m, s, keep = _mesh_source(dim, lo, hi, ncells, depth, holes, rho, c0, cell_c, src_pos, f0,
+                              src_sigma, src_amp, wavelet)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    Pd = (p + 1) ** dim
+    K = np.zeros((len(cells), Pd, Pd))
+    M = np.zeros((len(cells), Pd, Pd))
+    types = np.zeros(len(cells), dtype=np.int8)
+    _check(_lib.imex_host_element_matrices(ctypes.byref(m), p, alpha, ctypes.byref(s), len(cells),
+                                           cells.ctypes.data, K.ctypes.data_as(_dp), M.ctypes.data_as(_dp),
+                                           types.ctypes.data), "imex_host_element_matrices")
+    # column-major per cell -> (row, column)
+    return K.transpose(0, 2, 1).copy(), M.transpose(0, 2, 1).copy(), types
 
 
 class _TorchAllocator:
