@@ -143,6 +143,11 @@ typedef struct {
                                     the solve, while the other tiles run on a second stream with
                                     1 or 2 CTAs per SM (larger tiles) or 2 or 4 (smaller tiles);
                                     2D factorised contexts, direct solve; 0: not timed) */
+  int64_t solve_col_block;       /* independent columns per walk / dense-top CTA: the factor
+                                    blocks are staged once per block of columns (autotuned for
+                                    ncols > 1, IMEX_COL_BLOCK=n pins it) */
+  double solve_col_block_us[7];  /* setup timing of one whole step with 1, 2, 4, ..., 64 columns
+                                    per CTA (0: not timed) */
 } imex_stats;
 
 /*

@@ -770,6 +770,14 @@ struct imex_ctx {
   // larger request changes which CTAs of the neighbouring launches share an
   // SM with a walk CTA; the setup autotuner times a few requests.
   size_t smem_walk_req = 0;
+  // Independent columns per walk / dense-top CTA (autotuned for ncols > 1):
+  // the factor blocks are staged once per block of columns.  Shared memory
+  // of a walk CTA = blob + cell-matrix rows + cb x walk_vec doubles +
+  // walk_ilist ints; of a dense-top CTA = max_arows + cb x (max_zn +
+  // kThreads) doubles + top_ilist ints.
+  int col_block = 1;
+  size_t walk_fixed = 0, walk_vec = 0, top_fixed = 0, top_vec = 0;
+  float cb_us[7] = {};   // setup timing with 1, 2, 4, ..., 64 columns per CTA (0: not timed)
   int ntop = 0;
   int *top_comp = nullptr, *top_r0 = nullptr, *top_r1 = nullptr;
   int *zsize = nullptr, *zbase = nullptr, *zrow = nullptr;
@@ -1127,6 +1135,18 @@ constexpr size_t kWalkSmemBudget = 200 * 1024;  // shared memory per walk CTA (s
 constexpr size_t kTopSmemBudget = 200 * 1024;   // shared memory per dense-top CTA
 constexpr size_t kMaxDynSmem = 220 * 1024;      // dynamic shared memory limit we set (static use < 7 KB)
 
+// The walk kernel for a direction, staging mode and column mode (one column
+// per CTA, or a block of columns).
+using WalkFn = void (*)(WalkArgs);
+WalkFn walk_kernel(bool fwd, bool smem, bool cols) {
+  if (fwd) {
+    if (smem) return cols ? k_walk<true, true, true> : k_walk<true, true, false>;
+    return cols ? k_walk<true, false, true> : k_walk<true, false, false>;
+  }
+  if (smem) return cols ? k_walk<false, true, true> : k_walk<false, true, false>;
+  return cols ? k_walk<false, false, true> : k_walk<false, false, false>;
+}
+
 // The launches of the implicit solve: forward walk over the lower levels
 // (the first also forms every right-hand side from src), dense tops,
 // backward walk with the correction.  use_S selects the factor of S (step)
@@ -1176,6 +1196,8 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   w.cs_node = hs.nnodes;
   w.cs_c = hs.n_c;
   w.cs_upd = std::max<int64_t>(hs.upd_size, 1);
+  w.cb = c->col_block;
+  w.ncols = c->ncols;
   TopArgs z{};
   z.cta_comp = c->top_comp;
   z.cta_r0 = c->top_r0;
@@ -1204,6 +1226,8 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   z.cs_node = w.cs_node;
   z.cs_c = w.cs_c;
   z.cs_upd = w.cs_upd;
+  z.cb = w.cb;
+  z.ncols = w.ncols;
 
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1217,11 +1241,9 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
   auto walk = [&](int l, bool fwd) {
     w.cta0 = c->lev_cta0[l];
     w.first = (fwd && l == 0) ? 1 : 0;
-    cfg.gridDim = dim3(c->lev_ncta[l], c->ncols);
+    cfg.gridDim = dim3(c->lev_ncta[l], (c->ncols + c->col_block - 1) / c->col_block);
     cfg.dynamicSmemBytes = c->smem_walk_req;
-    if (c->walk_smem_mode)
-      return fwd ? cudaLaunchKernelEx(&cfg, k_walk<true, true>, w) : cudaLaunchKernelEx(&cfg, k_walk<false, true>, w);
-    return fwd ? cudaLaunchKernelEx(&cfg, k_walk<true, false>, w) : cudaLaunchKernelEx(&cfg, k_walk<false, false>, w);
+    return cudaLaunchKernelEx(&cfg, walk_kernel(fwd, c->walk_smem_mode != 0, c->col_block > 1), w);
   };
   PanelArgs pa{};
   pa.desc = c->pan_desc;
@@ -1265,15 +1287,34 @@ cudaError_t launch_solve_chain(imex_ctx* c, bool use_S, double ft, const double*
     for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph) e = panel(l, ph);
   }
   if (e == cudaSuccess && c->ntop > 0) {
-    cfg.gridDim = dim3(c->ntop, c->ncols);
+    cfg.gridDim = dim3(c->ntop, (c->ncols + c->col_block - 1) / c->col_block);
     cfg.dynamicSmemBytes = c->smem_top;
-    e = cudaLaunchKernelEx(&cfg, k_top, z);
+    e = cudaLaunchKernelEx(&cfg, c->col_block > 1 ? k_top<true> : k_top<false>, z);
   }
   for (int l = nlev - 1; l >= 0 && e == cudaSuccess; --l) {
     for (int ph = 2; ph < 4 && e == cudaSuccess; ++ph) e = panel(l, ph);
     if (e == cudaSuccess && c->lev_has_nodes[l]) e = walk(l, false);
   }
   return e;
+}
+
+// Columns per walk and dense-top CTA; false (nothing changed) if the
+// shared memory would exceed a CTA's limit.
+bool set_col_block(imex_ctx* c, int cb) {
+  cb = std::max(1, std::min(cb, c->ncols));
+  const size_t w = c->walk_fixed + (size_t)cb * c->walk_vec, tp = c->top_fixed + (size_t)cb * c->top_vec;
+  if (w > kMaxDynSmem || tp > kMaxDynSmem) return false;
+  c->col_block = cb;
+  c->smem_walk = w;
+  c->smem_walk_req = w;
+  c->smem_top = tp;
+  return true;
+}
+
+// IMEX_COL_BLOCK = n pins the columns per walk / dense-top CTA (else tuned).
+int col_block_env() {
+  const char* env = std::getenv("IMEX_COL_BLOCK");
+  return env ? std::max(1, std::atoi(env)) : 0;
 }
 
 // The split candidate in use (index into kSplitTile / kSplitPerSM).
@@ -2552,8 +2593,8 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       // (otherwise they are read from global memory).
       const size_t kp = (size_t)(plan.max_kp + (plan.max_kp & 1)) * sizeof(double);
       const size_t blob = (size_t)plan.max_blob * sizeof(double);
-      const size_t base = (size_t)(2 * plan.max_slots + plan.max_m + plan.max_pairs) * sizeof(double) +
-                          (size_t)plan.max_ilist * sizeof(int);
+      c->walk_vec = (size_t)(2 * plan.max_slots + plan.max_m + plan.max_pairs) * sizeof(double);
+      const size_t base = c->walk_vec + (size_t)plan.max_ilist * sizeof(int);
       c->walk_kp_smem = base + kp <= kMaxDynSmem ? 1 : 0;
       c->walk_max_kp = c->walk_kp_smem ? (plan.max_kp + (plan.max_kp & 1)) : 0;
       const size_t used = base + (c->walk_kp_smem ? kp : 0);
@@ -2561,11 +2602,14 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       c->walk_max_blob = c->walk_smem_mode ? plan.max_blob : 0;
       c->smem_walk = used + (c->walk_smem_mode ? blob : 0);
       c->smem_walk_req = c->smem_walk;
+      c->walk_fixed = c->smem_walk - c->walk_vec;
       c->lev_has_nodes = plan.lev_has_nodes;
       c->top_max_zn = std::max(2, plan.max_zn + (plan.max_zn & 1));
       c->top_max_arows = plan.max_arows;
       c->smem_top = (size_t)(c->top_max_zn + plan.max_arows + kThreads) * sizeof(double) +
                     (size_t)plan.max_tlist * sizeof(int);
+      c->top_vec = (size_t)(c->top_max_zn + kThreads) * sizeof(double);
+      c->top_fixed = c->smem_top - c->top_vec;
       if (c->smem_walk > kMaxDynSmem || c->smem_top > kMaxDynSmem) {
         delete c;
         return fail(IMEX_ERR_ARG, "solve schedule exceeds the shared memory of a CTA");
@@ -2840,10 +2884,11 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       e = e ? e : upload(c->tile_near[v], tile_lists[v][0]);
       e = e ? e : upload(c->tile_far[v], tile_lists[v][1]);
     }
-    for (auto fn : {k_walk<true, true>, k_walk<false, true>, k_walk<true, false>, k_walk<false, false>})
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k)
+      e = cudaFuncSetAttribute(walk_kernel(k & 1, k & 2, k & 4), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kMaxDynSmem);
+    for (auto fn : {k_top<true>, k_top<false>})
       if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_top, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
     if (e == cudaSuccess) {
@@ -3029,6 +3074,41 @@ static int autotune_tile_steps(imex_ctx* c) {
   cudaError_t e = copy_state(true);
   e = e ? e : cudaEventCreate(&ev[0]);
   e = e ? e : cudaEventCreate(&ev[1]);
+  // One untimed and four timed whole steps from the saved state.
+  auto time_steps = [&](float* us) {
+    e = copy_state(false);
+    if (e != cudaSuccess) return IMEX_OK;
+    int r = step_once(c, nullptr, nullptr);
+    e = cudaEventRecord(ev[0], nullptr);
+    for (int k = 0; k < 4 && r == IMEX_OK && e == cudaSuccess; ++k) r = step_once(c, nullptr, nullptr);
+    e = e ? e : cudaEventRecord(ev[1], nullptr);
+    e = e ? e : cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    e = e ? e : cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    *us = 1e3f * ms / 4.f;
+    return r;
+  };
+  int rc = IMEX_OK;
+  // Independent columns per walk / dense-top CTA (1, 2, 4, ..., 64), with the
+  // explicit variant chosen so far.
+  if (c->ncols > 1 && e == cudaSuccess) {
+    if (int pin = col_block_env()) {
+      set_col_block(c, pin);
+    } else {
+      float bbest = 1e30f;
+      int bcb = 1;
+      for (int k = 0; k < 7 && e == cudaSuccess && rc == IMEX_OK; ++k) {
+        const int cb = 1 << k;
+        if (cb > c->ncols || !set_col_block(c, cb)) continue;
+        rc = time_steps(&c->cb_us[k]);
+        if (e == cudaSuccess && rc == IMEX_OK && c->cb_us[k] < bbest) {
+          bbest = c->cb_us[k];
+          bcb = cb;
+        }
+      }
+      set_col_block(c, bcb);
+    }
+  }
   // Candidates: every explicit variant (or the pinned one) with each shared
   // memory request of the walk launches: what the walk needs, or enough that
   // fewer CTAs of other launches share its SM (140 and 184 KB).  A larger
@@ -3041,7 +3121,6 @@ static int autotune_tile_steps(imex_ctx* c) {
   float best = 1e30f;
   int best_var = c->xvar + (c->xsplit ? kExplicitSplit + split_index(c) : 0);
   size_t best_req = c->smem_walk;
-  int rc = IMEX_OK;
   for (int k = 0; k < explicit_variants(c) && e == cudaSuccess && rc == IMEX_OK; ++k) {
     if (pinned && k != explicit_env_variant(c)) continue;
     e = use_explicit(c, k);
@@ -3050,16 +3129,8 @@ static int autotune_tile_steps(imex_ctx* c) {
     for (int w = 0; w < 3 && e == cudaSuccess && rc == IMEX_OK; ++w) {
       if (wreq[w] > kMaxDynSmem || (w > 0 && wreq[w] == wreq[w - 1])) continue;
       c->smem_walk_req = wreq[w];
-      e = copy_state(false);
-      if (e != cudaSuccess) break;
-      rc = step_once(c, nullptr, nullptr);
-      e = cudaEventRecord(ev[0], nullptr);
-      for (int r = 0; r < 4 && rc == IMEX_OK && e == cudaSuccess; ++r) rc = step_once(c, nullptr, nullptr);
-      e = e ? e : cudaEventRecord(ev[1], nullptr);
-      e = e ? e : cudaEventSynchronize(ev[1]);
-      float ms = 0.f;
-      e = e ? e : cudaEventElapsedTime(&ms, ev[0], ev[1]);
-      const float us = 1e3f * ms / 4.f;
+      float us = 0.f;
+      rc = time_steps(&us);
       if (e != cudaSuccess) break;
       kbest = std::min(kbest, us);
       if (us < best) {
@@ -3708,6 +3779,8 @@ int imex_info(imex_ctx* c, imex_stats* st) {
   st->solve_ctas = widest;
   st->solve_smem_bytes = (int64_t)c->smem_walk_req;
   st->solve_smem_needed = (int64_t)c->smem_walk;
+  st->solve_col_block = c->col_block;
+  for (int k = 0; k < 7; ++k) st->solve_col_block_us[k] = c->cb_us[k];
   st->launches_per_step = launches_per_step(c);
   st->rhs_pairs = (int64_t)c->hs.contrib_pos.size();
   st->ncols = c->ncols;

@@ -153,8 +153,10 @@ struct WalkArgs {
   double* v_c;
   double* a_c;
   double dt;
-  // independent columns (blockIdx.y): strides of full-grid, I_c and update fields
+  // independent columns: strides of full-grid, I_c and update fields; a CTA
+  // takes the block of cb columns blockIdx.y * cb ... (of ncols)
   int64_t cs_node, cs_c, cs_upd;
+  int cb, ncols;
 };
 
 // Dense top block of every component: x_Z = A_Z (rhs_Z - updates from the
@@ -184,7 +186,8 @@ struct TopArgs {
   double* v_c;
   double* a_c;
   double dt;
-  int64_t cs_node, cs_c, cs_upd;  // independent columns (blockIdx.y)
+  int64_t cs_node, cs_c, cs_upd;  // independent columns: strides
+  int cb, ncols;                  // a CTA takes the block of cb columns blockIdx.y * cb ... (of ncols)
 };
 
 // Large supernodes of the walked levels (more than 256 diagonal or ancestor

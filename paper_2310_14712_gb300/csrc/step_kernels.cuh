@@ -222,9 +222,12 @@ __device__ __forceinline__ void explicit_tile(const ExplicitArgs& a, const Ops2D
   }
   __syncthreads();
 
-  // x pass: item = (row yy, cell cc), rows fastest.
+  // x pass: item = (row yy, cell cc), rows fastest.  Rows outside the grid
+  // (a tile past the last node row) feed no cell inside it: skipped.
   for (int it = tid; it < RY * NC; it += kThreads) {
     const int cc = it / RY, yy = it - cc * RY;
+    const int gyr = Y0 - p + yy;
+    if (gyr < 0 || gyr >= a.ny) continue;
     const int cx = cx0 + cc;
     if (cx < 0 || cx >= a.ncx) {   // a cell outside the grid contributes nothing
       if (cc >= 1) {
@@ -272,9 +275,11 @@ __device__ __forceinline__ void explicit_tile(const ExplicitArgs& a, const Ops2D
   }
   __syncthreads();
 
-  // y pass: item = (column xo, cell row cr), columns fastest.
+  // y pass: item = (column xo, cell row cr), columns fastest.  Columns
+  // past the last node column own no node: skipped.
   for (int it = tid; it < OX * NC; it += kThreads) {
     const int cr = it / OX, xo = it - cr * OX;
+    if (X0 + xo >= a.nx) continue;
     const int cy = cy0 + cr;
     if (cy < 0 || cy >= a.ncy) {   // a cell outside the grid contributes nothing
       if (cr >= 1) {
@@ -1078,26 +1083,31 @@ __device__ __forceinline__ double pair_product(const WalkArgs& a, const double* 
 // triangle is stored, staged and read.
 __device__ __forceinline__ int tri_size(int b) { return b * (b + 1) / 2; }
 
-template <bool kForward, bool kSmem>
+template <bool kForward, bool kSmem, bool kCols>
 __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
   extern __shared__ __align__(16) double sm[];
   const int cta = a.cta0 + blockIdx.x;
   const int tid = threadIdx.x;
-  // Column of an independent-columns context (blockIdx.y).
-  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
-  const double* src = a.SRC + on;
-  const double* fxc = a.fxc + oc;
-  double* rhs0 = a.rhs0 + oc;
-  double* sol = a.sol + oc;
-  double* upd = a.upd + (int64_t)blockIdx.y * a.cs_upd;
-  const Corr cor{a.mode, a.c_node, a.U + on, a.v_c + oc, a.a_c + oc, a.dt, src};
+  // Block of independent columns (blockIdx.y): col0 .. col0 + ncb - 1.  Every
+  // vector below holds one slice per column; the factor blocks are staged
+  // once for all of them, and each loop runs over (item, column) pairs with
+  // the item fastest.  kCols = false: one column per CTA (no column index
+  // arithmetic).
+  const int col0 = kCols ? blockIdx.y * a.cb : blockIdx.y, ncb = kCols ? min(a.cb, a.ncols - col0) : 1;
+  const int MS = a.max_slots, MM = a.max_m, MP = a.max_pairs;
+  auto on = [&](int c) { return (int64_t)(col0 + c) * a.cs_node; };
+  auto oc = [&](int c) { return (int64_t)(col0 + c) * a.cs_c; };
+  auto updc = [&](int c) { return a.upd + (int64_t)(col0 + c) * a.cs_upd; };
+  auto corr = [&](int c) {
+    return Corr{a.mode, a.c_node, a.U + on(c), a.v_c + oc(c), a.a_c + oc(c), a.dt, a.SRC + on(c)};
+  };
   double* blob = sm;                                   // max_blob (smem mode)
   double* kp = blob + a.max_blob;                      // max_kp: rows of the cell matrices (first launch)
-  double* vg = kp + a.max_kp;                          // max_slots: g (fwd) / y (bwd)
-  double* vy = vg + a.max_slots;                       // max_slots: y (fwd) / h (bwd)
-  double* vm = vy + a.max_slots;                       // max_m: x of the ancestor rows (bwd)
-  double* pc = vm + a.max_m;                           // max_pairs: pair products (first launch)
-  int* il = reinterpret_cast<int*>(pc + a.max_pairs);
+  double* vg = kp + a.max_kp;                          // cb x max_slots: g (fwd) / y (bwd)
+  double* vy = vg + (size_t)a.cb * MS;                 // cb x max_slots: y (fwd) / h (bwd)
+  double* vm = vy + (size_t)a.cb * MS;                 // cb x max_m: x of the ancestor rows (bwd)
+  double* pc = vm + (size_t)a.cb * MM;                 // cb x max_pairs: pair products (first launch)
+  int* il = reinterpret_cast<int*>(pc + (size_t)a.cb * MP);
   __shared__ int s_off[kForward ? kMaxPd : 1];         // grid offset of each local node of a cell
   if (kForward && a.first)
     for (int m = tid; m < a.Pd; m += kThreads)
@@ -1113,19 +1123,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
   async_copy_wait();
   const WalkList L(il);
   const int nslot = il[1], nm = il[2];
-  // Backward: the correction state of this thread's first two rows.
+  const int nsi = nslot * ncb;   // (slot, column) items
+  // Backward: the correction state of this thread's first two items.
   int pre_node[2] = {0, 0};
   double pre_v[2] = {0.0, 0.0}, pre_a[2] = {0.0, 0.0};
   if (!kForward) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const int sl = tid + q * kThreads;
-      if (sl < nslot) {
+      const int it = tid + q * kThreads;
+      if (it < nsi) {
+        const int c = kCols ? it / nslot : 0, sl = kCols ? it - c * nslot : it;
         const int* nd = L.node + 8 * L.slot[4 * sl];
         const int r = nd[1] + (sl - nd[4]);
-        pre_node[q] = cor.c_node[r];
-        pre_v[q] = cor.v_c[r];
-        pre_a[q] = cor.a_c[r];
+        pre_node[q] = a.c_node[r];
+        pre_v[q] = a.v_c[oc(c) + r];
+        pre_a[q] = a.a_c[oc(c) + r];
       }
     }
   }
@@ -1134,53 +1146,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
   if (a.skip && *a.skip) return;   // the iterative solve converged: nothing to do
   if (kForward) {
     if (a.first && a.rhs_given) {
-      for (int sl = tid; sl < nslot; sl += kThreads) {
+      for (int it = tid; it < nsi; it += kThreads) {
+        const int c = kCols ? it / nslot : 0, sl = kCols ? it - c * nslot : it;
         const int* st = L.slot + 4 * sl;
         const int* nd = L.node + 8 * st[0];
-        double v = rhs0[nd[1] + (sl - nd[4])];
+        const double* upd = updc(c);
+        double v = a.rhs0[oc(c) + nd[1] + (sl - nd[4])];
         for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(upd + il[k]);
-        vg[sl] = v;
+        vg[c * MS + sl] = v;
       }
     } else if (a.first) {
       const int npair = il[4], nrhs = il[3];
       // f_t at t_{n+1}, or at t_n for the central-difference form (mode 3).
       const double ft = a.ft_dev ? a.ft_dev[a.mode == 3 ? 0 : 1] : a.ft;
       const int np = il[5];
-      for (int k = tid; k < npair; k += kThreads) pc[k] = pair_product(a, src, KP, np, k, L.pair[4 * k], s_off);
+      for (int it = tid; it < npair * ncb; it += kThreads) {
+        const int c = kCols ? it / npair : 0, k = kCols ? it - c * npair : it;
+        pc[c * MP + k] = pair_product(a, a.SRC + on(c), KP, np, k, L.pair[4 * k], s_off);
+      }
       __syncthreads();
-      for (int k = tid; k < nrhs; k += kThreads) {
+      for (int it = tid; it < nrhs * ncb; it += kThreads) {
+        const int c = kCols ? it / nrhs : 0, k = kCols ? it - c * nrhs : it;
         const int* rr = L.rhs + 4 * k;
-        double v = ft * fxc[rr[0]];
-        for (int q = rr[1]; q < rr[2]; ++q) v -= pc[q];
-        if (rr[3] >= 0 && !a.rhs_only) vg[rr[3]] = v;
-        else rhs0[rr[0]] = v;
+        double v = ft * a.fxc[oc(c) + rr[0]];
+        for (int q = rr[1]; q < rr[2]; ++q) v -= pc[c * MP + q];
+        if (rr[3] >= 0 && !a.rhs_only) vg[c * MS + rr[3]] = v;
+        else a.rhs0[oc(c) + rr[0]] = v;
       }
       if (a.rhs_only) return;   // every row's right-hand side is in rhs0
       __syncthreads();
-      for (int sl = tid; sl < nslot; sl += kThreads) {
+      for (int it = tid; it < nsi; it += kThreads) {
+        const int c = kCols ? it / nslot : 0, sl = kCols ? it - c * nslot : it;
         const int* st = L.slot + 4 * sl;
-        double v = vg[sl];
+        const double* upd = updc(c);
+        double v = vg[c * MS + sl];
         for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(upd + il[k]);
-        vg[sl] = v;
+        vg[c * MS + sl] = v;
       }
     } else {
-      for (int sl = tid; sl < nslot; sl += kThreads) {
+      for (int it = tid; it < nsi; it += kThreads) {
+        const int c = kCols ? it / nslot : 0, sl = kCols ? it - c * nslot : it;
         const int* st = L.slot + 4 * sl;
         const int* nd = L.node + 8 * st[0];
-        double v = __ldcg(rhs0 + nd[1] + (sl - nd[4]));
+        const double* upd = updc(c);
+        double v = __ldcg(a.rhs0 + oc(c) + nd[1] + (sl - nd[4]));
 #pragma unroll 4
         for (int k = st[1]; k < st[2]; ++k) v -= __ldcg(upd + il[k]);
-        vg[sl] = v;
+        vg[c * MS + sl] = v;
       }
     }
     __syncthreads();
     // y = L_tt^{-1} g, every row of every supernode of this CTA; row i
     // reads entry (i, i - d) at d = 0, 1, ..., i (see tri_size).
-    for (int sl = tid; sl < nslot; sl += kThreads) {
+    for (int it = tid; it < nsi; it += kThreads) {
+      const int c = kCols ? it / nslot : 0, sl = kCols ? it - c * nslot : it;
       const int* nd = L.node + 8 * L.slot[4 * sl];
       const int b = nd[2], s0 = nd[4], i = sl - s0;
       const double* Lp = B + nd[6];
-      const double* g = vg + s0 + i;   // g[-d] = g_{i-d}
+      const double* g = vg + c * MS + s0 + i;   // g[-d] = g_{i-d}
       double y0 = 0.0, y1 = 0.0;
       int d = 0, q = i;
       for (; d + 2 <= i + 1; d += 2) {
@@ -1191,53 +1214,62 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
       }
       if (d <= i) y0 = fma(Lp[q], g[-d], y0);
       const double y = y0 + y1;
-      vy[sl] = y;
-      sol[nd[1] + i] = y;
+      vy[c * MS + sl] = y;
+      a.sol[oc(c) + nd[1] + i] = y;
     }
     __syncthreads();
     // upd_t = L_{rows,t} y_t.
-    for (int k = tid; k < nm; k += kThreads) {
+    for (int it = tid; it < nm * ncb; it += kThreads) {
+      const int c = kCols ? it / nm : 0, k = kCols ? it - c * nm : it;
       const int* nd = L.node + 8 * L.anc[2 * k];
       const int b = nd[2], m = nd[3], s0 = nd[4], kk = k - nd[5], ldr = m | 1;
       const double* L21 = B + nd[6] + tri_size(b);
+      const double* y = vy + c * MS + s0;
       double u0 = 0.0, u1 = 0.0;
       int j = 0;
       for (; j + 2 <= b; j += 2) {
-        u0 = fma(L21[kk + ldr * j], vy[s0 + j], u0);
-        u1 = fma(L21[kk + ldr * (j + 1)], vy[s0 + j + 1], u1);
+        u0 = fma(L21[kk + ldr * j], y[j], u0);
+        u1 = fma(L21[kk + ldr * (j + 1)], y[j + 1], u1);
       }
-      if (j < b) u0 = fma(L21[kk + ldr * j], vy[s0 + j], u0);
-      upd[nd[7] + kk] = u0 + u1;
+      if (j < b) u0 = fma(L21[kk + ldr * j], y[j], u0);
+      updc(c)[nd[7] + kk] = u0 + u1;
     }
   } else {
-    for (int k = tid; k < nm; k += kThreads) vm[k] = __ldcg(sol + L.anc[2 * k + 1]);
-    for (int sl = tid; sl < nslot; sl += kThreads) {
+    for (int it = tid; it < nm * ncb; it += kThreads) {
+      const int c = kCols ? it / nm : 0, k = kCols ? it - c * nm : it;
+      vm[c * MM + k] = __ldcg(a.sol + oc(c) + L.anc[2 * k + 1]);
+    }
+    for (int it = tid; it < nsi; it += kThreads) {
+      const int c = kCols ? it / nslot : 0, sl = kCols ? it - c * nslot : it;
       const int* nd = L.node + 8 * L.slot[4 * sl];
-      vg[sl] = __ldcg(sol + nd[1] + (sl - nd[4]));
+      vg[c * MS + sl] = __ldcg(a.sol + oc(c) + nd[1] + (sl - nd[4]));
     }
     __syncthreads();
     // h = y_t - L_{rows,t}^T x_rows.
-    for (int sl = tid; sl < nslot; sl += kThreads) {
+    for (int it = tid; it < nsi; it += kThreads) {
+      const int c = kCols ? it / nslot : 0, sl = kCols ? it - c * nslot : it;
       const int* nd = L.node + 8 * L.slot[4 * sl];
       const int b = nd[2], m = nd[3], i = sl - nd[4], mo = nd[5], ldr = m | 1;
       const double* L21 = B + nd[6] + tri_size(b) + (size_t)ldr * i;
+      const double* x = vm + c * MM + mo;
       double h0 = 0.0, h1 = 0.0;
       int k = 0;
       for (; k + 2 <= m; k += 2) {
-        h0 = fma(L21[k], vm[mo + k], h0);
-        h1 = fma(L21[k + 1], vm[mo + k + 1], h1);
+        h0 = fma(L21[k], x[k], h0);
+        h1 = fma(L21[k + 1], x[k + 1], h1);
       }
-      if (k < m) h0 = fma(L21[k], vm[mo + k], h0);
-      vy[sl] = vg[sl] - (h0 + h1);
+      if (k < m) h0 = fma(L21[k], x[k], h0);
+      vy[c * MS + sl] = vg[c * MS + sl] - (h0 + h1);
     }
     __syncthreads();
     // x_t = L_tt^{-T} h, then the correction of the row; column i reads
     // entry (i + d, i) at d = 0, 1, ..., b - 1 - i.
-    for (int sl = tid; sl < nslot; sl += kThreads) {
+    for (int it = tid; it < nsi; it += kThreads) {
+      const int c = kCols ? it / nslot : 0, sl = kCols ? it - c * nslot : it;
       const int* nd = L.node + 8 * L.slot[4 * sl];
       const int b = nd[2], s0 = nd[4], i = sl - s0, n = b - i;
       const double* Lp = B + nd[6];
-      const double* h = vy + s0 + i;   // h[d] = h_{i+d}
+      const double* h = vy + c * MS + s0 + i;   // h[d] = h_{i+d}
       double x0 = 0.0, x1 = 0.0;
       int d = 0, q = i;
       for (; d + 2 <= n; d += 2) {
@@ -1248,29 +1280,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_walk(WalkArgs a) {
       }
       if (d < n) x0 = fma(Lp[q], h[d], x0);
       const double x = x0 + x1;
-      sol[nd[1] + i] = x;
-      if (sl < tid + kThreads) cor.row_pre(nd[1] + i, x, pre_node[0], pre_v[0], pre_a[0]);
-      else if (sl < tid + 2 * kThreads) cor.row_pre(nd[1] + i, x, pre_node[1], pre_v[1], pre_a[1]);
+      a.sol[oc(c) + nd[1] + i] = x;
+      const Corr cor = corr(c);
+      if (it < tid + kThreads) cor.row_pre(nd[1] + i, x, pre_node[0], pre_v[0], pre_a[0]);
+      else if (it < tid + 2 * kThreads) cor.row_pre(nd[1] + i, x, pre_node[1], pre_v[1], pre_a[1]);
       else cor.row(nd[1] + i, x);
     }
   }
 }
 
+template <bool kCols>
 __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   extern __shared__ __align__(16) double tsm[];
   const int cta = blockIdx.x, tid = threadIdx.x;
-  // Column of an independent-columns context (blockIdx.y).
-  const int64_t on = (int64_t)blockIdx.y * a.cs_node, oc = (int64_t)blockIdx.y * a.cs_c;
-  const double* rhs0 = a.rhs0 + oc;
-  double* sol = a.sol + oc;
-  const double* upd = a.upd + (int64_t)blockIdx.y * a.cs_upd;
-  const Corr cor{a.mode, a.c_node, a.U + on, a.v_c + oc, a.a_c + oc, a.dt, a.Un ? a.Un + on : nullptr};
+  // Block of independent columns (blockIdx.y): col0 .. col0 + ncb - 1; the
+  // chunk of A_Z is staged once and each of its entries is loaded once for
+  // up to four columns.  kCols = false: one column per CTA.
+  const int col0 = kCols ? blockIdx.y * a.cb : blockIdx.y, ncb = kCols ? min(a.cb, a.ncols - col0) : 1;
+  auto on = [&](int c) { return (int64_t)(col0 + c) * a.cs_node; };
+  auto oc = [&](int c) { return (int64_t)(col0 + c) * a.cs_c; };
+  auto corr = [&](int c) {
+    return Corr{a.mode, a.c_node, a.U + on(c), a.v_c + oc(c), a.a_c + oc(c), a.dt, a.Un ? a.Un + on(c) : nullptr};
+  };
   const int comp = a.cta_comp[cta], r0 = a.cta_r0[cta], r1 = a.cta_r1[cta];
-  const int zn = a.zsize[comp], zb = a.zbase[comp], nr = r1 - r0;
-  double* zs = tsm;                               // max_zn (even): right-hand side of the block
-  double* Ac = zs + a.max_zn;                     // max_arows: this CTA's rows of A_Z
-  double* xs = Ac + a.max_arows;                  // kThreads: partial dot products
-  int* il = reinterpret_cast<int*>(xs + kThreads);  // per row {update begin, update end}, positions
+  const int zn = a.zsize[comp], zb = a.zbase[comp], nr = r1 - r0, MZ = a.max_zn;
+  double* zs = tsm;                               // cb x max_zn (even): right-hand sides of the block
+  double* Ac = zs + (size_t)a.cb * MZ;            // max_arows: this CTA's rows of A_Z
+  double* xs = Ac + a.max_arows;                  // cb x kThreads: partial dot products
+  int* il = reinterpret_cast<int*>(xs + (size_t)a.cb * kThreads);  // per row {update begin, end}, positions
   async_copy_16(Ac, a.zA + a.zA_off[comp] + (size_t)r0 * zn, ((int64_t)nr * zn + 1) / 2);
   async_copy_16(il, a.ilist + a.ilist_off[cta], a.ilist_len[cta] / 4);
   // c-index of this thread's first kZr rows of the block (registers: the
@@ -1281,15 +1318,17 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
 #pragma unroll
   for (int q = 0; q < kZr; ++q) zr[q] = tid + q * kThreads < zn ? a.zrow[zb + tid + q * kThreads] : 0;
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-  // The correction state of this thread's row (nr <= blockDim.x); not written
-  // by the launches of the step that run before this one.
+  // The correction state of this thread's row in the first column (nr <=
+  // blockDim.x); not written by the launches of the step that run before
+  // this one.
+  const Corr cor0 = corr(0);
   int row = 0, node = 0;
   double v_old = 0.0, a_old = 0.0;
   if (tid < nr) {
     row = a.zrow[zb + r0 + tid];
-    node = cor.c_node[row];
-    v_old = cor.v_c[row];
-    a_old = cor.a_c[row];
+    node = cor0.c_node[row];
+    v_old = cor0.v_c[row];
+    a_old = cor0.a_c[row];
   }
   async_copy_wait();
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
@@ -1297,52 +1336,90 @@ __global__ void __launch_bounds__(kThreads) k_top(TopArgs a) {
   // Inputs of the correction written by the earlier launches of the step,
   // loaded now so that their latency overlaps the gather.
   double u_in = 0.0, un_in = 0.0;
-  if (tid < nr && cor.mode != 2) {
-    u_in = __ldcg(cor.U + node);
-    if (cor.mode == 3) un_in = __ldcg(cor.Un + node);
+  if (tid < nr && cor0.mode != 2) {
+    u_in = __ldcg(cor0.U + node);
+    if (cor0.mode == 3) un_in = __ldcg(cor0.Un + node);
   }
-  // The whole right-hand side of this component's top block (redundant per CTA).
-  auto gather = [&](int i, int zri) {
+  // The whole right-hand side of this component's top block, every column
+  // (redundant per CTA).
+  auto gather = [&](int c, int i, int zri) {
     const int fb = il[2 * i], fe = il[2 * i + 1];
-    double v = __ldcg(rhs0 + zri);
+    const double* upd = a.upd + (int64_t)(col0 + c) * a.cs_upd;
+    double v = __ldcg(a.rhs0 + oc(c) + zri);
 #pragma unroll 4
     for (int k = fb; k < fe; ++k) v -= __ldcg(upd + il[k]);
-    zs[i] = v;
+    zs[(size_t)c * MZ + i] = v;
   };
 #pragma unroll
   for (int q = 0; q < kZr; ++q)
-    if (tid + q * kThreads < zn) gather(tid + q * kThreads, zr[q]);
-  for (int i = tid + kZr * kThreads; i < zn; i += kThreads) gather(i, a.zrow[zb + i]);
+    if (tid + q * kThreads < zn) gather(0, tid + q * kThreads, zr[q]);
+  for (int i = tid + kZr * kThreads; i < zn; i += kThreads) gather(0, i, a.zrow[zb + i]);
+  if (kCols)
+    for (int it = tid; it < zn * (ncb - 1); it += kThreads) {
+      const int c = 1 + it / zn, i = it - (c - 1) * zn;
+      gather(c, i, a.zrow[zb + i]);
+    }
   __syncthreads();
   // Rows of A_Z times z.  The chunk is stored column-major (row i, column
   // j at j * nr + i); thread (s, i) takes row i over the s-th of S column
   // slices, so a warp reads consecutive words, and the slices are summed
-  // pairwise (S - 1 additions per row, spread over the threads).
+  // pairwise (S - 1 additions per row, spread over the threads).  Per column
+  // the sums run in the same order whatever the column block.
   const int nslice = min(kThreads / max(nr, 1), max(zn / 2, 1));
   if (tid < nslice * nr) {
     const int s = tid / nr, i = tid - s * nr;
     const int j0 = zn * s / nslice, j1 = zn * (s + 1) / nslice;
     const double* Ai = Ac + i;
-    double s0 = 0.0, s1 = 0.0;
-    int j = j0;
-    for (; j + 2 <= j1; j += 2) {
-      s0 = fma(Ai[(size_t)j * nr], zs[j], s0);
-      s1 = fma(Ai[(size_t)(j + 1) * nr], zs[j + 1], s1);
+    int c = 0;
+    for (; kCols && c + 4 <= ncb; c += 4) {
+      const double* z = zs + (size_t)c * MZ;
+      double s0[4] = {0.0, 0.0, 0.0, 0.0}, s1[4] = {0.0, 0.0, 0.0, 0.0};
+      int j = j0;
+      for (; j + 2 <= j1; j += 2) {
+        const double e0 = Ai[(size_t)j * nr], e1 = Ai[(size_t)(j + 1) * nr];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          s0[q] = fma(e0, z[q * MZ + j], s0[q]);
+          s1[q] = fma(e1, z[q * MZ + j + 1], s1[q]);
+        }
+      }
+      if (j < j1) {
+        const double e0 = Ai[(size_t)j * nr];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s0[q] = fma(e0, z[q * MZ + j], s0[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xs[(size_t)(c + q) * kThreads + tid] = s0[q] + s1[q];
     }
-    if (j < j1) s0 = fma(Ai[(size_t)j * nr], zs[j], s0);
-    xs[tid] = s0 + s1;
+    for (; c < ncb; ++c) {
+      const double* z = zs + (size_t)c * MZ;
+      double s0 = 0.0, s1 = 0.0;
+      int j = j0;
+      for (; j + 2 <= j1; j += 2) {
+        s0 = fma(Ai[(size_t)j * nr], z[j], s0);
+        s1 = fma(Ai[(size_t)(j + 1) * nr], z[j + 1], s1);
+      }
+      if (j < j1) s0 = fma(Ai[(size_t)j * nr], z[j], s0);
+      xs[(size_t)c * kThreads + tid] = s0 + s1;
+    }
   }
   __syncthreads();
   for (int h = nslice; h > 1;) {
     const int h2 = (h + 1) / 2;   // slice s < h - h2 takes in slice s + h2
-    if (tid < (h - h2) * nr) xs[tid] += xs[tid + h2 * nr];
+    if (tid < (h - h2) * nr)
+      for (int c = 0; c < (kCols ? ncb : 1); ++c) xs[(size_t)c * kThreads + tid] += xs[(size_t)c * kThreads + tid + h2 * nr];
     h = h2;
     __syncthreads();
   }
   if (tid < nr) {
     const double x = xs[tid];
-    sol[row] = x;
-    cor.row_in(row, x, v_old, a_old, node, u_in, un_in);
+    a.sol[oc(0) + row] = x;
+    cor0.row_in(row, x, v_old, a_old, node, u_in, un_in);
+    for (int c = 1; kCols && c < ncb; ++c) {
+      const double xc = xs[(size_t)c * kThreads + tid];
+      a.sol[oc(c) + row] = xc;
+      corr(c).row(row, xc);
+    }
   }
 }
 

@@ -64,11 +64,13 @@ class Stats(ctypes.Structure):
          ("explicit_variant", ctypes.c_int64), ("explicit_sweep_us", ctypes.c_double),
          ("explicit_sweep_short_us", ctypes.c_double), ("large_supernodes", ctypes.c_int64),
          ("max_rows", ctypes.c_int64), ("solve_smem_needed", ctypes.c_int64),
-         ("explicit_split_us", ctypes.c_double * 4)]
+         ("explicit_split_us", ctypes.c_double * 4), ("solve_col_block", ctypes.c_int64),
+         ("solve_col_block_us", ctypes.c_double * 7)]
 
     def as_dict(self):
         out = {n: getattr(self, n) for n, _ in self._fields_}
         out["explicit_split_us"] = list(out["explicit_split_us"])
+        out["solve_col_block_us"] = list(out["solve_col_block_us"])
         return out
 
 

@@ -126,3 +126,23 @@ def test_explicit_variants_agree_bitwise(make, monkeypatch):
     ref = out[("large", None)][0]
     for key, (u, _) in out.items():
         assert np.array_equal(u, ref), key
+
+
+def test_column_blocks_agree_bitwise(monkeypatch):
+    # A walk / dense-top CTA takes a block of independent columns (the factor
+    # blocks staged once for all of them); per column the arithmetic is the
+    # same, so every block size (here 1, 3 with a ragged last block, 4 and
+    # all 10 columns) gives the same numbers bit for bit.
+    imex = _imex()
+    w = workloads.multisource(nsrc=10)
+    out = {}
+    for cb in (1, 3, 4, 10):
+        monkeypatch.setenv("IMEX_COL_BLOCK", str(cb))
+        with imex.Imex.from_workload(w, ncols=10) as g:
+            g.step(60)
+            assert g.info()["solve_col_block"] == cb
+            out[cb] = _state(g)
+    assert np.abs(out[1]["a_c"]).max() > 0
+    for cb in (3, 4, 10):
+        for k in out[1]:
+            assert np.array_equal(out[cb][k], out[1][k]), (cb, k)
