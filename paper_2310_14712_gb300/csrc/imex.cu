@@ -81,28 +81,36 @@ struct PcgCols {
   const double* gt_val;
 };
 
+template <int LPR>
 __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a, PcgCols t2) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[kWarps];
   const int n = a.n;
   const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  // Sparse products one warp per row: lanes stride the row (coalesced column
-  // and value loads), a fixed xor tree sums them; every lane gets the value.
+  // Sparse products: a group of LPR lanes per row (32 / LPR rows per warp in
+  // flight), lanes striding the row (coalesced column and value loads), a
+  // fixed xor tree within the group sums them; every lane of the group gets
+  // the value.  Rows go to warps in rounds, the same number for every lane
+  // of a warp.
+  constexpr int GPW = 32 / LPR;
   const int lane = threadIdx.x & 31, w0 = g0 >> 5, ws = gs >> 5;
-  auto warp_dot = [&](const int* ptr, const int* col, const double* val, const double* v, int i) {
-    const int end = ptr[i + 1];
+  const int sub = lane % LPR, grp = lane / LPR;
+  auto group_dot = [&](const int* ptr, const int* col, const double* val, const double* v, int i, bool ok) {
     double t0 = 0.0, t1 = 0.0;
-    int k = ptr[i] + lane;
-    for (; k + 32 < end; k += 64) {   // two independent gathers in flight per lane
-      const int c0 = col[k], c1 = col[k + 32];
-      const double v0 = val[k], v1 = val[k + 32];
-      t0 = fma(v0, __ldcg(v + c0), t0);
-      t1 = fma(v1, __ldcg(v + c1), t1);
+    if (ok) {
+      const int end = ptr[i + 1];
+      int k = ptr[i] + sub;
+      for (; k + LPR < end; k += 2 * LPR) {   // two independent gathers in flight per lane
+        const int c0 = col[k], c1 = col[k + LPR];
+        const double v0 = val[k], v1 = val[k + LPR];
+        t0 = fma(v0, __ldcg(v + c0), t0);
+        t1 = fma(v1, __ldcg(v + c1), t1);
+      }
+      if (k < end) t0 = fma(val[k], __ldcg(v + col[k]), t0);
     }
-    if (k < end) t0 = fma(val[k], __ldcg(v + col[k]), t0);
     double t = t0 + t1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    for (int o = LPR / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     return t;
   };
   // z = M^{-1} r
@@ -110,26 +118,16 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a, PcgCols t2) {
     if (a.precond == 2) {
       for (int i = g0; i < n; i += gs) a.z[i] = a.dinv[i] * a.r[i];
     } else {
-      for (int j = w0; j < n; j += ws) {   // w = G^T r, column j of G
-        const int end = a.gt_ptr[j + 1];
-        double t0 = 0.0, t1 = 0.0;
-        int k = a.gt_ptr[j] + lane;
-        for (; k + 32 < end; k += 64) {
-          const int r0 = a.gt_row[k], r1 = a.gt_row[k + 32];
-          const double g0v = t2.gt_val[k], g1v = t2.gt_val[k + 32];
-          t0 = fma(g0v, __ldcg(a.r + r0), t0);
-          t1 = fma(g1v, __ldcg(a.r + r1), t1);
-        }
-        if (k < end) t0 = fma(t2.gt_val[k], __ldcg(a.r + a.gt_row[k]), t0);
-        double t = t0 + t1;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) a.w[j] = t;
+      for (int base = w0 * GPW; base < n; base += ws * GPW) {   // w = G^T r, column j of G
+        const int j = base + grp;
+        const double wj = group_dot(a.gt_ptr, a.gt_row, t2.gt_val, a.r, j, j < n);
+        if (sub == 0 && j < n) a.w[j] = wj;
       }
       grid.sync();
-      for (int i = w0; i < n; i += ws) {
-        const double zi = warp_dot(a.g_ptr, a.g_col, a.g_val, a.w, i);
-        if (lane == 0) a.z[i] = zi;
+      for (int base = w0 * GPW; base < n; base += ws * GPW) {
+        const int i = base + grp;
+        const double zi = group_dot(a.g_ptr, a.g_col, a.g_val, a.w, i, i < n);
+        if (sub == 0 && i < n) a.z[i] = zi;
       }
       grid.sync();   // z is read below by other threads than its writers
     }
@@ -148,9 +146,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a, PcgCols t2) {
   }
   grid.sync();
   double bb = 0.0, rr = 0.0;
-  for (int i = w0; i < n; i += ws) {
-    const double ri0 = warp_dot(a.s_ptr, a.s_col, a.s_val, a.x, i);
-    if (lane == 0) {
+  for (int base = w0 * GPW; base < n; base += ws * GPW) {
+    const int i = base + grp;
+    const double ri0 = group_dot(a.s_ptr, a.s_col, a.s_val, a.x, i, i < n);
+    if (sub == 0 && i < n) {
       const double bi = a.b[i], ri = bi - ri0;
       a.r[i] = ri;
       bb = fma(bi, bi, bb);
@@ -166,51 +165,74 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a, PcgCols t2) {
   bool conv = rr_t <= tol2;
   int k = 0;
   if (!conv) {
-    apply_minv();
-    double rz = 0.0;
-    for (int i = g0; i < n; i += gs) {
-      a.p[i] = a.z[i];
-      rz = fma(a.r[i], a.z[i], rz);
-    }
-    block_partial(rz, a.part, 2, red);
-    grid.sync();
-    rz = grid_total(a.part, 2);
-    for (k = 1; k <= a.maxit; ++k) {
-      double pq = 0.0;
-      for (int i = w0; i < n; i += ws) {
-        const double qi = warp_dot(a.s_ptr, a.s_col, a.s_val, a.p, i);
-        if (lane == 0) {
-          a.q[i] = qi;
-          pq = fma(a.p[i], qi, pq);
+    // Preconditioned CG in the single-reduction form of Chronopoulos and
+    // Gear (Chronopoulos & Gear 1989, J. Comput. Appl. Math. 25): besides p
+    // it carries s = S p, so that per iteration the three inner products
+    // gamma = (r, u), delta = (S u, u) and (r, r) (u = M^{-1} r) are formed
+    // in one reduction: one grid barrier for them, one before S u, and two
+    // inside G G^T r (FSAI) or none (Jacobi, applied elementwise).  In exact
+    // arithmetic the iterates are those of standard PCG.  Partial sums
+    // alternate between two sets of slots by iteration parity, because the
+    // next iteration writes them before its next barrier.
+    auto reduce3 = [&](double gam, double del, double rr2, int set, double& G, double& D, double& R) {
+      block_partial(gam, a.part, 4 + 3 * set, red);
+      block_partial(del, a.part, 5 + 3 * set, red);
+      block_partial(rr2, a.part, 6 + 3 * set, red);
+      grid.sync();
+      G = grid_total(a.part, 4 + 3 * set);
+      D = grid_total(a.part, 5 + 3 * set);
+      R = grid_total(a.part, 6 + 3 * set);
+    };
+    // w = S u, with the partials of (r, u) and (w, u) of this thread's rows.
+    auto apply_S_u = [&](double& gam, double& del) {
+      for (int base = w0 * GPW; base < n; base += ws * GPW) {
+        const int i = base + grp;
+        const double wi = group_dot(a.s_ptr, a.s_col, a.s_val, a.z, i, i < n);
+        if (sub == 0 && i < n) {
+          const double ui = a.z[i];
+          a.v[i] = wi;
+          gam = fma(a.r[i], ui, gam);
+          del = fma(wi, ui, del);
         }
       }
-      block_partial(pq, a.part, 0, red);
-      grid.sync();
-      const double alpha = rz / grid_total(a.part, 0);
-      rr = 0.0;
+    };
+    apply_minv();
+    if (a.precond == 2) grid.sync();   // u complete before S u
+    double gam = 0.0, del = 0.0, R = rr_t;
+    apply_S_u(gam, del);
+    double rr_unused = 0.0;
+    reduce3(gam, del, rr_unused, 0, gam, del, rr_unused);
+    double alpha = gam / del, beta = 0.0;
+    for (k = 1; k <= a.maxit; ++k) {
+      double rr2 = 0.0;
       for (int i = g0; i < n; i += gs) {
-        a.x[i] = fma(alpha, a.p[i], a.x[i]);
-        const double ri = fma(-alpha, a.q[i], a.r[i]);
+        // First iteration: p = u, s = S u (p and s hold nothing yet).
+        const double pi = k == 1 ? a.z[i] : fma(beta, a.p[i], a.z[i]);
+        const double si = k == 1 ? a.v[i] : fma(beta, a.q[i], a.v[i]);
+        a.p[i] = pi;
+        a.q[i] = si;
+        a.x[i] = fma(alpha, pi, a.x[i]);
+        const double ri = fma(-alpha, si, a.r[i]);
         a.r[i] = ri;
-        rr = fma(ri, ri, rr);
+        rr2 = fma(ri, ri, rr2);
+        if (a.precond == 2) a.z[i] = a.dinv[i] * ri;
       }
-      block_partial(rr, a.part, 1, red);
-      grid.sync();
-      rr_t = grid_total(a.part, 1);
+      if (a.precond == 2) grid.sync();   // u complete before S u
+      else {
+        grid.sync();                      // r complete before G^T r
+        apply_minv();                     // ends with u complete
+      }
+      double g1 = 0.0, d1 = 0.0;
+      apply_S_u(g1, d1);
+      reduce3(g1, d1, rr2, k & 1, g1, d1, R);
+      rr_t = R;
       if (rr_t <= tol2) {
         conv = true;
         break;
       }
-      apply_minv();
-      double rzn = 0.0;
-      for (int i = g0; i < n; i += gs) rzn = fma(a.r[i], a.z[i], rzn);
-      block_partial(rzn, a.part, 2, red);
-      grid.sync();
-      rzn = grid_total(a.part, 2);
-      const double beta = rzn / rz;
-      rz = rzn;
-      for (int i = g0; i < n; i += gs) a.p[i] = fma(beta, a.p[i], a.z[i]);
-      grid.sync();
+      beta = g1 / gam;
+      alpha = g1 / (d1 - beta * g1 / alpha);
+      gam = g1;
     }
     if (k > a.maxit) k = a.maxit;
   }
@@ -815,6 +837,7 @@ struct imex_ctx {
   double pcg_tol = 1e-10;
   int pcg_maxit = 200;
   int pcg_grid = 0;
+  int pcg_lpr = 32;   // lanes per sparse row of the PCG products (from the mean row length of S)
   int64_t g_nnz = 0;
   int *s_ptr = nullptr, *s_col = nullptr;
   double* s_val = nullptr;
@@ -828,7 +851,8 @@ struct imex_ctx {
   int factorized = 1;
   double *m_val = nullptr, *dinv_m = nullptr, *if_sc_dev = nullptr;
   int *pr_ptr = nullptr, *pr_pos = nullptr, *if_base_dev = nullptr, *if_koff_dev = nullptr;
-  double *pcg_x = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_w = nullptr;
+  double *pcg_x = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_w = nullptr,
+         *pcg_v = nullptr;
   double *pcg_part = nullptr, *pcg_res = nullptr;
   // learned starting guess of the PCG solves: history a^c_{n-1}, a^c_{n-2}
   // (pcg_hist, 2 n_c) and the Adam state of the three weights (guess_state:
@@ -1380,6 +1404,16 @@ cudaError_t autotune_tile(imex_ctx* c) {
 
 // PCG on S (the step; Newmark correction) or, for the initial acceleration
 // of a context without a factorisation, on M^cc with Jacobi (mode 1).
+// The PCG kernel with `lpr` lanes per sparse row.
+const void* pcg_kernel(int lpr) {
+  switch (lpr) {
+    case 4: return (const void*)k_pcg<4>;
+    case 8: return (const void*)k_pcg<8>;
+    case 16: return (const void*)k_pcg<16>;
+    default: return (const void*)k_pcg<32>;
+  }
+}
+
 cudaError_t launch_pcg(imex_ctx* c, double* Ubuf, cudaStream_t s, bool on_M = false) {
   const HostSetup& hs = c->hs;
   PcgArgs a{};
@@ -1402,6 +1436,7 @@ cudaError_t launch_pcg(imex_ctx* c, double* Ubuf, cudaStream_t s, bool on_M = fa
   a.p = c->pcg_p;
   a.q = c->pcg_q;
   a.w = c->pcg_w;
+  a.v = c->pcg_v;
   a.part = c->pcg_part;
   a.tol = on_M ? 1e-12 : c->pcg_tol;
   a.maxit = on_M ? 100000 : c->pcg_maxit;
@@ -1420,7 +1455,7 @@ cudaError_t launch_pcg(imex_ctx* c, double* Ubuf, cudaStream_t s, bool on_M = fa
   a.dt = hs.dt;
   PcgCols t2{c->gt_val};
   void* args[] = {&a, &t2};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(c->pcg_grid), dim3(kThreads), args, 0, s);
+  return cudaLaunchCooperativeKernel(pcg_kernel(c->pcg_lpr), dim3(c->pcg_grid), dim3(kThreads), args, 0, s);
 }
 
 // Right-hand sides rhs0 = f_t f^c - K^c src of a context without a solve plan.
@@ -2731,8 +2766,8 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
       ar.add(&c->g_sg, gnz);
       ar.add(&c->g_isdiag, gnz);
       ar.add(&c->dinv, ncm);
-      for (double** v : {&c->pcg_x, &c->pcg_r, &c->pcg_z, &c->pcg_p, &c->pcg_q, &c->pcg_w}) ar.add(v, ncm);
-      ar.add(&c->pcg_part, 4 * std::max<int64_t>(1024, (ncm + kThreads - 1) / kThreads));
+      for (double** v : {&c->pcg_x, &c->pcg_r, &c->pcg_z, &c->pcg_p, &c->pcg_q, &c->pcg_w, &c->pcg_v}) ar.add(v, ncm);
+      ar.add(&c->pcg_part, 10 * std::max<int64_t>(1024, (ncm + kThreads - 1) / kThreads));
       ar.add(&c->pcg_hist, 2 * ncm);
       ar.add(&c->guess_state, 16);
       ar.add(&c->pcg_res, 2);
@@ -2817,16 +2852,23 @@ int setup_impl(const imex_mesh* mesh, int p, double alpha, double dt, const imex
     e = e ? e : upload(c->g_isdiag, pp.g_isdiag);
     e = e ? e : upload(c->dinv, pp.dinv);
     if (e == cudaSuccess) {
+      // Lanes per sparse row: about six entries of a mean row of S per lane
+      // (4 .. 32, a power of two).  Grid: small partitions one CTA per SM
+      // (the grid barriers grow with the CTAs: on the 256x128 plate, 8 lanes
+      // per row and one CTA per SM took 58 us per FSAI iteration, four CTAs
+      // per SM 78 us, 32 lanes 101 us); large ones (3D) every co-resident
+      // CTA; never more CTAs than the rows fill.
+      const double avg = hs.n_c > 0 ? (double)hs.S_ptr[hs.n_c] / (double)hs.n_c : 1.0;
+      c->pcg_lpr = 4;
+      while (c->pcg_lpr < 32 && c->pcg_lpr * 6 < avg) c->pcg_lpr *= 2;
       int occ = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg, kThreads, 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel(c->pcg_lpr), kThreads, 0);
       int nsm = 0;
       e = e ? e : cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-      // Sparse products take one warp per row.  Small partitions: at most one
-      // CTA per SM (fewer CTAs make the grid barriers cheaper); large ones
-      // (3D): every co-resident CTA, about four rows per warp.
-      const int64_t rows_ctas = std::max<int64_t>(1, (hs.n_c + 4 * kWarps - 1) / (4 * kWarps));
-      const int cap = hs.n_c >= 65536 ? nsm * occ : nsm;
-      c->pcg_grid = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)cap, 1024, (int64_t)nsm * occ, rows_ctas}));
+      const int64_t rows_per_cta = (int64_t)kWarps * (32 / c->pcg_lpr);
+      const int64_t rows_ctas = std::max<int64_t>(1, (hs.n_c + rows_per_cta - 1) / rows_per_cta);
+      const int64_t cap = hs.n_c >= 65536 ? (int64_t)nsm * occ : nsm;
+      c->pcg_grid = (int)std::max<int64_t>(1, std::min<int64_t>({cap, (int64_t)nsm * occ, 1024, rows_ctas}));
     }
     e = e ? e : upload(c->het_base, hb);
     e = e ? e : upload(c->het_koff, hk);

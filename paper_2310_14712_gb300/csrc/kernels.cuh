@@ -241,8 +241,9 @@ struct PcgArgs {
   const double* dinv;             // 1 / S_ii
   int precond;                    // 1: M^{-1} = G G^T; 2: M^{-1} = diag(S)^{-1}
   const double* b;                // right-hand side
-  double *x, *r, *z, *p, *q, *w;  // n each
-  double* part;                   // 4 x gridDim.x block partial sums
+  double *x, *r, *z, *p, *q, *w;  // n each: iterate, residual, u = M^{-1} r, direction, S p, G^T r
+  double* v;                      // n: S u
+  double* part;                   // 10 x gridDim.x block partial sums
   double tol;                     // stop when ||r|| <= tol ||b||
   int maxit;
   int* status;                    // [0] iterations of the last solve, [1] 1: converged, 0: fallback
