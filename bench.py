@@ -148,7 +148,10 @@ def measure_batched(imex, workloads, steps, stream, flush, rank=0, ws=1):
         n_act = st["n_d"] + st["n_c"]
         out[label] = {"value": n_act * ncols * steps / (ms * 1e-3), "ms_per_step": ms / steps,
                       "ncols": ncols, "explicit_variant": EXPLICIT_VARIANTS[st["explicit_variant"]],
-                      "explicit_autotune_us": explicit_autotune_us(st)}
+                      "explicit_autotune_us": explicit_autotune_us(st),
+                      "solve_col_block": st["solve_col_block"],
+                      "solve_col_block_autotune_us": {str(1 << k): (v or None)
+                                                      for k, v in enumerate(st["solve_col_block_us"])}}
         g.close()
     b = out["batched"]
     b.update({"workload": "multisource: [0,1]^2 minus a centred circle r=0.2, 16x16 cells, p=4, "
