@@ -3185,6 +3185,29 @@ static int autotune_tile_steps(imex_ctx* c) {
   }
   e = e ? e : use_explicit(c, best_var);
   c->smem_walk_req = best_req;
+  // The column block was tuned with the explicit variant chosen before; with
+  // the final variant and walk request, the neighbouring block sizes are
+  // timed once more and the fastest kept.
+  if (c->ncols > 1 && !col_block_env() && e == cudaSuccess && rc == IMEX_OK) {
+    const int cb0 = c->col_block;
+    float bbest = best;
+    int bcb = cb0;
+    for (int cb : {cb0 / 2, cb0 * 2}) {
+      if (cb < 1 || cb > c->ncols || !set_col_block(c, cb)) continue;
+      c->smem_walk_req = std::max(c->smem_walk, best_req);
+      float us = 0.f;
+      rc = time_steps(&us);
+      if (e != cudaSuccess || rc != IMEX_OK) break;
+      for (int k = 0; k < 7; ++k)
+        if ((1 << k) == cb) c->cb_us[k] = us;
+      if (us < bbest) {
+        bbest = us;
+        bcb = cb;
+      }
+    }
+    set_col_block(c, bcb);
+    c->smem_walk_req = std::max(c->smem_walk, best_req);
+  }
   if (ev[0]) cudaEventDestroy(ev[0]);
   if (ev[1]) cudaEventDestroy(ev[1]);
   e = e ? e : copy_state(false);
