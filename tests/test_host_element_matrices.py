@@ -6,7 +6,8 @@ for uncut cells (Sec. Spatial discretization).  Here its K_e and M_e, read back
 through imex_host_element_matrices, are compared entry by entry with the
 oracle's (oracle/discretize.py: spacetree_points + element_from_points for cut
 cells, uncut_element for uncut ones) on every cut cell and a few uncut and
-empty cells of a 2D plate and a small 3D box with a void.  The two sum the
+empty cells of a 2D plate, a small 3D box with a void and a plate with a
+wave speed per cell.  The two sum the
 same quadrature in different orders, so entries agree to roundoff (1e-12 of
 the largest entry of the cell's matrix).  No GPU is needed.
 """
@@ -55,8 +56,9 @@ def _check(w, n_uncut=3):
     ids = np.array(cut + uncut + empty, dtype=np.int64)
     assert len(cut) > 0 and len(uncut) > 0
     K, M, types = imex.host_element_matrices(ids, **w.kwargs())
+    speed = np.full(len(cells), float(w.c0)) if w.cell_c is None else np.asarray(w.cell_c, dtype=float)
     for q, cid in enumerate(ids):
-        kind, Ke, Me = _oracle_cell(grid, geom, cells[cid], w.alpha, w.depth, w.rho, w.c0)
+        kind, Ke, Me = _oracle_cell(grid, geom, cells[cid], w.alpha, w.depth, w.rho, float(speed[cid]))
         assert types[q] == TYPE_CODE[kind], (cid, types[q], kind)
         for lib, ref in ((K[q], Ke), (M[q], Me)):
             scale = max(np.abs(ref).max(), 1e-300)
@@ -75,6 +77,16 @@ def test_3d_box_with_a_void():
                            3.0, 0.08, 0)
     types = _check(w)
     assert (types == 1).sum() > 5
+
+
+def test_per_cell_wave_speed():
+    # The adjoint's workload: a wave speed per cell in [0.8, 1.2]; cut cells
+    # integrate rho c_e^2 on their spacetree, uncut cells scale the reference
+    # stiffness by c_e^2 / c0^2 (the mass does not depend on c).
+    w = workloads.adjoint()
+    assert w.cell_c is not None and np.ptp(w.cell_c) > 0.1
+    types = _check(w)
+    assert (types == 1).sum() > 10
 
 
 def test_out_of_range_cell_is_rejected():
