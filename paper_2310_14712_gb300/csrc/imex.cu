@@ -1508,10 +1508,13 @@ int compute_initial(imex_ctx* c, cudaStream_t s) {
 //  * Split level per component: the smallest level L >= 1 such that the nodes
 //    at levels >= L hold at most kZmax rows; those rows form the dense top.
 //  * Walked levels l = 0 .. max L - 1: the level's nodes of every component are
-//    packed into CTAs, largest FP64 work first onto the least-loaded CTA that
-//    still has a free warp and room in its shared-memory blob (<= 8 nodes,
-//    one warp each), aiming at one CTA per SM.  A CTA's blob holds its nodes'
-//    [L_tt^{-1} (ld b|1) | L_{rows,t} (ld m|1)], 16-byte aligned, for S and M^cc.
+//    packed into CTAs, largest FP64 work first (level 0: with the right-hand
+//    side pairs of their rows) onto the least-loaded CTA that has room in its
+//    shared-memory blob (at most kMaxNodesPerCTA nodes; all threads of a CTA
+//    share the rows of all its nodes in each phase), aiming at one CTA per SM;
+//    supernodes above kMaxWidth rows go to k_panel instead.  A CTA's blob
+//    holds its nodes' [L_tt^{-1} packed by diagonals | L_{rows,t} (ld m|1)],
+//    16-byte aligned, for S and M^cc.
 //  * Dense tops: each component's rows are cut into chunks so that the whole
 //    launch has about one CTA per SM.
 struct SolvePlan {
