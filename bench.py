@@ -9,7 +9,9 @@ update + prediction, interface products, implicit solve + correction) of the
 Timing (device, CUDA events on the launching stream):
   * value: K steps, each timed alone, with the 129 MB L2 flushed (a 256 MB
     write) between steps, outside the timed events; the sum of the step times
-    is the timed region.  Per-kernel times come from the same events.
+    is the timed region.  Per-kernel times come from a second pass of as many
+    flushed steps with an event between the explicit kernel and the solve
+    chain as well (imex_step_profile).
   * warm: K consecutive steps without flushes (the state stays L2-resident,
     as in a long simulation).
   * e2e: the public host-I/O call (imex_step_io): every step uploads that
@@ -19,7 +21,9 @@ Timing (device, CUDA events on the launching stream):
     workload, a bounded number of steps after its untimed setup.
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU
 (the method shards into independent problems; no data-path collective): the
-timed region is bracketed by barriers and the max over ranks is taken.
+timed region is bracketed by barriers and the max over ranks is taken.  The
+batched workload's 64 source columns are split between the ranks
+(replicas.shard_columns) and reported over the slowest rank's time.
 """
 import argparse
 import hashlib
