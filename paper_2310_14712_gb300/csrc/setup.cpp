@@ -449,7 +449,17 @@ CsrMat coo_to_csr(int n, std::vector<std::pair<int64_t, double>>& e) {
 
 namespace {
 
-// Multifrontal supernodal Cholesky over the nested-dissection tree.
+// fn(b, e) over [0, n) on the host's threads when the loop carries enough
+// work (about `work` operations in all); serially otherwise.  Every index is
+// computed by the same operations either way.
+void parallel_if(int64_t n, double work, const std::function<void(int64_t, int64_t)>& fn) {
+  if (work < 2e6) fn(0, n);
+  else parallel_for(n, fn);
+}
+
+// Multifrontal supernodal Cholesky over the nested-dissection tree.  The
+// large fronts (the separators near the root) run their independent rows and
+// columns on the host's threads; results do not depend on the thread count.
 std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
   const int n = (int)hs.n_c;
   F.vals.assign(0, 0.0);
@@ -504,20 +514,24 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
       if (!(d > 0.0)) return "implicit system is not positive definite";
       double l = std::sqrt(d);
       Fr[(size_t)j * fm + j] = l;
-      for (int i = j + 1; i < fm; ++i) {
-        double s = Fr[(size_t)i * fm + j];
-        for (int q = 0; q < j; ++q) s -= Fr[(size_t)i * fm + q] * Fr[(size_t)j * fm + q];
-        Fr[(size_t)i * fm + j] = s / l;
-      }
+      parallel_if(fm - j - 1, (double)(fm - j - 1) * j, [&](int64_t i0, int64_t i1) {
+        for (int i = j + 1 + (int)i0; i < j + 1 + (int)i1; ++i) {
+          double s = Fr[(size_t)i * fm + j];
+          for (int q = 0; q < j; ++q) s -= Fr[(size_t)i * fm + q] * Fr[(size_t)j * fm + q];
+          Fr[(size_t)i * fm + j] = s / l;
+        }
+      });
     }
     // Update matrix for the parent: F22 - L21 L21^T (lower part, m x m row-major).
     std::vector<double> U((size_t)m * m, 0.0);
-    for (int a = 0; a < m; ++a)
-      for (int bb = 0; bb <= a; ++bb) {
-        double s = Fr[(size_t)(b + a) * fm + b + bb];
-        for (int q = 0; q < b; ++q) s -= Fr[(size_t)(b + a) * fm + q] * Fr[(size_t)(b + bb) * fm + q];
-        U[(size_t)a * m + bb] = s;
-      }
+    parallel_if(m, 0.5 * m * m * (double)b, [&](int64_t a0, int64_t a1) {
+      for (int a = (int)a0; a < (int)a1; ++a)
+        for (int bb = 0; bb <= a; ++bb) {
+          double s = Fr[(size_t)(b + a) * fm + b + bb];
+          for (int q = 0; q < b; ++q) s -= Fr[(size_t)(b + a) * fm + q] * Fr[(size_t)(b + bb) * fm + q];
+          U[(size_t)a * m + bb] = s;
+        }
+    });
     upd[k] = std::move(U);
     // Store, per supernode, the inverse of its diagonal block and the block
     // below it, each in both layouts so that the forward (row-owner) and the
@@ -525,13 +539,15 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
     //   Linv  = L_tt^{-1}  (b x b, column-major, lower),  LinvT = Linv^T,
     //   L21   = L_{rows,t} (m x b, column-major),         L21T  = L21^T.
     std::vector<double> Li((size_t)b * b, 0.0);
-    for (int k = 0; k < b; ++k) {           // column k of L_tt^{-1}: L x = e_k
-      for (int i = k; i < b; ++i) {
-        double sum = (i == k) ? 1.0 : 0.0;
-        for (int q = k; q < i; ++q) sum -= Fr[(size_t)i * fm + q] * Li[q + (size_t)b * k];
-        Li[i + (size_t)b * k] = sum / Fr[(size_t)i * fm + i];
+    parallel_if(b, (double)b * b * b / 6.0, [&](int64_t k0, int64_t k1) {
+      for (int kc = (int)k0; kc < (int)k1; ++kc) {   // column kc of L_tt^{-1}: L x = e_kc
+        for (int i = kc; i < b; ++i) {
+          double sum = (i == kc) ? 1.0 : 0.0;
+          for (int q = kc; q < i; ++q) sum -= Fr[(size_t)i * fm + q] * Li[q + (size_t)b * kc];
+          Li[i + (size_t)b * kc] = sum / Fr[(size_t)i * fm + i];
+        }
       }
-    }
+    });
     // Dense L_tt (column-major), kept on the host for the dense top-level solve.
     F.ld_off[k] = (int64_t)F.Ld.size();
     F.Ld.resize(F.Ld.size() + (size_t)b * b, 0.0);
@@ -1308,10 +1324,13 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
 
   // ---------------------------------------------------------------- numeric
   {
+    // The factors of S and M^cc are independent: one thread each.
+    std::string errM;
+    std::thread tm([&] { errM = factorize(Mmat, hs, hs.Mcc); });
     std::string err = factorize(Smat, hs, hs.S);
+    tm.join();
     if (!err.empty()) return err;
-    err = factorize(Mmat, hs, hs.Mcc);
-    if (!err.empty()) return "M^cc: " + err;
+    if (!errM.empty()) return "M^cc: " + errM;
     try {
       hs.residual_S = factor_residual(hs, Smat, hs.S);
       hs.residual_M = factor_residual(hs, Mmat, hs.Mcc);
