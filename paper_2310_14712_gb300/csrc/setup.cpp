@@ -1239,8 +1239,10 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
           if (mv != 0.0) em.emplace_back(key, mv);
         }
     }
+    // The two conversions are independent: one thread each.
+    std::thread tmm([&] { Mmat = coo_to_csr(nc, em); });
     Smat = coo_to_csr(nc, es);
-    Mmat = coo_to_csr(nc, em);
+    tmm.join();
     hs.S_ptr = Smat.ptr;
     hs.S_col = Smat.col;
     hs.S_val = Smat.val;
