@@ -129,7 +129,7 @@ def time_flushed_phases(g, steps, stream, flush):
     return total
 
 
-def measure_batched(imex, workloads, steps, stream, flush, rank=0, ws=1):
+def measure_batched(imex, workloads, steps, stream, flush, rank=0, ws=1, device=None):
     """Independent source columns against the single-source form on the same
     geometry: the 16x16-cell plate with 64 seeded sources (one per column).
     With ws ranks the 64 columns are split between them (replicas.shard_columns:
@@ -148,7 +148,7 @@ def measure_batched(imex, workloads, steps, stream, flush, rank=0, ws=1):
         g = imex.Imex.from_workload(w, ncols=len(mine))
         st = g.info()
         g.step(5)
-        ms = reduce_max(time_flushed(g, steps, stream, flush), ws)
+        ms = reduce_max(time_flushed(g, steps, stream, flush), ws, device)
         n_act = st["n_d"] + st["n_c"]
         out[label] = {"value": n_act * ncols * steps / (ms * 1e-3), "ms_per_step": ms / steps,
                       "ncols": ncols, "explicit_variant": EXPLICIT_VARIANTS[st["explicit_variant"]],
@@ -654,7 +654,7 @@ def run_gpu(args):
         "wall_seconds_timed_loop": wall,
     }
     if ws > 1 and not args.no_extras:   # the batched columns split across the ranks
-        line["batched"] = measure_batched(imex, workloads, min(args.steps, 200), stream, flush, rank, ws)
+        line["batched"] = measure_batched(imex, workloads, min(args.steps, 200), stream, flush, rank, ws, device)
     if ws == 1 and not args.no_extras:
         line["batched"] = measure_batched(imex, workloads, min(args.steps, 200), stream, flush)
         line["learned_pcg"] = measure_learned_pcg(imex, w, min(args.steps, 20), stream, flush)
