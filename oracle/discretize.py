@@ -28,7 +28,10 @@ Local node order inside a cell is the same (x fastest).
 Pins: tests/test_oracle_discretize.py — K symmetric with the constant vector
 in its null space, 1^T M 1 equal to the alpha-weighted quadrature volume,
 the single-cell eigenfrequency table of Fig. fillRatioHZ, the cell-wise
-critical time step of Table criticaltimestepsizes, the analytic standing mode.
+critical time step of Table criticaltimestepsizes, the analytic standing mode,
+the load vector against closed-form integrals and against 1^T M u, the
+empty-cell threshold on a 1D cell resolved to 6e-11, K scaling with c^2.
+tests/test_oracle_mutations.py checks that mistakes planted here fail them.
 """
 import itertools
 import numpy as np

@@ -12,6 +12,10 @@ the step is 0.9 times the cell-wise critical step of an uncut cell,
 Multiple sources are independent right-hand sides: each is run as its own
 simulation (plain loop), which is what the batched GPU form must reproduce
 column by column.
+
+Pins (tests/test_oracle_pipeline.py): the time-step rule under wave-speed
+scaling (speed 2 halves dt exactly; the fastest uncut cell decides, cut
+cells do not); the source columns adding up to the run with all sources.
 """
 import numpy as np
 

@@ -10,7 +10,7 @@ The load separates into f(t) = f_t(t) f_x (Sec. Spatial discretization).
 
 Pins: tests/test_oracle_sources.py (closed-form values: Ricker peak 1 at t0,
 zeros at t0 +- 1/(sqrt(2) pi f0); Eq. ft zero at t0 and extremum at t0 -+ sigma_t;
-burst zero beyond n_c / f_s).
+burst zero beyond n_c / f_s and its value inside the second cycle).
 """
 import numpy as np
 

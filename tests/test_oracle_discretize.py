@@ -153,3 +153,61 @@ def test_standing_mode_second_order_in_time():
     e1, _ = _standing_mode_error(6, 5, 0.13, dt_scale=1.0)
     e2, _ = _standing_mode_error(6, 5, 0.13, dt_scale=0.5)
     assert 3.3 < e1 / e2 < 4.5
+
+
+def _load_sum(grid, geom, alpha, depth, f):
+    d = D.discretize(grid, geom, alpha, depth, fx=f)
+    return d, float(d.fx.sum())
+
+
+def test_load_vector_integrates_constant_and_linear_loads():
+    # Eq. f with the basis summing to one: sum_i f_i = int alpha f.  Without
+    # holes that is a closed form (GL integrates f exactly); the box does not
+    # start at the origin, so a wrong map from reference to physical points
+    # shows.  With holes the same quadrature gives 1^T M u / rho for u the
+    # nodal values of f (f in the span of the basis; uncut cells: GL load and
+    # GLL mass are both exact for degree 1; cut cells share M's points).
+    lin = lambda x: x[:, 0] + 2.0 * x[:, 1]
+    one = lambda x: np.ones(len(x))
+    grid = D.Grid((0.5, 0.0), (1.5, 1.0), (4, 3), 3)
+    none = G.Holes(np.zeros((0, 4)), 2)
+    assert _load_sum(grid, none, 1e-5, 3, one)[1] == pytest.approx(1.0, rel=1e-13)
+    # int x0 + 2 x1 over [0.5, 1.5] x [0, 1] = (1.5^2 - 0.5^2) / 2 + 2 * 1/2
+    assert _load_sum(grid, none, 1e-5, 3, lin)[1] == pytest.approx(2.0, rel=1e-13)
+    grid = D.Grid((0.5, 0.0), (1.5, 1.0), (8, 8), 3)
+    holes = G.Holes(np.array([[1.0, 0.5, 0.23, 0.17], [0.62, 0.2, 0.1, 0.1]]), 2)
+    X = grid.node_coords()
+    for f in (one, lin):
+        d, total = _load_sum(grid, holes, 1e-5, 3, f)
+        assert (d.cell_type == G.CUT).sum() > 10
+        u = np.where(d.active, f(X), 0.0)
+        assert total == pytest.approx(float(np.ones(len(X)) @ (d.M @ u)), rel=1e-12)
+
+
+def test_empty_cell_threshold_is_fill_ratio_1e_10():
+    # Sec. 2D example: a cell whose fill ratio is below 1e-10 is discarded.
+    # One 1D cell of unit length cut by the half-space x < eta: a binary tree
+    # of depth 34 puts the boundary in a leaf of length 2^-34 (5.8e-11), so
+    # the quadrature fill is eta to within that.
+    grid = D.Grid((0.0,), (1.0,), (1,), 2)
+    kept = D.discretize(grid, G.HalfSpace(0, 5e-10, 1), 1e-5, 34)
+    assert kept.cell_type[0] == G.CUT and abs(kept.fill[0] - 5e-10) < 6e-11
+    assert kept.active.all()
+    dropped = D.discretize(grid, G.HalfSpace(0, 2e-11, 1), 1e-5, 34)
+    assert dropped.cell_type[0] == G.EMPTY and dropped.fill[0] < 1e-10
+    assert not dropped.active.any()
+
+
+def test_stiffness_scales_with_the_square_of_the_wave_speed():
+    # Eq. K carries rho c^2 and Eq. Mglobal none: a wave speed of 2 in every
+    # cell, given per cell or as c0, multiplies K by 4 (exactly: a power of
+    # two) and leaves M alone, on uncut and cut cells alike.
+    grid = D.Grid((0.0, 0.0), (1.0, 1.0), (6, 6), 3)
+    holes = G.Holes(np.array([[0.5, 0.5, 0.2, 0.2]]), 2)
+    one = D.discretize(grid, holes, 1e-5, 3)
+    per_cell = D.discretize(grid, holes, 1e-5, 3, cell_c=np.full(36, 2.0))
+    as_c0 = D.discretize(grid, holes, 1e-5, 3, c0=2.0)
+    assert (one.cell_type == G.CUT).sum() > 5 and (one.cell_type == G.UNCUT).sum() > 5
+    for d in (per_cell, as_c0):
+        assert abs(d.K - 4.0 * one.K).max() == 0.0
+        assert abs(d.M - one.M).max() == 0.0

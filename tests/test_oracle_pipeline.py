@@ -16,6 +16,7 @@ drifts further from the reference than a reordering does.  Both variants
 bound the rounding floor of the GPU parity tests (tests/parity_util.py).
 """
 import numpy as np
+import pytest
 
 from oracle import pipeline
 from oracle.geometry import Holes
@@ -63,3 +64,39 @@ def test_reversed_quadrature_is_the_same_system_up_to_roundoff():
     phys = Holes(w.holes, 2).physical(s.grid.node_coords()) & s.disc.active
     assert pipeline.relative_l2(b.u, a.u, phys) < 1e-12
     assert pipeline.relative_l2(b.u, a.u, s.disc.active) < 2e-10
+
+
+def test_time_step_rule_takes_the_fastest_uncut_cell():
+    # dt = 0.9 * 2 / sqrt(lambda_max(K_e, M_e)) of an uncut cell at the largest
+    # wave speed among uncut cells.  lambda_max grows with c^2, so a speed of 2
+    # everywhere halves dt (a power of two: exactly), one uncut cell at speed 3
+    # divides it by 3, and a faster cut cell does not count.
+    holes = np.array([[0.5, 0.5, 0.2, 0.2]])
+    kw = dict(dim=2, lo=(0, 0), hi=(1, 1), ncells=(8, 8), p=3, alpha=1e-5, depth=3, holes=holes,
+              src_pos=np.array([[0.2, 0.2]]), f0=5.0, src_sigma=0.05)
+    base = pipeline.setup(**kw)
+    types = base.disc.cell_type
+    c = np.ones(len(types))
+    assert pipeline.setup(**kw, cell_c=c).dt == base.dt
+    assert pipeline.setup(**kw, cell_c=2.0 * c).dt == base.dt / 2
+    c[np.flatnonzero(types == 0)[5]] = 3.0
+    c[np.flatnonzero(types == 1)[0]] = 5.0
+    assert pipeline.setup(**kw, cell_c=c).dt == pytest.approx(base.dt / 3, rel=1e-13)
+
+
+def test_independent_columns_superpose_to_the_multi_source_run():
+    # The method is linear in the load (Fig. TrapCDMIMEX with f = f_t(t) f_x),
+    # and a setup with several bells sums their loads, so the columns of
+    # setup_columns (one source each) must add up to the run with all sources.
+    holes = np.array([[0.5, 0.5, 0.2, 0.2]])
+    pos = np.array([[0.2, 0.2], [0.8, 0.3], [0.25, 0.75]])
+    kw = dict(dim=2, lo=(0, 0), hi=(1, 1), ncells=(8, 8), p=3, alpha=1e-5, depth=3, holes=holes,
+              f0=5.0, src_sigma=0.05)
+    cols = pipeline.setup_columns(pos, **kw)
+    both = pipeline.setup(src_pos=pos, **kw)
+    total = sum(pipeline.run(c, 60).u for c in cols)
+    ref = pipeline.run(both, 60).u
+    assert np.linalg.norm(ref) > 0
+    assert pipeline.relative_l2(total, ref, both.disc.active) < 1e-12
+    # and each column differs from the others (its own source)
+    assert pipeline.relative_l2(pipeline.run(cols[1], 60).u, pipeline.run(cols[0], 60).u) > 0.5

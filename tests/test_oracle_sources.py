@@ -31,6 +31,9 @@ def test_sine_burst():
     assert float(sources.sine_burst(1.0 / fs, fs)) == pytest.approx(0.0, abs=1e-12)
     t = 0.25 / fs
     assert float(sources.sine_burst(t, fs)) == pytest.approx(np.sin(np.pi / 8) ** 2, rel=1e-12)
+    # The second of the two cycles: sin(2 pi 1.25) = 1, envelope sin^2(5 pi / 8).
+    t = 1.25 / fs
+    assert float(sources.sine_burst(t, fs)) == pytest.approx(np.sin(5 * np.pi / 8) ** 2, rel=1e-12)
 
 
 def test_bell_eq_fx():
