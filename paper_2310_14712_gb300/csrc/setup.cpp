@@ -15,6 +15,7 @@
 #include "setup.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -231,6 +232,61 @@ void tensor_basis(const Grid& g, const Lagrange1D& L, const double* xr, double* 
 }
 
 struct QPoint { double xr[3]; double w; bool phys; };
+
+// Quadrature points of one cut cell are taken in batches of kPointBatch; the
+// entries of K_e and M_e are updated kEntryBlock rows at a time.
+constexpr int kPointBatch = 64;
+constexpr int kEntryBlock = 8;
+
+// K_e += sum_j kw_j G_j G_j^T and M_e += sum_j mw_j N_j N_j^T over a batch of
+// nq points (G_j: DIM x Pd physical gradients, N_j: Pd values; column-major
+// Pd x Pd).  Each entry is loaded once per batch and takes the points in
+// order, every term formed as in a point-by-point loop
+// (s = sum_d G_j[d][a] (G_j[d][b] kw_j);  K_ab += s;  M_ab += N_j[a] (N_j[b] mw_j)),
+// so the sums are the same, term by term.
+template <int DIM>
+void accumulate_points(int nq, int Pd, const double* __restrict GB, const double* __restrict NB,
+                       const double* __restrict kw, const double* __restrict mw, double* __restrict gb,
+                       double* __restrict nb, double* __restrict Ke, double* __restrict Me) {
+  const size_t gs = (size_t)3 * Pd;            // stride of one point's gradients
+  for (int b = 0; b < Pd; ++b) {
+    for (int j = 0; j < nq; ++j) {
+      for (int d = 0; d < DIM; ++d) gb[j * DIM + d] = GB[j * gs + (size_t)d * Pd + b] * kw[j];
+      nb[j] = NB[(size_t)j * Pd + b] * mw[j];
+    }
+    double* __restrict kc = Ke + (size_t)Pd * b;
+    double* __restrict mc = Me + (size_t)Pd * b;
+    int a0 = 0;
+    for (; a0 + kEntryBlock <= Pd; a0 += kEntryBlock) {
+      double ka[kEntryBlock], ma[kEntryBlock];
+      for (int i = 0; i < kEntryBlock; ++i) { ka[i] = kc[a0 + i]; ma[i] = mc[a0 + i]; }
+      for (int j = 0; j < nq; ++j) {
+        const double* Gj = GB + j * gs + a0;
+        const double* Nj = NB + (size_t)j * Pd + a0;
+        const double* g = gb + j * DIM;
+        const double n = nb[j];
+        for (int i = 0; i < kEntryBlock; ++i) {
+          double sum = 0.0;
+          for (int d = 0; d < DIM; ++d) sum += Gj[(size_t)d * Pd + i] * g[d];
+          ka[i] += sum;
+          ma[i] += Nj[i] * n;
+        }
+      }
+      for (int i = 0; i < kEntryBlock; ++i) { kc[a0 + i] = ka[i]; mc[a0 + i] = ma[i]; }
+    }
+    for (int a = a0; a < Pd; ++a) {
+      double ka = kc[a], ma = mc[a];
+      for (int j = 0; j < nq; ++j) {
+        double sum = 0.0;
+        for (int d = 0; d < DIM; ++d) sum += GB[j * gs + (size_t)d * Pd + a] * gb[j * DIM + d];
+        ka += sum;
+        ma += NB[(size_t)j * Pd + a] * nb[j];
+      }
+      kc[a] = ka;
+      mc[a] = ma;
+    }
+  }
+}
 
 // Spacetree quadrature of one cut cell: bisect a (sub)cell in every axis while
 // the boundary meets its interior and level < depth; every leaf gets the
@@ -452,6 +508,22 @@ namespace {
 // fn(b, e) over [0, n) on the host's threads when the loop carries enough
 // work (about `work` operations in all); serially otherwise.  Every index is
 // computed by the same operations either way.
+// parallel_for with dynamic scheduling: threads take blocks of `grain`
+// indices from a shared counter, for loops whose iterations differ in cost.
+// fn must write only what belongs to its own indices.
+void parallel_for_dynamic(int64_t n, int64_t grain, const std::function<void(int64_t, int64_t)>& fn) {
+  unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+  nt = (unsigned)std::min<int64_t>(nt, (n + grain - 1) / grain);
+  if (nt <= 1) { fn(0, n); return; }
+  std::atomic<int64_t> next{0};
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&] {
+      for (int64_t b; (b = next.fetch_add(grain)) < n;) fn(b, std::min(n, b + grain));
+    });
+  for (auto& t : th) t.join();
+}
+
 void parallel_if(int64_t n, double work, const std::function<void(int64_t, int64_t)>& fn) {
   if (work < 2e6) fn(0, n);
   else parallel_for(n, fn);
@@ -460,6 +532,76 @@ void parallel_if(int64_t n, double work, const std::function<void(int64_t, int64
 // Multifrontal supernodal Cholesky over the nested-dissection tree.  The
 // large fronts (the separators near the root) run their independent rows and
 // columns on the host's threads; results do not depend on the thread count.
+// Columns of a front are factorised in panels of kPanel.
+constexpr int kPanel = 64;
+
+// Partial Cholesky of the first b columns of a front (fm x fm, row-major,
+// lower part valid): on return columns 0..b-1 hold L and the trailing block
+// holds F22 - L21 L21^T.  Each entry (i, j) is reduced by the products
+// L_iq L_jq one at a time in increasing q, starting from the assembled value,
+// and column j is then divided by L_jj: the column-by-column (dot-product)
+// form, with the same arithmetic per entry.  The order of work differs:
+// within a panel the columns are finished one by one using the panel's own
+// earlier columns, and then every entry to the right of the panel subtracts
+// the panel's products (in increasing q), so each panel is read from cache
+// rather than the whole front for every column.
+std::string partial_cholesky(double* Fr, int fm, int b) {
+  for (int j0 = 0; j0 < b; j0 += kPanel) {
+    const int j1 = std::min(b, j0 + kPanel);
+    for (int j = j0; j < j1; ++j) {
+      double* Rj = Fr + (size_t)j * fm;
+      double d = Rj[j];
+      for (int q = j0; q < j; ++q) d -= Rj[q] * Rj[q];
+      if (!(d > 0.0)) return "implicit system is not positive definite";
+      const double l = std::sqrt(d);
+      Rj[j] = l;
+      for (int i = j + 1; i < fm; ++i) {
+        double* Ri = Fr + (size_t)i * fm;
+        double s = Ri[j];
+        for (int q = j0; q < j; ++q) s -= Ri[q] * Rj[q];
+        Ri[j] = s / l;
+      }
+    }
+    const int ntr = fm - j1;
+    if (ntr <= 0) continue;
+    // Entries right of the panel, row by row, four columns at a time (four
+    // independent sums over the panel's q, each in increasing q).
+    auto rows = [&](int64_t r0, int64_t r1) {
+      for (int i = j1 + (int)r0; i < j1 + (int)r1; ++i) {
+        double* Ri = Fr + (size_t)i * fm;
+        int jj = j1;
+        for (; jj + 4 <= i + 1; jj += 4) {
+          const double* C0 = Fr + (size_t)jj * fm;
+          const double* C1 = C0 + fm;
+          const double* C2 = C1 + fm;
+          const double* C3 = C2 + fm;
+          double s0 = Ri[jj], s1 = Ri[jj + 1], s2 = Ri[jj + 2], s3 = Ri[jj + 3];
+          for (int q = j0; q < j1; ++q) {
+            const double x = Ri[q];
+            s0 -= x * C0[q];
+            s1 -= x * C1[q];
+            s2 -= x * C2[q];
+            s3 -= x * C3[q];
+          }
+          Ri[jj] = s0;
+          Ri[jj + 1] = s1;
+          Ri[jj + 2] = s2;
+          Ri[jj + 3] = s3;
+        }
+        for (; jj <= i; ++jj) {
+          const double* C = Fr + (size_t)jj * fm;
+          double s = Ri[jj];
+          for (int q = j0; q < j1; ++q) s -= Ri[q] * C[q];
+          Ri[jj] = s;
+        }
+      }
+    };
+    if (0.5 * ntr * (double)ntr * (j1 - j0) < 2e6) rows(0, ntr);
+    else parallel_for_dynamic(ntr, 16, rows);
+  }
+  return "";
+}
+
 std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
   const int n = (int)hs.n_c;
   F.vals.assign(0, 0.0);
@@ -507,31 +649,15 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
       }
       std::vector<double>().swap(upd[c]);
     }
-    // Dense partial Cholesky: columns 0..b-1 of the front.
-    for (int j = 0; j < b; ++j) {
-      double d = Fr[(size_t)j * fm + j];
-      for (int q = 0; q < j; ++q) d -= Fr[(size_t)j * fm + q] * Fr[(size_t)j * fm + q];
-      if (!(d > 0.0)) return "implicit system is not positive definite";
-      double l = std::sqrt(d);
-      Fr[(size_t)j * fm + j] = l;
-      parallel_if(fm - j - 1, (double)(fm - j - 1) * j, [&](int64_t i0, int64_t i1) {
-        for (int i = j + 1 + (int)i0; i < j + 1 + (int)i1; ++i) {
-          double s = Fr[(size_t)i * fm + j];
-          for (int q = 0; q < j; ++q) s -= Fr[(size_t)i * fm + q] * Fr[(size_t)j * fm + q];
-          Fr[(size_t)i * fm + j] = s / l;
-        }
-      });
+    // Dense partial Cholesky of columns 0..b-1; the trailing block becomes
+    // the update matrix for the parent, F22 - L21 L21^T (lower part, m x m row-major).
+    {
+      std::string err = partial_cholesky(Fr.data(), fm, b);
+      if (!err.empty()) return err;
     }
-    // Update matrix for the parent: F22 - L21 L21^T (lower part, m x m row-major).
     std::vector<double> U((size_t)m * m, 0.0);
-    parallel_if(m, 0.5 * m * m * (double)b, [&](int64_t a0, int64_t a1) {
-      for (int a = (int)a0; a < (int)a1; ++a)
-        for (int bb = 0; bb <= a; ++bb) {
-          double s = Fr[(size_t)(b + a) * fm + b + bb];
-          for (int q = 0; q < b; ++q) s -= Fr[(size_t)(b + a) * fm + q] * Fr[(size_t)(b + bb) * fm + q];
-          U[(size_t)a * m + bb] = s;
-        }
-    });
+    for (int a = 0; a < m; ++a)
+      for (int bb = 0; bb <= a; ++bb) U[(size_t)a * m + bb] = Fr[(size_t)(b + a) * fm + b + bb];
     upd[k] = std::move(U);
     // Store, per supernode, the inverse of its diagonal block and the block
     // below it, each in both layouts so that the forward (row-owner) and the
@@ -760,9 +886,10 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
       cutF_all((size_t)ncut0 * Pd * ncols);
   std::vector<double> cut_fill(ncut0), cut_lam(ncut0, 0.0);
   if (pb.scheme < kSchemeImex || pb.scheme > kSchemeTrapezoidal) return "unknown time integration scheme";
-  parallel_for(ncut0, [&](int64_t b, int64_t e) {
+  parallel_for_dynamic(ncut0, 8, [&](int64_t b, int64_t e) {
     std::vector<QPoint> pts;
-    std::vector<double> N(Pd), G(3 * Pd);
+    std::vector<double> NB((size_t)kPointBatch * Pd), GB((size_t)kPointBatch * 3 * Pd);
+    std::vector<double> kwB(kPointBatch), mwB(kPointBatch), gbB(kPointBatch * 3), nbB(kPointBatch);
     for (int64_t k = b; k < e; ++k) {
       int64_t cid = cut_cells[k];
       int ci[3] = {0, 0, 0};
@@ -776,29 +903,29 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
       double* Me = cutM_all.data() + (size_t)k * Pd * Pd;
       double* fe = cutF_all.data() + (size_t)k * Pd * ncols;
       const double c = cell_speed(cid);
-      for (const QPoint& q : pts) {
-        wall += q.w;
-        if (q.phys) wphys += q.w;
-        const double al = q.phys ? 1.0 : pb.alpha;
-        const double wq = q.w * jac * al;
-        tensor_basis(g, L1, q.xr, N.data(), G.data());
-        double xp[3];
-        for (int d = 0; d < dim; ++d) xp[d] = clo[d] + (q.xr[d] + 1.0) * 0.5 * g.h[d];
-        double fv[kMaxCols];
-        for (int col = 0; col < ncols; ++col) fv[col] = source_value(pb, xp, col);
-        const double kw = wq * pb.rho * c * c, mw = wq * pb.rho;
-        for (int bcol = 0; bcol < Pd; ++bcol) {
-          double gb[3];
-          for (int d = 0; d < dim; ++d) gb[d] = G[d * Pd + bcol] * kw;
-          const double nb = N[bcol] * mw;
-          for (int a = 0; a < Pd; ++a) {
-            double s = 0.0;
-            for (int d = 0; d < dim; ++d) s += G[d * Pd + a] * gb[d];
-            Ke[a + (size_t)Pd * bcol] += s;
-            Me[a + (size_t)Pd * bcol] += N[a] * nb;
-          }
-          for (int col = 0; col < ncols; ++col) fe[(size_t)col * Pd + bcol] += wq * fv[col] * N[bcol];
+      for (size_t q0 = 0; q0 < pts.size(); q0 += kPointBatch) {
+        const int nq = (int)std::min<size_t>(kPointBatch, pts.size() - q0);
+        for (int j = 0; j < nq; ++j) {
+          const QPoint& q = pts[q0 + j];
+          wall += q.w;
+          if (q.phys) wphys += q.w;
+          const double al = q.phys ? 1.0 : pb.alpha;
+          const double wq = q.w * jac * al;
+          double* N = NB.data() + (size_t)j * Pd;
+          tensor_basis(g, L1, q.xr, N, GB.data() + (size_t)j * 3 * Pd);
+          double xp[3];
+          for (int d = 0; d < dim; ++d) xp[d] = clo[d] + (q.xr[d] + 1.0) * 0.5 * g.h[d];
+          double fv[kMaxCols];
+          for (int col = 0; col < ncols; ++col) fv[col] = source_value(pb, xp, col);
+          kwB[j] = wq * pb.rho * c * c;
+          mwB[j] = wq * pb.rho;
+          for (int bcol = 0; bcol < Pd; ++bcol)
+            for (int col = 0; col < ncols; ++col) fe[(size_t)col * Pd + bcol] += wq * fv[col] * N[bcol];
         }
+        if (dim == 2)
+          accumulate_points<2>(nq, Pd, GB.data(), NB.data(), kwB.data(), mwB.data(), gbB.data(), nbB.data(), Ke, Me);
+        else
+          accumulate_points<3>(nq, Pd, GB.data(), NB.data(), kwB.data(), mwB.data(), gbB.data(), nbB.data(), Ke, Me);
       }
       cut_fill[k] = wphys / wall;
       if (pb.scheme == kSchemeCdmHrz) {
@@ -1025,8 +1152,12 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
             coords[d].push_back(ni[d]);
           }
         }
+        // Axes by decreasing extent; equal extents keep the axis order (a
+        // stable insertion sort of at most three entries).
         int order[3] = {0, 1, 2};
-        std::sort(order, order + dim, [&](int a, int b) { return (mx[a] - mn[a]) > (mx[b] - mn[b]); });
+        for (int a = 1; a < dim; ++a)
+          for (int q = a; q > 0 && (mx[order[q]] - mn[order[q]]) > (mx[order[q - 1]] - mn[order[q - 1]]); --q)
+            std::swap(order[q], order[q - 1]);
         for (int oi = 0; oi < dim && best_ax < 0; ++oi) {
           int ax = order[oi];
           std::vector<int>& cs = coords[ax];
