@@ -1357,6 +1357,7 @@ bool split_active(const imex_ctx* c) {
 // Kernel launches of one step.
 int64_t launches_per_step(const imex_ctx* c) {
   int64_t n = 1;   // explicit apply
+  if (split_active(c) && !scheme_is_cdm(c->hs.pb.scheme)) n += 1;   // its far tiles, on the side stream
   if (c->hs.n_c > 0 && !c->factorized) return n + 2;   // right-hand sides, PCG
   if (c->hs.n_c > 0) {
     for (size_t l = 0; l < c->lev_cta0.size(); ++l) n += (l == 0 || c->lev_ncta[l] > 0) ? 1 : 0;
