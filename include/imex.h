@@ -502,6 +502,24 @@ int imex_host_setup_export(const imex_mesh *mesh, int p, double alpha, double dt
                            imex_stats *stats);
 
 /*
+ * imex_host_implicit_system - run the host setup only (no GPU) and export the
+ * implicit system as the library factorises it (Fig. TrapCDMIMEX,
+ * "Calculation and factorization of system matrix"):
+ * S = M^cc + beta dt^2 K^cc (beta = 1/4) and M^cc on the pattern of S (zeros
+ * where M^cc has no entry), CSR over the c-indices (the library's
+ * nested-dissection order), full symmetric pattern, columns ascending.
+ * Two calls: with s_col == NULL only *n_c and *nnz are written; then, with
+ * *n_c and *nnz as returned, c_node (n_c: the grid node of each c-index),
+ * s_ptr (n_c + 1), s_col (nnz), s_val and m_val (nnz) are filled.  All
+ * arrays are host memory owned by the caller.  Same problem arguments as
+ * imex_setup.  Errors: IMEX_ERR_ARG (NULL sizes, sizes that differ from the
+ * system's on the second call), IMEX_ERR_GEOM, IMEX_ERR_ALLOC.
+ */
+int imex_host_implicit_system(const imex_mesh *mesh, int p, double alpha, double dt,
+                              const imex_source *src, int64_t *n_c, int64_t *nnz, int64_t *c_node,
+                              int64_t *s_ptr, int32_t *s_col, double *s_val, double *m_val);
+
+/*
  * imex_host_element_matrices - run the host discretisation only (no GPU, no
  * factorisation) and return the element matrices of `ncell` cells (flat cell
  * ids, x fastest) as the library assembles them (Sec. Spatial

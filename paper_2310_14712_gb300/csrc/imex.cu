@@ -2392,6 +2392,34 @@ void fill_stats(const HostSetup& hs, imex_stats* st) {
   st->dt_crit_cut_min = hs.dt_crit_cut_min;
 }
 
+int imex_host_implicit_system(const imex_mesh* mesh, int p, double alpha, double dt, const imex_source* src,
+                              int64_t* n_c, int64_t* nnz, int64_t* c_node, int64_t* s_ptr, int32_t* s_col,
+                              double* s_val, double* m_val) {
+  if (!n_c || !nnz) return fail(IMEX_ERR_ARG, "bad arguments");
+  try {
+    Problem pb;
+    if (int rc = build_context(mesh, p, alpha, dt, src, pb)) return rc;
+    HostSetup hs;
+    std::string err = build_setup(pb, hs);
+    if (!err.empty()) return fail(setup_error_code(err), err);
+    const int64_t nc = hs.n_c, nz = (int64_t)hs.S_col.size();
+    if (s_col) {   // the second call: arrays of the sizes the first one returned
+      if (*n_c != nc || *nnz != nz) return fail(IMEX_ERR_ARG, "array sizes differ from the system's");
+      if (!c_node || !s_ptr || !s_val || !m_val) return fail(IMEX_ERR_ARG, "bad arguments");
+      for (int64_t r = 0; r < nc; ++r) c_node[r] = hs.c_node[r];
+      for (int64_t r = 0; r <= nc; ++r) s_ptr[r] = hs.S_ptr[r];
+      std::memcpy(s_col, hs.S_col.data(), (size_t)nz * sizeof(int32_t));
+      std::memcpy(s_val, hs.S_val.data(), (size_t)nz * sizeof(double));
+      std::memcpy(m_val, hs.M_val.data(), (size_t)nz * sizeof(double));
+    }
+    *n_c = nc;
+    *nnz = nz;
+    return IMEX_OK;
+  } catch (const std::exception& ex) {
+    return fail(IMEX_ERR_ALLOC, std::string("host setup failed: ") + ex.what());
+  }
+}
+
 int imex_host_element_matrices(const imex_mesh* mesh, int p, double alpha, const imex_source* src, int ncell,
                                const int64_t* cells, double* K, double* M, int8_t* cell_type) {
   if (ncell < 0 || (ncell > 0 && (!cells || !K || !M))) return fail(IMEX_ERR_ARG, "bad arguments");

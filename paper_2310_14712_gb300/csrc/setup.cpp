@@ -605,7 +605,6 @@ std::string partial_cholesky(double* Fr, int fm, int b) {
 std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
   const int n = (int)hs.n_c;
   F.vals.assign(0, 0.0);
-  F.invdiag.assign(n, 0.0);
   int64_t total = 0;
   for (auto& t : hs.tree) {
     int b = t.end - t.beg, m = (int)t.rows.size();
@@ -689,7 +688,6 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
         LinvT[j + (size_t)b * i] = Li[i + (size_t)b * j];
       }
     for (int j = 0; j < b; ++j) {
-      F.invdiag[t.beg + j] = 1.0 / Fr[(size_t)j * fm + j];
       for (int i = 0; i < m; ++i) {
         L21[i + (size_t)m * j] = Fr[(size_t)(b + i) * fm + j];
         L21T[j + (size_t)b * i] = Fr[(size_t)(b + i) * fm + j];

@@ -68,7 +68,6 @@ struct TreeNode {
 
 struct Factor {
   std::vector<double> vals;    // per tree node: L_tt^{-1}, its transpose, L_{rows,t}, its transpose
-  std::vector<double> invdiag; // 1 / L_ii per c-index
   std::vector<double> Ld;      // per tree node: L_tt itself (column-major), host only
   std::vector<int64_t> ld_off; // offset of each node's L_tt in Ld
 };

@@ -117,12 +117,15 @@ _lib.imex_host_setup_export.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctyp
                                         ctypes.POINTER(Stats)]
 _lib.imex_host_element_matrices.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double,
                                             ctypes.POINTER(Source), ctypes.c_int, _vp, _dp, _dp, _vp]
+_lib.imex_host_implicit_system.argtypes = [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.POINTER(Source), _vp, _vp, _vp, _vp, _vp, _dp, _dp]
 
 # Every symbol include/imex.h declares (checked by the CPU tests).
 EXPORTS = ("imex_setup", "imex_setup_batch", "imex_setup_scheme", "imex_setup_pcg", "imex_adjoint", "imex_set_solver", "imex_pcg_train", "imex_pcg_train_guess", "imex_pcg_set_guess", "imex_pcg_fsai_closed_form", "imex_pcg_status",
            "imex_fsai_kaporin", "imex_step", "imex_step_profile", "imex_step_io", "imex_step_noalloc", "imex_fields", "imex_set_fields", "imex_set_step",
            "imex_set_initial", "imex_info", "imex_check_finite", "imex_last_error", "imex_destroy", "imex_gll_points",
-           "imex_gauss_points", "imex_host_setup_export", "imex_host_element_matrices", "imex_probe_fp64")
+           "imex_gauss_points", "imex_host_setup_export", "imex_host_element_matrices", "imex_host_implicit_system",
+           "imex_probe_fp64")
 
 
 class ImexError(RuntimeError):
@@ -249,6 +252,30 @@ def host_element_matrices(cells, dim, lo, hi, ncells, p, alpha, depth, holes, sr
                                            types.ctypes.data), "imex_host_element_matrices")
     # column-major per cell -> (row, column)
     return K.transpose(0, 2, 1).copy(), M.transpose(0, 2, 1).copy(), types
+
+
+def host_implicit_system(dim, lo, hi, ncells, p, alpha, depth, holes, src_pos, f0, src_sigma,
+                         src_amp=10.0, wavelet=0, rho=1.0, c0=1.0, cell_c=None, dt=0.0, **_):
+    """Host setup only (no GPU): the implicit system S = M^cc + dt^2/4 K^cc
+    and M^cc as the library factorises them, as (c_node, s_ptr, s_col, s_val,
+    m_val) in the library's c-order (CSR)."""
+    m, s, keep = _mesh_source(dim, lo, hi, ncells, depth, holes, rho, c0, cell_c, src_pos, f0,
+                              src_sigma, src_amp, wavelet)
+    n_c = ctypes.c_int64(0)
+    nnz = ctypes.c_int64(0)
+    _check(_lib.imex_host_implicit_system(ctypes.byref(m), p, alpha, dt, ctypes.byref(s), ctypes.byref(n_c),
+                                          ctypes.byref(nnz), None, None, None, None, None),
+           "imex_host_implicit_system")
+    c_node = np.zeros(n_c.value, dtype=np.int64)
+    ptr = np.zeros(n_c.value + 1, dtype=np.int64)
+    col = np.zeros(nnz.value, dtype=np.int32)
+    sv = np.zeros(nnz.value)
+    mv = np.zeros(nnz.value)
+    _check(_lib.imex_host_implicit_system(ctypes.byref(m), p, alpha, dt, ctypes.byref(s), ctypes.byref(n_c),
+                                          ctypes.byref(nnz), c_node.ctypes.data, ptr.ctypes.data, col.ctypes.data,
+                                          sv.ctypes.data_as(_dp), mv.ctypes.data_as(_dp)),
+           "imex_host_implicit_system")
+    return c_node, ptr, col, sv, mv
 
 
 class _TorchAllocator:

@@ -99,3 +99,49 @@ def test_setup_statistics_log_line():
     for k in ("n_d", "n_c", "n_cut", "n_uncut", "n_empty", "nnz_L"):
         assert rec[k] == st[k], k
     assert rec["dt"] == st["dt"] and rec["factorized"] == 1
+
+
+def test_host_setup_per_cell_wave_speed_matches_oracle():
+    # The adjoint's workload: a wave speed per cell in [0.8, 1.2].  The time
+    # step follows the fastest uncut cell, so it differs from the c0 rule.
+    w = workloads.adjoint()
+    st = _compare_partition(w)
+    c_uncut = np.asarray(w.cell_c)[pipeline.setup(**w.kwargs()).disc.cell_type == UNCUT].max()
+    assert c_uncut > 1.05 and st["dt"] < 0.95 * imex.host_setup_export(**{**w.kwargs(), "cell_c": None})[2]["dt"]
+
+
+def _box3d(p):
+    return workloads.Workload("box3d", 3, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (4, 4, 4), p, 1e-5, 2,
+                              np.array([[0.5, 0.45, 0.55, 0.3, 0.25, 0.2]]), np.array([[0.2, 0.3, 0.3]]),
+                              3.0, 0.08, 0)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_host_setup_3d_box_matches_oracle(p):
+    st = _compare_partition(_box3d(p))
+    assert st["n_cut"] > 0 and st["n_d"] > 0
+
+
+@pytest.mark.parametrize("make", [workloads.plate16, lambda: _box3d(3)], ids=["plate16", "box3d_p3"])
+def test_host_implicit_system_matches_oracle(make):
+    # S = M^cc + beta dt^2 K^cc as the library factorises it (Fig.
+    # TrapCDMIMEX) against the oracle's assembled M and K restricted to I_c,
+    # entry by entry in the library's c-order; the two assemble the same
+    # quadrature sums in different orders (roundoff, 1e-12 of the largest entry).
+    import scipy.sparse as sp
+    w = make()
+    c_node, ptr, col, sv, mv = imex.host_implicit_system(**w.kwargs())
+    s = pipeline.setup(**w.kwargs())
+    d = s.disc
+    assert np.array_equal(np.sort(c_node), np.flatnonzero(d.is_c))        # the c-set, any order
+    n = len(c_node)
+    S_lib = sp.csr_matrix((sv, col, ptr), shape=(n, n))
+    M_lib = sp.csr_matrix((mv, col, ptr), shape=(n, n))
+    M_ref = sp.csr_matrix(d.M)[c_node][:, c_node]
+    S_ref = M_ref + 0.25 * s.dt * s.dt * sp.csr_matrix(d.K)[c_node][:, c_node]
+    for lib, ref in ((S_lib, S_ref), (M_lib, M_ref)):
+        scale = abs(ref).max()
+        assert abs(lib - ref).max() <= 1e-12 * scale
+    # the pattern: columns ascending in every row and symmetric
+    assert all(np.all(np.diff(col[ptr[r]:ptr[r + 1]]) > 0) for r in range(n))
+    assert abs(S_lib - S_lib.T).max() <= 1e-14 * abs(S_lib).max()
