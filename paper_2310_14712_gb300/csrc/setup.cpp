@@ -18,9 +18,11 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
 #include <functional>
 #include <limits>
+#include <mutex>
 #include <numeric>
 #include <thread>
 
@@ -604,23 +606,40 @@ std::string partial_cholesky(double* Fr, int fm, int b) {
 
 std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
   const int n = (int)hs.n_c;
-  F.vals.assign(0, 0.0);
-  int64_t total = 0;
-  for (auto& t : hs.tree) {
-    int b = t.end - t.beg, m = (int)t.rows.size();
+  const int nnode = (int)hs.tree.size();
+  // Offsets of every node's blocks, in node order (the layout does not depend
+  // on the order in which the fronts are computed).
+  int64_t total = 0, ld_total = 0;
+  F.ld_off.assign(nnode, 0);
+  for (int k = 0; k < nnode; ++k) {
+    const TreeNode& t = hs.tree[k];
+    const int b = t.end - t.beg, m = (int)t.rows.size();
     total += 2LL * b * b + 2LL * m * b;
+    F.ld_off[k] = ld_total;
+    ld_total += (int64_t)b * b;
   }
   F.vals.assign(total, 0.0);
-  F.Ld.clear();
-  F.ld_off.assign(hs.tree.size(), 0);
-  std::vector<std::vector<double>> upd(hs.tree.size());
-  std::vector<std::vector<int>> children(hs.tree.size());
-  for (size_t k = 0; k < hs.tree.size(); ++k)
-    if (hs.tree[k].parent >= 0) children[hs.tree[k].parent].push_back((int)k);
-  std::vector<int> pos(n, -1);
-  for (size_t k = 0; k < hs.tree.size(); ++k) {
-    TreeNode& t = hs.tree[k];
+  F.Ld.assign(ld_total, 0.0);
+  std::vector<std::vector<double>> upd(nnode);
+  std::vector<std::vector<int>> children(nnode);
+  for (int k = 0; k < nnode; ++k)
+    if (hs.tree[k].parent >= 0) children[hs.tree[k].parent].push_back(k);
+
+  // One front: assemble it from A and the children's update matrices (in the
+  // children's order), factorise its b pivot columns, leave its own update
+  // matrix in upd[k] and store its blocks.  pos (n entries, all -1 on entry
+  // and on return) maps c-indices to front positions.
+  auto front = [&](int k, std::vector<int>& pos) -> std::string {
+    const TreeNode& t = hs.tree[k];
     const int b = t.end - t.beg, m = (int)t.rows.size(), fm = b + m;
+    struct Reset {   // clears the front's entries of pos on every return
+      std::vector<int>& pos;
+      const TreeNode& t;
+      ~Reset() {
+        for (int i = t.beg; i < t.end; ++i) pos[i] = -1;
+        for (int r : t.rows) pos[r] = -1;
+      }
+    } reset{pos, t};
     std::vector<double> Fr((size_t)fm * fm, 0.0);  // row-major frontal matrix (lower part)
     for (int i = 0; i < b; ++i) pos[t.beg + i] = i;
     for (int i = 0; i < m; ++i) pos[t.rows[i]] = b + i;
@@ -674,10 +693,9 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
       }
     });
     // Dense L_tt (column-major), kept on the host for the dense top-level solve.
-    F.ld_off[k] = (int64_t)F.Ld.size();
-    F.Ld.resize(F.Ld.size() + (size_t)b * b, 0.0);
+    double* Ld = F.Ld.data() + F.ld_off[k];
     for (int j = 0; j < b; ++j)
-      for (int i = j; i < b; ++i) F.Ld[F.ld_off[k] + i + (size_t)b * j] = Fr[(size_t)i * fm + j];
+      for (int i = j; i < b; ++i) Ld[i + (size_t)b * j] = Fr[(size_t)i * fm + j];
     double* Linv = F.vals.data() + t.off_diag;
     double* LinvT = F.vals.data() + t.off_diagT;
     double* L21 = F.vals.data() + t.off_rect;
@@ -693,10 +711,50 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
         L21T[j + (size_t)b * i] = Fr[(size_t)(b + i) * fm + j];
       }
     }
-    for (int i = 0; i < b; ++i) pos[t.beg + i] = -1;
-    for (int i = 0; i < m; ++i) pos[t.rows[i]] = -1;
+    return "";
+  };
+
+  // Fronts of different subtrees are independent: worker threads take any
+  // front whose children are done (a front's arithmetic does not depend on
+  // when it runs, so the factor is the same as in postorder).  After an
+  // error no new front starts; the error of the lowest node reported wins.
+  std::vector<int> pending(nnode), ready;
+  for (int k = 0; k < nnode; ++k) {
+    pending[k] = (int)children[k].size();
+    if (pending[k] == 0) ready.push_back(k);
   }
-  return "";
+  std::mutex mu;
+  std::condition_variable cv;
+  int done = 0, err_node = nnode;
+  bool stop = false;
+  std::string err_msg;
+  auto worker = [&] {
+    std::vector<int> pos(n, -1);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+      cv.wait(lk, [&] { return stop || done == nnode || !ready.empty(); });
+      if (stop || done == nnode) return;
+      const int k = ready.back();
+      ready.pop_back();
+      lk.unlock();
+      std::string e = front(k, pos);
+      lk.lock();
+      ++done;
+      if (!e.empty()) {
+        stop = true;
+        if (k < err_node) { err_node = k; err_msg = e; }
+      } else if (hs.tree[k].parent >= 0 && --pending[hs.tree[k].parent] == 0) {
+        ready.push_back(hs.tree[k].parent);
+      }
+      cv.notify_all();
+    }
+  };
+  const unsigned nt = (unsigned)std::max(1, std::min<int>(nnode, (int)std::max(1u, std::thread::hardware_concurrency())));
+  std::vector<std::thread> th;
+  for (unsigned i = 1; i < nt; ++i) th.emplace_back(worker);
+  worker();
+  for (auto& x : th) x.join();
+  return err_msg;
 }
 
 }  // namespace
