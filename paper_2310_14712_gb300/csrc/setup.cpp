@@ -20,6 +20,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
+#include <exception>
 #include <functional>
 #include <limits>
 #include <mutex>
@@ -462,18 +463,43 @@ double gen_max_eig(const double* K, const double* M, int n) {
   return m;
 }
 
+// The first exception thrown on any of several threads, rethrown by the
+// thread that joins them (an exception must not leave a std::thread).
+struct FirstError {
+  std::mutex mu;
+  std::exception_ptr first;
+  template <class F>
+  void run(F&& f) {
+    try {
+      f();
+    } catch (...) {
+      std::lock_guard<std::mutex> lock(mu);
+      if (!first) first = std::current_exception();
+    }
+  }
+  bool failed() {
+    std::lock_guard<std::mutex> lock(mu);
+    return (bool)first;
+  }
+  void rethrow() {
+    if (first) std::rethrow_exception(first);
+  }
+};
+
 void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& fn) {
   unsigned nt = std::max(1u, std::thread::hardware_concurrency());
   nt = (unsigned)std::min<int64_t>(nt, std::max<int64_t>(1, n / 16));
   if (nt <= 1) { fn(0, n); return; }
   std::vector<std::thread> th;
+  FirstError err;
   int64_t chunk = (n + nt - 1) / nt;
   for (unsigned t = 0; t < nt; ++t) {
     int64_t b = t * chunk, e = std::min<int64_t>(n, b + chunk);
     if (b >= e) break;
-    th.emplace_back(fn, b, e);
+    th.emplace_back([&fn, &err, b, e] { err.run([&] { fn(b, e); }); });
   }
   for (auto& t : th) t.join();
+  err.rethrow();
 }
 
 // Sparse symmetric matrix on the implicit partition, rows sorted (full pattern).
@@ -519,11 +545,15 @@ void parallel_for_dynamic(int64_t n, int64_t grain, const std::function<void(int
   if (nt <= 1) { fn(0, n); return; }
   std::atomic<int64_t> next{0};
   std::vector<std::thread> th;
+  FirstError err;
   for (unsigned t = 0; t < nt; ++t)
     th.emplace_back([&] {
-      for (int64_t b; (b = next.fetch_add(grain)) < n;) fn(b, std::min(n, b + grain));
+      err.run([&] {
+        for (int64_t b; !err.failed() && (b = next.fetch_add(grain)) < n;) fn(b, std::min(n, b + grain));
+      });
     });
   for (auto& t : th) t.join();
+  err.rethrow();
 }
 
 void parallel_if(int64_t n, double work, const std::function<void(int64_t, int64_t)>& fn) {
@@ -719,6 +749,7 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
   // when it runs, so the factor is the same as in postorder).  After an
   // error no new front starts; the error of the lowest node reported wins.
   std::vector<int> pending(nnode), ready;
+  ready.reserve(nnode);   // pushes under the lock never allocate
   for (int k = 0; k < nnode; ++k) {
     pending[k] = (int)children[k].size();
     if (pending[k] == 0) ready.push_back(k);
@@ -728,6 +759,7 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
   int done = 0, err_node = nnode;
   bool stop = false;
   std::string err_msg;
+  FirstError thrown;
   auto worker = [&] {
     std::vector<int> pos(n, -1);
     std::unique_lock<std::mutex> lk(mu);
@@ -737,7 +769,9 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
       const int k = ready.back();
       ready.pop_back();
       lk.unlock();
-      std::string e = front(k, pos);
+      std::string e;
+      thrown.run([&] { e = front(k, pos); });
+      if (e.empty() && thrown.failed()) e = "exception";
       lk.lock();
       ++done;
       if (!e.empty()) {
@@ -751,9 +785,10 @@ std::string factorize(const CsrMat& A, HostSetup& hs, Factor& F) {
   };
   const unsigned nt = (unsigned)std::max(1, std::min<int>(nnode, (int)std::max(1u, std::thread::hardware_concurrency())));
   std::vector<std::thread> th;
-  for (unsigned i = 1; i < nt; ++i) th.emplace_back(worker);
-  worker();
+  for (unsigned i = 1; i < nt; ++i) th.emplace_back([&] { thrown.run(worker); });
+  thrown.run(worker);
   for (auto& x : th) x.join();
+  thrown.rethrow();
   return err_msg;
 }
 
@@ -1427,9 +1462,11 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
         }
     }
     // The two conversions are independent: one thread each.
-    std::thread tmm([&] { Mmat = coo_to_csr(nc, em); });
-    Smat = coo_to_csr(nc, es);
+    FirstError err;
+    std::thread tmm([&] { err.run([&] { Mmat = coo_to_csr(nc, em); }); });
+    err.run([&] { Smat = coo_to_csr(nc, es); });
     tmm.join();
+    err.rethrow();
     hs.S_ptr = Smat.ptr;
     hs.S_col = Smat.col;
     hs.S_val = Smat.val;
@@ -1514,10 +1551,12 @@ std::string build_setup(const Problem& pbin, HostSetup& hs) {
   // ---------------------------------------------------------------- numeric
   {
     // The factors of S and M^cc are independent: one thread each.
-    std::string errM;
-    std::thread tm([&] { errM = factorize(Mmat, hs, hs.Mcc); });
-    std::string err = factorize(Smat, hs, hs.S);
+    std::string err, errM;
+    FirstError thrown;
+    std::thread tm([&] { thrown.run([&] { errM = factorize(Mmat, hs, hs.Mcc); }); });
+    thrown.run([&] { err = factorize(Smat, hs, hs.S); });
     tm.join();
+    thrown.rethrow();
     if (!err.empty()) return err;
     if (!errM.empty()) return "M^cc: " + errM;
     try {
