@@ -100,3 +100,34 @@ def test_independent_columns_superpose_to_the_multi_source_run():
     assert pipeline.relative_l2(total, ref, both.disc.active) < 1e-12
     # and each column differs from the others (its own source)
     assert pipeline.relative_l2(pipeline.run(cols[1], 60).u, pipeline.run(cols[0], 60).u) > 0.5
+
+
+def test_imex_stability_limit_on_the_plate_is_the_explicit_subsystems():
+    # Sec. Spring-coupled masses (Fig. springCoupledMassesElastic) shows the
+    # IMEX step limited by the explicit DOFs alone; the same holds on the
+    # immersed plate: with the critical step of the explicit subsystem,
+    # 2 / sqrt(lambda_max(K^dd, M^dd)), the potential energy u^T K u of a
+    # seeded random start (no load) stays bounded over 600 steps at 0.99 of
+    # it and grows without bound at 1.01.  The cell-wise step of the time
+    # step rule is a lower bound of that limit (element eigenvalue bound).
+    import scipy.linalg as sl
+    import scipy.sparse as sp
+    w = workloads.plate16()
+    s = pipeline.setup(**{**w.kwargs(), "src_amp": 0.0})
+    d = s.disc
+    Id = np.flatnonzero(d.is_d)
+    K = sp.csr_matrix(d.K)
+    mdd = sp.csr_matrix(d.M)[Id][:, Id].diagonal()
+    Kdd = K[Id][:, Id].toarray()
+    dt_x = 2.0 / np.sqrt(sl.eigh(Kdd / np.sqrt(np.outer(mdd, mdd)), eigvals_only=True)[-1])
+    dt_cell = s.dt / 0.9
+    assert 0.99 * dt_x < dt_cell <= dt_x
+    u0 = np.where(d.active, np.random.default_rng(3).standard_normal(len(d.active)), 0.0)
+    growth = {}
+    for fac in (0.99, 1.01):
+        e = []
+        NewmarkImex(d.M, d.K, d.fx, lambda t: 0.0, fac * dt_x, d.is_c, d.is_d).run(
+            600, u0=u0, callback=lambda st: e.append(float(st.u @ (K @ st.u))))
+        growth[fac] = max(e) / max(e[:50])
+    assert growth[0.99] < 1.5
+    assert growth[1.01] > 1e20
