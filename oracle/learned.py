@@ -132,19 +132,6 @@ def pcg(A, b, x0=None, apply_minv=None, tol=1e-10, maxit=1000):
     return x, maxit, float(np.linalg.norm(r) / nb)
 
 
-def train_fsai(indptr, indices, vals0, R, X, epochs, lr):
-    """Plain full-batch Adam on the FSAI loss; returns vals and the loss history."""
-    vals = np.array(vals0, dtype=np.float64)
-    m = np.zeros_like(vals)
-    v = np.zeros_like(vals)
-    hist = []
-    for t in range(1, epochs + 1):
-        loss, g = fsai_loss_grad(indptr, indices, vals, R, X)
-        hist.append(loss)
-        vals, m, v = adam_step(vals, g, m, v, t, lr)
-    return vals, hist
-
-
 def kaporin_loss_grad(S, indptr, indices, vals):
     """K(G) = tr(G^T S G) - 2 sum_i log G_ii and its gradient on the pattern:
     tr(G^T S G) = sum over the pattern of G_ij (S G)_ij, gradient 2 (S G)_ij

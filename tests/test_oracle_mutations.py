@@ -9,8 +9,10 @@ the unchanged copy must pass first, so that a failure really comes from the
 planted mistake.
 
 Mistakes that change nothing the method computes are not listed: swapping
-the order of the gradient components of the basis (K sums over them), or a
-floor on the trained diagonal of G that the training never reaches.
+the order of the gradient components of the basis (K sums over them), a
+floor on the trained diagonal of G that the training never reaches, or a
+constant factor per parameter in the gradient that Adam receives (its step
+divides the factor out).
 """
 import concurrent.futures as cf
 import os
